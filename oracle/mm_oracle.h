@@ -1,0 +1,37 @@
+/* mm_oracle.h -- plain FP64 CPU oracle (test infrastructure only; see mm_oracle.c). */
+#ifndef MM_ORACLE_H
+#define MM_ORACLE_H
+#include <stdint.h>
+
+typedef struct {
+    double sigma;        /* total convergence sigma = sigma_c + sigma_* (Eq. sigma) */
+    double gamma;        /* external shear */
+    double smooth_frac;  /* s = sigma_c / sigma */
+    double side;         /* source-plane side L, Einstein radii */
+    int32_t npix_side;   /* N_side; the map has N_side^2 pixels */
+    double nrays;        /* N_rays: mean rays per pixel without lensing */
+    double margin;       /* shot rectangle = margin x (L/|a|, L/|b|) per side */
+} orc_params;
+
+typedef struct {
+    double pix, delta, width, height;
+    int64_t nx, ny;
+} orc_geometry_t;
+
+int orc_geometry(const orc_params *P, orc_geometry_t *G);
+
+/* Map over the ray sub-rectangle [i0,i1) x [j0,j1) of the global grid, taking every
+ * `stride`-th ray in each direction (i0 < 0: the whole grid). counts has N_side^2
+ * entries; totals = {shot, in, out}. */
+int orc_map(const orc_params *P, const double *lx, const double *ly, const double *lm, int64_t nstar,
+            int64_t i0, int64_t i1, int64_t j0, int64_t j1, int64_t stride,
+            uint32_t *counts, uint64_t totals[3], int nthreads);
+
+/* Per-ray deflection alpha[2k..2k+1], source position ysrc[2k..2k+1] and flat pixel
+ * (or -1) of rays (ray_i[k], ray_j[k]). */
+int orc_rays(const orc_params *P, const double *lx, const double *ly, const double *lm, int64_t nstar,
+             const int64_t *ray_i, const int64_t *ray_j, int64_t n,
+             double *alpha, double *ysrc, int64_t *pixel, int nthreads);
+
+int orc_max_threads(void);
+#endif

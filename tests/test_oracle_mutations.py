@@ -1,0 +1,45 @@
+"""Each plausible mistake planted in a copy of the oracle must fail at least one pin.
+
+The copy is built in a temporary directory on the CPU; the real oracle is
+never modified. This shows that the pins in test_oracle_pins.py constrain
+every term of the lens equation, the lattice, the binning and the layout.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTATIONS = [
+    ("smooth term sign", "- sigma_c * x1 - a1", "+ sigma_c * x1 - a1"),
+    ("shear dropped on axis 1", "(1.0 - P->gamma) * x1", "(1.0) * x1"),
+    ("shear sign on axis 2", "(1.0 + P->gamma) * x2", "(1.0 - P->gamma) * x2"),
+    ("mass ignored", "s1 += lm[i] * d1 / r2;", "s1 += d1 / r2;"),
+    ("lattice offset", "(double)i + 0.5 - 0.5", "(double)i - 0.5"),
+    ("round instead of floor", "floor((y1 + 0.5 * P->side) / G->pix)", "floor((y1 + 0.5 * P->side) / G->pix + 0.5)"),
+    ("transposed map", "return (int64_t)u2 * P->npix_side + (int64_t)u1;", "return (int64_t)u1 * P->npix_side + (int64_t)u2;"),
+    ("deflection sign", "double y1 = (1.0 - P->gamma) * x1 - sigma_c * x1 - a1;",
+     "double y1 = (1.0 - P->gamma) * x1 - sigma_c * x1 + a1;"),
+    ("r^2 typo", "double r2 = d1 * d1 + d2 * d2;", "double r2 = d1 * d1 + d1 * d2;"),
+    ("ray spacing", "G->delta = G->pix / sqrt(P->nrays);", "G->delta = G->pix / P->nrays;"),
+    ("grid size", "G->nx = (int64_t)ceil(G->width / G->delta);", "G->nx = (int64_t)floor(G->width / G->delta);"),
+    ("wrong component", "s2 += lm[i] * d2 / r2;", "s2 += lm[i] * d1 / r2;"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_planted_mistake(tmp_path, name, old, new):
+    for d in ("oracle", "synth", "tests"):
+        shutil.copytree(os.path.join(ROOT, d), tmp_path / d,
+                        ignore=shutil.ignore_patterns("_build", "__pycache__", "*.so"))
+    src = tmp_path / "oracle" / "mm_oracle.c"
+    text = src.read_text()
+    assert text.count(old) == 1, f"mutation site not found: {old}"
+    src.write_text(text.replace(old, new))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        "tests/test_oracle_pins.py"], cwd=tmp_path, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1, f"planted mistake '{name}' was not caught:\n{r.stdout[-2000:]}"
+    assert "FAILED" in r.stdout
