@@ -1,0 +1,264 @@
+/*
+ * mm.h -- C ABI of the GB300 (sm_103a) microlensing magnification-map library.
+ *
+ * The library computes magnification maps by direct inverse ray-shooting:
+ * every ray of a regular image-plane grid is deflected by all N* point
+ * lenses, the smooth-matter and shear terms of the lens equation are added,
+ * and the ray is counted into the source-plane pixel where it lands.
+ *
+ *   Lens equation (Sect. 2, Eq. sigma):
+ *     y = diag(1 - gamma, 1 + gamma) x - sigma_c x - sum_i m_i (x - x_i) / |x - x_i|^2
+ *     sigma = sigma_c + sigma_*, smooth fraction s = sigma_c / sigma (Sect. 3.1).
+ *   Estimator (Sect. 2): mu_ij = N_ij / N_rays, N_rays = mean rays per pixel
+ *     without lensing.
+ *   Number of lenses (Sect. 2, Eq. nstar): N* = sigma_* A / (pi <M>), A = pi R^2.
+ *   Shooting grid (Sect. 3.2.2, Eq. square): L_pm = L / (1 - sigma -+ gamma).
+ *
+ * Conventions for every entry point:
+ *   - Returns MM_OK (0) or a negative MM_E* code; no exception or signal
+ *     crosses the ABI; mm_strerror() names the code, mm_last_error() gives
+ *     a message for the last failure on the calling thread.
+ *   - The caller owns every host buffer it passes; the library never keeps a
+ *     pointer to one after the call returns and never frees one.
+ *   - The library owns every device object behind an opaque handle
+ *     (mm_lenses, mm_map, mm_req) until the matching mm_release_* call or
+ *     mm_destroy. Handles are never reused within a context.
+ *   - One context is driven from one host thread, except mm_poll, which may
+ *     be called from any thread.
+ *   - Every kernel runs on the context's CUDA stream (given to mm_init).
+ *
+ * Geometry readings (where the paper is silent): the shot rectangle is
+ * `shoot_margin` times (L/|1-sigma-gamma|, L/|1-sigma+gamma|), centred on
+ * the origin; rays form a square lattice of spacing Delta = p / sqrt(N_rays)
+ * (p = L / N_side), nx = ceil(W / Delta), ny = ceil(H / Delta), ray (i, j)
+ * at ((i + 1/2 - nx/2) Delta, (j + 1/2 - ny/2) Delta); pixel
+ * (I, J) = (floor((y1 + L/2)/p), floor((y2 + L/2)/p)), stored at
+ * counts[J * N_side + I]; a ray outside [0, N_side)^2, non-finite, or
+ * exactly on a lens is counted as "out".
+ */
+#ifndef MM_H
+#define MM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define MM_OK          0
+#define MM_EINVAL     -1   /* malformed argument or ill-posed map */
+#define MM_ENOMEM     -2   /* over the context's HBM budget, or device allocation failed */
+#define MM_EBUSY      -3   /* request queue full */
+#define MM_ENOTFOUND  -4   /* unknown or released handle */
+#define MM_ETIMEDOUT  -5   /* mm_wait ran out of time (the request is still live) */
+#define MM_EDEVICE    -6   /* CUDA error; the context should be destroyed */
+#define MM_EAGAIN     -7   /* request not finished yet */
+#define MM_ECANCELED  -8   /* request cancelled before it ran */
+
+/* ---- enums ------------------------------------------------------------ */
+#define MM_FP32C  0   /* FP32 deflection sum, tile-relative coordinates, compensated
+                         accumulation, FP64 near-lens terms, float-float epilogue */
+#define MM_FP64   1   /* plain FP64 everywhere */
+
+#define MM_MASS_UNIT       0   /* m_i = 1 */
+#define MM_MASS_LOGNORMAL  1   /* m_i = exp(mass_mu + mass_s z), z ~ N(0, 1) */
+
+typedef struct mm_ctx mm_ctx;
+typedef uint64_t mm_lenses;   /* 0 is never a valid handle */
+typedef uint64_t mm_map;
+typedef uint64_t mm_req;
+
+/* Map request, in the paper's terms (Sect. 2 and 3.1). */
+typedef struct {
+    double   sigma;          /* total convergence sigma (Eq. sigma) */
+    double   gamma;          /* external shear gamma */
+    double   smooth_frac;    /* s = sigma_c / sigma, in [0, 1] */
+    double   side_re;        /* source-plane side L in Einstein radii of a unit mass, > 0 */
+    int32_t  npix_side;      /* N_side, 1 .. 32768; N_pix = N_side^2 */
+    double   nrays_per_pix;  /* N_rays > 0: mean rays per pixel without lensing */
+    double   shoot_margin;   /* shot rectangle per side / mapped-back source side; <= 0 means 1.5 */
+    int32_t  precision;      /* MM_FP32C or MM_FP64 */
+    int64_t  nstar;          /* N*; < 0: derived (Eq. nstar with the disc rule below) */
+    double   disc_radius;    /* lens-disc radius R; <= 0: derived */
+    int32_t  mass_model;     /* MM_MASS_UNIT or MM_MASS_LOGNORMAL */
+    double   mass_mu;        /* lognormal mu */
+    double   mass_s;         /* lognormal s */
+    uint64_t seed;           /* lens-field seed (SplitMix64 streams) */
+    int64_t  ray_rect[4];    /* [i0, i1, j0, j1) sub-rectangle of the global ray grid, or
+                                all -1 for the whole grid (tests and windowed runs) */
+} mm_params;
+
+/* Lens-field derivation used by mm_create_lenses when nstar < 0 or
+ * disc_radius <= 0 (reading of Sect. 2, after Eq. nstar: lenses fill a
+ * circle wider than the mapped-back source region):
+ *   R  = (shoot_margin / 2) * hypot(L/|1-sigma-gamma|, L/|1-sigma+gamma|) + 2,
+ *   N* = round(sigma_* R^2 / <M>),   sigma_* = (1 - s) sigma,
+ * and, when only N* is given, R = sqrt(N* <M> / sigma_*).
+ * <M> = 1 (unit) or exp(mass_mu + mass_s^2 / 2) (lognormal). */
+
+typedef struct {
+    uint64_t rays_shot;     /* rays of the (sub-)grid shot: nx * ny, or the rectangle's area */
+    uint64_t rays_in;       /* rays counted into the map */
+    uint64_t rays_out;      /* rays outside the map, non-finite or on a lens */
+    uint64_t interactions;  /* rays_shot * N* */
+    uint64_t nx, ny;        /* global ray-grid size */
+    int64_t  nstar;
+    double   seconds;       /* device time of the map's shoot, CUDA events (0 if unknown) */
+    double   mu_mean;       /* rays_in / (N_side^2 N_rays) */
+} mm_stats;
+
+typedef struct {
+    double  pix;        /* p = L / N_side */
+    double  delta;      /* lattice spacing p / sqrt(N_rays) */
+    double  width;      /* shot rectangle W */
+    double  height;     /* shot rectangle H */
+    int64_t nx, ny;     /* global ray-grid size */
+    int64_t nstar;      /* N* after derivation */
+    double  disc_radius;
+    double  mu_theory;  /* 1 / ((1 - sigma)^2 - gamma^2), Eq. mutheory */
+} mm_geometry;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`. hbm_budget_bytes caps the device
+ * memory the context may hold (0: 90 % of the free memory at init).
+ * cuda_stream is a cudaStream_t (for example torch.cuda.current_stream()
+ * .cuda_stream) or NULL for a stream the library creates. *out receives the
+ * context. Errors: MM_EINVAL (out NULL, bad device), MM_EDEVICE. */
+int mm_init(mm_ctx **out, int device, size_t hbm_budget_bytes, void *cuda_stream);
+
+/* Wait for all work, release every object and the context. NULL is a no-op. */
+int mm_destroy(mm_ctx *ctx);
+
+/* ---- parameters and geometry (host only, no device work) -------------- */
+
+/* Fill *p with the defaults: margin 1.5, MM_FP32C, derived N* and R, unit
+ * masses, seed 1, whole grid. Physical fields are zero and must be set. */
+int mm_params_default(mm_params *p);
+
+/* Validate *p and compute its geometry and derived lens-field size.
+ * Errors: MM_EINVAL (|1-sigma-+gamma| < 1e-3, side <= 0, N_side outside
+ * 1..32768, N_rays <= 0, smooth_frac outside [0, 1], bad enums, ray_rect
+ * outside the grid). */
+int mm_geometry_of(const mm_params *p, mm_geometry *g);
+
+/* ---- lens sets ---------------------------------------------------------- */
+
+/* Generate a seeded lens field on the host in FP64 (N* and R per the rule
+ * above; positions uniform in the disc by rejection sampling from the
+ * SplitMix64 stream seeded from p->seed; unit or lognormal masses), copy it
+ * to the device once, and build the FP32 tile copies there. Errors:
+ * MM_EINVAL, MM_ENOMEM (over budget), MM_EDEVICE. */
+int mm_create_lenses(mm_ctx *ctx, const mm_params *p, mm_lenses *out);
+
+/* The same from caller arrays x[n], y[n], m[n] (FP64, Einstein radii and
+ * unit masses); n may be 0. The arrays are copied before return. */
+int mm_create_lenses_from(mm_ctx *ctx, const double *x, const double *y, const double *m,
+                          int64_t n, mm_lenses *out);
+
+/* Copy a lens set back to caller arrays of n entries each (n must equal the
+ * set's size; any pointer may be NULL to skip that array). */
+int mm_lenses_fetch(mm_ctx *ctx, mm_lenses h, double *x, double *y, double *m, int64_t n);
+
+/* Number of lenses in a set. */
+int mm_lenses_count(mm_ctx *ctx, mm_lenses h, int64_t *n);
+
+int mm_release_lenses(mm_ctx *ctx, mm_lenses h);
+
+/* ---- synchronous shooting ---------------------------------------------- */
+
+/* Shoot one map (Sect. 2, inverse ray-shooting) with lens set `lenses` (0:
+ * generate one from *p, owned by the map) and return its handle when the
+ * map is complete on the device. The uint32 counts stay in HBM until
+ * mm_map_fetch / mm_release_map. Errors: MM_EINVAL, MM_ENOTFOUND,
+ * MM_ENOMEM, MM_EDEVICE. */
+int mm_shoot(mm_ctx *ctx, mm_lenses lenses, const mm_params *p, mm_map *out);
+
+/* Shoot n maps in ONE persistent launch (maps of different shapes, N* and
+ * precision=MM_FP32C share the launch; work is split into ray tiles that the
+ * CTAs take from a device counter). lenses[k] may be 0 (generated from
+ * params[k]). Each map's result is bit-identical to shooting it alone.
+ * maps_out[n] receives the handles. */
+int mm_shoot_batch(mm_ctx *ctx, int32_t n, const mm_lenses *lenses, const mm_params *params,
+                   mm_map *maps_out);
+
+/* Copy a map to host_counts[n_elems] (n_elems must equal N_side^2; may be
+ * NULL to fetch only the stats) and fill *st (may be NULL). Blocks until
+ * the map is complete. */
+int mm_map_fetch(mm_ctx *ctx, mm_map map, uint32_t *host_counts, size_t n_elems, mm_stats *st);
+
+/* Device address of a map's uint32 counts (N_side^2, row-major), valid until
+ * mm_release_map; for zero-copy use on the context's stream. */
+int mm_map_device_ptr(mm_ctx *ctx, mm_map map, void **dptr, size_t *n_elems);
+
+int mm_release_map(mm_ctx *ctx, mm_map map);
+
+/* ---- serving: continuous batching ----------------------------------------
+ * A request is admitted when a slot is free and its footprint (lens set +
+ * map + tile bookkeeping) fits the HBM budget; admitted requests are shot
+ * in waves: each wave is one persistent launch (replayed from a captured
+ * CUDA graph) over ray tiles of every admitted map, so maps that arrive
+ * while others run join at the next wave and their work overlaps on the
+ * device. Results are bit-identical to mm_shoot of the same map. */
+
+/* Enqueue a map request; never blocks. lenses may be 0 (the library
+ * generates the field from *p when the request is admitted). Errors:
+ * MM_EINVAL, MM_EBUSY (queue full), MM_ENOMEM (footprint can never fit). */
+int mm_submit(mm_ctx *ctx, mm_lenses lenses, const mm_params *p, mm_req *out);
+
+/* Non-blocking: *done = 1 and *map_out set when the request finished
+ * (the map is then owned by the caller as from mm_shoot), 0 otherwise.
+ * Returns the request's error code if it failed. */
+int mm_poll(mm_ctx *ctx, mm_req req, int *done, mm_map *map_out);
+
+/* Block until the request finishes or timeout_ns elapses (< 0: forever).
+ * Errors: MM_ETIMEDOUT (still running), or the request's own error. */
+int mm_wait(mm_ctx *ctx, mm_req req, int64_t timeout_ns, mm_map *map_out);
+
+/* Cancel a request that has not been admitted yet; MM_EBUSY if it already runs. */
+int mm_cancel(mm_ctx *ctx, mm_req req);
+
+/* Latency of a finished request: submit -> admit -> done, seconds (host clock). */
+int mm_req_times(mm_ctx *ctx, mm_req req, double *t_queue, double *t_total);
+
+/* Serving limits: max concurrently admitted maps, max queued requests, and the
+ * target device time of one wave in milliseconds (0 keeps the current value). */
+int mm_serve_config(mm_ctx *ctx, int32_t max_active, int32_t max_queued, double wave_ms);
+
+/* ---- tuning and inspection ------------------------------------------------ */
+
+/* Time every tile variant of the FP32 kernel on a small map with the given
+ * parameters and record the fastest for maps of its class (unit vs
+ * lognormal masses, N* bucket); *variant receives its id. */
+int mm_autotune(mm_ctx *ctx, const mm_params *p, int32_t *variant);
+
+/* Force a tile variant for subsequent FP32 shoots (-1: use the tuned table). */
+int mm_set_variant(mm_ctx *ctx, int32_t variant);
+
+/* Number of FP32 tile variants and a description of one. */
+int mm_variant_count(void);
+const char *mm_variant_name(int32_t variant);
+
+/* Per-ray deflection through the same kernel code as the map: for rays
+ * (ray_i[k], ray_j[k]) of the global grid, alpha_out[2k..2k+1] receives the
+ * star deflection sum_i m_i (x - x_i)/|x - x_i|^2 (Eq. sigma) and pixel_out[k]
+ * the flat pixel index the map kernel would count the ray into (-1: out).
+ * Any output pointer may be NULL. */
+int mm_debug_deflect(mm_ctx *ctx, mm_lenses lenses, const mm_params *p,
+                     const int64_t *ray_i, const int64_t *ray_j, int64_t n,
+                     double *alpha_out, int64_t *pixel_out);
+
+/* Device time (ms) of the last kernel launch of the most recent shoot, batch
+ * or debug call, measured with CUDA events on the context's stream, and the
+ * number of kernels that call launched. */
+int mm_last_kernel_ms(mm_ctx *ctx, double *ms, int32_t *launches);
+
+const char *mm_strerror(int code);
+const char *mm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MM_H */

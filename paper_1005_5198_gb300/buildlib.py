@@ -1,0 +1,83 @@
+"""Build the sm_103a shared library libmm.so in-tree (paper_1005_5198_gb300/_build).
+
+nvcc compiles the CUDA translation unit for sm_103a only, g++ the host runtime
+(plain IEEE arithmetic: no FMA contraction, so the seeded lens fields match
+other implementations bit for bit); the units compile in parallel and link
+into one shared library with the CUDA runtime linked statically.
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(BUILD, "libmm.so")
+CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+CU_SOURCES = ["mm_kernels.cu"]
+CPP_SOURCES = ["mm_host.cpp", "mm_serve.cpp"]
+HEADERS = ["mm_internal.h", "mm_ctx.h"]
+
+
+def _inputs():
+    files = [os.path.join(CSRC, f) for f in CU_SOURCES + CPP_SOURCES + HEADERS]
+    files.append(os.path.join(ROOT, "include", "mm.h"))
+    files.append(os.path.abspath(__file__))
+    return files
+
+
+def up_to_date() -> bool:
+    if not os.path.exists(LIB):
+        return False
+    t = os.path.getmtime(LIB)
+    return all(os.path.getmtime(f) <= t for f in _inputs())
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    if not force and up_to_date():
+        return LIB
+    os.makedirs(BUILD, exist_ok=True)
+    jobs, objs = [], []
+    for f in CU_SOURCES:
+        o = os.path.join(BUILD, f + ".o")
+        cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
+               "-I", os.path.join(ROOT, "include"), "-c", os.path.join(CSRC, f), "-o", o]
+        jobs.append((f, cmd))
+        objs.append(o)
+    for f in CPP_SOURCES:
+        o = os.path.join(BUILD, f + ".o")
+        cmd = ["g++", "-std=c++17", "-O2", "-fPIC", "-ffp-contract=off", "-Wall", "-Wextra",
+               "-I", os.path.join(CUDA_HOME, "include"), "-I", os.path.join(ROOT, "include"),
+               "-c", os.path.join(CSRC, f), "-o", o]
+        jobs.append((f, cmd))
+        objs.append(o)
+    procs = [(f, subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)) for f, c in jobs]
+    logs = []
+    for f, p in procs:
+        out, _ = p.communicate()
+        logs.append((f, out))
+        if p.returncode != 0:
+            raise RuntimeError(f"compiling {f} failed:\n{out}")
+    tmp = LIB + f".{os.getpid()}.tmp"
+    link = [NVCC, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lpthread", "-ldl", "-lrt"]
+    r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"linking libmm.so failed:\n{r.stdout}")
+    os.replace(tmp, LIB)
+    with open(os.path.join(BUILD, "ptxas.log"), "w") as fh:
+        for f, out in logs:
+            fh.write(f"== {f}\n{out}\n")
+    if verbose:
+        for f, out in logs:
+            sys.stdout.write(f"== {f}\n{out}\n")
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose=True))

@@ -1,0 +1,129 @@
+// mm_ctx.h -- private host-side runtime structures (context, objects, allocator).
+#pragma once
+#include <atomic>
+#include <condition_variable>
+#include <cstddef>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/mm.h"
+#include "mm_internal.h"
+
+namespace mm {
+
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+// Validated geometry of a map request (host FP64).
+struct Geo {
+    double sigma_c, sigma_star, a, b, pix, delta, width, height, mmean, radius, mu_theory;
+    long long nx, ny, nstar;
+    long long i0, j0, ni, nj;
+    long long tiles_x, tiles_y;
+    unsigned long long tiles() const { return (unsigned long long)tiles_x * (unsigned long long)tiles_y; }
+};
+int compute_geo(const mm_params *p, Geo *g);
+
+// Caching device allocator with a byte budget. Freed blocks are kept for reuse
+// (size-rounded) and returned to the driver only when the budget needs room.
+class DeviceArena {
+public:
+    void init(size_t budget) { budget_ = budget; }
+    int alloc(size_t bytes, void **out);          // MM_OK / MM_ENOMEM / MM_EDEVICE
+    void free(void *p);
+    bool fits(size_t bytes) const;                 // could an allocation of this size succeed now
+    size_t budget() const { return budget_; }
+    size_t held() const { return held_; }
+    void release_all();
+    static size_t round(size_t bytes);
+private:
+    mutable std::mutex mu_;
+    size_t budget_ = 0, held_ = 0;                 // held = in use + cached
+    size_t live_bytes_ = 0;
+    std::multimap<size_t, void *> cache_;
+    std::unordered_map<void *, size_t> live_;
+};
+
+struct LensSet {
+    long long n = 0, n_pad = 0;
+    double *dx = nullptr, *dy = nullptr, *dm = nullptr;
+    float4 *lh = nullptr;
+    float *lmf = nullptr;
+    bool unit_mass = true;
+    DeviceArena *arena = nullptr;
+    ~LensSet();
+    static size_t footprint(long long n);
+};
+
+struct MapObj {
+    mm_params p{};
+    Geo g{};
+    unsigned int *counts = nullptr;
+    unsigned long long *totals = nullptr;   // [in, out]
+    std::shared_ptr<LensSet> lenses;
+    cudaEvent_t done = nullptr;
+    double seconds = 0.0;
+    int variant = 0;
+    DeviceArena *arena = nullptr;
+    ~MapObj();
+    static size_t footprint(int npix_side);
+};
+
+struct Server;
+
+struct LaunchScratch {
+    WorkHeader *d_hdr = nullptr;
+    MapDesc *d_maps = nullptr;
+    unsigned long long *d_counter = nullptr;
+    int cap = 0;
+    WorkHeader *h_hdr = nullptr;      // pinned
+    MapDesc *h_maps = nullptr;        // pinned
+};
+
+}  // namespace mm
+
+struct mm_ctx {
+    int device = 0;
+    int sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    mm::DeviceArena arena;
+    std::mutex mu;                                            // handle tables
+    std::unordered_map<uint64_t, std::shared_ptr<mm::LensSet>> lenses;
+    std::unordered_map<uint64_t, std::shared_ptr<mm::MapObj>> maps;
+    std::atomic<uint64_t> next_handle{1};
+    mm::LaunchScratch scratch;                                // synchronous calls
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double last_ms = 0.0;
+    int last_launches = 0;
+    int forced_variant = -1;
+    std::map<int, int> tuned;                                 // class key -> variant
+    mm::Server *server = nullptr;
+};
+
+namespace mm {
+// Shared helpers used by the synchronous API and the server.
+int make_lenses_from_params(mm_ctx *ctx, const mm_params *p, const Geo &g, cudaStream_t s,
+                            std::shared_ptr<LensSet> *out);
+int upload_lenses(mm_ctx *ctx, const double *x, const double *y, const double *m, long long n, bool unit,
+                  cudaStream_t s, std::shared_ptr<LensSet> *out);
+int alloc_map(mm_ctx *ctx, const mm_params *p, const Geo &g, std::shared_ptr<LensSet> lenses, cudaStream_t s,
+              std::shared_ptr<MapObj> *out);
+void fill_desc(const MapObj &m, MapDesc *d);
+int choose_variant(mm_ctx *ctx, const mm_params *p, const Geo &g);
+int scratch_reserve(mm_ctx *ctx, LaunchScratch *sc, int n_maps);
+void scratch_free(mm_ctx *ctx, LaunchScratch *sc);
+uint64_t register_map(mm_ctx *ctx, std::shared_ptr<MapObj> m);
+int server_start(mm_ctx *ctx);
+void server_stop(mm_ctx *ctx);
+}  // namespace mm

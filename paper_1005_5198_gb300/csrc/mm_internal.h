@@ -1,0 +1,98 @@
+// mm_internal.h -- structures shared by the host runtime and the device kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mm {
+
+// Ray tile of one CTA: 64 columns x 32 rows of the global ray lattice. Thread t
+// owns column (t/32 % 2)*32 + t%32 and the 8 consecutive rows starting at
+// (t/64)*8, so the x-differences to a lens are shared by its 8 rays.
+constexpr int kThreads = 256;
+constexpr int kRaysPerThread = 8;
+constexpr int kTileX = 64;
+constexpr int kTileY = 32;
+constexpr int kTileRays = kTileX * kTileY;
+// Lenses are staged into shared memory in chunks of 512 (256 pairs, one per thread).
+constexpr int kChunkPairs = 256;
+constexpr int kChunkLenses = 2 * kChunkPairs;
+// A "null" lens: far enough to contribute < 1e-13 per component, near enough that
+// products of two squared distances stay normal in FP32.
+constexpr float kNullX = 1.0e13f;
+// Lenses within this distance (Einstein radii) of a tile's ray box are summed in FP64.
+constexpr float kNearRadius = 0.1f;
+// Variants of the FP32 tile kernel: (shared-reciprocal pairs per 4 lens pairs, fold interval).
+constexpr int kNumVariants = 8;
+
+// One map of a launch. Built on the host (FP64 geometry), read by the kernels.
+struct MapDesc {
+    // lattice
+    double delta;              // ray spacing
+    double half_nx, half_ny;   // nx/2, ny/2
+    long long nx, ny;          // global grid
+    long long i0, j0, ni, nj;  // shot sub-rectangle [i0, i0+ni) x [j0, j0+nj)
+    long long tiles_x;         // ceil(ni / 64)
+    unsigned long long tile_begin;   // first work item of this map in the launch
+    unsigned long long tile_count;   // work items of this map in the launch
+    unsigned long long tile_first;   // map tile index of its first work item (waves)
+    // plain FP64 lens equation (FP64 kernel and near-lens terms)
+    double one_m_gamma, one_p_gamma, sigma_c, half_side, pix;
+    // float-float epilogue: u = A*(2i+1-nx) + N/2 + S/p, S = sum m (x_l - x)/r^2 = -alpha
+    float ax_h, ax_l, ay_h, ay_l;   // A_x = (1-gamma-sigma_c) delta / (2p), A_y with 1+gamma
+    float ip_h, ip_l;               // 1/p
+    float half_n;                   // N_side / 2
+    float delta_f, delta_l;         // delta as float-float (ray offsets in a tile)
+    int nside;
+    int unit_mass;
+    int variant;
+    int precision;
+    long long nstar;
+    // lens set (device)
+    const double *lx, *ly, *lm;     // FP64 master copy [nstar]
+    const float4 *lh;               // (x_hi, y_hi, x_lo, y_lo) padded to a multiple of 512
+    const float *lmf;               // FP32 masses, padded (0 for padding)
+    // outputs (device)
+    unsigned int *counts;           // nside^2
+    unsigned long long *totals;     // [0] rays in, [1] rays out (shot is ni*nj)
+};
+
+// Debug dump: per requested ray, the tile work item it belongs to and its slot.
+struct DumpArgs {
+    const unsigned long long *tile;   // per work item: tile index within map 0
+    const int *begin;                 // per work item: first request [n_items + 1]
+    const int *local;                 // per request: local ray index iloc + 64 * jloc, ascending per item
+    const int *slot;                  // per request: output slot
+    double *alpha;                    // [2 * n_req]
+    long long *pixel;                 // [n_req]
+};
+
+// Per-launch header in device memory, so that a captured graph can be replayed
+// with new work (the host rewrites header + descriptors before each replay).
+struct WorkHeader {
+    unsigned long long total_work;        // tiles over all maps, or dump work items
+    int n_maps;
+    int pad;
+};
+
+struct LaunchArgs {
+    const WorkHeader *hdr;
+    const MapDesc *maps;                  // hdr->n_maps descriptors, tile_begin ascending
+    unsigned long long *work_counter;     // zeroed before the launch
+    DumpArgs dump;
+};
+
+// ---- launch wrappers (mm_kernels.cu) --------------------------------------
+// Build the FP32 tile copies of a lens set: lh[k] = split of (x[k], y[k]) for
+// k < n, null lenses for n <= k < n_pad; lmf likewise. n_pad % 512 == 0.
+cudaError_t launch_prepare_lenses(const double *x, const double *y, const double *m, long long n,
+                                  long long n_pad, float4 *lh, float *lmf, cudaStream_t s);
+// FP32 (compensated) shoot over the work of args (every map precision MM_FP32C);
+// grid = number of CTAs (persistent).
+cudaError_t launch_shoot_fp32(const LaunchArgs &args, int grid, bool dump, cudaStream_t s);
+// Plain FP64 shoot (every map precision MM_FP64).
+cudaError_t launch_shoot_fp64(const LaunchArgs &args, int grid, bool dump, cudaStream_t s);
+// CTAs per SM the kernels are compiled for.
+int shoot_ctas_per_sm(bool fp64);
+const char *variant_name(int v);
+
+}  // namespace mm

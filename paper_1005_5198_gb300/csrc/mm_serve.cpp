@@ -1,0 +1,486 @@
+// mm_serve.cpp -- continuous-batching request loop (mm_submit / mm_poll / mm_wait).
+//
+// Requests wait in a FIFO queue until a slot is free and their device footprint
+// (lens set + map) fits the context's HBM budget. Admitted maps are shot in
+// waves: each wave is one persistent launch of the FP32 kernel over a slice of
+// the ray tiles of EVERY admitted map (processor sharing: the wave's work budget
+// is divided evenly between the maps, leftovers handed out in admission order),
+// replayed from a captured CUDA graph whose descriptor buffers the host rewrites
+// before each replay. Requests that arrive while waves run join the next wave,
+// so their work overlaps on the device with the maps already running. Two waves
+// are kept in flight; a map is complete when the wave that carried its last tile
+// has finished. Each tile is computed exactly as in mm_shoot, so results are
+// bit-identical to shooting the map alone.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "mm_ctx.h"
+
+namespace mm {
+
+static double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct Request {
+    uint64_t id = 0;
+    mm_params p{};
+    Geo g{};
+    std::shared_ptr<LensSet> given;
+    std::shared_ptr<MapObj> map;
+    unsigned long long cursor = 0;     // next map tile to schedule
+    unsigned long long tiles = 0;
+    std::atomic<int> state{0};         // 0 queued, 1 active, 2 done, 3 failed, 4 cancelled
+    int err = 0;
+    std::string err_msg;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    size_t footprint = 0;
+    uint64_t map_handle = 0;
+};
+
+struct WaveItem {
+    std::shared_ptr<Request> req;
+    bool last;
+};
+
+struct Wave {
+    long long id = -1;
+    int buf = 0;
+    std::vector<WaveItem> items;
+    double interactions = 0;
+    cudaEvent_t start = nullptr, end = nullptr;
+};
+
+struct Server {
+    mm_ctx *ctx = nullptr;
+    std::thread th;
+    std::mutex mu;
+    std::condition_variable cv, done_cv;
+    bool stop = false;
+    std::deque<std::shared_ptr<Request>> queue;
+    std::vector<std::shared_ptr<Request>> active;
+    std::unordered_map<uint64_t, std::shared_ptr<Request>> reqs;
+    int max_active = 64, max_queued = 1 << 16;
+    double wave_ms = 8.0;
+    cudaStream_t stream = nullptr, upload = nullptr, capture = nullptr;
+    LaunchScratch sc[2], sc64[2];
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int graph_cap[2] = {0, 0};
+    cudaEvent_t ev_start[2] = {nullptr, nullptr}, ev_end[2] = {nullptr, nullptr};
+    std::deque<Wave> inflight;
+    long long wave_counter = 0;
+    double rate = 4.0e9;               // interactions per ms, refined from measured waves
+    std::atomic<uint64_t> next_id{1};
+    std::string fatal;
+};
+
+static void finish(Server *S, const std::shared_ptr<Request> &r, int state, int err, const std::string &msg)
+{
+    r->err = err;
+    r->err_msg = msg;
+    r->t_done = now_s();
+    r->state.store(state);
+    S->done_cv.notify_all();
+}
+
+// Admit queued requests while slots and memory allow (FIFO; the head blocks the rest).
+static void admit(Server *S, std::unique_lock<std::mutex> &lk)
+{
+    mm_ctx *ctx = S->ctx;
+    while (!S->queue.empty() && (int)S->active.size() < S->max_active) {
+        auto r = S->queue.front();
+        if (!ctx->arena.fits(r->footprint)) break;
+        S->queue.pop_front();
+        lk.unlock();
+        std::shared_ptr<LensSet> L = r->given;
+        int rc = MM_OK;
+        if (!L) {
+            // seeded field on the host, uploaded on the upload stream
+            rc = make_lenses_from_params(ctx, &r->p, r->g, S->upload, &L);
+        }
+        std::shared_ptr<MapObj> M;
+        if (!rc) rc = alloc_map(ctx, &r->p, r->g, L, S->stream, &M);
+        lk.lock();
+        if (rc) {
+            finish(S, r, 3, rc, mm_last_error());
+            continue;
+        }
+        r->map = M;
+        r->tiles = r->g.tiles();
+        r->t_admit = now_s();
+        r->state.store(1);
+        S->active.push_back(r);
+    }
+}
+
+static double tile_cost(const Request &r) { return (double)kTileRays * (double)std::max(r.map->lenses->n, 8LL); }
+
+static int capture_graph(Server *S, int b)
+{
+    mm_ctx *ctx = S->ctx;
+    LaunchScratch *sc = &S->sc[b];
+    if (S->gexec[b]) {
+        cudaGraphExecDestroy(S->gexec[b]);
+        S->gexec[b] = nullptr;
+    }
+    LaunchArgs a{};
+    a.hdr = sc->d_hdr;
+    a.maps = sc->d_maps;
+    a.work_counter = sc->d_counter;
+    const int grid = ctx->sms * shoot_ctas_per_sm(false);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(S->capture, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    cudaMemcpyAsync(sc->d_hdr, sc->h_hdr, sizeof(WorkHeader), cudaMemcpyHostToDevice, S->capture);
+    cudaMemcpyAsync(sc->d_maps, sc->h_maps, (size_t)sc->cap * sizeof(MapDesc), cudaMemcpyHostToDevice, S->capture);
+    cudaMemsetAsync(sc->d_counter, 0, sizeof(unsigned long long), S->capture);
+    launch_shoot_fp32(a, grid, false, S->capture);
+    e = cudaStreamEndCapture(S->capture, &g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&S->gexec[b], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    S->graph_cap[b] = sc->cap;
+    return MM_OK;
+}
+
+// Write the wave's descriptors into buffer b and enqueue it on the server stream.
+static int launch_wave(Server *S, Wave *w, const std::vector<unsigned long long> &sizes)
+{
+    mm_ctx *ctx = S->ctx;
+    const int b = w->buf;
+    int n32 = 0, n64 = 0;
+    for (auto &it : w->items) (it.req->p.precision == MM_FP64 ? n64 : n32)++;
+    int rc;
+    if ((rc = scratch_reserve(ctx, &S->sc[b], std::max(S->max_active, n32)))) return rc;
+    if (n64 && (rc = scratch_reserve(ctx, &S->sc64[b], n64))) return rc;
+    // order: decreasing per-tile cost within each precision (large tiles first)
+    std::vector<size_t> idx(w->items.size());
+    for (size_t k = 0; k < idx.size(); ++k) idx[k] = k;
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t c) {
+        return w->items[a].req->map->lenses->n > w->items[c].req->map->lenses->n;
+    });
+    unsigned long long tot32 = 0, tot64 = 0;
+    int k32 = 0, k64 = 0;
+    for (size_t q : idx) {
+        Request &r = *w->items[q].req;
+        const bool fp64 = r.p.precision == MM_FP64;
+        MapDesc *d = fp64 ? &S->sc64[b].h_maps[k64++] : &S->sc[b].h_maps[k32++];
+        fill_desc(*r.map, d);
+        d->tile_first = r.cursor;
+        d->tile_count = sizes[q];
+        d->tile_begin = fp64 ? tot64 : tot32;
+        (fp64 ? tot64 : tot32) += sizes[q];
+        r.cursor += sizes[q];
+    }
+    S->sc[b].h_hdr->total_work = tot32;
+    S->sc[b].h_hdr->n_maps = n32;
+    cudaEventRecord(S->ev_start[b], S->stream);
+    if (n32) {
+        if (!S->gexec[b] || S->graph_cap[b] != S->sc[b].cap) {
+            if ((rc = capture_graph(S, b))) return rc;
+        }
+        cudaError_t e = cudaGraphLaunch(S->gexec[b], S->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    }
+    if (n64) {
+        LaunchScratch *sc = &S->sc64[b];
+        sc->h_hdr->total_work = tot64;
+        sc->h_hdr->n_maps = n64;
+        cudaMemcpyAsync(sc->d_hdr, sc->h_hdr, sizeof(WorkHeader), cudaMemcpyHostToDevice, S->stream);
+        cudaMemcpyAsync(sc->d_maps, sc->h_maps, (size_t)n64 * sizeof(MapDesc), cudaMemcpyHostToDevice, S->stream);
+        cudaMemsetAsync(sc->d_counter, 0, sizeof(unsigned long long), S->stream);
+        LaunchArgs a{};
+        a.hdr = sc->d_hdr;
+        a.maps = sc->d_maps;
+        a.work_counter = sc->d_counter;
+        cudaError_t e = launch_shoot_fp64(a, ctx->sms * shoot_ctas_per_sm(true), false, S->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "fp64 wave launch");
+    }
+    cudaEventRecord(S->ev_end[b], S->stream);
+    for (auto &it : w->items)
+        if (it.last) cudaEventRecord(it.req->map->done, S->stream);
+    w->start = S->ev_start[b];
+    w->end = S->ev_end[b];
+    return MM_OK;
+}
+
+static void complete_wave(Server *S, Wave &w, std::unique_lock<std::mutex> &lk)
+{
+    lk.unlock();
+    cudaError_t e = cudaEventSynchronize(w.end);
+    float ms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, w.start, w.end);
+    lk.lock();
+    if (e != cudaSuccess) {
+        S->fatal = cudaGetErrorString(e);
+        for (auto &it : w.items) finish(S, it.req, 3, MM_EDEVICE, S->fatal);
+        return;
+    }
+    if (ms > 0.05f) S->rate = 0.7 * S->rate + 0.3 * (w.interactions / (double)ms);
+    for (auto &it : w.items) {
+        if (!it.last) continue;
+        auto &r = it.req;
+        r->map->seconds = std::max(0.0, now_s() - r->t_admit);   // admission to completion, host clock
+        r->map_handle = register_map(S->ctx, r->map);
+        S->active.erase(std::remove(S->active.begin(), S->active.end(), r), S->active.end());
+        finish(S, r, 2, MM_OK, "");
+    }
+}
+
+static void loop(Server *S)
+{
+    mm_ctx *ctx = S->ctx;
+    cudaSetDevice(ctx->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (;;) {
+        if (!S->fatal.empty()) {
+            for (auto &r : S->queue) finish(S, r, 3, MM_EDEVICE, S->fatal);
+            S->queue.clear();
+        }
+        if (S->stop) {
+            for (auto &r : S->queue) finish(S, r, 4, MM_ECANCELED, "server stopped");
+            S->queue.clear();
+        }
+        admit(S, lk);
+        bool have_work = false;
+        for (auto &r : S->active) have_work = have_work || r->cursor < r->tiles;
+        if (S->stop && S->inflight.empty() && !have_work) {
+            for (auto &r : S->active) finish(S, r, 4, MM_ECANCELED, "server stopped");
+            S->active.clear();
+            break;
+        }
+        if (have_work && S->inflight.size() < 2 && S->fatal.empty()) {
+            Wave w;
+            w.buf = (int)(S->wave_counter & 1);
+            w.id = S->wave_counter++;
+            // plan: even share of the work budget per live map
+            std::vector<std::shared_ptr<Request>> live;
+            for (auto &r : S->active)
+                if (r->cursor < r->tiles) live.push_back(r);
+            const double budget = std::max(1.0, S->wave_ms * S->rate);
+            const double share = budget / (double)live.size();
+            std::vector<unsigned long long> take(live.size(), 0);
+            double used = 0;
+            for (size_t k = 0; k < live.size(); ++k) {
+                const double c = tile_cost(*live[k]);
+                const unsigned long long left = live[k]->tiles - live[k]->cursor;
+                take[k] = std::min(left, (unsigned long long)std::max(1.0, std::floor(share / c)));
+                used += (double)take[k] * c;
+            }
+            for (size_t k = 0; k < live.size() && used < budget; ++k) {
+                const double c = tile_cost(*live[k]);
+                const unsigned long long left = live[k]->tiles - live[k]->cursor - take[k];
+                const unsigned long long extra = std::min(left, (unsigned long long)std::floor((budget - used) / c));
+                take[k] += extra;
+                used += (double)extra * c;
+            }
+            std::vector<unsigned long long> sizes;
+            for (size_t k = 0; k < live.size(); ++k) {
+                w.items.push_back(WaveItem{live[k], live[k]->cursor + take[k] == live[k]->tiles});
+                sizes.push_back(take[k]);
+                w.interactions += (double)take[k] * tile_cost(*live[k]);
+            }
+            int rc = launch_wave(S, &w, sizes);
+            if (rc) {
+                S->fatal = mm_last_error();
+                for (auto &it : w.items) finish(S, it.req, 3, rc, S->fatal);
+                continue;
+            }
+            S->inflight.push_back(std::move(w));
+            continue;
+        }
+        if (!S->inflight.empty()) {
+            Wave w = std::move(S->inflight.front());
+            S->inflight.pop_front();
+            complete_wave(S, w, lk);
+            continue;
+        }
+        S->cv.wait_for(lk, std::chrono::milliseconds(20));
+    }
+}
+
+int server_start(mm_ctx *ctx)
+{
+    if (ctx->server) return MM_OK;
+    auto *S = new Server();
+    S->ctx = ctx;
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->upload, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->capture, cudaStreamNonBlocking);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        e = cudaEventCreate(&S->ev_start[b]);
+        if (e == cudaSuccess) e = cudaEventCreate(&S->ev_end[b]);
+    }
+    if (e != cudaSuccess) {
+        delete S;
+        return cuda_fail(e, "server streams/events");
+    }
+    ctx->server = S;
+    S->th = std::thread(loop, S);
+    return MM_OK;
+}
+
+void server_stop(mm_ctx *ctx)
+{
+    Server *S = ctx->server;
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv.notify_all();
+    if (S->th.joinable()) S->th.join();
+    cudaStreamSynchronize(S->stream);
+    for (int b = 0; b < 2; ++b) {
+        if (S->gexec[b]) cudaGraphExecDestroy(S->gexec[b]);
+        scratch_free(ctx, &S->sc[b]);
+        scratch_free(ctx, &S->sc64[b]);
+        cudaEventDestroy(S->ev_start[b]);
+        cudaEventDestroy(S->ev_end[b]);
+    }
+    cudaStreamDestroy(S->stream);
+    cudaStreamDestroy(S->upload);
+    cudaStreamDestroy(S->capture);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->reqs.clear();
+    }
+    delete S;
+    ctx->server = nullptr;
+}
+
+static std::shared_ptr<Request> find_req(Server *S, mm_req id)
+{
+    auto it = S->reqs.find(id);
+    return it == S->reqs.end() ? nullptr : it->second;
+}
+
+}  // namespace mm
+
+using namespace mm;
+
+extern "C" {
+
+int mm_serve_config(mm_ctx *ctx, int32_t max_active, int32_t max_queued, double wave_ms)
+{
+    if (!ctx || max_active < 0 || max_queued < 0 || !(wave_ms >= 0.0)) return fail(MM_EINVAL, "bad serve config");
+    int rc = server_start(ctx);
+    if (rc) return rc;
+    Server *S = ctx->server;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (max_active) S->max_active = max_active;
+    if (max_queued) S->max_queued = max_queued;
+    if (wave_ms > 0.0) S->wave_ms = wave_ms;
+    return MM_OK;
+}
+
+int mm_submit(mm_ctx *ctx, mm_lenses lenses, const mm_params *p, mm_req *out)
+{
+    if (!ctx || !out) return fail(MM_EINVAL, "null argument");
+    auto r = std::make_shared<Request>();
+    int rc = compute_geo(p, &r->g);
+    if (rc) return rc;
+    r->p = *p;
+    if (lenses) {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        auto it = ctx->lenses.find(lenses);
+        if (it == ctx->lenses.end()) return fail(MM_ENOTFOUND, "unknown lens set");
+        r->given = it->second;
+        r->g.nstar = r->given->n;
+    }
+    r->footprint = MapObj::footprint(p->npix_side) + (r->given ? 0 : LensSet::footprint(r->g.nstar));
+    if (r->footprint > ctx->arena.budget()) return fail(MM_ENOMEM, "request footprint exceeds the HBM budget");
+    if ((rc = server_start(ctx))) return rc;
+    Server *S = ctx->server;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if ((int)S->queue.size() >= S->max_queued) return fail(MM_EBUSY, "request queue full");
+        r->id = S->next_id.fetch_add(1);
+        r->t_submit = now_s();
+        S->queue.push_back(r);
+        S->reqs[r->id] = r;
+    }
+    S->cv.notify_all();
+    *out = r->id;
+    return MM_OK;
+}
+
+int mm_poll(mm_ctx *ctx, mm_req req, int *done, mm_map *map_out)
+{
+    if (!ctx || !done) return fail(MM_EINVAL, "null argument");
+    Server *S = ctx->server;
+    if (!S) return fail(MM_ENOTFOUND, "unknown request");
+    std::shared_ptr<Request> r;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        r = find_req(S, req);
+    }
+    if (!r) return fail(MM_ENOTFOUND, "unknown request");
+    const int st = r->state.load();
+    *done = 0;
+    if (st == 2) {
+        *done = 1;
+        if (map_out) *map_out = r->map_handle;
+        return MM_OK;
+    }
+    if (st == 3) { *done = 1; return fail(r->err, r->err_msg); }
+    if (st == 4) { *done = 1; return fail(MM_ECANCELED, "request cancelled"); }
+    return MM_OK;
+}
+
+int mm_wait(mm_ctx *ctx, mm_req req, int64_t timeout_ns, mm_map *map_out)
+{
+    if (!ctx) return fail(MM_EINVAL, "null context");
+    Server *S = ctx->server;
+    if (!S) return fail(MM_ENOTFOUND, "unknown request");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto r = find_req(S, req);
+    if (!r) return fail(MM_ENOTFOUND, "unknown request");
+    auto pred = [&] { return r->state.load() >= 2; };
+    if (timeout_ns < 0) S->done_cv.wait(lk, pred);
+    else if (!S->done_cv.wait_for(lk, std::chrono::nanoseconds(timeout_ns), pred))
+        return fail(MM_ETIMEDOUT, "request still running");
+    const int st = r->state.load();
+    if (st == 2) {
+        if (map_out) *map_out = r->map_handle;
+        return MM_OK;
+    }
+    if (st == 4) return fail(MM_ECANCELED, "request cancelled");
+    return fail(r->err, r->err_msg);
+}
+
+int mm_cancel(mm_ctx *ctx, mm_req req)
+{
+    if (!ctx) return fail(MM_EINVAL, "null context");
+    Server *S = ctx->server;
+    if (!S) return fail(MM_ENOTFOUND, "unknown request");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto r = find_req(S, req);
+    if (!r) return fail(MM_ENOTFOUND, "unknown request");
+    auto it = std::find(S->queue.begin(), S->queue.end(), r);
+    if (it == S->queue.end()) return fail(MM_EBUSY, "request already admitted or finished");
+    S->queue.erase(it);
+    finish(S, r, 4, MM_ECANCELED, "cancelled");
+    return MM_OK;
+}
+
+int mm_req_times(mm_ctx *ctx, mm_req req, double *t_queue, double *t_total)
+{
+    if (!ctx) return fail(MM_EINVAL, "null context");
+    Server *S = ctx->server;
+    if (!S) return fail(MM_ENOTFOUND, "unknown request");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto r = find_req(S, req);
+    if (!r) return fail(MM_ENOTFOUND, "unknown request");
+    if (r->state.load() < 2) return fail(MM_EAGAIN, "request not finished");
+    if (t_queue) *t_queue = (r->t_admit > 0 ? r->t_admit : r->t_done) - r->t_submit;
+    if (t_total) *t_total = r->t_done - r->t_submit;
+    return MM_OK;
+}
+
+}  // extern "C"

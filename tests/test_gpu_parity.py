@@ -1,0 +1,404 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (stated for the FP32 compensated path and derived in the design doc):
+  * per-ray deflection: max |alpha_gpu - alpha_oracle| <= 1e-5 Einstein radii;
+  * rays binned to a different pixel than the oracle's: <= 1e-4 of the rays;
+  * maps: sum |N_gpu - N_oracle| <= 2e-4 of the rays shot (a misbinned ray
+    moves at most two pixel counts);
+  * ray totals exact: shot = nx * ny (or the rectangle's area) = in + out,
+    and the map sums to `in`.
+The plain FP64 kernel sums in the oracle's lens order; it may differ from the
+oracle only by rounding, so it allows <= max(1, 1e-8 * shot) misbinned rays
+and alpha within 1e-9 relative.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1005_5198_gb300 as mm
+import synth
+from oracle import field
+
+pytestmark = pytest.mark.gpu
+
+ALPHA_TOL = 1e-5
+MISBIN_TOL = 1e-4
+
+CFG0 = dict(sigma=0.4, gamma=0.0, smooth_frac=0.0, side=4.0, npix_side=128, nrays=100.0)
+CFG1 = dict(sigma=0.4, gamma=0.0, smooth_frac=0.0, side=20.0, npix_side=1024, nrays=2000.0)
+CFG2 = dict(sigma=0.8, gamma=0.3, smooth_frac=0.5, side=40.0, npix_side=2048, nrays=500.0)
+
+
+def field0():
+    return synth.lens_field(100, field.radius_for_nstar(100, 0.4), 1)
+
+
+def field1():
+    n, r = field.nstar_rule(0.4, 0.0, 0.0, 20.0)
+    return synth.lens_field(n, r, 2)
+
+
+def field2():
+    return synth.lens_field(25000, field.radius_for_nstar(25000, 0.4), 3)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    mm.build()
+    c = mm.mm_init(0)
+    yield c
+    mm.mm_destroy(c)
+
+
+def lens(ctx, f):
+    return mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
+
+
+def P(cfg, **kw):
+    d = dict(cfg)
+    d.update(kw)
+    return mm.params(**d)
+
+
+def shoot(ctx, lh, cfg, **kw):
+    m = mm.mm_shoot(ctx, lh, P(cfg, **kw))
+    counts, st = mm.mm_map_fetch(ctx, m)
+    mm.mm_release_map(ctx, m)
+    return counts, st
+
+
+def check_totals(counts, st, shot):
+    assert st["rays_shot"] == shot
+    assert st["rays_in"] + st["rays_out"] == shot
+    assert int(counts.sum(dtype=np.int64)) == st["rays_in"]
+
+
+def map_l1(a, b):
+    return int(np.abs(a.astype(np.int64) - b.astype(np.int64)).sum())
+
+
+def oracle_cfg(cfg):
+    return dict(cfg, margin=1.5)
+
+
+def rays_check(ctx, lh, cfg, f, ii, jj, precision=mm.MM_FP32C):
+    a_g, p_g = mm.mm_debug_deflect(ctx, lh, P(cfg, precision=precision), ii, jj)
+    a_o, _, p_o = oracle.shoot_rays(oracle_cfg(cfg), f, ii, jj)
+    err = np.hypot(a_g[:, 0] - a_o[:, 0], a_g[:, 1] - a_o[:, 1])
+    return err, float(np.mean(p_g != p_o)), a_g, a_o, p_g, p_o
+
+
+# ----------------------------------------------------------------- config 0 ---
+
+def test_cfg0_fp32_full_map_matches_oracle(ctx):
+    f = field0()
+    lh = lens(ctx, f)
+    got, st = shoot(ctx, lh, CFG0)
+    ref, tot = oracle.shoot_map(oracle_cfg(CFG0), f)
+    check_totals(got, st, tot["shot"])
+    assert st["interactions"] == tot["shot"] * 100
+    assert map_l1(got, ref) <= 2 * MISBIN_TOL * tot["shot"]
+    assert abs(st["rays_in"] - tot["inside"]) <= MISBIN_TOL * tot["shot"]
+
+
+def test_cfg0_fp32_every_ray_deflection_and_pixel(ctx):
+    f = field0()
+    lh = lens(ctx, f)
+    g = oracle.geometry(oracle_cfg(CFG0))
+    jj, ii = np.meshgrid(np.arange(g["ny"]), np.arange(g["nx"]), indexing="ij")
+    err, mis, *_ = rays_check(ctx, lh, CFG0, f, ii.ravel(), jj.ravel())
+    assert err.max() <= ALPHA_TOL, err.max()
+    assert mis <= MISBIN_TOL, mis
+
+
+def test_cfg0_fp64_matches_oracle(ctx):
+    f = field0()
+    lh = lens(ctx, f)
+    got, st = shoot(ctx, lh, CFG0, precision=mm.MM_FP64)
+    ref, tot = oracle.shoot_map(oracle_cfg(CFG0), f)
+    check_totals(got, st, tot["shot"])
+    assert map_l1(got, ref) <= 2 * max(1, 1e-8 * tot["shot"])
+    rng = np.random.default_rng(0)
+    g = oracle.geometry(oracle_cfg(CFG0))
+    ii, jj = rng.integers(0, g["nx"], 20000), rng.integers(0, g["ny"], 20000)
+    err, mis, a_g, a_o, p_g, p_o = rays_check(ctx, lh, CFG0, f, ii, jj, precision=mm.MM_FP64)
+    assert np.all(np.abs(a_g - a_o) <= 1e-9 * (1 + np.abs(a_o)))
+    assert np.sum(p_g != p_o) <= 1
+
+
+def test_fp32_map_is_deterministic(ctx):
+    f = field0()
+    lh = lens(ctx, f)
+    a, _ = shoot(ctx, lh, CFG0)
+    b, _ = shoot(ctx, lh, CFG0)
+    np.testing.assert_array_equal(a, b)
+
+
+# ----------------------------------------------------------------- config 1 ---
+
+def test_cfg1_sampled_rays(ctx):
+    f = field1()
+    assert f.n == 558
+    lh = lens(ctx, f)
+    g = oracle.geometry(oracle_cfg(CFG1))
+    rng = np.random.default_rng(1)
+    n = 1_000_000
+    ii, jj = rng.integers(0, g["nx"], n), rng.integers(0, g["ny"], n)
+    err, mis, *_ = rays_check(ctx, lh, CFG1, f, ii, jj)
+    assert err.max() <= ALPHA_TOL, err.max()
+    assert mis <= MISBIN_TOL, mis
+
+
+def test_cfg1_full_map_totals_and_window_parity(ctx):
+    f = field1()
+    lh = lens(ctx, f)
+    g = oracle.geometry(oracle_cfg(CFG1))
+    got, st = shoot(ctx, lh, CFG1)
+    check_totals(got, st, g["nx"] * g["ny"])
+    assert st["interactions"] == g["nx"] * g["ny"] * 558
+    # mean magnification of the full map is close to the theoretical one (weak check)
+    assert abs(st["mu_mean"] / field.mu_theory(0.4, 0.0) - 1) < 0.1
+    # a window of 2048^2 rays (ragged: not a multiple of the tile) against the oracle
+    c = g["nx"] // 2
+    rect = (c - 1000, c + 1049, c - 700, c + 1349)
+    gw, sw = shoot(ctx, lh, CFG1, ray_rect=rect)
+    ref, tot = oracle.shoot_map(oracle_cfg(CFG1), f, rect=rect)
+    check_totals(gw, sw, tot["shot"])
+    assert map_l1(gw, ref) <= 2 * MISBIN_TOL * tot["shot"]
+
+
+# ----------------------------------------------------------------- config 2 ---
+
+def test_cfg2_sampled_rays_and_window(ctx):
+    f = field2()
+    lh = lens(ctx, f)
+    g = oracle.geometry(oracle_cfg(CFG2))
+    rng = np.random.default_rng(2)
+    n = 200_000
+    ii, jj = rng.integers(0, g["nx"], n), rng.integers(0, g["ny"], n)
+    err, mis, *_ = rays_check(ctx, lh, CFG2, f, ii, jj)
+    assert err.max() <= ALPHA_TOL, err.max()
+    assert mis <= MISBIN_TOL, mis
+    ci, cj = g["nx"] // 2, g["ny"] // 2
+    rect = (ci - 300, ci + 301, cj - 200, cj + 250)
+    gw, sw = shoot(ctx, lh, CFG2, ray_rect=rect)
+    ref, tot = oracle.shoot_map(oracle_cfg(CFG2), f, rect=rect)
+    check_totals(gw, sw, tot["shot"])
+    assert map_l1(gw, ref) <= 2 * max(2, MISBIN_TOL * tot["shot"])
+
+
+# -------------------------------------------------------- lognormal masses ---
+
+def mix_windows(count=4, seed=4):
+    out = []
+    for d in synth.map_mix(count, seed):
+        cfg = dict(sigma=d.sigma, gamma=d.gamma, smooth_frac=d.smooth_frac, side=d.side, npix_side=d.npix_side,
+                   nrays=d.nrays)
+        mmean = field.mean_mass(1, 0.0, 0.5)
+        n, r = field.nstar_rule(d.sigma, d.gamma, d.smooth_frac, d.side, 1.5, mmean)
+        n = min(n, 20000)
+        f = synth.lens_field(n, r, d.seed, synth.MASS_LOGNORMAL, 0.0, 0.5)
+        g = oracle.geometry(oracle_cfg(cfg))
+        ci, cj = g["nx"] // 2, g["ny"] // 2
+        rect = (max(0, ci - 200), min(g["nx"], ci + 233), max(0, cj - 150), min(g["ny"], cj + 170))
+        out.append((cfg, f, rect))
+    return out
+
+
+def test_lognormal_mix_windows_match_oracle(ctx):
+    for cfg, f, rect in mix_windows():
+        lh = lens(ctx, f)
+        gw, sw = shoot(ctx, lh, cfg, ray_rect=rect)
+        ref, tot = oracle.shoot_map(oracle_cfg(cfg), f, rect=rect)
+        check_totals(gw, sw, tot["shot"])
+        assert map_l1(gw, ref) <= 2 * max(2, MISBIN_TOL * tot["shot"]), cfg
+        ii = np.arange(rect[0], rect[1], 7)
+        jj = np.full(ii.shape, (rect[2] + rect[3]) // 2)
+        err, mis, *_ = rays_check(ctx, lh, cfg, f, ii, jj)
+        assert err.max() <= ALPHA_TOL, (cfg, err.max())
+        mm.mm_release_lenses(ctx, lh)
+
+
+# ------------------------------------------------------------- edge cases ---
+
+def test_smooth_only_map_exact(ctx):
+    """N* = 0, all matter smooth: the FP32 epilogue must reproduce the oracle's exact integer map."""
+    cfg = dict(sigma=0.53, gamma=0.1, smooth_frac=1.0, side=2.0, npix_side=16, nrays=121.0)
+    empty = synth.lens_field(0, 1.0, 0)
+    lh = lens(ctx, empty)
+    got, st = shoot(ctx, lh, cfg)
+    ref, tot = oracle.shoot_map(oracle_cfg(cfg), empty)
+    np.testing.assert_array_equal(got, ref)
+    check_totals(got, st, tot["shot"])
+    got64, _ = shoot(ctx, lh, cfg, precision=mm.MM_FP64)
+    np.testing.assert_array_equal(got64, ref)
+
+
+def test_single_lens_and_ray_on_lens(ctx):
+    cfg = dict(sigma=0.0, gamma=0.0, smooth_frac=0.0, side=2.0, npix_side=16, nrays=16.0)
+    g = oracle.geometry(oracle_cfg(cfg))
+    x1 = (3 + 0.5 - 0.5 * g["nx"]) * g["delta"]
+    x2 = (5 + 0.5 - 0.5 * g["ny"]) * g["delta"]
+    f = synth.LensField(np.array([x1]), np.array([x2]), np.array([1.0]))
+    lh = lens(ctx, f)
+    for prec in (mm.MM_FP32C, mm.MM_FP64):
+        _, pix = mm.mm_debug_deflect(ctx, lh, P(cfg, precision=prec), [3], [5])
+        assert pix[0] == -1
+        got, st = shoot(ctx, lh, cfg, precision=prec)
+        ref, tot = oracle.shoot_map(oracle_cfg(cfg), f)
+        check_totals(got, st, tot["shot"])
+        assert map_l1(got, ref) <= 2
+
+
+def test_empty_and_tiny_rectangles(ctx):
+    f = field0()
+    lh = lens(ctx, f)
+    got, st = shoot(ctx, lh, CFG0, ray_rect=(10, 10, 0, 5))
+    assert st["rays_shot"] == 0 and got.sum() == 0
+    got, st = shoot(ctx, lh, CFG0, ray_rect=(1600, 1601, 1700, 1701))
+    ref, tot = oracle.shoot_map(oracle_cfg(CFG0), f, rect=(1600, 1601, 1700, 1701))
+    check_totals(got, st, 1)
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_odd_lens_counts_around_chunk_boundaries(ctx):
+    cfg = dict(sigma=0.4, gamma=0.1, smooth_frac=0.2, side=8.0, npix_side=256, nrays=9.0)
+    g = oracle.geometry(oracle_cfg(cfg))
+    rect = (g["nx"] // 2 - 150, g["nx"] // 2 + 150, g["ny"] // 2 - 100, g["ny"] // 2 + 100)
+    for n in (1, 2, 3, 511, 512, 513, 1025):
+        f = synth.lens_field(n, 12.0, 100 + n)
+        lh = lens(ctx, f)
+        got, st = shoot(ctx, lh, cfg, ray_rect=rect)
+        ref, tot = oracle.shoot_map(oracle_cfg(cfg), f, rect=rect)
+        check_totals(got, st, tot["shot"])
+        assert map_l1(got, ref) <= 2 * max(2, MISBIN_TOL * tot["shot"]), n
+        mm.mm_release_lenses(ctx, lh)
+
+
+def test_maximum_map_side(ctx):
+    """N_side = 32768, the largest map: flat pixel indices up to 2^30 agree with the oracle."""
+    cfg = dict(sigma=0.4, gamma=0.1, smooth_frac=0.2, side=8.0, npix_side=32768, nrays=0.01)
+    f = synth.lens_field(200, 10.0, 77)
+    lh = lens(ctx, f)
+    g = oracle.geometry(oracle_cfg(cfg))
+    rng = np.random.default_rng(3)
+    ii, jj = rng.integers(0, g["nx"], 50_000), rng.integers(0, g["ny"], 50_000)
+    err, mis, a_g, a_o, p_g, p_o = rays_check(ctx, lh, cfg, f, ii, jj)
+    assert err.max() <= ALPHA_TOL and mis <= MISBIN_TOL
+    assert p_o.max() > 2 ** 29
+    m = mm.mm_shoot(ctx, lh, P(cfg))
+    _, st = mm.mm_map_fetch(ctx, m, want_counts=False)
+    assert st["rays_shot"] == g["nx"] * g["ny"] == st["rays_in"] + st["rays_out"]
+    mm.mm_release_map(ctx, m)
+
+
+def test_every_variant_within_tolerance(ctx):
+    f = field1()
+    lh = lens(ctx, f)
+    g = oracle.geometry(oracle_cfg(CFG1))
+    rng = np.random.default_rng(7)
+    ii, jj = rng.integers(0, g["nx"], 100_000), rng.integers(0, g["ny"], 100_000)
+    try:
+        for v in range(mm.mm_variant_count()):
+            mm.mm_set_variant(ctx, v)
+            err, mis, *_ = rays_check(ctx, lh, CFG1, f, ii, jj)
+            assert err.max() <= ALPHA_TOL and mis <= MISBIN_TOL, (v, err.max(), mis)
+    finally:
+        mm.mm_set_variant(ctx, -1)
+
+
+# ---------------------------------------------- lens sets, batch, serving ---
+
+def test_library_lens_generator_matches_input_module(ctx):
+    for cfg, seed, model in ((CFG1, 2, 0), (dict(CFG2, nstar=3000), 9, 1)):
+        p = P(cfg, seed=seed, mass_model=model)
+        h = mm.mm_create_lenses(ctx, p)
+        x, y, m = mm.mm_lenses_fetch(ctx, h)
+        geo = mm.mm_geometry_of(p)
+        ref = synth.lens_field(geo["nstar"], geo["disc_radius"], seed, model, 0.0, 0.5)
+        np.testing.assert_array_equal(x, ref.x)
+        np.testing.assert_array_equal(y, ref.y)
+        np.testing.assert_allclose(m, ref.m, rtol=1e-14)
+
+
+def test_batch_results_identical_to_alone(ctx):
+    items = mix_windows(6, 11)
+    plist, hl, alone = [], [], []
+    for cfg, f, rect in items:
+        h = lens(ctx, f)
+        hl.append(h)
+        plist.append(P(cfg, ray_rect=rect))
+        alone.append(shoot(ctx, h, cfg, ray_rect=rect)[0])
+    maps = mm.mm_shoot_batch(ctx, hl, plist)
+    for m, a in zip(maps, alone):
+        got, _ = mm.mm_map_fetch(ctx, m)
+        np.testing.assert_array_equal(got, a)
+        mm.mm_release_map(ctx, m)
+
+
+def test_serving_results_identical_to_alone(ctx):
+    items = mix_windows(8, 12)
+    mm.mm_serve_config(ctx, max_active=4, wave_ms=0.5)
+    reqs, alone = [], []
+    for k, (cfg, f, rect) in enumerate(items):
+        h = lens(ctx, f)
+        alone.append(shoot(ctx, h, cfg, ray_rect=rect)[0])
+        reqs.append(mm.mm_submit(ctx, h, P(cfg, ray_rect=rect)))
+    for r, a in zip(reqs, alone):
+        m = mm.mm_wait(ctx, r, timeout_s=120)
+        got, st = mm.mm_map_fetch(ctx, m)
+        np.testing.assert_array_equal(got, a)
+        q, t = mm.mm_req_times(ctx, r)
+        assert 0 <= q <= t
+        mm.mm_release_map(ctx, m)
+
+
+def test_serving_generates_fields_and_polls(ctx):
+    cfg = dict(CFG0)
+    r = mm.mm_submit(ctx, 0, P(cfg, nstar=100, seed=1))
+    for _ in range(20000):
+        done, m = mm.mm_poll(ctx, r)
+        if done:
+            break
+    else:
+        m = mm.mm_wait(ctx, r, timeout_s=60)
+    got, st = mm.mm_map_fetch(ctx, m)
+    h = mm.mm_create_lenses(ctx, P(cfg, nstar=100, seed=1))
+    ref, _ = shoot(ctx, h, cfg)
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_admission_rejects_oversized_request_and_cancel():
+    mm.build()
+    c = mm.mm_init(0, hbm_budget_bytes=64 << 20)
+    try:
+        with pytest.raises(mm.MMError) as e:
+            mm.mm_submit(c, 0, P(CFG1, npix_side=8192))    # 256 MiB map > 64 MiB budget
+        assert e.value.code == mm.MM_ENOMEM
+        mm.mm_serve_config(c, max_active=1, wave_ms=0.5)
+        big = mm.mm_submit(c, 0, P(CFG1))
+        small = mm.mm_submit(c, 0, P(CFG0, nstar=100))
+        try:
+            mm.mm_cancel(c, small)
+            with pytest.raises(mm.MMError) as e2:
+                mm.mm_wait(c, small, timeout_s=10)
+            assert e2.value.code == mm.MM_ECANCELED
+        except mm.MMError as e3:                            # already admitted: cancel refuses
+            assert e3.code == mm.MM_EBUSY
+        with pytest.raises(mm.MMError) as e4:
+            mm.mm_wait(c, big, timeout_s=0.0)
+        assert e4.value.code in (mm.MM_ETIMEDOUT,)
+    finally:
+        mm.mm_destroy(c)
+
+
+def test_unknown_handles(ctx):
+    with pytest.raises(mm.MMError) as e:
+        mm.mm_shoot(ctx, 987654321, P(CFG0))
+    assert e.value.code == mm.MM_ENOTFOUND
+    with pytest.raises(mm.MMError):
+        mm.mm_map_fetch(ctx, 987654321)
+    with pytest.raises(mm.MMError):
+        mm.mm_release_lenses(ctx, 987654321)
