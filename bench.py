@@ -1,0 +1,351 @@
+"""Benchmark: direct inverse ray-shooting of the Fig. 1 map on one GB300.
+
+One step = one complete magnification map through the library's C ABI: the
+whole hot path (ray lattice, deflection sum over all N* lenses, lens-equation
+epilogue, binning) for the Fig. 1 workload -- sigma = 0.4, gamma = 0, L = 20
+Einstein radii, N_side = 1024, N_rays = 2000, N* = 558 unit lenses (1.31e10
+rays, 7.31e12 ray-lens interactions) -- with the lens set resident in HBM.
+
+Reported (one JSON line from rank 0):
+  value        ray-lens interactions / s, FP32 compensated path, whole job
+  e2e          the same through the public API with host buffers: lens arrays
+               uploaded from pinned memory, map shot, counts read back, per step
+  roofline     the shoot kernel against the FP32 ALU peak (152 SMs x 128 lanes
+               x 2 FLOP x 2070 MHz), algorithmic FLOP = 10 per interaction
+               (the paper's N_FLOP convention for the deflection of one ray by
+               one lens)
+  fp64         the plain FP64 kernel on a ray window of the same map
+  cpu_baseline the FP64 CPU oracle on a strided sample of the same map
+  clocks       nvidia-smi samples taken during the timed region
+
+--impl reference times the CPU oracle (the reference arm of this build).
+Multi-GPU (torchrun): every rank shoots its own map (independent problems, no
+collective), value = total interactions / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CFG1 = dict(sigma=0.4, gamma=0.0, smooth_frac=0.0, side=20.0, npix_side=1024, nrays=2000.0)
+SEED = 2
+FLOP_PER_INTERACTION = 10.0      # Eq. for Phi: N_FLOP = 10 per deflection evaluation
+SMS, LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_PEAK_TFLOPS = SMS * LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+WORKLOAD = ("Fig. 1 map: sigma=0.4, gamma=0, s=0, L=20 R_E, N_pix=1024^2, N_rays=2000, N*=558 unit masses "
+            "uniform in a disc of R=37.36 R_E (seed 2); 114487^2 = 1.31e10 rays")
+METRIC = "ray-lens interactions/s and maps/s on 1 GB300 (FP32 vs FP64); p50/p99 map latency"
+CPU_STRIDE = 12                   # oracle sample: every 12th ray row and column (1/144 of the rays)
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class Clocks:
+    """nvidia-smi sampler for the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power)}
+
+
+def kernel_traffic():
+    """DRAM bytes per launch of the shoot kernel from the committed ncu summary, if it was
+    taken on the current kernel source; otherwise None."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "shoot_fp32_traffic.json")
+    src = os.path.join(ROOT, "paper_1005_5198_gb300", "csrc", "mm_kernels.cu")
+    try:
+        rec = json.load(open(p))
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if rec.get("kernel_sha256") == h:
+            return rec["dram_bytes_per_full_launch"]
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
+def cpu_baseline(seconds_target: float = 15.0):
+    """The FP64 CPU oracle on a strided sample of the Fig. 1 map, host cores."""
+    import oracle
+    import synth
+    from oracle import field
+    n, r = field.nstar_rule(0.4, 0.0, 0.0, 20.0)
+    f = synth.lens_field(n, r, SEED)
+    cfg = dict(CFG1, margin=1.5)
+    oracle.build()
+    threads = oracle.max_threads()
+    t0 = time.perf_counter()
+    _, tot = oracle.shoot_map(cfg, f, stride=CPU_STRIDE, threads=threads)
+    dt = time.perf_counter() - t0
+    inter = tot["shot"] * n
+    return {"value": inter / dt, "unit": "interactions/s", "cores": threads, "kind": "oracle",
+            "sample": f"Fig. 1 map, every {CPU_STRIDE}th ray row and column ({tot['shot']} rays x {n} lenses "
+                      f"= {inter:.3e} interactions) in {dt:.1f} s, FP64, OpenMP"}
+
+
+def profile_case():
+    """Small case of the same kernel for ncu: a 4096 x 4096-ray window of the Fig. 1 map
+    (1.68e7 rays, 9.36e9 interactions), launched three times."""
+    import paper_1005_5198_gb300 as mm
+    import synth
+    from oracle import field as ofield
+    mm.build()
+    ctx = mm.mm_init(0)
+    n, r = ofield.nstar_rule(0.4, 0.0, 0.0, 20.0)
+    f = synth.lens_field(n, r, SEED)
+    lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
+    g = mm.mm_geometry_of(mm.params(**CFG1))
+    c = g["nx"] // 2
+    p = mm.params(**CFG1, ray_rect=(c - 2048, c + 2048, c - 2048, c + 2048))
+    for _ in range(3):
+        m = mm.mm_shoot(ctx, lh, p)
+        ms, _ = mm.mm_last_kernel_ms(ctx)
+        _, st = mm.mm_map_fetch(ctx, m, want_counts=False)
+        mm.mm_release_map(ctx, m)
+        print(f"window {st['rays_shot']} rays: {ms:.3f} ms, {st['interactions'] / ms / 1e9:.3e} interactions/s")
+    mm.mm_destroy(ctx)
+    return 0
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    from oracle import field
+    n, r = field.nstar_rule(0.4, 0.0, 0.0, 20.0)
+    f = synth.lens_field(n, r, SEED)
+    cfg = dict(CFG1, margin=1.5)
+    oracle.build()
+    threads = oracle.max_threads()
+    stride = 24                                     # 1/576 of the map per step
+    for _ in range(args.warmup):
+        oracle.shoot_map(cfg, f, stride=stride, threads=threads)
+    times, shot = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        _, tot = oracle.shoot_map(cfg, f, stride=stride, threads=threads)
+        times.append(time.perf_counter() - t0)
+        shot = tot["shot"]
+    inter = shot * n
+    value = inter * len(times) / sum(times)
+    line = {"metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": f"every {stride}th ray row and column per step"},
+            "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": threads, "kind": "oracle",
+                             "sample": f"every {stride}th ray row and column of the Fig. 1 map per step "
+                                       f"({shot} rays x {n} lenses)"},
+            "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="shoot a 4096^2-ray window of the Fig. 1 map three times (for ncu captures) and exit")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.profile_case:
+        return profile_case()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    import torch
+    import paper_1005_5198_gb300 as mm
+    import synth
+    from oracle import field as ofield      # N* rule of the oracle only to size the synthetic input
+
+    rank, world, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    mm.build()
+    ctx = mm.mm_init(local, 0, stream.cuda_stream)
+
+    n, r = ofield.nstar_rule(0.4, 0.0, 0.0, 20.0)
+    f = synth.lens_field(n, r, SEED + rank)
+    lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
+    p = mm.params(**CFG1)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")   # > 129 MB L2
+
+    def step():
+        m = mm.mm_shoot(ctx, lh, p)
+        kms, launches = mm.mm_last_kernel_ms(ctx)
+        _, st = mm.mm_map_fetch(ctx, m, want_counts=False)
+        mm.mm_release_map(ctx, m)
+        return st, kms, launches
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    step_ms, kern_ms, launches, inter = [], [], 0, 0
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)                       # evict L2 between timed steps (outside the events)
+            ev[k][0].record(stream)
+            st, kms, nl = step()
+            ev[k][1].record(stream)
+            kern_ms.append(kms)
+            launches += nl
+            inter += st["interactions"]
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_total = sum(step_ms) * 1e-3
+    if dist:
+        tt = torch.tensor([t_total], device=f"cuda:{local}")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+        ti = torch.tensor([float(inter)], device=f"cuda:{local}", dtype=torch.float64)
+        dist.all_reduce(ti)
+        inter = float(ti.item())
+    value = inter / t_total
+    maps_per_s = world * args.steps / t_total
+
+    # ---- e2e through the public API with host buffers (pinned) ----
+    hx = torch.from_numpy(f.x).pin_memory().numpy()
+    hy = torch.from_numpy(f.y).pin_memory().numpy()
+    hm = torch.from_numpy(f.m).pin_memory().numpy()
+    hc = torch.empty(CFG1["npix_side"] ** 2, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+    e2e_times = []
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = mm.mm_create_lenses_from(ctx, hx, hy, hm)
+        m = mm.mm_shoot(ctx, h, p)
+        counts, st = mm.mm_map_fetch(ctx, m, counts=hc)
+        mm.mm_release_map(ctx, m)
+        mm.mm_release_lenses(ctx, h)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_value = st["interactions"] * len(e2e_times) / sum(e2e_times)
+    h2d = 3 * f.x.nbytes
+    d2h = hc.nbytes + 16
+
+    # ---- plain FP64 kernel on a window of the same map ----
+    g = mm.mm_geometry_of(p)
+    c = g["nx"] // 2
+    win = (c - 1024, c + 1024, c - 512, c + 512)
+    m64 = mm.mm_shoot(ctx, lh, mm.params(**CFG1, precision=mm.MM_FP64, ray_rect=win))
+    ms64, _ = mm.mm_last_kernel_ms(ctx)
+    _, st64 = mm.mm_map_fetch(ctx, m64, want_counts=False)
+    mm.mm_release_map(ctx, m64)
+    fp64 = {"value": st64["interactions"] / (ms64 * 1e-3), "unit": "interactions/s",
+            "sample": f"2048 x 1024-ray window at the grid centre ({st64['interactions']:.3e} interactions)"}
+
+    clocks = clk.summary()
+    kmean = sum(kern_ms) / len(kern_ms)
+    achieved = FLOP_PER_INTERACTION * (inter / (world * args.steps)) / (kmean * 1e-3) / 1e12
+    traffic = kernel_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": "FP32 compensated (MM_FP32C)",
+                   "l2": "flushed between timed steps (256 MiB write outside the step events)",
+                   "parallelism": f"{world} independent maps, one per GPU"},
+        "maps_per_s": maps_per_s,
+        "e2e": {"value": e2e_value, "unit": "interactions/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "what": "mm_create_lenses_from (pinned host) + mm_shoot + mm_map_fetch (pinned host) per step"},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                     "peak_source": "recipe unit counts: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz",
+                     "kernel_ms": kmean,
+                     "frac_at_measured_clock": (achieved / (FP32_PEAK_TFLOPS * clocks["sm_mhz"] / SM_MAX_MHZ)
+                                                if clocks.get("sm_mhz") else None)},
+        "fp64": fp64,
+        "fp32_over_fp64": value / world / fp64["value"],
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    mm.mm_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

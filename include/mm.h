@@ -229,17 +229,28 @@ int mm_serve_config(mm_ctx *ctx, int32_t max_active, int32_t max_queued, double 
 
 /* ---- tuning and inspection ------------------------------------------------ */
 
-/* Time every tile variant of the FP32 kernel on a small map with the given
- * parameters and record the fastest for maps of its class (unit vs
- * lognormal masses, N* bucket); *variant receives its id. */
+/* Autotune for maps like *p: time every thread layout x tile variant of the
+ * FP32 kernel on a window of about 600 tiles of such a map, keep the fastest
+ * layout for the context and record the fastest variant for maps of p's class
+ * (unit vs lognormal masses, N* bucket by powers of two); *variant receives it.
+ * Layouts give bit-identical maps; variants differ only in rounding. */
 int mm_autotune(mm_ctx *ctx, const mm_params *p, int32_t *variant);
 
-/* Force a tile variant for subsequent FP32 shoots (-1: use the tuned table). */
+/* Force a tile variant for subsequent FP32 shoots (-1: use the tuned table).
+ * A variant fixes the share of lens pairs whose two reciprocals come from one
+ * reciprocal of their product, and the compensated-fold interval. */
 int mm_set_variant(mm_ctx *ctx, int32_t variant);
 
 /* Number of FP32 tile variants and a description of one. */
 int mm_variant_count(void);
 const char *mm_variant_name(int32_t variant);
+
+/* Set or read the FP32 thread layout of the context (how a 64 x 32-ray tile is
+ * split over threads); MM_EBUSY once serving has started. */
+int mm_set_layout(mm_ctx *ctx, int32_t layout);
+int mm_get_layout(mm_ctx *ctx, int32_t *layout);
+int mm_layout_count(void);
+const char *mm_layout_name(int32_t layout);
 
 /* Per-ray deflection through the same kernel code as the map: for rays
  * (ray_i[k], ray_j[k]) of the global grid, alpha_out[2k..2k+1] receives the

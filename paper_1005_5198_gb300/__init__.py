@@ -85,6 +85,10 @@ def _load():
         "mm_set_variant": [C.c_void_p, C.c_int32],
         "mm_variant_count": [],
         "mm_variant_name": [C.c_int32],
+        "mm_set_layout": [C.c_void_p, C.c_int32],
+        "mm_get_layout": [C.c_void_p, P(C.c_int32)],
+        "mm_layout_count": [],
+        "mm_layout_name": [C.c_int32],
         "mm_debug_deflect": [C.c_void_p, U64, P(mm_params), P(I64), P(I64), I64, P(D), P(I64)],
         "mm_last_kernel_ms": [C.c_void_p, P(D), P(C.c_int32)],
         "mm_strerror": [C.c_int],
@@ -95,6 +99,7 @@ def _load():
         fn.argtypes = args
         fn.restype = C.c_int
     lib.mm_variant_name.restype = C.c_char_p
+    lib.mm_layout_name.restype = C.c_char_p
     lib.mm_strerror.restype = C.c_char_p
     lib.mm_last_error.restype = C.c_char_p
     _lib = lib
@@ -290,6 +295,24 @@ def mm_variant_name(v: int) -> str:
     return _load().mm_variant_name(v).decode()
 
 
+def mm_set_layout(ctx: Ctx, layout: int) -> None:
+    _check(_load().mm_set_layout(ctx.handle, layout), "mm_set_layout")
+
+
+def mm_get_layout(ctx: Ctx) -> int:
+    v = C.c_int32()
+    _check(_load().mm_get_layout(ctx.handle, C.byref(v)), "mm_get_layout")
+    return v.value
+
+
+def mm_layout_count() -> int:
+    return _load().mm_layout_count()
+
+
+def mm_layout_name(v: int) -> str:
+    return _load().mm_layout_name(v).decode()
+
+
 def mm_debug_deflect(ctx: Ctx, lenses: int, p: mm_params, ray_i, ray_j):
     """(alpha [n, 2] float64, pixel [n] int64, -1 = out) through the map kernel's code."""
     ri = np.ascontiguousarray(ray_i, dtype=np.int64)
@@ -317,6 +340,7 @@ EXPORTED = [
     "mm_init", "mm_destroy", "mm_params_default", "mm_geometry_of", "mm_create_lenses", "mm_create_lenses_from",
     "mm_lenses_fetch", "mm_lenses_count", "mm_release_lenses", "mm_shoot", "mm_shoot_batch", "mm_map_fetch",
     "mm_map_device_ptr", "mm_release_map", "mm_submit", "mm_poll", "mm_wait", "mm_cancel", "mm_req_times",
-    "mm_serve_config", "mm_autotune", "mm_set_variant", "mm_variant_count", "mm_variant_name", "mm_debug_deflect",
+    "mm_serve_config", "mm_autotune", "mm_set_variant", "mm_variant_count", "mm_variant_name", "mm_set_layout",
+    "mm_get_layout", "mm_layout_count", "mm_layout_name", "mm_debug_deflect",
     "mm_last_kernel_ms", "mm_strerror", "mm_last_error",
 ]

@@ -107,6 +107,7 @@ struct mm_ctx {
     double last_ms = 0.0;
     int last_launches = 0;
     int forced_variant = -1;
+    int layout = 1;                                           // FP32 thread layout (bit-identical maps)
     std::map<int, int> tuned;                                 // class key -> variant
     mm::Server *server = nullptr;
 };

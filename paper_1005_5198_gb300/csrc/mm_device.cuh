@@ -1,0 +1,191 @@
+// mm_device.cuh -- device helpers shared by the shooting kernels (one copy per
+// translation unit): float-float arithmetic, shared-memory layout, the
+// persistent work loop and the debug-dump lookup.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "mm_internal.h"
+
+namespace mm {
+namespace dev {
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Error-free transformation a + b = s + e (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Add an FP64 value into a float-float accumulator (h, l).
+__device__ __forceinline__ void add_ff(float &h, float &l, double v)
+{
+    const float vh = __double2float_rn(v);
+    const float vl = __double2float_rn(v - (double)vh);
+    float s, e;
+    two_sum(h, vh, s, e);
+    h = s;
+    l = __fadd_rn(l, __fadd_rn(e, vl));
+}
+
+// Float-float u = (ch + cl) * n + base for an exactly representable integer-valued n.
+__device__ __forceinline__ void ff_axis(float ch, float cl, float n, float base, float &uh, float &ul)
+{
+    const float ph = __fmul_rn(ch, n);
+    float pe = __fmaf_rn(ch, n, -ph);
+    pe = __fmaf_rn(cl, n, pe);
+    float s, e;
+    two_sum(base, ph, s, e);
+    uh = s;
+    ul = __fadd_rn(e, pe);
+}
+
+// floor(u) for u = (uh + ul) + (sh + sl) * (iph + ipl), evaluated in float-float.
+__device__ __forceinline__ float ff_pixel(float uh, float ul, float sh, float sl, float iph, float ipl)
+{
+    const float th = __fmul_rn(sh, iph);
+    float te = __fmaf_rn(sh, iph, -th);
+    te = __fmaf_rn(sh, ipl, te);
+    te = __fmaf_rn(sl, iph, te);
+    float s, e;
+    two_sum(uh, th, s, e);
+    const float lo = __fadd_rn(__fadd_rn(e, ul), te);
+    const float I = floorf(s);
+    const float f = __fadd_rn(__fsub_rn(s, I), lo);
+    return __fadd_rn(I, floorf(f));
+}
+
+// Shared state of the persistent loop (first member of each kernel's shared block).
+struct LoopSmem {
+    unsigned long long g;
+    int map;
+    unsigned red_in, red_out;
+};
+
+struct __align__(16) SmemFP32 {
+    float4 pos[kChunkPairs];       // (xa, xb, ya, yb) relative to the tile centre
+    float2 mass[kChunkPairs];      // (ma, mb)
+    float4 acc[kTileRays];         // per ray: float-float sums (x_hi, x_lo, y_hi, y_lo), [slot][thread]
+    unsigned near_bits[2 * kChunkPairs / 32];
+    double cx, cy;                 // tile centre (FP64)
+    LoopSmem loop;
+};
+
+struct __align__(16) SmemFP64 {
+    double2 lens64[kChunkPairs];   // (x, y) of lens k of the chunk
+    double m64[kChunkPairs];
+    LoopSmem loop;
+};
+
+__device__ __forceinline__ int find_map(const LaunchArgs &A, int n_maps, unsigned long long g)
+{
+    int lo = 0, hi = n_maps - 1;
+    while (lo < hi) {                              // last map with tile_begin <= g
+        const int mid = (lo + hi + 1) >> 1;
+        if (A.maps[mid].tile_begin <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// First request of work item `item` with local ray index `mine` (requests of an item
+// are sorted by local index), or -1.
+__device__ __forceinline__ int dump_find(const DumpArgs &D, int item, int mine)
+{
+    int lo = D.begin[item], hi = D.begin[item + 1];
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (D.local[mid] < mine) lo = mid + 1; else hi = mid;
+    }
+    return (lo < D.begin[item + 1] && D.local[lo] == mine) ? lo : -1;
+}
+
+// Record one ray's result: debug dump, or a warp-aggregated count into the map
+// (every lane of the warp must call this together).
+template <bool DUMP>
+__device__ __forceinline__ void emit_ray(const LaunchArgs &A, const MapDesc &M, int item, int local, bool valid,
+                                         bool inside, unsigned pix, double alpha1, double alpha2, unsigned &cnt_in,
+                                         unsigned &cnt_out)
+{
+    if (DUMP) {
+        for (int q = dump_find(A.dump, item, local); q >= 0 && q < A.dump.begin[item + 1] && A.dump.local[q] == local;
+             ++q) {
+            const int sl = A.dump.slot[q];
+            A.dump.alpha[2 * sl] = alpha1;
+            A.dump.alpha[2 * sl + 1] = alpha2;
+            A.dump.pixel[sl] = inside ? (long long)pix : -1LL;
+        }
+    } else {
+        const unsigned key = inside ? pix : 0xffffffffu;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        if (inside && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(M.counts + pix, (unsigned)__popc(peers));
+        cnt_in += inside ? 1u : 0u;
+        cnt_out += (valid && !inside) ? 1u : 0u;
+    }
+}
+
+// Persistent loop: take work items from the launch's counter until exhausted,
+// run `body(M, tile, item, cnt_in, cnt_out)` on each, and add the in/out ray
+// counts to the map totals whenever the map changes and at exit.
+template <bool DUMP, typename Body>
+__device__ __forceinline__ void persistent_loop(const LaunchArgs &A, LoopSmem &S, Body body)
+{
+    const int tid = threadIdx.x;
+    int cur_map = -1;
+    unsigned long long run_in = 0, run_out = 0;   // meaningful in thread 0
+    const unsigned long long total_work = A.hdr->total_work;
+    const int n_maps = A.hdr->n_maps;
+    for (;;) {
+        if (tid == 0) {
+            const unsigned long long g = atomicAdd(A.work_counter, 1ULL);
+            S.g = g;
+            S.map = (g < total_work) ? (DUMP ? 0 : find_map(A, n_maps, g)) : -1;
+            S.red_in = 0;
+            S.red_out = 0;
+        }
+        __syncthreads();
+        const unsigned long long g = S.g;
+        const int mi = S.map;
+        if (g >= total_work) break;
+        if (tid == 0 && cur_map != mi) {
+            if (cur_map >= 0 && !DUMP) {
+                atomicAdd(A.maps[cur_map].totals + 0, run_in);
+                atomicAdd(A.maps[cur_map].totals + 1, run_out);
+            }
+            cur_map = mi;
+            run_in = run_out = 0;
+        }
+        const MapDesc &M = A.maps[mi];
+        const unsigned long long tile = DUMP ? A.dump.tile[g] : M.tile_first + (g - M.tile_begin);
+        unsigned ci = 0, co = 0;
+        body(M, tile, DUMP ? (int)g : 0, ci, co);
+        if (!DUMP) {
+            ci = __reduce_add_sync(0xffffffffu, ci);
+            co = __reduce_add_sync(0xffffffffu, co);
+            if ((tid & 31) == 0) {
+                atomicAdd(&S.red_in, ci);
+                atomicAdd(&S.red_out, co);
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            run_in += S.red_in;
+            run_out += S.red_out;
+        }
+        __syncthreads();                           // S.g / S.red_* are rewritten next iteration
+    }
+    if (tid == 0 && cur_map >= 0 && !DUMP) {
+        atomicAdd(A.maps[cur_map].totals + 0, run_in);
+        atomicAdd(A.maps[cur_map].totals + 1, run_out);
+    }
+}
+
+}  // namespace dev
+}  // namespace mm

@@ -452,10 +452,12 @@ static int launch_group(mm_ctx *ctx, std::vector<MapObj *> &group, bool fp64, co
     a.work_counter = sc->d_counter;
     if (dump) a.dump = *dump;
     const unsigned long long work = sc->h_hdr->total_work;
-    const long long cap = (long long)ctx->sms * shoot_ctas_per_sm(fp64);
+    const long long cap = (long long)ctx->sms * shoot_ctas_per_sm(fp64, ctx->layout);
     const int grid = (int)std::max(1LL, std::min((long long)work, cap));
     MM_CUDA(cudaEventRecord(ctx->ev0, s));
-    if (work > 0) MM_CUDA(fp64 ? launch_shoot_fp64(a, grid, dump != nullptr, s) : launch_shoot_fp32(a, grid, dump != nullptr, s));
+    if (work > 0)
+        MM_CUDA(fp64 ? launch_shoot_fp64(a, grid, dump != nullptr, s)
+                     : launch_shoot_fp32(a, ctx->layout, grid, dump != nullptr, s));
     MM_CUDA(cudaEventRecord(ctx->ev1, s));
     MM_CUDA(cudaEventSynchronize(ctx->ev1));     // pinned scratch is reused by the next call
     float t = 0.f;
@@ -882,32 +884,54 @@ int mm_autotune(mm_ctx *ctx, const mm_params *p, int32_t *variant)
     q.ray_rect[2] = (g.ny - wj) / 2; q.ray_rect[3] = q.ray_rect[2] + wj;
     std::shared_ptr<LensSet> L;
     if ((rc = make_lenses_from_params(ctx, &q, g, ctx->stream, &L))) return rc;
-    const int saved = ctx->forced_variant;
+    const int saved_v = ctx->forced_variant, saved_l = ctx->layout;
     double best = 1e300;
-    int best_v = 0;
-    for (int v = 0; v < kNumVariants; ++v) {
-        ctx->forced_variant = v;
-        double t_min = 1e300;
-        for (int rep = 0; rep < 3; ++rep) {
-            std::shared_ptr<MapObj> M;
-            Geo gq;
-            if ((rc = compute_geo(&q, &gq))) break;
-            gq.nstar = L->n;
-            if ((rc = alloc_map(ctx, &q, gq, L, ctx->stream, &M))) break;
-            std::vector<MapObj *> group{M.get()};
-            float ms = 0.f;
-            if ((rc = launch_group(ctx, group, false, nullptr, 0, ctx->stream, &ms))) break;
-            t_min = std::min(t_min, (double)ms);
+    int best_v = 0, best_l = saved_l;
+    for (int lay = 0; lay < kNumLayouts && !rc; ++lay) {
+        for (int v = 0; v < kNumVariants && !rc; ++v) {
+            ctx->forced_variant = v;
+            ctx->layout = lay;
+            double t_min = 1e300;
+            for (int rep = 0; rep < 3; ++rep) {
+                std::shared_ptr<MapObj> M;
+                Geo gq;
+                if ((rc = compute_geo(&q, &gq))) break;
+                gq.nstar = L->n;
+                if ((rc = alloc_map(ctx, &q, gq, L, ctx->stream, &M))) break;
+                std::vector<MapObj *> group{M.get()};
+                float ms = 0.f;
+                if ((rc = launch_group(ctx, group, false, nullptr, 0, ctx->stream, &ms))) break;
+                t_min = std::min(t_min, (double)ms);
+            }
+            if (t_min < best) { best = t_min; best_v = v; best_l = lay; }
         }
-        if (rc) break;
-        if (t_min < best) { best = t_min; best_v = v; }
     }
-    ctx->forced_variant = saved;
+    ctx->forced_variant = saved_v;
+    ctx->layout = rc ? saved_l : best_l;
     if (rc) return rc;
     ctx->tuned[class_key(p, g.nstar)] = best_v;
     if (variant) *variant = best_v;
     return MM_OK;
 }
+
+int mm_set_layout(mm_ctx *ctx, int32_t layout)
+{
+    if (!ctx || layout < 0 || layout >= kNumLayouts) return fail(MM_EINVAL, "bad layout");
+    if (ctx->server) return fail(MM_EBUSY, "the layout is fixed once serving has started");
+    ctx->layout = layout;
+    return MM_OK;
+}
+
+int mm_get_layout(mm_ctx *ctx, int32_t *layout)
+{
+    if (!ctx || !layout) return fail(MM_EINVAL, "null argument");
+    *layout = ctx->layout;
+    return MM_OK;
+}
+
+int mm_layout_count(void) { return kNumLayouts; }
+
+const char *mm_layout_name(int32_t layout) { return layout_name(layout); }
 
 int mm_last_kernel_ms(mm_ctx *ctx, double *ms, int32_t *launches)
 {

@@ -21,8 +21,12 @@ constexpr int kChunkLenses = 2 * kChunkPairs;
 constexpr float kNullX = 1.0e13f;
 // Lenses within this distance (Einstein radii) of a tile's ray box are summed in FP64.
 constexpr float kNearRadius = 0.1f;
-// Variants of the FP32 tile kernel: (shared-reciprocal pairs per 4 lens pairs, fold interval).
-constexpr int kNumVariants = 8;
+// Variants of the FP32 tile computation, chosen per map: (shared-reciprocal pairs per
+// 4 lens pairs, fold interval). They differ in rounding, within the accuracy target.
+constexpr int kNumVariants = 4;
+// Thread layouts of the FP32 kernel, chosen per launch: (columns x rows of the 64 x 32
+// tile per thread). They give bit-identical maps.
+constexpr int kNumLayouts = 4;
 
 // One map of a launch. Built on the host (FP64 geometry), read by the kernels.
 struct MapDesc {
@@ -86,13 +90,15 @@ struct LaunchArgs {
 // k < n, null lenses for n <= k < n_pad; lmf likewise. n_pad % 512 == 0.
 cudaError_t launch_prepare_lenses(const double *x, const double *y, const double *m, long long n,
                                   long long n_pad, float4 *lh, float *lmf, cudaStream_t s);
-// FP32 (compensated) shoot over the work of args (every map precision MM_FP32C);
-// grid = number of CTAs (persistent).
-cudaError_t launch_shoot_fp32(const LaunchArgs &args, int grid, bool dump, cudaStream_t s);
+// FP32 (compensated) shoot over the work of args (every map precision MM_FP32C) with
+// thread layout `layout`; grid = number of CTAs (persistent).
+cudaError_t launch_shoot_fp32(const LaunchArgs &args, int layout, int grid, bool dump, cudaStream_t s);
 // Plain FP64 shoot (every map precision MM_FP64).
 cudaError_t launch_shoot_fp64(const LaunchArgs &args, int grid, bool dump, cudaStream_t s);
-// CTAs per SM the kernels are compiled for.
-int shoot_ctas_per_sm(bool fp64);
+// CTAs per SM the kernels are compiled for (FP32: per thread layout).
+int shoot_ctas_per_sm(bool fp64, int layout);
+int layout_threads(int layout);
+const char *layout_name(int layout);
 const char *variant_name(int v);
 
 }  // namespace mm

@@ -130,14 +130,14 @@ static int capture_graph(Server *S, int b)
     a.hdr = sc->d_hdr;
     a.maps = sc->d_maps;
     a.work_counter = sc->d_counter;
-    const int grid = ctx->sms * shoot_ctas_per_sm(false);
+    const int grid = ctx->sms * shoot_ctas_per_sm(false, ctx->layout);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(S->capture, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
     cudaMemcpyAsync(sc->d_hdr, sc->h_hdr, sizeof(WorkHeader), cudaMemcpyHostToDevice, S->capture);
     cudaMemcpyAsync(sc->d_maps, sc->h_maps, (size_t)sc->cap * sizeof(MapDesc), cudaMemcpyHostToDevice, S->capture);
     cudaMemsetAsync(sc->d_counter, 0, sizeof(unsigned long long), S->capture);
-    launch_shoot_fp32(a, grid, false, S->capture);
+    launch_shoot_fp32(a, ctx->layout, grid, false, S->capture);
     e = cudaStreamEndCapture(S->capture, &g);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
     e = cudaGraphInstantiate(&S->gexec[b], g, 0);
@@ -197,7 +197,7 @@ static int launch_wave(Server *S, Wave *w, const std::vector<unsigned long long>
         a.hdr = sc->d_hdr;
         a.maps = sc->d_maps;
         a.work_counter = sc->d_counter;
-        cudaError_t e = launch_shoot_fp64(a, ctx->sms * shoot_ctas_per_sm(true), false, S->stream);
+        cudaError_t e = launch_shoot_fp64(a, ctx->sms * shoot_ctas_per_sm(true, 0), false, S->stream);
         if (e != cudaSuccess) return cuda_fail(e, "fp64 wave launch");
     }
     cudaEventRecord(S->ev_end[b], S->stream);
