@@ -16,6 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmm.so")
+ALU_RATES = os.path.join(BUILD, "alu_rates")     # pipe-throughput probe (measured FP32/MUFU/FP64 rates)
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -26,16 +27,16 @@ HEADERS = ["mm_internal.h", "mm_ctx.h", "mm_device.cuh", "mm_fp32.cuh"]
 
 
 def _inputs():
-    files = [os.path.join(CSRC, f) for f in CU_SOURCES + CPP_SOURCES + HEADERS]
+    files = [os.path.join(CSRC, f) for f in CU_SOURCES + CPP_SOURCES + HEADERS + ["alu_rates.cu"]]
     files.append(os.path.join(ROOT, "include", "mm.h"))
     files.append(os.path.abspath(__file__))
     return files
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(ALU_RATES):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(ALU_RATES))
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
@@ -57,6 +58,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
                "-c", os.path.join(CSRC, f), "-o", o]
         jobs.append((f, cmd))
         objs.append(o)
+    alu_tmp = ALU_RATES + f".{os.getpid()}.tmp"
+    jobs.append(("alu_rates.cu", [NVCC, *ARCH, "-O3", "-std=c++17", os.path.join(CSRC, "alu_rates.cu"), "-o", alu_tmp]))
     procs = [(f, subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)) for f, c in jobs]
     logs = []
     for f, p in procs:
@@ -70,6 +73,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"linking libmm.so failed:\n{r.stdout}")
     os.replace(tmp, LIB)
+    os.replace(alu_tmp, ALU_RATES)
     with open(os.path.join(BUILD, "ptxas.log"), "w") as fh:
         for f, out in logs:
             fh.write(f"== {f}\n{out}\n")
