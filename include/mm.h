@@ -261,6 +261,37 @@ int mm_debug_deflect(mm_ctx *ctx, mm_lenses lenses, const mm_params *p,
                      const int64_t *ray_i, const int64_t *ray_j, int64_t n,
                      double *alpha_out, int64_t *pixel_out);
 
+/* ---- shooting without allocation --------------------------------------------
+ * The paper has no counterpart to this call; it serves callers that cannot
+ * allocate device memory, such as code running under another runtime or
+ * framework that owns the GPU's memory and accounts for every byte, or a tight
+ * loop that cannot afford the device-wide synchronisation of cudaMalloc and
+ * cudaFree. It shoots one map with the FP32 kernel (thread layout and tile
+ * variant of a fresh context, so the map equals mm_shoot's on a fresh context)
+ * and allocates nothing: no context is needed, and the kernel's scratch (FP32
+ * lens tile copies, launch header, map descriptor, work counter) lives in one
+ * fixed __device__ array of about 2.6 MB that every GPU which loads the library
+ * holds until the process exits.
+ *   x, y, m   device arrays of nstar FP64 lens coordinates and masses, owned by
+ *             the caller; m is not read (may be NULL) when p->mass_model is
+ *             MM_MASS_UNIT. p->nstar and p->disc_radius are ignored.
+ *   nstar     0 .. 131072 (the scratch capacity); larger values return MM_EINVAL.
+ *   p         map parameters; p->precision must be MM_FP32C.
+ *   counts    device array of N_side^2 uint32 (row-major map), owned by the
+ *             caller; zeroed by the call.
+ *   totals    device array of 2 uint64 {rays in, rays out}; zeroed by the call.
+ *   cuda_stream  the stream to run on (NULL: the default stream).
+ * Runs on the current CUDA device; all pointers must belong to it. The call
+ * returns once the work is enqueued; the outputs are complete when the stream
+ * reaches it. The first call on a device looks up the scratch's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture. Every call shares the one scratch array, which keeps the
+ * last call's contents: calls whose work overlaps on the GPU (other streams,
+ * other threads) race and give wrong maps -- serialise them. Errors: MM_EINVAL,
+ * MM_EDEVICE. */
+int mm_shoot_noalloc(const double *x, const double *y, const double *m, int64_t nstar, const mm_params *p,
+                     uint32_t *counts, uint64_t *totals, void *cuda_stream);
+
 /* Device time (ms) of the last kernel launch of the most recent shoot, batch
  * or debug call, measured with CUDA events on the context's stream, and the
  * number of kernels that call launched. */

@@ -91,6 +91,8 @@ def _load():
         "mm_layout_name": [C.c_int32],
         "mm_debug_deflect": [C.c_void_p, U64, P(mm_params), P(I64), P(I64), I64, P(D), P(I64)],
         "mm_last_kernel_ms": [C.c_void_p, P(D), P(C.c_int32)],
+        "mm_shoot_noalloc": [C.c_void_p, C.c_void_p, C.c_void_p, I64, P(mm_params), C.c_void_p, C.c_void_p,
+                             C.c_void_p],
         "mm_strerror": [C.c_int],
         "mm_last_error": [],
     }
@@ -332,6 +334,15 @@ def mm_last_kernel_ms(ctx: Ctx) -> tuple[float, int]:
     return ms.value, n.value
 
 
+def mm_shoot_noalloc(x_ptr: int, y_ptr: int, m_ptr: int, nstar: int, p: mm_params, counts_ptr: int,
+                     totals_ptr: int, cuda_stream: int = 0) -> None:
+    """One FP32 map into caller-owned device buffers without any allocation by the library
+    (see include/mm.h). All pointers are device addresses (ints) on the current device."""
+    _check(_load().mm_shoot_noalloc(C.c_void_p(x_ptr), C.c_void_p(y_ptr), C.c_void_p(m_ptr or None), nstar,
+                                    C.byref(p), C.c_void_p(counts_ptr), C.c_void_p(totals_ptr),
+                                    C.c_void_p(cuda_stream or None)), "mm_shoot_noalloc")
+
+
 def mm_strerror(code: int) -> str:
     return _load().mm_strerror(code).decode()
 
@@ -342,5 +353,5 @@ EXPORTED = [
     "mm_map_device_ptr", "mm_release_map", "mm_submit", "mm_poll", "mm_wait", "mm_cancel", "mm_req_times",
     "mm_serve_config", "mm_autotune", "mm_set_variant", "mm_variant_count", "mm_variant_name", "mm_set_layout",
     "mm_get_layout", "mm_layout_count", "mm_layout_name", "mm_debug_deflect",
-    "mm_last_kernel_ms", "mm_strerror", "mm_last_error",
+    "mm_last_kernel_ms", "mm_shoot_noalloc", "mm_strerror", "mm_last_error",
 ]
