@@ -161,7 +161,7 @@ def profile_case():
         ms, _ = mm.mm_last_kernel_ms(ctx)
         _, st = mm.mm_map_fetch(ctx, m, want_counts=False)
         mm.mm_release_map(ctx, m)
-        print(f"window {st['rays_shot']} rays: {ms:.3f} ms, {st['interactions'] / ms / 1e9:.3e} interactions/s")
+        print(f"window {st['rays_shot']} rays: {ms:.3f} ms, {st['interactions'] / (ms * 1e-3):.3e} interactions/s")
     mm.mm_destroy(ctx)
     return 0
 
