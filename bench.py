@@ -107,6 +107,111 @@ class Clocks:
                 "samples": len(sm), "power_w_max": max(power)}
 
 
+def scaled_mix(count, seed, sides=(64, 128, 256), nrays=(10.0, 30.0, 100.0), cap=4e11, large_every=0):
+    """Map requests with the config-3 parameter distributions (sigma, gamma, s, L, lognormal masses),
+    scaled down in N_side and N_rays so that a phase fits in seconds; maps above `cap` interactions
+    are redrawn. Every `large_every`-th request is 4x the pixels (the "large" share of config 4)."""
+    import paper_1005_5198_gb300 as mm
+    import synth
+    out, k = [], 0
+    while len(out) < count:
+        k += 1
+        d = synth.map_mix(1, seed * 1000003 + k, sides=sides, nrays=nrays)[0]
+        large = bool(large_every) and (len(out) % large_every == large_every - 1)
+        nside = d.npix_side * (2 if large else 1)
+        p = mm.params(sigma=d.sigma, gamma=d.gamma, smooth_frac=d.smooth_frac, side=d.side, npix_side=nside,
+                      nrays=d.nrays, mass_model=mm.MM_MASS_LOGNORMAL, mass_s=0.5, seed=d.seed)
+        g = mm.mm_geometry_of(p)
+        inter = g["nx"] * g["ny"] * g["nstar"]
+        if inter > cap * (4 if large else 1) or g["nstar"] == 0:
+            continue
+        out.append((p, inter))
+    return out
+
+
+def batch_phase(mm, ctx, n_maps=64, seed=4):
+    """Config-3 shape, scaled: n maps of mixed shape and N* in ONE persistent launch, against the
+    same maps shot one by one, and against the plain FP64 kernel one by one on the smallest maps."""
+    mix = scaled_mix(n_maps, seed)
+    plist = [p for p, _ in mix]
+    total = sum(i for _, i in mix)
+    maps = mm.mm_shoot_batch(ctx, None, plist)          # warm-up (and lens generation)
+    for m in maps:
+        mm.mm_release_map(ctx, m)
+    t = []
+    for _ in range(3):
+        maps = mm.mm_shoot_batch(ctx, None, plist)
+        t.append(mm.mm_last_kernel_ms(ctx)[0])
+        for m in maps:
+            mm.mm_release_map(ctx, m)
+    batch_ms = min(t)
+    one_ms = 0.0
+    for p in plist:
+        m = mm.mm_shoot(ctx, 0, p)
+        one_ms += mm.mm_last_kernel_ms(ctx)[0]
+        mm.mm_release_map(ctx, m)
+    small = sorted(mix, key=lambda pi: pi[1])[:8]
+    f64_ms, f64_inter = 0.0, 0
+    for p, inter in small:
+        q = mm.params(**{k: getattr(p, k) for k, _ in mm.mm_params._fields_ if k != "ray_rect"})
+        q.precision = mm.MM_FP64
+        m = mm.mm_shoot(ctx, 0, q)
+        f64_ms += mm.mm_last_kernel_ms(ctx)[0]
+        f64_inter += inter
+        mm.mm_release_map(ctx, m)
+    return {"workload": f"{n_maps} maps, config-3 parameter mix (lognormal masses) scaled to N_side in "
+                        "{64,128,256}, N_rays in {10,30,100}, <= 4e11 interactions each",
+            "interactions": total, "batched_ms": batch_ms, "batched_interactions_per_s": total / (batch_ms * 1e-3),
+            "maps_per_s": n_maps / (batch_ms * 1e-3), "one_by_one_ms": one_ms,
+            "one_by_one_interactions_per_s": total / (one_ms * 1e-3),
+            "fp64_one_by_one_interactions_per_s": f64_inter / (f64_ms * 1e-3),
+            "fp64_sample": "the 8 smallest maps of the mix, plain FP64 kernel, one launch each"}
+
+
+def serve_phase(mm, ctx, rate_hz, seconds, seed, large_every=10):
+    """Poisson request stream through mm_submit / mm_poll; latency = submit to completion."""
+    import threading
+    import synth
+    n = max(8, int(rate_hz * seconds))
+    mix = scaled_mix(n, seed, large_every=large_every)
+    arrivals = synth.poisson_arrivals(n, rate_hz, seed)
+    reqs = [None] * n
+    t0 = time.perf_counter()
+
+    def submitter():
+        for k in range(n):
+            dt = arrivals[k] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            reqs[k] = mm.mm_submit(ctx, 0, mix[k][0])
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    done = [False] * n
+    lat, finished = [], 0
+    while finished < n:
+        progressed = False
+        for k in range(n):
+            if done[k] or reqs[k] is None:
+                continue
+            ok, m = mm.mm_poll(ctx, reqs[k])
+            if ok:
+                done[k] = True
+                finished += 1
+                progressed = True
+                lat.append(mm.mm_req_times(ctx, reqs[k])[1])
+                mm.mm_release_map(ctx, m)
+        if not progressed:
+            time.sleep(0.0005)
+    th.join()
+    wall = time.perf_counter() - t0
+    lat = np.array(lat) * 1e3
+    total = sum(i for _, i in mix)
+    return {"lambda_req_s": rate_hz, "requests": n, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
+            "sustained_interactions_per_s": total / wall, "wall_s": wall}
+
+
 def kernel_traffic():
     """DRAM bytes per launch of the shoot kernel from the committed ncu summary, if it was
     taken on the current kernel source; otherwise None."""
@@ -209,6 +314,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batch and serving phases")
     ap.add_argument("--profile-case", action="store_true",
                     help="shoot a 4096^2-ray window of the Fig. 1 map three times (for ncu captures) and exit")
     args = ap.parse_args()
@@ -312,6 +418,21 @@ def main():
     fp64 = {"value": st64["interactions"] / (ms64 * 1e-3), "unit": "interactions/s",
             "sample": f"2048 x 1024-ray window at the grid centre ({st64['interactions']:.3e} interactions)"}
 
+    # ---- batched persistent launch and served stream (scaled config-3 / config-4 shapes) ----
+    extra = {}
+    if not args.no_extras and world == 1:
+        extra["batch"] = batch_phase(mm, ctx)
+        mm.mm_serve_config(ctx, max_active=64, wave_ms=4.0)
+        capacity = extra["batch"]["batched_interactions_per_s"]          # the same mix shape, batched
+        mean_inter = np.mean([i for _, i in scaled_mix(200, 6, large_every=10)])
+        lam = 0.7 * capacity / mean_inter
+        extra["serving"] = {
+            "workload": "Poisson arrivals of the scaled config-3 mix plus every 10th request 4x the pixels; "
+                        "mm_submit/mm_poll continuous batching, latency from submit to completion",
+            "capacity_interactions_per_s": capacity, "mean_request_interactions": float(mean_inter),
+            "at_70pct_capacity": serve_phase(mm, ctx, lam, 20.0, 7),
+            "overload_3x": serve_phase(mm, ctx, 3.0 * lam, 5.0, 8)}
+
     clocks = clk.summary()
     kmean = sum(kern_ms) / len(kern_ms)
     achieved = FLOP_PER_INTERACTION * (inter / (world * args.steps)) / (kmean * 1e-3) / 1e12
@@ -337,6 +458,7 @@ def main():
         "fp32_over_fp64": value / world / fp64["value"],
         "clocks": clocks,
     }
+    line.update(extra)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     mm.mm_destroy(ctx)
