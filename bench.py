@@ -212,20 +212,40 @@ def serve_phase(mm, ctx, rate_hz, seconds, seed, large_every=10):
             "sustained_interactions_per_s": total / wall, "wall_s": wall}
 
 
-def kernel_traffic():
-    """DRAM bytes per launch of the shoot kernel from the committed ncu summary, if it was
-    taken on the current kernel source; otherwise None."""
+KERNEL_SOURCES = ["mm_fp32.cuh", "mm_device.cuh", "mm_internal.h", "mm_fp32_c2r4.cu"]
+
+
+def kernel_sha256():
     import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1005_5198_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def kernel_traffic():
+    """DRAM bytes per launch of the shoot kernel from the committed ncu record, if it was taken
+    on the current kernel source; otherwise None."""
     p = os.path.join(ROOT, "profiles", "shoot_fp32_traffic.json")
-    src = os.path.join(ROOT, "paper_1005_5198_gb300", "csrc", "mm_kernels.cu")
     try:
         rec = json.load(open(p))
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if rec.get("kernel_sha256") == h:
-            return rec["dram_bytes_per_full_launch"]
+        if rec.get("kernel_sha256") == kernel_sha256():
+            return rec["dram_bytes_per_launch"]
     except (OSError, ValueError, KeyError):
         pass
     return None
+
+
+def reduce_over_ranks(dist, device, t_total, inter):
+    """Whole-job figures: max time over ranks, sum of interactions over ranks."""
+    if dist is None:
+        return t_total, inter
+    import torch
+    tt = torch.tensor([t_total], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    ti = torch.tensor([float(inter)], device=device, dtype=torch.float64)
+    dist.all_reduce(ti)
+    return float(tt.item()), float(ti.item())
 
 
 def cpu_baseline(seconds_target: float = 15.0):
@@ -376,13 +396,7 @@ def main():
     torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_total = sum(step_ms) * 1e-3
-    if dist:
-        tt = torch.tensor([t_total], device=f"cuda:{local}")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
-        ti = torch.tensor([float(inter)], device=f"cuda:{local}", dtype=torch.float64)
-        dist.all_reduce(ti)
-        inter = float(ti.item())
+    t_total, inter = reduce_over_ranks(dist, f"cuda:{local}", t_total, inter)
     value = inter / t_total
     maps_per_s = world * args.steps / t_total
 

@@ -1,16 +1,22 @@
 // mm_serve.cpp -- continuous-batching request loop (mm_submit / mm_poll / mm_wait).
 //
-// Requests wait in a FIFO queue until a slot is free and their device footprint
-// (lens set + map) fits the context's HBM budget. Admitted maps are shot in
-// waves: each wave is one persistent launch of the FP32 kernel over a slice of
-// the ray tiles of EVERY admitted map (processor sharing: the wave's work budget
-// is divided evenly between the maps, leftovers handed out in admission order),
-// replayed from a captured CUDA graph whose descriptor buffers the host rewrites
-// before each replay. Requests that arrive while waves run join the next wave,
-// so their work overlaps on the device with the maps already running. Two waves
-// are kept in flight; a map is complete when the wave that carried its last tile
-// has finished. Each tile is computed exactly as in mm_shoot, so results are
-// bit-identical to shooting the map alone.
+// Admission: requests wait in a FIFO queue until a slot is free and their device
+// footprint (lens set + map) fits the context's HBM budget. Admission workers
+// (host threads with their own upload streams) then generate the seeded lens
+// field, upload it and allocate the map, off the scheduler's critical path, and
+// hand the request to the scheduler as "ready".
+//
+// Scheduling: ready maps are shot in waves. A wave is one persistent launch of
+// the FP32 kernel over a slice of the ray tiles of EVERY active map,
+// replayed from a captured CUDA graph whose descriptor buffer the host rewrites
+// before each replay. The slice sizes share a work budget evenly between the
+// active maps (processor sharing), and a wave always holds at least 4 tiles per
+// CTA of the grid when the maps have that much work left, so maps with few
+// tiles and many lenses cannot leave the GPU idle. Requests that arrive while
+// waves run join the next wave, so their work overlaps on the device with the
+// maps already running. Two waves are kept in flight; a map is complete when
+// the wave that carried its last tile has finished. Each tile is computed
+// exactly as in mm_shoot, so results are bit-identical to shooting the map alone.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -33,7 +39,7 @@ struct Request {
     std::shared_ptr<MapObj> map;
     unsigned long long cursor = 0;     // next map tile to schedule
     unsigned long long tiles = 0;
-    std::atomic<int> state{0};         // 0 queued, 1 active, 2 done, 3 failed, 4 cancelled
+    std::atomic<int> state{0};         // 0 queued, 1 admitted, 2 done, 3 failed, 4 cancelled
     int err = 0;
     std::string err_msg;
     double t_submit = 0, t_admit = 0, t_done = 0;
@@ -43,6 +49,7 @@ struct Request {
 
 struct WaveItem {
     std::shared_ptr<Request> req;
+    unsigned long long tiles;
     bool last;
 };
 
@@ -50,29 +57,37 @@ struct Wave {
     long long id = -1;
     int buf = 0;
     std::vector<WaveItem> items;
+    unsigned long long tiles = 0;
     double interactions = 0;
     cudaEvent_t start = nullptr, end = nullptr;
 };
 
+constexpr int kAdmitWorkers = 4;
+
 struct Server {
     mm_ctx *ctx = nullptr;
     std::thread th;
+    std::vector<std::thread> workers;
     std::mutex mu;
-    std::condition_variable cv, done_cv;
+    std::condition_variable cv, done_cv, admit_cv;
     bool stop = false;
-    std::deque<std::shared_ptr<Request>> queue;
-    std::vector<std::shared_ptr<Request>> active;
+    std::deque<std::shared_ptr<Request>> queue;      // submitted, not yet admitted
+    std::vector<std::shared_ptr<Request>> ready;     // prepared by a worker, not yet scheduled
+    std::vector<std::shared_ptr<Request>> active;    // being shot
+    int preparing = 0;                               // admitted, with a worker
+    size_t reserved_bytes = 0;                       // footprint of requests being prepared
     std::unordered_map<uint64_t, std::shared_ptr<Request>> reqs;
     int max_active = 64, max_queued = 1 << 16;
     double wave_ms = 8.0;
-    cudaStream_t stream = nullptr, upload = nullptr, capture = nullptr;
+    cudaStream_t stream = nullptr, capture = nullptr;
+    cudaStream_t upload[kAdmitWorkers] = {};
     LaunchScratch sc[2], sc64[2];
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int graph_cap[2] = {0, 0};
     cudaEvent_t ev_start[2] = {nullptr, nullptr}, ev_end[2] = {nullptr, nullptr};
     std::deque<Wave> inflight;
     long long wave_counter = 0;
-    double rate = 4.0e9;               // interactions per ms, refined from measured waves
+    double rate = 5.0e9;               // interactions per ms, refined from full waves
     std::atomic<uint64_t> next_id{1};
     std::string fatal;
 };
@@ -86,33 +101,50 @@ static void finish(Server *S, const std::shared_ptr<Request> &r, int state, int 
     S->done_cv.notify_all();
 }
 
-// Admit queued requests while slots and memory allow (FIFO; the head blocks the rest).
-static void admit(Server *S, std::unique_lock<std::mutex> &lk)
+// Admission worker: take the head of the queue when a slot is free and its footprint
+// fits, then generate/upload its lens field and allocate its map off the scheduler.
+static void admit_worker(Server *S, int idx)
 {
     mm_ctx *ctx = S->ctx;
-    while (!S->queue.empty() && (int)S->active.size() < S->max_active) {
+    cudaSetDevice(ctx->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (;;) {
+        // memory is also freed by callers releasing maps, which does not notify: re-check periodically
+        while (!(S->stop || (!S->queue.empty() &&
+                             (int)(S->active.size() + S->ready.size()) + S->preparing < S->max_active &&
+                             ctx->arena.fits(S->reserved_bytes + S->queue.front()->footprint))))
+            S->admit_cv.wait_for(lk, std::chrono::milliseconds(20));
+        if (S->stop) return;
         auto r = S->queue.front();
-        if (!ctx->arena.fits(r->footprint)) break;
         S->queue.pop_front();
+        S->preparing++;
+        S->reserved_bytes += r->footprint;
+        r->t_admit = now_s();
+        r->state.store(1);
         lk.unlock();
         std::shared_ptr<LensSet> L = r->given;
         int rc = MM_OK;
-        if (!L) {
-            // seeded field on the host, uploaded on the upload stream
-            rc = make_lenses_from_params(ctx, &r->p, r->g, S->upload, &L);
-        }
+        std::string msg;
+        if (!L) rc = make_lenses_from_params(ctx, &r->p, r->g, S->upload[idx], &L);
         std::shared_ptr<MapObj> M;
-        if (!rc) rc = alloc_map(ctx, &r->p, r->g, L, S->stream, &M);
-        lk.lock();
-        if (rc) {
-            finish(S, r, 3, rc, mm_last_error());
-            continue;
+        if (!rc) rc = alloc_map(ctx, &r->p, r->g, L, S->upload[idx], &M);
+        if (!rc) {
+            const cudaError_t e = cudaStreamSynchronize(S->upload[idx]);
+            if (e != cudaSuccess) rc = cuda_fail(e, "admission upload");
         }
-        r->map = M;
-        r->tiles = r->g.tiles();
-        r->t_admit = now_s();
-        r->state.store(1);
-        S->active.push_back(r);
+        if (rc) msg = mm_last_error();
+        lk.lock();
+        S->preparing--;
+        S->reserved_bytes -= r->footprint;
+        if (rc) {
+            finish(S, r, 3, rc, msg);
+        } else {
+            r->map = M;
+            r->tiles = r->g.tiles();
+            S->ready.push_back(r);
+        }
+        S->cv.notify_all();
+        S->admit_cv.notify_all();
     }
 }
 
@@ -147,8 +179,41 @@ static int capture_graph(Server *S, int b)
     return MM_OK;
 }
 
+// Slice sizes for the next wave: an even share of the work budget per live map, then
+// doubled shares until the wave holds at least `min_tiles` tiles (or all that is left).
+static void plan_wave(Server *S, Wave *w)
+{
+    std::vector<std::shared_ptr<Request>> live;
+    for (auto &r : S->active)
+        if (r->cursor < r->tiles) live.push_back(r);
+    if (live.empty()) return;
+    const unsigned long long min_tiles =
+        4ULL * (unsigned long long)S->ctx->sms * (unsigned long long)shoot_ctas_per_sm(false, S->ctx->layout);
+    unsigned long long left_all = 0;
+    for (auto &r : live) left_all += r->tiles - r->cursor;
+    double share = std::max(1.0, S->wave_ms * S->rate) / (double)live.size();
+    std::vector<unsigned long long> take(live.size(), 0);
+    for (int round = 0; round < 64; ++round) {
+        unsigned long long sum = 0;
+        for (size_t k = 0; k < live.size(); ++k) {
+            const unsigned long long left = live[k]->tiles - live[k]->cursor;
+            const double want = std::max(1.0, std::floor(share / tile_cost(*live[k])));
+            take[k] = std::min(left, (unsigned long long)std::min(want, 1e15));
+            sum += take[k];
+        }
+        if (sum >= std::min(min_tiles, left_all)) break;
+        share *= 2.0;
+    }
+    for (size_t k = 0; k < live.size(); ++k) {
+        if (!take[k]) continue;
+        w->items.push_back(WaveItem{live[k], take[k], live[k]->cursor + take[k] == live[k]->tiles});
+        w->tiles += take[k];
+        w->interactions += (double)take[k] * tile_cost(*live[k]);
+    }
+}
+
 // Write the wave's descriptors into buffer b and enqueue it on the server stream.
-static int launch_wave(Server *S, Wave *w, const std::vector<unsigned long long> &sizes)
+static int launch_wave(Server *S, Wave *w)
 {
     mm_ctx *ctx = S->ctx;
     const int b = w->buf;
@@ -166,15 +231,16 @@ static int launch_wave(Server *S, Wave *w, const std::vector<unsigned long long>
     unsigned long long tot32 = 0, tot64 = 0;
     int k32 = 0, k64 = 0;
     for (size_t q : idx) {
-        Request &r = *w->items[q].req;
+        WaveItem &it = w->items[q];
+        Request &r = *it.req;
         const bool fp64 = r.p.precision == MM_FP64;
         MapDesc *d = fp64 ? &S->sc64[b].h_maps[k64++] : &S->sc[b].h_maps[k32++];
         fill_desc(*r.map, d);
         d->tile_first = r.cursor;
-        d->tile_count = sizes[q];
+        d->tile_count = it.tiles;
         d->tile_begin = fp64 ? tot64 : tot32;
-        (fp64 ? tot64 : tot32) += sizes[q];
-        r.cursor += sizes[q];
+        (fp64 ? tot64 : tot32) += it.tiles;
+        r.cursor += it.tiles;
     }
     S->sc[b].h_hdr->total_work = tot32;
     S->sc[b].h_hdr->n_maps = n32;
@@ -220,7 +286,12 @@ static void complete_wave(Server *S, Wave &w, std::unique_lock<std::mutex> &lk)
         for (auto &it : w.items) finish(S, it.req, 3, MM_EDEVICE, S->fatal);
         return;
     }
-    if (ms > 0.05f) S->rate = 0.7 * S->rate + 0.3 * (w.interactions / (double)ms);
+    // refine the device rate from waves large enough to fill the GPU
+    const unsigned long long full = 2ULL * (unsigned long long)S->ctx->sms;
+    if (ms > 0.2f && w.tiles >= full) {
+        const double r = w.interactions / (double)ms;
+        S->rate = std::min(2.0e10, std::max(5.0e8, 0.8 * S->rate + 0.2 * r));
+    }
     for (auto &it : w.items) {
         if (!it.last) continue;
         auto &r = it.req;
@@ -229,6 +300,7 @@ static void complete_wave(Server *S, Wave &w, std::unique_lock<std::mutex> &lk)
         S->active.erase(std::remove(S->active.begin(), S->active.end(), r), S->active.end());
         finish(S, r, 2, MM_OK, "");
     }
+    S->admit_cv.notify_all();
 }
 
 static void loop(Server *S)
@@ -245,10 +317,11 @@ static void loop(Server *S)
             for (auto &r : S->queue) finish(S, r, 4, MM_ECANCELED, "server stopped");
             S->queue.clear();
         }
-        admit(S, lk);
+        for (auto &r : S->ready) S->active.push_back(r);
+        S->ready.clear();
         bool have_work = false;
         for (auto &r : S->active) have_work = have_work || r->cursor < r->tiles;
-        if (S->stop && S->inflight.empty() && !have_work) {
+        if (S->stop && S->inflight.empty() && !have_work && S->preparing == 0) {
             for (auto &r : S->active) finish(S, r, 4, MM_ECANCELED, "server stopped");
             S->active.clear();
             break;
@@ -257,34 +330,8 @@ static void loop(Server *S)
             Wave w;
             w.buf = (int)(S->wave_counter & 1);
             w.id = S->wave_counter++;
-            // plan: even share of the work budget per live map
-            std::vector<std::shared_ptr<Request>> live;
-            for (auto &r : S->active)
-                if (r->cursor < r->tiles) live.push_back(r);
-            const double budget = std::max(1.0, S->wave_ms * S->rate);
-            const double share = budget / (double)live.size();
-            std::vector<unsigned long long> take(live.size(), 0);
-            double used = 0;
-            for (size_t k = 0; k < live.size(); ++k) {
-                const double c = tile_cost(*live[k]);
-                const unsigned long long left = live[k]->tiles - live[k]->cursor;
-                take[k] = std::min(left, (unsigned long long)std::max(1.0, std::floor(share / c)));
-                used += (double)take[k] * c;
-            }
-            for (size_t k = 0; k < live.size() && used < budget; ++k) {
-                const double c = tile_cost(*live[k]);
-                const unsigned long long left = live[k]->tiles - live[k]->cursor - take[k];
-                const unsigned long long extra = std::min(left, (unsigned long long)std::floor((budget - used) / c));
-                take[k] += extra;
-                used += (double)extra * c;
-            }
-            std::vector<unsigned long long> sizes;
-            for (size_t k = 0; k < live.size(); ++k) {
-                w.items.push_back(WaveItem{live[k], live[k]->cursor + take[k] == live[k]->tiles});
-                sizes.push_back(take[k]);
-                w.interactions += (double)take[k] * tile_cost(*live[k]);
-            }
-            int rc = launch_wave(S, &w, sizes);
+            plan_wave(S, &w);
+            int rc = launch_wave(S, &w);
             if (rc) {
                 S->fatal = mm_last_error();
                 for (auto &it : w.items) finish(S, it.req, 3, rc, S->fatal);
@@ -310,8 +357,9 @@ int server_start(mm_ctx *ctx)
     S->ctx = ctx;
     cudaSetDevice(ctx->device);
     cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->upload, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->capture, cudaStreamNonBlocking);
+    for (int k = 0; k < kAdmitWorkers && e == cudaSuccess; ++k)
+        e = cudaStreamCreateWithFlags(&S->upload[k], cudaStreamNonBlocking);
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
         e = cudaEventCreate(&S->ev_start[b]);
         if (e == cudaSuccess) e = cudaEventCreate(&S->ev_end[b]);
@@ -322,6 +370,7 @@ int server_start(mm_ctx *ctx)
     }
     ctx->server = S;
     S->th = std::thread(loop, S);
+    for (int k = 0; k < kAdmitWorkers; ++k) S->workers.emplace_back(admit_worker, S, k);
     return MM_OK;
 }
 
@@ -334,6 +383,9 @@ void server_stop(mm_ctx *ctx)
         S->stop = true;
     }
     S->cv.notify_all();
+    S->admit_cv.notify_all();
+    for (auto &t : S->workers)
+        if (t.joinable()) t.join();
     if (S->th.joinable()) S->th.join();
     cudaStreamSynchronize(S->stream);
     for (int b = 0; b < 2; ++b) {
@@ -344,8 +396,8 @@ void server_stop(mm_ctx *ctx)
         cudaEventDestroy(S->ev_end[b]);
     }
     cudaStreamDestroy(S->stream);
-    cudaStreamDestroy(S->upload);
     cudaStreamDestroy(S->capture);
+    for (int k = 0; k < kAdmitWorkers; ++k) cudaStreamDestroy(S->upload[k]);
     {
         std::lock_guard<std::mutex> lk(S->mu);
         S->reqs.clear();
@@ -376,6 +428,7 @@ int mm_serve_config(mm_ctx *ctx, int32_t max_active, int32_t max_queued, double 
     if (max_active) S->max_active = max_active;
     if (max_queued) S->max_queued = max_queued;
     if (wave_ms > 0.0) S->wave_ms = wave_ms;
+    S->admit_cv.notify_all();
     return MM_OK;
 }
 
@@ -405,7 +458,7 @@ int mm_submit(mm_ctx *ctx, mm_lenses lenses, const mm_params *p, mm_req *out)
         S->queue.push_back(r);
         S->reqs[r->id] = r;
     }
-    S->cv.notify_all();
+    S->admit_cv.notify_one();
     *out = r->id;
     return MM_OK;
 }
@@ -428,8 +481,14 @@ int mm_poll(mm_ctx *ctx, mm_req req, int *done, mm_map *map_out)
         if (map_out) *map_out = r->map_handle;
         return MM_OK;
     }
-    if (st == 3) { *done = 1; return fail(r->err, r->err_msg); }
-    if (st == 4) { *done = 1; return fail(MM_ECANCELED, "request cancelled"); }
+    if (st == 3) {
+        *done = 1;
+        return fail(r->err, r->err_msg);
+    }
+    if (st == 4) {
+        *done = 1;
+        return fail(MM_ECANCELED, "request cancelled");
+    }
     return MM_OK;
 }
 
