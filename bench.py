@@ -436,7 +436,7 @@ def main():
     extra = {}
     if not args.no_extras and world == 1:
         extra["batch"] = batch_phase(mm, ctx)
-        mm.mm_serve_config(ctx, max_active=64, wave_ms=4.0)
+        mm.mm_serve_config(ctx, max_active=64, wave_ms=25.0)
         capacity = extra["batch"]["batched_interactions_per_s"]          # the same mix shape, batched
         mean_inter = np.mean([i for _, i in scaled_mix(200, 6, large_every=10)])
         lam = 0.7 * capacity / mean_inter

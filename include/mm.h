@@ -107,6 +107,9 @@ typedef struct {
     int64_t  nstar;
     double   seconds;       /* device time of the map's shoot, CUDA events (0 if unknown) */
     double   mu_mean;       /* rays_in / (N_side^2 N_rays) */
+    int32_t  lens_splits;   /* lens segments per ray tile: maps with few tiles (< 2048) and many
+                               lenses (> 1024) spread each tile's lens sum over several CTAs and
+                               combine the segments' float-float sums in segment order */
 } mm_stats;
 
 typedef struct {

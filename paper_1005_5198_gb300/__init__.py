@@ -40,7 +40,7 @@ class mm_params(C.Structure):
 class mm_stats(C.Structure):
     _fields_ = [("rays_shot", C.c_uint64), ("rays_in", C.c_uint64), ("rays_out", C.c_uint64),
                 ("interactions", C.c_uint64), ("nx", C.c_uint64), ("ny", C.c_uint64), ("nstar", C.c_int64),
-                ("seconds", C.c_double), ("mu_mean", C.c_double)]
+                ("seconds", C.c_double), ("mu_mean", C.c_double), ("lens_splits", C.c_int32)]
 
 
 class mm_geometry(C.Structure):

@@ -65,18 +65,27 @@ struct LensSet {
     static size_t footprint(long long n);
 };
 
+// Lens segments per tile for a map (see kSplitTargetItems): *splits >= 1 and the
+// lenses per segment, a multiple of the staging chunk.
+void lens_split(const Geo &g, int precision, int *splits, long long *seg_lenses);
+
 struct MapObj {
     mm_params p{};
     Geo g{};
     unsigned int *counts = nullptr;
     unsigned long long *totals = nullptr;   // [in, out]
+    int splits = 1;                          // lens segments per tile
+    long long seg_lenses = 0;
+    float4 *partial = nullptr;               // split tiles: segment sums
+    unsigned int *seg_done = nullptr;        // split tiles: finished segments per tile
     std::shared_ptr<LensSet> lenses;
     cudaEvent_t done = nullptr;
     double seconds = 0.0;
     int variant = 0;
     DeviceArena *arena = nullptr;
     ~MapObj();
-    static size_t footprint(int npix_side);
+    unsigned long long items() const { return g.tiles() * (unsigned long long)splits; }
+    static size_t footprint(const mm_params *p, const Geo &g);
 };
 
 struct Server;

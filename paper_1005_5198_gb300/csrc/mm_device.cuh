@@ -68,7 +68,21 @@ struct LoopSmem {
     unsigned long long g;
     int map;
     unsigned red_in, red_out;
+    int last_segment;              // split tiles: this CTA finished the tile's last segment
 };
+
+// Float-float addition of two (x_hi, x_lo, y_hi, y_lo) sums (lo parts unnormalised).
+__device__ __forceinline__ float4 ff_add4(float4 a, float4 b)
+{
+    float s, e;
+    two_sum(a.x, b.x, s, e);
+    a.x = s;
+    a.y = __fadd_rn(a.y, __fadd_rn(e, b.y));
+    two_sum(a.z, b.z, s, e);
+    a.z = s;
+    a.w = __fadd_rn(a.w, __fadd_rn(e, b.w));
+    return a;
+}
 
 struct __align__(16) SmemFP32 {
     float4 pos[kChunkPairs];       // (xa, xb, ya, yb) relative to the tile centre
@@ -88,9 +102,9 @@ struct __align__(16) SmemFP64 {
 __device__ __forceinline__ int find_map(const LaunchArgs &A, int n_maps, unsigned long long g)
 {
     int lo = 0, hi = n_maps - 1;
-    while (lo < hi) {                              // last map with tile_begin <= g
+    while (lo < hi) {                              // last map with item_begin <= g
         const int mid = (lo + hi + 1) >> 1;
-        if (A.maps[mid].tile_begin <= g) lo = mid; else hi = mid - 1;
+        if (A.maps[mid].item_begin <= g) lo = mid; else hi = mid - 1;
     }
     return lo;
 }
@@ -132,8 +146,8 @@ __device__ __forceinline__ void emit_ray(const LaunchArgs &A, const MapDesc &M, 
 }
 
 // Persistent loop: take work items from the launch's counter until exhausted,
-// run `body(M, tile, item, cnt_in, cnt_out)` on each, and add the in/out ray
-// counts to the map totals whenever the map changes and at exit.
+// run `body(M, tile, segment, dump_item, cnt_in, cnt_out)` on each, and add the
+// in/out ray counts to the map totals whenever the map changes and at exit.
 template <bool DUMP, typename Body>
 __device__ __forceinline__ void persistent_loop(const LaunchArgs &A, LoopSmem &S, Body body)
 {
@@ -163,9 +177,11 @@ __device__ __forceinline__ void persistent_loop(const LaunchArgs &A, LoopSmem &S
             run_in = run_out = 0;
         }
         const MapDesc &M = A.maps[mi];
-        const unsigned long long tile = DUMP ? A.dump.tile[g] : M.tile_first + (g - M.tile_begin);
+        const unsigned long long nsp = (unsigned long long)M.lens_splits;
+        const unsigned long long work =
+            DUMP ? A.dump.tile[g / nsp] * nsp + g % nsp : M.item_first + (g - M.item_begin);
         unsigned ci = 0, co = 0;
-        body(M, tile, DUMP ? (int)g : 0, ci, co);
+        body(M, work / nsp, (int)(work % nsp), DUMP ? (int)(g / nsp) : 0, ci, co);
         if (!DUMP) {
             ci = __reduce_add_sync(0xffffffffu, ci);
             co = __reduce_add_sync(0xffffffffu, co);

@@ -108,9 +108,9 @@ __device__ __forceinline__ void pair_step(const float4 P, const float2 Mm, const
     }
 }
 
-template <class L, int C, int R, int SHARED4, int FOLD, bool MASS, bool DUMP>
-__device__ void tile_fp32(const LaunchArgs &A, const MapDesc &M, unsigned long long tile, int item, SmemFP32 &S,
-                          unsigned &cnt_in, unsigned &cnt_out)
+template <class L, int C, int R, int SHARED4, int FOLD, bool MASS, bool DUMP, bool SPLIT>
+__device__ void tile_fp32(const LaunchArgs &A, const MapDesc &M, unsigned long long tile, int seg, int item,
+                          SmemFP32 &S, unsigned &cnt_in, unsigned &cnt_out)
 {
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -161,8 +161,10 @@ __device__ void tile_fp32(const LaunchArgs &A, const MapDesc &M, unsigned long l
         }
     unsigned onlens = 0;                              // bit c*R + r: ray exactly on a lens
 
-    const long long nstar = M.nstar;
-    for (long long base = 0; base < nstar; base += kChunkLenses) {
+    // lens range of this work item: all lenses, or one segment of a split tile
+    const long long lens_begin = SPLIT ? (long long)seg * M.seg_lenses : 0;
+    const long long nstar = (SPLIT && M.lens_splits > 1) ? min(M.nstar, lens_begin + M.seg_lenses) : M.nstar;
+    for (long long base = lens_begin; base < nstar; base += kChunkLenses) {
         // ---- stage 256 lens pairs relative to the tile centre ----
         __syncthreads();                               // previous chunk fully consumed
 #pragma unroll
@@ -264,6 +266,26 @@ __device__ void tile_fp32(const LaunchArgs &A, const MapDesc &M, unsigned long l
         }
     }
 
+    // ---- split tile: publish this segment's sums; the last segment combines them ----
+    float4 *part = nullptr;
+    if (SPLIT && M.lens_splits > 1) {
+        part = M.partial + (size_t)tile * (size_t)M.lens_splits * kTileRays;
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float4 a = acc.get(c, r);
+                if ((onlens >> (c * R + r)) & 1u) a.x = __int_as_float(0x7fc00000);   // NaN: ray on a lens
+                part[(size_t)seg * kTileRays + (col0 + 32 * c) + kTileX * (row0 + r)] = a;
+            }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) S.loop.last_segment = (atomicAdd(M.seg_done + tile, 1u) == (unsigned)(M.lens_splits - 1));
+        __syncthreads();
+        if (!S.loop.last_segment) return;
+        __threadfence();
+    }
+
     // ---- epilogue: lens equation and pixel (float-float) ----
     const float nsf = (float)M.nside;
 #pragma unroll
@@ -277,7 +299,14 @@ __device__ void tile_fp32(const LaunchArgs &A, const MapDesc &M, unsigned long l
             const long long gj = jb + row0 + r;
             float uyh, uyl;
             ff_axis(M.ay_h, M.ay_l, (float)(2 * gj + 1 - M.ny), M.half_n, uyh, uyl);
-            const float4 a = acc.get(c, r);
+            float4 a;
+            if (SPLIT && part) {                          // split tile: segments in order
+                const int local = (col0 + 32 * c) + kTileX * (row0 + r);
+                a = __ldcg(part + local);
+                for (int sg = 1; sg < M.lens_splits; ++sg) a = ff_add4(a, __ldcg(part + (size_t)sg * kTileRays + local));
+            } else {
+                a = acc.get(c, r);
+            }
             const float I1 = ff_pixel(uxh, uxl, a.x, a.y, M.ip_h, M.ip_l);
             const float I2 = ff_pixel(uyh, uyl, a.z, a.w, M.ip_h, M.ip_l);
             const bool valid = col_ok && gj < M.j0 + M.nj;
@@ -290,43 +319,51 @@ __device__ void tile_fp32(const LaunchArgs &A, const MapDesc &M, unsigned long l
     }
 }
 
-template <class L, int C, int R, int SHARED4, int FOLD, bool DUMP>
+template <class L, int C, int R, int SHARED4, int FOLD, bool DUMP, bool SPLIT>
 __device__ __forceinline__ void tile_fp32_any_mass(const LaunchArgs &A, const MapDesc &M, unsigned long long tile,
-                                                   int item, SmemFP32 &S, unsigned &ci, unsigned &co)
+                                                   int seg, int item, SmemFP32 &S, unsigned &ci, unsigned &co)
 {
-    if (M.unit_mass) tile_fp32<L, C, R, SHARED4, FOLD, false, DUMP>(A, M, tile, item, S, ci, co);
-    else tile_fp32<L, C, R, SHARED4, FOLD, true, DUMP>(A, M, tile, item, S, ci, co);
+    if (M.unit_mass) tile_fp32<L, C, R, SHARED4, FOLD, false, DUMP, SPLIT>(A, M, tile, seg, item, S, ci, co);
+    else tile_fp32<L, C, R, SHARED4, FOLD, true, DUMP, SPLIT>(A, M, tile, seg, item, S, ci, co);
 }
 
 // Runtime variant of a map (shared-reciprocal pairs per 4, fold interval).
-template <class L, int C, int R, bool DUMP>
-__device__ void tile_fp32_dispatch(const LaunchArgs &A, const MapDesc &M, unsigned long long tile, int item,
-                                   SmemFP32 &S, unsigned &ci, unsigned &co)
+template <class L, int C, int R, bool DUMP, bool SPLIT>
+__device__ void tile_fp32_dispatch(const LaunchArgs &A, const MapDesc &M, unsigned long long tile, int seg,
+                                   int item, SmemFP32 &S, unsigned &ci, unsigned &co)
 {
     switch (M.variant) {
-    case 1: tile_fp32_any_mass<L, C, R, 3, 32, DUMP>(A, M, tile, item, S, ci, co); break;
-    case 2: tile_fp32_any_mass<L, C, R, 2, 64, DUMP>(A, M, tile, item, S, ci, co); break;
-    case 3: tile_fp32_any_mass<L, C, R, 4, 64, DUMP>(A, M, tile, item, S, ci, co); break;
-    default: tile_fp32_any_mass<L, C, R, 3, 64, DUMP>(A, M, tile, item, S, ci, co); break;
+    case 1: tile_fp32_any_mass<L, C, R, 3, 32, DUMP, SPLIT>(A, M, tile, seg, item, S, ci, co); break;
+    case 2: tile_fp32_any_mass<L, C, R, 2, 64, DUMP, SPLIT>(A, M, tile, seg, item, S, ci, co); break;
+    case 3: tile_fp32_any_mass<L, C, R, 4, 64, DUMP, SPLIT>(A, M, tile, seg, item, S, ci, co); break;
+    default: tile_fp32_any_mass<L, C, R, 3, 64, DUMP, SPLIT>(A, M, tile, seg, item, S, ci, co); break;
     }
 }
 
-template <int C, int R, bool SREG, int MINB, bool DUMP>
+// SPLIT: the launch contains maps whose tiles are split over lens segments (kept out of
+// the kernel used for unsplit launches, whose register allocation it would crowd).
+template <int C, int R, bool SREG, int MINB, bool DUMP, bool SPLIT>
 __global__ void __launch_bounds__(Layout<C, R, SREG, MINB>::NT, MINB) k_shoot_fp32(const LaunchArgs A)
 {
     using L = Layout<C, R, SREG, MINB>;
     __shared__ SmemFP32 S;
-    persistent_loop<DUMP>(A, S.loop, [&](const MapDesc &M, unsigned long long tile, int item, unsigned &ci, unsigned &co) {
-        tile_fp32_dispatch<L, C, R, DUMP>(A, M, tile, item, S, ci, co);
+    persistent_loop<DUMP>(A, S.loop, [&](const MapDesc &M, unsigned long long tile, int seg, int item, unsigned &ci,
+                                          unsigned &co) {
+        tile_fp32_dispatch<L, C, R, DUMP, SPLIT>(A, M, tile, seg, item, S, ci, co);
     });
 }
 
 template <int C, int R, bool SREG, int MINB>
-cudaError_t launch_fp32_layout(const LaunchArgs &args, int grid, bool dump, cudaStream_t s)
+cudaError_t launch_fp32_layout(const LaunchArgs &args, int grid, bool dump, bool split, cudaStream_t s)
 {
     constexpr int NT = Layout<C, R, SREG, MINB>::NT;
-    if (dump) k_shoot_fp32<C, R, SREG, MINB, true><<<grid, NT, 0, s>>>(args);
-    else k_shoot_fp32<C, R, SREG, MINB, false><<<grid, NT, 0, s>>>(args);
+    if (split) {
+        if (dump) k_shoot_fp32<C, R, SREG, MINB, true, true><<<grid, NT, 0, s>>>(args);
+        else k_shoot_fp32<C, R, SREG, MINB, false, true><<<grid, NT, 0, s>>>(args);
+    } else {
+        if (dump) k_shoot_fp32<C, R, SREG, MINB, true, false><<<grid, NT, 0, s>>>(args);
+        else k_shoot_fp32<C, R, SREG, MINB, false, false><<<grid, NT, 0, s>>>(args);
+    }
     return cudaGetLastError();
 }
 

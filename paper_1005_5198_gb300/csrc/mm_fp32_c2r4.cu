@@ -4,8 +4,8 @@
 #include "mm_fp32.cuh"
 
 namespace mm {
-cudaError_t launch_fp32_layout1(const LaunchArgs &args, int grid, bool dump, cudaStream_t s)
+cudaError_t launch_fp32_layout1(const LaunchArgs &args, int grid, bool dump, bool split, cudaStream_t s)
 {
-    return dev::launch_fp32_layout<2, 4, true, 2>(args, grid, dump, s);
+    return dev::launch_fp32_layout<2, 4, true, 2>(args, grid, dump, split, s);
 }
 }  // namespace mm

@@ -11,10 +11,10 @@
 
 namespace mm {
 
-cudaError_t launch_fp32_layout0(const LaunchArgs &, int, bool, cudaStream_t);
-cudaError_t launch_fp32_layout1(const LaunchArgs &, int, bool, cudaStream_t);
-cudaError_t launch_fp32_layout2(const LaunchArgs &, int, bool, cudaStream_t);
-cudaError_t launch_fp32_layout3(const LaunchArgs &, int, bool, cudaStream_t);
+cudaError_t launch_fp32_layout0(const LaunchArgs &, int, bool, bool, cudaStream_t);
+cudaError_t launch_fp32_layout1(const LaunchArgs &, int, bool, bool, cudaStream_t);
+cudaError_t launch_fp32_layout2(const LaunchArgs &, int, bool, bool, cudaStream_t);
+cudaError_t launch_fp32_layout3(const LaunchArgs &, int, bool, bool, cudaStream_t);
 
 namespace dev {
 namespace {
@@ -91,9 +91,8 @@ template <bool DUMP>
 __global__ void __launch_bounds__(256, 1) k_shoot_fp64(const LaunchArgs A)
 {
     __shared__ SmemFP64 S;
-    persistent_loop<DUMP>(A, S.loop, [&](const MapDesc &M, unsigned long long tile, int item, unsigned &ci, unsigned &co) {
-        tile_fp64<DUMP>(A, M, tile, item, S, ci, co);
-    });
+    persistent_loop<DUMP>(A, S.loop, [&](const MapDesc &M, unsigned long long tile, int, int item, unsigned &ci,
+                                          unsigned &co) { tile_fp64<DUMP>(A, M, tile, item, S, ci, co); });
 }
 
 __global__ void k_prepare_lenses(const double *x, const double *y, const double *m, long long n, long long n_pad,
@@ -125,13 +124,13 @@ cudaError_t launch_prepare_lenses(const double *x, const double *y, const double
     return cudaGetLastError();
 }
 
-cudaError_t launch_shoot_fp32(const LaunchArgs &args, int layout, int grid, bool dump, cudaStream_t s)
+cudaError_t launch_shoot_fp32(const LaunchArgs &args, int layout, int grid, bool dump, bool split, cudaStream_t s)
 {
     switch (layout) {
-    case 1: return launch_fp32_layout1(args, grid, dump, s);
-    case 2: return launch_fp32_layout2(args, grid, dump, s);
-    case 3: return launch_fp32_layout3(args, grid, dump, s);
-    default: return launch_fp32_layout0(args, grid, dump, s);
+    case 1: return launch_fp32_layout1(args, grid, dump, split, s);
+    case 2: return launch_fp32_layout2(args, grid, dump, split, s);
+    case 3: return launch_fp32_layout3(args, grid, dump, split, s);
+    default: return launch_fp32_layout0(args, grid, dump, split, s);
     }
 }
 

@@ -254,11 +254,38 @@ MapObj::~MapObj()
     if (!arena) return;
     arena->free(counts);
     arena->free(totals);
+    arena->free(partial);
+    arena->free(seg_done);
 }
 
-size_t MapObj::footprint(int npix_side)
+void lens_split(const Geo &g, int precision, int *splits, long long *seg_lenses)
 {
-    return DeviceArena::round((size_t)npix_side * (size_t)npix_side * 4) + DeviceArena::round(16);
+    *splits = 1;
+    *seg_lenses = std::max(g.nstar, 1LL);
+    const unsigned long long tiles = g.tiles();
+    if (precision != MM_FP32C || tiles == 0 || tiles >= kSplitTargetItems || g.nstar <= 2 * kChunkLenses) return;
+    const long long chunks = (g.nstar + kChunkLenses - 1) / kChunkLenses;
+    const long long want = (long long)((kSplitTargetItems + tiles - 1) / tiles);
+    const long long s = std::min(chunks, want);
+    const long long seg_chunks = (chunks + s - 1) / s;
+    *seg_lenses = seg_chunks * kChunkLenses;
+    *splits = (int)((g.nstar + *seg_lenses - 1) / *seg_lenses);
+    if (*splits <= 1) {
+        *splits = 1;
+        *seg_lenses = g.nstar;
+    }
+}
+
+size_t MapObj::footprint(const mm_params *p, const Geo &g)
+{
+    int splits;
+    long long seg;
+    lens_split(g, p->precision, &splits, &seg);
+    size_t b = DeviceArena::round((size_t)p->npix_side * (size_t)p->npix_side * 4) + DeviceArena::round(16);
+    if (splits > 1)
+        b += DeviceArena::round(g.tiles() * (size_t)splits * kTileRays * sizeof(float4)) +
+             DeviceArena::round(g.tiles() * sizeof(unsigned));
+    return b;
 }
 
 // ------------------------------------------------------------ lens sets ---
@@ -318,6 +345,15 @@ int alloc_map(mm_ctx *ctx, const mm_params *p, const Geo &g, std::shared_ptr<Len
     if ((rc = ctx->arena.alloc(map_bytes(p), (void **)&M->counts)) ||
         (rc = ctx->arena.alloc(2 * sizeof(unsigned long long), (void **)&M->totals)))
         return rc;
+    Geo gl = g;
+    gl.nstar = M->lenses->n;
+    lens_split(gl, p->precision, &M->splits, &M->seg_lenses);
+    if (M->splits > 1) {
+        if ((rc = ctx->arena.alloc(g.tiles() * (size_t)M->splits * kTileRays * sizeof(float4), (void **)&M->partial)) ||
+            (rc = ctx->arena.alloc(g.tiles() * sizeof(unsigned), (void **)&M->seg_done)))
+            return rc;
+        MM_CUDA(cudaMemsetAsync(M->seg_done, 0, g.tiles() * sizeof(unsigned), s));
+    }
     MM_CUDA(cudaEventCreateWithFlags(&M->done, cudaEventDisableTiming));
     MM_CUDA(cudaMemsetAsync(M->counts, 0, map_bytes(p), s));
     MM_CUDA(cudaMemsetAsync(M->totals, 0, 2 * sizeof(unsigned long long), s));
@@ -363,6 +399,10 @@ void fill_desc(const MapObj &m, MapDesc *d)
     d->lh = m.lenses->lh; d->lmf = m.lenses->lmf;
     d->counts = m.counts;
     d->totals = m.totals;
+    d->lens_splits = m.splits;
+    d->seg_lenses = m.splits > 1 ? m.seg_lenses : std::max(m.lenses->n, 1LL);
+    d->partial = m.partial;
+    d->seg_done = m.seg_done;
 }
 
 static int class_key(const mm_params *p, long long nstar)
@@ -430,18 +470,22 @@ static int launch_group(mm_ctx *ctx, std::vector<MapObj *> &group, bool fp64, co
     LaunchScratch *sc = &ctx->scratch;
     int rc = scratch_reserve(ctx, sc, (int)group.size());
     if (rc) return rc;
-    std::stable_sort(group.begin(), group.end(),
-                     [](const MapObj *a, const MapObj *b) { return a->lenses->n > b->lenses->n; });
+    std::stable_sort(group.begin(), group.end(), [](const MapObj *a, const MapObj *b) {
+        const long long ca = a->splits > 1 ? a->seg_lenses : a->lenses->n;
+        const long long cb = b->splits > 1 ? b->seg_lenses : b->lenses->n;
+        return ca > cb;                                  // most expensive work items first
+    });
     unsigned long long total = 0;
     for (size_t k = 0; k < group.size(); ++k) {
         MapDesc *d = &sc->h_maps[k];
         fill_desc(*group[k], d);
-        d->tile_begin = total;
-        d->tile_first = 0;
-        d->tile_count = group[k]->g.tiles();
-        total += d->tile_count;
+        d->item_begin = total;
+        d->item_first = 0;
+        d->item_count = group[k]->items();
+        total += d->item_count;
     }
-    sc->h_hdr->total_work = dump ? dump_items : total;
+    // a debug dump covers dump_items tiles of one map, each with all its lens segments
+    sc->h_hdr->total_work = dump ? dump_items * (unsigned long long)group[0]->splits : total;
     sc->h_hdr->n_maps = (int)group.size();
     MM_CUDA(cudaMemcpyAsync(sc->d_hdr, sc->h_hdr, sizeof(WorkHeader), cudaMemcpyHostToDevice, s));
     MM_CUDA(cudaMemcpyAsync(sc->d_maps, sc->h_maps, group.size() * sizeof(MapDesc), cudaMemcpyHostToDevice, s));
@@ -455,9 +499,11 @@ static int launch_group(mm_ctx *ctx, std::vector<MapObj *> &group, bool fp64, co
     const long long cap = (long long)ctx->sms * shoot_ctas_per_sm(fp64, ctx->layout);
     const int grid = (int)std::max(1LL, std::min((long long)work, cap));
     MM_CUDA(cudaEventRecord(ctx->ev0, s));
+    bool split = false;
+    for (const MapObj *m : group) split = split || m->splits > 1;
     if (work > 0)
         MM_CUDA(fp64 ? launch_shoot_fp64(a, grid, dump != nullptr, s)
-                     : launch_shoot_fp32(a, ctx->layout, grid, dump != nullptr, s));
+                     : launch_shoot_fp32(a, ctx->layout, grid, dump != nullptr, split, s));
     MM_CUDA(cudaEventRecord(ctx->ev1, s));
     MM_CUDA(cudaEventSynchronize(ctx->ev1));     // pinned scratch is reused by the next call
     float t = 0.f;
@@ -756,6 +802,7 @@ int mm_map_fetch(mm_ctx *ctx, mm_map map, uint32_t *host_counts, size_t n_elems,
         st->nstar = M->lenses->n;
         st->seconds = M->seconds;
         st->mu_mean = (double)tot[0] / ((double)npix * M->p.nrays_per_pix);
+        st->lens_splits = M->splits;
     }
     return MM_OK;
 }

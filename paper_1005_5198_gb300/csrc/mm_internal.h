@@ -36,9 +36,12 @@ struct MapDesc {
     long long nx, ny;          // global grid
     long long i0, j0, ni, nj;  // shot sub-rectangle [i0, i0+ni) x [j0, j0+nj)
     long long tiles_x;         // ceil(ni / 64)
-    unsigned long long tile_begin;   // first work item of this map in the launch
-    unsigned long long tile_count;   // work items of this map in the launch
-    unsigned long long tile_first;   // map tile index of its first work item (waves)
+    // work items: tiles x lens segments; item w = tile * lens_splits + segment
+    unsigned long long item_begin;   // first work item of this map in the launch
+    unsigned long long item_count;   // work items of this map in the launch
+    unsigned long long item_first;   // map work item of the launch's first item (waves)
+    int lens_splits;                 // segments per tile (1: whole lens set in one CTA)
+    long long seg_lenses;            // lenses per segment, a multiple of kChunkLenses
     // plain FP64 lens equation (FP64 kernel and near-lens terms)
     double one_m_gamma, one_p_gamma, sigma_c, half_side, pix;
     // float-float epilogue: u = A*(2i+1-nx) + N/2 + S/p, S = sum m (x_l - x)/r^2 = -alpha
@@ -58,11 +61,20 @@ struct MapDesc {
     // outputs (device)
     unsigned int *counts;           // nside^2
     unsigned long long *totals;     // [0] rays in, [1] rays out (shot is ni*nj)
+    // split tiles (lens_splits > 1): per (tile, segment) the float-float sums of the
+    // tile's rays, [(tile * lens_splits + segment) * kTileRays + local ray], and per
+    // tile the number of segments finished
+    float4 *partial;
+    unsigned int *seg_done;
 };
 
-// Debug dump: per requested ray, the tile work item it belongs to and its slot.
+// Lens segments per tile of a map: split the lens set when a map has too few tiles to
+// fill the GPU, so that its work spreads over more CTAs. Depends only on the map.
+constexpr unsigned long long kSplitTargetItems = 2048;
+
+// Debug dump: per requested ray, the tile it belongs to and its slot.
 struct DumpArgs {
-    const unsigned long long *tile;   // per work item: tile index within map 0
+    const unsigned long long *tile;   // per dump tile: tile index within map 0 (work items = tiles x splits)
     const int *begin;                 // per work item: first request [n_items + 1]
     const int *local;                 // per request: local ray index iloc + 64 * jloc, ascending per item
     const int *slot;                  // per request: output slot
@@ -80,7 +92,7 @@ struct WorkHeader {
 
 struct LaunchArgs {
     const WorkHeader *hdr;
-    const MapDesc *maps;                  // hdr->n_maps descriptors, tile_begin ascending
+    const MapDesc *maps;                  // hdr->n_maps descriptors, item_begin ascending
     unsigned long long *work_counter;     // zeroed before the launch
     DumpArgs dump;
 };
@@ -91,8 +103,9 @@ struct LaunchArgs {
 cudaError_t launch_prepare_lenses(const double *x, const double *y, const double *m, long long n,
                                   long long n_pad, float4 *lh, float *lmf, cudaStream_t s);
 // FP32 (compensated) shoot over the work of args (every map precision MM_FP32C) with
-// thread layout `layout`; grid = number of CTAs (persistent).
-cudaError_t launch_shoot_fp32(const LaunchArgs &args, int layout, int grid, bool dump, cudaStream_t s);
+// thread layout `layout`; grid = number of CTAs (persistent); split: some map of the
+// launch has lens-split tiles.
+cudaError_t launch_shoot_fp32(const LaunchArgs &args, int layout, int grid, bool dump, bool split, cudaStream_t s);
 // Plain FP64 shoot (every map precision MM_FP64).
 cudaError_t launch_shoot_fp64(const LaunchArgs &args, int grid, bool dump, cudaStream_t s);
 // CTAs per SM the kernels are compiled for (FP32: per thread layout).

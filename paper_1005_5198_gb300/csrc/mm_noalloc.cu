@@ -129,11 +129,13 @@ extern "C" int mm_shoot_noalloc(const double *x, const double *y, const double *
     M.totals = reinterpret_cast<unsigned long long *>(totals);
     M.lenses = std::shared_ptr<LensSet>(&L, [](LensSet *) {});
     M.variant = kNoAllocVariant;
+    M.splits = 1;                            // no partial buffers without allocation: one CTA per tile
+    M.seg_lenses = std::max<long long>(nstar, 1);
     MapDesc d;
     fill_desc(M, &d);
-    d.tile_begin = 0;
-    d.tile_first = 0;
-    d.tile_count = g.tiles();
+    d.item_begin = 0;
+    d.item_first = 0;
+    d.item_count = g.tiles();
     WorkHeader h{};
     h.total_work = g.tiles();
     h.n_maps = 1;
@@ -153,7 +155,7 @@ extern "C" int mm_shoot_noalloc(const double *x, const double *y, const double *
     a.work_counter = &sc->counter;
     const long long cap = (long long)sms * shoot_ctas_per_sm(false, kNoAllocLayout);
     const int grid = (int)std::max(1LL, std::min((long long)h.total_work, cap));
-    if ((e = launch_shoot_fp32(a, kNoAllocLayout, grid, false, s)) != cudaSuccess)
+    if ((e = launch_shoot_fp32(a, kNoAllocLayout, grid, false, false, s)) != cudaSuccess)
         return cuda_fail(e, "no-alloc shoot launch");
     return MM_OK;
 }

@@ -14,8 +14,9 @@
 // CTA of the grid when the maps have that much work left, so maps with few
 // tiles and many lenses cannot leave the GPU idle. Requests that arrive while
 // waves run join the next wave, so their work overlaps on the device with the
-// maps already running. Two waves are kept in flight; a map is complete when
-// the wave that carried its last tile has finished. Each tile is computed
+// maps already running. Two waves are kept in flight, on two streams, so that the
+// next wave's CTAs start as the current wave's last tiles drain; a map is complete
+// when the wave that carried its last tile, and the wave before it, have finished. Each tile is computed
 // exactly as in mm_shoot, so results are bit-identical to shooting the map alone.
 #include <algorithm>
 #include <chrono>
@@ -37,8 +38,8 @@ struct Request {
     Geo g{};
     std::shared_ptr<LensSet> given;
     std::shared_ptr<MapObj> map;
-    unsigned long long cursor = 0;     // next map tile to schedule
-    unsigned long long tiles = 0;
+    unsigned long long cursor = 0;     // next work item to schedule
+    unsigned long long tiles = 0;      // work items of the map (tiles x lens segments)
     std::atomic<int> state{0};         // 0 queued, 1 admitted, 2 done, 3 failed, 4 cancelled
     int err = 0;
     std::string err_msg;
@@ -79,11 +80,12 @@ struct Server {
     std::unordered_map<uint64_t, std::shared_ptr<Request>> reqs;
     int max_active = 64, max_queued = 1 << 16;
     double wave_ms = 8.0;
-    cudaStream_t stream = nullptr, capture = nullptr;
+    cudaStream_t stream[2] = {nullptr, nullptr};     // waves alternate, so one fills the other's tail
+    cudaStream_t capture = nullptr;
     cudaStream_t upload[kAdmitWorkers] = {};
     LaunchScratch sc[2], sc64[2];
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    int graph_cap[2] = {0, 0};
+    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [buffer][split kernel]
+    int graph_cap[2][2] = {{0, 0}, {0, 0}};
     cudaEvent_t ev_start[2] = {nullptr, nullptr}, ev_end[2] = {nullptr, nullptr};
     std::deque<Wave> inflight;
     long long wave_counter = 0;
@@ -140,7 +142,7 @@ static void admit_worker(Server *S, int idx)
             finish(S, r, 3, rc, msg);
         } else {
             r->map = M;
-            r->tiles = r->g.tiles();
+            r->tiles = M->items();                       // work items: tiles x lens segments
             S->ready.push_back(r);
         }
         S->cv.notify_all();
@@ -148,15 +150,20 @@ static void admit_worker(Server *S, int idx)
     }
 }
 
-static double tile_cost(const Request &r) { return (double)kTileRays * (double)std::max(r.map->lenses->n, 8LL); }
+// Interactions of one work item (a tile, or one lens segment of a split tile).
+static double tile_cost(const Request &r)
+{
+    const long long n = r.map->splits > 1 ? r.map->seg_lenses : r.map->lenses->n;
+    return (double)kTileRays * (double)std::max(n, 8LL);
+}
 
-static int capture_graph(Server *S, int b)
+static int capture_graph(Server *S, int b, int split)
 {
     mm_ctx *ctx = S->ctx;
     LaunchScratch *sc = &S->sc[b];
-    if (S->gexec[b]) {
-        cudaGraphExecDestroy(S->gexec[b]);
-        S->gexec[b] = nullptr;
+    if (S->gexec[b][split]) {
+        cudaGraphExecDestroy(S->gexec[b][split]);
+        S->gexec[b][split] = nullptr;
     }
     LaunchArgs a{};
     a.hdr = sc->d_hdr;
@@ -169,13 +176,13 @@ static int capture_graph(Server *S, int b)
     cudaMemcpyAsync(sc->d_hdr, sc->h_hdr, sizeof(WorkHeader), cudaMemcpyHostToDevice, S->capture);
     cudaMemcpyAsync(sc->d_maps, sc->h_maps, (size_t)sc->cap * sizeof(MapDesc), cudaMemcpyHostToDevice, S->capture);
     cudaMemsetAsync(sc->d_counter, 0, sizeof(unsigned long long), S->capture);
-    launch_shoot_fp32(a, ctx->layout, grid, false, S->capture);
+    launch_shoot_fp32(a, ctx->layout, grid, false, split != 0, S->capture);
     e = cudaStreamEndCapture(S->capture, &g);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&S->gexec[b], g, 0);
+    e = cudaGraphInstantiate(&S->gexec[b][split], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-    S->graph_cap[b] = sc->cap;
+    S->graph_cap[b][split] = sc->cap;
     return MM_OK;
 }
 
@@ -212,7 +219,7 @@ static void plan_wave(Server *S, Wave *w)
     }
 }
 
-// Write the wave's descriptors into buffer b and enqueue it on the server stream.
+// Write the wave's descriptors into buffer b and enqueue it on stream b.
 static int launch_wave(Server *S, Wave *w)
 {
     mm_ctx *ctx = S->ctx;
@@ -225,9 +232,8 @@ static int launch_wave(Server *S, Wave *w)
     // order: decreasing per-tile cost within each precision (large tiles first)
     std::vector<size_t> idx(w->items.size());
     for (size_t k = 0; k < idx.size(); ++k) idx[k] = k;
-    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t c) {
-        return w->items[a].req->map->lenses->n > w->items[c].req->map->lenses->n;
-    });
+    std::stable_sort(idx.begin(), idx.end(),
+                     [&](size_t a, size_t c) { return tile_cost(*w->items[a].req) > tile_cost(*w->items[c].req); });
     unsigned long long tot32 = 0, tot64 = 0;
     int k32 = 0, k64 = 0;
     for (size_t q : idx) {
@@ -236,39 +242,47 @@ static int launch_wave(Server *S, Wave *w)
         const bool fp64 = r.p.precision == MM_FP64;
         MapDesc *d = fp64 ? &S->sc64[b].h_maps[k64++] : &S->sc[b].h_maps[k32++];
         fill_desc(*r.map, d);
-        d->tile_first = r.cursor;
-        d->tile_count = it.tiles;
-        d->tile_begin = fp64 ? tot64 : tot32;
+        d->item_first = r.cursor;
+        d->item_count = it.tiles;
+        d->item_begin = fp64 ? tot64 : tot32;
         (fp64 ? tot64 : tot32) += it.tiles;
         r.cursor += it.tiles;
     }
     S->sc[b].h_hdr->total_work = tot32;
     S->sc[b].h_hdr->n_maps = n32;
-    cudaEventRecord(S->ev_start[b], S->stream);
+    cudaStream_t st = S->stream[b];
+    cudaEventRecord(S->ev_start[b], st);
     if (n32) {
-        if (!S->gexec[b] || S->graph_cap[b] != S->sc[b].cap) {
-            if ((rc = capture_graph(S, b))) return rc;
+        int split = 0;
+        for (auto &it : w->items) split |= (it.req->p.precision == MM_FP32C && it.req->map->splits > 1) ? 1 : 0;
+        if (!S->gexec[b][split] || S->graph_cap[b][split] != S->sc[b].cap) {
+            if ((rc = capture_graph(S, b, split))) return rc;
         }
-        cudaError_t e = cudaGraphLaunch(S->gexec[b], S->stream);
+        cudaError_t e = cudaGraphLaunch(S->gexec[b][split], st);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
     }
     if (n64) {
         LaunchScratch *sc = &S->sc64[b];
         sc->h_hdr->total_work = tot64;
         sc->h_hdr->n_maps = n64;
-        cudaMemcpyAsync(sc->d_hdr, sc->h_hdr, sizeof(WorkHeader), cudaMemcpyHostToDevice, S->stream);
-        cudaMemcpyAsync(sc->d_maps, sc->h_maps, (size_t)n64 * sizeof(MapDesc), cudaMemcpyHostToDevice, S->stream);
-        cudaMemsetAsync(sc->d_counter, 0, sizeof(unsigned long long), S->stream);
+        cudaMemcpyAsync(sc->d_hdr, sc->h_hdr, sizeof(WorkHeader), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(sc->d_maps, sc->h_maps, (size_t)n64 * sizeof(MapDesc), cudaMemcpyHostToDevice, st);
+        cudaMemsetAsync(sc->d_counter, 0, sizeof(unsigned long long), st);
         LaunchArgs a{};
         a.hdr = sc->d_hdr;
         a.maps = sc->d_maps;
         a.work_counter = sc->d_counter;
-        cudaError_t e = launch_shoot_fp64(a, ctx->sms * shoot_ctas_per_sm(true, 0), false, S->stream);
+        cudaError_t e = launch_shoot_fp64(a, ctx->sms * shoot_ctas_per_sm(true, 0), false, st);
         if (e != cudaSuccess) return cuda_fail(e, "fp64 wave launch");
     }
-    cudaEventRecord(S->ev_end[b], S->stream);
+    cudaEventRecord(S->ev_end[b], st);
+    // a finishing map may have earlier tiles in the previous wave, which runs on the
+    // other stream: its completion event follows both
+    bool any_last = false;
+    for (auto &it : w->items) any_last = any_last || it.last;
+    if (any_last && w->id > 0) cudaStreamWaitEvent(st, S->ev_end[b ^ 1], 0);
     for (auto &it : w->items)
-        if (it.last) cudaEventRecord(it.req->map->done, S->stream);
+        if (it.last) cudaEventRecord(it.req->map->done, st);
     w->start = S->ev_start[b];
     w->end = S->ev_end[b];
     return MM_OK;
@@ -356,7 +370,8 @@ int server_start(mm_ctx *ctx)
     auto *S = new Server();
     S->ctx = ctx;
     cudaSetDevice(ctx->device);
-    cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+    cudaError_t e = cudaStreamCreateWithFlags(&S->stream[0], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->stream[1], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->capture, cudaStreamNonBlocking);
     for (int k = 0; k < kAdmitWorkers && e == cudaSuccess; ++k)
         e = cudaStreamCreateWithFlags(&S->upload[k], cudaStreamNonBlocking);
@@ -387,15 +402,18 @@ void server_stop(mm_ctx *ctx)
     for (auto &t : S->workers)
         if (t.joinable()) t.join();
     if (S->th.joinable()) S->th.join();
-    cudaStreamSynchronize(S->stream);
+    cudaStreamSynchronize(S->stream[0]);
+    cudaStreamSynchronize(S->stream[1]);
     for (int b = 0; b < 2; ++b) {
-        if (S->gexec[b]) cudaGraphExecDestroy(S->gexec[b]);
+        for (int k = 0; k < 2; ++k)
+            if (S->gexec[b][k]) cudaGraphExecDestroy(S->gexec[b][k]);
         scratch_free(ctx, &S->sc[b]);
         scratch_free(ctx, &S->sc64[b]);
         cudaEventDestroy(S->ev_start[b]);
         cudaEventDestroy(S->ev_end[b]);
     }
-    cudaStreamDestroy(S->stream);
+    cudaStreamDestroy(S->stream[0]);
+    cudaStreamDestroy(S->stream[1]);
     cudaStreamDestroy(S->capture);
     for (int k = 0; k < kAdmitWorkers; ++k) cudaStreamDestroy(S->upload[k]);
     {
@@ -446,7 +464,7 @@ int mm_submit(mm_ctx *ctx, mm_lenses lenses, const mm_params *p, mm_req *out)
         r->given = it->second;
         r->g.nstar = r->given->n;
     }
-    r->footprint = MapObj::footprint(p->npix_side) + (r->given ? 0 : LensSet::footprint(r->g.nstar));
+    r->footprint = MapObj::footprint(p, r->g) + (r->given ? 0 : LensSet::footprint(r->g.nstar));
     if (r->footprint > ctx->arena.budget()) return fail(MM_ENOMEM, "request footprint exceeds the HBM budget");
     if ((rc = server_start(ctx))) return rc;
     Server *S = ctx->server;

@@ -319,6 +319,34 @@ def test_every_variant_within_tolerance(ctx):
         mm.mm_set_variant(ctx, -1)
 
 
+def test_split_tiles_match_oracle(ctx):
+    """A window of the N* = 25 000 map has ~150 tiles: each tile's lens sum is split over several
+    CTAs and recombined; maps, deflections and pixels must still match the oracle."""
+    f = field2()
+    lh = lens(ctx, f)
+    g = oracle.geometry(oracle_cfg(CFG2))
+    rect = (g["nx"] // 3, g["nx"] // 3 + 577, g["ny"] // 2, g["ny"] // 2 + 389)
+    m = mm.mm_shoot(ctx, lh, P(CFG2, ray_rect=rect))
+    got, st = mm.mm_map_fetch(ctx, m)
+    mm.mm_release_map(ctx, m)
+    assert st["lens_splits"] > 1
+    ref, tot = oracle.shoot_map(oracle_cfg(CFG2), f, rect=rect)
+    check_totals(got, st, tot["shot"])
+    assert map_l1(got, ref) <= 2 * max(2, MISBIN_TOL * tot["shot"])
+    rng = np.random.default_rng(9)
+    ii = rng.integers(rect[0], rect[1], 4000)
+    jj = rng.integers(rect[2], rect[3], 4000)
+    a_g, p_g = mm.mm_debug_deflect(ctx, lh, P(CFG2, ray_rect=rect), ii, jj)
+    a_o, _, p_o = oracle.shoot_rays(oracle_cfg(CFG2), f, ii, jj)
+    err = np.hypot(a_g[:, 0] - a_o[:, 0], a_g[:, 1] - a_o[:, 1])
+    assert err.max() <= ALPHA_TOL and np.mean(p_g != p_o) <= MISBIN_TOL
+    # the whole-grid map of the same field has millions of tiles: no split
+    m = mm.mm_shoot(ctx, lh, P(CFG2, ray_rect=(0, 64 * 200, 0, 32 * 200)))
+    _, st = mm.mm_map_fetch(ctx, m, want_counts=False)
+    mm.mm_release_map(ctx, m)
+    assert st["lens_splits"] == 1
+
+
 def test_thread_layouts_give_bit_identical_maps(ctx):
     """Every thread layout runs the same per-ray FP32 operations on the same tiles."""
     items = mix_windows(2, 21)
