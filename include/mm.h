@@ -230,6 +230,30 @@ int mm_req_times(mm_ctx *ctx, mm_req req, double *t_queue, double *t_total);
  * target device time of one wave in milliseconds (0 keeps the current value). */
 int mm_serve_config(mm_ctx *ctx, int32_t max_active, int32_t max_queued, double wave_ms);
 
+/* ---- map statistics (Sect. 3.1, Eq. deltam) --------------------------------
+ * The paper compares maps by the RMS difference of Delta m = -2.5 log10(mu)
+ * (mu = N / N_rays per pixel) and by a two-sample Kolmogorov-Smirnov test on the
+ * Delta m distributions ("excellent agreement": RMS < 0.2 mag and K-S probability
+ * > 99.7 %). Readings: the RMS runs over pixels where both maps count at least
+ * one ray; empty pixels enter the K-S test with Delta m = +infinity; the K-S
+ * probability is the asymptotic Kolmogorov distribution at
+ * (sqrt(n_e) + 0.12 + 0.11/sqrt(n_e)) D, n_e = n_a n_b / (n_a + n_b). */
+typedef struct {
+    double  rms_dm;      /* RMS of Delta m_a - Delta m_b over pixels counted in both maps, mag */
+    int64_t n_rms;       /* pixels in the RMS */
+    int64_t zero_a;      /* empty pixels of map a */
+    int64_t zero_b;      /* empty pixels of map b */
+    double  ks_d;        /* K-S statistic of the Delta m distributions (exact) */
+    double  ks_p;        /* asymptotic K-S probability (null hypothesis not rejected) */
+    double  mean_mu_a;   /* mean magnification of each map */
+    double  mean_mu_b;
+} mm_compare;
+
+/* Compare two maps of the same N_side on the device (each map's own N_rays sets
+ * its mu). Waits for both maps. Errors: MM_EINVAL (different N_side),
+ * MM_ENOTFOUND, MM_EDEVICE. */
+int mm_map_compare(mm_ctx *ctx, mm_map a, mm_map b, mm_compare *out);
+
 /* ---- tuning and inspection ------------------------------------------------ */
 
 /* Autotune for maps like *p: time every thread layout x tile variant of the

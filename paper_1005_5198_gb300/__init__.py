@@ -43,6 +43,11 @@ class mm_stats(C.Structure):
                 ("seconds", C.c_double), ("mu_mean", C.c_double), ("lens_splits", C.c_int32)]
 
 
+class mm_compare(C.Structure):
+    _fields_ = [("rms_dm", C.c_double), ("n_rms", C.c_int64), ("zero_a", C.c_int64), ("zero_b", C.c_int64),
+                ("ks_d", C.c_double), ("ks_p", C.c_double), ("mean_mu_a", C.c_double), ("mean_mu_b", C.c_double)]
+
+
 class mm_geometry(C.Structure):
     _fields_ = [("pix", C.c_double), ("delta", C.c_double), ("width", C.c_double), ("height", C.c_double),
                 ("nx", C.c_int64), ("ny", C.c_int64), ("nstar", C.c_int64), ("disc_radius", C.c_double),
@@ -93,6 +98,7 @@ def _load():
         "mm_last_kernel_ms": [C.c_void_p, P(D), P(C.c_int32)],
         "mm_shoot_noalloc": [C.c_void_p, C.c_void_p, C.c_void_p, I64, P(mm_params), C.c_void_p, C.c_void_p,
                              C.c_void_p],
+        "mm_map_compare": [C.c_void_p, U64, U64, P(mm_compare)],
         "mm_strerror": [C.c_int],
         "mm_last_error": [],
     }
@@ -343,6 +349,13 @@ def mm_shoot_noalloc(x_ptr: int, y_ptr: int, m_ptr: int, nstar: int, p: mm_param
                                     C.c_void_p(cuda_stream or None)), "mm_shoot_noalloc")
 
 
+def mm_map_compare(ctx: Ctx, a: int, b: int) -> dict:
+    """RMS difference of Delta m and the K-S test between two maps (Sect. 3.1), on the device."""
+    out = mm_compare()
+    _check(_load().mm_map_compare(ctx.handle, a, b, C.byref(out)), "mm_map_compare")
+    return {k: getattr(out, k) for k, _ in mm_compare._fields_}
+
+
 def mm_strerror(code: int) -> str:
     return _load().mm_strerror(code).decode()
 
@@ -353,5 +366,5 @@ EXPORTED = [
     "mm_map_device_ptr", "mm_release_map", "mm_submit", "mm_poll", "mm_wait", "mm_cancel", "mm_req_times",
     "mm_serve_config", "mm_autotune", "mm_set_variant", "mm_variant_count", "mm_variant_name", "mm_set_layout",
     "mm_get_layout", "mm_layout_count", "mm_layout_name", "mm_debug_deflect",
-    "mm_last_kernel_ms", "mm_shoot_noalloc", "mm_strerror", "mm_last_error",
+    "mm_last_kernel_ms", "mm_shoot_noalloc", "mm_map_compare", "mm_strerror", "mm_last_error",
 ]

@@ -1,0 +1,196 @@
+// mm_stats.cu -- statistical comparison of two magnification maps on the device
+// (Sect. 3.1: RMS difference of the maps in magnitudes, and a two-sample
+// Kolmogorov-Smirnov test on the distributions of Delta m, Eq. deltam).
+//
+// Delta m_ij = -2.5 log10(mu_ij), mu_ij = N_ij / N_rays. Readings where the
+// paper is silent:
+//   * RMS: over the pixels where both maps count at least one ray (Delta m of an
+//     empty pixel is +infinity); the number of such pixels is reported;
+//   * K-S: empty pixels take Delta m = +infinity. Delta m is strictly decreasing in
+//     the integer count, so the K-S statistic of the Delta m samples equals that of
+//     the count samples: D = max_k |F_a(k) - F_b(k)| over the count histograms,
+//     which is computed exactly in integers here;
+//   * probability: the asymptotic Kolmogorov distribution,
+//     Q(l) = 2 sum_{j>=1} (-1)^(j-1) exp(-2 j^2 l^2), at
+//     l = (sqrt(n_e) + 0.12 + 0.11 / sqrt(n_e)) D, n_e = n_a n_b / (n_a + n_b)
+//     (Stephens' small-sample correction).
+#include <algorithm>
+#include <cmath>
+
+#include "mm_ctx.h"
+
+namespace mm {
+namespace {
+
+struct StatSums {
+    double sum_sq;                 // sum of (Delta m_a - Delta m_b)^2 over pixels counted in both maps
+    unsigned long long n_both;
+    unsigned long long zero_a, zero_b;
+    unsigned long long sum_a, sum_b;
+    unsigned int max_count;
+    int pad;
+    long long ks_num;              // max_k |c_a(k) n_b - c_b(k) n_a|
+};
+
+__global__ void k_dm_rms(const unsigned *a, const unsigned *b, long long n, double log10_ra, double log10_rb,
+                         StatSums *out)
+{
+    double sq = 0.0;
+    unsigned long long both = 0, za = 0, zb = 0, sa = 0, sb = 0;
+    unsigned mx = 0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const unsigned na = a[k], nb = b[k];
+        sa += na;
+        sb += nb;
+        mx = max(mx, max(na, nb));
+        za += na == 0u;
+        zb += nb == 0u;
+        if (na && nb) {
+            // Delta m_a - Delta m_b = -2.5 [(log10 N_a - log10 N_rays_a) - (log10 N_b - log10 N_rays_b)]
+            const double d = -2.5 * ((log10((double)na) - log10_ra) - (log10((double)nb) - log10_rb));
+            sq += d * d;
+            both += 1;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sq += __shfl_down_sync(0xffffffffu, sq, o);
+        both += __shfl_down_sync(0xffffffffu, both, o);
+        za += __shfl_down_sync(0xffffffffu, za, o);
+        zb += __shfl_down_sync(0xffffffffu, zb, o);
+        sa += __shfl_down_sync(0xffffffffu, sa, o);
+        sb += __shfl_down_sync(0xffffffffu, sb, o);
+        mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&out->sum_sq, sq);
+        atomicAdd(&out->n_both, both);
+        atomicAdd(&out->zero_a, za);
+        atomicAdd(&out->zero_b, zb);
+        atomicAdd(&out->sum_a, sa);
+        atomicAdd(&out->sum_b, sb);
+        atomicMax(&out->max_count, mx);
+    }
+}
+
+__global__ void k_hist(const unsigned *a, long long n, unsigned *hist)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        atomicAdd(hist + a[k], 1u);
+}
+
+// One CTA of 1024 threads: exact max_k |c_a(k) n_b - c_b(k) n_a| with c the cumulative
+// histograms (integers; n_a, n_b <= 2^30 so every product fits in 64 bits).
+__global__ void __launch_bounds__(1024) k_ks(const unsigned *ha, const unsigned *hb, long long nbins, long long na,
+                                             long long nb, StatSums *out)
+{
+    __shared__ long long sa[1024], sb[1024];
+    const int t = threadIdx.x;
+    const long long per = (nbins + 1023) / 1024;
+    const long long lo = min(nbins, t * per), hi = min(nbins, lo + per);
+    long long ca = 0, cb = 0;
+    for (long long k = lo; k < hi; ++k) {
+        ca += ha[k];
+        cb += hb[k];
+    }
+    sa[t] = ca;
+    sb[t] = cb;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {           // inclusive scan of the per-thread totals
+        const long long va = (t >= o) ? sa[t - o] : 0, vb = (t >= o) ? sb[t - o] : 0;
+        __syncthreads();
+        sa[t] += va;
+        sb[t] += vb;
+        __syncthreads();
+    }
+    ca = (t > 0) ? sa[t - 1] : 0;
+    cb = (t > 0) ? sb[t - 1] : 0;
+    long long best = 0;
+    for (long long k = lo; k < hi; ++k) {
+        ca += ha[k];
+        cb += hb[k];
+        const long long d = ca * nb - cb * na;
+        best = max(best, d < 0 ? -d : d);
+    }
+    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_down_sync(0xffffffffu, best, o));
+    if ((t & 31) == 0) atomicMax((unsigned long long *)&out->ks_num, (unsigned long long)best);
+}
+
+// Kolmogorov distribution survival function Q(l) = 2 sum (-1)^(j-1) exp(-2 j^2 l^2).
+double kolmogorov_q(double l)
+{
+    if (l < 0.2) return 1.0;
+    double s = 0.0, sign = 1.0;
+    for (int j = 1; j <= 200; ++j) {
+        const double term = std::exp(-2.0 * j * j * l * l);
+        s += sign * term;
+        if (term < 1e-17) break;
+        sign = -sign;
+    }
+    return std::min(1.0, std::max(0.0, 2.0 * s));
+}
+
+}  // namespace
+}  // namespace mm
+
+using namespace mm;
+
+extern "C" int mm_map_compare(mm_ctx *ctx, mm_map a, mm_map b, mm_compare *out)
+{
+    if (!ctx || !out) return fail(MM_EINVAL, "null argument");
+    std::shared_ptr<MapObj> A, B;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        auto ia = ctx->maps.find(a), ib = ctx->maps.find(b);
+        if (ia == ctx->maps.end() || ib == ctx->maps.end()) return fail(MM_ENOTFOUND, "unknown map");
+        A = ia->second;
+        B = ib->second;
+    }
+    if (A->p.npix_side != B->p.npix_side) return fail(MM_EINVAL, "maps of different N_side");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = ctx->stream;
+    cudaError_t e;
+    if ((e = cudaStreamWaitEvent(s, A->done, 0)) != cudaSuccess || (e = cudaStreamWaitEvent(s, B->done, 0)) != cudaSuccess)
+        return cuda_fail(e, "wait for maps");
+    const long long n = (long long)A->p.npix_side * A->p.npix_side;
+    struct Tmp {
+        DeviceArena *ar;
+        std::vector<void *> v;
+        ~Tmp() { for (void *p : v) ar->free(p); }
+    } tmp{&ctx->arena, {}};
+    StatSums *d_sum = nullptr;
+    int rc = ctx->arena.alloc(sizeof(StatSums), (void **)&d_sum);
+    if (rc) return rc;
+    tmp.v.push_back(d_sum);
+    if ((e = cudaMemsetAsync(d_sum, 0, sizeof(StatSums), s)) != cudaSuccess) return cuda_fail(e, "memset");
+    const int grid = std::max(1, std::min(4 * ctx->sms, (int)((n + 255) / 256)));
+    k_dm_rms<<<grid, 256, 0, s>>>(A->counts, B->counts, n, std::log10(A->p.nrays_per_pix),
+                                  std::log10(B->p.nrays_per_pix), d_sum);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_dm_rms");
+    StatSums h{};
+    if ((e = cudaMemcpyAsync(&h, d_sum, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(e, "stats readback");
+    // histograms of the counts over 0..max, then the exact K-S numerator
+    const long long nbins = (long long)h.max_count + 1;
+    unsigned *hist = nullptr;
+    if ((rc = ctx->arena.alloc((size_t)(2 * nbins) * sizeof(unsigned), (void **)&hist))) return rc;
+    tmp.v.push_back(hist);
+    if ((e = cudaMemsetAsync(hist, 0, (size_t)(2 * nbins) * sizeof(unsigned), s)) != cudaSuccess) return cuda_fail(e, "memset");
+    k_hist<<<grid, 256, 0, s>>>(A->counts, n, hist);
+    k_hist<<<grid, 256, 0, s>>>(B->counts, n, hist + nbins);
+    k_ks<<<1, 1024, 0, s>>>(hist, hist + nbins, nbins, n, n, d_sum);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_hist/k_ks");
+    if ((e = cudaMemcpyAsync(&h, d_sum, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(e, "stats readback");
+    out->n_rms = (int64_t)h.n_both;
+    out->rms_dm = h.n_both ? std::sqrt(h.sum_sq / (double)h.n_both) : 0.0;
+    out->zero_a = (int64_t)h.zero_a;
+    out->zero_b = (int64_t)h.zero_b;
+    out->ks_d = (double)h.ks_num / ((double)n * (double)n);
+    const double ne = (double)n * (double)n / (2.0 * (double)n), sq = std::sqrt(ne);
+    out->ks_p = kolmogorov_q((sq + 0.12 + 0.11 / sq) * out->ks_d);
+    out->mean_mu_a = (double)h.sum_a / ((double)n * A->p.nrays_per_pix);
+    out->mean_mu_b = (double)h.sum_b / ((double)n * B->p.nrays_per_pix);
+    return MM_OK;
+}

@@ -1,0 +1,60 @@
+"""Device map statistics (Sect. 3.1) against the oracle's, and the paper's agreement test
+applied to the FP32 and FP64 paths."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1005_5198_gb300 as mm
+import synth
+from oracle import field
+from oracle import stats as ostats
+
+pytestmark = pytest.mark.gpu
+
+CFG = dict(sigma=0.45, gamma=0.2, smooth_frac=0.3, side=6.0, npix_side=256, nrays=64.0)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    mm.build()
+    c = mm.mm_init(0)
+    yield c
+    mm.mm_destroy(c)
+
+
+def test_compare_matches_oracle_statistics(ctx):
+    n, r = field.nstar_rule(CFG["sigma"], CFG["gamma"], CFG["smooth_frac"], CFG["side"])
+    f = synth.lens_field(n, r, 31)
+    lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
+    a = mm.mm_shoot(ctx, lh, mm.params(**CFG))
+    b = mm.mm_shoot(ctx, lh, mm.params(**dict(CFG, nrays=25.0)))        # a noisier map of the same field
+    ca, _ = mm.mm_map_fetch(ctx, a)
+    cb, _ = mm.mm_map_fetch(ctx, b)
+    got = mm.mm_map_compare(ctx, a, b)
+    ref = ostats.compare(ca, 64.0, cb, 25.0)
+    print(got, ref)
+    assert got["ks_d"] == pytest.approx(ref["ks_d"], abs=1e-15)
+    assert got["n_rms"] == ref["n_rms"] and got["zero_a"] == ref["zero_a"] and got["zero_b"] == ref["zero_b"]
+    assert got["rms_dm"] == pytest.approx(ref["rms_dm"], rel=1e-9)
+    assert got["ks_p"] == pytest.approx(ref["ks_p"], abs=1e-6)
+    assert got["mean_mu_a"] == pytest.approx(ref["mean_mu_a"], rel=1e-12)
+    same = mm.mm_map_compare(ctx, a, a)
+    assert same["rms_dm"] == 0.0 and same["ks_d"] == 0.0 and same["ks_p"] == pytest.approx(1.0)
+    for m in (a, b):
+        mm.mm_release_map(ctx, m)
+
+
+def test_fp32_and_fp64_maps_agree_excellently(ctx):
+    """The paper's criterion for 'excellent agreement' (RMS < 0.2 mag, K-S probability > 99.7 %)
+    between the compensated FP32 path and the plain FP64 path on a config-0 map."""
+    cfg = dict(sigma=0.4, gamma=0.0, smooth_frac=0.0, side=4.0, npix_side=128, nrays=100.0)
+    f = synth.lens_field(100, field.radius_for_nstar(100, 0.4), 1)
+    lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
+    a = mm.mm_shoot(ctx, lh, mm.params(**cfg))
+    b = mm.mm_shoot(ctx, lh, mm.params(**cfg, precision=mm.MM_FP64))
+    r = mm.mm_map_compare(ctx, a, b)
+    print(r)
+    assert r["rms_dm"] < 0.2 and r["ks_p"] > 0.997
+    assert r["rms_dm"] < 1e-3           # in fact only a few rays per million differ
+    for m in (a, b):
+        mm.mm_release_map(ctx, m)
