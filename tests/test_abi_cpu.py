@@ -111,3 +111,16 @@ def test_input_generator_is_independent_of_method():
     assert "paper_1005_5198_gb300" not in src
     f = synth.lens_field(10, 3.0, 1)
     assert f.n == 10
+
+
+def test_sweep_plans_reproduce_printed_lens_counts():
+    """The sweep driver's sigma and gamma sweeps use the paper's parameter grids (Sect. 3.1)."""
+    from paper_1005_5198_gb300 import sweep
+    printed_sigma = [65, 163, 313, 558, 987, 1817, 3701, 9343, 41257]
+    got = [p["nstar"] for p in sweep.plan("sigma", 1024, 1000.0)]
+    assert got[:8] == printed_sigma[:8] and abs(got[8] - printed_sigma[8]) <= 10
+    printed_gamma = [741, 814, 1093, 1875, 4796, 41134, 41119, 4748, 1787, 956, 606]
+    assert [p["nstar"] for p in sweep.plan("gamma", 2048, 1000.0)] == printed_gamma
+    sm = sweep.plan("smooth", 2048, 1000.0)
+    assert len(sm) == 11 and sm[-1]["smooth_frac"] == 0.99
+    assert all(a["nstar"] >= b["nstar"] for a, b in zip(sm, sm[1:]))      # N* falls as s grows
