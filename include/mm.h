@@ -254,6 +254,31 @@ typedef struct {
  * MM_ENOTFOUND, MM_EDEVICE. */
 int mm_map_compare(mm_ctx *ctx, mm_map a, mm_map b, mm_compare *out);
 
+/* ---- extended sources (Sect. 1) --------------------------------------------
+ * The magnification of an extended source is the map convolved with the source
+ * profile. mu = N / N_rays per pixel; the profile is discretised on the pixel
+ * grid and normalised to unit sum:
+ *   MM_PROFILE_GAUSSIAN  w(i, j) = g(i) g(j), g(k) = exp(-(k p)^2 / (2 size^2)),
+ *                        |k| <= ceil(4 size / p) (square support, separable);
+ *   MM_PROFILE_DISC      w(i, j) = 1 where (i^2 + j^2) p^2 <= size^2 (uniform disc).
+ * Output pixels whose profile support leaves the map are NaN. */
+#define MM_PROFILE_GAUSSIAN 0
+#define MM_PROFILE_DISC     1
+
+/* Convolved magnification map into host_mu[n_elems] (n_elems = N_side^2, row-major,
+ * float). size_re: Gaussian sigma or disc radius in Einstein radii. Errors:
+ * MM_EINVAL (bad profile or size, profile wider than the map, wrong n_elems),
+ * MM_ENOTFOUND, MM_EDEVICE. */
+int mm_map_convolve(mm_ctx *ctx, mm_map map, int32_t profile, double size_re, float *host_mu, size_t n_elems);
+
+/* Light curve of an extended source moving on a straight track from (y1_start,
+ * y2_start) to (y1_end, y2_end) (source-plane Einstein radii, origin at the map
+ * centre): n_points samples, evenly spaced including both ends, of the convolved
+ * map, bilinearly interpolated between pixel centres (-L/2 + (I + 1/2) p);
+ * host_mu[k] is NaN where a sample needs a pixel without value. */
+int mm_map_lightcurve(mm_ctx *ctx, mm_map map, int32_t profile, double size_re, double y1_start, double y2_start,
+                      double y1_end, double y2_end, int64_t n_points, double *host_mu);
+
 /* ---- tuning and inspection ------------------------------------------------ */
 
 /* Autotune for maps like *p: time every thread layout x tile variant of the

@@ -21,6 +21,7 @@ MM_OK, MM_EINVAL, MM_ENOMEM, MM_EBUSY, MM_ENOTFOUND = 0, -1, -2, -3, -4
 MM_ETIMEDOUT, MM_EDEVICE, MM_EAGAIN, MM_ECANCELED = -5, -6, -7, -8
 MM_FP32C, MM_FP64 = 0, 1
 MM_MASS_UNIT, MM_MASS_LOGNORMAL = 0, 1
+MM_PROFILE_GAUSSIAN, MM_PROFILE_DISC = 0, 1
 
 
 class MMError(RuntimeError):
@@ -99,6 +100,8 @@ def _load():
         "mm_shoot_noalloc": [C.c_void_p, C.c_void_p, C.c_void_p, I64, P(mm_params), C.c_void_p, C.c_void_p,
                              C.c_void_p],
         "mm_map_compare": [C.c_void_p, U64, U64, P(mm_compare)],
+        "mm_map_convolve": [C.c_void_p, U64, C.c_int32, D, P(C.c_float), C.c_size_t],
+        "mm_map_lightcurve": [C.c_void_p, U64, C.c_int32, D, D, D, D, D, I64, P(D)],
         "mm_strerror": [C.c_int],
         "mm_last_error": [],
     }
@@ -356,6 +359,24 @@ def mm_map_compare(ctx: Ctx, a: int, b: int) -> dict:
     return {k: getattr(out, k) for k, _ in mm_compare._fields_}
 
 
+def mm_map_convolve(ctx: Ctx, m: int, profile: int, size_re: float) -> np.ndarray:
+    """Magnification map of an extended source (float32 [N_side, N_side], NaN near the edges)."""
+    _, n = mm_map_device_ptr(ctx, m)
+    out = np.zeros(n, dtype=np.float32)
+    _check(_load().mm_map_convolve(ctx.handle, m, profile, size_re, out.ctypes.data_as(C.POINTER(C.c_float)), n),
+           "mm_map_convolve")
+    side = int(round(n ** 0.5))
+    return out.reshape(side, side)
+
+
+def mm_map_lightcurve(ctx: Ctx, m: int, profile: int, size_re: float, start, end, n_points: int) -> np.ndarray:
+    """Magnification along a straight source track from start=(y1, y2) to end (Einstein radii)."""
+    out = np.zeros(n_points, dtype=np.float64)
+    _check(_load().mm_map_lightcurve(ctx.handle, m, profile, size_re, start[0], start[1], end[0], end[1],
+                                     n_points, _dptr(out)), "mm_map_lightcurve")
+    return out
+
+
 def mm_strerror(code: int) -> str:
     return _load().mm_strerror(code).decode()
 
@@ -366,5 +387,6 @@ EXPORTED = [
     "mm_map_device_ptr", "mm_release_map", "mm_submit", "mm_poll", "mm_wait", "mm_cancel", "mm_req_times",
     "mm_serve_config", "mm_autotune", "mm_set_variant", "mm_variant_count", "mm_variant_name", "mm_set_layout",
     "mm_get_layout", "mm_layout_count", "mm_layout_name", "mm_debug_deflect",
-    "mm_last_kernel_ms", "mm_shoot_noalloc", "mm_map_compare", "mm_strerror", "mm_last_error",
+    "mm_last_kernel_ms", "mm_shoot_noalloc", "mm_map_compare", "mm_map_convolve",
+    "mm_map_lightcurve", "mm_strerror", "mm_last_error",
 ]

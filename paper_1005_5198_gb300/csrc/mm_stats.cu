@@ -7,9 +7,10 @@
 //   * RMS: over the pixels where both maps count at least one ray (Delta m of an
 //     empty pixel is +infinity); the number of such pixels is reported;
 //   * K-S: empty pixels take Delta m = +infinity. Delta m is strictly decreasing in
-//     the integer count, so the K-S statistic of the Delta m samples equals that of
-//     the count samples: D = max_k |F_a(k) - F_b(k)| over the count histograms,
-//     which is computed exactly in integers here;
+//     mu, so the K-S statistic of the Delta m samples is the supremum over mu of
+//     |P(mu_a >= mu) - P(mu_b >= mu)|, attained at sample values; it is computed
+//     exactly from the two count histograms (survivor counts at every value
+//     k / N_rays present in either map);
 //   * probability: the asymptotic Kolmogorov distribution,
 //     Q(l) = 2 sum_{j>=1} (-1)^(j-1) exp(-2 j^2 l^2), at
 //     l = (sqrt(n_e) + 0.12 + 0.11 / sqrt(n_e)) D, n_e = n_a n_b / (n_a + n_b)
@@ -78,22 +79,22 @@ __global__ void k_hist(const unsigned *a, long long n, unsigned *hist)
         atomicAdd(hist + a[k], 1u);
 }
 
-// One CTA of 1024 threads: exact max_k |c_a(k) n_b - c_b(k) n_a| with c the cumulative
-// histograms (integers; n_a, n_b <= 2^30 so every product fits in 64 bits).
-__global__ void __launch_bounds__(1024) k_ks(const unsigned *ha, const unsigned *hb, long long nbins, long long na,
-                                             long long nb, StatSums *out)
+// One CTA of 1024 threads: inclusive prefix sums ca[k], cb[k] of the two count
+// histograms (so P(N >= k) = (n - c[k-1]) / n).
+__global__ void __launch_bounds__(1024) k_scan(const unsigned *ha, const unsigned *hb, long long nbins, long long *ca,
+                                               long long *cb)
 {
     __shared__ long long sa[1024], sb[1024];
     const int t = threadIdx.x;
     const long long per = (nbins + 1023) / 1024;
     const long long lo = min(nbins, t * per), hi = min(nbins, lo + per);
-    long long ca = 0, cb = 0;
+    long long ta = 0, tb = 0;
     for (long long k = lo; k < hi; ++k) {
-        ca += ha[k];
-        cb += hb[k];
+        ta += ha[k];
+        tb += hb[k];
     }
-    sa[t] = ca;
-    sb[t] = cb;
+    sa[t] = ta;
+    sb[t] = tb;
     __syncthreads();
     for (int o = 1; o < 1024; o <<= 1) {           // inclusive scan of the per-thread totals
         const long long va = (t >= o) ? sa[t - o] : 0, vb = (t >= o) ? sb[t - o] : 0;
@@ -102,17 +103,47 @@ __global__ void __launch_bounds__(1024) k_ks(const unsigned *ha, const unsigned 
         sb[t] += vb;
         __syncthreads();
     }
-    ca = (t > 0) ? sa[t - 1] : 0;
-    cb = (t > 0) ? sb[t - 1] : 0;
-    long long best = 0;
+    ta = (t > 0) ? sa[t - 1] : 0;
+    tb = (t > 0) ? sb[t - 1] : 0;
     for (long long k = lo; k < hi; ++k) {
-        ca += ha[k];
-        cb += hb[k];
-        const long long d = ca * nb - cb * na;
+        ta += ha[k];
+        tb += hb[k];
+        ca[k] = ta;
+        cb[k] = tb;
+    }
+}
+
+// Number of samples of a map with mu = N / nr >= m: n - c[kmin - 1], kmin the smallest
+// count with kmin / nr >= m (divisions correctly rounded, as in the oracle's Delta m).
+__device__ __forceinline__ long long survivors(const long long *c, long long nbins, long long n, double nr, double m)
+{
+    long long k = (long long)ceil(m * nr);
+    if (k < 0) k = 0;
+    while (k > 0 && __ddiv_rn((double)(k - 1), nr) >= m) --k;
+    while (k < nbins && __ddiv_rn((double)k, nr) < m) ++k;
+    if (k >= nbins) return 0;
+    return n - (k > 0 ? c[k - 1] : 0);
+}
+
+// D numerator: max over every value mu = k / nr present in either map of
+// |S_a(mu) n_b - S_b(mu) n_a|, S the survivor counts; the K-S supremum over Delta m
+// thresholds is attained at these points (Delta m is decreasing in mu).
+__global__ void k_ks_eval(const unsigned *ha, const unsigned *hb, const long long *ca, const long long *cb,
+                          long long nbins, long long na, long long nb, double ra, double rb, StatSums *out)
+{
+    long long best = 0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < 2 * nbins;
+         q += (long long)gridDim.x * blockDim.x) {
+        const bool from_a = q < nbins;
+        const long long k = from_a ? q : q - nbins;
+        if ((from_a ? ha[k] : hb[k]) == 0u) continue;
+        const double m = __ddiv_rn((double)k, from_a ? ra : rb);
+        const long long sa = survivors(ca, nbins, na, ra, m), sb = survivors(cb, nbins, nb, rb, m);
+        const long long d = sa * nb - sb * na;
         best = max(best, d < 0 ? -d : d);
     }
     for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_down_sync(0xffffffffu, best, o));
-    if ((t & 31) == 0) atomicMax((unsigned long long *)&out->ks_num, (unsigned long long)best);
+    if ((threadIdx.x & 31) == 0) atomicMax((unsigned long long *)&out->ks_num, (unsigned long long)best);
 }
 
 // Kolmogorov distribution survival function Q(l) = 2 sum (-1)^(j-1) exp(-2 j^2 l^2).
@@ -170,16 +201,22 @@ extern "C" int mm_map_compare(mm_ctx *ctx, mm_map a, mm_map b, mm_compare *out)
     if ((e = cudaMemcpyAsync(&h, d_sum, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return cuda_fail(e, "stats readback");
-    // histograms of the counts over 0..max, then the exact K-S numerator
+    // histograms of the counts over 0..max and their prefix sums, then the exact K-S numerator
     const long long nbins = (long long)h.max_count + 1;
     unsigned *hist = nullptr;
+    long long *cum = nullptr;
     if ((rc = ctx->arena.alloc((size_t)(2 * nbins) * sizeof(unsigned), (void **)&hist))) return rc;
     tmp.v.push_back(hist);
+    if ((rc = ctx->arena.alloc((size_t)(2 * nbins) * sizeof(long long), (void **)&cum))) return rc;
+    tmp.v.push_back(cum);
     if ((e = cudaMemsetAsync(hist, 0, (size_t)(2 * nbins) * sizeof(unsigned), s)) != cudaSuccess) return cuda_fail(e, "memset");
     k_hist<<<grid, 256, 0, s>>>(A->counts, n, hist);
     k_hist<<<grid, 256, 0, s>>>(B->counts, n, hist + nbins);
-    k_ks<<<1, 1024, 0, s>>>(hist, hist + nbins, nbins, n, n, d_sum);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_hist/k_ks");
+    k_scan<<<1, 1024, 0, s>>>(hist, hist + nbins, nbins, cum, cum + nbins);
+    const int egrid = std::max(1, std::min(4 * ctx->sms, (int)((2 * nbins + 255) / 256)));
+    k_ks_eval<<<egrid, 256, 0, s>>>(hist, hist + nbins, cum, cum + nbins, nbins, n, n, A->p.nrays_per_pix,
+                                    B->p.nrays_per_pix, d_sum);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_hist/k_scan/k_ks_eval");
     if ((e = cudaMemcpyAsync(&h, d_sum, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return cuda_fail(e, "stats readback");

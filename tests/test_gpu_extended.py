@@ -1,0 +1,56 @@
+"""Extended-source maps and light curves on the device (Sect. 1) against the oracle."""
+import numpy as np
+import pytest
+
+import paper_1005_5198_gb300 as mm
+import synth
+from oracle import extended as oext
+from oracle import field
+
+pytestmark = pytest.mark.gpu
+
+CFG = dict(sigma=0.45, gamma=0.2, smooth_frac=0.3, side=6.0, npix_side=256, nrays=64.0)
+
+
+@pytest.fixture(scope="module")
+def shot():
+    mm.build()
+    c = mm.mm_init(0)
+    n, r = field.nstar_rule(CFG["sigma"], CFG["gamma"], CFG["smooth_frac"], CFG["side"])
+    f = synth.lens_field(n, r, 41)
+    lh = mm.mm_create_lenses_from(c, f.x, f.y, f.m)
+    m = mm.mm_shoot(c, lh, mm.params(**CFG))
+    counts, _ = mm.mm_map_fetch(c, m)
+    yield c, m, counts
+    mm.mm_destroy(c)
+
+
+@pytest.mark.parametrize("profile,size", [(mm.MM_PROFILE_GAUSSIAN, 0.05), (mm.MM_PROFILE_GAUSSIAN, 0.011),
+                                          (mm.MM_PROFILE_DISC, 0.12), (mm.MM_PROFILE_DISC, 0.02)])
+def test_convolved_map_matches_oracle(shot, profile, size):
+    ctx, m, counts = shot
+    got = mm.mm_map_convolve(ctx, m, profile, size)
+    ref = oext.convolve(counts, CFG["nrays"], profile, size, CFG["side"] / CFG["npix_side"])
+    np.testing.assert_array_equal(np.isnan(got), np.isnan(ref))
+    ok = ~np.isnan(ref)
+    assert ok.sum() > 0.5 * ref.size
+    np.testing.assert_allclose(got[ok], ref[ok], rtol=2e-5, atol=1e-6)
+
+
+def test_lightcurve_matches_oracle(shot):
+    ctx, m, counts = shot
+    start, end = (-2.5, -1.7), (2.3, 2.6)           # runs off the valid region at both ends
+    got = mm.mm_map_lightcurve(ctx, m, mm.MM_PROFILE_GAUSSIAN, 0.04, start, end, 500)
+    field_ref = oext.convolve(counts, CFG["nrays"], 0, 0.04, CFG["side"] / CFG["npix_side"])
+    ref = oext.lightcurve(field_ref, CFG["side"], start, end, 500)
+    np.testing.assert_array_equal(np.isnan(got), np.isnan(ref))
+    ok = ~np.isnan(ref)
+    assert ok.sum() > 300
+    np.testing.assert_allclose(got[ok], ref[ok], rtol=2e-5, atol=1e-6)
+
+
+def test_profile_wider_than_map_rejected(shot):
+    ctx, m, _ = shot
+    with pytest.raises(mm.MMError) as e:
+        mm.mm_map_convolve(ctx, m, mm.MM_PROFILE_DISC, 10.0)
+    assert e.value.code == mm.MM_EINVAL

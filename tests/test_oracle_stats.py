@@ -35,6 +35,15 @@ def test_ks_statistic_hand_cases():
     assert stats.ks_probability(1.0, 100, 100) < 1e-20
 
 
+def test_ks_with_different_ray_densities():
+    """With different N_rays the count-to-Delta-m maps differ: K-S must compare mu, not counts."""
+    a = np.array([64, 64, 128, 128])            # mu = 1, 1, 2, 2 at N_rays = 64
+    b = np.array([25, 50, 50, 50])              # mu = 1, 2, 2, 2 at N_rays = 25
+    d = stats.ks_statistic(stats.delta_m(a, 64.0), stats.delta_m(b, 25.0))
+    assert d == pytest.approx(0.25)
+    assert stats.ks_statistic(a, b) == 1.0      # counts alone would say the samples are disjoint
+
+
 def test_ks_of_counts_equals_ks_of_delta_m():
     """Delta m is strictly decreasing in the count, so the K-S statistic is the same on counts."""
     rng = np.random.default_rng(3)
