@@ -187,6 +187,31 @@ int mm_shoot(mm_ctx *ctx, mm_lenses lenses, const mm_params *p, mm_map *out);
 int mm_shoot_batch(mm_ctx *ctx, int32_t n, const mm_lenses *lenses, const mm_params *params,
                    mm_map *maps_out);
 
+/* Shoot the rays of p's ray_rect (the image-plane lattice of Sect. 2, in part)
+ * into an existing map, whose counts and totals add up: a map can be shot in
+ * parts, for example band by band, and resumed after an interruption from the
+ * first part not yet shot. p must equal the map's parameters except ray_rect;
+ * lenses (0: the map's own lens set) must have the map's lens count. Each
+ * part's tiles sum their lenses as mm_shoot over the whole ray grid does (the
+ * map's kernel variant, the whole grid's lens split) and integer counts
+ * commute, so parts whose ray_rect starts on the 64 x 32-ray tile grid
+ * (i0 % 64 == 0, j0 % 32 == 0), shot into a map made with an empty ray_rect
+ * and covering the grid once, give that one-shot map bit for bit. Blocks until
+ * the part is shot. Errors: MM_EINVAL, MM_ENOTFOUND, MM_ENOMEM, MM_EDEVICE. */
+int mm_shoot_into(mm_ctx *ctx, mm_lenses lenses, const mm_params *p, mm_map map);
+
+/* Recreate a map from a checkpoint: host_counts[n_elems] and *st as
+ * mm_map_fetch returned them (rays_shot, rays_in, rays_out, nx, ny, nstar and
+ * seconds are read). p must hold the map's parameters (ray_rect is ignored);
+ * lenses (0: generated from p, as mm_shoot does) must have st->nstar lenses.
+ * The new map continues with mm_shoot_into; the rays already shot are the
+ * caller's record. Copies the host data before it returns. Errors: MM_EINVAL
+ * (sizes, or counts that do not sum to rays_in, or rays_in + rays_out !=
+ * rays_shot, or a geometry or lens count other than the checkpoint's),
+ * MM_ENOTFOUND, MM_ENOMEM, MM_EDEVICE. */
+int mm_map_restore(mm_ctx *ctx, mm_lenses lenses, const mm_params *p, const uint32_t *host_counts, size_t n_elems,
+                   const mm_stats *st, mm_map *out);
+
 /* Copy a map to host_counts[n_elems] (n_elems must equal N_side^2; may be
  * NULL to fetch only the stats) and fill *st (may be NULL). Blocks until
  * the map is complete. */

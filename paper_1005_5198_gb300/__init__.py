@@ -78,6 +78,8 @@ def _load():
         "mm_release_lenses": [C.c_void_p, U64],
         "mm_shoot": [C.c_void_p, U64, P(mm_params), P(U64)],
         "mm_shoot_batch": [C.c_void_p, C.c_int32, P(U64), P(mm_params), P(U64)],
+        "mm_shoot_into": [C.c_void_p, U64, P(mm_params), U64],
+        "mm_map_restore": [C.c_void_p, U64, P(mm_params), P(C.c_uint32), C.c_size_t, P(mm_stats), P(U64)],
         "mm_map_fetch": [C.c_void_p, U64, P(C.c_uint32), C.c_size_t, P(mm_stats)],
         "mm_map_device_ptr": [C.c_void_p, U64, P(C.c_void_p), P(C.c_size_t)],
         "mm_release_map": [C.c_void_p, U64],
@@ -221,8 +223,23 @@ def mm_shoot_batch(ctx: Ctx, lenses, plist) -> list[int]:
     return list(out)
 
 
+def mm_shoot_into(ctx: Ctx, lenses: int, p: mm_params, m: int) -> None:
+    """Add the rays of p.ray_rect to an existing map (shooting in parts / resuming)."""
+    _check(_load().mm_shoot_into(ctx.handle, lenses, C.byref(p), m), "mm_shoot_into")
+
+
 def _stats_dict(st: mm_stats) -> dict:
     return {k: getattr(st, k) for k, _ in mm_stats._fields_}
+
+
+def mm_map_restore(ctx: Ctx, lenses: int, p: mm_params, counts: np.ndarray, stats: dict) -> int:
+    """A new map from a checkpoint (the counts and stats dict of mm_map_fetch)."""
+    c = np.ascontiguousarray(counts, dtype=np.uint32).ravel()
+    st = mm_stats(**{k: stats[k] for k, _ in mm_stats._fields_})
+    out = C.c_uint64()
+    _check(_load().mm_map_restore(ctx.handle, lenses, C.byref(p), c.ctypes.data_as(C.POINTER(C.c_uint32)), c.size,
+                                  C.byref(st), C.byref(out)), "mm_map_restore")
+    return out.value
 
 
 def mm_map_fetch(ctx: Ctx, m: int, counts: np.ndarray | None = None, want_counts: bool = True):
@@ -383,7 +400,8 @@ def mm_strerror(code: int) -> str:
 
 EXPORTED = [
     "mm_init", "mm_destroy", "mm_params_default", "mm_geometry_of", "mm_create_lenses", "mm_create_lenses_from",
-    "mm_lenses_fetch", "mm_lenses_count", "mm_release_lenses", "mm_shoot", "mm_shoot_batch", "mm_map_fetch",
+    "mm_lenses_fetch", "mm_lenses_count", "mm_release_lenses", "mm_shoot", "mm_shoot_batch", "mm_shoot_into",
+    "mm_map_restore", "mm_map_fetch",
     "mm_map_device_ptr", "mm_release_map", "mm_submit", "mm_poll", "mm_wait", "mm_cancel", "mm_req_times",
     "mm_serve_config", "mm_autotune", "mm_set_variant", "mm_variant_count", "mm_variant_name", "mm_set_layout",
     "mm_get_layout", "mm_layout_count", "mm_layout_name", "mm_debug_deflect",

@@ -14,11 +14,20 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/mm.h"
 #include "mm_internal.h"
 
 namespace mm {
+
+// NVTX range over a host call (visible in Nsight timelines; no cost without a tool attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
@@ -78,6 +87,8 @@ struct MapObj {
     long long seg_lenses = 0;
     float4 *partial = nullptr;               // split tiles: segment sums
     unsigned int *seg_done = nullptr;        // split tiles: finished segments per tile
+    unsigned long long shot_total = 0;       // rays shot into the map (grows with mm_shoot_into)
+    bool owns_outputs = true;                // false: counts/totals belong to another map
     std::shared_ptr<LensSet> lenses;
     cudaEvent_t done = nullptr;
     double seconds = 0.0;
@@ -128,7 +139,7 @@ int make_lenses_from_params(mm_ctx *ctx, const mm_params *p, const Geo &g, cudaS
 int upload_lenses(mm_ctx *ctx, const double *x, const double *y, const double *m, long long n, bool unit,
                   cudaStream_t s, std::shared_ptr<LensSet> *out);
 int alloc_map(mm_ctx *ctx, const mm_params *p, const Geo &g, std::shared_ptr<LensSet> lenses, cudaStream_t s,
-              std::shared_ptr<MapObj> *out);
+              std::shared_ptr<MapObj> *out, const MapObj *into = nullptr);
 void fill_desc(const MapObj &m, MapDesc *d);
 int choose_variant(mm_ctx *ctx, const mm_params *p, const Geo &g);
 int scratch_reserve(mm_ctx *ctx, LaunchScratch *sc, int n_maps);

@@ -252,8 +252,10 @@ MapObj::~MapObj()
 {
     if (done) cudaEventDestroy(done);
     if (!arena) return;
-    arena->free(counts);
-    arena->free(totals);
+    if (owns_outputs) {
+        arena->free(counts);
+        arena->free(totals);
+    }
     arena->free(partial);
     arena->free(seg_done);
 }
@@ -334,20 +336,33 @@ static uint64_t new_handle(mm_ctx *ctx) { return ctx->next_handle.fetch_add(1); 
 static size_t map_bytes(const mm_params *p) { return (size_t)p->npix_side * (size_t)p->npix_side * 4; }
 
 int alloc_map(mm_ctx *ctx, const mm_params *p, const Geo &g, std::shared_ptr<LensSet> lenses, cudaStream_t s,
-              std::shared_ptr<MapObj> *out)
+              std::shared_ptr<MapObj> *out, const MapObj *into)
 {
     auto M = std::make_shared<MapObj>();
     M->arena = &ctx->arena;
     M->p = *p;
     M->g = g;
     M->lenses = std::move(lenses);
+    M->owns_outputs = !into;
     int rc;
-    if ((rc = ctx->arena.alloc(map_bytes(p), (void **)&M->counts)) ||
-        (rc = ctx->arena.alloc(2 * sizeof(unsigned long long), (void **)&M->totals)))
-        return rc;
-    Geo gl = g;
-    gl.nstar = M->lenses->n;
-    lens_split(gl, p->precision, &M->splits, &M->seg_lenses);
+    if (into) {
+        // a part of another map: its counts, totals and variant, and the lens split of the
+        // whole ray grid, so that the part's tiles sum their lenses as a one-shot map's do
+        M->counts = into->counts;
+        M->totals = into->totals;
+        Geo whole = g;
+        whole.nstar = M->lenses->n;
+        whole.tiles_x = (g.nx + kTileX - 1) / kTileX;
+        whole.tiles_y = (g.ny + kTileY - 1) / kTileY;
+        lens_split(whole, p->precision, &M->splits, &M->seg_lenses);
+    } else {
+        if ((rc = ctx->arena.alloc(map_bytes(p), (void **)&M->counts)) ||
+            (rc = ctx->arena.alloc(2 * sizeof(unsigned long long), (void **)&M->totals)))
+            return rc;
+        Geo gl = g;
+        gl.nstar = M->lenses->n;
+        lens_split(gl, p->precision, &M->splits, &M->seg_lenses);
+    }
     if (M->splits > 1) {
         if ((rc = ctx->arena.alloc(g.tiles() * (size_t)M->splits * kTileRays * sizeof(float4), (void **)&M->partial)) ||
             (rc = ctx->arena.alloc(g.tiles() * sizeof(unsigned), (void **)&M->seg_done)))
@@ -355,9 +370,12 @@ int alloc_map(mm_ctx *ctx, const mm_params *p, const Geo &g, std::shared_ptr<Len
         MM_CUDA(cudaMemsetAsync(M->seg_done, 0, g.tiles() * sizeof(unsigned), s));
     }
     MM_CUDA(cudaEventCreateWithFlags(&M->done, cudaEventDisableTiming));
-    MM_CUDA(cudaMemsetAsync(M->counts, 0, map_bytes(p), s));
-    MM_CUDA(cudaMemsetAsync(M->totals, 0, 2 * sizeof(unsigned long long), s));
-    M->variant = choose_variant(ctx, p, g);
+    if (!into) {
+        MM_CUDA(cudaMemsetAsync(M->counts, 0, map_bytes(p), s));
+        MM_CUDA(cudaMemsetAsync(M->totals, 0, 2 * sizeof(unsigned long long), s));
+    }
+    M->variant = into ? into->variant : choose_variant(ctx, p, g);
+    M->shot_total = (unsigned long long)g.ni * (unsigned long long)g.nj;
     *out = M;
     return MM_OK;
 }
@@ -663,6 +681,7 @@ int mm_geometry_of(const mm_params *p, mm_geometry *out)
 
 int mm_create_lenses(mm_ctx *ctx, const mm_params *p, mm_lenses *out)
 {
+    NvtxRange nvtx_("mm_create_lenses");
     if (!ctx || !out) return fail(MM_EINVAL, "null argument");
     Geo g;
     int rc = compute_geo(p, &g);
@@ -680,6 +699,7 @@ int mm_create_lenses(mm_ctx *ctx, const mm_params *p, mm_lenses *out)
 
 int mm_create_lenses_from(mm_ctx *ctx, const double *x, const double *y, const double *m, int64_t n, mm_lenses *out)
 {
+    NvtxRange nvtx_("mm_create_lenses_from");
     if (!ctx || !out || n < 0 || (n > 0 && (!x || !y || !m))) return fail(MM_EINVAL, "bad lens arrays");
     bool unit = true;
     for (int64_t k = 0; k < n; ++k) {
@@ -735,6 +755,7 @@ int mm_release_lenses(mm_ctx *ctx, mm_lenses h)
 
 int mm_shoot(mm_ctx *ctx, mm_lenses lenses, const mm_params *p, mm_map *out)
 {
+    NvtxRange nvtx_("mm_shoot");
     if (!ctx || !out) return fail(MM_EINVAL, "null argument");
     cudaSetDevice(ctx->device);
     std::shared_ptr<MapObj> M;
@@ -753,6 +774,7 @@ int mm_shoot(mm_ctx *ctx, mm_lenses lenses, const mm_params *p, mm_map *out)
 
 int mm_shoot_batch(mm_ctx *ctx, int32_t n, const mm_lenses *lenses, const mm_params *params, mm_map *maps_out)
 {
+    NvtxRange nvtx_("mm_shoot_batch");
     if (!ctx || n < 0 || (n > 0 && (!params || !maps_out))) return fail(MM_EINVAL, "bad batch arguments");
     cudaSetDevice(ctx->device);
     std::vector<std::shared_ptr<MapObj>> objs((size_t)n);
@@ -778,8 +800,77 @@ int mm_shoot_batch(mm_ctx *ctx, int32_t n, const mm_lenses *lenses, const mm_par
     return MM_OK;
 }
 
+int mm_shoot_into(mm_ctx *ctx, mm_lenses lenses, const mm_params *p, mm_map map)
+{
+    NvtxRange nvtx_("mm_shoot_into");
+    if (!ctx || !p) return fail(MM_EINVAL, "null argument");
+    auto T = find_map(ctx, map);
+    if (!T) return fail(MM_ENOTFOUND, "unknown map");
+    const mm_params &q = T->p;
+    const double margin_p = p->shoot_margin > 0 ? p->shoot_margin : 1.5, margin_q = q.shoot_margin > 0 ? q.shoot_margin : 1.5;
+    if (p->sigma != q.sigma || p->gamma != q.gamma || p->smooth_frac != q.smooth_frac || p->side_re != q.side_re ||
+        p->npix_side != q.npix_side || p->nrays_per_pix != q.nrays_per_pix || margin_p != margin_q ||
+        p->precision != q.precision)
+        return fail(MM_EINVAL, "parameters differ from the map's (only ray_rect may change)");
+    cudaSetDevice(ctx->device);
+    std::shared_ptr<LensSet> L = T->lenses;
+    if (lenses) {
+        L = find_lenses(ctx, lenses);
+        if (!L) return fail(MM_ENOTFOUND, "unknown lens set");
+        if (L->n != T->lenses->n) return fail(MM_EINVAL, "lens set differs in size from the map's");
+    }
+    Geo g;
+    int rc = compute_geo(p, &g);
+    if (rc) return rc;
+    g.nstar = L->n;
+    std::shared_ptr<MapObj> M;
+    if ((rc = alloc_map(ctx, p, g, L, ctx->stream, &M, T.get()))) return rc;
+    MM_CUDA(cudaStreamWaitEvent(ctx->stream, T->done, 0));
+    ctx->last_launches = 0;
+    std::vector<MapObj *> group{M.get()};
+    float ms = 0.f;
+    rc = launch_group(ctx, group, p->precision == MM_FP64, nullptr, 0, ctx->stream, &ms);
+    if (rc) return rc;
+    MM_CUDA(cudaEventRecord(T->done, ctx->stream));
+    T->shot_total += M->shot_total;
+    T->seconds += ms * 1e-3;
+    return MM_OK;
+}
+
+int mm_map_restore(mm_ctx *ctx, mm_lenses lenses, const mm_params *p, const uint32_t *host_counts, size_t n_elems,
+                   const mm_stats *st, mm_map *out)
+{
+    NvtxRange nvtx_("mm_map_restore");
+    if (!ctx || !p || !host_counts || !st || !out) return fail(MM_EINVAL, "null argument");
+    mm_params q = *p;
+    for (int k = 0; k < 4; ++k) q.ray_rect[k] = 0;      // a map of no rays, then the checkpoint's counts
+    const size_t npix = (size_t)q.npix_side * (size_t)q.npix_side;
+    if (q.npix_side > 0 && n_elems != npix) return fail(MM_EINVAL, "n_elems must equal N_side^2");
+    cudaSetDevice(ctx->device);
+    std::shared_ptr<MapObj> M;
+    int rc = prepare_map(ctx, lenses, &q, &M);
+    if (rc) return rc;
+    if (st->nstar != M->lenses->n || st->nx != (uint64_t)M->g.nx || st->ny != (uint64_t)M->g.ny)
+        return fail(MM_EINVAL, "checkpoint was taken with other parameters or another lens count");
+    unsigned long long sum = 0;
+    for (size_t k = 0; k < npix; ++k) sum += host_counts[k];
+    if (sum != st->rays_in || st->rays_in + st->rays_out != st->rays_shot ||
+        st->rays_shot > (uint64_t)M->g.nx * (uint64_t)M->g.ny)
+        return fail(MM_EINVAL, "checkpoint counts and totals disagree");
+    const unsigned long long tot[2] = {st->rays_in, st->rays_out};
+    MM_CUDA(cudaMemcpyAsync(M->counts, host_counts, npix * 4, cudaMemcpyHostToDevice, ctx->stream));
+    MM_CUDA(cudaMemcpyAsync(M->totals, tot, sizeof(tot), cudaMemcpyHostToDevice, ctx->stream));
+    MM_CUDA(cudaEventRecord(M->done, ctx->stream));
+    MM_CUDA(cudaStreamSynchronize(ctx->stream));        // host buffers may go as soon as this returns
+    M->shot_total = st->rays_shot;
+    M->seconds = st->seconds;
+    *out = register_map(ctx, M);
+    return MM_OK;
+}
+
 int mm_map_fetch(mm_ctx *ctx, mm_map map, uint32_t *host_counts, size_t n_elems, mm_stats *st)
 {
+    NvtxRange nvtx_("mm_map_fetch");
     if (!ctx) return fail(MM_EINVAL, "null context");
     auto M = find_map(ctx, map);
     if (!M) return fail(MM_ENOTFOUND, "unknown map");
@@ -793,7 +884,7 @@ int mm_map_fetch(mm_ctx *ctx, mm_map map, uint32_t *host_counts, size_t n_elems,
     MM_CUDA(cudaStreamSynchronize(ctx->stream));
     if (st) {
         std::memset(st, 0, sizeof(*st));
-        st->rays_shot = (uint64_t)M->g.ni * (uint64_t)M->g.nj;
+        st->rays_shot = M->shot_total;
         st->rays_in = tot[0];
         st->rays_out = tot[1];
         st->interactions = st->rays_shot * (uint64_t)M->lenses->n;
@@ -836,6 +927,7 @@ int mm_release_map(mm_ctx *ctx, mm_map map)
 int mm_debug_deflect(mm_ctx *ctx, mm_lenses lenses, const mm_params *p, const int64_t *ray_i, const int64_t *ray_j,
                      int64_t n, double *alpha_out, int64_t *pixel_out)
 {
+    NvtxRange nvtx_("mm_debug_deflect");
     if (!ctx || n < 0 || (n > 0 && (!ray_i || !ray_j))) return fail(MM_EINVAL, "bad ray arrays");
     if (n > (1LL << 28)) return fail(MM_EINVAL, "too many rays for one debug call");
     cudaSetDevice(ctx->device);
@@ -918,6 +1010,7 @@ const char *mm_variant_name(int32_t variant) { return variant_name(variant); }
 
 int mm_autotune(mm_ctx *ctx, const mm_params *p, int32_t *variant)
 {
+    NvtxRange nvtx_("mm_autotune");
     if (!ctx || !p) return fail(MM_EINVAL, "null argument");
     Geo g;
     int rc = compute_geo(p, &g);

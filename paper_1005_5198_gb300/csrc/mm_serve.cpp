@@ -124,6 +124,7 @@ static void admit_worker(Server *S, int idx)
         r->t_admit = now_s();
         r->state.store(1);
         lk.unlock();
+        NvtxRange nvtx_("mm serve admission");
         std::shared_ptr<LensSet> L = r->given;
         int rc = MM_OK;
         std::string msg;
@@ -222,6 +223,7 @@ static void plan_wave(Server *S, Wave *w)
 // Write the wave's descriptors into buffer b and enqueue it on stream b.
 static int launch_wave(Server *S, Wave *w)
 {
+    NvtxRange nvtx_("mm serve wave");
     mm_ctx *ctx = S->ctx;
     const int b = w->buf;
     int n32 = 0, n64 = 0;
