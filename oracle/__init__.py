@@ -37,6 +37,10 @@ class _Params(C.Structure):
                 ("margin", C.c_double)]
 
 
+class _Far(C.Structure):
+    _fields_ = [("order", C.c_int32), ("ratio", C.c_double), ("block_tiles", C.c_int32)]
+
+
 class _Geom(C.Structure):
     _fields_ = [("pix", C.c_double), ("delta", C.c_double), ("width", C.c_double),
                 ("height", C.c_double), ("nx", C.c_int64), ("ny", C.c_int64)]
@@ -66,6 +70,10 @@ def _load():
             lib.orc_map.argtypes = [C.POINTER(_Params), d, d, d, C.c_int64, C.c_int64, C.c_int64, C.c_int64,
                                     C.c_int64, C.c_int64, u32, u64, C.c_int]
             lib.orc_rays.argtypes = [C.POINTER(_Params), d, d, d, C.c_int64, i64, i64, C.c_int64, d, d, i64, C.c_int]
+            lib.orc_far_map.argtypes = [C.POINTER(_Params), C.POINTER(_Far), d, d, d, C.c_int64, C.c_int64,
+                                        C.c_int64, C.c_int64, C.c_int64, u32, u64, d, C.c_int]
+            lib.orc_far_rays.argtypes = [C.POINTER(_Params), C.POINTER(_Far), d, d, d, C.c_int64, C.c_int64,
+                                         C.c_int64, i64, i64, C.c_int64, d, d, i64, d, C.c_int]
             lib.orc_max_threads.restype = C.c_int
             _lib = lib
     return _lib
@@ -129,6 +137,50 @@ def shoot_rays(p, field, ray_i, ray_j, threads: int = 0):
     if rc != 0:
         raise ValueError("oracle rays failed (bad parameters)")
     return alpha, ysrc, pix
+
+
+def _far(far) -> _Far:
+    return _Far(int(far["order"]), float(far["ratio"]), int(far["block_tiles"]))
+
+
+def far_map(p, field, far, rect=None, threads: int = 0):
+    """Far-field approximation of the map (the tree code's idea on blocks of rays, Sect. 2.1,
+    Eq. hierarchical): far = {order P, ratio q, block_tiles bt}. Returns counts [N_side, N_side],
+    totals {shot, in, out} and the largest truncation bound of any block."""
+    x, y, m = _lens_arrays(field)
+    n = int(p["npix_side"] if isinstance(p, dict) else p.npix_side)
+    counts = np.zeros(n * n, dtype=np.uint32)
+    totals = np.zeros(3, dtype=np.uint64)
+    bmax = C.c_double(0.0)
+    i0, i1, j0, j1 = rect if rect is not None else (-1, -1, -1, -1)
+    rc = _load().orc_far_map(C.byref(_params(p)), C.byref(_far(far)), _ptr(x, C.c_double), _ptr(y, C.c_double),
+                             _ptr(m, C.c_double), x.size, i0, i1, j0, j1, _ptr(counts, C.c_uint32),
+                             _ptr(totals, C.c_uint64), C.byref(bmax), int(threads))
+    if rc != 0:
+        raise ValueError("oracle far-field map failed (bad parameters)")
+    return counts.reshape(n, n), dict(shot=int(totals[0]), inside=int(totals[1]), out=int(totals[2])), bmax.value
+
+
+def far_rays(p, field, far, ray_i, ray_j, origin=(0, 0), threads: int = 0):
+    """Per-ray far-field alpha [n,2], source position [n,2], flat pixel [n] (-1 = out) and
+    truncation bound [n]; blocks are counted from the rectangle origin (i0, j0)."""
+    x, y, m = _lens_arrays(field)
+    ri = np.ascontiguousarray(ray_i, dtype=np.int64)
+    rj = np.ascontiguousarray(ray_j, dtype=np.int64)
+    n = ri.size
+    alpha = np.zeros((n, 2), dtype=np.float64)
+    ysrc = np.zeros((n, 2), dtype=np.float64)
+    pix = np.zeros(n, dtype=np.int64)
+    bound = np.zeros(n, dtype=np.float64)
+    if n == 0:
+        return alpha, ysrc, pix, bound
+    rc = _load().orc_far_rays(C.byref(_params(p)), C.byref(_far(far)), _ptr(x, C.c_double), _ptr(y, C.c_double),
+                              _ptr(m, C.c_double), x.size, int(origin[0]), int(origin[1]), _ptr(ri, C.c_int64),
+                              _ptr(rj, C.c_int64), n, _ptr(alpha, C.c_double), _ptr(ysrc, C.c_double),
+                              _ptr(pix, C.c_int64), _ptr(bound, C.c_double), int(threads))
+    if rc != 0:
+        raise ValueError("oracle far-field rays failed (bad parameters)")
+    return alpha, ysrc, pix, bound
 
 
 def max_threads() -> int:

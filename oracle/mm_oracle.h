@@ -33,5 +33,27 @@ int orc_rays(const orc_params *P, const double *lx, const double *ly, const doub
              const int64_t *ray_i, const int64_t *ray_j, int64_t n,
              double *alpha, double *ysrc, int64_t *pixel, int nthreads);
 
+/* Far-field approximation on blocks of rays (see mm_oracle.c): series order P,
+ * near ratio q (a lens is summed exactly iff |d| < rho / q) and the block side
+ * in 64 x 32-ray tiles; blocks are counted from the shot rectangle's origin. */
+typedef struct {
+    int32_t order;        /* P >= 1 */
+    double ratio;         /* q in (0, 1) */
+    int32_t block_tiles;  /* bt >= 1: a block is 64 bt x 32 bt rays */
+} orc_far_params;
+
+/* Map of the rectangle [i0,i1) x [j0,j1) (i0 < 0: the whole grid) with the far
+ * field of each block replaced by its truncated series; *bound_max = the largest
+ * truncation bound of any block (at |w| = rho). */
+int orc_far_map(const orc_params *P, const orc_far_params *F, const double *lx, const double *ly, const double *lm,
+                int64_t nstar, int64_t i0, int64_t i1, int64_t j0, int64_t j1,
+                uint32_t *counts, uint64_t totals[3], double *bound_max, int nthreads);
+
+/* Per-ray far-field deflection, source position, pixel and truncation bound of
+ * rays (ray_i[k], ray_j[k]) of a rectangle whose origin is (i0, j0). */
+int orc_far_rays(const orc_params *P, const orc_far_params *F, const double *lx, const double *ly, const double *lm,
+                 int64_t nstar, int64_t i0, int64_t j0, const int64_t *ray_i, const int64_t *ray_j, int64_t n,
+                 double *alpha, double *ysrc, int64_t *pixel, double *bound, int nthreads);
+
 int orc_max_threads(void);
 #endif

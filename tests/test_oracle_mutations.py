@@ -28,10 +28,25 @@ MUTATIONS = [
     ("grid size", "G->nx = (int64_t)ceil(G->width / G->delta);", "G->nx = (int64_t)floor(G->width / G->delta);"),
     ("wrong component", "s2 += lm[i] * d2 / r2;", "s2 += lm[i] * d1 / r2;"),
 ]
+PINS = "tests/test_oracle_pins.py"
+
+# far-field approximation (Sect. 2.1, Eq. hierarchical), pinned by test_oracle_far.py
+FAR = "tests/test_oracle_far.py"
+FAR_MUTATIONS = [
+    ("far series sign", "double complex t = -lm[i] * u;", "double complex t = lm[i] * u;"),
+    ("far series power", "        t *= u;\n", "        t *= u * u;\n"),
+    ("far series index shift", "f += B->c[l] * wl;", "f += B->c[l] * wl * w;"),
+    ("far conjugate dropped", "*a2 = -cimag(f) + s2;", "*a2 = cimag(f) + s2;"),
+    ("near radius squared twice", "if (d1 * d1 + d2 * d2 < rn * rn) {", "if (d1 * d1 + d2 * d2 < rn) {"),
+    ("near lenses dropped", "for (int64_t k = 0; k < B->nnear; ++k)", "for (int64_t k = 0; k < 0; ++k)"),
+    ("tail bound exponent", "pow(t, F->order)", "pow(t, F->order + 1)"),
+    ("block radius halved", "B->rho = G->delta * sqrt(", "B->rho = 0.5 * G->delta * sqrt("),
+]
 
 
-@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_pins_catch_planted_mistake(tmp_path, name, old, new):
+@pytest.mark.parametrize("name,old,new,pins", [m + (PINS,) for m in MUTATIONS] + [m + (FAR,) for m in FAR_MUTATIONS],
+                         ids=[m[0] for m in MUTATIONS + FAR_MUTATIONS])
+def test_pins_catch_planted_mistake(tmp_path, name, old, new, pins):
     for d in ("oracle", "synth", "tests"):
         shutil.copytree(os.path.join(ROOT, d), tmp_path / d,
                         ignore=shutil.ignore_patterns("_build", "__pycache__", "*.so"))
@@ -40,6 +55,6 @@ def test_pins_catch_planted_mistake(tmp_path, name, old, new):
     assert text.count(old) == 1, f"mutation site not found: {old}"
     src.write_text(text.replace(old, new))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        "tests/test_oracle_pins.py"], cwd=tmp_path, capture_output=True, text=True, timeout=600)
+                        pins], cwd=tmp_path, capture_output=True, text=True, timeout=600)
     assert r.returncode == 1, f"planted mistake '{name}' was not caught:\n{r.stdout[-2000:]}"
     assert "FAILED" in r.stdout
