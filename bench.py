@@ -267,9 +267,10 @@ def cpu_baseline(seconds_target: float = 15.0):
                       f"= {inter:.3e} interactions) in {dt:.1f} s, FP64, OpenMP"}
 
 
-def profile_case():
+def profile_case(kind="fp32"):
     """Small case of the same kernel for ncu: a 4096 x 4096-ray window of the Fig. 1 map
-    (1.68e7 rays, 9.36e9 interactions), launched three times."""
+    (1.68e7 rays, 9.36e9 interactions), launched three times; kind "far" shoots it with
+    the far-field approximation (MM_FAR32, default order, ratio and block)."""
     import paper_1005_5198_gb300 as mm
     import synth
     from oracle import field as ofield
@@ -280,7 +281,8 @@ def profile_case():
     lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
     g = mm.mm_geometry_of(mm.params(**CFG1))
     c = g["nx"] // 2
-    p = mm.params(**CFG1, ray_rect=(c - 2048, c + 2048, c - 2048, c + 2048))
+    p = mm.params(**CFG1, ray_rect=(c - 2048, c + 2048, c - 2048, c + 2048),
+                  precision=mm.MM_FAR32 if kind == "far" else mm.MM_FP32C)
     for _ in range(3):
         m = mm.mm_shoot(ctx, lh, p)
         ms, _ = mm.mm_last_kernel_ms(ctx)
@@ -335,13 +337,14 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batch and serving phases")
-    ap.add_argument("--profile-case", action="store_true",
-                    help="shoot a 4096^2-ray window of the Fig. 1 map three times (for ncu captures) and exit")
+    ap.add_argument("--profile-case", nargs="?", const="fp32", choices=["fp32", "far"],
+                    help="shoot a 4096^2-ray window of the Fig. 1 map three times, exactly (fp32) or with the "
+                         "far-field approximation MM_FAR32 (far), for ncu captures, and exit")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.profile_case:
-        return profile_case()
+        return profile_case(args.profile_case)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
 

@@ -61,6 +61,18 @@ extern "C" {
 #define MM_FP32C  0   /* FP32 deflection sum, tile-relative coordinates, compensated
                          accumulation, FP64 near-lens terms, float-float epilogue */
 #define MM_FP64   1   /* plain FP64 everywhere */
+#define MM_FAR32  2   /* far-field approximation, the tree code's idea (Sect. 2.1, Eq.
+                         hierarchical) on blocks of rays: the ray lattice is cut into
+                         blocks of far_block x far_block tiles (64 x 32 rays each);
+                         lenses within rho / far_ratio of a block's centre (rho: the
+                         block's half-diagonal) are summed exactly for each of its rays
+                         (FP32 with FP64 terms near the tile, as MM_FP32C); the others
+                         enter far_order terms of the series of sum m / (z - z_i) about
+                         the centre. Per-ray truncation error <= sum over far lenses of
+                         m t^P / (|d| (1 - t)), t = |z - z_B| / |d| < far_ratio, d the
+                         lens offset from the centre; its largest value over the map's
+                         blocks is mm_stats.far_bound. Cost per ray: P complex FMAs plus
+                         the near lenses, instead of N* interactions. */
 
 #define MM_MASS_UNIT       0   /* m_i = 1 */
 #define MM_MASS_LOGNORMAL  1   /* m_i = exp(mass_mu + mass_s z), z ~ N(0, 1) */
@@ -88,6 +100,10 @@ typedef struct {
     uint64_t seed;           /* lens-field seed (SplitMix64 streams) */
     int64_t  ray_rect[4];    /* [i0, i1, j0, j1) sub-rectangle of the global ray grid, or
                                 all -1 for the whole grid (tests and windowed runs) */
+    int32_t  far_order;      /* MM_FAR32: series terms P, 1 .. 32 (default 16) */
+    double   far_ratio;      /* MM_FAR32: near ratio q, 0 < q <= 0.9 (default 0.3) */
+    int32_t  far_block;      /* MM_FAR32: block side in ray tiles, 1 .. 64 (default 8); blocks
+                                are counted from the origin of the shot rectangle */
 } mm_params;
 
 /* Lens-field derivation used by mm_create_lenses when nstar < 0 or
@@ -110,6 +126,8 @@ typedef struct {
     int32_t  lens_splits;   /* lens segments per ray tile: maps with few tiles (< 2048) and many
                                lenses (> 1024) spread each tile's lens sum over several CTAs and
                                combine the segments' float-float sums in segment order */
+    double   far_bound;     /* MM_FAR32: largest truncation bound of any ray (Einstein radii,
+                               evaluated at the block radius); 0 for the exact precisions */
 } mm_stats;
 
 typedef struct {

@@ -19,7 +19,7 @@ from .buildlib import LIB, build, up_to_date  # noqa: F401
 
 MM_OK, MM_EINVAL, MM_ENOMEM, MM_EBUSY, MM_ENOTFOUND = 0, -1, -2, -3, -4
 MM_ETIMEDOUT, MM_EDEVICE, MM_EAGAIN, MM_ECANCELED = -5, -6, -7, -8
-MM_FP32C, MM_FP64 = 0, 1
+MM_FP32C, MM_FP64, MM_FAR32 = 0, 1, 2
 MM_MASS_UNIT, MM_MASS_LOGNORMAL = 0, 1
 MM_PROFILE_GAUSSIAN, MM_PROFILE_DISC = 0, 1
 
@@ -35,13 +35,15 @@ class mm_params(C.Structure):
                 ("npix_side", C.c_int32), ("nrays_per_pix", C.c_double), ("shoot_margin", C.c_double),
                 ("precision", C.c_int32), ("nstar", C.c_int64), ("disc_radius", C.c_double),
                 ("mass_model", C.c_int32), ("mass_mu", C.c_double), ("mass_s", C.c_double), ("seed", C.c_uint64),
-                ("ray_rect", C.c_int64 * 4)]
+                ("ray_rect", C.c_int64 * 4), ("far_order", C.c_int32), ("far_ratio", C.c_double),
+                ("far_block", C.c_int32)]
 
 
 class mm_stats(C.Structure):
     _fields_ = [("rays_shot", C.c_uint64), ("rays_in", C.c_uint64), ("rays_out", C.c_uint64),
                 ("interactions", C.c_uint64), ("nx", C.c_uint64), ("ny", C.c_uint64), ("nstar", C.c_int64),
-                ("seconds", C.c_double), ("mu_mean", C.c_double), ("lens_splits", C.c_int32)]
+                ("seconds", C.c_double), ("mu_mean", C.c_double), ("lens_splits", C.c_int32),
+                ("far_bound", C.c_double)]
 
 
 class mm_compare(C.Structure):

@@ -17,6 +17,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "../../include/mm.h"
+#include "mm_far.h"
 #include "mm_internal.h"
 
 namespace mm {
@@ -32,6 +33,13 @@ struct NvtxRange {
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);
+
+// Return the library status of a failed CUDA call from the enclosing function.
+#define MM_CUDA(call)                                       \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
 
 // Validated geometry of a map request (host FP64).
 struct Geo {
@@ -89,6 +97,13 @@ struct MapObj {
     unsigned int *seg_done = nullptr;        // split tiles: finished segments per tile
     unsigned long long shot_total = 0;       // rays shot into the map (grows with mm_shoot_into)
     bool owns_outputs = true;                // false: counts/totals belong to another map
+    // MM_FAR32: block series, near lists and the largest tail bound (mm_far.cu)
+    FarDesc far{};
+    float *far_coef = nullptr;
+    unsigned long long *far_off = nullptr;
+    int *far_idx = nullptr;
+    unsigned int *far_bmax = nullptr;
+    double far_bound = 0.0;
     std::shared_ptr<LensSet> lenses;
     cudaEvent_t done = nullptr;
     double seconds = 0.0;
@@ -104,10 +119,12 @@ struct Server;
 struct LaunchScratch {
     WorkHeader *d_hdr = nullptr;
     MapDesc *d_maps = nullptr;
+    FarDesc *d_far = nullptr;         // MM_FAR32 launches: one per map, parallel to d_maps
     unsigned long long *d_counter = nullptr;
     int cap = 0;
     WorkHeader *h_hdr = nullptr;      // pinned
     MapDesc *h_maps = nullptr;        // pinned
+    FarDesc *h_far = nullptr;         // pinned
 };
 
 }  // namespace mm
@@ -141,6 +158,10 @@ int upload_lenses(mm_ctx *ctx, const double *x, const double *y, const double *m
 int alloc_map(mm_ctx *ctx, const mm_params *p, const Geo &g, std::shared_ptr<LensSet> lenses, cudaStream_t s,
               std::shared_ptr<MapObj> *out, const MapObj *into = nullptr);
 void fill_desc(const MapObj &m, MapDesc *d);
+// MM_FAR32: build the block series and near lists of map m on stream s (synchronises
+// once, to size the near lists); free them.
+int far_prepare(mm_ctx *ctx, MapObj &m, cudaStream_t s);
+void far_release(MapObj &m);
 int choose_variant(mm_ctx *ctx, const mm_params *p, const Geo &g);
 int scratch_reserve(mm_ctx *ctx, LaunchScratch *sc, int n_maps);
 void scratch_free(mm_ctx *ctx, LaunchScratch *sc);

@@ -1,0 +1,687 @@
+// mm_far.cu -- the far-field approximation MM_FAR32 (see mm_far.h): the tree code's
+// idea of Sect. 2.1 (Eq. hierarchical: near lenses one by one, distant ones grouped;
+// pseudo-lens deflections computed at test rays and interpolated for the rays around
+// them), recast for the GPU. The test ray is the centre of a block of ray tiles; the
+// "interpolation" is the series of the far lenses' deflection about it, with a
+// rigorous tail bound instead of an empirical accuracy.
+//
+// Per map, before its rays are shot:
+//   k_far_count  near-lens count of every block, one warp per block (FP32 offsets,
+//                explicit rounding, so that every kernel decides alike);
+//   k_far_scan   exclusive prefix sum of the counts (near-list offsets);
+//   k_far_fill   the near lenses of every block in index order, one warp per block;
+//   k_far_setup  per block: the series coefficients c'_0 (float-float) and c'_l
+//                (FP32), l < P, and the tail bound.
+// Then the persistent k_shoot_far takes work items of whole blocks (or single tile
+// rows of a block, when a map has few blocks): the block's series and near lenses
+// are staged in shared memory once, and its 64 x 32-ray tiles follow without a
+// barrier. Each ray evaluates the series by Horner's rule in v = (z - z_B) / rho
+// (packed f32x2 over pairs of rows) and adds its block's near lenses: FP32 terms
+// relative to the tile centre, FP64 terms for lenses within kNearRadius of the
+// tile's ray box. The float-float lens equation is the exact FP32 kernel's; the
+// count goes to the map by run-length warp aggregation (rays of a warp share a
+// lattice row, so equal pixels come in runs). The debug dump runs the same tile
+// code one tile at a time.
+#include <algorithm>
+#include <cmath>
+
+#include "mm_ctx.h"
+#include "mm_device.cuh"
+#include "mm_far.h"
+
+namespace mm {
+namespace dev {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kFarWarps = kFarThreads / 32;
+constexpr int kShootThreads = 256;                 // threads of the shoot kernels' CTAs (2 per SM)
+constexpr int kFarRows = kTileRays / kShootThreads; // rays per thread: one column, 8 rows
+
+__device__ __forceinline__ void split_d(double v, float &h, float &l)
+{
+    h = __double2float_rn(v);
+    l = __double2float_rn(v - (double)h);
+}
+
+// Centre of block (bx, by) of map M (FP64).
+__device__ __forceinline__ void far_centre(const MapDesc &M, const FarDesc &F, long long bx, long long by,
+                                           double &xb, double &yb)
+{
+    const long long bw = 64LL * F.bt, bh = 32LL * F.bt;
+    xb = ((double)(M.i0 + bx * bw + bw / 2) - M.half_nx) * M.delta;
+    yb = ((double)(M.j0 + by * bh + bh / 2) - M.half_ny) * M.delta;
+}
+
+// Offset of a lens (float-float coordinates q) from a float-float centre, and its
+// squared length, rounded step by step, so that every kernel takes the same near
+// decision for the same lens and block.
+__device__ __forceinline__ void far_offset(const float4 q, float cxh, float cxl, float cyh, float cyl, float &dx,
+                                           float &dy, float &r2)
+{
+    dx = __fadd_rn(__fsub_rn(q.x, cxh), __fsub_rn(q.z, cxl));
+    dy = __fadd_rn(__fsub_rn(q.y, cyh), __fsub_rn(q.w, cyl));
+    r2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+}
+
+// One warp per block: the near-lens count of block b into a[b].
+__global__ void __launch_bounds__(kFarThreads) k_far_count(const MapDesc M, const FarDesc F, unsigned long long *a)
+{
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * kFarWarps;
+    for (long long b = (long long)blockIdx.x * kFarWarps + (threadIdx.x >> 5); b < F.nblocks; b += warps) {
+        double xb, yb;
+        far_centre(M, F, b % F.blocks_x, b / F.blocks_x, xb, yb);
+        float cxh, cxl, cyh, cyl;
+        split_d(xb, cxh, cxl);
+        split_d(yb, cyh, cyl);
+        unsigned cnt = 0;
+        for (long long k = lane; k < M.nstar; k += 32) {
+            float dx, dy, r2;
+            far_offset(M.lh[k], cxh, cxl, cyh, cyl, dx, dy, r2);
+            cnt += r2 < F.rn2 ? 1u : 0u;
+        }
+        cnt = __reduce_add_sync(kFull, cnt);
+        if (lane == 0) a[b] = cnt;
+    }
+}
+
+// One warp per block: the near lenses of block b, in index order, from near_off[b].
+__global__ void __launch_bounds__(kFarThreads) k_far_fill(const MapDesc M, const FarDesc F, int *near_idx)
+{
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * kFarWarps;
+    for (long long b = (long long)blockIdx.x * kFarWarps + (threadIdx.x >> 5); b < F.nblocks; b += warps) {
+        double xb, yb;
+        far_centre(M, F, b % F.blocks_x, b / F.blocks_x, xb, yb);
+        float cxh, cxl, cyh, cyl;
+        split_d(xb, cxh, cxl);
+        split_d(yb, cyh, cyl);
+        unsigned long long out = F.near_off[b];
+        for (long long base = 0; base < M.nstar; base += 32) {
+            const long long k = base + lane;
+            bool near = false;
+            if (k < M.nstar) {
+                float dx, dy, r2;
+                far_offset(M.lh[k], cxh, cxl, cyh, cyl, dx, dy, r2);
+                near = r2 < F.rn2;
+            }
+            const unsigned bal = __ballot_sync(kFull, near);
+            if (near) near_idx[out + __popc(bal & ((1u << lane) - 1u))] = (int)k;
+            out += __popc(bal);
+        }
+    }
+}
+
+// One CTA of 1024 threads walks the array in chunks, carrying the running total.
+__global__ void __launch_bounds__(1024) k_far_scan(unsigned long long *a, long long n)
+{
+    __shared__ unsigned long long wsum[32];
+    __shared__ unsigned long long carry;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (long long base = 0; base < n; base += 1024) {
+        const long long i = base + threadIdx.x;
+        const unsigned long long v = i < n ? a[i] : 0ULL;
+        unsigned long long x = v;                             // inclusive scan within the warp
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {                                         // inclusive scan of the warp totals
+            unsigned long long t = wsum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(kFull, t, o);
+                if (lane >= o) t += y;
+            }
+            wsum[lane] = t;
+        }
+        __syncthreads();
+        if (i < n) a[i] = carry + (w > 0 ? wsum[w - 1] : 0ULL) + x - v;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += wsum[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) a[n] = carry;
+}
+
+// Per block: ordered near list, series coefficients and tail bound. PMAX >= F.order.
+template <int PMAX, bool MASS>
+__global__ void __launch_bounds__(kFarThreads) k_far_setup(const MapDesc M, const FarDesc F, float *coef)
+{
+    constexpr int NC = PMAX > 1 ? PMAX - 1 : 1;
+    __shared__ float red_c[kFarWarps][2 * NC];
+    __shared__ float4 red_0[kFarWarps];
+    __shared__ float red_b[kFarWarps];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int P = F.order;
+    const float rho = F.rho;
+    for (long long b = blockIdx.x; b < F.nblocks; b += gridDim.x) {
+        double xb, yb;
+        far_centre(M, F, b % F.blocks_x, b / F.blocks_x, xb, yb);
+        float cxh, cxl, cyh, cyl;
+        split_d(xb, cxh, cxl);
+        split_d(yb, cyh, cyl);
+        float c0rh = 0.f, c0rl = 0.f, c0ih = 0.f, c0il = 0.f;
+        float cr[NC], ci[NC];
+#pragma unroll
+        for (int l = 0; l < NC; ++l) cr[l] = ci[l] = 0.f;
+        float bnd = 0.f;
+        for (long long k = tid; k < M.nstar; k += kFarThreads) {
+            float dx, dy, r2;
+            far_offset(M.lh[k], cxh, cxl, cyh, cyl, dx, dy, r2);
+            if (!(r2 < F.rn2)) {                              // far (the near lenses are k_far_fill's)
+                const float m = MASS ? M.lmf[k] : 1.f;
+                const float inv = rcp_approx(r2);
+                const float ur = __fmul_rn(dx, inv), ui = -__fmul_rn(dy, inv);   // u = 1 / d
+                float tr = -m * ur, ti = -m * ui;                                 // -m / d
+                float s, e;
+                two_sum(c0rh, tr, s, e);
+                c0rh = s;
+                c0rl = __fadd_rn(c0rl, e);
+                two_sum(c0ih, ti, s, e);
+                c0ih = s;
+                c0il = __fadd_rn(c0il, e);
+                const float sr = rho * ur, si = rho * ui;                         // rho / d, |rho / d| < q
+#pragma unroll
+                for (int l = 1; l < PMAX; ++l) {
+                    if (l < P) {                                                  // -m rho^l / d^(l+1)
+                        const float nr = fmaf(tr, sr, -ti * si);
+                        const float ni = fmaf(tr, si, ti * sr);
+                        tr = nr;
+                        ti = ni;
+                        cr[l - 1] += tr;
+                        ci[l - 1] += ti;
+                    }
+                }
+                const float dinv = rsqrtf(r2);                                    // 1 / |d|
+                const float t = rho * dinv;
+                bnd = fmaf(m * dinv, exp2f((float)P * __log2f(t)) / (1.f - t), bnd);
+            }
+        }
+        // CTA reduction: butterfly within warps, then warps in order
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float s, e;
+            const float rh = __shfl_xor_sync(kFull, c0rh, o), rl = __shfl_xor_sync(kFull, c0rl, o);
+            two_sum(c0rh, rh, s, e);
+            c0rh = s;
+            c0rl = __fadd_rn(__fadd_rn(c0rl, rl), e);
+            const float ih = __shfl_xor_sync(kFull, c0ih, o), il = __shfl_xor_sync(kFull, c0il, o);
+            two_sum(c0ih, ih, s, e);
+            c0ih = s;
+            c0il = __fadd_rn(__fadd_rn(c0il, il), e);
+#pragma unroll
+            for (int l = 0; l < NC; ++l) {
+                if (l + 1 < P) {
+                    cr[l] += __shfl_xor_sync(kFull, cr[l], o);
+                    ci[l] += __shfl_xor_sync(kFull, ci[l], o);
+                }
+            }
+            bnd += __shfl_xor_sync(kFull, bnd, o);
+        }
+        if (lane == 0) {
+            red_0[w] = make_float4(c0rh, c0rl, c0ih, c0il);
+#pragma unroll
+            for (int l = 0; l < NC; ++l) {
+                red_c[w][2 * l] = cr[l];
+                red_c[w][2 * l + 1] = ci[l];
+            }
+            red_b[w] = bnd;
+        }
+        __syncthreads();
+        float *cb = coef + b * (long long)F.stride;
+        if (tid == 0) {
+            float4 a0 = red_0[0];
+            float tb = red_b[0];
+            for (int q = 1; q < kFarWarps; ++q) {
+                a0 = ff_add4(a0, red_0[q]);
+                tb += red_b[q];
+            }
+            cb[0] = a0.x;
+            cb[1] = a0.y;
+            cb[2] = a0.z;
+            cb[3] = a0.w;
+            // a little above the FP32 sum (fast log2 / exp2, rounding), so that the bound stays a bound
+            atomicMax(F.bound_max, __float_as_uint(tb * 1.001f));
+        }
+        for (int c = tid; c < 2 * (P - 1); c += kFarThreads) {
+            float v = red_c[0][c];
+            for (int q = 1; q < kFarWarps; ++q) v += red_c[q][c];
+            cb[4 + c] = v;
+        }
+        __syncthreads();                                      // red_* are rewritten by the next block
+    }
+}
+
+constexpr int kNearCap = 512;                 // near lenses staged at once per item
+
+struct __align__(16) SmemFar {
+    float4 nl[kNearCap];                      // near lens offset from the block centre, float-float (xh, xl, yh, yl)
+    float nm[kNearCap];                       // its mass
+    int ng[kNearCap];                         // its index, for FP64 terms
+    float coef[4 + 2 * (kFarMaxOrder - 1)];   // the block's series
+    unsigned long long next;                  // next work item (production loop)
+    long long chunk0;                         // first near lens held in nl/nm/ng
+    LoopSmem loop;                            // debug dump loop
+    unsigned red_in, red_out;
+};
+
+// Stage the series of block blk and its near lenses [c0, c0 + kNearCap) into shared
+// memory (called by all threads; the caller synchronises before and after).
+__device__ __forceinline__ void far_stage(const MapDesc &M, const FarDesc &F, long long blk, long long c0, bool coefs,
+                                          SmemFar &S)
+{
+    const int tid = threadIdx.x;
+    if (coefs)
+        for (int c = tid; c < 4 + 2 * (F.order - 1); c += kShootThreads) S.coef[c] = F.coef[blk * (long long)F.stride + c];
+    double xb, yb;
+    far_centre(M, F, blk % F.blocks_x, blk / F.blocks_x, xb, yb);
+    float cxh, cxl, cyh, cyl;
+    split_d(xb, cxh, cxl);
+    split_d(yb, cyh, cyl);
+    const unsigned long long off0 = F.near_off[blk];
+    const long long n_near = (long long)(F.near_off[blk + 1] - off0);
+    const long long end = min(n_near, c0 + (long long)kNearCap);
+    for (long long k = c0 + tid; k < end; k += kShootThreads) {
+        const int g = F.near_idx[off0 + k];
+        const float4 q = M.lh[g];
+        float sh, se, th, te;
+        two_sum(q.x, -cxh, sh, se);                           // exact split of x_h - c_h
+        two_sum(q.y, -cyh, th, te);
+        S.nl[k - c0] = make_float4(sh, __fadd_rn(se, __fsub_rn(q.z, cxl)), th, __fadd_rn(te, __fsub_rn(q.w, cyl)));
+        S.nm[k - c0] = M.unit_mass ? 1.f : M.lmf[g];
+        S.ng[k - c0] = g;
+    }
+    if (tid == 0) S.chunk0 = c0;
+}
+
+// Production binning: rays of a warp lie along one lattice row, so equal pixels
+// come in runs; the first lane of each run adds the run's length.
+__device__ __forceinline__ void far_bin(const MapDesc &M, bool valid, bool inside, unsigned pix, unsigned &cnt_in,
+                                        unsigned &cnt_out)
+{
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned key = inside ? pix : 0xffffffffu;
+    const unsigned left = __shfl_up_sync(kFull, key, 1);
+    const bool start = lane == 0 || left != key;
+    const unsigned starts = __ballot_sync(kFull, start);
+    if (inside && start) {
+        const unsigned above = starts & ~((2u << lane) - 1u);    // run starts after this lane
+        const unsigned next = above ? (unsigned)(__ffs(above) - 1) : 32u;
+        atomicAdd(M.counts + pix, next - lane);
+    }
+    cnt_in += inside ? 1u : 0u;
+    cnt_out += (valid && !inside) ? 1u : 0u;
+}
+
+// The rays of tile (tx, ty), whose block's series and first near chunk are staged in
+// S. Near lists longer than kNearCap are re-staged chunk by chunk (uniform syncs).
+template <bool DUMP, bool MASS>
+__device__ void far_tile(const LaunchArgs &A, const FarDesc &F, const MapDesc &M, long long blk, long long tx,
+                         long long ty, int item, SmemFar &S, unsigned &cnt_in, unsigned &cnt_out)
+{
+    constexpr int K = kFarRows;
+    const int tid = threadIdx.x, w = tid >> 5;
+    const int iloc = (w & 1) * 32 + (tid & 31);
+    const int jloc0 = (w >> 1) * K;
+    const long long ib = M.i0 + tx * kTileX, jb = M.j0 + ty * kTileY;
+    const long long bw = 64LL * F.bt, bh = 32LL * F.bt;
+    const long long ibB = M.i0 + (blk % F.blocks_x) * bw, jbB = M.j0 + (blk / F.blocks_x) * bh;
+    const int P = F.order;
+
+    // ---- far series: Horner's rule in v = (z - z_B) / rho, packed over row pairs ----
+    // Lattice offsets are formed in 32-bit integers (|n| <= bw / 2) and rows by exact
+    // float steps: no 64-bit integer conversion per ray.
+    const float nxo = (float)(int)(ib + iloc - ibB - bw / 2) + 0.5f;
+    const float vx = __fmaf_rn(nxo, F.dv_h, __fmul_rn(nxo, F.dv_l));
+    const float nyo0 = (float)(int)(jb + jloc0 - jbB - bh / 2) + 0.5f;
+    float4 acc[K];
+    {
+        constexpr int H = K / 2;
+        float2 VY[H], VYN[H], SR[H], SI[H];
+#pragma unroll
+        for (int q = 0; q < H; ++q) {
+            const float na = nyo0 + (float)(2 * q), nb = nyo0 + (float)(2 * q + 1);
+            VY[q] = make_float2(__fmaf_rn(na, F.dv_h, __fmul_rn(na, F.dv_l)), __fmaf_rn(nb, F.dv_h, __fmul_rn(nb, F.dv_l)));
+            VYN[q] = make_float2(-VY[q].x, -VY[q].y);
+            SR[q] = SI[q] = make_float2(0.f, 0.f);
+        }
+        const float2 VX = make_float2(vx, vx);
+        if (P > 1) {
+            const float tr = S.coef[4 + 2 * (P - 2)], ti = S.coef[5 + 2 * (P - 2)];
+#pragma unroll
+            for (int q = 0; q < H; ++q) {
+                SR[q] = make_float2(tr, tr);
+                SI[q] = make_float2(ti, ti);
+            }
+            for (int l = P - 2; l >= 1; --l) {                // s <- s v + c'_l
+                const float cr = S.coef[4 + 2 * (l - 1)], ci = S.coef[5 + 2 * (l - 1)];
+                const float2 CR = make_float2(cr, cr), CI = make_float2(ci, ci);
+#pragma unroll
+                for (int q = 0; q < H; ++q) {
+                    const float2 nr = __ffma2_rn(SI[q], VYN[q], __ffma2_rn(SR[q], VX, CR));
+                    const float2 ni = __ffma2_rn(SR[q], VY[q], __ffma2_rn(SI[q], VX, CI));
+                    SR[q] = nr;
+                    SI[q] = ni;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < H; ++q) {                     // s <- s v
+                const float2 nr = __ffma2_rn(SI[q], VYN[q], __fmul2_rn(SR[q], VX));
+                const float2 ni = __ffma2_rn(SR[q], VY[q], __fmul2_rn(SI[q], VX));
+                SR[q] = nr;
+                SI[q] = ni;
+            }
+        }
+        // float-float sums S = -alpha: the far part is -conj(c'_0 + s) = (-Re, +Im)
+        const float c0rh = S.coef[0], c0rl = S.coef[1], c0ih = S.coef[2], c0il = S.coef[3];
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+            const float sr = (r & 1) ? SR[r >> 1].y : SR[r >> 1].x;
+            const float si = (r & 1) ? SI[r >> 1].y : SI[r >> 1].x;
+            float s, e;
+            two_sum(-c0rh, -sr, s, e);
+            acc[r].x = s;
+            acc[r].y = __fadd_rn(-c0rl, e);
+            two_sum(c0ih, si, s, e);
+            acc[r].z = s;
+            acc[r].w = __fadd_rn(c0il, e);
+        }
+    }
+
+    // ---- the block's near lenses, exactly, relative to the tile centre ----
+    const unsigned long long off0 = F.near_off[blk];
+    const long long n_near = (long long)(F.near_off[blk + 1] - off0);
+    unsigned onlens = 0;
+    if (n_near > 0) {
+        const float dlt = M.delta_f, dll = M.delta_l;
+        // tile centre offset from the block centre (float-float): k lattice steps, k integer
+        const float kx = (float)(int)(ib - ibB + 32 - bw / 2), ky = (float)(int)(jb - jbB + 16 - bh / 2);
+        const float txh = __fmul_rn(kx, dlt), txl = __fmaf_rn(kx, dll, __fmaf_rn(kx, dlt, -txh));
+        const float tyh = __fmul_rn(ky, dlt), tyl = __fmaf_rn(ky, dll, __fmaf_rn(ky, dlt, -tyh));
+        const float rxn = (float)iloc - 31.5f;
+        const float rx = __fmaf_rn(rxn, dlt, __fmul_rn(rxn, dll));
+        float ry[K], nxs[K], nys[K];
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+            const float ryn = (float)(jloc0 + r) - 15.5f;
+            ry[r] = __fmaf_rn(ryn, dlt, __fmul_rn(ryn, dll));
+            nxs[r] = nys[r] = 0.f;
+        }
+        const float hx = 32.0f * dlt + kNearRadius, hy = 16.0f * dlt + kNearRadius;
+        for (long long c0 = 0; c0 < n_near; c0 += kNearCap) {
+            if (S.chunk0 != c0) {                             // long near list: stage this chunk
+                __syncthreads();
+                far_stage(M, F, blk, c0, false, S);
+                __syncthreads();
+            }
+            const int cnt = (int)min((long long)kNearCap, n_near - c0);
+            for (int j = 0; j < cnt; ++j) {
+                const float4 L = S.nl[j];
+                const float lx = __fadd_rn(__fsub_rn(L.x, txh), __fsub_rn(L.y, txl));   // from the tile centre
+                const float ly = __fadd_rn(__fsub_rn(L.z, tyh), __fsub_rn(L.w, tyl));
+                if (fabsf(lx) < hx && fabsf(ly) < hy) {       // within kNearRadius of the tile: FP64
+                    const int g = S.ng[j];
+                    const double xl = M.lx[g], yl = M.ly[g];
+                    const double ml = MASS ? M.lm[g] : 1.0;
+                    const double x1 = ((double)(ib + iloc) + 0.5 - M.half_nx) * M.delta;
+#pragma unroll
+                    for (int r = 0; r < K; ++r) {
+                        const double x2 = ((double)(jb + jloc0 + r) + 0.5 - M.half_ny) * M.delta;
+                        const double d1 = xl - x1, d2 = yl - x2;
+                        const double r2 = d1 * d1 + d2 * d2;
+                        if (r2 == 0.0) {
+                            onlens |= 1u << r;
+                        } else {
+                            const double t = ml / r2;
+                            add_ff(acc[r].x, acc[r].y, t * d1);
+                            add_ff(acc[r].z, acc[r].w, t * d2);
+                        }
+                    }
+                    continue;
+                }
+                const float m = MASS ? S.nm[j] : 1.f;
+                const float dX = lx - rx;
+                const float dX2 = dX * dX;
+#pragma unroll
+                for (int r = 0; r < K; ++r) {
+                    const float dY = ly - ry[r];
+                    const float t = m * rcp_approx(fmaf(dY, dY, dX2));
+                    nxs[r] = fmaf(t, dX, nxs[r]);
+                    nys[r] = fmaf(t, dY, nys[r]);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+            float s, e;
+            two_sum(acc[r].x, nxs[r], s, e);
+            acc[r].x = s;
+            acc[r].y = __fadd_rn(acc[r].y, e);
+            two_sum(acc[r].z, nys[r], s, e);
+            acc[r].z = s;
+            acc[r].w = __fadd_rn(acc[r].w, e);
+        }
+    }
+
+    // ---- lens equation and pixel (float-float), as in the exact FP32 kernel ----
+    const float nsf = (float)M.nside;
+    const long long gi = ib + iloc;
+    float uxh, uxl;
+    ff_axis(M.ax_h, M.ax_l, (float)(int)(2 * gi + 1 - M.nx), M.half_n, uxh, uxl);
+    const bool col_ok = gi < M.i0 + M.ni;
+    const float ay0 = (float)(int)(2 * (jb + jloc0) + 1 - M.ny);     // |2 j + 1 - ny| < 2^23: exact steps
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const long long gj = jb + jloc0 + r;
+        float uyh, uyl;
+        ff_axis(M.ay_h, M.ay_l, ay0 + (float)(2 * r), M.half_n, uyh, uyl);
+        const float4 a = acc[r];
+        const float I1 = ff_pixel(uxh, uxl, a.x, a.y, M.ip_h, M.ip_l);
+        const float I2 = ff_pixel(uyh, uyl, a.z, a.w, M.ip_h, M.ip_l);
+        const bool valid = col_ok && gj < M.j0 + M.nj;
+        const bool inside =
+            valid && !((onlens >> r) & 1u) && I1 >= 0.f && I1 < nsf && I2 >= 0.f && I2 < nsf;
+        const unsigned pix = inside ? (unsigned)I2 * (unsigned)M.nside + (unsigned)I1 : 0xffffffffu;
+        if (DUMP)
+            emit_ray<true>(A, M, item, iloc + kTileX * (jloc0 + r), valid, inside, pix, -((double)a.x + (double)a.y),
+                           -((double)a.z + (double)a.w), cnt_in, cnt_out);
+        else
+            far_bin(M, valid, inside, pix, cnt_in, cnt_out);
+    }
+}
+
+// Production: persistent over work items of all maps of the launch. An item is a
+// group of F.rows_per_item tile rows of one block (all its tile columns); its series
+// and near lenses are staged once, and the next item is fetched ahead.
+template <bool MASS>
+__device__ void far_item(const LaunchArgs &A, const FarDesc &F, const MapDesc &M, unsigned long long it, SmemFar &S,
+                         unsigned &ci, unsigned &co)
+{
+    const long long gpb = F.bt / F.rows_per_item;             // items per block
+    const long long blk = (long long)(it / (unsigned long long)gpb);
+    const long long grp = (long long)(it % (unsigned long long)gpb);
+    far_stage(M, F, blk, 0, true, S);
+    __syncthreads();
+    const long long bx = blk % F.blocks_x, by = blk / F.blocks_x;
+    const long long tiles_y = (M.nj + kTileY - 1) / kTileY;
+    for (long long ty = by * F.bt + grp * F.rows_per_item; ty < by * F.bt + (grp + 1) * F.rows_per_item; ++ty) {
+        if (ty >= tiles_y) break;
+        for (long long tx = bx * F.bt; tx < (bx + 1) * F.bt && tx < M.tiles_x; ++tx)
+            far_tile<false, MASS>(A, F, M, blk, tx, ty, 0, S, ci, co);
+    }
+}
+
+__global__ void __launch_bounds__(kShootThreads, 2) k_shoot_far(const LaunchArgs A, const FarDesc *far,
+                                                             unsigned long long total_items)
+{
+    __shared__ SmemFar S;
+    const int tid = threadIdx.x;
+    const int n_maps = A.hdr->n_maps;
+    if (tid == 0) S.next = atomicAdd(A.work_counter, 1ULL);
+    __syncthreads();
+    for (;;) {
+        const unsigned long long g = S.next;
+        if (g >= total_items) break;
+        if (tid == 0) {
+            S.red_in = 0;
+            S.red_out = 0;
+        }
+        __syncthreads();                                      // every thread has read S.next
+        if (tid == 0) S.next = atomicAdd(A.work_counter, 1ULL);
+        int lo = 0, hi = n_maps - 1;                          // last map with item_begin <= g
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (far[mid].item_begin <= g) lo = mid; else hi = mid - 1;
+        }
+        const MapDesc &M = A.maps[lo];
+        const FarDesc &F = far[lo];
+        unsigned ci = 0, co = 0;
+        if (M.unit_mass) far_item<false>(A, F, M, g - F.item_begin, S, ci, co);
+        else far_item<true>(A, F, M, g - F.item_begin, S, ci, co);
+        ci = __reduce_add_sync(kFull, ci);
+        co = __reduce_add_sync(kFull, co);
+        if ((tid & 31) == 0) {
+            atomicAdd(&S.red_in, ci);
+            atomicAdd(&S.red_out, co);
+        }
+        __syncthreads();                                      // also: shared data of this item consumed
+        if (tid == 0) {
+            if (S.red_in) atomicAdd(M.totals + 0, (unsigned long long)S.red_in);
+            if (S.red_out) atomicAdd(M.totals + 1, (unsigned long long)S.red_out);
+        }
+    }
+}
+
+// Debug dump: the tiles of the request through the same tile code, one tile per item.
+__global__ void __launch_bounds__(kShootThreads, 2) k_shoot_far_dump(const LaunchArgs A, const FarDesc *far)
+{
+    __shared__ SmemFar S;
+    persistent_loop<true>(A, S.loop, [&](const MapDesc &M, unsigned long long tile, int, int item, unsigned &ci,
+                                         unsigned &co) {
+        const FarDesc &F = far[&M - A.maps];
+        const long long tx = (long long)(tile % (unsigned long long)M.tiles_x);
+        const long long ty = (long long)(tile / (unsigned long long)M.tiles_x);
+        const long long blk = (ty / F.bt) * F.blocks_x + tx / F.bt;
+        __syncthreads();
+        far_stage(M, F, blk, 0, true, S);
+        __syncthreads();
+        if (M.unit_mass) far_tile<true, false>(A, F, M, blk, tx, ty, item, S, ci, co);
+        else far_tile<true, true>(A, F, M, blk, tx, ty, item, S, ci, co);
+    });
+}
+
+}  // namespace
+}  // namespace dev
+
+cudaError_t launch_far_count(const MapDesc &M, const FarDesc &F, unsigned long long *a, int grid, cudaStream_t s)
+{
+    dev::k_far_count<<<grid, kFarThreads, 0, s>>>(M, F, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_far_scan(unsigned long long *a, long long n, cudaStream_t s)
+{
+    dev::k_far_scan<<<1, 1024, 0, s>>>(a, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_far_setup(const MapDesc &M, const FarDesc &F, float *coef, int *near_idx, int grid,
+                             cudaStream_t s)
+{
+    dev::k_far_fill<<<grid, kFarThreads, 0, s>>>(M, F, near_idx);
+    const bool mass = !M.unit_mass;
+    if (F.order <= 8) {
+        if (mass) dev::k_far_setup<8, true><<<grid, kFarThreads, 0, s>>>(M, F, coef);
+        else dev::k_far_setup<8, false><<<grid, kFarThreads, 0, s>>>(M, F, coef);
+    } else if (F.order <= 16) {
+        if (mass) dev::k_far_setup<16, true><<<grid, kFarThreads, 0, s>>>(M, F, coef);
+        else dev::k_far_setup<16, false><<<grid, kFarThreads, 0, s>>>(M, F, coef);
+    } else {
+        if (mass) dev::k_far_setup<32, true><<<grid, kFarThreads, 0, s>>>(M, F, coef);
+        else dev::k_far_setup<32, false><<<grid, kFarThreads, 0, s>>>(M, F, coef);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shoot_far(const LaunchArgs &args, const FarDesc *far, unsigned long long total_items, int grid,
+                             bool dump, cudaStream_t s)
+{
+    if (dump) dev::k_shoot_far_dump<<<grid, dev::kShootThreads, 0, s>>>(args, far);
+    else dev::k_shoot_far<<<grid, dev::kShootThreads, 0, s>>>(args, far, total_items);
+    return cudaGetLastError();
+}
+
+int far_ctas_per_sm() { return 2; }
+
+// ---- host: per-map preparation ------------------------------------------------
+
+void far_release(MapObj &m)
+{
+    if (!m.arena) return;
+    m.arena->free(m.far_coef);
+    m.arena->free(m.far_off);
+    m.arena->free(m.far_idx);
+    m.arena->free(m.far_bmax);
+    m.far_coef = nullptr;
+    m.far_off = nullptr;
+    m.far_idx = nullptr;
+    m.far_bmax = nullptr;
+}
+
+int far_prepare(mm_ctx *ctx, MapObj &m, cudaStream_t s)
+{
+    far_release(m);
+    const Geo &g = m.g;
+    const mm_params &p = m.p;
+    FarDesc &F = m.far;
+    F = FarDesc{};
+    F.order = p.far_order;
+    F.bt = p.far_block;
+    const long long bw = 64LL * F.bt, bh = 32LL * F.bt;
+    F.blocks_x = (g.ni + bw - 1) / bw;
+    F.blocks_y = (g.nj + bh - 1) / bh;
+    F.nblocks = F.blocks_x * F.blocks_y;
+    F.stride = (4 + 2 * (F.order - 1) + 3) & ~3;
+    // whole blocks as work items when there are enough of them to fill the GPU, else tile rows
+    const long long ctas = (long long)ctx->sms * far_ctas_per_sm();
+    F.rows_per_item = F.nblocks >= 4 * ctas ? F.bt : 1;
+    F.items = (unsigned long long)F.nblocks * (unsigned long long)(F.bt / F.rows_per_item);
+    F.item_begin = 0;
+    const double rho = g.delta * std::sqrt((double)(bw / 2) * (double)(bw / 2) + (double)(bh / 2) * (double)(bh / 2));
+    const double rn = rho / p.far_ratio;
+    F.rn2 = (float)(rn * rn);
+    F.rho = (float)rho;
+    const double dv = g.delta / rho;
+    F.dv_h = (float)dv;
+    F.dv_l = (float)(dv - (double)F.dv_h);
+    int rc;
+    if ((rc = ctx->arena.alloc(sizeof(unsigned), (void **)&m.far_bmax))) return rc;
+    MM_CUDA(cudaMemsetAsync(m.far_bmax, 0, sizeof(unsigned), s));
+    F.bound_max = m.far_bmax;
+    if (F.nblocks == 0) return MM_OK;
+    if ((rc = ctx->arena.alloc((size_t)F.nblocks * F.stride * sizeof(float), (void **)&m.far_coef)) ||
+        (rc = ctx->arena.alloc((size_t)(F.nblocks + 1) * sizeof(unsigned long long), (void **)&m.far_off)))
+        return rc;
+    MapDesc d;
+    fill_desc(m, &d);
+    const int grid = (int)std::max(1LL, std::min(F.nblocks, (long long)ctx->sms * 8));
+    MM_CUDA(launch_far_count(d, F, m.far_off, grid, s));
+    MM_CUDA(launch_far_scan(m.far_off, F.nblocks, s));
+    unsigned long long total = 0;
+    MM_CUDA(cudaMemcpyAsync(&total, m.far_off + F.nblocks, sizeof(total), cudaMemcpyDeviceToHost, s));
+    MM_CUDA(cudaStreamSynchronize(s));
+    if (total > (unsigned long long)INT32_MAX) return fail(MM_ENOMEM, "far field: near lists too long (lower far_block)");
+    if ((rc = ctx->arena.alloc(std::max<size_t>(1, (size_t)total) * sizeof(int), (void **)&m.far_idx))) return rc;
+    F.coef = m.far_coef;
+    F.near_off = m.far_off;
+    F.near_idx = m.far_idx;
+    MM_CUDA(launch_far_setup(d, F, m.far_coef, m.far_idx, grid, s));
+    return MM_OK;
+}
+
+}  // namespace mm

@@ -31,11 +31,6 @@ int cuda_fail(cudaError_t e, const char *what)
     return fail(MM_EDEVICE, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-#define MM_CUDA(call)                                     \
-    do {                                                  \
-        cudaError_t e_ = (call);                          \
-        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
-    } while (0)
 
 // ------------------------------------------------ seeded lens field (FP64) ---
 // SplitMix64 (Steele, Lea & Flood 2014): output k of a generator seeded with s
@@ -98,7 +93,14 @@ static bool finite(double v) { return std::isfinite(v); }
 int compute_geo(const mm_params *p, Geo *g)
 {
     if (!p || !g) return fail(MM_EINVAL, "null params");
-    if (p->precision != MM_FP32C && p->precision != MM_FP64) return fail(MM_EINVAL, "precision must be MM_FP32C or MM_FP64");
+    if (p->precision != MM_FP32C && p->precision != MM_FP64 && p->precision != MM_FAR32)
+        return fail(MM_EINVAL, "precision must be MM_FP32C, MM_FP64 or MM_FAR32");
+    if (p->precision == MM_FAR32) {
+        if (p->far_order < 1 || p->far_order > kFarMaxOrder) return fail(MM_EINVAL, "far_order must be in 1..32");
+        if (!finite(p->far_ratio) || !(p->far_ratio > 0.0) || p->far_ratio > 0.9)
+            return fail(MM_EINVAL, "far_ratio must be in (0, 0.9]");
+        if (p->far_block < 1 || p->far_block > kFarMaxBlock) return fail(MM_EINVAL, "far_block must be in 1..64");
+    }
     if (p->mass_model != MM_MASS_UNIT && p->mass_model != MM_MASS_LOGNORMAL) return fail(MM_EINVAL, "bad mass_model");
     if (!finite(p->sigma) || !finite(p->gamma) || p->sigma < 0.0) return fail(MM_EINVAL, "sigma must be finite and >= 0, gamma finite");
     if (!finite(p->side_re) || !(p->side_re > 0.0)) return fail(MM_EINVAL, "side_re must be > 0");
@@ -258,6 +260,7 @@ MapObj::~MapObj()
     }
     arena->free(partial);
     arena->free(seg_done);
+    far_release(*this);
 }
 
 void lens_split(const Geo &g, int precision, int *splits, long long *seg_lenses)
@@ -457,11 +460,17 @@ int scratch_reserve(mm_ctx *ctx, LaunchScratch *sc, int n_maps)
         const int cap = std::max(n_maps, std::max(64, 2 * sc->cap));
         if (sc->d_maps) cudaFree(sc->d_maps);
         if (sc->h_maps) cudaFreeHost(sc->h_maps);
+        if (sc->d_far) cudaFree(sc->d_far);
+        if (sc->h_far) cudaFreeHost(sc->h_far);
         sc->d_maps = nullptr;
         sc->h_maps = nullptr;
+        sc->d_far = nullptr;
+        sc->h_far = nullptr;
         sc->cap = 0;
         MM_CUDA(cudaMalloc(&sc->d_maps, (size_t)cap * sizeof(MapDesc)));
         MM_CUDA(cudaMallocHost(&sc->h_maps, (size_t)cap * sizeof(MapDesc)));
+        MM_CUDA(cudaMalloc(&sc->d_far, (size_t)cap * sizeof(FarDesc)));
+        MM_CUDA(cudaMallocHost(&sc->h_far, (size_t)cap * sizeof(FarDesc)));
         sc->cap = cap;
     }
     (void)ctx;
@@ -476,14 +485,18 @@ void scratch_free(mm_ctx *ctx, LaunchScratch *sc)
     if (sc->d_counter) cudaFree(sc->d_counter);
     if (sc->h_hdr) cudaFreeHost(sc->h_hdr);
     if (sc->h_maps) cudaFreeHost(sc->h_maps);
+    if (sc->d_far) cudaFree(sc->d_far);
+    if (sc->h_far) cudaFreeHost(sc->h_far);
     *sc = LaunchScratch{};
 }
 
 // Launch one precision group of maps as one persistent launch on stream s,
-// bracketed by ctx->ev0/ev1. Maps are ordered by decreasing per-tile cost.
-static int launch_group(mm_ctx *ctx, std::vector<MapObj *> &group, bool fp64, const DumpArgs *dump,
+// bracketed by ctx->ev0/ev1. Maps are ordered by decreasing per-tile cost. For
+// MM_FAR32 the bracket also holds each map's block preparation.
+static int launch_group(mm_ctx *ctx, std::vector<MapObj *> &group, int precision, const DumpArgs *dump,
                         unsigned long long dump_items, cudaStream_t s, float *ms)
 {
+    const bool fp64 = precision == MM_FP64, far = precision == MM_FAR32;
     if (group.empty()) return MM_OK;
     LaunchScratch *sc = &ctx->scratch;
     int rc = scratch_reserve(ctx, sc, (int)group.size());
@@ -514,14 +527,31 @@ static int launch_group(mm_ctx *ctx, std::vector<MapObj *> &group, bool fp64, co
     a.work_counter = sc->d_counter;
     if (dump) a.dump = *dump;
     const unsigned long long work = sc->h_hdr->total_work;
-    const long long cap = (long long)ctx->sms * shoot_ctas_per_sm(fp64, ctx->layout);
+    const long long cap =
+        (long long)ctx->sms * (far ? far_ctas_per_sm() : shoot_ctas_per_sm(fp64, ctx->layout));
     const int grid = (int)std::max(1LL, std::min((long long)work, cap));
     MM_CUDA(cudaEventRecord(ctx->ev0, s));
+    unsigned long long far_items = 0;
+    if (far) {
+        for (size_t k = 0; k < group.size(); ++k) {
+            if ((rc = far_prepare(ctx, *group[k], s))) return rc;
+            group[k]->far.item_begin = far_items;
+            far_items += group[k]->far.items;
+            sc->h_far[k] = group[k]->far;
+            ctx->last_launches += group[k]->far.nblocks > 0 ? 3 : 0;
+        }
+        MM_CUDA(cudaMemcpyAsync(sc->d_far, sc->h_far, group.size() * sizeof(FarDesc), cudaMemcpyHostToDevice, s));
+    }
     bool split = false;
     for (const MapObj *m : group) split = split || m->splits > 1;
-    if (work > 0)
-        MM_CUDA(fp64 ? launch_shoot_fp64(a, grid, dump != nullptr, s)
-                     : launch_shoot_fp32(a, ctx->layout, grid, dump != nullptr, split, s));
+    if (work > 0) {
+        if (far && !dump)
+            MM_CUDA(launch_shoot_far(a, sc->d_far, far_items, (int)std::max(1LL, std::min((long long)far_items, cap)),
+                                     false, s));
+        else if (far) MM_CUDA(launch_shoot_far(a, sc->d_far, 0, grid, true, s));
+        else if (fp64) MM_CUDA(launch_shoot_fp64(a, grid, dump != nullptr, s));
+        else MM_CUDA(launch_shoot_fp32(a, ctx->layout, grid, dump != nullptr, split, s));
+    }
     MM_CUDA(cudaEventRecord(ctx->ev1, s));
     MM_CUDA(cudaEventSynchronize(ctx->ev1));     // pinned scratch is reused by the next call
     float t = 0.f;
@@ -529,6 +559,15 @@ static int launch_group(mm_ctx *ctx, std::vector<MapObj *> &group, bool fp64, co
     *ms = t;
     ctx->last_ms = t;
     ctx->last_launches += work > 0 ? 1 : 0;
+    if (far) {
+        for (MapObj *m : group) {                 // the largest tail bound of the map's blocks
+            unsigned bits = 0;
+            MM_CUDA(cudaMemcpy(&bits, m->far_bmax, sizeof(bits), cudaMemcpyDeviceToHost));
+            float b;
+            std::memcpy(&b, &bits, sizeof(b));
+            m->far_bound = std::max(m->far_bound, (double)b);
+        }
+    }
     return MM_OK;
 }
 
@@ -658,6 +697,9 @@ int mm_params_default(mm_params *p)
     p->mass_s = 0.5;
     p->seed = 1;
     for (int k = 0; k < 4; ++k) p->ray_rect[k] = -1;
+    p->far_order = 16;
+    p->far_ratio = 0.3;
+    p->far_block = 8;
     return MM_OK;
 }
 
@@ -764,7 +806,7 @@ int mm_shoot(mm_ctx *ctx, mm_lenses lenses, const mm_params *p, mm_map *out)
     ctx->last_launches = 0;
     std::vector<MapObj *> group{M.get()};
     float ms = 0.f;
-    rc = launch_group(ctx, group, p->precision == MM_FP64, nullptr, 0, ctx->stream, &ms);
+    rc = launch_group(ctx, group, p->precision, nullptr, 0, ctx->stream, &ms);
     if (rc) return rc;
     MM_CUDA(cudaEventRecord(M->done, ctx->stream));
     M->seconds = ms * 1e-3;
@@ -783,17 +825,17 @@ int mm_shoot_batch(mm_ctx *ctx, int32_t n, const mm_lenses *lenses, const mm_par
         if (rc) return rc;
     }
     ctx->last_launches = 0;
-    std::vector<MapObj *> g32, g64;
-    for (auto &o : objs) (o->p.precision == MM_FP64 ? g64 : g32).push_back(o.get());
-    float ms32 = 0.f, ms64 = 0.f;
-    int rc = launch_group(ctx, g32, false, nullptr, 0, ctx->stream, &ms32);
-    if (rc) return rc;
-    rc = launch_group(ctx, g64, true, nullptr, 0, ctx->stream, &ms64);
-    if (rc) return rc;
-    ctx->last_ms = ms32 + ms64;
+    std::vector<MapObj *> groups[3];                  // by precision: MM_FP32C, MM_FP64, MM_FAR32
+    for (auto &o : objs) groups[o->p.precision].push_back(o.get());
+    float ms[3] = {0.f, 0.f, 0.f};
+    for (int k = 0; k < 3; ++k) {
+        int rc = launch_group(ctx, groups[k], k, nullptr, 0, ctx->stream, &ms[k]);
+        if (rc) return rc;
+    }
+    ctx->last_ms = ms[0] + ms[1] + ms[2];
     for (int k = 0; k < n; ++k) {
         auto &o = objs[(size_t)k];
-        o->seconds = (o->p.precision == MM_FP64 ? ms64 : ms32) * 1e-3;
+        o->seconds = ms[o->p.precision] * 1e-3;
         MM_CUDA(cudaEventRecord(o->done, ctx->stream));
         maps_out[k] = register_map(ctx, o);
     }
@@ -810,7 +852,9 @@ int mm_shoot_into(mm_ctx *ctx, mm_lenses lenses, const mm_params *p, mm_map map)
     const double margin_p = p->shoot_margin > 0 ? p->shoot_margin : 1.5, margin_q = q.shoot_margin > 0 ? q.shoot_margin : 1.5;
     if (p->sigma != q.sigma || p->gamma != q.gamma || p->smooth_frac != q.smooth_frac || p->side_re != q.side_re ||
         p->npix_side != q.npix_side || p->nrays_per_pix != q.nrays_per_pix || margin_p != margin_q ||
-        p->precision != q.precision)
+        p->precision != q.precision ||
+        (p->precision == MM_FAR32 &&
+         (p->far_order != q.far_order || p->far_ratio != q.far_ratio || p->far_block != q.far_block)))
         return fail(MM_EINVAL, "parameters differ from the map's (only ray_rect may change)");
     cudaSetDevice(ctx->device);
     std::shared_ptr<LensSet> L = T->lenses;
@@ -829,11 +873,12 @@ int mm_shoot_into(mm_ctx *ctx, mm_lenses lenses, const mm_params *p, mm_map map)
     ctx->last_launches = 0;
     std::vector<MapObj *> group{M.get()};
     float ms = 0.f;
-    rc = launch_group(ctx, group, p->precision == MM_FP64, nullptr, 0, ctx->stream, &ms);
+    rc = launch_group(ctx, group, p->precision, nullptr, 0, ctx->stream, &ms);
     if (rc) return rc;
     MM_CUDA(cudaEventRecord(T->done, ctx->stream));
     T->shot_total += M->shot_total;
     T->seconds += ms * 1e-3;
+    T->far_bound = std::max(T->far_bound, M->far_bound);
     return MM_OK;
 }
 
@@ -894,6 +939,7 @@ int mm_map_fetch(mm_ctx *ctx, mm_map map, uint32_t *host_counts, size_t n_elems,
         st->seconds = M->seconds;
         st->mu_mean = (double)tot[0] / ((double)npix * M->p.nrays_per_pix);
         st->lens_splits = M->splits;
+        st->far_bound = M->far_bound;
     }
     return MM_OK;
 }
@@ -989,7 +1035,7 @@ int mm_debug_deflect(mm_ctx *ctx, mm_lenses lenses, const mm_params *p, const in
     ctx->last_launches = 0;
     std::vector<MapObj *> group{M.get()};
     float ms = 0.f;
-    rc = launch_group(ctx, group, p->precision == MM_FP64, &d, items.size(), s, &ms);
+    rc = launch_group(ctx, group, p->precision, &d, items.size(), s, &ms);
     if (rc) return rc;
     if (alpha_out) MM_CUDA(cudaMemcpyAsync(alpha_out, d_alpha, (size_t)n * 16, cudaMemcpyDeviceToHost, s));
     if (pixel_out) MM_CUDA(cudaMemcpyAsync(pixel_out, d_pixel, (size_t)n * 8, cudaMemcpyDeviceToHost, s));

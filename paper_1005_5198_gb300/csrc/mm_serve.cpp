@@ -458,6 +458,7 @@ int mm_submit(mm_ctx *ctx, mm_lenses lenses, const mm_params *p, mm_req *out)
     auto r = std::make_shared<Request>();
     int rc = compute_geo(p, &r->g);
     if (rc) return rc;
+    if (p->precision == MM_FAR32) return fail(MM_EINVAL, "served maps are MM_FP32C or MM_FP64 (shoot MM_FAR32 with mm_shoot)");
     r->p = *p;
     if (lenses) {
         std::lock_guard<std::mutex> lk(ctx->mu);

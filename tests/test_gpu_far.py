@@ -1,0 +1,214 @@
+"""MM_FAR32, the far-field approximation (the tree code's idea on blocks of rays,
+Sect. 2.1, Eq. hierarchical), against the oracle's statement of the same
+approximation (oracle.far_rays / oracle.far_map), and against the exact method.
+
+The GPU and the oracle compute the same approximation, so they agree to FP32
+accuracy. Per ray the bar is |alpha_GPU - alpha_oracle| <= 1e-5 R_E, the exact
+path's target. Maps may differ only by rays whose source position lies within
+the FP32 error of a pixel edge, so the bar is 2e-4 of the rays. The tail bound
+the GPU reports is the oracle's, up to FP32 rounding."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1005_5198_gb300 as mm
+import synth
+from oracle import field
+
+pytestmark = pytest.mark.gpu
+
+CFG0 = dict(sigma=0.4, gamma=0.0, smooth_frac=0.0, side=4.0, npix_side=128, nrays=100.0)
+CFG1 = dict(sigma=0.4, gamma=0.0, smooth_frac=0.0, side=20.0, npix_side=1024, nrays=2000.0)
+CFG2 = dict(sigma=0.8, gamma=0.3, smooth_frac=0.5, side=40.0, npix_side=2048, nrays=500.0)
+FAR_DEFAULT = dict(order=16, ratio=0.3, block_tiles=8)
+ALPHA_TOL = 1e-5
+MISBIN = 2e-4
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    mm.build()
+    c = mm.mm_init(0)
+    yield c
+    mm.mm_destroy(c)
+
+
+def P(cfg, far, **kw):
+    d = dict(cfg, precision=mm.MM_FAR32, far_order=far["order"], far_ratio=far["ratio"],
+             far_block=far["block_tiles"])
+    d.update(kw)
+    return mm.params(**d)
+
+
+def ocfg(cfg):
+    return dict(cfg, margin=1.5)
+
+
+def field0():
+    return synth.lens_field(100, field.radius_for_nstar(100, 0.4), 1)
+
+
+def sample_rays(nx, ny, n, seed, rect=None):
+    rng = np.random.default_rng(seed)
+    i0, i1, j0, j1 = rect if rect is not None else (0, nx, 0, ny)
+    return rng.integers(i0, i1, n), rng.integers(j0, j1, n)
+
+
+def check_rays(ctx, lh, f, cfg, far, ii, jj, rect=None):
+    kw = {} if rect is None else dict(ray_rect=rect)
+    a_g, p_g = mm.mm_debug_deflect(ctx, lh, P(cfg, far, **kw), ii, jj)
+    origin = (0, 0) if rect is None else (rect[0], rect[2])
+    a_o, y_o, p_o, b_o = oracle.far_rays(ocfg(cfg), f, far, ii, jj, origin=origin)
+    err = np.hypot(*(a_g - a_o).T)
+    assert err.max() <= ALPHA_TOL, f"max |d alpha| = {err.max():.3g}"
+    # pixels differ only where the oracle's source position is within the error of an edge
+    bad = p_g != p_o
+    if bad.any():
+        pix = cfg["side"] / cfg["npix_side"]
+        u = (y_o[bad] + cfg["side"] / 2) / pix
+        edge = np.abs(u - np.round(u)).min(axis=1) * pix
+        assert np.all(edge <= 4 * err[bad] + 1e-9), "a pixel mismatch away from a pixel edge"
+    assert bad.mean() <= MISBIN
+    return err, b_o
+
+
+@pytest.mark.parametrize("far", [FAR_DEFAULT, dict(order=4, ratio=0.5, block_tiles=4),
+                                 dict(order=1, ratio=0.2, block_tiles=2), dict(order=32, ratio=0.6, block_tiles=16),
+                                 dict(order=9, ratio=0.45, block_tiles=3)],
+                         ids=["default", "P4", "P1", "P32", "P9-bt3"])
+def test_rays_match_the_oracle_config0(ctx, far):
+    f = field0()
+    lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
+    g = mm.mm_geometry_of(mm.params(**CFG0))
+    ii, jj = sample_rays(g["nx"], g["ny"], 20000, 1)
+    check_rays(ctx, lh, f, CFG0, far, ii, jj)
+    mm.mm_release_lenses(ctx, lh)
+
+
+def test_map_matches_the_oracle_and_the_bound_config0(ctx):
+    f = field0()
+    lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
+    for far in (FAR_DEFAULT, dict(order=6, ratio=0.5, block_tiles=4)):
+        m = mm.mm_shoot(ctx, lh, P(CFG0, far))
+        got, st = mm.mm_map_fetch(ctx, m)
+        mm.mm_release_map(ctx, m)
+        ref, tot, bmax = oracle.far_map(ocfg(CFG0), f, far)
+        assert st["rays_shot"] == tot["shot"] and st["rays_in"] + st["rays_out"] == st["rays_shot"]
+        assert int(got.sum()) == st["rays_in"]
+        assert int(np.abs(got.astype(np.int64) - ref).sum()) <= 2 * MISBIN * tot["shot"]
+        assert st["far_bound"] == pytest.approx(bmax, rel=2e-3)
+    mm.mm_release_lenses(ctx, lh)
+
+
+def test_every_lens_near_is_the_exact_method(ctx):
+    f = field0()
+    lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
+    far = dict(order=8, ratio=1e-6, block_tiles=8)             # rho / q covers the whole field
+    m = mm.mm_shoot(ctx, lh, P(CFG0, far))
+    got, st = mm.mm_map_fetch(ctx, m)
+    mm.mm_release_map(ctx, m)
+    ref, tot = oracle.shoot_map(ocfg(CFG0), f)                  # the exact method's oracle
+    assert st["far_bound"] == 0.0 and st["rays_shot"] == tot["shot"]
+    assert int(np.abs(got.astype(np.int64) - ref).sum()) <= 2 * MISBIN * tot["shot"]
+    mm.mm_release_lenses(ctx, lh)
+
+
+def test_ragged_window_with_lognormal_masses(ctx):
+    f = synth.lens_field(300, 12.0, 7, model=synth.MASS_LOGNORMAL)
+    lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
+    cfg = dict(sigma=0.55, gamma=0.2, smooth_frac=0.3, side=6.0, npix_side=96, nrays=60.0)
+    g = mm.mm_geometry_of(mm.params(**cfg))
+    rect = (37, min(g["nx"], 37 + 1000), 11, min(g["ny"], 11 + 700))      # blocks from (37, 11)
+    far = dict(order=12, ratio=0.4, block_tiles=2)
+    ii, jj = sample_rays(g["nx"], g["ny"], 8000, 2, rect)
+    check_rays(ctx, lh, f, cfg, far, ii, jj, rect=rect)
+    m = mm.mm_shoot(ctx, lh, P(cfg, far, ray_rect=rect))
+    got, st = mm.mm_map_fetch(ctx, m)
+    mm.mm_release_map(ctx, m)
+    ref, tot, _ = oracle.far_map(ocfg(cfg), f, far, rect=rect)
+    assert st["rays_shot"] == tot["shot"] == (rect[1] - rect[0]) * (rect[3] - rect[2])
+    assert int(np.abs(got.astype(np.int64) - ref).sum()) <= 2 * MISBIN * tot["shot"] + 2
+    mm.mm_release_lenses(ctx, lh)
+
+
+@pytest.mark.parametrize("cfg,seed,n", [(CFG1, 2, 6000), (CFG2, 3, 3000)], ids=["fig1", "config2"])
+def test_full_size_sampled_rays(ctx, cfg, seed, n):
+    """Full-size maps: rays sampled over the whole grid, launched as mm_shoot would."""
+    if cfg is CFG1:
+        nstar, radius = field.nstar_rule(0.4, 0.0, 0.0, 20.0)
+    else:
+        nstar, radius = 25000, 250.0
+    f = synth.lens_field(nstar, radius, seed)
+    lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
+    g = mm.mm_geometry_of(mm.params(**cfg))
+    ii, jj = sample_rays(g["nx"], g["ny"], n, seed)
+    err, bound = check_rays(ctx, lh, f, cfg, FAR_DEFAULT, ii, jj)
+    assert bound.max() < 1e-6                                  # the default is exact to FP32 accuracy
+    mm.mm_release_lenses(ctx, lh)
+
+
+def test_far_map_against_the_exact_gpu_map_fig1_window(ctx):
+    """The default far field reproduces the exact FP32 map: same counts but for edge rays."""
+    nstar, radius = field.nstar_rule(0.4, 0.0, 0.0, 20.0)
+    f = synth.lens_field(nstar, radius, 2)
+    lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
+    g = mm.mm_geometry_of(mm.params(**CFG1))
+    c = g["nx"] // 2
+    rect = (c - 4096, c + 4096, c - 4096, c + 4096)
+    m_far = mm.mm_shoot(ctx, lh, P(CFG1, FAR_DEFAULT, ray_rect=rect))
+    m_ex = mm.mm_shoot(ctx, lh, mm.params(**CFG1, ray_rect=rect))
+    far, st_f = mm.mm_map_fetch(ctx, m_far)
+    ex, st_e = mm.mm_map_fetch(ctx, m_ex)
+    cmp = mm.mm_map_compare(ctx, m_far, m_ex)
+    assert st_f["rays_shot"] == st_e["rays_shot"]
+    assert int(np.abs(far.astype(np.int64) - ex).sum()) <= 2 * MISBIN * st_f["rays_shot"]
+    assert cmp["rms_dm"] < 0.01 and cmp["ks_p"] > 0.99          # far below the shot noise 1.09 / sqrt(N)
+    for m in (m_far, m_ex):
+        mm.mm_release_map(ctx, m)
+    mm.mm_release_lenses(ctx, lh)
+
+
+def test_block_aligned_parts_equal_one_shot(ctx):
+    cfg = dict(CFG0, precision=mm.MM_FAR32)
+    g = mm.mm_geometry_of(mm.params(**CFG0))
+    whole = mm.mm_shoot(ctx, 0, P(CFG0, FAR_DEFAULT))
+    w_counts, w_st = mm.mm_map_fetch(ctx, whole)
+    mm.mm_release_map(ctx, whole)
+    m = mm.mm_shoot(ctx, 0, P(CFG0, FAR_DEFAULT, ray_rect=(0, 0, 0, 0)))
+    bw, bh = 64 * 8, 32 * 8
+    for (i0, i1) in ((0, 2 * bw), (2 * bw, g["nx"])):
+        for (j0, j1) in ((0, 5 * bh), (5 * bh, g["ny"])):
+            mm.mm_shoot_into(ctx, 0, P(CFG0, FAR_DEFAULT, ray_rect=(i0, i1, j0, j1)), m)
+    got, st = mm.mm_map_fetch(ctx, m)
+    mm.mm_release_map(ctx, m)
+    assert np.array_equal(got, w_counts) and st["rays_shot"] == w_st["rays_shot"]
+    assert st["far_bound"] == pytest.approx(w_st["far_bound"], rel=1e-6)
+    assert cfg["precision"] == mm.MM_FAR32
+
+
+def test_far_parameters_validated_and_not_served(ctx):
+    for bad in (dict(far_order=0), dict(far_order=33), dict(far_ratio=0.0), dict(far_ratio=0.95),
+                dict(far_block=0), dict(far_block=65)):
+        p = P(CFG0, FAR_DEFAULT)
+        for k, v in bad.items():
+            setattr(p, k, v)
+        with pytest.raises(mm.MMError) as e:
+            mm.mm_shoot(ctx, 0, p)
+        assert e.value.code == mm.MM_EINVAL
+    with pytest.raises(mm.MMError) as e:
+        mm.mm_submit(ctx, 0, P(CFG0, FAR_DEFAULT))
+    assert e.value.code == mm.MM_EINVAL
+
+
+def test_batch_mixes_precisions(ctx):
+    f = field0()
+    lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
+    plist = [mm.params(**CFG0), P(CFG0, FAR_DEFAULT), mm.params(**CFG0, precision=mm.MM_FP64)]
+    maps = mm.mm_shoot_batch(ctx, [lh] * 3, plist)
+    ref, tot = oracle.shoot_map(ocfg(CFG0), f)
+    for m in maps:
+        got, st = mm.mm_map_fetch(ctx, m)
+        assert st["rays_shot"] == tot["shot"]
+        assert int(np.abs(got.astype(np.int64) - ref).sum()) <= 2 * MISBIN * tot["shot"]
+        mm.mm_release_map(ctx, m)
+    mm.mm_release_lenses(ctx, lh)
