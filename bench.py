@@ -215,6 +215,47 @@ def serve_phase(mm, ctx, rate_hz, seconds, seed, large_every=10):
 KERNEL_SOURCES = ["mm_fp32.cuh", "mm_device.cuh", "mm_internal.h", "mm_fp32_c2r4.cu"]
 
 
+def far_phase(mm, ctx, lh_fig1, exact_ms):
+    """The far-field approximation MM_FAR32 (the tree code's idea, Sect. 2.1; default order 16,
+    ratio 0.3, 8 x 8-tile blocks), timed outside the headline region: the Fig. 1 map against the
+    exact FP32 map of the same lenses, and the sigma = 0.8, N* = 25000 map (600 x 120 R_E shot
+    region, 9.4e10 rays), whose exact shoot would take interactions / (the headline rate)."""
+    import synth
+    out = {"params": {"far_order": 16, "far_ratio": 0.3, "far_block": 8},
+           "timing": "CUDA events around block preparation + shoot (mm_last_kernel_ms), best of 3"}
+    m = mm.mm_shoot(ctx, lh_fig1, mm.params(**CFG1))
+    ex, st_ex = mm.mm_map_fetch(ctx, m)
+    ex = ex.copy()
+    mm.mm_release_map(ctx, m)
+    times = []
+    for _ in range(3):
+        m = mm.mm_shoot(ctx, lh_fig1, mm.params(**CFG1, precision=mm.MM_FAR32))
+        times.append(mm.mm_last_kernel_ms(ctx)[0])
+        far, st = mm.mm_map_fetch(ctx, m)
+        mm.mm_release_map(ctx, m)
+    t = min(times)
+    out["fig1"] = {"ms": t, "equivalent_interactions_per_s": st["interactions"] / (t * 1e-3),
+                   "speedup_vs_exact": exact_ms / t, "far_bound_re": st["far_bound"],
+                   "rays_moved_vs_exact_fraction": float(np.abs(far.astype(np.int64) - ex).sum()) / 2 / st["rays_shot"]}
+    f2 = synth.lens_field(25000, 250.0, 3)
+    lh2 = mm.mm_create_lenses_from(ctx, f2.x, f2.y, f2.m)
+    cfg2 = dict(sigma=0.8, gamma=0.3, smooth_frac=0.5, side=40.0, npix_side=2048, nrays=500.0)
+    times = []
+    for _ in range(2):
+        m = mm.mm_shoot(ctx, lh2, mm.params(**cfg2, precision=mm.MM_FAR32))
+        times.append(mm.mm_last_kernel_ms(ctx)[0])
+        _, st2 = mm.mm_map_fetch(ctx, m, want_counts=False)
+        mm.mm_release_map(ctx, m)
+    mm.mm_release_lenses(ctx, lh2)
+    t2 = min(times)
+    exact_rate = st_ex["interactions"] / (exact_ms * 1e-3)
+    out["sigma08_nstar25000"] = {"ms": t2, "rays": st2["rays_shot"],
+                                 "equivalent_interactions_per_s": st2["interactions"] / (t2 * 1e-3),
+                                 "exact_estimated_s": st2["interactions"] / exact_rate,
+                                 "far_bound_re": st2["far_bound"]}
+    return out
+
+
 def kernel_sha256():
     import hashlib
     h = hashlib.sha256()
@@ -336,7 +377,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the batch and serving phases")
+    ap.add_argument("--no-extras", action="store_true", help="skip the far-field, batch and serving phases")
     ap.add_argument("--profile-case", nargs="?", const="fp32", choices=["fp32", "far"],
                     help="shoot a 4096^2-ray window of the Fig. 1 map three times, exactly (fp32) or with the "
                          "far-field approximation MM_FAR32 (far), for ncu captures, and exit")
@@ -438,6 +479,7 @@ def main():
     # ---- batched persistent launch and served stream (scaled config-3 / config-4 shapes) ----
     extra = {}
     if not args.no_extras and world == 1:
+        extra["far_field"] = far_phase(mm, ctx, lh, sum(kern_ms) / len(kern_ms))
         extra["batch"] = batch_phase(mm, ctx)
         mm.mm_serve_config(ctx, max_active=64, wave_ms=25.0)
         capacity = extra["batch"]["batched_interactions_per_s"]          # the same mix shape, batched

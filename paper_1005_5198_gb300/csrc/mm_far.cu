@@ -377,19 +377,13 @@ __device__ void far_tile(const LaunchArgs &A, const FarDesc &F, const MapDesc &M
                 SI[q] = ni;
             }
         }
-        // float-float sums S = -alpha: the far part is -conj(c'_0 + s) = (-Re, +Im)
-        const float c0rh = S.coef[0], c0rl = S.coef[1], c0ih = S.coef[2], c0il = S.coef[3];
+        // float-float sums of S = -alpha without c'_0 (folded into the pixel bases below):
+        // the series remainder contributes -conj(s) = (-Re s, +Im s)
 #pragma unroll
         for (int r = 0; r < K; ++r) {
             const float sr = (r & 1) ? SR[r >> 1].y : SR[r >> 1].x;
             const float si = (r & 1) ? SI[r >> 1].y : SI[r >> 1].x;
-            float s, e;
-            two_sum(-c0rh, -sr, s, e);
-            acc[r].x = s;
-            acc[r].y = __fadd_rn(-c0rl, e);
-            two_sum(c0ih, si, s, e);
-            acc[r].z = s;
-            acc[r].w = __fadd_rn(c0il, e);
+            acc[r] = make_float4(-sr, 0.f, si, 0.f);
         }
     }
 
@@ -469,17 +463,37 @@ __device__ void far_tile(const LaunchArgs &A, const FarDesc &F, const MapDesc &M
     }
 
     // ---- lens equation and pixel (float-float), as in the exact FP32 kernel ----
+    // u = A (2i + 1 - n) + N/2 + S / p with S = -alpha; the block's c'_0 part of S/p
+    // is the same for all its rays and enters the bases kx = N/2 - Re c'_0 / p,
+    // ky = N/2 + Im c'_0 / p (float-float).
+    const float c0rh = S.coef[0], c0rl = S.coef[1], c0ih = S.coef[2], c0il = S.coef[3];
+    float kxh, kxl, kyh, kyl;
+    {
+        float ph = __fmul_rn(c0rh, M.ip_h);
+        float pe = __fmaf_rn(c0rh, M.ip_h, -ph);
+        pe = __fmaf_rn(c0rh, M.ip_l, __fmaf_rn(c0rl, M.ip_h, pe));
+        float e;
+        two_sum(M.half_n, -ph, kxh, e);
+        kxl = __fsub_rn(e, pe);
+        ph = __fmul_rn(c0ih, M.ip_h);
+        pe = __fmaf_rn(c0ih, M.ip_h, -ph);
+        pe = __fmaf_rn(c0ih, M.ip_l, __fmaf_rn(c0il, M.ip_h, pe));
+        two_sum(M.half_n, ph, kyh, e);
+        kyl = __fadd_rn(e, pe);
+    }
     const float nsf = (float)M.nside;
     const long long gi = ib + iloc;
     float uxh, uxl;
-    ff_axis(M.ax_h, M.ax_l, (float)(int)(2 * gi + 1 - M.nx), M.half_n, uxh, uxl);
+    ff_axis(M.ax_h, M.ax_l, (float)(int)(2 * gi + 1 - M.nx), kxh, uxh, uxl);
+    uxl = __fadd_rn(uxl, kxl);
     const bool col_ok = gi < M.i0 + M.ni;
     const float ay0 = (float)(int)(2 * (jb + jloc0) + 1 - M.ny);     // |2 j + 1 - ny| < 2^23: exact steps
 #pragma unroll
     for (int r = 0; r < K; ++r) {
         const long long gj = jb + jloc0 + r;
         float uyh, uyl;
-        ff_axis(M.ay_h, M.ay_l, ay0 + (float)(2 * r), M.half_n, uyh, uyl);
+        ff_axis(M.ay_h, M.ay_l, ay0 + (float)(2 * r), kyh, uyh, uyl);
+        uyl = __fadd_rn(uyl, kyl);
         const float4 a = acc[r];
         const float I1 = ff_pixel(uxh, uxl, a.x, a.y, M.ip_h, M.ip_l);
         const float I2 = ff_pixel(uyh, uyl, a.z, a.w, M.ip_h, M.ip_l);
@@ -487,9 +501,10 @@ __device__ void far_tile(const LaunchArgs &A, const FarDesc &F, const MapDesc &M
         const bool inside =
             valid && !((onlens >> r) & 1u) && I1 >= 0.f && I1 < nsf && I2 >= 0.f && I2 < nsf;
         const unsigned pix = inside ? (unsigned)I2 * (unsigned)M.nside + (unsigned)I1 : 0xffffffffu;
-        if (DUMP)
-            emit_ray<true>(A, M, item, iloc + kTileX * (jloc0 + r), valid, inside, pix, -((double)a.x + (double)a.y),
-                           -((double)a.z + (double)a.w), cnt_in, cnt_out);
+        if (DUMP)                                             // alpha = conj(c'_0) - S
+            emit_ray<true>(A, M, item, iloc + kTileX * (jloc0 + r), valid, inside, pix,
+                           ((double)c0rh + (double)c0rl) - ((double)a.x + (double)a.y),
+                           -((double)c0ih + (double)c0il) - ((double)a.z + (double)a.w), cnt_in, cnt_out);
         else
             far_bin(M, valid, inside, pix, cnt_in, cnt_out);
     }
