@@ -131,12 +131,17 @@ def test_cfg0_fp64_matches_oracle(ctx):
     assert np.sum(p_g != p_o) <= 1
 
 
-def test_fp32_map_is_deterministic(ctx):
+def test_maps_are_deterministic(ctx):
+    """Counts are integer atomics and every float sum has a fixed order, so repeated runs give
+    the same map bit for bit: ten runs of the FP32 path, three of FP64 and of the far field."""
     f = field0()
     lh = lens(ctx, f)
-    a, _ = shoot(ctx, lh, CFG0)
-    b, _ = shoot(ctx, lh, CFG0)
-    np.testing.assert_array_equal(a, b)
+    for kw, runs in ((dict(), 10), (dict(precision=mm.MM_FP64), 3), (dict(precision=mm.MM_FAR32), 3)):
+        first, st0 = shoot(ctx, lh, CFG0, **kw)
+        for _ in range(runs - 1):
+            again, st = shoot(ctx, lh, CFG0, **kw)
+            np.testing.assert_array_equal(first, again)
+            assert (st["rays_in"], st["rays_out"]) == (st0["rays_in"], st0["rays_out"])
 
 
 # ----------------------------------------------------------------- config 1 ---
