@@ -212,3 +212,39 @@ def test_batch_mixes_precisions(ctx):
         assert int(np.abs(got.astype(np.int64) - ref).sum()) <= 2 * MISBIN * tot["shot"]
         mm.mm_release_map(ctx, m)
     mm.mm_release_lenses(ctx, lh)
+
+
+def test_near_lists_longer_than_the_staging_buffer(ctx):
+    """1500 lenses all near (ratio 1e-6): every block's near list spans three shared-memory
+    chunks (512 lenses each), re-staged tile by tile; the result is the exact method's."""
+    f = synth.lens_field(1500, 12.0, 11)
+    lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
+    cfg = dict(sigma=0.4, gamma=0.1, smooth_frac=0.0, side=3.0, npix_side=64, nrays=40.0)
+    far = dict(order=4, ratio=1e-6, block_tiles=2)
+    g = mm.mm_geometry_of(mm.params(**cfg))
+    ii, jj = sample_rays(g["nx"], g["ny"], 6000, 4)
+    check_rays(ctx, lh, f, cfg, far, ii, jj)
+    a_exact, _, _ = oracle.shoot_rays(ocfg(cfg), f, ii, jj)
+    a_far, _ = mm.mm_debug_deflect(ctx, lh, P(cfg, far), ii, jj)
+    assert np.hypot(*(a_far - a_exact).T).max() <= ALPHA_TOL
+    m = mm.mm_shoot(ctx, lh, P(cfg, far))
+    got, st = mm.mm_map_fetch(ctx, m)
+    mm.mm_release_map(ctx, m)
+    ref, tot = oracle.shoot_map(ocfg(cfg), f)
+    assert st["far_bound"] == 0.0 and st["rays_shot"] == tot["shot"]
+    assert int(np.abs(got.astype(np.int64) - ref).sum()) <= 2 * MISBIN * tot["shot"]
+    mm.mm_release_lenses(ctx, lh)
+
+
+def test_no_lenses_gives_the_smooth_closed_form(ctx):
+    """N* = 0: only the smooth convergence and shear; every ray lands as for Eq. mutheory."""
+    cfg = dict(sigma=0.3, gamma=0.2, smooth_frac=1.0, side=2.0, npix_side=32, nrays=25.0)
+    empty = synth.lens_field(0, 1.0, 1)
+    lh = mm.mm_create_lenses_from(ctx, empty.x, empty.y, empty.m)
+    m = mm.mm_shoot(ctx, lh, P(cfg, FAR_DEFAULT))
+    got, st = mm.mm_map_fetch(ctx, m)
+    mm.mm_release_map(ctx, m)
+    ref, tot = oracle.shoot_map(ocfg(cfg), empty)
+    np.testing.assert_array_equal(got, ref)
+    assert st["far_bound"] == 0.0 and st["rays_in"] == tot["inside"]
+    mm.mm_release_lenses(ctx, lh)
