@@ -219,8 +219,8 @@ int mm_shoot_batch(mm_ctx *ctx, int32_t n, const mm_lenses *lenses, const mm_par
 int mm_shoot_into(mm_ctx *ctx, mm_lenses lenses, const mm_params *p, mm_map map);
 
 /* Recreate a map from a checkpoint: host_counts[n_elems] and *st as
- * mm_map_fetch returned them (rays_shot, rays_in, rays_out, nx, ny, nstar and
- * seconds are read). p must hold the map's parameters (ray_rect is ignored);
+ * mm_map_fetch returned them (rays_shot, rays_in, rays_out, nx, ny, nstar,
+ * seconds and far_bound are read). p must hold the map's parameters (ray_rect is ignored);
  * lenses (0: generated from p, as mm_shoot does) must have st->nstar lenses.
  * The new map continues with mm_shoot_into; the rays already shot are the
  * caller's record. Copies the host data before it returns. Errors: MM_EINVAL

@@ -909,6 +909,7 @@ int mm_map_restore(mm_ctx *ctx, mm_lenses lenses, const mm_params *p, const uint
     MM_CUDA(cudaStreamSynchronize(ctx->stream));        // host buffers may go as soon as this returns
     M->shot_total = st->rays_shot;
     M->seconds = st->seconds;
+    M->far_bound = st->far_bound;
     *out = register_map(ctx, M);
     return MM_OK;
 }

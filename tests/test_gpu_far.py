@@ -183,6 +183,9 @@ def test_block_aligned_parts_equal_one_shot(ctx):
     mm.mm_release_map(ctx, m)
     assert np.array_equal(got, w_counts) and st["rays_shot"] == w_st["rays_shot"]
     assert st["far_bound"] == pytest.approx(w_st["far_bound"], rel=1e-6)
+    m2 = mm.mm_map_restore(ctx, 0, P(CFG0, FAR_DEFAULT), got, st)       # a checkpoint keeps the bound
+    assert mm.mm_map_fetch(ctx, m2, want_counts=False)[1]["far_bound"] == st["far_bound"]
+    mm.mm_release_map(ctx, m2)
     assert cfg["precision"] == mm.MM_FAR32
 
 
