@@ -148,7 +148,8 @@ __global__ void __launch_bounds__(1024) k_far_scan(unsigned long long *a, long l
     if (threadIdx.x == 0) a[n] = carry;
 }
 
-// Per block: ordered near list, series coefficients and tail bound. PMAX >= F.order.
+// One CTA per block: the series coefficients of its far lenses and its tail bound at
+// |w| = rho (the near lenses are k_far_fill's). PMAX >= F.order.
 template <int PMAX, bool MASS>
 __global__ void __launch_bounds__(kFarThreads) k_far_setup(const MapDesc M, const FarDesc F, float *coef)
 {
