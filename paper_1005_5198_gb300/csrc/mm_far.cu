@@ -259,6 +259,7 @@ __global__ void __launch_bounds__(kFarThreads) k_far_setup(const MapDesc M, cons
 }
 
 constexpr int kNearCap = 512;                 // near lenses staged at once per item
+constexpr int kNearFold = 32;                 // near terms summed in FP32 between float-float folds
 
 struct __align__(16) SmemFar {
     float4 nl[kNearCap];                      // near lens offset from the block centre, float-float (xh, xl, yh, yl)
@@ -415,51 +416,54 @@ __device__ void far_tile(const LaunchArgs &A, const FarDesc &F, const MapDesc &M
                 __syncthreads();
             }
             const int cnt = (int)min((long long)kNearCap, n_near - c0);
-            for (int j = 0; j < cnt; ++j) {
-                const float4 L = S.nl[j];
-                const float lx = __fadd_rn(__fsub_rn(L.x, txh), __fsub_rn(L.y, txl));   // from the tile centre
-                const float ly = __fadd_rn(__fsub_rn(L.z, tyh), __fsub_rn(L.w, tyl));
-                if (fabsf(lx) < hx && fabsf(ly) < hy) {       // within kNearRadius of the tile: FP64
-                    const int g = S.ng[j];
-                    const double xl = M.lx[g], yl = M.ly[g];
-                    const double ml = MASS ? M.lm[g] : 1.0;
-                    const double x1 = ((double)(ib + iloc) + 0.5 - M.half_nx) * M.delta;
+            for (int j0 = 0; j0 < cnt; j0 += kNearFold) {
+                for (int j = j0; j < min(cnt, j0 + kNearFold); ++j) {
+                    const float4 L = S.nl[j];
+                    const float lx = __fadd_rn(__fsub_rn(L.x, txh), __fsub_rn(L.y, txl));   // from the tile centre
+                    const float ly = __fadd_rn(__fsub_rn(L.z, tyh), __fsub_rn(L.w, tyl));
+                    if (fabsf(lx) < hx && fabsf(ly) < hy) {   // within kNearRadius of the tile: FP64
+                        const int g = S.ng[j];
+                        const double xl = M.lx[g], yl = M.ly[g];
+                        const double ml = MASS ? M.lm[g] : 1.0;
+                        const double x1 = ((double)(ib + iloc) + 0.5 - M.half_nx) * M.delta;
+#pragma unroll
+                        for (int r = 0; r < K; ++r) {
+                            const double x2 = ((double)(jb + jloc0 + r) + 0.5 - M.half_ny) * M.delta;
+                            const double d1 = xl - x1, d2 = yl - x2;
+                            const double r2 = d1 * d1 + d2 * d2;
+                            if (r2 == 0.0) {
+                                onlens |= 1u << r;
+                            } else {
+                                const double t = ml / r2;
+                                add_ff(acc[r].x, acc[r].y, t * d1);
+                                add_ff(acc[r].z, acc[r].w, t * d2);
+                            }
+                        }
+                        continue;
+                    }
+                    const float m = MASS ? S.nm[j] : 1.f;
+                    const float dX = lx - rx;
+                    const float dX2 = dX * dX;
 #pragma unroll
                     for (int r = 0; r < K; ++r) {
-                        const double x2 = ((double)(jb + jloc0 + r) + 0.5 - M.half_ny) * M.delta;
-                        const double d1 = xl - x1, d2 = yl - x2;
-                        const double r2 = d1 * d1 + d2 * d2;
-                        if (r2 == 0.0) {
-                            onlens |= 1u << r;
-                        } else {
-                            const double t = ml / r2;
-                            add_ff(acc[r].x, acc[r].y, t * d1);
-                            add_ff(acc[r].z, acc[r].w, t * d2);
-                        }
+                        const float dY = ly - ry[r];
+                        const float t = m * rcp_approx(fmaf(dY, dY, dX2));
+                        nxs[r] = fmaf(t, dX, nxs[r]);
+                        nys[r] = fmaf(t, dY, nys[r]);
                     }
-                    continue;
                 }
-                const float m = MASS ? S.nm[j] : 1.f;
-                const float dX = lx - rx;
-                const float dX2 = dX * dX;
 #pragma unroll
-                for (int r = 0; r < K; ++r) {
-                    const float dY = ly - ry[r];
-                    const float t = m * rcp_approx(fmaf(dY, dY, dX2));
-                    nxs[r] = fmaf(t, dX, nxs[r]);
-                    nys[r] = fmaf(t, dY, nys[r]);
+                for (int r = 0; r < K; ++r) {                 // compensated fold every kNearFold lenses
+                    float s, e;
+                    two_sum(acc[r].x, nxs[r], s, e);
+                    acc[r].x = s;
+                    acc[r].y = __fadd_rn(acc[r].y, e);
+                    two_sum(acc[r].z, nys[r], s, e);
+                    acc[r].z = s;
+                    acc[r].w = __fadd_rn(acc[r].w, e);
+                    nxs[r] = nys[r] = 0.f;
                 }
             }
-        }
-#pragma unroll
-        for (int r = 0; r < K; ++r) {
-            float s, e;
-            two_sum(acc[r].x, nxs[r], s, e);
-            acc[r].x = s;
-            acc[r].y = __fadd_rn(acc[r].y, e);
-            two_sum(acc[r].z, nys[r], s, e);
-            acc[r].z = s;
-            acc[r].w = __fadd_rn(acc[r].w, e);
         }
     }
 

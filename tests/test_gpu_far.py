@@ -239,15 +239,20 @@ def test_near_lists_longer_than_the_staging_buffer(ctx):
     mm.mm_release_lenses(ctx, lh)
 
 
-def test_no_lenses_gives_the_smooth_closed_form(ctx):
-    """N* = 0: only the smooth convergence and shear; every ray lands as for Eq. mutheory."""
-    cfg = dict(sigma=0.3, gamma=0.2, smooth_frac=1.0, side=2.0, npix_side=32, nrays=25.0)
+def test_no_lenses_gives_the_smooth_map_exactly(ctx):
+    """N* = 0: only the smooth convergence and shear. The far path's lens equation is the exact
+    FP32 path's, so both give the oracle's integer map (parameters without rays on pixel edges)."""
+    cfg = dict(sigma=0.53, gamma=0.1, smooth_frac=1.0, side=2.0, npix_side=16, nrays=121.0)
     empty = synth.lens_field(0, 1.0, 1)
     lh = mm.mm_create_lenses_from(ctx, empty.x, empty.y, empty.m)
-    m = mm.mm_shoot(ctx, lh, P(cfg, FAR_DEFAULT))
-    got, st = mm.mm_map_fetch(ctx, m)
-    mm.mm_release_map(ctx, m)
+    maps = []
+    for p in (P(cfg, FAR_DEFAULT), mm.params(**cfg)):
+        m = mm.mm_shoot(ctx, lh, p)
+        got, st = mm.mm_map_fetch(ctx, m)
+        mm.mm_release_map(ctx, m)
+        maps.append((got, st))
     ref, tot = oracle.shoot_map(ocfg(cfg), empty)
-    np.testing.assert_array_equal(got, ref)
-    assert st["far_bound"] == 0.0 and st["rays_in"] == tot["inside"]
+    np.testing.assert_array_equal(maps[0][0], ref)
+    np.testing.assert_array_equal(maps[0][0], maps[1][0])
+    assert maps[0][1]["far_bound"] == 0.0 and maps[0][1]["rays_in"] == tot["inside"]
     mm.mm_release_lenses(ctx, lh)
