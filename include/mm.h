@@ -269,8 +269,11 @@ int mm_cancel(mm_ctx *ctx, mm_req req);
 /* Latency of a finished request: submit -> admit -> done, seconds (host clock). */
 int mm_req_times(mm_ctx *ctx, mm_req req, double *t_queue, double *t_total);
 
-/* Serving limits: max concurrently admitted maps, max queued requests, and the
- * target device time of one wave in milliseconds (0 keeps the current value). */
+/* Serving limits: max concurrently admitted maps (default 64), max queued
+ * requests (65536), and the target device time of one wave in milliseconds
+ * (default 12; 0 keeps the current value of any argument). A request completes
+ * about two waves after it joins one, so the wave length sets the latency floor;
+ * waves below ~8 ms lose throughput to launch overhead. */
 int mm_serve_config(mm_ctx *ctx, int32_t max_active, int32_t max_queued, double wave_ms);
 
 /* ---- map statistics (Sect. 3.1, Eq. deltam) --------------------------------

@@ -79,7 +79,7 @@ struct Server {
     size_t reserved_bytes = 0;                       // footprint of requests being prepared
     std::unordered_map<uint64_t, std::shared_ptr<Request>> reqs;
     int max_active = 64, max_queued = 1 << 16;
-    double wave_ms = 8.0;
+    double wave_ms = 12.0;             // shorter waves cut latency, below ~8 ms the launch overhead shows
     cudaStream_t stream[2] = {nullptr, nullptr};     // waves alternate, so one fills the other's tail
     cudaStream_t capture = nullptr;
     cudaStream_t upload[kAdmitWorkers] = {};
