@@ -15,7 +15,25 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .buildlib import LIB, build, up_to_date  # noqa: F401
+from .buildlib import CHECKED_LIB, LIB, up_to_date  # noqa: F401
+from .buildlib import build as _build_lib
+
+_checked = False
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile libmm.so (the checked variant after use_checked_build()) if it is out of date."""
+    return _build_lib(force=force, verbose=verbose, checked=_checked)
+
+
+def use_checked_build() -> None:
+    """Load the checked build (every guarded device access tests its index; a failure is reported
+    as MM_EDEVICE "bounds check failed"). Call before the first use of the library."""
+    global LIB, _checked
+    if _lib is not None:
+        raise RuntimeError("the library is already loaded")
+    _checked = True
+    LIB = _build_lib(checked=True)
 
 MM_OK, MM_EINVAL, MM_ENOMEM, MM_EBUSY, MM_ENOTFOUND = 0, -1, -2, -3, -4
 MM_ETIMEDOUT, MM_EDEVICE, MM_EAGAIN, MM_ECANCELED = -5, -6, -7, -8

@@ -34,33 +34,45 @@ def _inputs():
     return files
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB) or not os.path.exists(ALU_RATES):
+# Checked build (-DMM_CHECKS): every guarded device access tests its index and a
+# failure comes back as MM_EDEVICE instead of a fault; for debugging, not timing.
+CHECKED_BUILD = os.path.join(BUILD, "checked")
+CHECKED_LIB = os.path.join(CHECKED_BUILD, "libmm.so")
+
+
+def up_to_date(checked: bool = False) -> bool:
+    outs = [CHECKED_LIB] if checked else [LIB, ALU_RATES]
+    if not all(os.path.exists(o) for o in outs):
         return False
-    t = min(os.path.getmtime(LIB), os.path.getmtime(ALU_RATES))
+    t = min(os.path.getmtime(o) for o in outs)
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    lib_path = CHECKED_LIB if checked else LIB
+    if not force and up_to_date(checked):
+        return lib_path
+    out_dir = CHECKED_BUILD if checked else BUILD
+    os.makedirs(out_dir, exist_ok=True)
+    defs = ["-DMM_CHECKS"] if checked else []
     jobs, objs = [], []
     for f in CU_SOURCES:
-        o = os.path.join(BUILD, f + ".o")
-        cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
+        o = os.path.join(out_dir, f + ".o")
+        cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v", *defs,
                "-I", os.path.join(ROOT, "include"), "-c", os.path.join(CSRC, f), "-o", o]
         jobs.append((f, cmd))
         objs.append(o)
     for f in CPP_SOURCES:
-        o = os.path.join(BUILD, f + ".o")
-        cmd = ["g++", "-std=c++17", "-O2", "-fPIC", "-ffp-contract=off", "-Wall", "-Wextra",
+        o = os.path.join(out_dir, f + ".o")
+        cmd = ["g++", "-std=c++17", "-O2", "-fPIC", "-ffp-contract=off", "-Wall", "-Wextra", *defs,
                "-I", os.path.join(CUDA_HOME, "include"), "-I", os.path.join(ROOT, "include"),
                "-c", os.path.join(CSRC, f), "-o", o]
         jobs.append((f, cmd))
         objs.append(o)
     alu_tmp = ALU_RATES + f".{os.getpid()}.tmp"
-    jobs.append(("alu_rates.cu", [NVCC, *ARCH, "-O3", "-std=c++17", os.path.join(CSRC, "alu_rates.cu"), "-o", alu_tmp]))
+    if not checked:
+        jobs.append(("alu_rates.cu", [NVCC, *ARCH, "-O3", "-std=c++17", os.path.join(CSRC, "alu_rates.cu"), "-o",
+                                      alu_tmp]))
     procs = [(f, subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)) for f, c in jobs]
     logs = []
     for f, p in procs:
@@ -68,21 +80,22 @@ def build(force: bool = False, verbose: bool = False) -> str:
         logs.append((f, out))
         if p.returncode != 0:
             raise RuntimeError(f"compiling {f} failed:\n{out}")
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib_path + f".{os.getpid()}.tmp"
     link = [NVCC, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lpthread", "-ldl", "-lrt"]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"linking libmm.so failed:\n{r.stdout}")
-    os.replace(tmp, LIB)
-    os.replace(alu_tmp, ALU_RATES)
-    with open(os.path.join(BUILD, "ptxas.log"), "w") as fh:
+    os.replace(tmp, lib_path)
+    if not checked:
+        os.replace(alu_tmp, ALU_RATES)
+    with open(os.path.join(out_dir, "ptxas.log"), "w") as fh:
         for f, out in logs:
             fh.write(f"== {f}\n{out}\n")
     if verbose:
         for f, out in logs:
             sys.stdout.write(f"== {f}\n{out}\n")
-    return LIB
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv))

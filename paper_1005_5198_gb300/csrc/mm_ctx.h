@@ -121,6 +121,7 @@ struct LaunchScratch {
     MapDesc *d_maps = nullptr;
     FarDesc *d_far = nullptr;         // MM_FAR32 launches: one per map, parallel to d_maps
     unsigned long long *d_counter = nullptr;
+    unsigned int *d_check = nullptr;  // checked builds: bounds-check word of the launches (LaunchArgs::check)
     int cap = 0;
     WorkHeader *h_hdr = nullptr;      // pinned
     MapDesc *h_maps = nullptr;        // pinned

@@ -7,8 +7,30 @@
 
 #include "mm_internal.h"
 
+// Checked builds (-DMM_CHECKS): a failed bounds check records its site code in
+// *check (the first failure wins) and the guarded access is skipped, so that a
+// bad index becomes a status the host reads instead of a fault. Other builds
+// compile the checks away.
+#ifdef MM_CHECKS
+#define MM_BOUNDS(check, cond, code) \
+    ((cond) ? true : (atomicCAS((check), 0u, (unsigned)(code)), false))
+#else
+#define MM_BOUNDS(check, cond, code) true
+#endif
+
 namespace mm {
 namespace dev {
+
+// Site codes of the bounds checks.
+enum CheckSite : unsigned {
+    kChkMapCount = 1,       // a count outside the N_side^2 map
+    kChkLensTile = 2,       // an FP32 lens tile read past the padded lens set
+    kChkLensFP64 = 3,       // an FP64 lens read past N*
+    kChkPartial = 4,        // a split tile's partial sums outside its buffer
+    kChkSegDone = 5,        // a split tile's segment counter outside its buffer
+    kChkNearList = 6,       // a far-field near-list access outside the list
+    kChkFarBlock = 7,       // a far-field block index outside the map's blocks
+};
 
 __device__ __forceinline__ float rcp_approx(float x)
 {
@@ -139,7 +161,9 @@ __device__ __forceinline__ void emit_ray(const LaunchArgs &A, const MapDesc &M, 
     } else {
         const unsigned key = inside ? pix : 0xffffffffu;
         const unsigned peers = __match_any_sync(0xffffffffu, key);
-        if (inside && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(M.counts + pix, (unsigned)__popc(peers));
+        if (inside && (int)(threadIdx.x & 31) == __ffs(peers) - 1 &&
+            MM_BOUNDS(A.check, pix < (unsigned)M.nside * (unsigned)M.nside, kChkMapCount))
+            atomicAdd(M.counts + pix, (unsigned)__popc(peers));
         cnt_in += inside ? 1u : 0u;
         cnt_out += (valid && !inside) ? 1u : 0u;
     }

@@ -107,7 +107,8 @@ __global__ void __launch_bounds__(kFarThreads) k_far_fill(const MapDesc M, const
                 near = r2 < F.rn2;
             }
             const unsigned bal = __ballot_sync(kFull, near);
-            if (near) near_idx[out + __popc(bal & ((1u << lane) - 1u))] = (int)k;
+            const unsigned long long at = out + __popc(bal & ((1u << lane) - 1u));
+            if (near && MM_BOUNDS(F.check, at < F.near_off[b + 1], kChkNearList)) near_idx[at] = (int)k;
             out += __popc(bal);
         }
     }
@@ -289,7 +290,9 @@ __device__ __forceinline__ void far_stage(const MapDesc &M, const FarDesc &F, lo
     const long long n_near = (long long)(F.near_off[blk + 1] - off0);
     const long long end = min(n_near, c0 + (long long)kNearCap);
     for (long long k = c0 + tid; k < end; k += kShootThreads) {
+        if (!MM_BOUNDS(F.check, off0 + k < F.near_off[F.nblocks], kChkNearList)) continue;
         const int g = F.near_idx[off0 + k];
+        if (!MM_BOUNDS(F.check, g >= 0 && g < M.nstar, kChkNearList)) continue;
         const float4 q = M.lh[g];
         float sh, se, th, te;
         two_sum(q.x, -cxh, sh, se);                           // exact split of x_h - c_h
@@ -303,15 +306,15 @@ __device__ __forceinline__ void far_stage(const MapDesc &M, const FarDesc &F, lo
 
 // Production binning: rays of a warp lie along one lattice row, so equal pixels
 // come in runs; the first lane of each run adds the run's length.
-__device__ __forceinline__ void far_bin(const MapDesc &M, bool valid, bool inside, unsigned pix, unsigned &cnt_in,
-                                        unsigned &cnt_out)
+__device__ __forceinline__ void far_bin(const MapDesc &M, unsigned *check, bool valid, bool inside, unsigned pix,
+                                        unsigned &cnt_in, unsigned &cnt_out)
 {
     const unsigned lane = threadIdx.x & 31;
     const unsigned key = inside ? pix : 0xffffffffu;
     const unsigned left = __shfl_up_sync(kFull, key, 1);
     const bool start = lane == 0 || left != key;
     const unsigned starts = __ballot_sync(kFull, start);
-    if (inside && start) {
+    if (inside && start && MM_BOUNDS(check, pix < (unsigned)M.nside * (unsigned)M.nside, kChkMapCount)) {
         const unsigned above = starts & ~((2u << lane) - 1u);    // run starts after this lane
         const unsigned next = above ? (unsigned)(__ffs(above) - 1) : 32u;
         atomicAdd(M.counts + pix, next - lane);
@@ -511,7 +514,7 @@ __device__ void far_tile(const LaunchArgs &A, const FarDesc &F, const MapDesc &M
                            ((double)c0rh + (double)c0rl) - ((double)a.x + (double)a.y),
                            -((double)c0ih + (double)c0il) - ((double)a.z + (double)a.w), cnt_in, cnt_out);
         else
-            far_bin(M, valid, inside, pix, cnt_in, cnt_out);
+            far_bin(M, A.check, valid, inside, pix, cnt_in, cnt_out);
     }
 }
 
@@ -525,6 +528,7 @@ __device__ void far_item(const LaunchArgs &A, const FarDesc &F, const MapDesc &M
     const long long gpb = F.bt / F.rows_per_item;             // items per block
     const long long blk = (long long)(it / (unsigned long long)gpb);
     const long long grp = (long long)(it % (unsigned long long)gpb);
+    if (!MM_BOUNDS(A.check, blk < F.nblocks, kChkFarBlock)) return;
     far_stage(M, F, blk, 0, true, S);
     __syncthreads();
     const long long bx = blk % F.blocks_x, by = blk / F.blocks_x;
@@ -587,6 +591,7 @@ __global__ void __launch_bounds__(kShootThreads, 2) k_shoot_far_dump(const Launc
         const long long tx = (long long)(tile % (unsigned long long)M.tiles_x);
         const long long ty = (long long)(tile / (unsigned long long)M.tiles_x);
         const long long blk = (ty / F.bt) * F.blocks_x + tx / F.bt;
+        if (!MM_BOUNDS(A.check, blk < F.nblocks, kChkFarBlock)) return;
         __syncthreads();
         far_stage(M, F, blk, 0, true, S);
         __syncthreads();
@@ -683,6 +688,7 @@ int far_prepare(mm_ctx *ctx, MapObj &m, cudaStream_t s)
     if ((rc = ctx->arena.alloc(sizeof(unsigned), (void **)&m.far_bmax))) return rc;
     MM_CUDA(cudaMemsetAsync(m.far_bmax, 0, sizeof(unsigned), s));
     F.bound_max = m.far_bmax;
+    F.check = ctx->scratch.d_check;                 // the launch group's bounds-check word
     if (F.nblocks == 0) return MM_OK;
     if ((rc = ctx->arena.alloc((size_t)F.nblocks * F.stride * sizeof(float), (void **)&m.far_coef)) ||
         (rc = ctx->arena.alloc((size_t)(F.nblocks + 1) * sizeof(unsigned long long), (void **)&m.far_off)))

@@ -36,6 +36,7 @@ struct FarDesc {
                                           // near_idx[near_off[b] .. near_off[b + 1])
     const int *near_idx;                  // ascending lens indices per block
     unsigned int *bound_max;              // bits of the largest block bound (a positive float)
+    unsigned int *check;                  // checked builds: first failed bounds check (see LaunchArgs)
     // work items of the production launch: groups of rows_per_item tile rows of a block
     int rows_per_item;                    // 1 or bt
     unsigned long long items;             // nblocks * bt / rows_per_item

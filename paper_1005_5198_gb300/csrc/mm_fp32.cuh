@@ -170,8 +170,9 @@ __device__ void tile_fp32(const LaunchArgs &A, const MapDesc &M, unsigned long l
 #pragma unroll
         for (int t = tid; t < kChunkPairs; t += L::NT) {   // pair t; warps stage whole 32-pair blocks
             const long long la = base + 2 * t;              // lh is padded: la + 1 < padded size
-            const float4 qa = M.lh[la];
-            const float4 qb = M.lh[la + 1];
+            const bool in_set = MM_BOUNDS(A.check, la + 1 < lens_padded(M.nstar), kChkLensTile);
+            const float4 qa = in_set ? M.lh[la] : make_float4(kNullX, 0.f, 0.f, 0.f);
+            const float4 qb = in_set ? M.lh[la + 1] : make_float4(kNullX, 0.f, 0.f, 0.f);
             float xa = __fadd_rn(__fsub_rn(qa.x, cxh), __fsub_rn(qa.z, cxl));
             float ya = __fadd_rn(__fsub_rn(qa.y, cyh), __fsub_rn(qa.w, cyl));
             float xb = __fadd_rn(__fsub_rn(qb.x, cxh), __fsub_rn(qb.z, cxl));
@@ -179,7 +180,7 @@ __device__ void tile_fp32(const LaunchArgs &A, const MapDesc &M, unsigned long l
             const bool na = fabsf(xa) < hx && fabsf(ya) < hy;
             const bool nb = fabsf(xb) < hx && fabsf(yb) < hy;
             float ma = 1.f, mb = 1.f;
-            if (MASS) {
+            if (MASS && in_set) {
                 ma = M.lmf[la];
                 mb = M.lmf[la + 1];
             }
@@ -240,6 +241,7 @@ __device__ void tile_fp32(const LaunchArgs &A, const MapDesc &M, unsigned long l
                     const int b = __ffs(bits) - 1;
                     bits &= bits - 1;
                     const long long g = base + 2 * (32 * (k >> 1) + b) + (k & 1);
+                    if (!MM_BOUNDS(A.check, g < M.nstar, kChkLensFP64)) continue;
                     const double xl = M.lx[g], yl = M.ly[g];
                     const double ml = MASS ? M.lm[g] : 1.0;
 #pragma unroll
@@ -276,11 +278,20 @@ __device__ void tile_fp32(const LaunchArgs &A, const MapDesc &M, unsigned long l
             for (int r = 0; r < R; ++r) {
                 float4 a = acc.get(c, r);
                 if ((onlens >> (c * R + r)) & 1u) a.x = __int_as_float(0x7fc00000);   // NaN: ray on a lens
-                part[(size_t)seg * kTileRays + (col0 + 32 * c) + kTileX * (row0 + r)] = a;
+                const size_t pi = (size_t)seg * kTileRays + (col0 + 32 * c) + kTileX * (row0 + r);
+                if (MM_BOUNDS(A.check, (tile * (size_t)M.lens_splits) * kTileRays + pi <
+                                           (size_t)M.tiles_x * (size_t)((M.nj + kTileY - 1) / kTileY) *
+                                               (size_t)M.lens_splits * kTileRays,
+                               kChkPartial))
+                    part[pi] = a;
             }
         __threadfence();
         __syncthreads();
-        if (tid == 0) S.loop.last_segment = (atomicAdd(M.seg_done + tile, 1u) == (unsigned)(M.lens_splits - 1));
+        if (tid == 0)
+            S.loop.last_segment =
+                MM_BOUNDS(A.check, tile < (unsigned long long)M.tiles_x * (unsigned long long)((M.nj + kTileY - 1) / kTileY),
+                          kChkSegDone) &&
+                (atomicAdd(M.seg_done + tile, 1u) == (unsigned)(M.lens_splits - 1));
         __syncthreads();
         if (!S.loop.last_segment) return;
         __threadfence();

@@ -454,6 +454,8 @@ int scratch_reserve(mm_ctx *ctx, LaunchScratch *sc, int n_maps)
     if (!sc->d_hdr) {
         MM_CUDA(cudaMalloc(&sc->d_hdr, sizeof(WorkHeader)));
         MM_CUDA(cudaMalloc(&sc->d_counter, sizeof(unsigned long long)));
+        MM_CUDA(cudaMalloc(&sc->d_check, sizeof(unsigned int)));
+        MM_CUDA(cudaMemset(sc->d_check, 0, sizeof(unsigned int)));
         MM_CUDA(cudaMallocHost(&sc->h_hdr, sizeof(WorkHeader)));
     }
     if (n_maps > sc->cap) {
@@ -483,6 +485,7 @@ void scratch_free(mm_ctx *ctx, LaunchScratch *sc)
     if (sc->d_hdr) cudaFree(sc->d_hdr);
     if (sc->d_maps) cudaFree(sc->d_maps);
     if (sc->d_counter) cudaFree(sc->d_counter);
+    if (sc->d_check) cudaFree(sc->d_check);
     if (sc->h_hdr) cudaFreeHost(sc->h_hdr);
     if (sc->h_maps) cudaFreeHost(sc->h_maps);
     if (sc->d_far) cudaFree(sc->d_far);
@@ -525,7 +528,11 @@ static int launch_group(mm_ctx *ctx, std::vector<MapObj *> &group, int precision
     a.hdr = sc->d_hdr;
     a.maps = sc->d_maps;
     a.work_counter = sc->d_counter;
+    a.check = sc->d_check;
     if (dump) a.dump = *dump;
+#ifdef MM_CHECKS
+    MM_CUDA(cudaMemsetAsync(sc->d_check, 0, sizeof(unsigned int), s));
+#endif
     const unsigned long long work = sc->h_hdr->total_work;
     const long long cap =
         (long long)ctx->sms * (far ? far_ctas_per_sm() : shoot_ctas_per_sm(fp64, ctx->layout));
@@ -559,6 +566,11 @@ static int launch_group(mm_ctx *ctx, std::vector<MapObj *> &group, int precision
     *ms = t;
     ctx->last_ms = t;
     ctx->last_launches += work > 0 ? 1 : 0;
+#ifdef MM_CHECKS
+    unsigned bad = 0;
+    MM_CUDA(cudaMemcpy(&bad, sc->d_check, sizeof(bad), cudaMemcpyDeviceToHost));
+    if (bad) return fail(MM_EDEVICE, "bounds check failed at site " + std::to_string(bad));
+#endif
     if (far) {
         for (MapObj *m : group) {                 // the largest tail bound of the map's blocks
             unsigned bits = 0;

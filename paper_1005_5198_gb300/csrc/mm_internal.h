@@ -95,7 +95,15 @@ struct LaunchArgs {
     const MapDesc *maps;                  // hdr->n_maps descriptors, item_begin ascending
     unsigned long long *work_counter;     // zeroed before the launch
     DumpArgs dump;
+    unsigned int *check;                  // checked builds (MM_CHECKS): code of the first failed
+                                          // bounds check, zeroed before the launch; else unused
 };
+
+// Padded length of a lens set's FP32 tile copies (whole chunks plus one null chunk).
+__host__ __device__ inline long long lens_padded(long long nstar)
+{
+    return (nstar + kChunkLenses - 1) / kChunkLenses * kChunkLenses + kChunkLenses;
+}
 
 // ---- launch wrappers (mm_kernels.cu) --------------------------------------
 // Build the FP32 tile copies of a lens set: lh[k] = split of (x[k], y[k]) for

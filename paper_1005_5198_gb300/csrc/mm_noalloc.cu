@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <string>
 
 #include "mm_ctx.h"
 
@@ -32,6 +33,7 @@ struct NoAllocScratch {
     WorkHeader hdr;
     MapDesc desc;
     unsigned long long counter;
+    unsigned int check;                 // checked builds: first failed bounds check of the call
 };
 
 // The scratch. In host code this name is only a stand-in for the symbol: its
@@ -81,6 +83,7 @@ __global__ void k_noalloc_setup(const WorkHeader hdr, const MapDesc desc, NoAllo
     sc->hdr = hdr;
     sc->desc = desc;
     sc->counter = 0ULL;
+    sc->check = 0u;
 }
 
 }  // namespace
@@ -153,9 +156,17 @@ extern "C" int mm_shoot_noalloc(const double *x, const double *y, const double *
     a.hdr = &sc->hdr;
     a.maps = &sc->desc;
     a.work_counter = &sc->counter;
+    a.check = &sc->check;
     const long long cap = (long long)sms * shoot_ctas_per_sm(false, kNoAllocLayout);
     const int grid = (int)std::max(1LL, std::min((long long)h.total_work, cap));
     if ((e = launch_shoot_fp32(a, kNoAllocLayout, grid, false, false, s)) != cudaSuccess)
         return cuda_fail(e, "no-alloc shoot launch");
+#ifdef MM_CHECKS
+    unsigned bad = 0;                   // checked builds wait for the shoot and read its checks
+    if ((e = cudaMemcpyAsync(&bad, &sc->check, sizeof(bad), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(e, "no-alloc bounds check readback");
+    if (bad) return fail(MM_EDEVICE, "bounds check failed at site " + std::to_string(bad));
+#endif
     return MM_OK;
 }

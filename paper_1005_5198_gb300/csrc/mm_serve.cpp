@@ -170,6 +170,7 @@ static int capture_graph(Server *S, int b, int split)
     a.hdr = sc->d_hdr;
     a.maps = sc->d_maps;
     a.work_counter = sc->d_counter;
+    a.check = sc->d_check;
     const int grid = ctx->sms * shoot_ctas_per_sm(false, ctx->layout);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(S->capture, cudaStreamCaptureModeThreadLocal);
@@ -274,6 +275,7 @@ static int launch_wave(Server *S, Wave *w)
         a.hdr = sc->d_hdr;
         a.maps = sc->d_maps;
         a.work_counter = sc->d_counter;
+        a.check = sc->d_check;
         cudaError_t e = launch_shoot_fp64(a, ctx->sms * shoot_ctas_per_sm(true, 0), false, st);
         if (e != cudaSuccess) return cuda_fail(e, "fp64 wave launch");
     }
@@ -296,12 +298,26 @@ static void complete_wave(Server *S, Wave &w, std::unique_lock<std::mutex> &lk)
     cudaError_t e = cudaEventSynchronize(w.end);
     float ms = 0.f;
     if (e == cudaSuccess) cudaEventElapsedTime(&ms, w.start, w.end);
+#ifdef MM_CHECKS
+    // checked builds: a failed bounds check of any wave (never reset) stops the server
+    unsigned bad = 0, bad64 = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&bad, S->sc[w.buf].d_check, sizeof(bad), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && S->sc64[w.buf].d_check)
+        e = cudaMemcpy(&bad64, S->sc64[w.buf].d_check, sizeof(bad64), cudaMemcpyDeviceToHost);
+#endif
     lk.lock();
     if (e != cudaSuccess) {
         S->fatal = cudaGetErrorString(e);
         for (auto &it : w.items) finish(S, it.req, 3, MM_EDEVICE, S->fatal);
         return;
     }
+#ifdef MM_CHECKS
+    if (bad || bad64) {
+        S->fatal = "bounds check failed at site " + std::to_string(bad ? bad : bad64);
+        for (auto &it : w.items) finish(S, it.req, 3, MM_EDEVICE, S->fatal);
+        return;
+    }
+#endif
     // refine the device rate from waves large enough to fill the GPU
     const unsigned long long full = 2ULL * (unsigned long long)S->ctx->sms;
     if (ms > 0.2f && w.tiles >= full) {

@@ -124,3 +124,13 @@ def test_sweep_plans_reproduce_printed_lens_counts():
     sm = sweep.plan("smooth", 2048, 1000.0)
     assert len(sm) == 11 and sm[-1]["smooth_frac"] == 0.99
     assert all(a["nstar"] >= b["nstar"] for a, b in zip(sm, sm[1:]))      # N* falls as s grows
+
+
+def test_checked_build_exports_the_same_symbols():
+    """The checked variant (-DMM_CHECKS) compiles and exports the ABI of the normal build."""
+    import ctypes
+    from paper_1005_5198_gb300 import buildlib
+    path = buildlib.build(checked=True)
+    lib = ctypes.CDLL(path)
+    for name in mm.EXPORTED:
+        assert hasattr(lib, name), name
