@@ -303,13 +303,14 @@ __device__ void tile_fp32(const LaunchArgs &A, const MapDesc &M, unsigned long l
     for (int c = 0; c < C; ++c) {
         const long long gi = ib + col0 + 32 * c;
         float uxh, uxl;
-        ff_axis(M.ax_h, M.ax_l, (float)(2 * gi + 1 - M.nx), M.half_n, uxh, uxl);
+        // |2 i + 1 - nx| < 2^23: a 32-bit conversion (the 64-bit one runs on the FP64 pipe), same value
+        ff_axis(M.ax_h, M.ax_l, (float)(int)(2 * gi + 1 - M.nx), M.half_n, uxh, uxl);
         const bool col_ok = gi < M.i0 + M.ni;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const long long gj = jb + row0 + r;
             float uyh, uyl;
-            ff_axis(M.ay_h, M.ay_l, (float)(2 * gj + 1 - M.ny), M.half_n, uyh, uyl);
+            ff_axis(M.ay_h, M.ay_l, (float)(int)(2 * gj + 1 - M.ny), M.half_n, uyh, uyl);
             float4 a;
             if (SPLIT && part) {                          // split tile: segments in order
                 const int local = (col0 + 32 * c) + kTileX * (row0 + r);
