@@ -144,7 +144,7 @@ __device__ __forceinline__ int dump_find(const DumpArgs &D, int item, int mine)
 }
 
 // Record one ray's result: debug dump, or a warp-aggregated count into the map
-// (every lane of the warp must call this together).
+// (every lane of the warp must call this together, lanes in column order).
 template <bool DUMP>
 __device__ __forceinline__ void emit_ray(const LaunchArgs &A, const MapDesc &M, int item, int local, bool valid,
                                          bool inside, unsigned pix, double alpha1, double alpha2, unsigned &cnt_in,
@@ -159,11 +159,17 @@ __device__ __forceinline__ void emit_ray(const LaunchArgs &A, const MapDesc &M, 
             A.dump.pixel[sl] = inside ? (long long)pix : -1LL;
         }
     } else {
+        // The lanes of a warp hold consecutive columns of one lattice row, so rays that
+        // land in the same pixel come in runs: the first lane of each run adds its length.
+        const unsigned lane = threadIdx.x & 31;
         const unsigned key = inside ? pix : 0xffffffffu;
-        const unsigned peers = __match_any_sync(0xffffffffu, key);
-        if (inside && (int)(threadIdx.x & 31) == __ffs(peers) - 1 &&
-            MM_BOUNDS(A.check, pix < (unsigned)M.nside * (unsigned)M.nside, kChkMapCount))
-            atomicAdd(M.counts + pix, (unsigned)__popc(peers));
+        const unsigned left = __shfl_up_sync(0xffffffffu, key, 1);
+        const bool start = lane == 0 || left != key;
+        const unsigned starts = __ballot_sync(0xffffffffu, start);
+        if (inside && start && MM_BOUNDS(A.check, pix < (unsigned)M.nside * (unsigned)M.nside, kChkMapCount)) {
+            const unsigned above = starts & ~((2u << lane) - 1u);     // run starts after this lane
+            atomicAdd(M.counts + pix, (above ? (unsigned)(__ffs(above) - 1) : 32u) - lane);
+        }
         cnt_in += inside ? 1u : 0u;
         cnt_out += (valid && !inside) ? 1u : 0u;
     }
