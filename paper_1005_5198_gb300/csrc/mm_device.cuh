@@ -87,7 +87,7 @@ __device__ __forceinline__ float ff_pixel(float uh, float ul, float sh, float sl
 
 // Shared state of the persistent loop (first member of each kernel's shared block).
 struct LoopSmem {
-    unsigned long long g;
+    unsigned long long g;          // the next work item (fetched ahead) and its map
     int map;
     unsigned red_in, red_out;
     int last_segment;              // split tiles: this CTA finished the tile's last segment
@@ -177,7 +177,9 @@ __device__ __forceinline__ void emit_ray(const LaunchArgs &A, const MapDesc &M, 
 
 // Persistent loop: take work items from the launch's counter until exhausted,
 // run `body(M, tile, segment, dump_item, cnt_in, cnt_out)` on each, and add the
-// in/out ray counts to the map totals whenever the map changes and at exit.
+// in/out ray counts to the map totals whenever the map changes and at exit. The
+// next item is fetched while the current one runs, so the counter's latency is
+// hidden behind the work.
 template <bool DUMP, typename Body>
 __device__ __forceinline__ void persistent_loop(const LaunchArgs &A, LoopSmem &S, Body body)
 {
@@ -186,25 +188,31 @@ __device__ __forceinline__ void persistent_loop(const LaunchArgs &A, LoopSmem &S
     unsigned long long run_in = 0, run_out = 0;   // meaningful in thread 0
     const unsigned long long total_work = A.hdr->total_work;
     const int n_maps = A.hdr->n_maps;
+    if (tid == 0) {
+        const unsigned long long g = atomicAdd(A.work_counter, 1ULL);
+        S.g = g;
+        S.map = (g < total_work) ? (DUMP ? 0 : find_map(A, n_maps, g)) : -1;
+        S.red_in = 0;
+        S.red_out = 0;
+    }
+    __syncthreads();
     for (;;) {
-        if (tid == 0) {
-            const unsigned long long g = atomicAdd(A.work_counter, 1ULL);
-            S.g = g;
-            S.map = (g < total_work) ? (DUMP ? 0 : find_map(A, n_maps, g)) : -1;
-            S.red_in = 0;
-            S.red_out = 0;
-        }
-        __syncthreads();
         const unsigned long long g = S.g;
         const int mi = S.map;
         if (g >= total_work) break;
-        if (tid == 0 && cur_map != mi) {
-            if (cur_map >= 0 && !DUMP) {
-                atomicAdd(A.maps[cur_map].totals + 0, run_in);
-                atomicAdd(A.maps[cur_map].totals + 1, run_out);
+        __syncthreads();                           // every thread has read S.g and S.map
+        if (tid == 0) {
+            const unsigned long long gn = atomicAdd(A.work_counter, 1ULL);   // the next item, ahead
+            S.g = gn;
+            S.map = (gn < total_work) ? (DUMP ? 0 : find_map(A, n_maps, gn)) : -1;
+            if (cur_map != mi) {
+                if (cur_map >= 0 && !DUMP) {
+                    atomicAdd(A.maps[cur_map].totals + 0, run_in);
+                    atomicAdd(A.maps[cur_map].totals + 1, run_out);
+                }
+                cur_map = mi;
+                run_in = run_out = 0;
             }
-            cur_map = mi;
-            run_in = run_out = 0;
         }
         const MapDesc &M = A.maps[mi];
         const unsigned long long nsp = (unsigned long long)M.lens_splits;
@@ -224,8 +232,10 @@ __device__ __forceinline__ void persistent_loop(const LaunchArgs &A, LoopSmem &S
         if (tid == 0) {
             run_in += S.red_in;
             run_out += S.red_out;
+            S.red_in = 0;                          // for the next item (its body may hold no barrier)
+            S.red_out = 0;
         }
-        __syncthreads();                           // S.g / S.red_* are rewritten next iteration
+        __syncthreads();                           // S.g, S.map and S.red_* are ready for the next item
     }
     if (tid == 0 && cur_map >= 0 && !DUMP) {
         atomicAdd(A.maps[cur_map].totals + 0, run_in);
