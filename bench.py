@@ -216,12 +216,13 @@ KERNEL_SOURCES = ["mm_fp32.cuh", "mm_device.cuh", "mm_internal.h", "mm_fp32_c2r4
 
 
 def far_phase(mm, ctx, lh_fig1, exact_ms):
-    """The far-field approximation MM_FAR32 (the tree code's idea, Sect. 2.1; default order 16,
-    ratio 0.3, 8 x 8-tile blocks), timed outside the headline region: the Fig. 1 map against the
+    """The far-field approximation MM_FAR32 (the tree code's idea, Sect. 2.1; the library's default
+    order, ratio and block), timed outside the headline region: the Fig. 1 map against the
     exact FP32 map of the same lenses, and the sigma = 0.8, N* = 25000 map (600 x 120 R_E shot
     region, 9.4e10 rays), whose exact shoot would take interactions / (the headline rate)."""
     import synth
-    out = {"params": {"far_order": 16, "far_ratio": 0.3, "far_block": 8},
+    d = mm.params()
+    out = {"params": {"far_order": d.far_order, "far_ratio": d.far_ratio, "far_block": d.far_block},
            "timing": "CUDA events around block preparation + shoot (mm_last_kernel_ms), best of 3"}
     m = mm.mm_shoot(ctx, lh_fig1, mm.params(**CFG1))
     ex, st_ex = mm.mm_map_fetch(ctx, m)

@@ -100,8 +100,8 @@ typedef struct {
     uint64_t seed;           /* lens-field seed (SplitMix64 streams) */
     int64_t  ray_rect[4];    /* [i0, i1, j0, j1) sub-rectangle of the global ray grid, or
                                 all -1 for the whole grid (tests and windowed runs) */
-    int32_t  far_order;      /* MM_FAR32: series terms P, 1 .. 32 (default 16) */
-    double   far_ratio;      /* MM_FAR32: near ratio q, 0 < q <= 0.9 (default 0.3) */
+    int32_t  far_order;      /* MM_FAR32: series terms P, 1 .. 32 (default 10) */
+    double   far_ratio;      /* MM_FAR32: near ratio q, 0 < q <= 0.9 (default 0.15) */
     int32_t  far_block;      /* MM_FAR32: block side in ray tiles, 1 .. 64 (default 8); blocks
                                 are counted from the origin of the shot rectangle */
 } mm_params;

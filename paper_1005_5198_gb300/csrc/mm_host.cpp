@@ -709,8 +709,8 @@ int mm_params_default(mm_params *p)
     p->mass_s = 0.5;
     p->seed = 1;
     for (int k = 0; k < 4; ++k) p->ray_rect[k] = -1;
-    p->far_order = 16;
-    p->far_ratio = 0.3;
+    p->far_order = 10;
+    p->far_ratio = 0.15;
     p->far_block = 8;
     return MM_OK;
 }

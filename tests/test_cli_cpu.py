@@ -12,7 +12,7 @@ def test_shipped_configs_load_and_give_the_paper_geometry():
     g = mm.mm_geometry_of(cli.to_params(cli.load_config("fig1")))
     assert (g["nx"], g["ny"], g["nstar"]) == (114487, 114487, 558)          # Fig. 1: N* = 558 (Sect. 3.2.1)
     p = cli.to_params(cli.load_config("sigma08"))
-    assert p.precision == mm.MM_FAR32 and p.nstar == 25000 and p.far_order == 16
+    assert p.precision == mm.MM_FAR32 and p.nstar == 25000 and p.far_order == 10
 
 
 def test_overrides_and_errors(tmp_path):

@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 CFG0 = dict(sigma=0.4, gamma=0.0, smooth_frac=0.0, side=4.0, npix_side=128, nrays=100.0)
 CFG1 = dict(sigma=0.4, gamma=0.0, smooth_frac=0.0, side=20.0, npix_side=1024, nrays=2000.0)
 CFG2 = dict(sigma=0.8, gamma=0.3, smooth_frac=0.5, side=40.0, npix_side=2048, nrays=500.0)
-FAR_DEFAULT = dict(order=16, ratio=0.3, block_tiles=8)
+FAR_DEFAULT = dict(order=10, ratio=0.15, block_tiles=8)     # the library's defaults
 ALPHA_TOL = 1e-5
 MISBIN = 2e-4
 
