@@ -467,3 +467,28 @@ def test_unknown_handles(ctx):
         mm.mm_map_fetch(ctx, 987654321)
     with pytest.raises(mm.MMError):
         mm.mm_release_lenses(ctx, 987654321)
+
+
+def test_large_lens_count_streams_through_chunks(ctx):
+    """N* = 200 000 (391 lens chunks per tile): lenses are streamed through shared memory, so
+    N* is bounded by device memory only. A ray window matches the oracle, and the far field's
+    sampled rays match the far-field oracle."""
+    nstar = 200000
+    f = synth.lens_field(nstar, float(np.sqrt(nstar / 0.4)), 21)
+    lh = lens(ctx, f)
+    cfg = dict(sigma=0.4, gamma=0.0, smooth_frac=0.0, side=4.0, npix_side=64, nrays=50.0)
+    g = mm.mm_geometry_of(P(cfg))
+    c = g["nx"] // 2
+    rect = (c - 160, c + 160, c - 96, c + 96)                  # 61 440 rays: 1.2e10 interactions
+    got, st = shoot(ctx, lh, cfg, ray_rect=rect)
+    ref, tot = oracle.shoot_map(oracle_cfg(cfg), f, rect=rect)
+    assert st["rays_shot"] == tot["shot"] and st["nstar"] == nstar
+    check_totals(got, st, tot["shot"])
+    assert int(np.abs(got.astype(np.int64) - ref).sum()) <= max(2, 2e-4 * tot["shot"])
+    rng = np.random.default_rng(21)
+    ii, jj = rng.integers(0, g["nx"], 300), rng.integers(0, g["ny"], 300)
+    far = dict(order=10, ratio=0.15, block_tiles=8)
+    a_g, _ = mm.mm_debug_deflect(ctx, lh, P(cfg, precision=mm.MM_FAR32, far_order=far["order"],
+                                           far_ratio=far["ratio"], far_block=far["block_tiles"]), ii, jj)
+    a_o, _, _, _ = oracle.far_rays(oracle_cfg(cfg), f, far, ii, jj)
+    assert np.hypot(*(a_g - a_o).T).max() <= 1e-5
