@@ -40,6 +40,7 @@ sys.path.insert(0, ROOT)
 CFG1 = dict(sigma=0.4, gamma=0.0, smooth_frac=0.0, side=20.0, npix_side=1024, nrays=2000.0)
 SEED = 2
 FLOP_PER_INTERACTION = 10.0      # Eq. for Phi: N_FLOP = 10 per deflection evaluation
+USEFUL_OPS_PER_INTERACTION = 6.0  # FP32 lane operations no implementation avoids: 2 sub, 1 mul, 3 fma
 SMS, LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SMS * LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 WORKLOAD = ("Fig. 1 map: sigma=0.4, gamma=0, s=0, L=20 R_E, N_pix=1024^2, N_rays=2000, N*=558 unit masses "
@@ -515,7 +516,12 @@ def main():
                      "peak_source": "recipe unit counts: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz",
                      "kernel_ms": kmean,
                      "frac_at_measured_clock": (achieved / (FP32_PEAK_TFLOPS * clocks["sm_mhz"] / SM_MAX_MHZ)
-                                                if clocks.get("sm_mhz") else None)},
+                                                if clocks.get("sm_mhz") else None),
+                     # the irreducible FP32 lane operations of an interaction (2 subtractions,
+                     # 1 multiply, 3 FMAs) per second, against the FP32 lane peak
+                     "useful_frac": USEFUL_OPS_PER_INTERACTION * (inter / (world * args.steps)) / (kmean * 1e-3)
+                                    / (SMS * LANES * SM_MAX_MHZ * 1e6),
+                     "useful_ops_per_interaction": USEFUL_OPS_PER_INTERACTION},
         "fp64": fp64,
         "fp32_over_fp64": value / world / fp64["value"],
         "clocks": clocks,
