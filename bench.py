@@ -225,20 +225,24 @@ def far_phase(mm, ctx, lh_fig1, exact_ms):
     d = mm.params()
     out = {"params": {"far_order": d.far_order, "far_ratio": d.far_ratio, "far_block": d.far_block},
            "timing": "CUDA events around block preparation + shoot (mm_last_kernel_ms), best of 3"}
-    m = mm.mm_shoot(ctx, lh_fig1, mm.params(**CFG1))
-    ex, st_ex = mm.mm_map_fetch(ctx, m)
+    m_ex = mm.mm_shoot(ctx, lh_fig1, mm.params(**CFG1))
+    ex, st_ex = mm.mm_map_fetch(ctx, m_ex)
     ex = ex.copy()
-    mm.mm_release_map(ctx, m)
     times = []
-    for _ in range(3):
+    for k in range(3):
         m = mm.mm_shoot(ctx, lh_fig1, mm.params(**CFG1, precision=mm.MM_FAR32))
         times.append(mm.mm_last_kernel_ms(ctx)[0])
         far, st = mm.mm_map_fetch(ctx, m)
-        mm.mm_release_map(ctx, m)
+        if k < 2:
+            mm.mm_release_map(ctx, m)
+    cmp = mm.mm_map_compare(ctx, m, m_ex)            # the paper's map statistics (Sect. 3.1)
+    mm.mm_release_map(ctx, m)
+    mm.mm_release_map(ctx, m_ex)
     t = min(times)
     out["fig1"] = {"ms": t, "equivalent_interactions_per_s": st["interactions"] / (t * 1e-3),
                    "speedup_vs_exact": exact_ms / t, "far_bound_re": st["far_bound"],
-                   "rays_moved_vs_exact_fraction": float(np.abs(far.astype(np.int64) - ex).sum()) / 2 / st["rays_shot"]}
+                   "rays_moved_vs_exact_fraction": float(np.abs(far.astype(np.int64) - ex).sum()) / 2 / st["rays_shot"],
+                   "vs_exact_rms_delta_m": cmp["rms_dm"], "vs_exact_ks_probability": cmp["ks_p"]}
     f2 = synth.lens_field(25000, 250.0, 3)
     lh2 = mm.mm_create_lenses_from(ctx, f2.x, f2.y, f2.m)
     cfg2 = dict(sigma=0.8, gamma=0.3, smooth_frac=0.5, side=40.0, npix_side=2048, nrays=500.0)
