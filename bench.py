@@ -242,7 +242,8 @@ def far_phase(mm, ctx, lh_fig1, exact_ms):
     out["fig1"] = {"ms": t, "equivalent_interactions_per_s": st["interactions"] / (t * 1e-3),
                    "speedup_vs_exact": exact_ms / t, "far_bound_re": st["far_bound"],
                    "rays_moved_vs_exact_fraction": float(np.abs(far.astype(np.int64) - ex).sum()) / 2 / st["rays_shot"],
-                   "vs_exact_rms_delta_m": cmp["rms_dm"], "vs_exact_ks_probability": cmp["ks_p"]}
+                   "vs_exact_rms_delta_m": cmp["rms_dm"], "vs_exact_ks_probability": cmp["ks_p"],
+                   "far_block_used": st["far_block"]}
     f2 = synth.lens_field(25000, 250.0, 3)
     lh2 = mm.mm_create_lenses_from(ctx, f2.x, f2.y, f2.m)
     cfg2 = dict(sigma=0.8, gamma=0.3, smooth_frac=0.5, side=40.0, npix_side=2048, nrays=500.0)
@@ -258,7 +259,7 @@ def far_phase(mm, ctx, lh_fig1, exact_ms):
     out["sigma08_nstar25000"] = {"ms": t2, "rays": st2["rays_shot"],
                                  "equivalent_interactions_per_s": st2["interactions"] / (t2 * 1e-3),
                                  "exact_estimated_s": st2["interactions"] / exact_rate,
-                                 "far_bound_re": st2["far_bound"]}
+                                 "far_bound_re": st2["far_bound"], "far_block_used": st2["far_block"]}
     return out
 
 

@@ -102,8 +102,11 @@ typedef struct {
                                 all -1 for the whole grid (tests and windowed runs) */
     int32_t  far_order;      /* MM_FAR32: series terms P, 1 .. 32 (default 10) */
     double   far_ratio;      /* MM_FAR32: near ratio q, 0 < q <= 0.9 (default 0.15) */
-    int32_t  far_block;      /* MM_FAR32: block side in ray tiles, 1 .. 64 (default 8); blocks
-                                are counted from the origin of the shot rectangle */
+    int32_t  far_block;      /* MM_FAR32: block side in ray tiles, 1 .. 64, or 0 (default): the
+                                side that minimises a cost model of block preparation
+                                (blocks x N* x P) against near-lens work (rays x near lenses
+                                per block), from the whole ray grid, N* and the lens disc.
+                                Blocks are counted from the origin of the shot rectangle */
 } mm_params;
 
 /* Lens-field derivation used by mm_create_lenses when nstar < 0 or
@@ -128,6 +131,7 @@ typedef struct {
                                combine the segments' float-float sums in segment order */
     double   far_bound;     /* MM_FAR32: largest truncation bound of any ray (Einstein radii,
                                evaluated at the block radius); 0 for the exact precisions */
+    int32_t  far_block;     /* MM_FAR32: the block side (tiles) used; 0 for the exact precisions */
 } mm_stats;
 
 typedef struct {
@@ -139,6 +143,8 @@ typedef struct {
     int64_t nstar;      /* N* after derivation */
     double  disc_radius;
     double  mu_theory;  /* 1 / ((1 - sigma)^2 - gamma^2), Eq. mutheory */
+    int32_t far_block;  /* MM_FAR32: the block side in tiles for these parameters (the automatic
+                           choice when far_block = 0, with N* above) */
 } mm_geometry;
 
 /* ---- context ------------------------------------------------------------ */

@@ -61,7 +61,7 @@ class mm_stats(C.Structure):
     _fields_ = [("rays_shot", C.c_uint64), ("rays_in", C.c_uint64), ("rays_out", C.c_uint64),
                 ("interactions", C.c_uint64), ("nx", C.c_uint64), ("ny", C.c_uint64), ("nstar", C.c_int64),
                 ("seconds", C.c_double), ("mu_mean", C.c_double), ("lens_splits", C.c_int32),
-                ("far_bound", C.c_double)]
+                ("far_bound", C.c_double), ("far_block", C.c_int32)]
 
 
 class mm_compare(C.Structure):
@@ -72,7 +72,7 @@ class mm_compare(C.Structure):
 class mm_geometry(C.Structure):
     _fields_ = [("pix", C.c_double), ("delta", C.c_double), ("width", C.c_double), ("height", C.c_double),
                 ("nx", C.c_int64), ("ny", C.c_int64), ("nstar", C.c_int64), ("disc_radius", C.c_double),
-                ("mu_theory", C.c_double)]
+                ("mu_theory", C.c_double), ("far_block", C.c_int32)]
 
 
 _lib = None

@@ -113,7 +113,7 @@ def cmd_shoot(args):
         if args.parts is None:
             m = mm_shoot(ctx, 0, p)
         else:
-            align = 32 * (p.far_block if p.precision == MM_FAR32 else 1)
+            align = 32 * (g["far_block"] if p.precision == MM_FAR32 else 1)
             plan = band_plan(g["ny"], args.parts, align)
             start = 0
             if args.checkpoint and os.path.exists(args.checkpoint):

@@ -163,6 +163,9 @@ void fill_desc(const MapObj &m, MapDesc *d);
 // once, to size the near lists); free them.
 int far_prepare(mm_ctx *ctx, MapObj &m, cudaStream_t s);
 void far_release(MapObj &m);
+// The far field's block side for parameters p, a grid g and N* lenses: p.far_block, or for 0
+// the side that minimises the modelled time (mm_far.cu).
+int far_block_for(const Geo &g, const mm_params &p, long long nstar);
 int choose_variant(mm_ctx *ctx, const mm_params *p, const Geo &g);
 int scratch_reserve(mm_ctx *ctx, LaunchScratch *sc, int n_maps);
 void scratch_free(mm_ctx *ctx, LaunchScratch *sc);

@@ -658,6 +658,37 @@ void far_release(MapObj &m)
     m.far_bmax = nullptr;
 }
 
+// Costs of the block-size model, fitted to GB300 timings of the Fig. 1 map (558 lenses,
+// 1.3e10 rays) and the sigma = 0.8 map (25 000 lenses, 9.4e10 rays) at blocks of 8 and
+// 16 tiles: block preparation per block, lens and series term; near-lens work per ray and
+// near lens; and a small cost per block (launch work, coefficients), which also breaks ties.
+constexpr double kSetupCost = 2.15e-12;      // seconds per block x lens x term
+constexpr double kNearCost = 0.81e-12;       // seconds per ray x near lens
+constexpr double kBlockCost = 2.0e-9;        // seconds per block
+
+int far_block_for(const Geo &g, const mm_params &p, long long nstar)
+{
+    if (p.far_block > 0) return p.far_block;
+    // the whole ray grid, so that every part of a map (mm_shoot_into) chooses alike
+    const double rays = (double)g.nx * (double)g.ny;
+    const double density = g.radius > 0.0 ? (double)nstar / (M_PI * g.radius * g.radius) : 0.0;
+    double best = 0.0;
+    int best_bt = 8;
+    for (int bt = 1; bt <= kFarMaxBlock; bt *= 2) {
+        const double bw = 64.0 * bt, bh = 32.0 * bt;
+        const double blocks = std::ceil((double)g.nx / bw) * std::ceil((double)g.ny / bh);
+        const double rho = g.delta * std::sqrt(0.25 * (bw * bw + bh * bh));
+        const double near = density * M_PI * (rho / p.far_ratio) * (rho / p.far_ratio);
+        const double cost = blocks * (double)nstar * (double)p.far_order * kSetupCost + rays * near * kNearCost +
+                            blocks * kBlockCost;
+        if (bt == 1 || cost < best) {
+            best = cost;
+            best_bt = bt;
+        }
+    }
+    return best_bt;
+}
+
 int far_prepare(mm_ctx *ctx, MapObj &m, cudaStream_t s)
 {
     far_release(m);
@@ -666,7 +697,7 @@ int far_prepare(mm_ctx *ctx, MapObj &m, cudaStream_t s)
     FarDesc &F = m.far;
     F = FarDesc{};
     F.order = p.far_order;
-    F.bt = p.far_block;
+    F.bt = far_block_for(g, p, m.lenses->n);
     const long long bw = 64LL * F.bt, bh = 32LL * F.bt;
     F.blocks_x = (g.ni + bw - 1) / bw;
     F.blocks_y = (g.nj + bh - 1) / bh;

@@ -99,7 +99,7 @@ int compute_geo(const mm_params *p, Geo *g)
         if (p->far_order < 1 || p->far_order > kFarMaxOrder) return fail(MM_EINVAL, "far_order must be in 1..32");
         if (!finite(p->far_ratio) || !(p->far_ratio > 0.0) || p->far_ratio > 0.9)
             return fail(MM_EINVAL, "far_ratio must be in (0, 0.9]");
-        if (p->far_block < 1 || p->far_block > kFarMaxBlock) return fail(MM_EINVAL, "far_block must be in 1..64");
+        if (p->far_block < 0 || p->far_block > kFarMaxBlock) return fail(MM_EINVAL, "far_block must be in 0..64");
     }
     if (p->mass_model != MM_MASS_UNIT && p->mass_model != MM_MASS_LOGNORMAL) return fail(MM_EINVAL, "bad mass_model");
     if (!finite(p->sigma) || !finite(p->gamma) || p->sigma < 0.0) return fail(MM_EINVAL, "sigma must be finite and >= 0, gamma finite");
@@ -711,7 +711,7 @@ int mm_params_default(mm_params *p)
     for (int k = 0; k < 4; ++k) p->ray_rect[k] = -1;
     p->far_order = 10;
     p->far_ratio = 0.15;
-    p->far_block = 8;
+    p->far_block = 0;
     return MM_OK;
 }
 
@@ -730,6 +730,7 @@ int mm_geometry_of(const mm_params *p, mm_geometry *out)
     out->nstar = g.nstar;
     out->disc_radius = g.radius;
     out->mu_theory = g.mu_theory;
+    out->far_block = far_block_for(g, *p, g.nstar);
     return MM_OK;
 }
 
@@ -953,6 +954,7 @@ int mm_map_fetch(mm_ctx *ctx, mm_map map, uint32_t *host_counts, size_t n_elems,
         st->mu_mean = (double)tot[0] / ((double)npix * M->p.nrays_per_pix);
         st->lens_splits = M->splits;
         st->far_bound = M->far_bound;
+        st->far_block = M->p.precision == MM_FAR32 ? far_block_for(M->g, M->p, M->lenses->n) : 0;
     }
     return MM_OK;
 }

@@ -134,3 +134,19 @@ def test_checked_build_exports_the_same_symbols():
     lib = ctypes.CDLL(path)
     for name in mm.EXPORTED:
         assert hasattr(lib, name), name
+
+
+def test_far_block_choice():
+    """far_block = 0: the block side that minimises the modelled time; given sides pass through."""
+    fig1 = dict(sigma=0.4, gamma=0.0, side=20.0, npix_side=1024, nrays=2000.0, precision=mm.MM_FAR32)
+    assert mm.mm_geometry_of(mm.params(**fig1))["far_block"] == 8
+    cfg2 = dict(sigma=0.8, gamma=0.3, smooth_frac=0.5, side=40.0, npix_side=2048, nrays=500.0, nstar=25000,
+                disc_radius=250.0, precision=mm.MM_FAR32)
+    assert mm.mm_geometry_of(mm.params(**cfg2))["far_block"] == 16
+    sides = [mm.mm_geometry_of(mm.params(**dict(fig1, nstar=n)))["far_block"] for n in (10 ** 3, 10 ** 5, 10 ** 7, 10 ** 9)]
+    assert sides == sorted(sides) and sides[-1] == 64             # more lenses: larger blocks
+    assert mm.mm_geometry_of(mm.params(**dict(fig1, far_block=3)))["far_block"] == 3
+    bad = mm.params(**fig1)
+    bad.far_block = -1
+    with pytest.raises(mm.MMError):
+        mm.mm_geometry_of(bad)

@@ -189,9 +189,25 @@ def test_block_aligned_parts_equal_one_shot(ctx):
     assert cfg["precision"] == mm.MM_FAR32
 
 
+def test_automatic_block_equals_the_chosen_explicit_block(ctx):
+    f = field0()
+    lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
+    auto = mm.params(**CFG0, precision=mm.MM_FAR32)                      # far_block = 0 by default
+    bt = mm.mm_geometry_of(auto)["far_block"]
+    got = []
+    for p in (auto, P(CFG0, dict(order=auto.far_order, ratio=auto.far_ratio, block_tiles=bt))):
+        m = mm.mm_shoot(ctx, lh, p)
+        counts, st = mm.mm_map_fetch(ctx, m)
+        mm.mm_release_map(ctx, m)
+        got.append(counts)
+        assert st["far_block"] == bt
+    np.testing.assert_array_equal(got[0], got[1])
+    mm.mm_release_lenses(ctx, lh)
+
+
 def test_far_parameters_validated_and_not_served(ctx):
     for bad in (dict(far_order=0), dict(far_order=33), dict(far_ratio=0.0), dict(far_ratio=0.95),
-                dict(far_block=0), dict(far_block=65)):
+                dict(far_block=-1), dict(far_block=65)):
         p = P(CFG0, FAR_DEFAULT)
         for k, v in bad.items():
             setattr(p, k, v)
