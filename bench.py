@@ -341,6 +341,35 @@ def profile_case(kind="fp32"):
     return 0
 
 
+def far_scaling(counts=(10 ** 4, 10 ** 5, 10 ** 6, 10 ** 7, 10 ** 8)):
+    """The far field (MM_FAR32, default order and ratio, automatic block) on the Fig. 1 geometry
+    (sigma = 0.4, 1024^2 pixels of 20 R_E, 1.31e10 rays) with N* lenses spread over the disc that
+    Eq. nstar gives for sigma_* = 0.4; one JSON line per N*. Lenses come from the library's seeded
+    generator; the time is block preparation + shoot (CUDA events), the best of two."""
+    import paper_1005_5198_gb300 as mm
+    mm.build()
+    ctx = mm.mm_init(0)
+    try:
+        for n in counts:
+            p = mm.params(**CFG1, nstar=n, precision=mm.MM_FAR32)
+            lh = mm.mm_create_lenses(ctx, p)
+            best, st = None, None
+            for _ in range(2):
+                m = mm.mm_shoot(ctx, lh, p)
+                ms = mm.mm_last_kernel_ms(ctx)[0]
+                _, st = mm.mm_map_fetch(ctx, m, want_counts=False)
+                mm.mm_release_map(ctx, m)
+                best = ms if best is None else min(best, ms)
+            mm.mm_release_lenses(ctx, lh)
+            print(json.dumps({"nstar": n, "ms": best, "rays": st["rays_shot"], "far_block": st["far_block"],
+                              "far_bound_re": st["far_bound"], "mu_mean": st["mu_mean"],
+                              "exact_interactions": st["interactions"],
+                              "equivalent_interactions_per_s": st["interactions"] / (best * 1e-3)}), flush=True)
+    finally:
+        mm.mm_destroy(ctx)
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -389,7 +418,11 @@ def main():
     ap.add_argument("--profile-case", nargs="?", const="fp32", choices=["fp32", "far"],
                     help="shoot a 4096^2-ray window of the Fig. 1 map three times, exactly (fp32) or with the "
                          "far-field approximation MM_FAR32 (far), for ncu captures, and exit")
+    ap.add_argument("--far-scaling", action="store_true",
+                    help="time the far field on the Fig. 1 geometry for N* = 1e4 .. 1e8 and exit")
     args = ap.parse_args()
+    if args.far_scaling:
+        return far_scaling()
     if args.impl == "reference":
         return run_reference(args)
     if args.profile_case:

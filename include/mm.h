@@ -105,7 +105,8 @@ typedef struct {
     int32_t  far_block;      /* MM_FAR32: block side in ray tiles, 1 .. 64, or 0 (default): the
                                 side that minimises a cost model of block preparation
                                 (blocks x N* x P) against near-lens work (rays x near lenses
-                                per block), from the whole ray grid, N* and the lens disc.
+                                per block), from the whole ray grid, the lens count and the
+                                largest lens distance from the origin.
                                 Blocks are counted from the origin of the shot rectangle */
 } mm_params;
 
@@ -144,7 +145,8 @@ typedef struct {
     double  disc_radius;
     double  mu_theory;  /* 1 / ((1 - sigma)^2 - gamma^2), Eq. mutheory */
     int32_t far_block;  /* MM_FAR32: the block side in tiles for these parameters (the automatic
-                           choice when far_block = 0, with N* above) */
+                           choice when far_block = 0, for the N* and disc radius above; a map
+                           shot with another lens set reports its own in mm_stats) */
 } mm_geometry;
 
 /* ---- context ------------------------------------------------------------ */

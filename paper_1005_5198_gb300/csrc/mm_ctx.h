@@ -77,6 +77,7 @@ struct LensSet {
     float4 *lh = nullptr;
     float *lmf = nullptr;
     bool unit_mass = true;
+    double radius = 0.0;                   // largest |x_i| of the set (the far field's density estimate)
     DeviceArena *arena = nullptr;
     ~LensSet();
     static size_t footprint(long long n);
@@ -163,9 +164,9 @@ void fill_desc(const MapObj &m, MapDesc *d);
 // once, to size the near lists); free them.
 int far_prepare(mm_ctx *ctx, MapObj &m, cudaStream_t s);
 void far_release(MapObj &m);
-// The far field's block side for parameters p, a grid g and N* lenses: p.far_block, or for 0
-// the side that minimises the modelled time (mm_far.cu).
-int far_block_for(const Geo &g, const mm_params &p, long long nstar);
+// The far field's block side for parameters p, a grid g and N* lenses in a disc of the given
+// radius: p.far_block, or for 0 the side that minimises the modelled time (mm_far.cu).
+int far_block_for(const Geo &g, const mm_params &p, long long nstar, double radius);
 int choose_variant(mm_ctx *ctx, const mm_params *p, const Geo &g);
 int scratch_reserve(mm_ctx *ctx, LaunchScratch *sc, int n_maps);
 void scratch_free(mm_ctx *ctx, LaunchScratch *sc);

@@ -666,12 +666,12 @@ constexpr double kSetupCost = 2.15e-12;      // seconds per block x lens x term
 constexpr double kNearCost = 0.81e-12;       // seconds per ray x near lens
 constexpr double kBlockCost = 2.0e-9;        // seconds per block
 
-int far_block_for(const Geo &g, const mm_params &p, long long nstar)
+int far_block_for(const Geo &g, const mm_params &p, long long nstar, double radius)
 {
     if (p.far_block > 0) return p.far_block;
     // the whole ray grid, so that every part of a map (mm_shoot_into) chooses alike
     const double rays = (double)g.nx * (double)g.ny;
-    const double density = g.radius > 0.0 ? (double)nstar / (M_PI * g.radius * g.radius) : 0.0;
+    const double density = radius > 0.0 ? (double)nstar / (M_PI * radius * radius) : 0.0;
     double best = 0.0;
     int best_bt = 8;
     for (int bt = 1; bt <= kFarMaxBlock; bt *= 2) {
@@ -697,7 +697,7 @@ int far_prepare(mm_ctx *ctx, MapObj &m, cudaStream_t s)
     FarDesc &F = m.far;
     F = FarDesc{};
     F.order = p.far_order;
-    F.bt = far_block_for(g, p, m.lenses->n);
+    F.bt = far_block_for(g, p, m.lenses->n, m.lenses->radius);
     const long long bw = 64LL * F.bt, bh = 32LL * F.bt;
     F.blocks_x = (g.ni + bw - 1) / bw;
     F.blocks_y = (g.nj + bh - 1) / bh;

@@ -304,6 +304,7 @@ int upload_lenses(mm_ctx *ctx, const double *x, const double *y, const double *m
     // padded to whole chunks, plus one extra chunk of null lenses
     L->n_pad = (n + kChunkLenses - 1) / kChunkLenses * kChunkLenses + kChunkLenses;
     L->unit_mass = unit;
+    for (long long k = 0; k < n; ++k) L->radius = std::max(L->radius, std::hypot(x[k], y[k]));
     const size_t nb = (size_t)std::max(n, 1LL) * sizeof(double);
     int rc;
     if ((rc = ctx->arena.alloc(nb, (void **)&L->dx)) || (rc = ctx->arena.alloc(nb, (void **)&L->dy)) ||
@@ -328,6 +329,7 @@ int make_lenses_from_params(mm_ctx *ctx, const mm_params *p, const Geo &g, cudaS
     generate_field(p->seed, g.nstar, g.radius, p->mass_model, p->mass_mu, p->mass_s, x, y, m);
     int rc = upload_lenses(ctx, x.data(), y.data(), m.data(), g.nstar, p->mass_model == MM_MASS_UNIT, s, out);
     if (rc) return rc;
+    (*out)->radius = g.radius;           // the disc the field fills (as mm_geometry_of reports it)
     MM_CUDA(cudaStreamSynchronize(s));   // host vectors go out of scope
     return MM_OK;
 }
@@ -730,7 +732,7 @@ int mm_geometry_of(const mm_params *p, mm_geometry *out)
     out->nstar = g.nstar;
     out->disc_radius = g.radius;
     out->mu_theory = g.mu_theory;
-    out->far_block = far_block_for(g, *p, g.nstar);
+    out->far_block = far_block_for(g, *p, g.nstar, g.radius);
     return MM_OK;
 }
 
@@ -954,7 +956,7 @@ int mm_map_fetch(mm_ctx *ctx, mm_map map, uint32_t *host_counts, size_t n_elems,
         st->mu_mean = (double)tot[0] / ((double)npix * M->p.nrays_per_pix);
         st->lens_splits = M->splits;
         st->far_bound = M->far_bound;
-        st->far_block = M->p.precision == MM_FAR32 ? far_block_for(M->g, M->p, M->lenses->n) : 0;
+        st->far_block = M->p.precision == MM_FAR32 ? far_block_for(M->g, M->p, M->lenses->n, M->lenses->radius) : 0;
     }
     return MM_OK;
 }
