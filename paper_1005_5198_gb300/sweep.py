@@ -52,7 +52,7 @@ def plan(sweep: str, npix: int, nrays: float, side: float = 20.0, precision: str
 
 
 def run(sweep: str, npix: int, nrays: float, max_interactions: float, device: int = 0, precision: str = "fp32c",
-        max_rays: float = 2e12):
+        max_rays: float = 2e12, compare_exact: bool = False):
     mm.build()
     ctx = mm.mm_init(device)
     out = []
@@ -76,6 +76,15 @@ def run(sweep: str, npix: int, nrays: float, max_interactions: float, device: in
             m = mm.mm_shoot(ctx, 0, pt["params"])
             ms, _ = mm.mm_last_kernel_ms(ctx)
             _, st = mm.mm_map_fetch(ctx, m, want_counts=False)
+            if compare_exact and pt["interactions"] <= max_interactions:
+                # the paper's map statistics (Sect. 3.1) against the exact FP32 map of the same lenses
+                q = pt["params"]
+                q.precision = mm.MM_FP32C
+                ex = mm.mm_shoot(ctx, 0, q)
+                row["exact_ms"] = mm.mm_last_kernel_ms(ctx)[0]
+                cmp = mm.mm_map_compare(ctx, m, ex)
+                row.update(rms_dm_vs_exact=cmp["rms_dm"], ks_p_vs_exact=cmp["ks_p"], ks_d_vs_exact=cmp["ks_d"])
+                mm.mm_release_map(ctx, ex)
             mm.mm_release_map(ctx, m)
             row.update(kernel_ms=ms, interactions_per_s=st["interactions"] / (ms * 1e-3) if ms > 0 else None,
                        mu_map=st["mu_mean"], lens_splits=st["lens_splits"], far_bound=st["far_bound"])
@@ -83,6 +92,21 @@ def run(sweep: str, npix: int, nrays: float, max_interactions: float, device: in
     finally:
         mm.mm_destroy(ctx)
     return out
+
+
+def compare_table(rows, sweep, npix, nrays):
+    head = (f"Sweep `{sweep}`, N_pix = {npix}^2, N_rays = {nrays:g}, L = 20 R_E: far field against the exact FP32 "
+            "map of the same lenses (Sect. 3.1 statistics)\n\n"
+            "| sigma | gamma | s | N* | far ms | exact ms | speed-up | bound (R_E) | RMS delta-m (mag) | K-S D | "
+            "K-S probability |\n|---|---|---|---|---|---|---|---|---|---|---|\n")
+    lines = []
+    for r in rows:
+        if "rms_dm_vs_exact" not in r:
+            continue
+        lines.append(f"| {r['sigma']} | {r['gamma']} | {r['smooth_frac']} | {r['nstar']} | {r['kernel_ms']:.1f} | "
+                     f"{r['exact_ms']:.1f} | {r['exact_ms'] / r['kernel_ms']:.1f}x | {r['far_bound']:.1g} | "
+                     f"{r['rms_dm_vs_exact']:.2e} | {r['ks_d_vs_exact']:.2e} | {r['ks_p_vs_exact']:.4f} |")
+    return head + "\n".join(lines) + "\n"
 
 
 def table(rows, sweep, npix, nrays, precision="fp32c"):
@@ -115,14 +139,22 @@ def main(argv=None):
     ap.add_argument("--max-interactions", type=float, default=2e14)
     ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp32c")
     ap.add_argument("--max-rays", type=float, default=2e12, help="far field: skip points with more rays")
+    ap.add_argument("--compare-exact", action="store_true",
+                    help="far field: also shoot the exact FP32 map of each point (up to --max-interactions) and "
+                         "report the paper's map statistics between the two")
     ap.add_argument("--json", action="store_true", help="print JSON lines instead of a table")
     a = ap.parse_args(argv)
-    rows = run(a.sweep, a.npix, a.nrays, a.max_interactions, precision=a.precision, max_rays=a.max_rays)
+    if a.compare_exact and a.precision != "far32":
+        raise SystemExit("--compare-exact needs --precision far32")
+    rows = run(a.sweep, a.npix, a.nrays, a.max_interactions, precision=a.precision, max_rays=a.max_rays,
+               compare_exact=a.compare_exact)
     if a.json:
         for r in rows:
             print(json.dumps(r))
     else:
         sys.stdout.write(table(rows, a.sweep, a.npix, a.nrays, a.precision))
+        if a.compare_exact:
+            sys.stdout.write("\n" + compare_table(rows, a.sweep, a.npix, a.nrays))
     return 0
 
 
