@@ -111,6 +111,8 @@ struct MapObj {
     int variant = 0;
     DeviceArena *arena = nullptr;
     ~MapObj();
+    // work items of the exact kernels and of debug dumps: tiles x lens segments (far-field
+    // launches take FarDesc::items, known after far_prepare)
     unsigned long long items() const { return g.tiles() * (unsigned long long)splits; }
     static size_t footprint(const mm_params *p, const Geo &g);
 };
@@ -161,8 +163,9 @@ int alloc_map(mm_ctx *ctx, const mm_params *p, const Geo &g, std::shared_ptr<Len
               std::shared_ptr<MapObj> *out, const MapObj *into = nullptr);
 void fill_desc(const MapObj &m, MapDesc *d);
 // MM_FAR32: build the block series and near lists of map m on stream s (synchronises
-// once, to size the near lists); free them.
-int far_prepare(mm_ctx *ctx, MapObj &m, cudaStream_t s);
+// once, to size the near lists; its kernels record failed bounds checks in *check in
+// checked builds); free them.
+int far_prepare(mm_ctx *ctx, MapObj &m, cudaStream_t s, unsigned int *check);
 void far_release(MapObj &m);
 // The far field's block side for parameters p, a grid g and N* lenses in a disc of the given
 // radius: p.far_block, or for 0 the side that minimises the modelled time (mm_far.cu).

@@ -565,8 +565,9 @@ __global__ void __launch_bounds__(kShootThreads, 2) k_shoot_far(const LaunchArgs
         const MapDesc &M = A.maps[lo];
         const FarDesc &F = far[lo];
         unsigned ci = 0, co = 0;
-        if (M.unit_mass) far_item<false>(A, F, M, g - F.item_begin, S, ci, co);
-        else far_item<true>(A, F, M, g - F.item_begin, S, ci, co);
+        const unsigned long long it = F.item_first + (g - F.item_begin);
+        if (M.unit_mass) far_item<false>(A, F, M, it, S, ci, co);
+        else far_item<true>(A, F, M, it, S, ci, co);
         ci = __reduce_add_sync(kFull, ci);
         co = __reduce_add_sync(kFull, co);
         if ((tid & 31) == 0) {
@@ -689,7 +690,7 @@ int far_block_for(const Geo &g, const mm_params &p, long long nstar, double radi
     return best_bt;
 }
 
-int far_prepare(mm_ctx *ctx, MapObj &m, cudaStream_t s)
+int far_prepare(mm_ctx *ctx, MapObj &m, cudaStream_t s, unsigned int *check)
 {
     far_release(m);
     const Geo &g = m.g;
@@ -719,7 +720,7 @@ int far_prepare(mm_ctx *ctx, MapObj &m, cudaStream_t s)
     if ((rc = ctx->arena.alloc(sizeof(unsigned), (void **)&m.far_bmax))) return rc;
     MM_CUDA(cudaMemsetAsync(m.far_bmax, 0, sizeof(unsigned), s));
     F.bound_max = m.far_bmax;
-    F.check = ctx->scratch.d_check;                 // the launch group's bounds-check word
+    F.check = check;                                // the caller's bounds-check word
     if (F.nblocks == 0) return MM_OK;
     if ((rc = ctx->arena.alloc((size_t)F.nblocks * F.stride * sizeof(float), (void **)&m.far_coef)) ||
         (rc = ctx->arena.alloc((size_t)(F.nblocks + 1) * sizeof(unsigned long long), (void **)&m.far_off)))

@@ -40,7 +40,8 @@ struct FarDesc {
     // work items of the production launch: groups of rows_per_item tile rows of a block
     int rows_per_item;                    // 1 or bt
     unsigned long long items;             // nblocks * bt / rows_per_item
-    unsigned long long item_begin;        // first item of this map in the launch
+    unsigned long long item_begin;        // first launch item of this map
+    unsigned long long item_first;        // the map item of that launch item (serving waves)
 };
 
 // Near-lens count of every block into a[b] (b < F.nblocks).

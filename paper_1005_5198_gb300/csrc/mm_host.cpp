@@ -290,6 +290,13 @@ size_t MapObj::footprint(const mm_params *p, const Geo &g)
     if (splits > 1)
         b += DeviceArena::round(g.tiles() * (size_t)splits * kTileRays * sizeof(float4)) +
              DeviceArena::round(g.tiles() * sizeof(unsigned));
+    if (p->precision == MM_FAR32) {              // block series, near-list offsets and lists (estimated)
+        const long long bt = far_block_for(g, *p, g.nstar, g.radius);
+        const size_t blocks = (size_t)((g.ni + 64 * bt - 1) / (64 * bt)) * (size_t)((g.nj + 32 * bt - 1) / (32 * bt));
+        const size_t stride = (size_t)((4 + 2 * (p->far_order - 1) + 3) & ~3);
+        b += DeviceArena::round(blocks * stride * sizeof(float)) + DeviceArena::round((blocks + 1) * 8) +
+             DeviceArena::round(blocks * 64 * sizeof(int)) + DeviceArena::round(sizeof(unsigned));
+    }
     return b;
 }
 
@@ -543,7 +550,7 @@ static int launch_group(mm_ctx *ctx, std::vector<MapObj *> &group, int precision
     unsigned long long far_items = 0;
     if (far) {
         for (size_t k = 0; k < group.size(); ++k) {
-            if ((rc = far_prepare(ctx, *group[k], s))) return rc;
+            if ((rc = far_prepare(ctx, *group[k], s, sc->d_check))) return rc;
             group[k]->far.item_begin = far_items;
             far_items += group[k]->far.items;
             sc->h_far[k] = group[k]->far;

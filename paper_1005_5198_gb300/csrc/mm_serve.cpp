@@ -6,8 +6,12 @@
 // field, upload it and allocate the map, off the scheduler's critical path, and
 // hand the request to the scheduler as "ready".
 //
+// Far-field maps (MM_FAR32) are served too: their workers also build the block
+// series and near lists, and their work items are the far field's block rows.
+//
 // Scheduling: ready maps are shot in waves. A wave is one persistent launch of
-// the FP32 kernel over a slice of the ray tiles of EVERY active map,
+// the FP32 kernel over a slice of the ray tiles of EVERY active map (plus one
+// launch each for the FP64 and the far-field maps of the wave),
 // replayed from a captured CUDA graph whose descriptor buffer the host rewrites
 // before each replay. The slice sizes share a work budget evenly between the
 // active maps (processor sharing), and a wave always holds at least 4 tiles per
@@ -83,7 +87,8 @@ struct Server {
     cudaStream_t stream[2] = {nullptr, nullptr};     // waves alternate, so one fills the other's tail
     cudaStream_t capture = nullptr;
     cudaStream_t upload[kAdmitWorkers] = {};
-    LaunchScratch sc[2], sc64[2];
+    LaunchScratch sc[2], sc64[2], scfar[2];          // per wave buffer: FP32, FP64 and far-field maps
+    unsigned int *far_check = nullptr;               // bounds-check word of the workers' far preparation
     cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [buffer][split kernel]
     int graph_cap[2][2] = {{0, 0}, {0, 0}};
     cudaEvent_t ev_start[2] = {nullptr, nullptr}, ev_end[2] = {nullptr, nullptr};
@@ -131,6 +136,7 @@ static void admit_worker(Server *S, int idx)
         if (!L) rc = make_lenses_from_params(ctx, &r->p, r->g, S->upload[idx], &L);
         std::shared_ptr<MapObj> M;
         if (!rc) rc = alloc_map(ctx, &r->p, r->g, L, S->upload[idx], &M);
+        if (!rc && r->p.precision == MM_FAR32) rc = far_prepare(ctx, *M, S->upload[idx], S->far_check);
         if (!rc) {
             const cudaError_t e = cudaStreamSynchronize(S->upload[idx]);
             if (e != cudaSuccess) rc = cuda_fail(e, "admission upload");
@@ -143,7 +149,8 @@ static void admit_worker(Server *S, int idx)
             finish(S, r, 3, rc, msg);
         } else {
             r->map = M;
-            r->tiles = M->items();                       // work items: tiles x lens segments
+            // work items: tiles x lens segments, or the far field's block rows
+            r->tiles = r->p.precision == MM_FAR32 ? M->far.items : M->items();
             S->ready.push_back(r);
         }
         S->cv.notify_all();
@@ -151,9 +158,16 @@ static void admit_worker(Server *S, int idx)
     }
 }
 
-// Interactions of one work item (a tile, or one lens segment of a split tile).
+// A far-field ray costs about as much device time as this many exact interactions
+// (80 ms for the 1.3e10 rays of the Fig. 1 map, against 0.185 ps per interaction).
+constexpr double kFarRayInteractions = 33.0;
+
+// Interactions of one work item (a tile, or one lens segment of a split tile), or their
+// equivalent for a far-field item (rows of tiles of a block).
 static double tile_cost(const Request &r)
 {
+    if (r.p.precision == MM_FAR32)
+        return (double)kTileRays * (double)r.map->far.rows_per_item * (double)r.map->far.bt * kFarRayInteractions;
     const long long n = r.map->splits > 1 ? r.map->seg_lenses : r.map->lenses->n;
     return (double)kTileRays * (double)std::max(n, 8LL);
 }
@@ -227,21 +241,35 @@ static int launch_wave(Server *S, Wave *w)
     NvtxRange nvtx_("mm serve wave");
     mm_ctx *ctx = S->ctx;
     const int b = w->buf;
-    int n32 = 0, n64 = 0;
-    for (auto &it : w->items) (it.req->p.precision == MM_FP64 ? n64 : n32)++;
+    int n32 = 0, n64 = 0, nfar = 0;
+    for (auto &it : w->items) {
+        const int pr = it.req->p.precision;
+        (pr == MM_FP64 ? n64 : pr == MM_FAR32 ? nfar : n32)++;
+    }
     int rc;
     if ((rc = scratch_reserve(ctx, &S->sc[b], std::max(S->max_active, n32)))) return rc;
     if (n64 && (rc = scratch_reserve(ctx, &S->sc64[b], n64))) return rc;
+    if (nfar && (rc = scratch_reserve(ctx, &S->scfar[b], nfar))) return rc;
     // order: decreasing per-tile cost within each precision (large tiles first)
     std::vector<size_t> idx(w->items.size());
     for (size_t k = 0; k < idx.size(); ++k) idx[k] = k;
     std::stable_sort(idx.begin(), idx.end(),
                      [&](size_t a, size_t c) { return tile_cost(*w->items[a].req) > tile_cost(*w->items[c].req); });
-    unsigned long long tot32 = 0, tot64 = 0;
-    int k32 = 0, k64 = 0;
+    unsigned long long tot32 = 0, tot64 = 0, totfar = 0;
+    int k32 = 0, k64 = 0, kfar = 0;
     for (size_t q : idx) {
         WaveItem &it = w->items[q];
         Request &r = *it.req;
+        if (r.p.precision == MM_FAR32) {            // far field: its own descriptors and item range
+            fill_desc(*r.map, &S->scfar[b].h_maps[kfar]);
+            FarDesc &F = S->scfar[b].h_far[kfar++];
+            F = r.map->far;
+            F.item_begin = totfar;
+            F.item_first = r.cursor;
+            totfar += it.tiles;
+            r.cursor += it.tiles;
+            continue;
+        }
         const bool fp64 = r.p.precision == MM_FP64;
         MapDesc *d = fp64 ? &S->sc64[b].h_maps[k64++] : &S->sc[b].h_maps[k32++];
         fill_desc(*r.map, d);
@@ -279,6 +307,23 @@ static int launch_wave(Server *S, Wave *w)
         cudaError_t e = launch_shoot_fp64(a, ctx->sms * shoot_ctas_per_sm(true, 0), false, st);
         if (e != cudaSuccess) return cuda_fail(e, "fp64 wave launch");
     }
+    if (nfar) {
+        LaunchScratch *sc = &S->scfar[b];
+        sc->h_hdr->total_work = totfar;
+        sc->h_hdr->n_maps = nfar;
+        cudaMemcpyAsync(sc->d_hdr, sc->h_hdr, sizeof(WorkHeader), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(sc->d_maps, sc->h_maps, (size_t)nfar * sizeof(MapDesc), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(sc->d_far, sc->h_far, (size_t)nfar * sizeof(FarDesc), cudaMemcpyHostToDevice, st);
+        cudaMemsetAsync(sc->d_counter, 0, sizeof(unsigned long long), st);
+        LaunchArgs a{};
+        a.hdr = sc->d_hdr;
+        a.maps = sc->d_maps;
+        a.work_counter = sc->d_counter;
+        a.check = sc->d_check;
+        const long long grid = std::min((long long)totfar, (long long)ctx->sms * far_ctas_per_sm());
+        cudaError_t e = launch_shoot_far(a, sc->d_far, totfar, (int)std::max(1LL, grid), false, st);
+        if (e != cudaSuccess) return cuda_fail(e, "far-field wave launch");
+    }
     cudaEventRecord(S->ev_end[b], st);
     // a finishing map may have earlier tiles in the previous wave, which runs on the
     // other stream: its completion event follows both
@@ -300,10 +345,14 @@ static void complete_wave(Server *S, Wave &w, std::unique_lock<std::mutex> &lk)
     if (e == cudaSuccess) cudaEventElapsedTime(&ms, w.start, w.end);
 #ifdef MM_CHECKS
     // checked builds: a failed bounds check of any wave (never reset) stops the server
-    unsigned bad = 0, bad64 = 0;
+    unsigned bad = 0, bad64 = 0, badfar = 0, badprep = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&bad, S->sc[w.buf].d_check, sizeof(bad), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && S->sc64[w.buf].d_check)
         e = cudaMemcpy(&bad64, S->sc64[w.buf].d_check, sizeof(bad64), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && S->scfar[w.buf].d_check)
+        e = cudaMemcpy(&badfar, S->scfar[w.buf].d_check, sizeof(badfar), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&badprep, S->far_check, sizeof(badprep), cudaMemcpyDeviceToHost);
+    bad64 = bad64 ? bad64 : badfar ? badfar : badprep;
 #endif
     lk.lock();
     if (e != cudaSuccess) {
@@ -397,6 +446,8 @@ int server_start(mm_ctx *ctx)
         e = cudaEventCreate(&S->ev_start[b]);
         if (e == cudaSuccess) e = cudaEventCreate(&S->ev_end[b]);
     }
+    if (e == cudaSuccess) e = cudaMalloc(&S->far_check, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(S->far_check, 0, sizeof(unsigned int));
     if (e != cudaSuccess) {
         delete S;
         return cuda_fail(e, "server streams/events");
@@ -427,9 +478,11 @@ void server_stop(mm_ctx *ctx)
             if (S->gexec[b][k]) cudaGraphExecDestroy(S->gexec[b][k]);
         scratch_free(ctx, &S->sc[b]);
         scratch_free(ctx, &S->sc64[b]);
+        scratch_free(ctx, &S->scfar[b]);
         cudaEventDestroy(S->ev_start[b]);
         cudaEventDestroy(S->ev_end[b]);
     }
+    if (S->far_check) cudaFree(S->far_check);
     cudaStreamDestroy(S->stream[0]);
     cudaStreamDestroy(S->stream[1]);
     cudaStreamDestroy(S->capture);
@@ -474,7 +527,6 @@ int mm_submit(mm_ctx *ctx, mm_lenses lenses, const mm_params *p, mm_req *out)
     auto r = std::make_shared<Request>();
     int rc = compute_geo(p, &r->g);
     if (rc) return rc;
-    if (p->precision == MM_FAR32) return fail(MM_EINVAL, "served maps are MM_FP32C or MM_FP64 (shoot MM_FAR32 with mm_shoot)");
     r->p = *p;
     if (lenses) {
         std::lock_guard<std::mutex> lk(ctx->mu);

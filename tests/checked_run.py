@@ -60,9 +60,10 @@ def main():
         got, st = mm.mm_map_fetch(ctx, m)
         mm.mm_release_map(ctx, m)
         close(got, ref, tot["shot"], "parts")
-        # served requests (FP32 and FP64 waves)
+        # served requests (FP32, FP64 and far-field waves)
         reqs = [mm.mm_submit(ctx, lh, mm.params(**CFG0, precision=p)) for p in (mm.MM_FP32C, mm.MM_FP64)] + \
-               [mm.mm_submit(ctx, 0, mm.params(**SPLIT, nstar=2000, disc_radius=8.0))]
+               [mm.mm_submit(ctx, 0, mm.params(**SPLIT, nstar=2000, disc_radius=8.0)),
+                mm.mm_submit(ctx, lb, mm.params(**SPLIT, precision=mm.MM_FAR32, far_ratio=0.05))]
         for r in reqs:
             h = mm.mm_wait(ctx, r, 120.0)
             mm.mm_release_map(ctx, h)

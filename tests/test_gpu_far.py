@@ -211,7 +211,7 @@ def test_automatic_block_equals_the_chosen_explicit_block(ctx):
     mm.mm_release_lenses(ctx, lh)
 
 
-def test_far_parameters_validated_and_not_served(ctx):
+def test_far_parameters_validated(ctx):
     for bad in (dict(far_order=0), dict(far_order=33), dict(far_ratio=0.0), dict(far_ratio=0.95),
                 dict(far_block=-1), dict(far_block=65)):
         p = P(CFG0, FAR_DEFAULT)
@@ -220,9 +220,35 @@ def test_far_parameters_validated_and_not_served(ctx):
         with pytest.raises(mm.MMError) as e:
             mm.mm_shoot(ctx, 0, p)
         assert e.value.code == mm.MM_EINVAL
-    with pytest.raises(mm.MMError) as e:
-        mm.mm_submit(ctx, 0, P(CFG0, FAR_DEFAULT))
-    assert e.value.code == mm.MM_EINVAL
+        with pytest.raises(mm.MMError) as e:
+            mm.mm_submit(ctx, 0, p)
+        assert e.value.code == mm.MM_EINVAL
+
+
+def test_served_far_maps_identical_to_alone(ctx):
+    """Far-field requests served together with exact ones (waves carry slices of each map's
+    block rows) give the maps shot alone, bit for bit."""
+    mm.mm_serve_config(ctx, max_active=6, wave_ms=0.5)
+    cases = [(dict(CFG0), dict(order=10, ratio=0.15, block_tiles=0)),
+             (dict(CFG0, sigma=0.5, gamma=0.1), dict(order=12, ratio=0.3, block_tiles=2)),
+             (dict(sigma=0.55, gamma=0.2, smooth_frac=0.3, side=6.0, npix_side=96, nrays=60.0),
+              dict(order=8, ratio=0.2, block_tiles=1)),
+             (dict(CFG0, sigma=0.3), None)]                                # an exact map in the mix
+    f = synth.lens_field(300, 12.0, 7, model=synth.MASS_LOGNORMAL)
+    lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
+    reqs, alone = [], []
+    for cfg, far in cases * 2:
+        p = P(cfg, far) if far else mm.params(**cfg)
+        m = mm.mm_shoot(ctx, lh, p)
+        alone.append(mm.mm_map_fetch(ctx, m)[0].copy())
+        mm.mm_release_map(ctx, m)
+        reqs.append(mm.mm_submit(ctx, lh, p))
+    for r, a in zip(reqs, alone):
+        m = mm.mm_wait(ctx, r, timeout_s=120)
+        got, st = mm.mm_map_fetch(ctx, m)
+        np.testing.assert_array_equal(got, a)
+        mm.mm_release_map(ctx, m)
+    mm.mm_release_lenses(ctx, lh)
 
 
 def test_batch_mixes_precisions(ctx):
