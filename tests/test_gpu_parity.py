@@ -492,3 +492,45 @@ def test_large_lens_count_streams_through_chunks(ctx):
                                            far_ratio=far["ratio"], far_block=far["block_tiles"]), ii, jj)
     a_o, _, _, _ = oracle.far_rays(oracle_cfg(cfg), f, far, ii, jj)
     assert np.hypot(*(a_g - a_o).T).max() <= 1e-5
+
+
+def test_serving_stress_mixed_precisions_with_cancellations(ctx):
+    """96 requests of FP32, FP64 and far-field maps of varied shape submitted at once to a server
+    of 5 slots, every 7th cancelled right away (if still queued). Every request ends exactly once:
+    cancelled before it ran, or done with exact totals; a sample equals the same map shot alone."""
+    mm.mm_serve_config(ctx, max_active=5, wave_ms=1.0)
+    f = synth.lens_field(200, 10.0, 31, model=synth.MASS_LOGNORMAL)
+    lh = lens(ctx, f)
+    kinds = [dict(), dict(precision=mm.MM_FP64), dict(precision=mm.MM_FAR32)]
+    rng = np.random.default_rng(5)
+    reqs = []
+    for k in range(96):
+        sigma = float(rng.uniform(0.2, 0.55))
+        cfg = dict(sigma=sigma, gamma=float(rng.uniform(0.0, 0.25)), smooth_frac=float(rng.uniform(0.0, 0.5)),
+                   side=3.0, npix_side=int(rng.choice([32, 48, 64])), nrays=float(rng.choice([10.0, 20.0])))
+        p = P(cfg, **kinds[k % 3])
+        r = mm.mm_submit(ctx, lh, p)
+        cancelled = False
+        if k % 7 == 3:
+            try:
+                mm.mm_cancel(ctx, r)
+                cancelled = True
+            except mm.MMError as e:                      # already admitted: it runs to completion
+                assert e.code == mm.MM_EBUSY
+        reqs.append((r, p, cancelled))
+    assert any(c for _, _, c in reqs)
+    for k, (r, p, cancelled) in enumerate(reqs):
+        if cancelled:
+            with pytest.raises(mm.MMError) as e:
+                mm.mm_wait(ctx, r, timeout_s=60)
+            assert e.value.code == mm.MM_ECANCELED
+            continue
+        m = mm.mm_wait(ctx, r, timeout_s=300)
+        got, st = mm.mm_map_fetch(ctx, m)
+        check_totals(got, st, st["nx"] * st["ny"])
+        mm.mm_release_map(ctx, m)
+        if k % 8 == 0:
+            a = mm.mm_shoot(ctx, lh, p)
+            alone, _ = mm.mm_map_fetch(ctx, a)
+            mm.mm_release_map(ctx, a)
+            np.testing.assert_array_equal(got, alone)
