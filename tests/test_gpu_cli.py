@@ -34,3 +34,14 @@ def test_checkpoint_of_another_config_is_refused(tmp_path):
     assert cli.main(base + ["--max-parts-this-run", "1"]) == cli.EXIT_INTERRUPTED
     with pytest.raises(SystemExit):
         cli.main(base + ["--set", "sigma=0.45"])
+
+
+def test_image_and_lightcurve(tmp_path):
+    img = tmp_path / "m.png"
+    assert cli.main(["shoot", "--config", "small", "--out", str(tmp_path / "m.npy"), "--image", str(img)]) == 0
+    assert img.read_bytes()[:8] == b"\x89PNG\r\n\x1a\n"
+    lc_path = tmp_path / "lc.npy"
+    assert cli.main(["lightcurve", "--config", "small", "--profile", "gaussian", "--size", "0.05",
+                     "--start=-1.5,0", "--end=1.5,0.2", "--points", "300", "--out", str(lc_path)]) == 0
+    lc = np.load(lc_path)
+    assert lc.shape == (300,) and np.isfinite(lc).all() and (lc > 0).all()
