@@ -1,6 +1,7 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
-Tolerances (stated for the FP32 compensated path and derived in the design doc):
+Tolerances for the FP32 compensated path (rays passing very close to a lens
+carry the largest FP32 error, about 6e-6 Einstein radii on these fields):
   * per-ray deflection: max |alpha_gpu - alpha_oracle| <= 1e-5 Einstein radii;
   * rays binned to a different pixel than the oracle's: <= 1e-4 of the rays;
   * maps: sum |N_gpu - N_oracle| <= 2e-4 of the rays shot (a misbinned ray
