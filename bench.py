@@ -415,6 +415,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the far-field, batch and serving phases")
     ap.add_argument("--wave-ms", type=float, default=12.0, help="serving: target device time of one wave")
+    ap.add_argument("--serve-priority", type=float, default=0.8,
+                    help="serving: share of each wave given shortest remaining work first (0: processor sharing)")
     ap.add_argument("--profile-case", nargs="?", const="fp32", choices=["fp32", "far"],
                     help="shoot a 4096^2-ray window of the Fig. 1 map three times, exactly (fp32) or with the "
                          "far-field approximation MM_FAR32 (far), for ncu captures, and exit")
@@ -523,6 +525,7 @@ def main():
         extra["far_field"] = far_phase(mm, ctx, lh, sum(kern_ms) / len(kern_ms))
         extra["batch"] = batch_phase(mm, ctx)
         mm.mm_serve_config(ctx, max_active=64, wave_ms=args.wave_ms)
+        mm.mm_serve_priority(ctx, args.serve_priority)
         capacity = extra["batch"]["batched_interactions_per_s"]          # the same mix shape, batched
         mean_inter = np.mean([i for _, i in scaled_mix(200, 6, large_every=10)])
         lam = 0.7 * capacity / mean_inter
@@ -530,7 +533,7 @@ def main():
             "workload": "Poisson arrivals of the scaled config-3 mix plus every 10th request 4x the pixels; "
                         "mm_submit/mm_poll continuous batching, latency from submit to completion",
             "capacity_interactions_per_s": capacity, "mean_request_interactions": float(mean_inter),
-            "wave_ms": args.wave_ms,
+            "wave_ms": args.wave_ms, "priority_share": args.serve_priority,
             "at_70pct_capacity": serve_phase(mm, ctx, lam, 20.0, 7),
             "overload_3x": serve_phase(mm, ctx, 3.0 * lam, 5.0, 8)}
 

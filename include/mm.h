@@ -284,6 +284,28 @@ int mm_req_times(mm_ctx *ctx, mm_req req, double *t_queue, double *t_total);
  * waves below ~8 ms lose throughput to launch overhead. */
 int mm_serve_config(mm_ctx *ctx, int32_t max_active, int32_t max_queued, double wave_ms);
 
+/* How a wave's work budget (about wave_ms of device time) is divided between
+ * the admitted maps: the share priority_share (0..1, default 0.8) goes to the
+ * maps in increasing order of remaining work (shortest remaining work first),
+ * the rest evenly to all of them (processor sharing); every map with work
+ * left gets at least one work item per wave, so none starves. 0 is plain
+ * processor sharing. Admission from the queue stays first come, first served.
+ * Applies from the next wave. Errors: MM_EINVAL (share outside [0, 1]). */
+int mm_serve_priority(mm_ctx *ctx, double priority_share);
+
+/* The division above as a pure host function (no context, no GPU), for
+ * inspection and tests. n maps with left[k] work items remaining, each worth
+ * cost[k] > 0 interactions (or their device-time equivalent); budget > 0 in
+ * the same unit. Writes take[k], the items of map k in the wave: a
+ * priority_share of the budget to the maps in increasing order of
+ * left[k] * cost[k] (ties by index), each taking up to ceil(rest / cost[k])
+ * items while budget remains, then floor((1 - priority_share) budget /
+ * (n cost[k])) more items, at least one, per map; take[k] <= left[k]. The
+ * budget is doubled (up to 64 times) until the wave holds at least
+ * min(min_items, sum of left) items. Errors: MM_EINVAL. */
+int mm_serve_plan(const uint64_t *left, const double *cost, int32_t n, double budget, double priority_share,
+                  uint64_t min_items, uint64_t *take);
+
 /* ---- map statistics (Sect. 3.1, Eq. deltam) --------------------------------
  * The paper compares maps by the RMS difference of Delta m = -2.5 log10(mu)
  * (mu = N / N_rays per pixel) and by a two-sample Kolmogorov-Smirnov test on the

@@ -109,6 +109,8 @@ def _load():
         "mm_cancel": [C.c_void_p, U64],
         "mm_req_times": [C.c_void_p, U64, P(D), P(D)],
         "mm_serve_config": [C.c_void_p, C.c_int32, C.c_int32, D],
+        "mm_serve_priority": [C.c_void_p, D],
+        "mm_serve_plan": [P(C.c_uint64), P(D), C.c_int32, D, D, C.c_uint64, P(C.c_uint64)],
         "mm_autotune": [C.c_void_p, P(mm_params), P(C.c_int32)],
         "mm_set_variant": [C.c_void_p, C.c_int32],
         "mm_variant_count": [],
@@ -325,6 +327,23 @@ def mm_serve_config(ctx: Ctx, max_active: int = 0, max_queued: int = 0, wave_ms:
     _check(_load().mm_serve_config(ctx.handle, max_active, max_queued, wave_ms), "mm_serve_config")
 
 
+def mm_serve_priority(ctx: Ctx, priority_share: float) -> None:
+    _check(_load().mm_serve_priority(ctx.handle, priority_share), "mm_serve_priority")
+
+
+def mm_serve_plan(left, cost, budget: float, priority_share: float, min_items: int = 0) -> np.ndarray:
+    """Items per map of one serving wave (host only, no GPU): see mm_serve_plan in mm.h."""
+    left = np.ascontiguousarray(left, dtype=np.uint64)
+    cost = np.ascontiguousarray(cost, dtype=np.float64)
+    if left.shape != cost.shape or left.ndim != 1:
+        raise ValueError("left and cost must be 1-D arrays of the same length")
+    take = np.zeros_like(left)
+    u64p, f64p = C.POINTER(C.c_uint64), C.POINTER(C.c_double)
+    _check(_load().mm_serve_plan(left.ctypes.data_as(u64p), cost.ctypes.data_as(f64p), len(left), budget,
+                                 priority_share, min_items, take.ctypes.data_as(u64p)), "mm_serve_plan")
+    return take
+
+
 def mm_autotune(ctx: Ctx, p: mm_params) -> int:
     v = C.c_int32()
     _check(_load().mm_autotune(ctx.handle, C.byref(p), C.byref(v)), "mm_autotune")
@@ -423,7 +442,7 @@ EXPORTED = [
     "mm_lenses_fetch", "mm_lenses_count", "mm_release_lenses", "mm_shoot", "mm_shoot_batch", "mm_shoot_into",
     "mm_map_restore", "mm_map_fetch",
     "mm_map_device_ptr", "mm_release_map", "mm_submit", "mm_poll", "mm_wait", "mm_cancel", "mm_req_times",
-    "mm_serve_config", "mm_autotune", "mm_set_variant", "mm_variant_count", "mm_variant_name", "mm_set_layout",
+    "mm_serve_config", "mm_serve_priority", "mm_serve_plan", "mm_autotune", "mm_set_variant", "mm_variant_count", "mm_variant_name", "mm_set_layout",
     "mm_get_layout", "mm_layout_count", "mm_layout_name", "mm_debug_deflect",
     "mm_last_kernel_ms", "mm_shoot_noalloc", "mm_map_compare", "mm_map_convolve",
     "mm_map_lightcurve", "mm_strerror", "mm_last_error",

@@ -13,10 +13,13 @@
 // the FP32 kernel over a slice of the ray tiles of EVERY active map (plus one
 // launch each for the FP64 and the far-field maps of the wave),
 // replayed from a captured CUDA graph whose descriptor buffer the host rewrites
-// before each replay. The slice sizes share a work budget evenly between the
-// active maps (processor sharing), and a wave always holds at least 4 tiles per
-// CTA of the grid when the maps have that much work left, so maps with few
-// tiles and many lenses cannot leave the GPU idle. Requests that arrive while
+// before each replay. The slice sizes divide a work budget between the active
+// maps: a priority share goes to the maps with the least work left (shortest
+// remaining work first, which cuts both the median and the tail latency of a
+// mixed stream), the rest evenly (processor sharing, which keeps every map
+// moving). A wave always holds at least 4 tiles per CTA of the grid when the
+// maps have that much work left, so maps with few tiles and many lenses cannot
+// leave the GPU idle. Requests that arrive while
 // waves run join the next wave, so their work overlaps on the device with the
 // maps already running. Two waves are kept in flight, on two streams, so that the
 // next wave's CTAs start as the current wave's last tiles drain; a map is complete
@@ -84,6 +87,7 @@ struct Server {
     std::unordered_map<uint64_t, std::shared_ptr<Request>> reqs;
     int max_active = 64, max_queued = 1 << 16;
     double wave_ms = 12.0;             // shorter waves cut latency, below ~8 ms the launch overhead shows
+    double priority = 0.8;             // share of a wave's budget given shortest remaining work first
     cudaStream_t stream[2] = {nullptr, nullptr};     // waves alternate, so one fills the other's tail
     cudaStream_t capture = nullptr;
     cudaStream_t upload[kAdmitWorkers] = {};
@@ -161,15 +165,20 @@ static void admit_worker(Server *S, int idx)
 // A far-field ray costs about as much device time as this many exact interactions
 // (80 ms for the 1.3e10 rays of the Fig. 1 map, against 0.185 ps per interaction).
 constexpr double kFarRayInteractions = 33.0;
+// An interaction of the plain FP64 kernel costs about this many of the FP32 kernel's
+// (DFMA runs at 1/64 of the FP32 lane rate; measured 4.1e10 against 5.4e12 per second).
+constexpr double kFp64Interactions = 130.0;
 
-// Interactions of one work item (a tile, or one lens segment of a split tile), or their
-// equivalent for a far-field item (rows of tiles of a block).
+// Device time of one work item (a tile, or one lens segment of a split tile) in FP32
+// interactions, or their equivalent for an FP64 tile or a far-field item (rows of tiles
+// of a block).
 static double tile_cost(const Request &r)
 {
     if (r.p.precision == MM_FAR32)
         return (double)kTileRays * (double)r.map->far.rows_per_item * (double)r.map->far.bt * kFarRayInteractions;
     const long long n = r.map->splits > 1 ? r.map->seg_lenses : r.map->lenses->n;
-    return (double)kTileRays * (double)std::max(n, 8LL);
+    const double c = (double)kTileRays * (double)std::max(n, 8LL);
+    return r.p.precision == MM_FP64 ? c * kFp64Interactions : c;
 }
 
 static int capture_graph(Server *S, int b, int split)
@@ -202,8 +211,40 @@ static int capture_graph(Server *S, int b, int split)
     return MM_OK;
 }
 
-// Slice sizes for the next wave: an even share of the work budget per live map, then
-// doubled shares until the wave holds at least `min_tiles` tiles (or all that is left).
+// Items of each map in one wave (mm_serve_plan): a `priority` share of the budget to
+// the maps in increasing order of remaining work, the rest evenly, at least one item per
+// map; the budget doubles until the wave holds min(min_items, all that is left).
+static void plan_slices(const unsigned long long *left, const double *cost, int n, double budget, double priority,
+                        unsigned long long min_items, unsigned long long *take)
+{
+    unsigned long long left_all = 0;
+    for (int k = 0; k < n; ++k) left_all += left[k];
+    std::vector<int> order(n);
+    for (int k = 0; k < n; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return (double)left[a] * cost[a] < (double)left[b] * cost[b]; });
+    for (int round = 0; round < 64; ++round) {
+        unsigned long long sum = 0;
+        double rest = priority * budget;
+        for (int k = 0; k < n; ++k) take[k] = 0;
+        for (int q = 0; q < n && rest > 0.0; ++q) {
+            const int k = order[q];
+            const double want = std::min(std::ceil(rest / cost[k]), 1e15);
+            take[k] = std::min(left[k], (unsigned long long)want);
+            rest -= (double)take[k] * cost[k];
+        }
+        const double even = (1.0 - priority) * budget / (double)std::max(n, 1);
+        for (int k = 0; k < n; ++k) {
+            const double want = std::min(std::max(1.0, std::floor(even / cost[k])), 1e15);
+            take[k] = std::min(left[k], take[k] + (unsigned long long)want);
+            sum += take[k];
+        }
+        if (sum >= std::min(min_items, left_all)) break;
+        budget *= 2.0;
+    }
+}
+
+// Slices of the next wave over the live maps.
 static void plan_wave(Server *S, Wave *w)
 {
     std::vector<std::shared_ptr<Request>> live;
@@ -212,26 +253,20 @@ static void plan_wave(Server *S, Wave *w)
     if (live.empty()) return;
     const unsigned long long min_tiles =
         4ULL * (unsigned long long)S->ctx->sms * (unsigned long long)shoot_ctas_per_sm(false, S->ctx->layout);
-    unsigned long long left_all = 0;
-    for (auto &r : live) left_all += r->tiles - r->cursor;
-    double share = std::max(1.0, S->wave_ms * S->rate) / (double)live.size();
-    std::vector<unsigned long long> take(live.size(), 0);
-    for (int round = 0; round < 64; ++round) {
-        unsigned long long sum = 0;
-        for (size_t k = 0; k < live.size(); ++k) {
-            const unsigned long long left = live[k]->tiles - live[k]->cursor;
-            const double want = std::max(1.0, std::floor(share / tile_cost(*live[k])));
-            take[k] = std::min(left, (unsigned long long)std::min(want, 1e15));
-            sum += take[k];
-        }
-        if (sum >= std::min(min_tiles, left_all)) break;
-        share *= 2.0;
+    const int n = (int)live.size();
+    std::vector<unsigned long long> left(n), take(n);
+    std::vector<double> cost(n);
+    for (int k = 0; k < n; ++k) {
+        left[k] = live[k]->tiles - live[k]->cursor;
+        cost[k] = tile_cost(*live[k]);
     }
-    for (size_t k = 0; k < live.size(); ++k) {
+    plan_slices(left.data(), cost.data(), n, std::max(1.0, S->wave_ms * S->rate), S->priority, min_tiles,
+                take.data());
+    for (int k = 0; k < n; ++k) {
         if (!take[k]) continue;
         w->items.push_back(WaveItem{live[k], take[k], live[k]->cursor + take[k] == live[k]->tiles});
         w->tiles += take[k];
-        w->interactions += (double)take[k] * tile_cost(*live[k]);
+        w->interactions += (double)take[k] * cost[k];
     }
 }
 
@@ -518,6 +553,31 @@ int mm_serve_config(mm_ctx *ctx, int32_t max_active, int32_t max_queued, double 
     if (max_queued) S->max_queued = max_queued;
     if (wave_ms > 0.0) S->wave_ms = wave_ms;
     S->admit_cv.notify_all();
+    return MM_OK;
+}
+
+int mm_serve_priority(mm_ctx *ctx, double priority_share)
+{
+    if (!ctx || !(priority_share >= 0.0 && priority_share <= 1.0)) return fail(MM_EINVAL, "priority share outside [0, 1]");
+    int rc = server_start(ctx);
+    if (rc) return rc;
+    Server *S = ctx->server;
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->priority = priority_share;
+    return MM_OK;
+}
+
+int mm_serve_plan(const uint64_t *left, const double *cost, int32_t n, double budget, double priority_share,
+                  uint64_t min_items, uint64_t *take)
+{
+    if (n < 0 || (n > 0 && (!left || !cost || !take)) || !(budget > 0.0) ||
+        !(priority_share >= 0.0 && priority_share <= 1.0))
+        return fail(MM_EINVAL, "bad plan arguments");
+    for (int k = 0; k < n; ++k)
+        if (!(cost[k] > 0.0) || !std::isfinite(cost[k])) return fail(MM_EINVAL, "work item cost must be positive");
+    static_assert(sizeof(unsigned long long) == sizeof(uint64_t), "item counts are 64-bit");
+    plan_slices(reinterpret_cast<const unsigned long long *>(left), cost, n, budget, priority_share, min_items,
+                reinterpret_cast<unsigned long long *>(take));
     return MM_OK;
 }
 

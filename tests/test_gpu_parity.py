@@ -404,21 +404,47 @@ def test_batch_results_identical_to_alone(ctx):
         mm.mm_release_map(ctx, m)
 
 
-def test_serving_results_identical_to_alone(ctx):
+@pytest.mark.parametrize("priority", [0.8, 0.0, 1.0])
+def test_serving_results_identical_to_alone(ctx, priority):
     items = mix_windows(8, 12)
     mm.mm_serve_config(ctx, max_active=4, wave_ms=0.5)
-    reqs, alone = [], []
-    for k, (cfg, f, rect) in enumerate(items):
-        h = lens(ctx, f)
-        alone.append(shoot(ctx, h, cfg, ray_rect=rect)[0])
-        reqs.append(mm.mm_submit(ctx, h, P(cfg, ray_rect=rect)))
-    for r, a in zip(reqs, alone):
-        m = mm.mm_wait(ctx, r, timeout_s=120)
-        got, st = mm.mm_map_fetch(ctx, m)
-        np.testing.assert_array_equal(got, a)
-        q, t = mm.mm_req_times(ctx, r)
-        assert 0 <= q <= t
-        mm.mm_release_map(ctx, m)
+    mm.mm_serve_priority(ctx, priority)
+    try:
+        reqs, alone = [], []
+        for k, (cfg, f, rect) in enumerate(items):
+            h = lens(ctx, f)
+            alone.append(shoot(ctx, h, cfg, ray_rect=rect)[0])
+            reqs.append(mm.mm_submit(ctx, h, P(cfg, ray_rect=rect)))
+        for r, a in zip(reqs, alone):
+            m = mm.mm_wait(ctx, r, timeout_s=120)
+            got, st = mm.mm_map_fetch(ctx, m)
+            np.testing.assert_array_equal(got, a)
+            q, t = mm.mm_req_times(ctx, r)
+            assert 0 <= q <= t
+            mm.mm_release_map(ctx, m)
+    finally:
+        mm.mm_serve_priority(ctx, 0.8)
+
+
+def test_serving_small_request_overtakes_a_large_one(ctx):
+    """Shortest remaining work first: a small map submitted just after a large one
+    finishes first, and the large one still finishes (every map moves each wave)."""
+    mm.mm_serve_config(ctx, max_active=8, wave_ms=0.5)
+    mm.mm_serve_priority(ctx, 1.0)
+    try:
+        big = mm.mm_submit(ctx, 0, P(CFG1, nstar=558, seed=2, ray_rect=(0, 16384, 0, 8192)))   # 7.5e10
+        small = mm.mm_submit(ctx, 0, P(CFG0, nstar=100, seed=1, ray_rect=(0, 640, 0, 640)))    # 4.1e7
+        ms = mm.mm_wait(ctx, small, timeout_s=120)
+        mb = mm.mm_wait(ctx, big, timeout_s=120)
+        _, tsmall = mm.mm_req_times(ctx, small)
+        _, tbig = mm.mm_req_times(ctx, big)
+        assert tsmall < tbig
+        _, st = mm.mm_map_fetch(ctx, mb, want_counts=False)
+        assert st["rays_shot"] == 16384 * 8192 == st["rays_in"] + st["rays_out"]
+        mm.mm_release_map(ctx, ms)
+        mm.mm_release_map(ctx, mb)
+    finally:
+        mm.mm_serve_priority(ctx, 0.8)
 
 
 def test_serving_generates_fields_and_polls(ctx):
