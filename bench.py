@@ -41,6 +41,7 @@ CFG1 = dict(sigma=0.4, gamma=0.0, smooth_frac=0.0, side=20.0, npix_side=1024, nr
 SEED = 2
 FLOP_PER_INTERACTION = 10.0      # Eq. for Phi: N_FLOP = 10 per deflection evaluation
 USEFUL_OPS_PER_INTERACTION = 6.0  # FP32 lane operations no implementation avoids: 2 sub, 1 mul, 3 fma
+USEFUL_OPS_WITH_MASSES = 7.0      # the same plus the mass product, for maps with a mass spectrum
 SMS, LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SMS * LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 WORKLOAD = ("Fig. 1 map: sigma=0.4, gamma=0, s=0, L=20 R_E, N_pix=1024^2, N_rays=2000, N*=558 unit masses "
@@ -163,7 +164,10 @@ def batch_phase(mm, ctx, n_maps=64, seed=4):
     return {"workload": f"{n_maps} maps, config-3 parameter mix (lognormal masses) scaled to N_side in "
                         "{64,128,256}, N_rays in {10,30,100}, <= 4e11 interactions each",
             "interactions": total, "batched_ms": batch_ms, "batched_interactions_per_s": total / (batch_ms * 1e-3),
-            "maps_per_s": n_maps / (batch_ms * 1e-3), "one_by_one_ms": one_ms,
+            "maps_per_s": n_maps / (batch_ms * 1e-3),
+            "frac_nflop10": FLOP_PER_INTERACTION * total / (batch_ms * 1e-3) / (FP32_PEAK_TFLOPS * 1e12),
+            "useful_frac": USEFUL_OPS_WITH_MASSES * total / (batch_ms * 1e-3) / (SMS * LANES * SM_MAX_MHZ * 1e6),
+            "one_by_one_ms": one_ms,
             "one_by_one_interactions_per_s": total / (one_ms * 1e-3),
             "fp64_one_by_one_interactions_per_s": f64_inter / (f64_ms * 1e-3),
             "fp64_sample": "the 8 smallest maps of the mix, plain FP64 kernel, one launch each"}

@@ -230,6 +230,35 @@ def test_lognormal_mix_windows_match_oracle(ctx):
         mm.mm_release_lenses(ctx, lh)
 
 
+@pytest.mark.parametrize("spectrum", ["lognormal", "light", "wide", "with_zeros"])
+def test_mass_spectra_match_oracle(ctx, spectrum):
+    """The FP32 path with mass spectra other than unit masses: lognormal masses, the same
+    times 1/256, log-uniform masses spanning five decades, and lognormal masses with
+    every seventh lens of zero mass."""
+    cfg = dict(sigma=0.5, gamma=0.2, smooth_frac=0.2, side=4.0, npix_side=64, nrays=64.0)
+    f0 = synth.lens_field(700, 12.0, 31, synth.MASS_LOGNORMAL)
+    m = f0.m.copy()
+    if spectrum == "light":
+        m = m / 256.0
+    elif spectrum == "wide":
+        m = 10.0 ** np.random.default_rng(31).uniform(-4.0, 1.0, len(m))
+    elif spectrum == "with_zeros":
+        m[::7] = 0.0
+    f = synth.LensField(f0.x, f0.y, m)
+    g = oracle.geometry(oracle_cfg(cfg))
+    rect = (g["nx"] // 2 - 160, g["nx"] // 2 + 150, g["ny"] // 2 - 100, g["ny"] // 2 + 90)
+    lh = lens(ctx, f)
+    got, st = shoot(ctx, lh, cfg, ray_rect=rect)
+    ref, tot = oracle.shoot_map(oracle_cfg(cfg), f, rect=rect)
+    check_totals(got, st, tot["shot"])
+    assert map_l1(got, ref) <= 2 * max(2, MISBIN_TOL * tot["shot"]), spectrum
+    jj, ii = np.meshgrid(np.arange(rect[2], rect[3], 3), np.arange(rect[0], rect[1], 5), indexing="ij")
+    err, mis, *_ = rays_check(ctx, lh, cfg, f, ii.ravel(), jj.ravel())
+    assert err.max() <= ALPHA_TOL, (spectrum, err.max())
+    assert mis <= MISBIN_TOL
+    mm.mm_release_lenses(ctx, lh)
+
+
 # ------------------------------------------------------------- edge cases ---
 
 def test_smooth_only_map_exact(ctx):
