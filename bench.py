@@ -319,10 +319,12 @@ def cpu_baseline(seconds_target: float = 15.0):
                       f"= {inter:.3e} interactions) in {dt:.1f} s, FP64, OpenMP"}
 
 
-def profile_case(kind="fp32"):
-    """Small case of the same kernel for ncu: a 4096 x 4096-ray window of the Fig. 1 map
-    (1.68e7 rays, 9.36e9 interactions), launched three times; kind "far" shoots it with
-    the far-field approximation (MM_FAR32, default order, ratio and block)."""
+def profile_case(kind="fp32", window=4096):
+    """Small case of the same kernel for ncu: a window x window-ray window at the centre of
+    the Fig. 1 map (4096: 1.68e7 rays, 9.36e9 interactions), launched three times; kind
+    "far" shoots it with the far-field approximation (MM_FAR32, default order, ratio and
+    block; from 16384, 2048 blocks of 8 x 8 tiles, its work items are whole blocks as on
+    the full map)."""
     import paper_1005_5198_gb300 as mm
     import synth
     from oracle import field as ofield
@@ -333,7 +335,8 @@ def profile_case(kind="fp32"):
     lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
     g = mm.mm_geometry_of(mm.params(**CFG1))
     c = g["nx"] // 2
-    p = mm.params(**CFG1, ray_rect=(c - 2048, c + 2048, c - 2048, c + 2048),
+    h = window // 2
+    p = mm.params(**CFG1, ray_rect=(c - h, c + h, c - h, c + h),
                   precision=mm.MM_FAR32 if kind == "far" else mm.MM_FP32C)
     for _ in range(3):
         m = mm.mm_shoot(ctx, lh, p)
@@ -421,8 +424,9 @@ def main():
     ap.add_argument("--wave-ms", type=float, default=12.0, help="serving: target device time of one wave")
     ap.add_argument("--serve-priority", type=float, default=0.8,
                     help="serving: share of each wave given shortest remaining work first (0: processor sharing)")
+    ap.add_argument("--profile-window", type=int, default=4096, help="--profile-case: window side in rays")
     ap.add_argument("--profile-case", nargs="?", const="fp32", choices=["fp32", "far"],
-                    help="shoot a 4096^2-ray window of the Fig. 1 map three times, exactly (fp32) or with the "
+                    help="shoot a window (--profile-window, 4096^2 rays) of the Fig. 1 map three times, exactly (fp32) or with the "
                          "far-field approximation MM_FAR32 (far), for ncu captures, and exit")
     ap.add_argument("--far-scaling", action="store_true",
                     help="time the far field on the Fig. 1 geometry for N* = 1e4 .. 1e8 and exit")
@@ -432,7 +436,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.profile_case:
-        return profile_case(args.profile_case)
+        return profile_case(args.profile_case, args.profile_window)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
 
