@@ -364,7 +364,8 @@ int mm_map_lightcurve(mm_ctx *ctx, mm_map map, int32_t profile, double size_re, 
  * Layouts give bit-identical maps; variants differ only in rounding. */
 int mm_autotune(mm_ctx *ctx, const mm_params *p, int32_t *variant);
 
-/* Force a tile variant for subsequent FP32 shoots (-1: use the tuned table).
+/* Force a tile variant for subsequent FP32 shoots (-1: use the tuned table,
+ * else the default: variant 0 for unit masses, 2 for lens sets with masses).
  * A variant fixes the share of lens pairs whose two reciprocals come from one
  * reciprocal of their product, and the compensated-fold interval. */
 int mm_set_variant(mm_ctx *ctx, int32_t variant);

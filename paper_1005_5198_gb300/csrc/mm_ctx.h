@@ -170,7 +170,7 @@ void far_release(MapObj &m);
 // The far field's block side for parameters p, a grid g and N* lenses in a disc of the given
 // radius: p.far_block, or for 0 the side that minimises the modelled time (mm_far.cu).
 int far_block_for(const Geo &g, const mm_params &p, long long nstar, double radius);
-int choose_variant(mm_ctx *ctx, const mm_params *p, const Geo &g);
+int choose_variant(mm_ctx *ctx, bool unit_mass, long long nstar);
 int scratch_reserve(mm_ctx *ctx, LaunchScratch *sc, int n_maps);
 void scratch_free(mm_ctx *ctx, LaunchScratch *sc);
 uint64_t register_map(mm_ctx *ctx, std::shared_ptr<MapObj> m);

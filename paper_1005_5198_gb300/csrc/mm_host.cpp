@@ -386,7 +386,7 @@ int alloc_map(mm_ctx *ctx, const mm_params *p, const Geo &g, std::shared_ptr<Len
         MM_CUDA(cudaMemsetAsync(M->counts, 0, map_bytes(p), s));
         MM_CUDA(cudaMemsetAsync(M->totals, 0, 2 * sizeof(unsigned long long), s));
     }
-    M->variant = into ? into->variant : choose_variant(ctx, p, g);
+    M->variant = into ? into->variant : choose_variant(ctx, M->lenses->unit_mass, M->lenses->n);
     M->shot_total = (unsigned long long)g.ni * (unsigned long long)g.nj;
     *out = M;
     return MM_OK;
@@ -435,19 +435,19 @@ void fill_desc(const MapObj &m, MapDesc *d)
     d->seg_done = m.seg_done;
 }
 
-static int class_key(const mm_params *p, long long nstar)
+static int class_key(bool unit_mass, long long nstar)
 {
     int b = 0;
     while (b < 40 && (1LL << b) <= nstar) ++b;
-    return (p->mass_model == MM_MASS_UNIT ? 0 : 1000) + b;
+    return (unit_mass ? 0 : 1000) + b;
 }
 
-int choose_variant(mm_ctx *ctx, const mm_params *p, const Geo &g)
+int choose_variant(mm_ctx *ctx, bool unit_mass, long long nstar)
 {
     if (ctx->forced_variant >= 0) return ctx->forced_variant;
-    auto it = ctx->tuned.find(class_key(p, g.nstar));
+    auto it = ctx->tuned.find(class_key(unit_mass, nstar));
     if (it != ctx->tuned.end()) return it->second;
-    return 0;
+    return default_variant(unit_mass);
 }
 
 uint64_t register_map(mm_ctx *ctx, std::shared_ptr<MapObj> m)
@@ -1119,7 +1119,7 @@ int mm_autotune(mm_ctx *ctx, const mm_params *p, int32_t *variant)
     ctx->forced_variant = saved_v;
     ctx->layout = rc ? saved_l : best_l;
     if (rc) return rc;
-    ctx->tuned[class_key(p, g.nstar)] = best_v;
+    ctx->tuned[class_key(L->unit_mass, L->n)] = best_v;
     if (variant) *variant = best_v;
     return MM_OK;
 }

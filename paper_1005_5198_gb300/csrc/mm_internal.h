@@ -24,6 +24,10 @@ constexpr float kNearRadius = 0.1f;
 // Variants of the FP32 tile computation, chosen per map: (shared-reciprocal pairs per
 // 4 lens pairs, fold interval). They differ in rounding, within the accuracy target.
 constexpr int kNumVariants = 4;
+// Variant of a map without a tuned entry: 0 (3 of 4 pairs share) for unit masses, 2 (2 of
+// 4) with masses, where a shared pair also pays two mass products per ray (on GB300 a
+// batch of 64 lognormal-mass maps ran at 4.89e12 interactions/s with 2, 4.78e12 with 0).
+__host__ __device__ constexpr int default_variant(bool unit_mass) { return unit_mass ? 0 : 2; }
 // Thread layouts of the FP32 kernel, chosen per launch: (columns x rows of the 64 x 32
 // tile per thread). They give bit-identical maps.
 constexpr int kNumLayouts = 4;

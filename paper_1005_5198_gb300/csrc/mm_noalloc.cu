@@ -24,7 +24,6 @@ namespace {
 constexpr long long kNoAllocMaxLenses = 131072;
 constexpr long long kNoAllocPad = (kNoAllocMaxLenses + kChunkLenses - 1) / kChunkLenses * kChunkLenses + kChunkLenses;
 constexpr int kNoAllocLayout = 1;       // the default thread layout of a fresh context
-constexpr int kNoAllocVariant = 0;      // the default tile variant of a fresh context
 constexpr int kMaxDevices = 64;
 
 struct NoAllocScratch {
@@ -131,7 +130,7 @@ extern "C" int mm_shoot_noalloc(const double *x, const double *y, const double *
     M.counts = counts;
     M.totals = reinterpret_cast<unsigned long long *>(totals);
     M.lenses = std::shared_ptr<LensSet>(&L, [](LensSet *) {});
-    M.variant = kNoAllocVariant;
+    M.variant = default_variant(L.unit_mass);   // as a fresh context chooses
     M.splits = 1;                            // no partial buffers without allocation: one CTA per tile
     M.seg_lenses = std::max<long long>(nstar, 1);
     MapDesc d;
