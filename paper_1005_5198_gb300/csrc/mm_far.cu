@@ -323,6 +323,53 @@ __device__ __forceinline__ void far_bin(const MapDesc &M, unsigned *check, bool 
     cnt_out += (valid && !inside) ? 1u : 0u;
 }
 
+// Float-float steps on a pair of rows (f32x2). Lane by lane they round exactly as
+// ff_axis / ff_pixel / two_sum do: x - y is formed as fma(y, -1, x) (an exact product,
+// one rounding), and the negated products -RN(c n) as RN((-c) n). Only the sign of an
+// exact zero may differ, which no pixel index sees.
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
+
+__device__ __forceinline__ float2 sub2(float2 x, float2 y, float2 m1) { return __ffma2_rn(y, m1, x); }
+
+// s = RN(a + b) and its rounding error e, given nb = -b.
+__device__ __forceinline__ void two_sum2(float2 a, float2 nb, float2 m1, float2 &s, float2 &e)
+{
+    s = sub2(a, nb, m1);
+    const float2 bb = sub2(s, a, m1);
+    const float2 e1 = sub2(a, sub2(s, bb, m1), m1);
+    e = sub2(e1, __fadd2_rn(nb, bb), m1);                 // e1 + (b - bb)
+}
+
+// u = (ch + cl) n + base in float-float, for two exactly representable n (nch = -ch).
+__device__ __forceinline__ void ff_axis2(float2 ch, float2 nch, float2 cl, float2 n, float2 base, float2 m1,
+                                         float2 &uh, float2 &ul)
+{
+    const float2 nph = __fmul2_rn(nch, n);
+    float2 pe = __ffma2_rn(ch, n, nph);
+    pe = __ffma2_rn(cl, n, pe);
+    float2 e;
+    two_sum2(base, nph, m1, uh, e);
+    ul = __fadd2_rn(e, pe);
+}
+
+// floor(u) for u = (uh + ul) + (sh + sl) (iph + ipl), two rays (niph = -iph).
+__device__ __forceinline__ float2 ff_pixel2(float2 uh, float2 ul, float2 sh, float2 sl, float2 iph, float2 niph,
+                                            float2 ipl, float2 m1)
+{
+    const float2 nth = __fmul2_rn(sh, niph);
+    float2 te = __ffma2_rn(sh, iph, nth);
+    te = __ffma2_rn(sh, ipl, te);
+    te = __ffma2_rn(sl, iph, te);
+    float2 s, e;
+    two_sum2(uh, nth, m1, s, e);
+    const float2 lo = __fadd2_rn(__fadd2_rn(e, ul), te);
+    const float2 I = make_float2(floorf(s.x), floorf(s.y));
+    const float2 f = __fadd2_rn(sub2(s, I, m1), lo);
+    return __fadd2_rn(I, make_float2(floorf(f.x), floorf(f.y)));
+}
+
+__device__ __forceinline__ float &lane(float2 &v, int l) { return l ? v.y : v.x; }
+
 // The rays of tile (tx, ty), whose block's series and first near chunk are staged in
 // S. Near lists longer than kNearCap are re-staged chunk by chunk (uniform syncs).
 template <bool DUMP, bool MASS>
@@ -344,9 +391,10 @@ __device__ void far_tile(const LaunchArgs &A, const FarDesc &F, const MapDesc &M
     const float nxo = (float)(int)(ib + iloc - ibB - bw / 2) + 0.5f;
     const float vx = __fmaf_rn(nxo, F.dv_h, __fmul_rn(nxo, F.dv_l));
     const float nyo0 = (float)(int)(jb + jloc0 - jbB - bh / 2) + 0.5f;
-    float4 acc[K];
+    constexpr int H = K / 2;
+    // float-float sums of S = -alpha per row pair (lane l: row 2q + l): x (hi, lo), y (hi, lo)
+    float2 SXh[H], SXl[H], SYh[H], SYl[H];
     {
-        constexpr int H = K / 2;
         float2 VY[H], VYN[H], SR[H], SI[H];
 #pragma unroll
         for (int q = 0; q < H; ++q) {
@@ -385,10 +433,10 @@ __device__ void far_tile(const LaunchArgs &A, const FarDesc &F, const MapDesc &M
         // float-float sums of S = -alpha without c'_0 (folded into the pixel bases below):
         // the series remainder contributes -conj(s) = (-Re s, +Im s)
 #pragma unroll
-        for (int r = 0; r < K; ++r) {
-            const float sr = (r & 1) ? SR[r >> 1].y : SR[r >> 1].x;
-            const float si = (r & 1) ? SI[r >> 1].y : SI[r >> 1].x;
-            acc[r] = make_float4(-sr, 0.f, si, 0.f);
+        for (int q = 0; q < H; ++q) {
+            SXh[q] = make_float2(-SR[q].x, -SR[q].y);
+            SYh[q] = SI[q];
+            SXl[q] = SYl[q] = make_float2(0.f, 0.f);
         }
     }
 
@@ -438,8 +486,8 @@ __device__ void far_tile(const LaunchArgs &A, const FarDesc &F, const MapDesc &M
                                 onlens |= 1u << r;
                             } else {
                                 const double t = ml / r2;
-                                add_ff(acc[r].x, acc[r].y, t * d1);
-                                add_ff(acc[r].z, acc[r].w, t * d2);
+                                add_ff(lane(SXh[r >> 1], r & 1), lane(SXl[r >> 1], r & 1), t * d1);
+                                add_ff(lane(SYh[r >> 1], r & 1), lane(SYl[r >> 1], r & 1), t * d2);
                             }
                         }
                         continue;
@@ -458,12 +506,14 @@ __device__ void far_tile(const LaunchArgs &A, const FarDesc &F, const MapDesc &M
 #pragma unroll
                 for (int r = 0; r < K; ++r) {                 // compensated fold every kNearFold lenses
                     float s, e;
-                    two_sum(acc[r].x, nxs[r], s, e);
-                    acc[r].x = s;
-                    acc[r].y = __fadd_rn(acc[r].y, e);
-                    two_sum(acc[r].z, nys[r], s, e);
-                    acc[r].z = s;
-                    acc[r].w = __fadd_rn(acc[r].w, e);
+                    float &xh = lane(SXh[r >> 1], r & 1), &xl = lane(SXl[r >> 1], r & 1);
+                    float &yh = lane(SYh[r >> 1], r & 1), &yl = lane(SYl[r >> 1], r & 1);
+                    two_sum(xh, nxs[r], s, e);
+                    xh = s;
+                    xl = __fadd_rn(xl, e);
+                    two_sum(yh, nys[r], s, e);
+                    yh = s;
+                    yl = __fadd_rn(yl, e);
                     nxs[r] = nys[r] = 0.f;
                 }
             }
@@ -496,25 +546,35 @@ __device__ void far_tile(const LaunchArgs &A, const FarDesc &F, const MapDesc &M
     uxl = __fadd_rn(uxl, kxl);
     const bool col_ok = gi < M.i0 + M.ni;
     const float ay0 = (float)(int)(2 * (jb + jloc0) + 1 - M.ny);     // |2 j + 1 - ny| < 2^23: exact steps
+    const float2 m1 = dup2(-1.f), iph = dup2(M.ip_h), niph = dup2(-M.ip_h), ipl = dup2(M.ip_l);
+    const float2 UXH = dup2(uxh), UXL = dup2(uxl);
 #pragma unroll
-    for (int r = 0; r < K; ++r) {
-        const long long gj = jb + jloc0 + r;
-        float uyh, uyl;
-        ff_axis(M.ay_h, M.ay_l, ay0 + (float)(2 * r), kyh, uyh, uyl);
-        uyl = __fadd_rn(uyl, kyl);
-        const float4 a = acc[r];
-        const float I1 = ff_pixel(uxh, uxl, a.x, a.y, M.ip_h, M.ip_l);
-        const float I2 = ff_pixel(uyh, uyl, a.z, a.w, M.ip_h, M.ip_l);
-        const bool valid = col_ok && gj < M.j0 + M.nj;
-        const bool inside =
-            valid && !((onlens >> r) & 1u) && I1 >= 0.f && I1 < nsf && I2 >= 0.f && I2 < nsf;
-        const unsigned pix = inside ? (unsigned)I2 * (unsigned)M.nside + (unsigned)I1 : 0xffffffffu;
-        if (DUMP)                                             // alpha = conj(c'_0) - S
-            emit_ray<true>(A, M, item, iloc + kTileX * (jloc0 + r), valid, inside, pix,
-                           ((double)c0rh + (double)c0rl) - ((double)a.x + (double)a.y),
-                           -((double)c0ih + (double)c0il) - ((double)a.z + (double)a.w), cnt_in, cnt_out);
-        else
-            far_bin(M, A.check, valid, inside, pix, cnt_in, cnt_out);
+    for (int q = 0; q < H; ++q) {
+        float2 uyh, uyl;
+        ff_axis2(dup2(M.ay_h), dup2(-M.ay_h), dup2(M.ay_l), make_float2(ay0 + (float)(4 * q), ay0 + (float)(4 * q + 2)),
+                 dup2(kyh), m1, uyh, uyl);
+        uyl = __fadd2_rn(uyl, dup2(kyl));
+        const float2 I1 = ff_pixel2(UXH, UXL, SXh[q], SXl[q], iph, niph, ipl, m1);
+        const float2 I2 = ff_pixel2(uyh, uyl, SYh[q], SYl[q], iph, niph, ipl, m1);
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            const int r = 2 * q + l;
+            const long long gj = jb + jloc0 + r;
+            const float i1 = l ? I1.y : I1.x, i2 = l ? I2.y : I2.x;
+            const bool valid = col_ok && gj < M.j0 + M.nj;
+            const bool inside =
+                valid && !((onlens >> r) & 1u) && i1 >= 0.f && i1 < nsf && i2 >= 0.f && i2 < nsf;
+            const unsigned pix = inside ? (unsigned)i2 * (unsigned)M.nside + (unsigned)i1 : 0xffffffffu;
+            if (DUMP) {                                       // alpha = conj(c'_0) - S
+                const float xh = l ? SXh[q].y : SXh[q].x, xl = l ? SXl[q].y : SXl[q].x;
+                const float yh = l ? SYh[q].y : SYh[q].x, yl = l ? SYl[q].y : SYl[q].x;
+                emit_ray<true>(A, M, item, iloc + kTileX * (jloc0 + r), valid, inside, pix,
+                               ((double)c0rh + (double)c0rl) - ((double)xh + (double)xl),
+                               -((double)c0ih + (double)c0il) - ((double)yh + (double)yl), cnt_in, cnt_out);
+            } else {
+                far_bin(M, A.check, valid, inside, pix, cnt_in, cnt_out);
+            }
+        }
     }
 }
 
