@@ -306,18 +306,20 @@ __device__ __forceinline__ void far_stage(const MapDesc &M, const FarDesc &F, lo
 
 // Production binning: rays of a warp lie along one lattice row, so equal pixels
 // come in runs; the first lane of each run adds the run's length.
-__device__ __forceinline__ void far_bin(const MapDesc &M, unsigned *check, bool valid, bool inside, unsigned pix,
-                                        unsigned &cnt_in, unsigned &cnt_out)
+// counts / npix: the map's counts and N_side^2, passed by value: read through the map
+// descriptor they would be reloaded after every atomic, which may alias it.
+__device__ __forceinline__ void far_bin(unsigned *counts, unsigned npix, unsigned *check, bool valid, bool inside,
+                                        unsigned pix, unsigned &cnt_in, unsigned &cnt_out)
 {
     const unsigned lane = threadIdx.x & 31;
     const unsigned key = inside ? pix : 0xffffffffu;
     const unsigned left = __shfl_up_sync(kFull, key, 1);
     const bool start = lane == 0 || left != key;
     const unsigned starts = __ballot_sync(kFull, start);
-    if (inside && start && MM_BOUNDS(check, pix < (unsigned)M.nside * (unsigned)M.nside, kChkMapCount)) {
+    if (inside && start && MM_BOUNDS(check, pix < npix, kChkMapCount)) {
         const unsigned above = starts & ~((2u << lane) - 1u);    // run starts after this lane
         const unsigned next = above ? (unsigned)(__ffs(above) - 1) : 32u;
-        atomicAdd(M.counts + pix, next - lane);
+        atomicAdd(counts + pix, next - lane);
     }
     cnt_in += inside ? 1u : 0u;
     cnt_out += (valid && !inside) ? 1u : 0u;
@@ -539,7 +541,11 @@ __device__ void far_tile(const LaunchArgs &A, const FarDesc &F, const MapDesc &M
         two_sum(M.half_n, ph, kyh, e);
         kyl = __fadd_rn(e, pe);
     }
-    const float nsf = (float)M.nside;
+    // the descriptor's fields in registers for the rows below (atomics may alias it)
+    const unsigned nside = (unsigned)M.nside, npix = nside * nside;
+    unsigned *const counts = M.counts;
+    const int rows_valid = (int)min((long long)K, max(0LL, M.j0 + M.nj - (jb + jloc0)));   // rows r < this are in the grid
+    const float nsf = (float)nside;
     const long long gi = ib + iloc;
     float uxh, uxl;
     ff_axis(M.ax_h, M.ax_l, (float)(int)(2 * gi + 1 - M.nx), kxh, uxh, uxl);
@@ -547,24 +553,23 @@ __device__ void far_tile(const LaunchArgs &A, const FarDesc &F, const MapDesc &M
     const bool col_ok = gi < M.i0 + M.ni;
     const float ay0 = (float)(int)(2 * (jb + jloc0) + 1 - M.ny);     // |2 j + 1 - ny| < 2^23: exact steps
     const float2 m1 = dup2(-1.f), iph = dup2(M.ip_h), niph = dup2(-M.ip_h), ipl = dup2(M.ip_l);
+    const float2 ayh = dup2(M.ay_h), nayh = dup2(-M.ay_h), ayl = dup2(M.ay_l);
     const float2 UXH = dup2(uxh), UXL = dup2(uxl);
 #pragma unroll
     for (int q = 0; q < H; ++q) {
         float2 uyh, uyl;
-        ff_axis2(dup2(M.ay_h), dup2(-M.ay_h), dup2(M.ay_l), make_float2(ay0 + (float)(4 * q), ay0 + (float)(4 * q + 2)),
-                 dup2(kyh), m1, uyh, uyl);
+        ff_axis2(ayh, nayh, ayl, make_float2(ay0 + (float)(4 * q), ay0 + (float)(4 * q + 2)), dup2(kyh), m1, uyh, uyl);
         uyl = __fadd2_rn(uyl, dup2(kyl));
         const float2 I1 = ff_pixel2(UXH, UXL, SXh[q], SXl[q], iph, niph, ipl, m1);
         const float2 I2 = ff_pixel2(uyh, uyl, SYh[q], SYl[q], iph, niph, ipl, m1);
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
             const int r = 2 * q + l;
-            const long long gj = jb + jloc0 + r;
             const float i1 = l ? I1.y : I1.x, i2 = l ? I2.y : I2.x;
-            const bool valid = col_ok && gj < M.j0 + M.nj;
+            const bool valid = col_ok && r < rows_valid;
             const bool inside =
                 valid && !((onlens >> r) & 1u) && i1 >= 0.f && i1 < nsf && i2 >= 0.f && i2 < nsf;
-            const unsigned pix = inside ? (unsigned)i2 * (unsigned)M.nside + (unsigned)i1 : 0xffffffffu;
+            const unsigned pix = inside ? (unsigned)i2 * nside + (unsigned)i1 : 0xffffffffu;
             if (DUMP) {                                       // alpha = conj(c'_0) - S
                 const float xh = l ? SXh[q].y : SXh[q].x, xl = l ? SXl[q].y : SXl[q].x;
                 const float yh = l ? SYh[q].y : SYh[q].x, yl = l ? SYl[q].y : SYl[q].x;
@@ -572,7 +577,7 @@ __device__ void far_tile(const LaunchArgs &A, const FarDesc &F, const MapDesc &M
                                ((double)c0rh + (double)c0rl) - ((double)xh + (double)xl),
                                -((double)c0ih + (double)c0il) - ((double)yh + (double)yl), cnt_in, cnt_out);
             } else {
-                far_bin(M, A.check, valid, inside, pix, cnt_in, cnt_out);
+                far_bin(counts, npix, A.check, valid, inside, pix, cnt_in, cnt_out);
             }
         }
     }
