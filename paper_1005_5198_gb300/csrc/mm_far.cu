@@ -372,11 +372,38 @@ __device__ __forceinline__ float2 ff_pixel2(float2 uh, float2 ul, float2 sh, flo
 
 __device__ __forceinline__ float &lane(float2 &v, int l) { return l ? v.y : v.x; }
 
+// Pixel bases of a block's rays: u = A (2i + 1 - n) + N/2 + S / p with S = -alpha; the
+// block's c'_0 part of S/p is the same for all its rays and enters the bases
+// kx = N/2 - Re c'_0 / p, ky = N/2 + Im c'_0 / p (float-float). Needs the block's
+// series staged in S.
+struct FarBase {
+    float kxh, kxl, kyh, kyl;
+};
+
+__device__ __forceinline__ FarBase far_base(const MapDesc &M, const SmemFar &S)
+{
+    const float c0rh = S.coef[0], c0rl = S.coef[1], c0ih = S.coef[2], c0il = S.coef[3];
+    FarBase B;
+    float ph = __fmul_rn(c0rh, M.ip_h);
+    float pe = __fmaf_rn(c0rh, M.ip_h, -ph);
+    pe = __fmaf_rn(c0rh, M.ip_l, __fmaf_rn(c0rl, M.ip_h, pe));
+    float e;
+    two_sum(M.half_n, -ph, B.kxh, e);
+    B.kxl = __fsub_rn(e, pe);
+    ph = __fmul_rn(c0ih, M.ip_h);
+    pe = __fmaf_rn(c0ih, M.ip_h, -ph);
+    pe = __fmaf_rn(c0ih, M.ip_l, __fmaf_rn(c0il, M.ip_h, pe));
+    two_sum(M.half_n, ph, B.kyh, e);
+    B.kyl = __fadd_rn(e, pe);
+    return B;
+}
+
 // The rays of tile (tx, ty), whose block's series and first near chunk are staged in
 // S. Near lists longer than kNearCap are re-staged chunk by chunk (uniform syncs).
 template <bool DUMP, bool MASS>
-__device__ void far_tile(const LaunchArgs &A, const FarDesc &F, const MapDesc &M, long long blk, long long tx,
-                         long long ty, int item, SmemFar &S, unsigned &cnt_in, unsigned &cnt_out)
+__device__ void far_tile(const LaunchArgs &A, const FarDesc &F, const MapDesc &M, long long blk, long long bx,
+                         long long by, const FarBase &B, long long tx, long long ty, int item, SmemFar &S,
+                         unsigned &cnt_in, unsigned &cnt_out)
 {
     constexpr int K = kFarRows;
     const int tid = threadIdx.x, w = tid >> 5;
@@ -384,7 +411,7 @@ __device__ void far_tile(const LaunchArgs &A, const FarDesc &F, const MapDesc &M
     const int jloc0 = (w >> 1) * K;
     const long long ib = M.i0 + tx * kTileX, jb = M.j0 + ty * kTileY;
     const long long bw = 64LL * F.bt, bh = 32LL * F.bt;
-    const long long ibB = M.i0 + (blk % F.blocks_x) * bw, jbB = M.j0 + (blk / F.blocks_x) * bh;
+    const long long ibB = M.i0 + bx * bw, jbB = M.j0 + by * bh;     // block (bx, by) = blk, from the caller
     const int P = F.order;
 
     // ---- far series: Horner's rule in v = (z - z_B) / rho, packed over row pairs ----
@@ -523,24 +550,7 @@ __device__ void far_tile(const LaunchArgs &A, const FarDesc &F, const MapDesc &M
     }
 
     // ---- lens equation and pixel (float-float), as in the exact FP32 kernel ----
-    // u = A (2i + 1 - n) + N/2 + S / p with S = -alpha; the block's c'_0 part of S/p
-    // is the same for all its rays and enters the bases kx = N/2 - Re c'_0 / p,
-    // ky = N/2 + Im c'_0 / p (float-float).
-    const float c0rh = S.coef[0], c0rl = S.coef[1], c0ih = S.coef[2], c0il = S.coef[3];
-    float kxh, kxl, kyh, kyl;
-    {
-        float ph = __fmul_rn(c0rh, M.ip_h);
-        float pe = __fmaf_rn(c0rh, M.ip_h, -ph);
-        pe = __fmaf_rn(c0rh, M.ip_l, __fmaf_rn(c0rl, M.ip_h, pe));
-        float e;
-        two_sum(M.half_n, -ph, kxh, e);
-        kxl = __fsub_rn(e, pe);
-        ph = __fmul_rn(c0ih, M.ip_h);
-        pe = __fmaf_rn(c0ih, M.ip_h, -ph);
-        pe = __fmaf_rn(c0ih, M.ip_l, __fmaf_rn(c0il, M.ip_h, pe));
-        two_sum(M.half_n, ph, kyh, e);
-        kyl = __fadd_rn(e, pe);
-    }
+    const float kxh = B.kxh, kxl = B.kxl, kyh = B.kyh, kyl = B.kyl;
     // the descriptor's fields in registers for the rows below (atomics may alias it)
     const unsigned nside = (unsigned)M.nside, npix = nside * nside;
     unsigned *const counts = M.counts;
@@ -574,8 +584,8 @@ __device__ void far_tile(const LaunchArgs &A, const FarDesc &F, const MapDesc &M
                 const float xh = l ? SXh[q].y : SXh[q].x, xl = l ? SXl[q].y : SXl[q].x;
                 const float yh = l ? SYh[q].y : SYh[q].x, yl = l ? SYl[q].y : SYl[q].x;
                 emit_ray<true>(A, M, item, iloc + kTileX * (jloc0 + r), valid, inside, pix,
-                               ((double)c0rh + (double)c0rl) - ((double)xh + (double)xl),
-                               -((double)c0ih + (double)c0il) - ((double)yh + (double)yl), cnt_in, cnt_out);
+                               ((double)S.coef[0] + (double)S.coef[1]) - ((double)xh + (double)xl),
+                               -((double)S.coef[2] + (double)S.coef[3]) - ((double)yh + (double)yl), cnt_in, cnt_out);
             } else {
                 far_bin(counts, npix, A.check, valid, inside, pix, cnt_in, cnt_out);
             }
@@ -597,11 +607,12 @@ __device__ void far_item(const LaunchArgs &A, const FarDesc &F, const MapDesc &M
     far_stage(M, F, blk, 0, true, S);
     __syncthreads();
     const long long bx = blk % F.blocks_x, by = blk / F.blocks_x;
+    const FarBase B = far_base(M, S);
     const long long tiles_y = (M.nj + kTileY - 1) / kTileY;
     for (long long ty = by * F.bt + grp * F.rows_per_item; ty < by * F.bt + (grp + 1) * F.rows_per_item; ++ty) {
         if (ty >= tiles_y) break;
         for (long long tx = bx * F.bt; tx < (bx + 1) * F.bt && tx < M.tiles_x; ++tx)
-            far_tile<false, MASS>(A, F, M, blk, tx, ty, 0, S, ci, co);
+            far_tile<false, MASS>(A, F, M, blk, bx, by, B, tx, ty, 0, S, ci, co);
     }
 }
 
@@ -661,8 +672,9 @@ __global__ void __launch_bounds__(kShootThreads, 2) k_shoot_far_dump(const Launc
         __syncthreads();
         far_stage(M, F, blk, 0, true, S);
         __syncthreads();
-        if (M.unit_mass) far_tile<true, false>(A, F, M, blk, tx, ty, item, S, ci, co);
-        else far_tile<true, true>(A, F, M, blk, tx, ty, item, S, ci, co);
+        const FarBase B = far_base(M, S);
+        if (M.unit_mass) far_tile<true, false>(A, F, M, blk, tx / F.bt, ty / F.bt, B, tx, ty, item, S, ci, co);
+        else far_tile<true, true>(A, F, M, blk, tx / F.bt, ty / F.bt, B, tx, ty, item, S, ci, co);
     });
 }
 
