@@ -307,9 +307,11 @@ __device__ __forceinline__ void far_stage(const MapDesc &M, const FarDesc &F, lo
 // Production binning: rays of a warp lie along one lattice row, so equal pixels
 // come in runs; the first lane of each run adds the run's length.
 // counts / npix: the map's counts and N_side^2, passed by value: read through the map
-// descriptor they would be reloaded after every atomic, which may alias it.
-__device__ __forceinline__ void far_bin(unsigned *counts, unsigned npix, unsigned *check, bool valid, bool inside,
-                                        unsigned pix, unsigned &cnt_in, unsigned &cnt_out)
+// descriptor they would be reloaded after every atomic, which may alias it. The first
+// lane of a run also adds the run's length to cnt_in (the production kernel counts the
+// valid rays per tile and takes the rays out as the difference).
+__device__ __forceinline__ void far_bin(unsigned *counts, unsigned npix, unsigned *check, bool inside, unsigned pix,
+                                        unsigned &cnt_in)
 {
     const unsigned lane = threadIdx.x & 31;
     const unsigned key = inside ? pix : 0xffffffffu;
@@ -318,11 +320,10 @@ __device__ __forceinline__ void far_bin(unsigned *counts, unsigned npix, unsigne
     const unsigned starts = __ballot_sync(kFull, start);
     if (inside && start && MM_BOUNDS(check, pix < npix, kChkMapCount)) {
         const unsigned above = starts & ~((2u << lane) - 1u);    // run starts after this lane
-        const unsigned next = above ? (unsigned)(__ffs(above) - 1) : 32u;
-        atomicAdd(counts + pix, next - lane);
+        const unsigned run = (above ? (unsigned)(__ffs(above) - 1) : 32u) - lane;
+        atomicAdd(counts + pix, run);
+        cnt_in += run;
     }
-    cnt_in += inside ? 1u : 0u;
-    cnt_out += (valid && !inside) ? 1u : 0u;
 }
 
 // Float-float steps on a pair of rows (f32x2). Lane by lane they round exactly as
@@ -561,6 +562,7 @@ __device__ void far_tile(const LaunchArgs &A, const FarDesc &F, const MapDesc &M
     ff_axis(M.ax_h, M.ax_l, (float)(int)(2 * gi + 1 - M.nx), kxh, uxh, uxl);
     uxl = __fadd_rn(uxl, kxl);
     const bool col_ok = gi < M.i0 + M.ni;
+    if (!DUMP) cnt_out += col_ok ? (unsigned)rows_valid : 0u;    // valid rays; out = valid - in (per warp)
     const float ay0 = (float)(int)(2 * (jb + jloc0) + 1 - M.ny);     // |2 j + 1 - ny| < 2^23: exact steps
     const float2 m1 = dup2(-1.f), iph = dup2(M.ip_h), niph = dup2(-M.ip_h), ipl = dup2(M.ip_l);
     const float2 ayh = dup2(M.ay_h), nayh = dup2(-M.ay_h), ayl = dup2(M.ay_l);
@@ -587,7 +589,7 @@ __device__ void far_tile(const LaunchArgs &A, const FarDesc &F, const MapDesc &M
                                ((double)S.coef[0] + (double)S.coef[1]) - ((double)xh + (double)xl),
                                -((double)S.coef[2] + (double)S.coef[3]) - ((double)yh + (double)yl), cnt_in, cnt_out);
             } else {
-                far_bin(counts, npix, A.check, valid, inside, pix, cnt_in, cnt_out);
+                far_bin(counts, npix, A.check, inside, pix, cnt_in);
             }
         }
     }
@@ -645,7 +647,7 @@ __global__ void __launch_bounds__(kShootThreads, 2) k_shoot_far(const LaunchArgs
         if (M.unit_mass) far_item<false>(A, F, M, it, S, ci, co);
         else far_item<true>(A, F, M, it, S, ci, co);
         ci = __reduce_add_sync(kFull, ci);
-        co = __reduce_add_sync(kFull, co);
+        co = __reduce_add_sync(kFull, co) - ci;               // valid rays of the warp minus those in the map
         if ((tid & 31) == 0) {
             atomicAdd(&S.red_in, ci);
             atomicAdd(&S.red_out, co);
