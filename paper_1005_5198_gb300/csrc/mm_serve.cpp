@@ -163,8 +163,8 @@ static void admit_worker(Server *S, int idx)
 }
 
 // A far-field ray costs about as much device time as this many exact interactions
-// (80 ms for the 1.3e10 rays of the Fig. 1 map, against 0.185 ps per interaction).
-constexpr double kFarRayInteractions = 33.0;
+// (64 ms for the 1.3e10 rays of the Fig. 1 map, against 0.185 ps per interaction).
+constexpr double kFarRayInteractions = 26.0;
 // An interaction of the plain FP64 kernel costs about this many of the FP32 kernel's
 // (DFMA runs at 1/64 of the FP32 lane rate; measured 4.1e10 against 5.4e12 per second).
 constexpr double kFp64Interactions = 130.0;
