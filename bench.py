@@ -60,10 +60,11 @@ class Clocks:
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device: int):
+    def __init__(self, device: int, directory: str | None = None):
+        import tempfile
         self.device = device
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device}.csv")
+        self.path = os.path.join(directory or tempfile.gettempdir(), f"clocks_rank{device}.csv")
 
     def __enter__(self):
         try:
@@ -425,6 +426,9 @@ def main():
     ap.add_argument("--serve-priority", type=float, default=0.8,
                     help="serving: share of each wave given shortest remaining work first (0: processor sharing)")
     ap.add_argument("--profile-window", type=int, default=4096, help="--profile-case: window side in rays")
+    ap.add_argument("--clocks-dir", default=None,
+                    help="where the nvidia-smi samples of the timed region go (clocks_rank<N>.csv; default: the "
+                         "system's temporary directory)")
     ap.add_argument("--profile-case", nargs="?", const="fp32", choices=["fp32", "far"],
                     help="shoot a window (--profile-window, 4096^2 rays) of the Fig. 1 map three times, exactly (fp32) or with the "
                          "far-field approximation MM_FAR32 (far), for ncu captures, and exit")
@@ -476,7 +480,7 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    with Clocks(local) as clk:
+    with Clocks(local, args.clocks_dir) as clk:
         for k in range(args.steps):
             flush.fill_(k & 0xFF)                       # evict L2 between timed steps (outside the events)
             ev[k][0].record(stream)
