@@ -221,6 +221,66 @@ def serve_phase(mm, ctx, rate_hz, seconds, seed, large_every=10):
 KERNEL_SOURCES = ["mm_fp32.cuh", "mm_device.cuh", "mm_internal.h", "mm_fp32_c2r4.cu"]
 
 
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of this GPU type (MEASURED_PEAKS.json), else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def downstream_phase(mm, ctx, side=8192):
+    """The rows after the map: the map statistics of Sect. 3.1 (mm_map_compare: RMS of Delta m and the
+    K-S test) and an extended source's light curve (mm_map_lightcurve: the map convolved with a Gaussian
+    or disc profile on the device, then sampled along a track), on two side^2 maps (256 MiB of counts
+    each at 8192^2, more than L2) of the Fig. 1 field at N_rays = 10, shot with the far field (default
+    order and order 14). Each call returns with its result on the host; times are host clocks around
+    it (best of 3 after one warm-up). Algorithmic bytes: compare reads both maps once (8 B/pixel); the
+    Gaussian's two separable passes read and write a map each (16 B/pixel); the disc reads the counts
+    and writes the convolved map (8 B/pixel)."""
+    peak, peak_src = hbm_peak_gbs()
+    base = dict(sigma=0.4, gamma=0.0, smooth_frac=0.0, side=20.0, npix_side=side, nrays=10.0, seed=SEED)
+    pa = mm.params(**base, precision=mm.MM_FAR32)
+    pb = mm.params(**base, precision=mm.MM_FAR32, far_order=14)
+    lh = mm.mm_create_lenses(ctx, pa)
+    ma, mb = mm.mm_shoot(ctx, lh, pa), mm.mm_shoot(ctx, lh, pb)
+    npix = side * side
+    pix_re = 20.0 / side
+
+    def timed(fn):
+        fn()
+        best, res = 1e30, None
+        for _ in range(3):
+            t0 = time.perf_counter()
+            res = fn()
+            best = min(best, time.perf_counter() - t0)
+        return best, res
+
+    def line(sec, nbytes, extra):
+        gbs = nbytes / sec / 1e9
+        return dict(extra, ms=sec * 1e3, pixels_per_s=npix / sec, algorithmic_bytes=nbytes, achieved_gbs=gbs,
+                    hbm_frac=gbs / peak)
+
+    t_cmp, st = timed(lambda: mm.mm_map_compare(ctx, ma, mb))
+    track = ((-8.0, -3.0), (8.0, 3.0))
+    g_size, d_size = 0.02, 0.02
+    t_g, _ = timed(lambda: mm.mm_map_lightcurve(ctx, ma, mm.MM_PROFILE_GAUSSIAN, g_size, *track, 1000))
+    t_d, _ = timed(lambda: mm.mm_map_lightcurve(ctx, ma, mm.MM_PROFILE_DISC, d_size, *track, 1000))
+    h = int(np.ceil(4.0 * g_size / pix_re))
+    hd = int(d_size / pix_re)
+    out = {"workload": f"two {side}^2 maps of the Fig. 1 field (N_rays = 10, far field), {npix:.3e} pixels each",
+           "hbm_peak_gbs": peak, "hbm_peak_source": peak_src,
+           "compare": line(t_cmp, 8 * npix, {"rms_dm": st["rms_dm"], "ks_p": st["ks_p"]}),
+           "lightcurve_gaussian": line(t_g, 16 * npix, {"size_re": g_size, "taps_per_pass": 2 * h + 1,
+                                                        "points": 1000}),
+           "lightcurve_disc": line(t_d, 8 * npix, {"size_re": d_size, "radius_pixels": hd, "points": 1000})}
+    mm.mm_release_map(ctx, ma)
+    mm.mm_release_map(ctx, mb)
+    mm.mm_release_lenses(ctx, lh)
+    return out
+
+
 def far_phase(mm, ctx, lh_fig1, exact_ms):
     """The far-field approximation MM_FAR32 (the tree code's idea, Sect. 2.1; the library's default
     order, ratio and block), timed outside the headline region: the Fig. 1 map against the
@@ -429,9 +489,10 @@ def main():
     ap.add_argument("--clocks-dir", default=None,
                     help="where the nvidia-smi samples of the timed region go (clocks_rank<N>.csv; default: the "
                          "system's temporary directory)")
-    ap.add_argument("--profile-case", nargs="?", const="fp32", choices=["fp32", "far"],
-                    help="shoot a window (--profile-window, 4096^2 rays) of the Fig. 1 map three times, exactly (fp32) or with the "
-                         "far-field approximation MM_FAR32 (far), for ncu captures, and exit")
+    ap.add_argument("--profile-case", nargs="?", const="fp32", choices=["fp32", "far", "downstream"],
+                    help="for ncu captures, then exit: shoot a window (--profile-window, 4096^2 rays) of the Fig. 1 map "
+                         "three times, exactly (fp32) or with the far-field approximation MM_FAR32 (far); or run the "
+                         "map statistics and light curves on two 8192^2 maps (downstream)")
     ap.add_argument("--far-scaling", action="store_true",
                     help="time the far field on the Fig. 1 geometry for N* = 1e4 .. 1e8 and exit")
     args = ap.parse_args()
@@ -439,6 +500,13 @@ def main():
         return far_scaling()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_case == "downstream":               # map statistics and light curves (ncu captures)
+        import paper_1005_5198_gb300 as mm
+        mm.build()
+        ctx = mm.mm_init(0)
+        print(json.dumps(downstream_phase(mm, ctx)))
+        mm.mm_destroy(ctx)
+        return 0
     if args.profile_case:
         return profile_case(args.profile_case, args.profile_window)
     if args.warmup < 3:
@@ -535,6 +603,7 @@ def main():
     extra = {}
     if not args.no_extras and world == 1:
         extra["far_field"] = far_phase(mm, ctx, lh, sum(kern_ms) / len(kern_ms))
+        extra["downstream"] = downstream_phase(mm, ctx)
         extra["batch"] = batch_phase(mm, ctx)
         mm.mm_serve_config(ctx, max_active=64, wave_ms=args.wave_ms)
         mm.mm_serve_priority(ctx, args.serve_priority)

@@ -67,6 +67,147 @@ __global__ void k_disc(const unsigned *cin, float *out, int n, const int *span, 
     }
 }
 
+// ---- tiled forms of the passes above: the same per-pixel sums in the same order ----
+
+constexpr int kGaussRowTile = 256;                     // outputs per CTA along a row (= threads)
+constexpr int kGaussColTileW = 32, kGaussColTileH = 64;   // column pass: 32 columns x 64 rows per CTA
+constexpr int kDiscTileW = 64, kDiscTileH = 32;        // disc: 64 x 32 outputs per CTA
+constexpr size_t kTileSmemMax = 48 * 1024;             // dynamic shared memory of a tiled CTA (no opt-in);
+                                                       // wider supports take the untiled kernels
+
+__host__ __device__ inline size_t gauss_row_smem(int h) { return (size_t)(2 * h + 1 + kGaussRowTile + 2 * h) * 4; }
+__host__ __device__ inline size_t gauss_col_smem(int h)
+{
+    return (size_t)(2 * h + 1 + (kGaussColTileH + 2 * h) * kGaussColTileW) * 4;
+}
+__host__ __device__ inline size_t disc_smem(int H)
+{
+    return (size_t)(kDiscTileH + 2 * H) * (kDiscTileW + 2 * H + 1) * 8 + (size_t)(2 * H + 1) * 4;
+}
+
+// Row pass (dir 0 of k_gauss_pass): a CTA stages the row segment [i0 - h, i0 + 256 + h)
+// and the taps in shared memory; thread t sums output i0 + t.
+template <bool FROM_COUNTS>
+__global__ void __launch_bounds__(kGaussRowTile) k_gauss_rows(const unsigned *cin, const float *fin, float *out, int n,
+                                                              const float *g, int h, float inv_nrays)
+{
+    extern __shared__ float sm[];
+    float *const gs = sm, *const seg = sm + 2 * h + 1;      // taps [2h + 1], inputs [256 + 2h]
+    for (int k = threadIdx.x; k < 2 * h + 1; k += blockDim.x) gs[k] = g[k];
+    const int segs = (n + kGaussRowTile - 1) / kGaussRowTile;
+    const long long tiles = (long long)n * segs;
+    for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int j = (int)(t / segs), i0 = (int)(t % segs) * kGaussRowTile;
+        __syncthreads();                                       // previous tile read; taps staged
+        for (int q = threadIdx.x; q < kGaussRowTile + 2 * h; q += blockDim.x) {
+            const int i = i0 - h + q;
+            float v = 0.f;
+            if (i >= 0 && i < n) {
+                const long long src = (long long)j * n + i;
+                v = FROM_COUNTS ? (float)cin[src] * inv_nrays : fin[src];
+            }
+            seg[q] = v;
+        }
+        __syncthreads();
+        const int i = i0 + (int)threadIdx.x;
+        if (i < n) {
+            float o = __int_as_float(0x7fc00000);
+            if (i - h >= 0 && i + h < n) {
+                float acc = 0.f;
+                for (int k = 0; k <= 2 * h; ++k) acc = fmaf(gs[k], seg[threadIdx.x + k], acc);
+                o = acc;
+            }
+            out[(long long)j * n + i] = o;
+        }
+    }
+}
+
+// Column pass (dir 1): a CTA stages rows [r0 - h, r0 + 64 + h) of 32 columns; thread
+// (column tx, row group ty) sums rows ty, ty + 8, ... of the tile.
+__global__ void __launch_bounds__(256) k_gauss_cols(const float *fin, float *out, int n, const float *g, int h)
+{
+    extern __shared__ float sm[];
+    float *const gs = sm, *const tile = sm + 2 * h + 1;    // taps, then [(64 + 2h) x 32]
+    for (int k = threadIdx.x; k < 2 * h + 1; k += blockDim.x) gs[k] = g[k];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int cols = (n + kGaussColTileW - 1) / kGaussColTileW, rows = (n + kGaussColTileH - 1) / kGaussColTileH;
+    const long long tiles = (long long)cols * rows;
+    for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int c0 = (int)(t % cols) * kGaussColTileW, r0 = (int)(t / cols) * kGaussColTileH;
+        __syncthreads();
+        for (int q = threadIdx.x; q < (kGaussColTileH + 2 * h) * kGaussColTileW; q += blockDim.x) {
+            const int j = r0 - h + q / kGaussColTileW, i = c0 + q % kGaussColTileW;
+            tile[q] = (j >= 0 && j < n && i < n) ? fin[(long long)j * n + i] : 0.f;
+        }
+        __syncthreads();
+        const int i = c0 + tx;
+        for (int rr = ty; rr < kGaussColTileH; rr += 8) {
+            const int j = r0 + rr;
+            if (i >= n || j >= n) continue;
+            float o = __int_as_float(0x7fc00000);
+            if (j - h >= 0 && j + h < n) {
+                float acc = 0.f;
+                for (int k = 0; k <= 2 * h; ++k) acc = fmaf(gs[k], tile[(rr + k) * kGaussColTileW + tx], acc);
+                o = acc;
+            }
+            out[(long long)j * n + i] = o;
+        }
+    }
+}
+
+// Disc: a CTA stages the counts of rows [r0 - H, r0 + 32 + H) x columns [c0 - H, c0 + 64 + H)
+// as 64-bit prefix sums along each row (one warp per row, with a leading zero), so the
+// sum over a row span [i - w, i + w] is one exact difference, as k_disc's 64-bit sum.
+__global__ void __launch_bounds__(256) k_disc_tiled(const unsigned *cin, float *out, int n, const int *span, int H,
+                                                    float scale)
+{
+    extern __shared__ unsigned long long psm[];
+    const int W = kDiscTileW + 2 * H + 1;                  // prefix row length
+    unsigned long long *const pre = psm;                   // [(32 + 2H) x W]
+    int *const sp = (int *)(psm + (size_t)(kDiscTileH + 2 * H) * W);
+    for (int k = threadIdx.x; k < 2 * H + 1; k += blockDim.x) sp[k] = span[k];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cols = (n + kDiscTileW - 1) / kDiscTileW, rows = (n + kDiscTileH - 1) / kDiscTileH;
+    const long long tiles = (long long)cols * rows;
+    for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int c0 = (int)(t % cols) * kDiscTileW, r0 = (int)(t / cols) * kDiscTileH;
+        __syncthreads();
+        for (int rr = warp; rr < kDiscTileH + 2 * H; rr += 8) {   // prefix sums of tile row rr
+            const int j = r0 - H + rr;
+            unsigned long long carry = 0;
+            if (lane == 0) pre[(size_t)rr * W] = 0;
+            for (int x0 = 0; x0 < W - 1; x0 += 32) {
+                const int x = x0 + lane, i = c0 - H + x;
+                unsigned long long v = (x < W - 1 && j >= 0 && j < n && i >= 0 && i < n) ? cin[(long long)j * n + i] : 0;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned long long u = __shfl_up_sync(0xffffffffu, v, o);
+                    if (lane >= o) v += u;
+                }
+                if (x < W - 1) pre[(size_t)rr * W + x + 1] = carry + v;
+                carry += __shfl_sync(0xffffffffu, v, 31);
+            }
+        }
+        __syncthreads();
+        const int c = threadIdx.x & (kDiscTileW - 1), rg = threadIdx.x / kDiscTileW;   // 4 row groups
+        const int i = c0 + c;
+        for (int r = rg; r < kDiscTileH; r += 4) {
+            const int j = r0 + r;
+            if (i >= n || j >= n) continue;
+            float o = __int_as_float(0x7fc00000);
+            if (i - H >= 0 && i + H < n && j - H >= 0 && j + H < n) {
+                float acc = 0.f;
+                for (int dj = -H; dj <= H; ++dj) {
+                    const int w = sp[dj + H];
+                    const unsigned long long *row = pre + (size_t)(r + dj + H) * W;
+                    acc += (float)(row[c + H + w + 1] - row[c + H - w]);
+                }
+                o = acc * scale;
+            }
+            out[(long long)j * n + i] = o;
+        }
+    }
+}
+
 // Bilinear samples of the convolved map at source positions (Einstein radii).
 __global__ void k_track(const float *f, int n, double half_side, double pix, double y1a, double y2a, double y1b,
                         double y2b, long long npts, double *mu)
@@ -106,8 +247,15 @@ int convolve(mm_ctx *ctx, const MapObj &M, int profile, double size_re, float *d
         int rc = ctx->arena.alloc(g.size() * sizeof(float), (void **)&dg);
         if (rc) return rc;
         if ((e = cudaMemcpyAsync(dg, g.data(), g.size() * sizeof(float), cudaMemcpyHostToDevice, s)) == cudaSuccess) {
-            k_gauss_pass<true><<<grid, 256, 0, s>>>(M.counts, nullptr, tmp, n, dg, h, 0, inv_nrays);
-            k_gauss_pass<false><<<grid, 256, 0, s>>>(nullptr, tmp, dst, n, dg, h, 1, 1.0f);
+            const size_t srow = gauss_row_smem(h), scol = gauss_col_smem(h);
+            if (srow <= kTileSmemMax)
+                k_gauss_rows<true><<<grid, kGaussRowTile, srow, s>>>(M.counts, nullptr, tmp, n, dg, h, inv_nrays);
+            else
+                k_gauss_pass<true><<<grid, 256, 0, s>>>(M.counts, nullptr, tmp, n, dg, h, 0, inv_nrays);
+            if (scol <= kTileSmemMax)
+                k_gauss_cols<<<grid, 256, scol, s>>>(tmp, dst, n, dg, h);
+            else
+                k_gauss_pass<false><<<grid, 256, 0, s>>>(nullptr, tmp, dst, n, dg, h, 1, 1.0f);
             e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         }
@@ -128,7 +276,11 @@ int convolve(mm_ctx *ctx, const MapObj &M, int profile, double size_re, float *d
     int rc = ctx->arena.alloc(span.size() * sizeof(int), (void **)&ds);
     if (rc) return rc;
     if ((e = cudaMemcpyAsync(ds, span.data(), span.size() * sizeof(int), cudaMemcpyHostToDevice, s)) == cudaSuccess) {
-        k_disc<<<grid, 256, 0, s>>>(M.counts, dst, n, ds, H, (float)(1.0 / ((double)taps * M.p.nrays_per_pix)));
+        const float scale = (float)(1.0 / ((double)taps * M.p.nrays_per_pix));
+        if (disc_smem(H) <= kTileSmemMax)
+            k_disc_tiled<<<grid, 256, disc_smem(H), s>>>(M.counts, dst, n, ds, H, scale);
+        else
+            k_disc<<<grid, 256, 0, s>>>(M.counts, dst, n, ds, H, scale);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     }

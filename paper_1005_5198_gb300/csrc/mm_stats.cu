@@ -23,6 +23,11 @@
 namespace mm {
 namespace {
 
+// Shared-memory histograms: up to 96 KB per CTA (12288 bins per map); 200 KB of an SM's
+// shared memory shared between the CTAs of a launch.
+constexpr size_t kHistSmemMax = 96 * 1024;
+constexpr size_t kSmemPerSm = 200 * 1024;
+
 struct StatSums {
     double sum_sq;                 // sum of (Delta m_a - Delta m_b)^2 over pixels counted in both maps
     unsigned long long n_both;
@@ -33,11 +38,10 @@ struct StatSums {
     long long ks_num;              // max_k |c_a(k) n_b - c_b(k) n_a|
 };
 
-__global__ void k_dm_rms(const unsigned *a, const unsigned *b, long long n, double log10_ra, double log10_rb,
-                         StatSums *out)
+// Pass 1 over both maps: sums, empty pixels and the largest count (no logarithms).
+__global__ void k_scan_stats(const unsigned *a, const unsigned *b, long long n, StatSums *out)
 {
-    double sq = 0.0;
-    unsigned long long both = 0, za = 0, zb = 0, sa = 0, sb = 0;
+    unsigned long long za = 0, zb = 0, sa = 0, sb = 0;
     unsigned mx = 0;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
         const unsigned na = a[k], nb = b[k];
@@ -46,16 +50,8 @@ __global__ void k_dm_rms(const unsigned *a, const unsigned *b, long long n, doub
         mx = max(mx, max(na, nb));
         za += na == 0u;
         zb += nb == 0u;
-        if (na && nb) {
-            // Delta m_a - Delta m_b = -2.5 [(log10 N_a - log10 N_rays_a) - (log10 N_b - log10 N_rays_b)]
-            const double d = -2.5 * ((log10((double)na) - log10_ra) - (log10((double)nb) - log10_rb));
-            sq += d * d;
-            both += 1;
-        }
     }
     for (int o = 16; o > 0; o >>= 1) {
-        sq += __shfl_down_sync(0xffffffffu, sq, o);
-        both += __shfl_down_sync(0xffffffffu, both, o);
         za += __shfl_down_sync(0xffffffffu, za, o);
         zb += __shfl_down_sync(0xffffffffu, zb, o);
         sa += __shfl_down_sync(0xffffffffu, sa, o);
@@ -63,8 +59,6 @@ __global__ void k_dm_rms(const unsigned *a, const unsigned *b, long long n, doub
         mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
     }
     if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&out->sum_sq, sq);
-        atomicAdd(&out->n_both, both);
         atomicAdd(&out->zero_a, za);
         atomicAdd(&out->zero_b, zb);
         atomicAdd(&out->sum_a, sa);
@@ -73,10 +67,69 @@ __global__ void k_dm_rms(const unsigned *a, const unsigned *b, long long n, doub
     }
 }
 
-__global__ void k_hist(const unsigned *a, long long n, unsigned *hist)
+// lg[k] = log10(k) for the counts 1 .. nbins - 1 that a pixel can hold (lg[0] unused): the
+// per-pixel logarithms of pass 2 become table reads of the same values.
+__global__ void k_log_table(long long nbins, double *lg)
 {
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
-        atomicAdd(hist + a[k], 1u);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nbins; k += (long long)gridDim.x * blockDim.x)
+        lg[k] = k ? log10((double)k) : 0.0;
+}
+
+// Add 1 to h[key] for every lane holding key (skipped: kNoKey); lanes with equal keys
+// are merged first, so a warp issues one atomic per distinct key.
+constexpr unsigned kNoKey = 0xffffffffu;
+
+__device__ __forceinline__ void hist_add(unsigned *h, unsigned key, unsigned lane)
+{
+    const unsigned same = __match_any_sync(0xffffffffu, key);
+    if (key != kNoKey && lane == (unsigned)(__ffs(same) - 1)) atomicAdd(h + key, (unsigned)__popc(same));
+}
+
+// Pass 2 over both maps: the RMS of Delta m_a - Delta m_b over pixels counted in both,
+//   Delta m_a - Delta m_b = -2.5 [(log10 N_a - log10 N_rays_a) - (log10 N_b - log10 N_rays_b)],
+// and the two count histograms (bins 0 .. nbins - 1, nbins = largest count + 1), kept
+// per CTA in shared memory when SHARED and added to ha / hb at the end.
+template <bool SHARED>
+__global__ void __launch_bounds__(256) k_rms_hist(const unsigned *a, const unsigned *b, long long n, const double *lg,
+                                                  double log10_ra, double log10_rb, long long nbins, unsigned *ha,
+                                                  unsigned *hb, StatSums *out)
+{
+    extern __shared__ unsigned sh[];                          // SHARED: [2 nbins]
+    unsigned *const sa = SHARED ? sh : ha, *const sb = SHARED ? sh + nbins : hb;
+    if (SHARED) {
+        for (long long k = threadIdx.x; k < 2 * nbins; k += blockDim.x) sh[k] = 0u;
+        __syncthreads();
+    }
+    const unsigned lane = threadIdx.x & 31;
+    double sq = 0.0;
+    unsigned long long both = 0;
+    // warp-uniform trip count: the lanes of a warp take consecutive pixels, those past n hold no key
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long w0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31u); w0 < n; w0 += stride) {
+        const long long k = w0 + lane;
+        const bool in = k < n;
+        const unsigned na = in ? a[k] : kNoKey, nb = in ? b[k] : kNoKey;
+        if (in && na && nb) {
+            const double d = -2.5 * ((lg[na] - log10_ra) - (lg[nb] - log10_rb));
+            sq += d * d;
+            both += 1;
+        }
+        hist_add(sa, na, lane);
+        hist_add(sb, nb, lane);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sq += __shfl_down_sync(0xffffffffu, sq, o);
+        both += __shfl_down_sync(0xffffffffu, both, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&out->sum_sq, sq);
+        atomicAdd(&out->n_both, both);
+    }
+    if (SHARED) {
+        __syncthreads();
+        for (long long k = threadIdx.x; k < 2 * nbins; k += blockDim.x)
+            if (sh[k]) atomicAdd(k < nbins ? ha + k : hb + (k - nbins), sh[k]);
+    }
 }
 
 // One CTA of 1024 threads: inclusive prefix sums ca[k], cb[k] of the two count
@@ -194,29 +247,43 @@ extern "C" int mm_map_compare(mm_ctx *ctx, mm_map a, mm_map b, mm_compare *out)
     tmp.v.push_back(d_sum);
     if ((e = cudaMemsetAsync(d_sum, 0, sizeof(StatSums), s)) != cudaSuccess) return cuda_fail(e, "memset");
     const int grid = std::max(1, std::min(4 * ctx->sms, (int)((n + 255) / 256)));
-    k_dm_rms<<<grid, 256, 0, s>>>(A->counts, B->counts, n, std::log10(A->p.nrays_per_pix),
-                                  std::log10(B->p.nrays_per_pix), d_sum);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_dm_rms");
+    k_scan_stats<<<grid, 256, 0, s>>>(A->counts, B->counts, n, d_sum);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_scan_stats");
     StatSums h{};
     if ((e = cudaMemcpyAsync(&h, d_sum, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return cuda_fail(e, "stats readback");
-    // histograms of the counts over 0..max and their prefix sums, then the exact K-S numerator
+    // log10 table over the counts, histograms of the counts over 0..max with the RMS pass,
+    // then their prefix sums and the exact K-S numerator
     const long long nbins = (long long)h.max_count + 1;
     unsigned *hist = nullptr;
     long long *cum = nullptr;
+    double *lg = nullptr;
     if ((rc = ctx->arena.alloc((size_t)(2 * nbins) * sizeof(unsigned), (void **)&hist))) return rc;
     tmp.v.push_back(hist);
     if ((rc = ctx->arena.alloc((size_t)(2 * nbins) * sizeof(long long), (void **)&cum))) return rc;
     tmp.v.push_back(cum);
+    if ((rc = ctx->arena.alloc((size_t)nbins * sizeof(double), (void **)&lg))) return rc;
+    tmp.v.push_back(lg);
     if ((e = cudaMemsetAsync(hist, 0, (size_t)(2 * nbins) * sizeof(unsigned), s)) != cudaSuccess) return cuda_fail(e, "memset");
-    k_hist<<<grid, 256, 0, s>>>(A->counts, n, hist);
-    k_hist<<<grid, 256, 0, s>>>(B->counts, n, hist + nbins);
+    k_log_table<<<std::max(1, std::min(ctx->sms, (int)((nbins + 255) / 256))), 256, 0, s>>>(nbins, lg);
+    const size_t smem = (size_t)(2 * nbins) * sizeof(unsigned);
+    const double lra = std::log10(A->p.nrays_per_pix), lrb = std::log10(B->p.nrays_per_pix);
+    if (smem <= kHistSmemMax) {                                // histograms per CTA in shared memory
+        if ((e = cudaFuncSetAttribute(k_rms_hist<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kHistSmemMax)) != cudaSuccess)
+            return cuda_fail(e, "k_rms_hist shared memory");
+        const int per_sm = std::max(1, std::min(4, (int)(kSmemPerSm / std::max<size_t>(smem, 1))));
+        k_rms_hist<true><<<std::max(1, std::min(per_sm * ctx->sms, (int)((n + 255) / 256))), 256, smem, s>>>(
+            A->counts, B->counts, n, lg, lra, lrb, nbins, hist, hist + nbins, d_sum);
+    } else {
+        k_rms_hist<false><<<grid, 256, 0, s>>>(A->counts, B->counts, n, lg, lra, lrb, nbins, hist, hist + nbins, d_sum);
+    }
     k_scan<<<1, 1024, 0, s>>>(hist, hist + nbins, nbins, cum, cum + nbins);
     const int egrid = std::max(1, std::min(4 * ctx->sms, (int)((2 * nbins + 255) / 256)));
     k_ks_eval<<<egrid, 256, 0, s>>>(hist, hist + nbins, cum, cum + nbins, nbins, n, n, A->p.nrays_per_pix,
                                     B->p.nrays_per_pix, d_sum);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_hist/k_scan/k_ks_eval");
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_rms_hist/k_scan/k_ks_eval");
     if ((e = cudaMemcpyAsync(&h, d_sum, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return cuda_fail(e, "stats readback");

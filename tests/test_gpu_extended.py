@@ -54,3 +54,38 @@ def test_profile_wider_than_map_rejected(shot):
     with pytest.raises(mm.MMError) as e:
         mm.mm_map_convolve(ctx, m, mm.MM_PROFILE_DISC, 10.0)
     assert e.value.code == mm.MM_EINVAL
+
+
+# Wide supports: the tiled kernels stage a support in 48 KB of shared memory (the Gaussian's
+# column pass up to a half-width of 155 pixels, the disc up to a radius of 15 pixels); wider
+# ones run the untiled kernels. Sizes on both sides of each limit, on a 320^2 map.
+CFG_WIDE = dict(CFG, npix_side=320, side=7.5)            # pixel 0.0234375 R_E
+
+
+@pytest.fixture(scope="module")
+def shot_wide():
+    mm.build()
+    c = mm.mm_init(0)
+    n, r = field.nstar_rule(CFG_WIDE["sigma"], CFG_WIDE["gamma"], CFG_WIDE["smooth_frac"], CFG_WIDE["side"])
+    f = synth.lens_field(n, r, 43)
+    lh = mm.mm_create_lenses_from(c, f.x, f.y, f.m)
+    m = mm.mm_shoot(c, lh, mm.params(**CFG_WIDE))
+    counts, _ = mm.mm_map_fetch(c, m)
+    yield c, m, counts
+    mm.mm_destroy(c)
+
+
+@pytest.mark.parametrize("profile,size,half_width", [
+    (mm.MM_PROFILE_GAUSSIAN, 0.905, 155), (mm.MM_PROFILE_GAUSSIAN, 0.93, 159),
+    (mm.MM_PROFILE_DISC, 0.3633, 15), (mm.MM_PROFILE_DISC, 0.5039, 21)])
+def test_wide_supports_match_oracle(shot_wide, profile, size, half_width):
+    ctx, m, counts = shot_wide
+    pix = CFG_WIDE["side"] / CFG_WIDE["npix_side"]
+    h = int(np.ceil(4.0 * size / pix)) if profile == mm.MM_PROFILE_GAUSSIAN else int(np.floor(size / pix))
+    assert h == half_width
+    got = mm.mm_map_convolve(ctx, m, profile, size)
+    ref = oext.convolve(counts, CFG_WIDE["nrays"], profile, size, pix)
+    np.testing.assert_array_equal(np.isnan(got), np.isnan(ref))
+    ok = ~np.isnan(ref)
+    assert ok.sum() == (CFG_WIDE["npix_side"] - 2 * h) ** 2
+    np.testing.assert_allclose(got[ok], ref[ok], rtol=2e-5, atol=1e-6)

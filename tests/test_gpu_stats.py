@@ -22,16 +22,21 @@ def ctx():
     mm.mm_destroy(c)
 
 
-def test_compare_matches_oracle_statistics(ctx):
-    n, r = field.nstar_rule(CFG["sigma"], CFG["gamma"], CFG["smooth_frac"], CFG["side"])
+# The device builds the count histograms per CTA in shared memory up to 12288 bins (the
+# largest count + 1) and in global memory beyond; the second case has counts above that.
+@pytest.mark.parametrize("npix,nrays_a,nrays_b,shared_hist", [(256, 64.0, 25.0, True), (64, 4000.0, 1000.0, False)])
+def test_compare_matches_oracle_statistics(ctx, npix, nrays_a, nrays_b, shared_hist):
+    cfg = dict(CFG, npix_side=npix, nrays=nrays_a)
+    n, r = field.nstar_rule(cfg["sigma"], cfg["gamma"], cfg["smooth_frac"], cfg["side"])
     f = synth.lens_field(n, r, 31)
     lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
-    a = mm.mm_shoot(ctx, lh, mm.params(**CFG))
-    b = mm.mm_shoot(ctx, lh, mm.params(**dict(CFG, nrays=25.0)))        # a noisier map of the same field
+    a = mm.mm_shoot(ctx, lh, mm.params(**cfg))
+    b = mm.mm_shoot(ctx, lh, mm.params(**dict(cfg, nrays=nrays_b)))     # a noisier map of the same field
     ca, _ = mm.mm_map_fetch(ctx, a)
     cb, _ = mm.mm_map_fetch(ctx, b)
+    assert (max(int(ca.max()), int(cb.max())) + 1 <= 12288) == shared_hist
     got = mm.mm_map_compare(ctx, a, b)
-    ref = ostats.compare(ca, 64.0, cb, 25.0)
+    ref = ostats.compare(ca, nrays_a, cb, nrays_b)
     print(got, ref)
     assert got["ks_d"] == pytest.approx(ref["ks_d"], abs=1e-15)
     assert got["n_rms"] == ref["n_rms"] and got["zero_a"] == ref["zero_a"] and got["zero_b"] == ref["zero_b"]
