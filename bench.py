@@ -361,6 +361,30 @@ def reduce_over_ranks(dist, device, t_total, inter):
     return float(tt.item()), float(ti.item())
 
 
+def host_cpu():
+    """The host CPU's model name and architecture (from lscpu, else /proc/cpuinfo, else platform)."""
+    import platform
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for line in fh:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return f"{model or platform.processor() or 'unknown'} ({platform.machine()}, {os.cpu_count()} logical CPUs)"
+
+
 def cpu_baseline(seconds_target: float = 15.0):
     """The FP64 CPU oracle on a strided sample of the Fig. 1 map, host cores."""
     import oracle
@@ -375,7 +399,7 @@ def cpu_baseline(seconds_target: float = 15.0):
     _, tot = oracle.shoot_map(cfg, f, stride=CPU_STRIDE, threads=threads)
     dt = time.perf_counter() - t0
     inter = tot["shot"] * n
-    return {"value": inter / dt, "unit": "interactions/s", "cores": threads, "kind": "oracle",
+    return {"value": inter / dt, "unit": "interactions/s", "cores": threads, "kind": "oracle", "host": host_cpu(),
             "sample": f"Fig. 1 map, every {CPU_STRIDE}th ray row and column ({tot['shot']} rays x {n} lenses "
                       f"= {inter:.3e} interactions) in {dt:.1f} s, FP64, OpenMP"}
 
@@ -467,6 +491,7 @@ def run_reference(args):
             "impl": "reference",
             "config": {"workload": WORKLOAD, "sample": f"every {stride}th ray row and column per step"},
             "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": threads, "kind": "oracle",
+                             "host": host_cpu(),
                              "sample": f"every {stride}th ray row and column of the Fig. 1 map per step "
                                        f"({shot} rays x {n} lenses)"},
             "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
