@@ -69,7 +69,8 @@ __global__ void k_disc(const unsigned *cin, float *out, int n, const int *span, 
 
 // ---- tiled forms of the passes above: the same per-pixel sums in the same order ----
 
-constexpr int kGaussRowTile = 256;                     // outputs per CTA along a row (= threads)
+constexpr int kGaussRowThreads = 256, kGaussRowPer = 4;   // row pass: 4 outputs per thread, 256 apart
+constexpr int kGaussRowTile = kGaussRowThreads * kGaussRowPer;   // outputs per CTA along a row
 constexpr int kGaussColTileW = 32, kGaussColTileH = 64;   // column pass: 32 columns x 64 rows per CTA
 constexpr int kDiscTileW = 64, kDiscTileH = 32;        // disc: 64 x 32 outputs per CTA
 constexpr size_t kTileSmemMax = 48 * 1024;             // dynamic shared memory of a tiled CTA (no opt-in);
@@ -85,14 +86,15 @@ __host__ __device__ inline size_t disc_smem(int H)
     return (size_t)(kDiscTileH + 2 * H) * (kDiscTileW + 2 * H + 1) * 8 + (size_t)(2 * H + 1) * 4;
 }
 
-// Row pass (dir 0 of k_gauss_pass): a CTA stages the row segment [i0 - h, i0 + 256 + h)
-// and the taps in shared memory; thread t sums output i0 + t.
+// Row pass (dir 0 of k_gauss_pass): a CTA stages the row segment [i0 - h, i0 + 1024 + h)
+// and the taps in shared memory; thread t sums outputs i0 + t + 256 u (u < 4), tap by tap,
+// so a tap weight is read once for four outputs (each output still adds its taps in order).
 template <bool FROM_COUNTS>
-__global__ void __launch_bounds__(kGaussRowTile) k_gauss_rows(const unsigned *cin, const float *fin, float *out, int n,
-                                                              const float *g, int h, float inv_nrays)
+__global__ void __launch_bounds__(kGaussRowThreads) k_gauss_rows(const unsigned *cin, const float *fin, float *out,
+                                                                 int n, const float *g, int h, float inv_nrays)
 {
     extern __shared__ float sm[];
-    float *const gs = sm, *const seg = sm + 2 * h + 1;      // taps [2h + 1], inputs [256 + 2h]
+    float *const gs = sm, *const seg = sm + 2 * h + 1;      // taps [2h + 1], inputs [1024 + 2h]
     for (int k = threadIdx.x; k < 2 * h + 1; k += blockDim.x) gs[k] = g[k];
     const int segs = (n + kGaussRowTile - 1) / kGaussRowTile;
     const long long tiles = (long long)n * segs;
@@ -109,15 +111,19 @@ __global__ void __launch_bounds__(kGaussRowTile) k_gauss_rows(const unsigned *ci
             seg[q] = v;
         }
         __syncthreads();
-        const int i = i0 + (int)threadIdx.x;
-        if (i < n) {
-            float o = __int_as_float(0x7fc00000);
-            if (i - h >= 0 && i + h < n) {
-                float acc = 0.f;
-                for (int k = 0; k <= 2 * h; ++k) acc = fmaf(gs[k], seg[threadIdx.x + k], acc);
-                o = acc;
-            }
-            out[(long long)j * n + i] = o;
+        float acc[kGaussRowPer];
+#pragma unroll
+        for (int u = 0; u < kGaussRowPer; ++u) acc[u] = 0.f;
+        for (int k = 0; k <= 2 * h; ++k) {
+            const float gk = gs[k];
+#pragma unroll
+            for (int u = 0; u < kGaussRowPer; ++u)
+                acc[u] = fmaf(gk, seg[threadIdx.x + kGaussRowThreads * u + k], acc[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < kGaussRowPer; ++u) {
+            const int i = i0 + (int)threadIdx.x + kGaussRowThreads * u;
+            if (i < n) out[(long long)j * n + i] = (i - h >= 0 && i + h < n) ? acc[u] : __int_as_float(0x7fc00000);
         }
     }
 }
@@ -140,17 +146,21 @@ __global__ void __launch_bounds__(256) k_gauss_cols(const float *fin, float *out
             tile[q] = (j >= 0 && j < n && i < n) ? fin[(long long)j * n + i] : 0.f;
         }
         __syncthreads();
+        // thread (tx, ty) sums rows ty + 8 u of the tile, tap by tap (a weight read once for 8 outputs)
+        constexpr int kPer = kGaussColTileH / 8;
+        float acc[kPer];
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) acc[u] = 0.f;
+        for (int k = 0; k <= 2 * h; ++k) {
+            const float gk = gs[k];
+#pragma unroll
+            for (int u = 0; u < kPer; ++u) acc[u] = fmaf(gk, tile[(ty + 8 * u + k) * kGaussColTileW + tx], acc[u]);
+        }
         const int i = c0 + tx;
-        for (int rr = ty; rr < kGaussColTileH; rr += 8) {
-            const int j = r0 + rr;
-            if (i >= n || j >= n) continue;
-            float o = __int_as_float(0x7fc00000);
-            if (j - h >= 0 && j + h < n) {
-                float acc = 0.f;
-                for (int k = 0; k <= 2 * h; ++k) acc = fmaf(gs[k], tile[(rr + k) * kGaussColTileW + tx], acc);
-                o = acc;
-            }
-            out[(long long)j * n + i] = o;
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const int j = r0 + ty + 8 * u;
+            if (i < n && j < n) out[(long long)j * n + i] = (j - h >= 0 && j + h < n) ? acc[u] : __int_as_float(0x7fc00000);
         }
     }
 }
@@ -249,7 +259,7 @@ int convolve(mm_ctx *ctx, const MapObj &M, int profile, double size_re, float *d
         if ((e = cudaMemcpyAsync(dg, g.data(), g.size() * sizeof(float), cudaMemcpyHostToDevice, s)) == cudaSuccess) {
             const size_t srow = gauss_row_smem(h), scol = gauss_col_smem(h);
             if (srow <= kTileSmemMax)
-                k_gauss_rows<true><<<grid, kGaussRowTile, srow, s>>>(M.counts, nullptr, tmp, n, dg, h, inv_nrays);
+                k_gauss_rows<true><<<grid, kGaussRowThreads, srow, s>>>(M.counts, nullptr, tmp, n, dg, h, inv_nrays);
             else
                 k_gauss_pass<true><<<grid, 256, 0, s>>>(M.counts, nullptr, tmp, n, dg, h, 0, inv_nrays);
             if (scol <= kTileSmemMax)
