@@ -209,7 +209,10 @@ __global__ void __launch_bounds__(256) k_disc_tiled(const unsigned *cin, float *
                 for (int dj = -H; dj <= H; ++dj) {
                     const int w = sp[dj + H];
                     const unsigned long long *row = pre + (size_t)(r + dj + H) * W;
-                    acc += (float)(row[c + H + w + 1] - row[c + H - w]);
+                    const unsigned long long d = row[c + H + w + 1] - row[c + H - w];
+                    // the same float either way; the 64-bit conversion runs on the FP64 pipe
+                    if (d >> 32) acc += (float)d;
+                    else acc += (float)(unsigned)d;
                 }
                 o = acc * scale;
             }
