@@ -179,16 +179,21 @@ __global__ void __launch_bounds__(256) k_disc_tiled(const unsigned *cin, float *
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int cols = (n + kDiscTileW - 1) / kDiscTileW, rows = (n + kDiscTileH - 1) / kDiscTileH;
     const long long tiles = (long long)cols * rows;
+    // below this count every span of at most 2H + 1 pixels sums to less than 2^32
+    const unsigned small_count = (unsigned)(0xffffffffull / (unsigned long long)(2 * H + 1));
     for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
         const int c0 = (int)(t % cols) * kDiscTileW, r0 = (int)(t / cols) * kDiscTileH;
         __syncthreads();
+        int large = 0;
         for (int rr = warp; rr < kDiscTileH + 2 * H; rr += 8) {   // prefix sums of tile row rr
             const int j = r0 - H + rr;
             unsigned long long carry = 0;
             if (lane == 0) pre[(size_t)rr * W] = 0;
             for (int x0 = 0; x0 < W - 1; x0 += 32) {
                 const int x = x0 + lane, i = c0 - H + x;
-                unsigned long long v = (x < W - 1 && j >= 0 && j < n && i >= 0 && i < n) ? cin[(long long)j * n + i] : 0;
+                const unsigned cnt = (x < W - 1 && j >= 0 && j < n && i >= 0 && i < n) ? cin[(long long)j * n + i] : 0u;
+                large |= cnt >= small_count;
+                unsigned long long v = cnt;
                 for (int o = 1; o < 32; o <<= 1) {
                     const unsigned long long u = __shfl_up_sync(0xffffffffu, v, o);
                     if (lane >= o) v += u;
@@ -197,7 +202,9 @@ __global__ void __launch_bounds__(256) k_disc_tiled(const unsigned *cin, float *
                 carry += __shfl_sync(0xffffffffu, v, 31);
             }
         }
-        __syncthreads();
+        // with no large count in the tile every span sum fits 32 bits, and converts to the same
+        // float through 32 bits (the 64-bit conversion runs on the FP64 pipe)
+        const bool spans32 = !__syncthreads_or(large);
         const int c = threadIdx.x & (kDiscTileW - 1), rg = threadIdx.x / kDiscTileW;   // 4 row groups
         const int i = c0 + c;
         for (int r = rg; r < kDiscTileH; r += 4) {
@@ -206,13 +213,18 @@ __global__ void __launch_bounds__(256) k_disc_tiled(const unsigned *cin, float *
             float o = __int_as_float(0x7fc00000);
             if (i - H >= 0 && i + H < n && j - H >= 0 && j + H < n) {
                 float acc = 0.f;
-                for (int dj = -H; dj <= H; ++dj) {
-                    const int w = sp[dj + H];
-                    const unsigned long long *row = pre + (size_t)(r + dj + H) * W;
-                    const unsigned long long d = row[c + H + w + 1] - row[c + H - w];
-                    // the same float either way; the 64-bit conversion runs on the FP64 pipe
-                    if (d >> 32) acc += (float)d;
-                    else acc += (float)(unsigned)d;
+                if (spans32) {
+                    for (int dj = -H; dj <= H; ++dj) {
+                        const int w = sp[dj + H];
+                        const unsigned long long *row = pre + (size_t)(r + dj + H) * W;
+                        acc += (float)(unsigned)(row[c + H + w + 1] - row[c + H - w]);
+                    }
+                } else {
+                    for (int dj = -H; dj <= H; ++dj) {
+                        const int w = sp[dj + H];
+                        const unsigned long long *row = pre + (size_t)(r + dj + H) * W;
+                        acc += (float)(row[c + H + w + 1] - row[c + H - w]);
+                    }
                 }
                 o = acc * scale;
             }
