@@ -67,12 +67,36 @@ __global__ void k_scan_stats(const unsigned *a, const unsigned *b, long long n, 
     }
 }
 
-// lg[k] = log10(k) for the counts 1 .. nbins - 1 that a pixel can hold (lg[0] unused): the
-// per-pixel logarithms of pass 2 become table reads of the same values.
-__global__ void k_log_table(long long nbins, double *lg)
+// Per count k >= 1 that a pixel can hold, Delta m up to the factor -2.5 of each map,
+// log10(k) - log10(N_rays), as a float-float pair (hi, lo) of its FP64 value: pass 2
+// then forms the per-pixel differences in FP32 arithmetic (the FP64 pipe runs at 1/64 of
+// the FP32 rate). ta[0], tb[0] unused.
+__global__ void k_log_table(long long nbins, double log10_ra, double log10_rb, float2 *ta, float2 *tb)
 {
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nbins; k += (long long)gridDim.x * blockDim.x)
-        lg[k] = k ? log10((double)k) : 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nbins; k += (long long)gridDim.x * blockDim.x) {
+        const double l = k ? log10((double)k) : 0.0, va = l - log10_ra, vb = l - log10_rb;
+        const float ah = __double2float_rn(va), bh = __double2float_rn(vb);
+        ta[k] = make_float2(ah, __double2float_rn(va - (double)ah));
+        tb[k] = make_float2(bh, __double2float_rn(vb - (double)bh));
+    }
+}
+
+// Float-float helpers (error-free transformations: Knuth's TwoSum, FMA-based TwoProd).
+__device__ __forceinline__ void ff_two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (sh, sl) += (ph, pl), renormalised.
+__device__ __forceinline__ void ff_accumulate(float &sh, float &sl, float ph, float pl)
+{
+    float s, e;
+    ff_two_sum(sh, ph, s, e);
+    e = __fadd_rn(e, __fadd_rn(sl, pl));
+    sh = __fadd_rn(s, e);
+    sl = __fsub_rn(e, __fsub_rn(sh, s));
 }
 
 // Add 1 to h[key] for every lane holding key (skipped: kNoKey); lanes with equal keys
@@ -86,13 +110,15 @@ __device__ __forceinline__ void hist_add(unsigned *h, unsigned key, unsigned lan
 }
 
 // Pass 2 over both maps: the RMS of Delta m_a - Delta m_b over pixels counted in both,
-//   Delta m_a - Delta m_b = -2.5 [(log10 N_a - log10 N_rays_a) - (log10 N_b - log10 N_rays_b)],
-// and the two count histograms (bins 0 .. nbins - 1, nbins = largest count + 1), kept
-// per CTA in shared memory when SHARED and added to ha / hb at the end.
+//   Delta m_a - Delta m_b = -2.5 [(log10 N_a - log10 N_rays_a) - (log10 N_b - log10 N_rays_b)]
+//                         = -2.5 (ta[N_a] - tb[N_b]),
+// the difference and its square in float-float (about 1e-14 relative), summed per thread in
+// float-float and then in FP64; and the two count histograms (bins 0 .. nbins - 1,
+// nbins = largest count + 1), kept per CTA in shared memory when SHARED and added to ha / hb.
 template <bool SHARED>
-__global__ void __launch_bounds__(256) k_rms_hist(const unsigned *a, const unsigned *b, long long n, const double *lg,
-                                                  double log10_ra, double log10_rb, long long nbins, unsigned *ha,
-                                                  unsigned *hb, StatSums *out)
+__global__ void __launch_bounds__(256) k_rms_hist(const unsigned *a, const unsigned *b, long long n, const float2 *ta,
+                                                  const float2 *tb, long long nbins, unsigned *ha, unsigned *hb,
+                                                  StatSums *out)
 {
     extern __shared__ unsigned sh[];                          // SHARED: [2 nbins]
     unsigned *const sa = SHARED ? sh : ha, *const sb = SHARED ? sh + nbins : hb;
@@ -101,7 +127,7 @@ __global__ void __launch_bounds__(256) k_rms_hist(const unsigned *a, const unsig
         __syncthreads();
     }
     const unsigned lane = threadIdx.x & 31;
-    double sq = 0.0;
+    float qh = 0.f, ql = 0.f;                                 // float-float sum of (Delta m_a - Delta m_b)^2 / 6.25
     unsigned long long both = 0;
     // warp-uniform trip count: the lanes of a warp take consecutive pixels, those past n hold no key
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -110,13 +136,21 @@ __global__ void __launch_bounds__(256) k_rms_hist(const unsigned *a, const unsig
         const bool in = k < n;
         const unsigned na = in ? a[k] : kNoKey, nb = in ? b[k] : kNoKey;
         if (in && na && nb) {
-            const double d = -2.5 * ((lg[na] - log10_ra) - (lg[nb] - log10_rb));
-            sq += d * d;
+            // d = ta[na] - tb[nb] in float-float, then d^2
+            const float2 x = ta[na], y = tb[nb];
+            float dh, dl;
+            ff_two_sum(x.x, -y.x, dh, dl);
+            dl = __fadd_rn(dl, __fsub_rn(x.y, y.y));
+            const float d = __fadd_rn(dh, dl), de = __fsub_rn(dl, __fsub_rn(d, dh));
+            const float ph = __fmul_rn(d, d);
+            const float pl = __fmaf_rn(d, d, -ph) + 2.f * d * de;
+            ff_accumulate(qh, ql, ph, pl);
             both += 1;
         }
         hist_add(sa, na, lane);
         hist_add(sb, nb, lane);
     }
+    double sq = 6.25 * ((double)qh + (double)ql);              // Delta m differences carry the factor -2.5
     for (int o = 16; o > 0; o >>= 1) {
         sq += __shfl_down_sync(0xffffffffu, sq, o);
         both += __shfl_down_sync(0xffffffffu, both, o);
@@ -258,26 +292,28 @@ extern "C" int mm_map_compare(mm_ctx *ctx, mm_map a, mm_map b, mm_compare *out)
     const long long nbins = (long long)h.max_count + 1;
     unsigned *hist = nullptr;
     long long *cum = nullptr;
-    double *lg = nullptr;
+    float2 *tab = nullptr;                                     // [2 nbins]: map a, then map b
     if ((rc = ctx->arena.alloc((size_t)(2 * nbins) * sizeof(unsigned), (void **)&hist))) return rc;
     tmp.v.push_back(hist);
     if ((rc = ctx->arena.alloc((size_t)(2 * nbins) * sizeof(long long), (void **)&cum))) return rc;
     tmp.v.push_back(cum);
-    if ((rc = ctx->arena.alloc((size_t)nbins * sizeof(double), (void **)&lg))) return rc;
-    tmp.v.push_back(lg);
+    if ((rc = ctx->arena.alloc((size_t)(2 * nbins) * sizeof(float2), (void **)&tab))) return rc;
+    tmp.v.push_back(tab);
     if ((e = cudaMemsetAsync(hist, 0, (size_t)(2 * nbins) * sizeof(unsigned), s)) != cudaSuccess) return cuda_fail(e, "memset");
-    k_log_table<<<std::max(1, std::min(ctx->sms, (int)((nbins + 255) / 256))), 256, 0, s>>>(nbins, lg);
-    const size_t smem = (size_t)(2 * nbins) * sizeof(unsigned);
     const double lra = std::log10(A->p.nrays_per_pix), lrb = std::log10(B->p.nrays_per_pix);
+    k_log_table<<<std::max(1, std::min(ctx->sms, (int)((nbins + 255) / 256))), 256, 0, s>>>(nbins, lra, lrb, tab,
+                                                                                           tab + nbins);
+    const size_t smem = (size_t)(2 * nbins) * sizeof(unsigned);
     if (smem <= kHistSmemMax) {                                // histograms per CTA in shared memory
         if ((e = cudaFuncSetAttribute(k_rms_hist<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)kHistSmemMax)) != cudaSuccess)
             return cuda_fail(e, "k_rms_hist shared memory");
         const int per_sm = std::max(1, std::min(4, (int)(kSmemPerSm / std::max<size_t>(smem, 1))));
         k_rms_hist<true><<<std::max(1, std::min(per_sm * ctx->sms, (int)((n + 255) / 256))), 256, smem, s>>>(
-            A->counts, B->counts, n, lg, lra, lrb, nbins, hist, hist + nbins, d_sum);
+            A->counts, B->counts, n, tab, tab + nbins, nbins, hist, hist + nbins, d_sum);
     } else {
-        k_rms_hist<false><<<grid, 256, 0, s>>>(A->counts, B->counts, n, lg, lra, lrb, nbins, hist, hist + nbins, d_sum);
+        k_rms_hist<false><<<grid, 256, 0, s>>>(A->counts, B->counts, n, tab, tab + nbins, nbins, hist, hist + nbins,
+                                               d_sum);
     }
     k_scan<<<1, 1024, 0, s>>>(hist, hist + nbins, nbins, cum, cum + nbins);
     const int egrid = std::max(1, std::min(4 * ctx->sms, (int)((2 * nbins + 255) / 256)));
