@@ -166,69 +166,83 @@ __global__ void __launch_bounds__(256) k_gauss_cols(const float *fin, float *out
 }
 
 // Disc: a CTA stages the counts of rows [r0 - H, r0 + 32 + H) x columns [c0 - H, c0 + 64 + H)
-// as 64-bit prefix sums along each row (one warp per row, with a leading zero), so the
-// sum over a row span [i - w, i + w] is one exact difference, as k_disc's 64-bit sum.
+// as prefix sums along each row (one warp per row, with a leading zero), so the sum over a row
+// span [i - w, i + w] is one difference, as k_disc's 64-bit sum. The prefix sums are taken
+// modulo 2^32 first: a CTA-wide vote finds whether any count of the tile reaches
+// 2^32 / (2H + 1); if none does, every span sum is below 2^32, so the 32-bit difference is
+// exact and converts to the same float. Otherwise the tile is staged again in 64 bits.
+template <typename P>
+__device__ __forceinline__ int disc_prefix_rows(const unsigned *cin, int n, int r0, int c0, int H, int W, P *pre,
+                                                unsigned small_count)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int large = 0;
+    for (int rr = warp; rr < kDiscTileH + 2 * H; rr += 8) {       // prefix sums of tile row rr
+        const int j = r0 - H + rr;
+        P carry = 0;
+        if (lane == 0) pre[(size_t)rr * W] = 0;
+        for (int x0 = 0; x0 < W - 1; x0 += 32) {
+            const int x = x0 + lane, i = c0 - H + x;
+            const unsigned cnt = (x < W - 1 && j >= 0 && j < n && i >= 0 && i < n) ? cin[(long long)j * n + i] : 0u;
+            large |= cnt >= small_count;
+            P v = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const P u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += u;
+            }
+            if (x < W - 1) pre[(size_t)rr * W + x + 1] = carry + v;
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
+    }
+    return large;
+}
+
+template <typename P>
+__device__ __forceinline__ void disc_outputs(const P *pre, const int *sp, float *out, int n, int r0, int c0, int H,
+                                             int W, float scale)
+{
+    const int c = threadIdx.x & (kDiscTileW - 1), rg = threadIdx.x / kDiscTileW;   // 4 row groups
+    const int i = c0 + c;
+    for (int r = rg; r < kDiscTileH; r += 4) {
+        const int j = r0 + r;
+        if (i >= n || j >= n) continue;
+        float o = __int_as_float(0x7fc00000);
+        if (i - H >= 0 && i + H < n && j - H >= 0 && j + H < n) {
+            float acc = 0.f;
+            for (int dj = -H; dj <= H; ++dj) {
+                const int w = sp[dj + H];
+                const P *row = pre + (size_t)(r + dj + H) * W;
+                acc += (float)(P)(row[c + H + w + 1] - row[c + H - w]);
+            }
+            o = acc * scale;
+        }
+        out[(long long)j * n + i] = o;
+    }
+}
+
 __global__ void __launch_bounds__(256) k_disc_tiled(const unsigned *cin, float *out, int n, const int *span, int H,
                                                     float scale)
 {
     extern __shared__ unsigned long long psm[];
     const int W = kDiscTileW + 2 * H + 1;                  // prefix row length
-    unsigned long long *const pre = psm;                   // [(32 + 2H) x W]
+    unsigned long long *const pre64 = psm;                 // [(32 + 2H) x W], or the same bytes as
+    unsigned *const pre32 = (unsigned *)psm;               // [(32 + 2H) x W] 32-bit sums
     int *const sp = (int *)(psm + (size_t)(kDiscTileH + 2 * H) * W);
     for (int k = threadIdx.x; k < 2 * H + 1; k += blockDim.x) sp[k] = span[k];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int cols = (n + kDiscTileW - 1) / kDiscTileW, rows = (n + kDiscTileH - 1) / kDiscTileH;
     const long long tiles = (long long)cols * rows;
-    // below this count every span of at most 2H + 1 pixels sums to less than 2^32
     const unsigned small_count = (unsigned)(0xffffffffull / (unsigned long long)(2 * H + 1));
     for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
         const int c0 = (int)(t % cols) * kDiscTileW, r0 = (int)(t / cols) * kDiscTileH;
         __syncthreads();
-        int large = 0;
-        for (int rr = warp; rr < kDiscTileH + 2 * H; rr += 8) {   // prefix sums of tile row rr
-            const int j = r0 - H + rr;
-            unsigned long long carry = 0;
-            if (lane == 0) pre[(size_t)rr * W] = 0;
-            for (int x0 = 0; x0 < W - 1; x0 += 32) {
-                const int x = x0 + lane, i = c0 - H + x;
-                const unsigned cnt = (x < W - 1 && j >= 0 && j < n && i >= 0 && i < n) ? cin[(long long)j * n + i] : 0u;
-                large |= cnt >= small_count;
-                unsigned long long v = cnt;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const unsigned long long u = __shfl_up_sync(0xffffffffu, v, o);
-                    if (lane >= o) v += u;
-                }
-                if (x < W - 1) pre[(size_t)rr * W + x + 1] = carry + v;
-                carry += __shfl_sync(0xffffffffu, v, 31);
-            }
-        }
-        // with no large count in the tile every span sum fits 32 bits, and converts to the same
-        // float through 32 bits (the 64-bit conversion runs on the FP64 pipe)
-        const bool spans32 = !__syncthreads_or(large);
-        const int c = threadIdx.x & (kDiscTileW - 1), rg = threadIdx.x / kDiscTileW;   // 4 row groups
-        const int i = c0 + c;
-        for (int r = rg; r < kDiscTileH; r += 4) {
-            const int j = r0 + r;
-            if (i >= n || j >= n) continue;
-            float o = __int_as_float(0x7fc00000);
-            if (i - H >= 0 && i + H < n && j - H >= 0 && j + H < n) {
-                float acc = 0.f;
-                if (spans32) {
-                    for (int dj = -H; dj <= H; ++dj) {
-                        const int w = sp[dj + H];
-                        const unsigned long long *row = pre + (size_t)(r + dj + H) * W;
-                        acc += (float)(unsigned)(row[c + H + w + 1] - row[c + H - w]);
-                    }
-                } else {
-                    for (int dj = -H; dj <= H; ++dj) {
-                        const int w = sp[dj + H];
-                        const unsigned long long *row = pre + (size_t)(r + dj + H) * W;
-                        acc += (float)(row[c + H + w + 1] - row[c + H - w]);
-                    }
-                }
-                o = acc * scale;
-            }
-            out[(long long)j * n + i] = o;
+        const int large = disc_prefix_rows<unsigned>(cin, n, r0, c0, H, W, pre32, small_count);
+        if (!__syncthreads_or(large)) {
+            disc_outputs<unsigned>(pre32, sp, out, n, r0, c0, H, W, scale);
+        } else {                                           // a count of 2^32 / (2H + 1) or more: 64 bits
+            __syncthreads();
+            disc_prefix_rows<unsigned long long>(cin, n, r0, c0, H, W, pre64, small_count);
+            __syncthreads();
+            disc_outputs<unsigned long long>(pre64, sp, out, n, r0, c0, H, W, scale);
         }
     }
 }
