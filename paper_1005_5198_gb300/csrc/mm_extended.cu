@@ -1,7 +1,7 @@
-// mm_extended.cu -- magnification of extended sources: the map convolved with a
-// source profile (Sect. 1: "the magnification of an extended source is found by
-// convolving a source profile with the magnification map"), and light curves of
-// a source moving along a straight track across the convolved map.
+// mm_extended.cu -- magnification of extended sources (Sect. 1): a point-source map,
+// convolved with the brightness profile of a finite source, gives that source's
+// magnification at every position; light curves sample the convolved map along a
+// straight track of the source.
 //
 // Readings where the paper gives no detail:
 //   * mu = N / N_rays per pixel; the profile is discretised on the pixel grid and
