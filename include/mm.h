@@ -331,8 +331,8 @@ typedef struct {
 int mm_map_compare(mm_ctx *ctx, mm_map a, mm_map b, mm_compare *out);
 
 /* ---- extended sources (Sect. 1) --------------------------------------------
- * The magnification of an extended source is the map convolved with the source
- * profile. mu = N / N_rays per pixel; the profile is discretised on the pixel
+ * A finite source's magnification at each position: the point-source map
+ * convolved with its brightness profile. mu = N / N_rays per pixel; the profile is discretised on the pixel
  * grid and normalised to unit sum:
  *   MM_PROFILE_GAUSSIAN  w(i, j) = g(i) g(j), g(k) = exp(-(k p)^2 / (2 size^2)),
  *                        |k| <= ceil(4 size / p) (square support, separable);

@@ -1,7 +1,7 @@
 """Extended-source magnification of the oracle (TEST INFRASTRUCTURE; see the package docstring).
 
-Sect. 1: the magnification of an extended source is the magnification map
-convolved with the source profile. Readings (the same as the library's, written
+Sect. 1: a finite source's magnification at each position is the point-source
+map convolved with its brightness profile. Readings (the same as the library's, written
 independently): mu = N / N_rays per pixel; the profile is discretised on the
 pixel grid and normalised to unit sum -- Gaussian w(i, j) = g(i) g(j) with
 g(k) = exp(-(k p)^2 / (2 s^2)) for |k| <= ceil(4 s / p), or a uniform disc
