@@ -2,7 +2,9 @@
 
 The copy is built in a temporary directory on the CPU; the real oracle is
 never modified. This shows that the pins in test_oracle_pins.py constrain
-every term of the lens equation, the lattice, the binning and the layout.
+every term of the lens equation, the lattice, the binning and the layout,
+those in test_oracle_far.py the far-field series, and those in
+test_oracle_stats.py the K-S probability of the map statistics.
 """
 import os
 import shutil
@@ -44,13 +46,27 @@ FAR_MUTATIONS = [
 ]
 
 
-@pytest.mark.parametrize("name,old,new,pins", [m + (PINS,) for m in MUTATIONS] + [m + (FAR,) for m in FAR_MUTATIONS],
-                         ids=[m[0] for m in MUTATIONS + FAR_MUTATIONS])
-def test_pins_catch_planted_mistake(tmp_path, name, old, new, pins):
+# map statistics (Sect. 3.1): the K-S probability, pinned by test_oracle_stats.py
+STATS = "tests/test_oracle_stats.py"
+STATS_MUTATIONS = [
+    ("K-S n_e as the sum of the sizes", "ne = na * nb / (na + nb)", "ne = na + nb"),
+    ("K-S n_e as the smaller size", "ne = na * nb / (na + nb)", "ne = min(na, nb)"),
+    ("K-S correction dropped", "kolmogorov((s + 0.12 + 0.11 / s) * d)", "kolmogorov(s * d)"),
+    ("K-S 0.11/sqrt(n_e) term dropped", "kolmogorov((s + 0.12 + 0.11 / s) * d)", "kolmogorov((s + 0.12) * d)"),
+    ("K-S 0.11 * sqrt(n_e) instead of 0.11/sqrt(n_e)", "kolmogorov((s + 0.12 + 0.11 / s) * d)",
+     "kolmogorov((s + 0.12 + 0.11 * s) * d)"),
+]
+
+CASES = ([m + (PINS, "mm_oracle.c") for m in MUTATIONS] + [m + (FAR, "mm_oracle.c") for m in FAR_MUTATIONS]
+         + [m + (STATS, "stats.py") for m in STATS_MUTATIONS])
+
+
+@pytest.mark.parametrize("name,old,new,pins,target", CASES, ids=[c[0] for c in CASES])
+def test_pins_catch_planted_mistake(tmp_path, name, old, new, pins, target):
     for d in ("oracle", "synth", "tests"):
         shutil.copytree(os.path.join(ROOT, d), tmp_path / d,
                         ignore=shutil.ignore_patterns("_build", "__pycache__", "*.so"))
-    src = tmp_path / "oracle" / "mm_oracle.c"
+    src = tmp_path / "oracle" / target
     text = src.read_text()
     assert text.count(old) == 1, f"mutation site not found: {old}"
     src.write_text(text.replace(old, new))

@@ -51,3 +51,43 @@ def test_ks_of_counts_equals_ks_of_delta_m():
     b = rng.poisson(31.0, 5000)
     assert stats.ks_statistic(stats.delta_m(a, 30.0), stats.delta_m(b, 30.0)) == pytest.approx(
         stats.ks_statistic(a, b), abs=1e-15)
+
+
+# Critical values of the Kolmogorov distribution, Q(lambda) = P(K > lambda), as tabulated by
+# Smirnov (1948) and reprinted in standard statistical tables: the probability the K-S test of
+# Sect. 3.1 reports at intermediate D, where neither 0 nor 1 pins it.
+KOLMOGOROV_TABLE = [(0.20, 1.0727), (0.10, 1.2238), (0.05, 1.3581), (0.025, 1.4802), (0.01, 1.6276),
+                    (0.005, 1.7308), (0.001, 1.9495)]
+
+
+@pytest.mark.parametrize("na,nb", [(3000, 1500), (12, 6), (40, 10)])
+def test_ks_probability_at_tabulated_kolmogorov_points(na, nb):
+    """D is placed where the corrected argument (sqrt(n_e) + 0.12 + 0.11/sqrt(n_e)) D, with
+    n_e = n_a n_b / (n_a + n_b), equals a tabulated critical value; the probability must equal that
+    value's significance level. Unequal sample sizes make n_e differ from n_a, n_b, their sum or their
+    geometric mean; n_e = 1000 makes the correction small but visible (a 0.4 % shift of the argument
+    moves Q(1.3581) by 3 %), n_e = 4 and 8 make the 0.11/sqrt(n_e) term visible. The table's
+    four decimals fix Q to about 5e-5."""
+    ne = na * nb / (na + nb)
+    for alpha, lam in KOLMOGOROV_TABLE:
+        d = lam / (math.sqrt(ne) + 0.12 + 0.11 / math.sqrt(ne))
+        assert stats.ks_probability(d, na, nb) == pytest.approx(alpha, abs=1e-4), (na, nb, alpha)
+    # symmetric in the two samples
+    assert stats.ks_probability(0.3, na, nb) == stats.ks_probability(0.3, nb, na)
+
+
+def test_ks_probability_tracks_the_exact_two_sample_distribution():
+    """The asymptotic form approximates the exact permutation distribution of the two-sample
+    statistic (computed by scipy's exact method, a separate routine): within a quarter of its value
+    for samples of 60 .. 300, where a wrong n_e would be off by one or more orders of magnitude."""
+    from scipy import stats as ss
+    rng = np.random.default_rng(5)
+    for na, nb in [(40, 20), (60, 30), (200, 100)]:
+        for shift in (0.0, 0.4, 0.8):
+            x, y = rng.normal(0.0, 1.0, na), rng.normal(shift, 1.0, nb)
+            r = ss.ks_2samp(x, y, method="exact")
+            d = stats.ks_statistic(x, y)
+            assert d == pytest.approx(r.statistic, abs=1e-15)
+            p = stats.ks_probability(d, na, nb)
+            if r.pvalue > 1e-3:
+                assert abs(p - r.pvalue) <= 0.25 * r.pvalue, (na, nb, shift, p, r.pvalue)
