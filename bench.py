@@ -10,10 +10,10 @@ Reported (one JSON line from rank 0):
   value        ray-lens interactions / s, FP32 compensated path, whole job
   e2e          the same through the public API with host buffers: lens arrays
                uploaded from pinned memory, map shot, counts read back, per step
-  roofline     the shoot kernel against the FP32 ALU peak (152 SMs x 128 lanes
-               x 2 FLOP x 2070 MHz), algorithmic FLOP = 10 per interaction
-               (the paper's N_FLOP convention for the deflection of one ray by
-               one lens)
+  roofline     the shoot kernel against the FP32 ALU peak (the device's SMs x
+               128 lanes x 2 FLOP x 2070 MHz), algorithmic FLOP = 10 per
+               interaction (the paper's N_FLOP convention for the deflection of
+               one ray by one lens); also against the measured FFMA rate
   fp64         the plain FP64 kernel on a ray window of the same map
   cpu_baseline the FP64 CPU oracle on a strided sample of the same map
   clocks       nvidia-smi samples taken during the timed region
@@ -42,8 +42,31 @@ SEED = 2
 FLOP_PER_INTERACTION = 10.0      # Eq. for Phi: N_FLOP = 10 per deflection evaluation
 USEFUL_OPS_PER_INTERACTION = 6.0  # FP32 lane operations no implementation avoids: 2 sub, 1 mul, 3 fma
 USEFUL_OPS_WITH_MASSES = 7.0      # the same plus the mass product, for maps with a mass spectrum
-SMS, LANES, SM_MAX_MHZ = 152, 128, 2070.0
-FP32_PEAK_TFLOPS = SMS * LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+LANES, SM_MAX_MHZ = 128, 2070.0
+# FFMA lane operations per SM per clock measured on GB300 by the pipe probe (bench.py --alu-rates,
+# alu_rates.cu): the attainable FP32 rate, slightly under the 128 lanes of the data sheet
+FFMA_MEASURED_LANE_OPS = 125.1
+
+
+def fp32_peak_tflops(sms: int, lane_ops: float = LANES) -> float:
+    """FP32 FLOP peak: SMs x lane operations per clock x 2 FLOP (FMA) x the maximum SM clock."""
+    return sms * lane_ops * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def lane_peak_per_s(sms: int) -> float:
+    """FP32 lane operations per second at the maximum SM clock."""
+    return sms * LANES * SM_MAX_MHZ * 1e6
+
+
+def device_sms(device: int) -> int:
+    import torch
+    return int(torch.cuda.get_device_properties(device).multi_processor_count)
+
+
+def lens_rule(mm, p):
+    """N* and disc radius of a map from the library's own rule (Eq. nstar with the disc reading)."""
+    g = mm.mm_geometry_of(p)
+    return int(g["nstar"]), float(g["disc_radius"])
 WORKLOAD = ("Fig. 1 map: sigma=0.4, gamma=0, s=0, L=20 R_E, N_pix=1024^2, N_rays=2000, N*=558 unit masses "
             "uniform in a disc of R=37.36 R_E (seed 2); 114487^2 = 1.31e10 rays")
 METRIC = "ray-lens interactions/s and maps/s on 1 GB300 (FP32 vs FP64); p50/p99 map latency"
@@ -132,7 +155,7 @@ def scaled_mix(count, seed, sides=(64, 128, 256), nrays=(10.0, 30.0, 100.0), cap
     return out
 
 
-def batch_phase(mm, ctx, n_maps=64, seed=4):
+def batch_phase(mm, ctx, sms, n_maps=64, seed=4):
     """Config-3 shape, scaled: n maps of mixed shape and N* in ONE persistent launch, against the
     same maps shot one by one, and against the plain FP64 kernel one by one on the smallest maps."""
     mix = scaled_mix(n_maps, seed)
@@ -166,8 +189,8 @@ def batch_phase(mm, ctx, n_maps=64, seed=4):
                         "{64,128,256}, N_rays in {10,30,100}, <= 4e11 interactions each",
             "interactions": total, "batched_ms": batch_ms, "batched_interactions_per_s": total / (batch_ms * 1e-3),
             "maps_per_s": n_maps / (batch_ms * 1e-3),
-            "frac_nflop10": FLOP_PER_INTERACTION * total / (batch_ms * 1e-3) / (FP32_PEAK_TFLOPS * 1e12),
-            "useful_frac": USEFUL_OPS_WITH_MASSES * total / (batch_ms * 1e-3) / (SMS * LANES * SM_MAX_MHZ * 1e6),
+            "frac_nflop10": FLOP_PER_INTERACTION * total / (batch_ms * 1e-3) / (fp32_peak_tflops(sms) * 1e12),
+            "useful_frac": USEFUL_OPS_WITH_MASSES * total / (batch_ms * 1e-3) / lane_peak_per_s(sms),
             "one_by_one_ms": one_ms,
             "one_by_one_interactions_per_s": total / (one_ms * 1e-3),
             "fp64_one_by_one_interactions_per_s": f64_inter / (f64_ms * 1e-3),
@@ -412,10 +435,9 @@ def profile_case(kind="fp32", window=4096):
     the full map)."""
     import paper_1005_5198_gb300 as mm
     import synth
-    from oracle import field as ofield
     mm.build()
     ctx = mm.mm_init(0)
-    n, r = ofield.nstar_rule(0.4, 0.0, 0.0, 20.0)
+    n, r = lens_rule(mm, mm.params(**CFG1))
     f = synth.lens_field(n, r, SEED)
     lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
     g = mm.mm_geometry_of(mm.params(**CFG1))
@@ -520,7 +542,13 @@ def main():
                          "map statistics and light curves on two 8192^2 maps (downstream)")
     ap.add_argument("--far-scaling", action="store_true",
                     help="time the far field on the Fig. 1 geometry for N* = 1e4 .. 1e8 and exit")
+    ap.add_argument("--alu-rates", action="store_true",
+                    help="build and run the arithmetic-pipe probe (FFMA, FFMA2, MUFU, DFMA and the shooting "
+                         "mix per SM per clock: the roofline's denominators) and exit")
     args = ap.parse_args()
+    if args.alu_rates:
+        from paper_1005_5198_gb300.buildlib import build_alu_rates
+        return subprocess.run([build_alu_rates()]).returncode
     if args.far_scaling:
         return far_scaling()
     if args.impl == "reference":
@@ -540,7 +568,6 @@ def main():
     import torch
     import paper_1005_5198_gb300 as mm
     import synth
-    from oracle import field as ofield      # N* rule of the oracle only to size the synthetic input
 
     rank, world, local = dist_env()
     dist = None
@@ -551,8 +578,10 @@ def main():
     stream = torch.cuda.current_stream()
     mm.build()
     ctx = mm.mm_init(local, 0, stream.cuda_stream)
+    sms = device_sms(local)
+    peak = fp32_peak_tflops(sms)
 
-    n, r = ofield.nstar_rule(0.4, 0.0, 0.0, 20.0)
+    n, r = lens_rule(mm, mm.params(**CFG1))
     f = synth.lens_field(n, r, SEED + rank)
     lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
     p = mm.params(**CFG1)
@@ -629,7 +658,7 @@ def main():
     if not args.no_extras and world == 1:
         extra["far_field"] = far_phase(mm, ctx, lh, sum(kern_ms) / len(kern_ms))
         extra["downstream"] = downstream_phase(mm, ctx)
-        extra["batch"] = batch_phase(mm, ctx)
+        extra["batch"] = batch_phase(mm, ctx, sms)
         mm.mm_serve_config(ctx, max_active=64, wave_ms=args.wave_ms)
         mm.mm_serve_priority(ctx, args.serve_priority)
         capacity = extra["batch"]["batched_interactions_per_s"]          # the same mix shape, batched
@@ -658,16 +687,21 @@ def main():
         "e2e": {"value": e2e_value, "unit": "interactions/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "what": "mm_create_lenses_from (pinned host) + mm_shoot + mm_map_fetch (pinned host) per step"},
         "gpu_launches": launches,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                     "peak_source": "recipe unit counts: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz",
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"recipe unit counts: {sms} SMs (from the device) x 128 FP32 lanes x 2 FLOP "
+                                    f"x 2070 MHz",
                      "kernel_ms": kmean,
-                     "frac_at_measured_clock": (achieved / (FP32_PEAK_TFLOPS * clocks["sm_mhz"] / SM_MAX_MHZ)
+                     "frac_at_measured_clock": (achieved / (peak * clocks["sm_mhz"] / SM_MAX_MHZ)
                                                 if clocks.get("sm_mhz") else None),
+                     # against the FFMA rate the pipe probe measured (125.1 of 128 lane operations per
+                     # SM per clock) at the maximum clock
+                     "frac_of_measured_ffma": achieved / fp32_peak_tflops(sms, FFMA_MEASURED_LANE_OPS),
+                     "measured_ffma_lane_ops_per_sm_clk": FFMA_MEASURED_LANE_OPS,
                      # the irreducible FP32 lane operations of an interaction (2 subtractions,
                      # 1 multiply, 3 FMAs) per second, against the FP32 lane peak
                      "useful_frac": USEFUL_OPS_PER_INTERACTION * (inter / (world * args.steps)) / (kmean * 1e-3)
-                                    / (SMS * LANES * SM_MAX_MHZ * 1e6),
+                                    / lane_peak_per_s(sms),
                      "useful_ops_per_interaction": USEFUL_OPS_PER_INTERACTION},
         "fp64": fp64,
         "fp32_over_fp64": value / world / fp64["value"],

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmm.so")
-ALU_RATES = os.path.join(BUILD, "alu_rates")     # pipe-throughput probe (measured FP32/MUFU/FP64 rates)
+ALU_RATES = os.path.join(BUILD, "alu_rates")     # pipe-throughput probe, built only on request (build_alu_rates)
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -28,7 +28,7 @@ HEADERS = ["mm_internal.h", "mm_ctx.h", "mm_device.cuh", "mm_fp32.cuh", "mm_far.
 
 
 def _inputs():
-    files = [os.path.join(CSRC, f) for f in CU_SOURCES + CPP_SOURCES + HEADERS + ["alu_rates.cu"]]
+    files = [os.path.join(CSRC, f) for f in CU_SOURCES + CPP_SOURCES + HEADERS]
     files.append(os.path.join(ROOT, "include", "mm.h"))
     files.append(os.path.abspath(__file__))
     return files
@@ -41,7 +41,7 @@ CHECKED_LIB = os.path.join(CHECKED_BUILD, "libmm.so")
 
 
 def up_to_date(checked: bool = False) -> bool:
-    outs = [CHECKED_LIB] if checked else [LIB, ALU_RATES]
+    outs = [CHECKED_LIB] if checked else [LIB]
     if not all(os.path.exists(o) for o in outs):
         return False
     t = min(os.path.getmtime(o) for o in outs)
@@ -69,10 +69,6 @@ def build(force: bool = False, verbose: bool = False, checked: bool = False) -> 
                "-c", os.path.join(CSRC, f), "-o", o]
         jobs.append((f, cmd))
         objs.append(o)
-    alu_tmp = ALU_RATES + f".{os.getpid()}.tmp"
-    if not checked:
-        jobs.append(("alu_rates.cu", [NVCC, *ARCH, "-O3", "-std=c++17", os.path.join(CSRC, "alu_rates.cu"), "-o",
-                                      alu_tmp]))
     procs = [(f, subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)) for f, c in jobs]
     logs = []
     for f, p in procs:
@@ -86,8 +82,6 @@ def build(force: bool = False, verbose: bool = False, checked: bool = False) -> 
     if r.returncode != 0:
         raise RuntimeError(f"linking libmm.so failed:\n{r.stdout}")
     os.replace(tmp, lib_path)
-    if not checked:
-        os.replace(alu_tmp, ALU_RATES)
     with open(os.path.join(out_dir, "ptxas.log"), "w") as fh:
         for f, out in logs:
             fh.write(f"== {f}\n{out}\n")
@@ -95,6 +89,20 @@ def build(force: bool = False, verbose: bool = False, checked: bool = False) -> 
         for f, out in logs:
             sys.stdout.write(f"== {f}\n{out}\n")
     return lib_path
+
+
+def build_alu_rates() -> str:
+    """Compile the arithmetic-pipe probe (alu_rates.cu: FFMA, FFMA2, MUFU and DFMA rates per SM per
+    clock, and the shooting kernel's instruction mix) as a standalone program. It measures the
+    roofline's denominators and is not part of libmm.so."""
+    src = os.path.join(CSRC, "alu_rates.cu")
+    os.makedirs(BUILD, exist_ok=True)
+    if os.path.exists(ALU_RATES) and os.path.getmtime(ALU_RATES) >= os.path.getmtime(src):
+        return ALU_RATES
+    tmp = ALU_RATES + f".{os.getpid()}.tmp"
+    subprocess.run([NVCC, *ARCH, "-O3", "-std=c++17", src, "-o", tmp], check=True)
+    os.replace(tmp, ALU_RATES)
+    return ALU_RATES
 
 
 if __name__ == "__main__":
