@@ -396,11 +396,14 @@ int mm_debug_deflect(mm_ctx *ctx, mm_lenses lenses, const mm_params *p,
  * framework that owns the GPU's memory and accounts for every byte, or a tight
  * loop that cannot afford the device-wide synchronisation of cudaMalloc and
  * cudaFree. It shoots one map with the FP32 kernel (thread layout and tile
- * variant of a fresh context, so the map equals mm_shoot's on a fresh context)
- * and allocates nothing: no context is needed, and the kernel's scratch (FP32
- * lens tile copies, launch header, map descriptor, work counter) lives in one
- * fixed __device__ array of about 2.6 MB that every GPU which loads the library
- * holds until the process exits.
+ * variant of a fresh context) and allocates nothing: no context is needed, and
+ * the kernel's scratch (FP32 lens tile copies, launch header, map descriptor,
+ * work counter) lives in one fixed __device__ array of about 2.6 MB that every
+ * GPU which loads the library holds until the process exits. Each ray tile sums
+ * all its lenses in one CTA: for maps that mm_shoot does not split over lens
+ * segments (2048 tiles or more, or 1024 lenses or fewer) the counts equal
+ * mm_shoot's on a fresh context bit for bit; maps that mm_shoot splits may
+ * differ from it by rounding at pixel edges, within the FP32 path's tolerances.
  *   x, y, m   device arrays of nstar FP64 lens coordinates and masses, owned by
  *             the caller; m is not read (may be NULL) when p->mass_model is
  *             MM_MASS_UNIT. p->nstar and p->disc_radius are ignored.
@@ -414,10 +417,12 @@ int mm_debug_deflect(mm_ctx *ctx, mm_lenses lenses, const mm_params *p,
  * returns once the work is enqueued; the outputs are complete when the stream
  * reaches it. The first call on a device looks up the scratch's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture. Every call shares the one scratch array, which keeps the
- * last call's contents: calls whose work overlaps on the GPU (other streams,
- * other threads) race and give wrong maps -- serialise them. Errors: MM_EINVAL,
- * MM_EDEVICE. */
+ * any stream capture. The address is kept for the rest of the process and is
+ * valid for the device's primary context: do not call this entry point on a
+ * device after cudaDeviceReset has destroyed that context. Every call shares the
+ * one scratch array, which keeps the last call's contents: calls whose work
+ * overlaps on the GPU (other streams, other threads) race and give wrong maps --
+ * serialise them. Errors: MM_EINVAL, MM_EDEVICE. */
 int mm_shoot_noalloc(const double *x, const double *y, const double *m, int64_t nstar, const mm_params *p,
                      uint32_t *counts, uint64_t *totals, void *cuda_stream);
 

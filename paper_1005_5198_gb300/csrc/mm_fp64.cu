@@ -104,7 +104,7 @@ __global__ void k_prepare_lenses(const double *x, const double *y, const double 
             const double xv = x[k], yv = y[k];
             const float xh = __double2float_rn(xv), yh = __double2float_rn(yv);
             lh[k] = make_float4(xh, yh, __double2float_rn(xv - (double)xh), __double2float_rn(yv - (double)yh));
-            lmf[k] = __double2float_rn(m[k]);
+            lmf[k] = m ? __double2float_rn(m[k]) : 1.0f;     // no mass array: unit masses
         } else {
             lh[k] = make_float4(kNullX, 0.f, 0.f, 0.f);
             lmf[k] = 0.f;

@@ -58,24 +58,6 @@ int scratch_address(int dev, NoAllocScratch **out)
     return MM_OK;
 }
 
-// FP32 tile copies of caller lens arrays into the scratch (m == nullptr: unit masses).
-__global__ void k_noalloc_lenses(const double *x, const double *y, const double *m, long long n, long long n_pad,
-                                 NoAllocScratch *sc)
-{
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n_pad;
-         k += (long long)gridDim.x * blockDim.x) {
-        if (k < n) {
-            const double xv = x[k], yv = y[k];
-            const float xh = __double2float_rn(xv), yh = __double2float_rn(yv);
-            sc->lh[k] = make_float4(xh, yh, __double2float_rn(xv - (double)xh), __double2float_rn(yv - (double)yh));
-            sc->lmf[k] = m ? __double2float_rn(m[k]) : 1.0f;
-        } else {
-            sc->lh[k] = make_float4(kNullX, 0.f, 0.f, 0.f);
-            sc->lmf[k] = 0.f;
-        }
-    }
-}
-
 // Write the launch header and map descriptor, and zero the work counter.
 __global__ void k_noalloc_setup(const WorkHeader hdr, const MapDesc desc, NoAllocScratch *sc)
 {
@@ -145,9 +127,9 @@ extern "C" int mm_shoot_noalloc(const double *x, const double *y, const double *
     // outputs start at zero; every piece of scratch is rewritten below
     if ((e = cudaMemsetAsync(counts, 0, npix * sizeof(uint32_t), s)) != cudaSuccess) return cuda_fail(e, "clear counts");
     if ((e = cudaMemsetAsync(totals, 0, 2 * sizeof(uint64_t), s)) != cudaSuccess) return cuda_fail(e, "clear totals");
-    const int pgrid = (int)std::min<long long>((L.n_pad + 255) / 256, 4096LL);
-    k_noalloc_lenses<<<pgrid, 256, 0, s>>>(x, y, L.unit_mass ? nullptr : m, nstar, L.n_pad, sc);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "no-alloc lens preparation");
+    // the library's lens preparation, writing into the scratch (no mass array: unit masses)
+    if ((e = launch_prepare_lenses(x, y, L.unit_mass ? nullptr : m, nstar, L.n_pad, sc->lh, sc->lmf, s)) != cudaSuccess)
+        return cuda_fail(e, "no-alloc lens preparation");
     k_noalloc_setup<<<1, 1, 0, s>>>(h, d, sc);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "no-alloc setup");
     if (h.total_work == 0) return MM_OK;
