@@ -243,6 +243,19 @@ int mm_map_restore(mm_ctx *ctx, mm_lenses lenses, const mm_params *p, const uint
  * the map is complete. */
 int mm_map_fetch(mm_ctx *ctx, mm_map map, uint32_t *host_counts, size_t n_elems, mm_stats *st);
 
+/* Normalised map on the device, copied to host_out[n_elems] (n_elems = N_side^2,
+ * row-major, FP32):
+ *   MM_MAP_MU       mu_ij = N_ij / N_rays (Sect. 2, the inverse ray-shooting estimator);
+ *   MM_MAP_DELTA_M  Delta m_ij = -2.5 log10(max(N_ij, 1) / N_rays) (Eq. deltam), an empty
+ *                   pixel clamped to one ray (the paper gives no value for mu = 0).
+ * *n_empty (may be NULL) receives the number of pixels with N_ij = 0 (the clamped ones).
+ * FP32 arithmetic: mu within 2e-7 relative, Delta m within 3e-6 mag of the FP64 values.
+ * Blocks until the map is complete. Errors: MM_EINVAL (kind, NULL buffer or wrong
+ * n_elems), MM_ENOTFOUND, MM_ENOMEM, MM_EDEVICE. */
+#define MM_MAP_MU       0
+#define MM_MAP_DELTA_M  1
+int mm_map_fetch_mu(mm_ctx *ctx, mm_map map, int32_t kind, float *host_out, size_t n_elems, int64_t *n_empty);
+
 /* Device address of a map's uint32 counts (N_side^2, row-major), valid until
  * mm_release_map; for zero-copy use on the context's stream. */
 int mm_map_device_ptr(mm_ctx *ctx, mm_map map, void **dptr, size_t *n_elems);

@@ -40,6 +40,7 @@ MM_ETIMEDOUT, MM_EDEVICE, MM_EAGAIN, MM_ECANCELED = -5, -6, -7, -8
 MM_FP32C, MM_FP64, MM_FAR32 = 0, 1, 2
 MM_MASS_UNIT, MM_MASS_LOGNORMAL = 0, 1
 MM_PROFILE_GAUSSIAN, MM_PROFILE_DISC = 0, 1
+MM_MAP_MU, MM_MAP_DELTA_M = 0, 1
 
 
 class MMError(RuntimeError):
@@ -102,6 +103,7 @@ def _load():
         "mm_map_restore": [C.c_void_p, U64, P(mm_params), P(C.c_uint32), C.c_size_t, P(mm_stats), P(U64)],
         "mm_map_fetch": [C.c_void_p, U64, P(C.c_uint32), C.c_size_t, P(mm_stats)],
         "mm_map_device_ptr": [C.c_void_p, U64, P(C.c_void_p), P(C.c_size_t)],
+        "mm_map_fetch_mu": [C.c_void_p, U64, C.c_int32, P(C.c_float), C.c_size_t, P(I64)],
         "mm_release_map": [C.c_void_p, U64],
         "mm_submit": [C.c_void_p, U64, P(mm_params), P(U64)],
         "mm_poll": [C.c_void_p, U64, P(C.c_int), P(U64)],
@@ -283,6 +285,18 @@ def mm_map_fetch(ctx: Ctx, m: int, counts: np.ndarray | None = None, want_counts
     return counts.reshape(side, side), _stats_dict(st)
 
 
+def mm_map_fetch_mu(ctx: Ctx, m: int, kind: int = MM_MAP_MU):
+    """(float32 [N_side, N_side] of mu = N / N_rays, or of Delta m with empty pixels clamped to one
+    ray (kind MM_MAP_DELTA_M), computed on the device; number of empty pixels)."""
+    _, n = mm_map_device_ptr(ctx, m)
+    out = np.zeros(n, dtype=np.float32)
+    empty = C.c_int64()
+    _check(_load().mm_map_fetch_mu(ctx.handle, m, kind, out.ctypes.data_as(C.POINTER(C.c_float)), n,
+                                   C.byref(empty)), "mm_map_fetch_mu")
+    side = int(round(n ** 0.5))
+    return out.reshape(side, side), empty.value
+
+
 def mm_map_device_ptr(ctx: Ctx, m: int) -> tuple[int, int]:
     ptr, n = C.c_void_p(), C.c_size_t()
     _check(_load().mm_map_device_ptr(ctx.handle, m, C.byref(ptr), C.byref(n)), "mm_map_device_ptr")
@@ -440,7 +454,7 @@ def mm_strerror(code: int) -> str:
 EXPORTED = [
     "mm_init", "mm_destroy", "mm_params_default", "mm_geometry_of", "mm_create_lenses", "mm_create_lenses_from",
     "mm_lenses_fetch", "mm_lenses_count", "mm_release_lenses", "mm_shoot", "mm_shoot_batch", "mm_shoot_into",
-    "mm_map_restore", "mm_map_fetch",
+    "mm_map_restore", "mm_map_fetch", "mm_map_fetch_mu",
     "mm_map_device_ptr", "mm_release_map", "mm_submit", "mm_poll", "mm_wait", "mm_cancel", "mm_req_times",
     "mm_serve_config", "mm_serve_priority", "mm_serve_plan", "mm_autotune", "mm_set_variant", "mm_variant_count", "mm_variant_name", "mm_set_layout",
     "mm_get_layout", "mm_layout_count", "mm_layout_name", "mm_debug_deflect",

@@ -21,6 +21,41 @@ namespace {
 
 constexpr int K64 = 8;   // rays per thread (one column, 8 rows), 256 threads per 64 x 32 tile
 
+// One lens's term of the deflection sum for one ray (Eq. sigma), with every rounding
+// fixed (explicit FP64 intrinsics), so that the map kernel and the ray-list kernel below
+// compute each ray identically. A ray exactly on a lens sets `on` and adds nothing.
+__device__ __forceinline__ void fp64_term(double x1, double x2, double2 L, double m, double &a1, double &a2, bool &on)
+{
+    const double d1 = __dsub_rn(x1, L.x), d2 = __dsub_rn(x2, L.y);
+    const double r2 = __fma_rn(d1, d1, __dmul_rn(d2, d2));
+    if (r2 == 0.0) {
+        on = true;
+    } else {
+        const double t = __ddiv_rn(m, r2);
+        a1 = __fma_rn(t, d1, a1);
+        a2 = __fma_rn(t, d2, a2);
+    }
+}
+
+// Lattice coordinate of ray index g along one axis: (g + 1/2 - n/2) delta.
+__device__ __forceinline__ double fp64_lattice(long long g, double half_n, double delta)
+{
+    return __dmul_rn(__dsub_rn(__dadd_rn((double)g, 0.5), half_n), delta);
+}
+
+// Lens equation and pixel (Eq. sigma, then floor((y + L/2) / p) per axis): the flat
+// pixel index, or -1 when the ray lands outside the map or is not finite.
+__device__ __forceinline__ long long fp64_pixel(const MapDesc &M, double x1, double x2, double a1, double a2)
+{
+    const double y1 = __dsub_rn(__fma_rn(M.one_m_gamma, x1, -__dmul_rn(M.sigma_c, x1)), a1);
+    const double y2 = __dsub_rn(__fma_rn(M.one_p_gamma, x2, -__dmul_rn(M.sigma_c, x2)), a2);
+    const double u1 = floor(__ddiv_rn(__dadd_rn(y1, M.half_side), M.pix));
+    const double u2 = floor(__ddiv_rn(__dadd_rn(y2, M.half_side), M.pix));
+    const double nsd = (double)M.nside;
+    if (!(u1 >= 0.0 && u1 < nsd && u2 >= 0.0 && u2 < nsd)) return -1;
+    return (long long)u2 * (long long)M.nside + (long long)u1;
+}
+
 template <bool DUMP>
 __device__ void tile_fp64(const LaunchArgs &A, const MapDesc &M, unsigned long long tile, int item, SmemFP64 &S,
                           unsigned &cnt_in, unsigned &cnt_out)
@@ -35,14 +70,15 @@ __device__ void tile_fp64(const LaunchArgs &A, const MapDesc &M, unsigned long l
     const long long ib = M.i0 + tx * kTileX;
     const long long jb = M.j0 + ty * kTileY;
     const long long gi = ib + iloc;
-    const double x1 = ((double)gi + 0.5 - M.half_nx) * M.delta;
+    const double x1 = fp64_lattice(gi, M.half_nx, M.delta);
     double x2[K64], a1[K64], a2[K64];
+    bool on[K64];
 #pragma unroll
     for (int r = 0; r < K64; ++r) {
-        x2[r] = ((double)(jb + jloc0 + r) + 0.5 - M.half_ny) * M.delta;
+        x2[r] = fp64_lattice(jb + jloc0 + r, M.half_ny, M.delta);
         a1[r] = a2[r] = 0.0;
+        on[r] = false;
     }
-    unsigned onlens = 0;
     for (long long base = 0; base < M.nstar; base += kChunkPairs) {
         __syncthreads();
         {
@@ -58,31 +94,17 @@ __device__ void tile_fp64(const LaunchArgs &A, const MapDesc &M, unsigned long l
             const double2 Lp = S.lens64[k];
             const double m = S.m64[k];
 #pragma unroll
-            for (int r = 0; r < K64; ++r) {
-                const double d1 = x1 - Lp.x, d2 = x2[r] - Lp.y;
-                const double r2 = d1 * d1 + d2 * d2;
-                if (r2 == 0.0) {
-                    onlens |= 1u << r;
-                } else {
-                    const double t = m / r2;
-                    a1[r] += t * d1;
-                    a2[r] += t * d2;
-                }
-            }
+            for (int r = 0; r < K64; ++r) fp64_term(x1, x2[r], Lp, m, a1[r], a2[r], on[r]);
         }
     }
     const bool col_ok = gi < M.i0 + M.ni;
-    const double nsd = (double)M.nside;
 #pragma unroll
     for (int r = 0; r < K64; ++r) {
         const long long gj = jb + jloc0 + r;
-        const double y1 = M.one_m_gamma * x1 - M.sigma_c * x1 - a1[r];
-        const double y2 = M.one_p_gamma * x2[r] - M.sigma_c * x2[r] - a2[r];
-        const double u1 = floor((y1 + M.half_side) / M.pix);
-        const double u2 = floor((y2 + M.half_side) / M.pix);
+        const long long px = fp64_pixel(M, x1, x2[r], a1[r], a2[r]);
         const bool valid = col_ok && gj < M.j0 + M.nj;
-        const bool inside = valid && !((onlens >> r) & 1u) && u1 >= 0.0 && u1 < nsd && u2 >= 0.0 && u2 < nsd;
-        const unsigned pix = inside ? (unsigned)u2 * (unsigned)M.nside + (unsigned)u1 : 0xffffffffu;
+        const bool inside = valid && !on[r] && px >= 0;
+        const unsigned pix = inside ? (unsigned)px : 0xffffffffu;
         emit_ray<DUMP>(A, M, item, iloc + kTileX * (jloc0 + r), valid, inside, pix, a1[r], a2[r], cnt_in, cnt_out);
     }
 }
@@ -112,6 +134,41 @@ __global__ void k_prepare_lenses(const double *x, const double *y, const double 
     }
 }
 
+// Rays of a list (global lattice indices), one thread each, through the map kernel's
+// per-ray FP64 arithmetic (fp64_lattice, fp64_term in lens order, fp64_pixel): each ray's
+// deflection and pixel equal the ones the FP64 map kernel computes for it, at the cost of
+// that ray alone rather than of its whole tile. Lenses are staged through shared memory
+// in chunks of 256, as in the map kernel.
+__global__ void __launch_bounds__(256) k_rays_fp64(const MapDesc M, const long long *ri, const long long *rj,
+                                                   long long n, double *alpha, long long *pixel)
+{
+    __shared__ double2 lens64[kChunkPairs];
+    __shared__ double m64[kChunkPairs];
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const bool act = k < n;
+    const double x1 = act ? fp64_lattice(ri[k], M.half_nx, M.delta) : 0.0;
+    const double x2 = act ? fp64_lattice(rj[k], M.half_ny, M.delta) : 0.0;
+    double a1 = 0.0, a2 = 0.0;
+    bool on = false;
+    for (long long base = 0; base < M.nstar; base += kChunkPairs) {
+        __syncthreads();
+        const long long g = base + threadIdx.x;
+        if (g < M.nstar) {
+            lens64[threadIdx.x] = make_double2(M.lx[g], M.ly[g]);
+            m64[threadIdx.x] = M.lm[g];
+        }
+        __syncthreads();
+        const int c = (int)min((long long)kChunkPairs, M.nstar - base);
+        if (act)
+            for (int q = 0; q < c; ++q) fp64_term(x1, x2, lens64[q], m64[q], a1, a2, on);
+    }
+    if (act) {
+        alpha[2 * k] = a1;
+        alpha[2 * k + 1] = a2;
+        pixel[k] = on ? -1LL : fp64_pixel(M, x1, x2, a1, a2);
+    }
+}
+
 }  // namespace
 }  // namespace dev
 
@@ -121,6 +178,14 @@ cudaError_t launch_prepare_lenses(const double *x, const double *y, const double
     if (n_pad <= 0) return cudaSuccess;
     const int grid = (int)min((n_pad + 255) / 256, (long long)4096);
     dev::k_prepare_lenses<<<grid, 256, 0, s>>>(x, y, m, n, n_pad, lh, lmf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rays_fp64(const MapDesc &M, const long long *ri, const long long *rj, long long n, double *alpha,
+                             long long *pixel, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    dev::k_rays_fp64<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(M, ri, rj, n, alpha, pixel);
     return cudaGetLastError();
 }
 

@@ -630,6 +630,48 @@ using namespace mm;
 
 // ================================================================ C ABI ====
 
+// FP64 per-ray deflections: every FP64 ray is computed independently of its tile, so the
+// listed rays run one thread each (the map kernel's per-ray arithmetic) instead of
+// through their whole tiles.
+static int debug_rays_fp64(mm_ctx *ctx, const MapObj &M, const int64_t *ray_i, const int64_t *ray_j, int64_t n,
+                           double *alpha_out, int64_t *pixel_out)
+{
+    struct Tmp {
+        DeviceArena *a;
+        std::vector<void *> v;
+        ~Tmp() { for (void *p : v) a->free(p); }
+    } tmp{&ctx->arena, {}};
+    auto dalloc = [&](size_t bytes, void **out) -> int {
+        int r = ctx->arena.alloc(bytes, out);
+        if (!r) tmp.v.push_back(*out);
+        return r;
+    };
+    long long *d_i, *d_j, *d_pixel;
+    double *d_alpha;
+    int rc;
+    if ((rc = dalloc((size_t)n * 8, (void **)&d_i)) || (rc = dalloc((size_t)n * 8, (void **)&d_j)) ||
+        (rc = dalloc((size_t)n * 16, (void **)&d_alpha)) || (rc = dalloc((size_t)n * 8, (void **)&d_pixel)))
+        return rc;
+    MapDesc d;
+    fill_desc(M, &d);
+    cudaStream_t s = ctx->stream;
+    static_assert(sizeof(long long) == sizeof(int64_t), "ray indices are 64-bit");
+    MM_CUDA(cudaMemcpyAsync(d_i, ray_i, (size_t)n * 8, cudaMemcpyHostToDevice, s));
+    MM_CUDA(cudaMemcpyAsync(d_j, ray_j, (size_t)n * 8, cudaMemcpyHostToDevice, s));
+    cudaEvent_t e0 = ctx->ev0, e1 = ctx->ev1;
+    MM_CUDA(cudaEventRecord(e0, s));
+    MM_CUDA(launch_rays_fp64(d, d_i, d_j, n, d_alpha, d_pixel, s));
+    MM_CUDA(cudaEventRecord(e1, s));
+    if (alpha_out) MM_CUDA(cudaMemcpyAsync(alpha_out, d_alpha, (size_t)n * 16, cudaMemcpyDeviceToHost, s));
+    if (pixel_out) MM_CUDA(cudaMemcpyAsync(pixel_out, d_pixel, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+    MM_CUDA(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    MM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    ctx->last_ms = ms;
+    ctx->last_launches = 1;
+    return MM_OK;
+}
+
 extern "C" {
 
 const char *mm_strerror(int code)
@@ -1006,6 +1048,10 @@ int mm_debug_deflect(mm_ctx *ctx, mm_lenses lenses, const mm_params *p, const in
     if (rc) return rc;
     if (n == 0) return MM_OK;
     const Geo &g = M->g;
+    for (int64_t k = 0; k < n; ++k)
+        if (ray_i[k] < g.i0 || ray_j[k] < g.j0 || ray_i[k] >= g.i0 + g.ni || ray_j[k] >= g.j0 + g.nj)
+            return fail(MM_EINVAL, "ray outside the shot grid");
+    if (p->precision == MM_FP64) return debug_rays_fp64(ctx, *M, ray_i, ray_j, n, alpha_out, pixel_out);
     // group the requested rays by the tile the map kernel would put them in,
     // sorted by (tile, local ray index) so the kernel can binary-search
     std::vector<std::pair<unsigned long long, int>> key((size_t)n);

@@ -114,6 +114,11 @@ __host__ __device__ inline long long lens_padded(long long nstar)
 // k < n, null lenses for n <= k < n_pad; lmf likewise. n_pad % 512 == 0.
 cudaError_t launch_prepare_lenses(const double *x, const double *y, const double *m, long long n,
                                   long long n_pad, float4 *lh, float *lmf, cudaStream_t s);
+// Plain FP64 deflection and pixel of n listed rays (global lattice indices ri[k], rj[k])
+// of map M, one thread per ray, with the FP64 map kernel's per-ray arithmetic:
+// alpha[2k..2k+1], pixel[k] (-1: out or on a lens). Device arrays.
+cudaError_t launch_rays_fp64(const MapDesc &M, const long long *ri, const long long *rj, long long n, double *alpha,
+                             long long *pixel, cudaStream_t s);
 // FP32 (compensated) shoot over the work of args (every map precision MM_FP32C) with
 // thread layout `layout`; grid = number of CTAs (persistent); split: some map of the
 // launch has lens-split tiles.

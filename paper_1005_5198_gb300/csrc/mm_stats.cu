@@ -334,3 +334,79 @@ extern "C" int mm_map_compare(mm_ctx *ctx, mm_map a, mm_map b, mm_compare *out)
     out->mean_mu_b = (double)h.sum_b / ((double)n * B->p.nrays_per_pix);
     return MM_OK;
 }
+
+// ---- normalised maps (Sect. 2, the estimator; Eq. deltam) ------------------------
+
+namespace mm {
+namespace {
+
+// Per pixel mu = N / N_rays, or Delta m = -2.5 log10(max(N, 1) / N_rays) (an empty pixel
+// is clamped to one ray, which bounds its Delta m), in FP32 from the uint32 counts; the
+// number of empty pixels goes to *n_empty. Four pixels per thread and step (16-byte loads
+// and stores; both buffers come from the arena, 256-byte aligned), the last n % 4 pixels
+// by the first threads of block 0.
+__global__ void __launch_bounds__(256) k_map_normalise(const unsigned *c, long long n, int kind, float inv_nrays,
+                                                       float log10_nrays, float *out, unsigned long long *n_empty)
+{
+    auto one = [&](unsigned v) {
+        return kind == MM_MAP_DELTA_M ? -2.5f * (log10f((float)max(v, 1u)) - log10_nrays) : (float)v * inv_nrays;
+    };
+    unsigned long long z = 0;
+    const long long n4 = n / 4;
+    const uint4 *c4 = reinterpret_cast<const uint4 *>(c);
+    float4 *o4 = reinterpret_cast<float4 *>(out);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n4; k += (long long)gridDim.x * blockDim.x) {
+        const uint4 v = c4[k];
+        o4[k] = make_float4(one(v.x), one(v.y), one(v.z), one(v.w));
+        z += (v.x == 0u) + (v.y == 0u) + (v.z == 0u) + (v.w == 0u);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < n - 4 * n4) {
+        const long long k = 4 * n4 + threadIdx.x;
+        out[k] = one(c[k]);
+        z += c[k] == 0u;
+    }
+    z = __reduce_add_sync(0xffffffffu, (unsigned)z);
+    if ((threadIdx.x & 31) == 0 && z) atomicAdd(n_empty, z);
+}
+
+}  // namespace
+}  // namespace mm
+
+extern "C" int mm_map_fetch_mu(mm_ctx *ctx, mm_map map, int32_t kind, float *host_out, size_t n_elems,
+                               int64_t *n_empty)
+{
+    if (!ctx) return fail(MM_EINVAL, "null context");
+    if (kind != MM_MAP_MU && kind != MM_MAP_DELTA_M) return fail(MM_EINVAL, "kind must be MM_MAP_MU or MM_MAP_DELTA_M");
+    std::shared_ptr<MapObj> M;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        auto it = ctx->maps.find(map);
+        if (it == ctx->maps.end()) return fail(MM_ENOTFOUND, "unknown map");
+        M = it->second;
+    }
+    const long long n = (long long)M->p.npix_side * M->p.npix_side;
+    if (!host_out || n_elems != (size_t)n) return fail(MM_EINVAL, "host buffer must hold N_side^2 floats");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = ctx->stream;
+    cudaError_t e;
+    if ((e = cudaStreamWaitEvent(s, M->done, 0)) != cudaSuccess) return cuda_fail(e, "wait for map");
+    float *buf = nullptr;
+    int rc = ctx->arena.alloc((size_t)n * sizeof(float) + 256, (void **)&buf);
+    if (rc) return rc;
+    unsigned long long *d_empty = reinterpret_cast<unsigned long long *>(buf + n + (4 - n % 4) % 4);
+    unsigned long long h_empty = 0;
+    const double nr = M->p.nrays_per_pix;
+    const int grid = std::max(1, std::min(4 * ctx->sms, (int)((n / 4 + 255) / 256)));
+    if ((e = cudaMemsetAsync(d_empty, 0, sizeof(unsigned long long), s)) == cudaSuccess) {
+        k_map_normalise<<<grid, 256, 0, s>>>(M->counts, n, kind, (float)(1.0 / nr), (float)std::log10(nr), buf,
+                                             d_empty);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, buf, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_empty, d_empty, sizeof(h_empty), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    ctx->arena.free(buf);
+    if (e != cudaSuccess) return cuda_fail(e, "normalised map");
+    if (n_empty) *n_empty = (int64_t)h_empty;
+    return MM_OK;
+}

@@ -52,7 +52,9 @@ def plan(sweep: str, npix: int, nrays: float, side: float = 20.0, precision: str
 
 
 def run(sweep: str, npix: int, nrays: float, max_interactions: float, device: int = 0, precision: str = "fp32c",
-        max_rays: float = 2e12, compare_exact: bool = False):
+        max_rays: float = 2e12, compare_exact: bool = False, keep_counts: bool = False):
+    """Shoot every point of a sweep; one row per point (keep_counts: each row also holds the map's
+    uint32 counts, [N_side, N_side])."""
     mm.build()
     ctx = mm.mm_init(device)
     out = []
@@ -75,7 +77,9 @@ def run(sweep: str, npix: int, nrays: float, max_interactions: float, device: in
                 continue
             m = mm.mm_shoot(ctx, 0, pt["params"])
             ms, _ = mm.mm_last_kernel_ms(ctx)
-            _, st = mm.mm_map_fetch(ctx, m, want_counts=False)
+            counts, st = mm.mm_map_fetch(ctx, m, want_counts=keep_counts)
+            if keep_counts:
+                row["counts"] = counts.copy()
             if compare_exact and pt["interactions"] <= max_interactions:
                 # the paper's map statistics (Sect. 3.1) against the exact FP32 map of the same lenses
                 q = pt["params"]
@@ -87,7 +91,8 @@ def run(sweep: str, npix: int, nrays: float, max_interactions: float, device: in
                 mm.mm_release_map(ctx, ex)
             mm.mm_release_map(ctx, m)
             row.update(kernel_ms=ms, interactions_per_s=st["interactions"] / (ms * 1e-3) if ms > 0 else None,
-                       mu_map=st["mu_mean"], lens_splits=st["lens_splits"], far_bound=st["far_bound"])
+                       mu_map=st["mu_mean"], lens_splits=st["lens_splits"], far_bound=st["far_bound"],
+                       rays_shot=st["rays_shot"], rays_in=st["rays_in"], rays_out=st["rays_out"])
             out.append(row)
     finally:
         mm.mm_destroy(ctx)

@@ -89,3 +89,36 @@ def test_wide_supports_match_oracle(shot_wide, profile, size, half_width):
     ok = ~np.isnan(ref)
     assert ok.sum() == (CFG_WIDE["npix_side"] - 2 * h) ** 2
     np.testing.assert_allclose(got[ok], ref[ok], rtol=2e-5, atol=1e-6)
+
+
+def test_disc_tiles_with_large_counts_use_64_bit_sums():
+    """The tiled disc kernel sums each tile's rows in 32 bits unless a count of the tile reaches
+    2^32 / (2H + 1), when the tile is summed again in 64 bits. A seeded synthetic map (put on the
+    device by mm_map_restore) with a few pixels above that bound in one corner, convolved with a disc of
+    radius 8 pixels (under the tiled limit of 15), has tiles of both kinds in one launch; all match
+    the oracle."""
+    mm.build()
+    c = mm.mm_init(0)
+    try:
+        n, nrays, side = 256, 1.0e6, 4.0
+        pix = side / n
+        size = 8.5 * pix                                   # H = 8: bound 2^32 / 17 = 252645135
+        rng = np.random.default_rng(5)
+        counts = rng.poisson(1000.0, (n, n)).astype(np.uint32)
+        counts[10:14, 20:22] = np.uint32(300_000_000)      # 8 pixels above the bound
+        p = mm.params(sigma=0.4, gamma=0.0, smooth_frac=1.0, side=side, npix_side=n, nrays=nrays)
+        g = mm.mm_geometry_of(p)
+        tot = int(counts.sum(dtype=np.int64))
+        assert tot <= g["nx"] * g["ny"]
+        st = dict(rays_shot=tot, rays_in=tot, rays_out=0, interactions=0, nx=g["nx"], ny=g["ny"], nstar=0,
+                  seconds=0.0, mu_mean=0.0, lens_splits=1, far_bound=0.0, far_block=0)
+        m = mm.mm_map_restore(c, 0, p, counts, st)
+        got = mm.mm_map_convolve(c, m, mm.MM_PROFILE_DISC, size)
+        ref = oext.convolve(counts, nrays, mm.MM_PROFILE_DISC, size, pix)
+        np.testing.assert_array_equal(np.isnan(got), np.isnan(ref))
+        ok = ~np.isnan(ref)
+        assert ok.sum() == (n - 16) ** 2
+        np.testing.assert_allclose(got[ok], ref[ok], rtol=2e-6, atol=1e-9)
+        assert np.nanmax(ref) > 100 * np.nanmedian(ref)     # the large pixels reach some outputs
+    finally:
+        mm.mm_destroy(c)

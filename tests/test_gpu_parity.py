@@ -181,11 +181,13 @@ def test_cfg1_full_map_totals_and_window_parity(ctx):
 # ----------------------------------------------------------------- config 2 ---
 
 def test_cfg2_sampled_rays_and_window(ctx):
+    """Config 2 (sigma = 0.8, s = 0.5, gamma = 0.3, N* = 25000): 10^6 rays sampled over the whole
+    686921 x 137385-ray grid against the oracle, and a ragged 601 x 450-ray window map."""
     f = field2()
     lh = lens(ctx, f)
     g = oracle.geometry(oracle_cfg(CFG2))
     rng = np.random.default_rng(2)
-    n = 200_000
+    n = 1_000_000
     ii, jj = rng.integers(0, g["nx"], n), rng.integers(0, g["ny"], n)
     err, mis, *_ = rays_check(ctx, lh, CFG2, f, ii, jj)
     assert err.max() <= ALPHA_TOL, err.max()
@@ -196,6 +198,83 @@ def test_cfg2_sampled_rays_and_window(ctx):
     ref, tot = oracle.shoot_map(oracle_cfg(CFG2), f, rect=rect)
     check_totals(gw, sw, tot["shot"])
     assert map_l1(gw, ref) <= 2 * max(2, MISBIN_TOL * tot["shot"])
+
+
+def central_window_rect(g, cfg, window_px=256, margin=1.5):
+    """Rays of the global grid that the mean lens equation, y = diag(1-sigma-gamma, 1-sigma+gamma) x,
+    maps into the central window_px^2 pixels, widened by `margin` per side (Eq. square applied to
+    the window): [i0, i1) x [j0, j1)."""
+    a = abs(1 - cfg["sigma"] - cfg["gamma"])
+    b = abs(1 - cfg["sigma"] + cfg["gamma"])
+    hs = 0.5 * window_px * g["pix"]
+    hx, hy = margin * hs / a, margin * hs / b
+    d = g["delta"]
+    i0 = max(0, int(np.floor(-hx / d + g["nx"] / 2))); i1 = min(g["nx"], int(np.ceil(hx / d + g["nx"] / 2)))
+    j0 = max(0, int(np.floor(-hy / d + g["ny"] / 2))); j1 = min(g["ny"], int(np.ceil(hy / d + g["ny"] / 2)))
+    return i0, i1, j0, j1
+
+
+def test_cfg2_central_window_error_report(ctx):
+    """Error report of config 2 on the rays that map back to the central 256^2-pixel window (x 1.5):
+    a 75 x 15 Einstein-radius region of 1.47e9 rays. The FP32 map of the whole window is shot
+    (totals exact); every 16th ray row and column of it (5.8e6 rays) is computed by the oracle,
+    by the FP32 kernel (through the map kernel's code) and by the plain FP64 kernel, and for each
+    GPU form the report gives the max and mean |d alpha| (Einstein radii), the fraction of rays
+    binned to another pixel, and the L1 distance of the strided maps over the rays shot. Bars:
+    FP32 max |d alpha| <= 1e-5, misbinned <= 1e-4, L1 <= 2e-4; FP64 alpha within 1e-9 relative,
+    misbinned <= max(1, 1e-8 n) rays."""
+    import json
+    f = field2()
+    lh = lens(ctx, f)
+    g = oracle.geometry(oracle_cfg(CFG2))
+    rect = central_window_rect(g, CFG2)
+    assert 85000 <= rect[1] - rect[0] <= 87000 and 17000 <= rect[3] - rect[2] <= 17400
+    gw, sw = shoot(ctx, lh, CFG2, ray_rect=rect)
+    check_totals(gw, sw, (rect[1] - rect[0]) * (rect[3] - rect[2]))
+    stride = 16
+    jj, ii = np.meshgrid(np.arange(rect[2], rect[3], stride), np.arange(rect[0], rect[1], stride), indexing="ij")
+    ii, jj = ii.ravel(), jj.ravel()
+    n = ii.size
+    a_o, _, p_o = oracle.shoot_rays(oracle_cfg(CFG2), f, ii, jj)
+    nside = CFG2["npix_side"]
+    map_o = np.bincount(p_o[p_o >= 0], minlength=nside * nside)
+    report = {"workload": "config 2, central 256^2-pixel window x 1.5 (rays " + str(rect) + f"), every {stride}th "
+                          f"ray row and column: {n} rays x {f.n} lenses",
+              "window_map_fp32": {"rays_shot": sw["rays_shot"], "rays_in": sw["rays_in"], "rays_out": sw["rays_out"]}}
+    for name, prec in (("fp32", mm.MM_FP32C), ("fp64", mm.MM_FP64)):
+        a_g, p_g = mm.mm_debug_deflect(ctx, lh, P(CFG2, precision=prec), ii, jj)
+        err = np.hypot(a_g[:, 0] - a_o[:, 0], a_g[:, 1] - a_o[:, 1])
+        mis = int(np.sum(p_g != p_o))
+        map_g = np.bincount(p_g[p_g >= 0], minlength=nside * nside)
+        l1 = int(np.abs(map_g - map_o).sum())
+        report[name] = {"max_dalpha_re": float(err.max()), "mean_dalpha_re": float(err.mean()),
+                        "misbinned_fraction": mis / n, "strided_map_l1_over_rays": l1 / n,
+                        "max_rel_dalpha": float(np.max(np.abs(a_g - a_o) / (1 + np.abs(a_o))))}
+        if prec == mm.MM_FP32C:
+            assert err.max() <= ALPHA_TOL, err.max()
+            assert mis <= MISBIN_TOL * n, mis
+            assert l1 <= 2 * MISBIN_TOL * n, l1
+        else:
+            assert np.all(np.abs(a_g - a_o) <= 1e-9 * (1 + np.abs(a_o)))
+            assert mis <= max(1, 1e-8 * n), mis
+    print("CFG2_WINDOW_REPORT " + json.dumps(report))
+
+
+def test_fp64_ray_list_equals_the_fp64_map_kernel(ctx):
+    """Per-ray FP64 results (mm_debug_deflect, one thread per listed ray) equal the FP64 map kernel's:
+    every ray of a ragged sheared window, binned on the host, gives the map bit for bit."""
+    cfg = dict(sigma=0.6, gamma=0.25, smooth_frac=0.3, side=3.0, npix_side=48, nrays=36.0)
+    f = synth.lens_field(777, 14.0, 12, synth.MASS_LOGNORMAL)
+    lh = lens(ctx, f)
+    g = oracle.geometry(oracle_cfg(cfg))
+    rect = (g["nx"] // 2 - 211, g["nx"] // 2 + 190, g["ny"] // 2 - 95, g["ny"] // 2 + 70)
+    got, st = shoot(ctx, lh, cfg, ray_rect=rect, precision=mm.MM_FP64)
+    jj, ii = np.meshgrid(np.arange(rect[2], rect[3]), np.arange(rect[0], rect[1]), indexing="ij")
+    _, pix = mm.mm_debug_deflect(ctx, lh, P(cfg, precision=mm.MM_FP64), ii.ravel(), jj.ravel())
+    inside = pix[pix >= 0]
+    np.testing.assert_array_equal(np.bincount(inside, minlength=48 * 48).reshape(48, 48), got)
+    assert (inside.size, int(np.sum(pix < 0))) == (st["rays_in"], st["rays_out"])
+    mm.mm_release_lenses(ctx, lh)
 
 
 # -------------------------------------------------------- lognormal masses ---

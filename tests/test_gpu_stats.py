@@ -63,3 +63,38 @@ def test_fp32_and_fp64_maps_agree_excellently(ctx):
     assert r["rms_dm"] < 1e-3           # in fact only a few rays per million differ
     for m in (a, b):
         mm.mm_release_map(ctx, m)
+
+
+def restore_counts(ctx, counts, nrays, side=6.0):
+    """A map on the device holding the given host counts (mm_map_restore of a lens-free map whose
+    totals are the counts' sum): seeded synthetic input for the downstream kernels."""
+    n = counts.shape[0]
+    p = mm.params(sigma=0.45, gamma=0.2, smooth_frac=1.0, side=side, npix_side=n, nrays=nrays)
+    g = mm.mm_geometry_of(p)
+    tot = int(counts.sum(dtype=np.int64))
+    assert tot <= g["nx"] * g["ny"]
+    st = dict(rays_shot=tot, rays_in=tot, rays_out=0, interactions=0, nx=g["nx"], ny=g["ny"], nstar=0, seconds=0.0,
+              mu_mean=0.0, lens_splits=1, far_bound=0.0, far_block=0)
+    return mm.mm_map_restore(ctx, 0, p, counts, st)
+
+
+@pytest.mark.parametrize("nside,lam", [(129, 3.0), (256, 400.0)])
+def test_normalised_map_matches_oracle(ctx, nside, lam):
+    """mm_map_fetch_mu against the estimator mu = N / N_rays and Eq. deltam (oracle, FP64) on a seeded
+    synthetic count map with empty pixels, a few counts above 2^24 (not exact in FP32) and an odd side
+    (N_side^2 not a multiple of 4). Empty pixels are clamped to one ray for Delta m and counted."""
+    rng = np.random.default_rng(nside)
+    counts = rng.poisson(lam, (nside, nside)).astype(np.uint32)
+    counts.ravel()[rng.integers(0, nside * nside, 7)] = np.uint32(3_000_000_017)
+    nrays = lam * 0.9
+    m = restore_counts(ctx, counts, nrays)
+    mu, empty = mm.mm_map_fetch_mu(ctx, m, mm.MM_MAP_MU)
+    assert empty == int(np.sum(counts == 0)) and (lam > 100 or empty > 0)
+    np.testing.assert_allclose(mu, counts.astype(np.float64) / nrays, rtol=2e-7, atol=0)
+    dm, empty2 = mm.mm_map_fetch_mu(ctx, m, mm.MM_MAP_DELTA_M)
+    assert empty2 == empty
+    ref = ostats.delta_m(np.maximum(counts, 1), nrays)
+    np.testing.assert_allclose(dm, ref, rtol=0, atol=3e-6)
+    with pytest.raises(mm.MMError):
+        mm.mm_map_fetch_mu(ctx, m, 7)
+    mm.mm_release_map(ctx, m)
