@@ -155,9 +155,9 @@ def scaled_mix(count, seed, sides=(64, 128, 256), nrays=(10.0, 30.0, 100.0), cap
     return out
 
 
-def batch_phase(mm, ctx, sms, n_maps=64, seed=4):
-    """Config-3 shape, scaled: n maps of mixed shape and N* in ONE persistent launch, against the
-    same maps shot one by one, and against the plain FP64 kernel one by one on the smallest maps."""
+def scaled_batch_phase(mm, ctx, sms, n_maps=64, seed=4):
+    """Secondary line: the config-3 parameter mix scaled down (N_side in {64, 128, 256}, N_rays in
+    {10, 30, 100}, maps above 4e11 interactions redrawn) in ONE persistent launch, best of 3."""
     mix = scaled_mix(n_maps, seed)
     plist = [p for p, _ in mix]
     total = sum(i for _, i in mix)
@@ -171,74 +171,141 @@ def batch_phase(mm, ctx, sms, n_maps=64, seed=4):
         for m in maps:
             mm.mm_release_map(ctx, m)
     batch_ms = min(t)
-    one_ms = 0.0
-    for p in plist:
-        m = mm.mm_shoot(ctx, 0, p)
-        one_ms += mm.mm_last_kernel_ms(ctx)[0]
-        mm.mm_release_map(ctx, m)
-    small = sorted(mix, key=lambda pi: pi[1])[:8]
-    f64_ms, f64_inter = 0.0, 0
-    for p, inter in small:
-        q = mm.params(**{k: getattr(p, k) for k, _ in mm.mm_params._fields_ if k != "ray_rect"})
-        q.precision = mm.MM_FP64
-        m = mm.mm_shoot(ctx, 0, q)
-        f64_ms += mm.mm_last_kernel_ms(ctx)[0]
-        f64_inter += inter
-        mm.mm_release_map(ctx, m)
     return {"workload": f"{n_maps} maps, config-3 parameter mix (lognormal masses) scaled to N_side in "
                         "{64,128,256}, N_rays in {10,30,100}, <= 4e11 interactions each",
             "interactions": total, "batched_ms": batch_ms, "batched_interactions_per_s": total / (batch_ms * 1e-3),
-            "maps_per_s": n_maps / (batch_ms * 1e-3),
-            "frac_nflop10": FLOP_PER_INTERACTION * total / (batch_ms * 1e-3) / (fp32_peak_tflops(sms) * 1e12),
-            "useful_frac": USEFUL_OPS_WITH_MASSES * total / (batch_ms * 1e-3) / lane_peak_per_s(sms),
-            "one_by_one_ms": one_ms,
-            "one_by_one_interactions_per_s": total / (one_ms * 1e-3),
-            "fp64_one_by_one_interactions_per_s": f64_inter / (f64_ms * 1e-3),
-            "fp64_sample": "the 8 smallest maps of the mix, plain FP64 kernel, one launch each"}
+            "maps_per_s": n_maps / (batch_ms * 1e-3)}
 
 
-CFG2 = dict(sigma=0.8, gamma=0.3, smooth_frac=0.5, side=40.0, npix_side=2048, nrays=500.0)
-CFG2_NSTAR, CFG2_SEED = 25000, 3
+CFG3_SIDES, CFG3_NRAYS, CFG3_CAP = (256, 512, 1024), (100.0, 300.0, 1000.0), 5e13
 
 
-def config2_phase(mm, ctx, sms, band_fraction=16):
-    """The exact FP32 path on the high-optical-depth map (sigma = 0.8, s = 0.5, gamma = 0.3, L = 40,
-    2048^2 pixels, N_rays = 500, N* = 25000 unit lenses in a disc of 250 R_E, seed 3): the central
-    band of 1/band_fraction of the ray rows across the whole width of the 686921 x 137385-ray grid
-    (600 x 120 R_E), one mm_shoot with that ray_rect, timed by CUDA events (mm_last_kernel_ms)."""
-    import synth
-    p0 = mm.params(**CFG2, nstar=CFG2_NSTAR)
-    g = mm.mm_geometry_of(p0)
-    f = synth.lens_field(int(g["nstar"]), float(g["disc_radius"]), CFG2_SEED)
-    lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
-    h = g["ny"] // (2 * band_fraction)
-    rect = (0, g["nx"], g["ny"] // 2 - h, g["ny"] // 2 + h)
-    p = mm.params(**CFG2, nstar=CFG2_NSTAR, ray_rect=rect)
-    m = mm.mm_shoot(ctx, lh, p)
-    ms, _ = mm.mm_last_kernel_ms(ctx)
-    _, st = mm.mm_map_fetch(ctx, m, want_counts=False)
-    mm.mm_release_map(ctx, m)
-    mm.mm_release_lenses(ctx, lh)
-    rate = st["interactions"] / (ms * 1e-3)
-    return {"workload": f"sigma=0.8, s=0.5, gamma=0.3, L=40 R_E, 2048^2 px, N_rays=500, N*=25000 unit masses "
-                        f"(R=250 R_E, seed 3): ray rows [{rect[2]}, {rect[3]}) of {g['ny']} (1/{band_fraction} of the "
-                        f"grid, full width {g['nx']})",
-            "rays": st["rays_shot"], "interactions": st["interactions"], "ms": ms,
-            "interactions_per_s": rate,
+def config3_phase(mm, ctx, sms, n_maps=64, seed=4, fp64_interactions_per_map=6e9):
+    """The batched pattern on its own workload: 64 maps with sigma ~ U(0.2, 1.5), gamma ~ U(0, 0.6),
+    s ~ U(0, 0.9), L ~ U(10, 40) R_E, N_side in {256, 512, 1024}, N_rays in {100, 300, 1000},
+    lognormal(0, 0.5) masses, N* by the library's rule with <M> = e^0.125 (seeded; draws with
+    min |1 - sigma -+ gamma| < 0.05 redrawn, and maps above 5e13 interactions redrawn: the capped
+    variant, about 4.4e14 interactions in all). Lens sets are made first; then the 64 maps in ONE
+    persistent launch (mm_shoot_batch, timed by CUDA events), the same maps one by one (mm_shoot),
+    a bit-identity check of batched against alone on 8 maps, and the plain FP64 kernel one map at a
+    time on a central band of each map's ray rows holding about 6e9 interactions."""
+    mix = scaled_mix(n_maps, seed, sides=CFG3_SIDES, nrays=CFG3_NRAYS, cap=CFG3_CAP)
+    plist = [p for p, _ in mix]
+    total = sum(i for _, i in mix)
+    lenses = [mm.mm_create_lenses(ctx, p) for p in plist]
+    small = sorted(range(n_maps), key=lambda k: mix[k][1])[:4]
+    warm = mm.mm_shoot_batch(ctx, [lenses[k] for k in small], [plist[k] for k in small])   # kernels warm
+    for m in warm:
+        mm.mm_release_map(ctx, m)
+    batched = mm.mm_shoot_batch(ctx, lenses, plist)
+    batch_ms = mm.mm_last_kernel_ms(ctx)[0]
+    one_ms, identical, checked = 0.0, 0, 0
+    check = set(sorted(range(n_maps), key=lambda k: mix[k][1])[::8])        # 8 maps across the sizes
+    for k, p in enumerate(plist):
+        m = mm.mm_shoot(ctx, lenses[k], p)
+        one_ms += mm.mm_last_kernel_ms(ctx)[0]
+        if k in check:
+            a, _ = mm.mm_map_fetch(ctx, m)
+            b, _ = mm.mm_map_fetch(ctx, batched[k])
+            identical += int(np.array_equal(a, b))
+            checked += 1
+        mm.mm_release_map(ctx, m)
+    for m in batched:
+        mm.mm_release_map(ctx, m)
+    f64_ms, f64_inter = 0.0, 0
+    for k, p in enumerate(plist):
+        g = mm.mm_geometry_of(p)
+        rows = max(1, min(g["ny"], int(fp64_interactions_per_map / max(1, g["nx"] * g["nstar"]))))
+        q = mm.params(**{f: getattr(p, f) for f, _ in mm.mm_params._fields_ if f != "ray_rect"})
+        q.precision = mm.MM_FP64
+        q.ray_rect[:] = [0, g["nx"], g["ny"] // 2 - rows // 2, g["ny"] // 2 - rows // 2 + rows]
+        m = mm.mm_shoot(ctx, lenses[k], q)
+        f64_ms += mm.mm_last_kernel_ms(ctx)[0]
+        _, st = mm.mm_map_fetch(ctx, m, want_counts=False)
+        f64_inter += st["interactions"]
+        mm.mm_release_map(ctx, m)
+    for h in lenses:
+        mm.mm_release_lenses(ctx, h)
+    rate = total / (batch_ms * 1e-3)
+    inters = sorted(i for _, i in mix)
+    return {"workload": f"{n_maps} maps of the config-3 mix: sigma~U(0.2,1.5), gamma~U(0,0.6), s~U(0,0.9), "
+                        "L~U(10,40) R_E, N_side in {256,512,1024}, N_rays in {100,300,1000}, lognormal(0,0.5) "
+                        "masses, seed 4; maps above 5e13 interactions redrawn (capped variant)",
+            "interactions": total, "interactions_median": inters[len(inters) // 2], "interactions_max": inters[-1],
+            "nstar_max": max(int(mm.mm_geometry_of(p)["nstar"]) for p in plist),
+            "batched_ms": batch_ms, "batched_interactions_per_s": rate, "maps_per_s": n_maps / (batch_ms * 1e-3),
             "frac_nflop10": FLOP_PER_INTERACTION * rate / (fp32_peak_tflops(sms) * 1e12),
-            "useful_frac": USEFUL_OPS_PER_INTERACTION * rate / lane_peak_per_s(sms),
-            "whole_map_estimated_s": g["nx"] * g["ny"] * g["nstar"] / rate,
-            "lens_splits": st["lens_splits"]}
+            "useful_frac": USEFUL_OPS_WITH_MASSES * rate / lane_peak_per_s(sms),
+            "one_by_one_ms": one_ms, "one_by_one_interactions_per_s": total / (one_ms * 1e-3),
+            "one_by_one_maps_per_s": n_maps / (one_ms * 1e-3),
+            "batched_identical_to_alone": f"{identical} of {checked} maps bit-identical",
+            "fp64_one_by_one_interactions_per_s": f64_inter / (f64_ms * 1e-3),
+            "fp64_sample": f"plain FP64 kernel, each of the {n_maps} maps on a central band of its ray rows "
+                           f"(about {fp64_interactions_per_map:.0e} interactions per map, {f64_inter:.3e} in all)",
+            "fp32_batched_over_fp64": rate / (f64_inter / (f64_ms * 1e-3))}
 
 
-def serve_phase(mm, ctx, rate_hz, seconds, seed, large_every=10):
-    """Poisson request stream through mm_submit / mm_poll; latency = submit to completion."""
-    import threading
+def config4_stream(count, seed, large_every=10, cap=CFG3_CAP, large_cap=2e14):
+    """Requests of the served workload: the config-3 mix (capped at 5e13 interactions) with every
+    large_every-th request "large": 2048^2 pixels and N* = 20000 lognormal lenses in the disc that
+    Eq. nstar gives for kappa_* = sigma_*, its other parameters from the mix (redrawn above 2e14
+    interactions)."""
+    import paper_1005_5198_gb300 as mm
     import synth
-    n = max(8, int(rate_hz * seconds))
-    mix = scaled_mix(n, seed, large_every=large_every)
-    arrivals = synth.poisson_arrivals(n, rate_hz, seed)
+    out, k = [], 0
+    while len(out) < count:
+        k += 1
+        d = synth.map_mix(1, seed * 1000003 + k, sides=CFG3_SIDES, nrays=CFG3_NRAYS)[0]
+        large = large_every and len(out) % large_every == large_every - 1
+        kw = dict(sigma=d.sigma, gamma=d.gamma, smooth_frac=d.smooth_frac, side=d.side, nrays=d.nrays,
+                  mass_model=mm.MM_MASS_LOGNORMAL, mass_s=0.5, seed=d.seed)
+        p = mm.params(**kw, npix_side=2048, nstar=20000) if large else mm.params(**kw, npix_side=d.npix_side)
+        g = mm.mm_geometry_of(p)
+        inter = g["nx"] * g["ny"] * g["nstar"]
+        if inter > (large_cap if large else cap) or g["nstar"] == 0:
+            continue
+        out.append((p, inter, bool(large)))
+    return out
+
+
+def config4_phase(mm, ctx, capacity, args, overload_s=45.0, load_s=90.0, drain_s=45.0):
+    """The served workload (config 4): (i) the stated Poisson stream, lambda = 20 requests/s for 200
+    arrivals, about 70x one GPU's capacity: observed for overload_s after the first arrival, then the
+    rest is cancelled; (ii) lambda scaled to 70 % of the capacity measured by the batched launch on
+    the config-3 maps, arrivals for load_s, then up to drain_s for the last ones. HBM-budgeted
+    admission, device-resident lens sets and maps, waves of continuous batching."""
+    import synth
+    mm.mm_serve_config(ctx, max_active=64, wave_ms=args.wave_ms)
+    mm.mm_serve_priority(ctx, args.serve_priority)
+    sample = config4_stream(400, 6)
+    mean_inter = float(np.mean([i for _, i, _ in sample]))
+    over = config4_stream(200, 8)
+    res_over = serve_phase(mm, ctx, over, synth.poisson_arrivals(200, 20.0, 8), overload_s, 0.0)
+    lam = 0.7 * capacity / mean_inter
+    n70 = max(8, int(round(lam * load_s)))
+    load = config4_stream(n70, 7)
+    res_70 = serve_phase(mm, ctx, load, synth.poisson_arrivals(n70, lam, 7), 0.0, drain_s)
+    return {"workload": "config-4 stream: Poisson arrivals of the config-3 mix (capped at 5e13 interactions) "
+                        "with every 10th request large (2048^2 px, N*=20000 lognormal lenses, kappa_*=sigma_*, "
+                        "capped at 2e14); mm_submit/mm_poll continuous batching, latency from submit to completion",
+            "capacity_interactions_per_s": capacity, "mean_request_interactions": mean_inter,
+            "wave_ms": args.wave_ms, "priority_share": args.serve_priority,
+            "overload_lambda_20": dict(res_over, lambda_req_s=20.0, observed_s=overload_s),
+            "at_70pct_capacity": dict(res_70, lambda_req_s=lam)}
+
+
+def serve_phase(mm, ctx, stream, arrivals, observe_s, drain_s):
+    """Submit `stream` at the given arrival times (mm_submit), poll completions (mm_poll) until all
+    are done or `observe_s` after the first arrival plus up to `drain_s` after the last arrival,
+    then cancel what is left (mm_cancel) and wait for it. Latency = submit to completion (host
+    clock, mm_req_times). Requests not done at the end enter the censored percentiles with their
+    age at that moment (a lower bound of their latency). Device throughput = interactions of the
+    work items shot during the run (mm_serve_stats) / run time."""
+    import threading
+    n = len(stream)
     reqs = [None] * n
+    t_sub = [None] * n
+    s0 = mm.mm_serve_stats(ctx)
     t0 = time.perf_counter()
 
     def submitter():
@@ -246,13 +313,16 @@ def serve_phase(mm, ctx, rate_hz, seconds, seed, large_every=10):
             dt = arrivals[k] - (time.perf_counter() - t0)
             if dt > 0:
                 time.sleep(dt)
-            reqs[k] = mm.mm_submit(ctx, 0, mix[k][0])
+            t_sub[k] = time.perf_counter()
+            reqs[k] = mm.mm_submit(ctx, 0, stream[k][0])
 
     th = threading.Thread(target=submitter)
     th.start()
+    end = max(observe_s, arrivals[-1] + drain_s)
     done = [False] * n
-    lat, finished = [], 0
-    while finished < n:
+    lat = [None] * n
+    finished = 0
+    while finished < n and time.perf_counter() - t0 < end:
         progressed = False
         for k in range(n):
             if done[k] or reqs[k] is None:
@@ -262,17 +332,44 @@ def serve_phase(mm, ctx, rate_hz, seconds, seed, large_every=10):
                 done[k] = True
                 finished += 1
                 progressed = True
-                lat.append(mm.mm_req_times(ctx, reqs[k])[1])
+                lat[k] = mm.mm_req_times(ctx, reqs[k])[1]
                 mm.mm_release_map(ctx, m)
         if not progressed:
-            time.sleep(0.0005)
+            time.sleep(0.005)        # latency comes from the server's own clock, not this loop's
     th.join()
-    wall = time.perf_counter() - t0
-    lat = np.array(lat) * 1e3
-    total = sum(i for _, i in mix)
-    return {"lambda_req_s": rate_hz, "requests": n, "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
-            "sustained_interactions_per_s": total / wall, "wall_s": wall}
+    t_end = time.perf_counter()
+    s1 = mm.mm_serve_stats(ctx)
+    wall = t_end - t0
+    cancelled = 0
+    for k in range(n):
+        if done[k]:
+            continue
+        try:
+            mm.mm_cancel(ctx, reqs[k])
+            cancelled += 1
+        except mm.MMError:
+            pass
+    for k in range(n):                                   # wait for the rest to end (cancelled or done)
+        if done[k]:
+            continue
+        try:
+            m = mm.mm_wait(ctx, reqs[k], timeout_s=600)
+            mm.mm_release_map(ctx, m)
+        except mm.MMError as e:
+            if e.code != mm.MM_ECANCELED:
+                raise
+    lat_done = np.array([x for x in lat if x is not None]) * 1e3
+    censored = np.array([lat[k] * 1e3 if lat[k] is not None else (t_end - t_sub[k]) * 1e3 for k in range(n)])
+    pct = (lambda a, q: float(np.percentile(a, q)) if len(a) else None)
+    large_done = [lat[k] * 1e3 for k in range(n) if lat[k] is not None and stream[k][2]]
+    return {"requests": n, "completed": int(len(lat_done)), "cancelled_at_end": cancelled,
+            "large_requests": int(sum(1 for x in stream if x[2])), "large_completed": len(large_done),
+            "p50_ms": pct(lat_done, 50), "p99_ms": pct(lat_done, 99), "max_ms": pct(lat_done, 100),
+            "censored_p50_ms": pct(censored, 50), "censored_p99_ms": pct(censored, 99),
+            "offered_interactions_per_s": sum(x[1] for x in stream) / max(arrivals[-1], 1e-9),
+            "sustained_interactions_per_s": (s1["interactions"] - s0["interactions"]) / wall,
+            "completed_interactions_per_s": sum(stream[k][1] for k in range(n) if done[k]) / wall,
+            "wall_s": wall}
 
 
 KERNEL_SOURCES = ["mm_fp32.cuh", "mm_device.cuh", "mm_internal.h", "mm_fp32_c2r4.cu"]
@@ -693,19 +790,9 @@ def main():
         extra["config2_exact"] = config2_phase(mm, ctx, sms)
         extra["far_field"] = far_phase(mm, ctx, lh, sum(kern_ms) / len(kern_ms))
         extra["downstream"] = downstream_phase(mm, ctx)
-        extra["batch"] = batch_phase(mm, ctx, sms)
-        mm.mm_serve_config(ctx, max_active=64, wave_ms=args.wave_ms)
-        mm.mm_serve_priority(ctx, args.serve_priority)
-        capacity = extra["batch"]["batched_interactions_per_s"]          # the same mix shape, batched
-        mean_inter = np.mean([i for _, i in scaled_mix(200, 6, large_every=10)])
-        lam = 0.7 * capacity / mean_inter
-        extra["serving"] = {
-            "workload": "Poisson arrivals of the scaled config-3 mix plus every 10th request 4x the pixels; "
-                        "mm_submit/mm_poll continuous batching, latency from submit to completion",
-            "capacity_interactions_per_s": capacity, "mean_request_interactions": float(mean_inter),
-            "wave_ms": args.wave_ms, "priority_share": args.serve_priority,
-            "at_70pct_capacity": serve_phase(mm, ctx, lam, 20.0, 7),
-            "overload_3x": serve_phase(mm, ctx, 3.0 * lam, 5.0, 8)}
+        extra["batch"] = config3_phase(mm, ctx, sms)
+        extra["batch_scaled"] = scaled_batch_phase(mm, ctx, sms)
+        extra["serving"] = config4_phase(mm, ctx, extra["batch"]["batched_interactions_per_s"], args)
 
     clocks = clk.summary()
     kmean = sum(kern_ms) / len(kern_ms)

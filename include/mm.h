@@ -249,7 +249,7 @@ int mm_map_fetch(mm_ctx *ctx, mm_map map, uint32_t *host_counts, size_t n_elems,
  *   MM_MAP_DELTA_M  Delta m_ij = -2.5 log10(max(N_ij, 1) / N_rays) (Eq. deltam), an empty
  *                   pixel clamped to one ray (the paper gives no value for mu = 0).
  * *n_empty (may be NULL) receives the number of pixels with N_ij = 0 (the clamped ones).
- * FP32 arithmetic: mu within 2e-7 relative, Delta m within 3e-6 mag of the FP64 values.
+ * FP32 arithmetic: mu within 2e-7 relative, Delta m within 1e-5 mag of the FP64 values.
  * Blocks until the map is complete. Errors: MM_EINVAL (kind, NULL buffer or wrong
  * n_elems), MM_ENOTFOUND, MM_ENOMEM, MM_EDEVICE. */
 #define MM_MAP_MU       0
@@ -284,8 +284,25 @@ int mm_poll(mm_ctx *ctx, mm_req req, int *done, mm_map *map_out);
  * Errors: MM_ETIMEDOUT (still running), or the request's own error. */
 int mm_wait(mm_ctx *ctx, mm_req req, int64_t timeout_ns, mm_map *map_out);
 
-/* Cancel a request that has not been admitted yet; MM_EBUSY if it already runs. */
+/* Cancel a request. A queued request ends at once; an admitted one stops before its
+ * next work item is scheduled (work already on the GPU finishes first, and the map
+ * is dropped); either way it then reports MM_ECANCELED. MM_EBUSY if the request has
+ * finished or all of its work is already on the GPU (it will complete normally). */
 int mm_cancel(mm_ctx *ctx, mm_req req);
+
+/* Serving counters since the context's server started (all zero before the first
+ * mm_submit or mm_serve_config). */
+typedef struct {
+    uint64_t waves;         /* waves completed */
+    uint64_t items;         /* work items (ray tiles, or far-field block rows) they shot */
+    double   interactions;  /* ray-lens interactions of those items: each item's share of its
+                               map's rays x N* (for far-field maps, the exact method's count) */
+    uint64_t completed, cancelled, failed;   /* requests ended each way */
+    int32_t  queued;        /* requests waiting for admission now */
+    int32_t  preparing;     /* admitted, lens field and map being prepared */
+    int32_t  active;        /* admitted and prepared, being shot */
+} mm_serve_stats_t;
+int mm_serve_stats(mm_ctx *ctx, mm_serve_stats_t *out);
 
 /* Latency of a finished request: submit -> admit -> done, seconds (host clock). */
 int mm_req_times(mm_ctx *ctx, mm_req req, double *t_queue, double *t_total);

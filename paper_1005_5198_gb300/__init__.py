@@ -70,6 +70,12 @@ class mm_compare(C.Structure):
                 ("ks_d", C.c_double), ("ks_p", C.c_double), ("mean_mu_a", C.c_double), ("mean_mu_b", C.c_double)]
 
 
+class mm_serve_stats_t(C.Structure):
+    _fields_ = [("waves", C.c_uint64), ("items", C.c_uint64), ("interactions", C.c_double),
+                ("completed", C.c_uint64), ("cancelled", C.c_uint64), ("failed", C.c_uint64),
+                ("queued", C.c_int32), ("preparing", C.c_int32), ("active", C.c_int32)]
+
+
 class mm_geometry(C.Structure):
     _fields_ = [("pix", C.c_double), ("delta", C.c_double), ("width", C.c_double), ("height", C.c_double),
                 ("nx", C.c_int64), ("ny", C.c_int64), ("nstar", C.c_int64), ("disc_radius", C.c_double),
@@ -110,6 +116,7 @@ def _load():
         "mm_wait": [C.c_void_p, U64, I64, P(U64)],
         "mm_cancel": [C.c_void_p, U64],
         "mm_req_times": [C.c_void_p, U64, P(D), P(D)],
+        "mm_serve_stats": [C.c_void_p, P(mm_serve_stats_t)],
         "mm_serve_config": [C.c_void_p, C.c_int32, C.c_int32, D],
         "mm_serve_priority": [C.c_void_p, D],
         "mm_serve_plan": [P(C.c_uint64), P(D), C.c_int32, D, D, C.c_uint64, P(C.c_uint64)],
@@ -337,6 +344,14 @@ def mm_req_times(ctx: Ctx, req: int) -> tuple[float, float]:
     return q.value, t.value
 
 
+def mm_serve_stats(ctx: Ctx) -> dict:
+    """Serving counters: waves, items, interactions shot, requests completed / cancelled / failed,
+    and the requests queued, being prepared and active now."""
+    out = mm_serve_stats_t()
+    _check(_load().mm_serve_stats(ctx.handle, C.byref(out)), "mm_serve_stats")
+    return {k: getattr(out, k) for k, _ in mm_serve_stats_t._fields_}
+
+
 def mm_serve_config(ctx: Ctx, max_active: int = 0, max_queued: int = 0, wave_ms: float = 0.0) -> None:
     _check(_load().mm_serve_config(ctx.handle, max_active, max_queued, wave_ms), "mm_serve_config")
 
@@ -455,7 +470,7 @@ EXPORTED = [
     "mm_init", "mm_destroy", "mm_params_default", "mm_geometry_of", "mm_create_lenses", "mm_create_lenses_from",
     "mm_lenses_fetch", "mm_lenses_count", "mm_release_lenses", "mm_shoot", "mm_shoot_batch", "mm_shoot_into",
     "mm_map_restore", "mm_map_fetch", "mm_map_fetch_mu",
-    "mm_map_device_ptr", "mm_release_map", "mm_submit", "mm_poll", "mm_wait", "mm_cancel", "mm_req_times",
+    "mm_map_device_ptr", "mm_release_map", "mm_submit", "mm_poll", "mm_wait", "mm_cancel", "mm_req_times", "mm_serve_stats",
     "mm_serve_config", "mm_serve_priority", "mm_serve_plan", "mm_autotune", "mm_set_variant", "mm_variant_count", "mm_variant_name", "mm_set_layout",
     "mm_get_layout", "mm_layout_count", "mm_layout_name", "mm_debug_deflect",
     "mm_last_kernel_ms", "mm_shoot_noalloc", "mm_map_compare", "mm_map_convolve",

@@ -48,6 +48,8 @@ struct Request {
     unsigned long long cursor = 0;     // next work item to schedule
     unsigned long long tiles = 0;      // work items of the map (tiles x lens segments)
     std::atomic<int> state{0};         // 0 queued, 1 admitted, 2 done, 3 failed, 4 cancelled
+    bool cancel = false;               // admitted, then cancelled: stop at the next wave (under the mutex)
+    double work = 0;                   // ray-lens interactions of the whole map (rays x N*)
     int err = 0;
     std::string err_msg;
     double t_submit = 0, t_admit = 0, t_done = 0;
@@ -59,6 +61,7 @@ struct WaveItem {
     std::shared_ptr<Request> req;
     unsigned long long tiles;
     bool last;
+    double work;                       // the item's share of the map's interactions
 };
 
 struct Wave {
@@ -101,10 +104,14 @@ struct Server {
     double rate = 5.0e9;               // interactions per ms, refined from full waves
     std::atomic<uint64_t> next_id{1};
     std::string fatal;
+    // counters since the server started (mm_serve_stats)
+    unsigned long long n_waves = 0, n_items = 0, n_completed = 0, n_cancelled = 0, n_failed = 0;
+    double work_done = 0;              // interactions of the work items of completed waves
 };
 
 static void finish(Server *S, const std::shared_ptr<Request> &r, int state, int err, const std::string &msg)
 {
+    (state == 2 ? S->n_completed : state == 4 ? S->n_cancelled : S->n_failed)++;
     r->err = err;
     r->err_msg = msg;
     r->t_done = now_s();
@@ -155,6 +162,7 @@ static void admit_worker(Server *S, int idx)
             r->map = M;
             // work items: tiles x lens segments, or the far field's block rows
             r->tiles = r->p.precision == MM_FAR32 ? M->far.items : M->items();
+            r->work = (double)r->g.ni * (double)r->g.nj * (double)L->n;
             S->ready.push_back(r);
         }
         S->cv.notify_all();
@@ -249,7 +257,7 @@ static void plan_wave(Server *S, Wave *w)
 {
     std::vector<std::shared_ptr<Request>> live;
     for (auto &r : S->active)
-        if (r->cursor < r->tiles) live.push_back(r);
+        if (r->cursor < r->tiles && !r->cancel) live.push_back(r);
     if (live.empty()) return;
     const unsigned long long min_tiles =
         4ULL * (unsigned long long)S->ctx->sms * (unsigned long long)shoot_ctas_per_sm(false, S->ctx->layout);
@@ -264,7 +272,8 @@ static void plan_wave(Server *S, Wave *w)
                 take.data());
     for (int k = 0; k < n; ++k) {
         if (!take[k]) continue;
-        w->items.push_back(WaveItem{live[k], take[k], live[k]->cursor + take[k] == live[k]->tiles});
+        w->items.push_back(WaveItem{live[k], take[k], live[k]->cursor + take[k] == live[k]->tiles,
+                                    live[k]->work * (double)take[k] / (double)live[k]->tiles});
         w->tiles += take[k];
         w->interactions += (double)take[k] * cost[k];
     }
@@ -408,6 +417,11 @@ static void complete_wave(Server *S, Wave &w, std::unique_lock<std::mutex> &lk)
         const double r = w.interactions / (double)ms;
         S->rate = std::min(2.0e10, std::max(5.0e8, 0.8 * S->rate + 0.2 * r));
     }
+    S->n_waves++;
+    for (auto &it : w.items) {
+        S->n_items += it.tiles;
+        S->work_done += it.work;
+    }
     for (auto &it : w.items) {
         if (!it.last) continue;
         auto &r = it.req;
@@ -433,10 +447,27 @@ static void loop(Server *S)
             for (auto &r : S->queue) finish(S, r, 4, MM_ECANCELED, "server stopped");
             S->queue.clear();
         }
-        for (auto &r : S->ready) S->active.push_back(r);
+        for (auto &r : S->ready) {
+            if (r->cancel) finish(S, r, 4, MM_ECANCELED, "cancelled");    // prepared, never shot
+            else S->active.push_back(r);
+        }
         S->ready.clear();
+        // cancelled maps leave once no wave in flight holds their tiles
+        for (size_t k = 0; k < S->active.size();) {
+            auto r = S->active[k];
+            bool held = false;
+            for (auto &w : S->inflight)
+                for (auto &it : w.items) held = held || it.req == r;
+            if (r->cancel && !held) {
+                S->active.erase(S->active.begin() + (long)k);
+                finish(S, r, 4, MM_ECANCELED, "cancelled");
+                S->admit_cv.notify_all();
+            } else {
+                ++k;
+            }
+        }
         bool have_work = false;
-        for (auto &r : S->active) have_work = have_work || r->cursor < r->tiles;
+        for (auto &r : S->active) have_work = have_work || (r->cursor < r->tiles && !r->cancel);
         if (S->stop && S->inflight.empty() && !have_work && S->preparing == 0) {
             for (auto &r : S->active) finish(S, r, 4, MM_ECANCELED, "server stopped");
             S->active.clear();
@@ -671,9 +702,35 @@ int mm_cancel(mm_ctx *ctx, mm_req req)
     auto r = find_req(S, req);
     if (!r) return fail(MM_ENOTFOUND, "unknown request");
     auto it = std::find(S->queue.begin(), S->queue.end(), r);
-    if (it == S->queue.end()) return fail(MM_EBUSY, "request already admitted or finished");
-    S->queue.erase(it);
-    finish(S, r, 4, MM_ECANCELED, "cancelled");
+    if (it != S->queue.end()) {
+        S->queue.erase(it);
+        finish(S, r, 4, MM_ECANCELED, "cancelled");
+        return MM_OK;
+    }
+    // admitted: stops before its next work item is scheduled, unless all of it is on the GPU
+    if (r->state.load() != 1 || r->cancel || (r->tiles > 0 && r->cursor >= r->tiles))
+        return fail(MM_EBUSY, "request already finished or fully scheduled");
+    r->cancel = true;
+    S->cv.notify_all();
+    return MM_OK;
+}
+
+int mm_serve_stats(mm_ctx *ctx, mm_serve_stats_t *out)
+{
+    if (!ctx || !out) return fail(MM_EINVAL, "null argument");
+    std::memset(out, 0, sizeof(*out));
+    Server *S = ctx->server;
+    if (!S) return MM_OK;
+    std::lock_guard<std::mutex> lk(S->mu);
+    out->waves = S->n_waves;
+    out->items = S->n_items;
+    out->interactions = S->work_done;
+    out->completed = S->n_completed;
+    out->cancelled = S->n_cancelled;
+    out->failed = S->n_failed;
+    out->queued = (int32_t)S->queue.size();
+    out->preparing = S->preparing;
+    out->active = (int32_t)(S->active.size() + S->ready.size());
     return MM_OK;
 }
 

@@ -512,9 +512,20 @@ def test_batch_results_identical_to_alone(ctx):
         mm.mm_release_map(ctx, m)
 
 
+def large_request():
+    """A "large" request of the served mix: 2048^2 pixels and N* = 20000 lognormal lenses with
+    kappa_* = sigma_* (disc radius from Eq. nstar), here at N_rays = 4 (3.4e8 rays)."""
+    cfg = dict(sigma=0.45, gamma=0.2, smooth_frac=0.3, side=20.0, npix_side=2048, nrays=4.0)
+    mmean = field.mean_mass(1, 0.0, 0.5)
+    f = synth.lens_field(20000, field.radius_for_nstar(20000, 0.45 * 0.7, mmean), 77, synth.MASS_LOGNORMAL)
+    return cfg, f, None
+
+
 @pytest.mark.parametrize("priority", [0.8, 0.0, 1.0])
 def test_serving_results_identical_to_alone(ctx, priority):
-    items = mix_windows(8, 12)
+    """Eight mixed-shape windows and one large whole map, served together through continuous
+    batching, each equal bit for bit to the same map shot alone."""
+    items = mix_windows(8, 12) + [large_request()]
     mm.mm_serve_config(ctx, max_active=4, wave_ms=0.5)
     mm.mm_serve_priority(ctx, priority)
     try:
@@ -553,6 +564,40 @@ def test_serving_small_request_overtakes_a_large_one(ctx):
         mm.mm_release_map(ctx, mb)
     finally:
         mm.mm_serve_priority(ctx, 0.8)
+
+
+def test_serving_cancels_an_admitted_request(ctx):
+    """An admitted request cancelled in mid-map stops at the next wave and reports MM_ECANCELED; the
+    counters account for it, and the server goes on serving (a later request equals its map alone)."""
+    mm.mm_serve_config(ctx, max_active=4, wave_ms=0.5)
+    before = mm.mm_serve_stats(ctx)
+    f = field1()
+    lh = lens(ctx, f)
+    big = mm.mm_submit(ctx, lh, P(CFG1))                 # the Fig. 1 map, 7.3e12 interactions
+    import time
+    time.sleep(0.3)
+    mm.mm_cancel(ctx, big)
+    with pytest.raises(mm.MMError) as e:
+        mm.mm_wait(ctx, big, timeout_s=60)
+    assert e.value.code == mm.MM_ECANCELED
+    with pytest.raises(mm.MMError) as e2:                 # ended: nothing left to cancel
+        mm.mm_cancel(ctx, big)
+    assert e2.value.code == mm.MM_EBUSY
+    after = mm.mm_serve_stats(ctx)
+    assert after["cancelled"] == before["cancelled"] + 1
+    shot = after["interactions"] - before["interactions"]
+    assert 0 < shot < 0.9 * 7.31e12
+    assert after["active"] == 0 and after["queued"] == 0
+    cfg = dict(CFG0)
+    r = mm.mm_submit(ctx, 0, P(cfg, nstar=100, seed=1))
+    m = mm.mm_wait(ctx, r, timeout_s=60)
+    got, _ = mm.mm_map_fetch(ctx, m)
+    h = mm.mm_create_lenses(ctx, P(cfg, nstar=100, seed=1))
+    ref, _ = shoot(ctx, h, cfg)
+    np.testing.assert_array_equal(got, ref)
+    done = mm.mm_serve_stats(ctx)
+    assert done["completed"] == after["completed"] + 1 and done["waves"] > after["waves"]
+    mm.mm_release_map(ctx, m)
 
 
 def test_serving_generates_fields_and_polls(ctx):
