@@ -177,6 +177,40 @@ def scaled_batch_phase(mm, ctx, sms, n_maps=64, seed=4):
             "maps_per_s": n_maps / (batch_ms * 1e-3)}
 
 
+CFG2 = dict(sigma=0.8, gamma=0.3, smooth_frac=0.5, side=40.0, npix_side=2048, nrays=500.0)
+CFG2_NSTAR, CFG2_SEED = 25000, 3
+
+
+def config2_phase(mm, ctx, sms, band_fraction=16):
+    """The exact FP32 path on the high-optical-depth map (sigma = 0.8, s = 0.5, gamma = 0.3, L = 40,
+    2048^2 pixels, N_rays = 500, N* = 25000 unit lenses in a disc of 250 R_E, seed 3): the central
+    band of 1/band_fraction of the ray rows across the whole width of the 686921 x 137385-ray grid
+    (600 x 120 R_E), one mm_shoot with that ray_rect, timed by CUDA events (mm_last_kernel_ms)."""
+    import synth
+    p0 = mm.params(**CFG2, nstar=CFG2_NSTAR)
+    g = mm.mm_geometry_of(p0)
+    f = synth.lens_field(int(g["nstar"]), float(g["disc_radius"]), CFG2_SEED)
+    lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
+    h = g["ny"] // (2 * band_fraction)
+    rect = (0, g["nx"], g["ny"] // 2 - h, g["ny"] // 2 + h)
+    p = mm.params(**CFG2, nstar=CFG2_NSTAR, ray_rect=rect)
+    m = mm.mm_shoot(ctx, lh, p)
+    ms, _ = mm.mm_last_kernel_ms(ctx)
+    _, st = mm.mm_map_fetch(ctx, m, want_counts=False)
+    mm.mm_release_map(ctx, m)
+    mm.mm_release_lenses(ctx, lh)
+    rate = st["interactions"] / (ms * 1e-3)
+    return {"workload": f"sigma=0.8, s=0.5, gamma=0.3, L=40 R_E, 2048^2 px, N_rays=500, N*=25000 unit masses "
+                        f"(R=250 R_E, seed 3): ray rows [{rect[2]}, {rect[3]}) of {g['ny']} (1/{band_fraction} of the "
+                        f"grid, full width {g['nx']})",
+            "rays": st["rays_shot"], "interactions": st["interactions"], "ms": ms,
+            "interactions_per_s": rate,
+            "frac_nflop10": FLOP_PER_INTERACTION * rate / (fp32_peak_tflops(sms) * 1e12),
+            "useful_frac": USEFUL_OPS_PER_INTERACTION * rate / lane_peak_per_s(sms),
+            "whole_map_estimated_s": g["nx"] * g["ny"] * g["nstar"] / rate,
+            "lens_splits": st["lens_splits"]}
+
+
 CFG3_SIDES, CFG3_NRAYS, CFG3_CAP = (256, 512, 1024), (100.0, 300.0, 1000.0), 5e13
 
 
