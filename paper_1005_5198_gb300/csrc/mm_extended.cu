@@ -45,7 +45,8 @@ __global__ void k_gauss_pass(const unsigned *cin, const float *fin, float *out, 
     }
 }
 
-// Disc: direct sum over row spans; span[dj + H] = half-width of the disc on row dj.
+// Disc: direct sum over row spans; span[dj + H] = half-width of the disc on row dj. The integer
+// total of the disc is converted to float once and scaled by 1 / (taps N_rays).
 __global__ void k_disc(const unsigned *cin, float *out, int n, const int *span, int H, float scale)
 {
     const long long total = (long long)n * n;
@@ -55,128 +56,181 @@ __global__ void k_disc(const unsigned *cin, float *out, int n, const int *span, 
             out[q] = __int_as_float(0x7fc00000);
             continue;
         }
-        float s = 0.f;
+        unsigned long long total = 0;
         for (int dj = -H; dj <= H; ++dj) {
             const int w = span[dj + H];
             const unsigned *row = cin + (long long)(j + dj) * n + i;
-            unsigned long long rs = 0;
-            for (int di = -w; di <= w; ++di) rs += row[di];
-            s += (float)rs;
+            for (int di = -w; di <= w; ++di) total += row[di];
         }
-        out[q] = s * scale;
+        out[q] = (float)total * scale;
     }
 }
 
 // ---- tiled forms of the passes above: the same per-pixel sums in the same order ----
 
-constexpr int kGaussRowThreads = 256, kGaussRowPer = 4;   // row pass: 4 outputs per thread, 256 apart
-constexpr int kGaussRowTile = kGaussRowThreads * kGaussRowPer;   // outputs per CTA along a row
-constexpr int kGaussColTileW = 32, kGaussColTileH = 64;   // column pass: 32 columns x 64 rows per CTA
 constexpr int kDiscTileW = 64, kDiscTileH = 32;        // disc: 64 x 32 outputs per CTA
 constexpr size_t kTileSmemMax = 48 * 1024;             // dynamic shared memory of a tiled CTA (no opt-in);
                                                        // wider supports take the untiled kernels
 
-__host__ __device__ inline size_t gauss_row_smem(int h) { return (size_t)(2 * h + 1 + kGaussRowTile + 2 * h) * 4; }
+// Gaussian passes, register-blocked: a thread owns kGG groups of 8 consecutive outputs along the
+// pass direction and runs the taps in chunks of 8. For a chunk it loads the 15 inputs that its 8
+// outputs need into registers once and makes 64 FMAs from them, so shared memory supplies about one
+// word per 4 FMAs instead of one or more per FMA. Every output still adds its taps in order
+// (fmaf, tap 0 first), exactly as k_gauss_pass does.
+constexpr int kGG = 2;                                  // groups of 8 outputs per thread
+constexpr int kGRows = 32;                              // row pass: tile rows, one per lane
+constexpr int kGRowOut = 8 * kGG * 8;                   // row pass: outputs per tile row (8 warps)
+constexpr int kGColOut = 8 * kGG * 8;                   // column pass: output rows per tile (8 warps)
+constexpr int kGCols = 32;                              // column pass: tile columns, one per lane
+
+__host__ __device__ inline int gauss_row_stride(int h) { return (kGRowOut + 2 * h) | 1; }   // odd: rows hit distinct banks
+__host__ __device__ inline int gauss_taps_padded(int h) { return (2 * h + 1 + 7) & ~7; }
+__host__ __device__ inline size_t gauss_row_smem(int h)
+{
+    return ((size_t)gauss_taps_padded(h) + (size_t)kGRows * gauss_row_stride(h)) * 4;
+}
 __host__ __device__ inline size_t gauss_col_smem(int h)
 {
-    return (size_t)(2 * h + 1 + (kGaussColTileH + 2 * h) * kGaussColTileW) * 4;
+    return ((size_t)gauss_taps_padded(h) + (size_t)(kGColOut + 2 * h) * kGCols) * 4;
 }
 __host__ __device__ inline size_t disc_smem(int H)
 {
     return (size_t)(kDiscTileH + 2 * H) * (kDiscTileW + 2 * H + 1) * 8 + (size_t)(2 * H + 1) * 4;
 }
 
-// Row pass (dir 0 of k_gauss_pass): a CTA stages the row segment [i0 - h, i0 + 1024 + h)
-// and the taps in shared memory; thread t sums outputs i0 + t + 256 u (u < 4), tap by tap,
-// so a tap weight is read once for four outputs (each output still adds its taps in order).
+// acc[u] += sum over taps k of [k0, k0 + 8) of g[k] x[u + k - k0], tap by tap, for the 8 outputs
+// whose inputs start at x (stride st between consecutive inputs).
+__device__ __forceinline__ void gauss_chunk8(const float *gk, const float *x, int st, float *acc)
+{
+    float v[15];
+#pragma unroll
+    for (int q = 0; q < 15; ++q) v[q] = x[q * st];
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+        const float w = gk[kk];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] = fmaf(w, v[u + kk], acc[u]);
+    }
+}
+
+// The taps of one thread's groups over a staged tile: x0 = first input of the thread's first group,
+// gstep = distance between its groups, st = distance between consecutive inputs.
+__device__ __forceinline__ void gauss_taps(const float *gs, int taps, const float *x0, int gstep, int st,
+                                           float (&acc)[kGG][8])
+{
+#pragma unroll
+    for (int q = 0; q < kGG; ++q)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[q][u] = 0.f;
+    int k0 = 0;
+    for (; k0 + 8 <= taps; k0 += 8) {
+        float gk[8];
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) gk[kk] = gs[k0 + kk];
+#pragma unroll
+        for (int q = 0; q < kGG; ++q) gauss_chunk8(gk, x0 + q * gstep + k0 * st, st, acc[q]);
+    }
+    for (; k0 < taps; ++k0) {                              // the last taps, one at a time
+        const float w = gs[k0];
+#pragma unroll
+        for (int q = 0; q < kGG; ++q)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[q][u] = fmaf(w, x0[q * gstep + (u + k0) * st], acc[q][u]);
+    }
+}
+
+// Row pass (dir 0 of k_gauss_pass): a CTA stages rows [r0, r0 + 32) x columns [c0 - h, c0 + 128 + h)
+// (the inputs, as floats) and the taps; lane l takes row r0 + l, warp w outputs c0 + 16 w .. + 16.
+// The outputs go back through shared memory so that the global stores run along rows.
 template <bool FROM_COUNTS>
-__global__ void __launch_bounds__(kGaussRowThreads) k_gauss_rows(const unsigned *cin, const float *fin, float *out,
-                                                                 int n, const float *g, int h, float inv_nrays)
+__global__ void __launch_bounds__(256) k_gauss_rows(const unsigned *cin, const float *fin, float *out, int n,
+                                                    const float *g, int h, float inv_nrays)
 {
     extern __shared__ float sm[];
-    float *const gs = sm, *const seg = sm + 2 * h + 1;      // taps [2h + 1], inputs [1024 + 2h]
-    for (int k = threadIdx.x; k < 2 * h + 1; k += blockDim.x) gs[k] = g[k];
-    const int segs = (n + kGaussRowTile - 1) / kGaussRowTile;
-    const long long tiles = (long long)n * segs;
+    const int taps = 2 * h + 1, S = gauss_row_stride(h), W = kGRowOut + 2 * h;
+    float *const gs = sm, *const tile = sm + gauss_taps_padded(h);
+    for (int k = threadIdx.x; k < taps; k += blockDim.x) gs[k] = g[k];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int cols = (n + kGRowOut - 1) / kGRowOut, rows = (n + kGRows - 1) / kGRows;
+    const long long tiles = (long long)cols * rows;
     for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
-        const int j = (int)(t / segs), i0 = (int)(t % segs) * kGaussRowTile;
-        __syncthreads();                                       // previous tile read; taps staged
-        for (int q = threadIdx.x; q < kGaussRowTile + 2 * h; q += blockDim.x) {
-            const int i = i0 - h + q;
+        const int c0 = (int)(t % cols) * kGRowOut, r0 = (int)(t / cols) * kGRows;
+        __syncthreads();                                   // previous tile's outputs written; taps staged
+        for (int q = threadIdx.x; q < kGRows * W; q += blockDim.x) {
+            const int rr = q / W, x = q % W, j = r0 + rr, i = c0 - h + x;
             float v = 0.f;
-            if (i >= 0 && i < n) {
+            if (j < n && i >= 0 && i < n) {
                 const long long src = (long long)j * n + i;
                 v = FROM_COUNTS ? (float)cin[src] * inv_nrays : fin[src];
             }
-            seg[q] = v;
+            tile[rr * S + x] = v;
         }
         __syncthreads();
-        float acc[kGaussRowPer];
+        float acc[kGG][8];
+        gauss_taps(gs, taps, tile + lane * S + w * 8 * kGG, 8, 1, acc);
+        __syncthreads();                                   // every thread has read the inputs
 #pragma unroll
-        for (int u = 0; u < kGaussRowPer; ++u) acc[u] = 0.f;
-        for (int k = 0; k <= 2 * h; ++k) {
-            const float gk = gs[k];
+        for (int q = 0; q < kGG; ++q)
 #pragma unroll
-            for (int u = 0; u < kGaussRowPer; ++u)
-                acc[u] = fmaf(gk, seg[threadIdx.x + kGaussRowThreads * u + k], acc[u]);
-        }
-#pragma unroll
-        for (int u = 0; u < kGaussRowPer; ++u) {
-            const int i = i0 + (int)threadIdx.x + kGaussRowThreads * u;
-            if (i < n) out[(long long)j * n + i] = (i - h >= 0 && i + h < n) ? acc[u] : __int_as_float(0x7fc00000);
+            for (int u = 0; u < 8; ++u) tile[lane * S + w * 8 * kGG + 8 * q + u] = acc[q][u];
+        __syncthreads();
+        for (int q = threadIdx.x; q < kGRows * kGRowOut; q += blockDim.x) {
+            const int rr = q / kGRowOut, x = q % kGRowOut, j = r0 + rr, i = c0 + x;
+            if (j < n && i < n)
+                out[(long long)j * n + i] = (i - h >= 0 && i + h < n) ? tile[rr * S + x] : __int_as_float(0x7fc00000);
         }
     }
 }
 
-// Column pass (dir 1): a CTA stages rows [r0 - h, r0 + 64 + h) of 32 columns; thread
-// (column tx, row group ty) sums rows ty, ty + 8, ... of the tile.
+// Column pass (dir 1): a CTA stages rows [r0 - h, r0 + 128 + h) of 32 columns; lane l takes column
+// c0 + l, warp w the output rows r0 + 16 w .. + 16 (stores along rows of 32 columns).
 __global__ void __launch_bounds__(256) k_gauss_cols(const float *fin, float *out, int n, const float *g, int h)
 {
     extern __shared__ float sm[];
-    float *const gs = sm, *const tile = sm + 2 * h + 1;    // taps, then [(64 + 2h) x 32]
-    for (int k = threadIdx.x; k < 2 * h + 1; k += blockDim.x) gs[k] = g[k];
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int cols = (n + kGaussColTileW - 1) / kGaussColTileW, rows = (n + kGaussColTileH - 1) / kGaussColTileH;
+    const int taps = 2 * h + 1;
+    float *const gs = sm, *const tile = sm + gauss_taps_padded(h);      // taps, then [(128 + 2h) x 32]
+    for (int k = threadIdx.x; k < taps; k += blockDim.x) gs[k] = g[k];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int cols = (n + kGCols - 1) / kGCols, rows = (n + kGColOut - 1) / kGColOut;
     const long long tiles = (long long)cols * rows;
     for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
-        const int c0 = (int)(t % cols) * kGaussColTileW, r0 = (int)(t / cols) * kGaussColTileH;
+        const int c0 = (int)(t % cols) * kGCols, r0 = (int)(t / cols) * kGColOut;
         __syncthreads();
-        for (int q = threadIdx.x; q < (kGaussColTileH + 2 * h) * kGaussColTileW; q += blockDim.x) {
-            const int j = r0 - h + q / kGaussColTileW, i = c0 + q % kGaussColTileW;
+        for (int q = threadIdx.x; q < (kGColOut + 2 * h) * kGCols; q += blockDim.x) {
+            const int j = r0 - h + q / kGCols, i = c0 + q % kGCols;
             tile[q] = (j >= 0 && j < n && i < n) ? fin[(long long)j * n + i] : 0.f;
         }
         __syncthreads();
-        // thread (tx, ty) sums rows ty + 8 u of the tile, tap by tap (a weight read once for 8 outputs)
-        constexpr int kPer = kGaussColTileH / 8;
-        float acc[kPer];
+        float acc[kGG][8];
+        gauss_taps(gs, taps, tile + (w * 8 * kGG) * kGCols + lane, 8 * kGCols, kGCols, acc);
+        const int i = c0 + lane;
 #pragma unroll
-        for (int u = 0; u < kPer; ++u) acc[u] = 0.f;
-        for (int k = 0; k <= 2 * h; ++k) {
-            const float gk = gs[k];
+        for (int q = 0; q < kGG; ++q)
 #pragma unroll
-            for (int u = 0; u < kPer; ++u) acc[u] = fmaf(gk, tile[(ty + 8 * u + k) * kGaussColTileW + tx], acc[u]);
-        }
-        const int i = c0 + tx;
-#pragma unroll
-        for (int u = 0; u < kPer; ++u) {
-            const int j = r0 + ty + 8 * u;
-            if (i < n && j < n) out[(long long)j * n + i] = (j - h >= 0 && j + h < n) ? acc[u] : __int_as_float(0x7fc00000);
-        }
+            for (int u = 0; u < 8; ++u) {
+                const int j = r0 + w * 8 * kGG + 8 * q + u;
+                if (i < n && j < n)
+                    out[(long long)j * n + i] = (j - h >= 0 && j + h < n) ? acc[q][u] : __int_as_float(0x7fc00000);
+            }
     }
 }
 
 // Disc: a CTA stages the counts of rows [r0 - H, r0 + 32 + H) x columns [c0 - H, c0 + 64 + H)
 // as prefix sums along each row (one warp per row, with a leading zero), so the sum over a row
-// span [i - w, i + w] is one difference, as k_disc's 64-bit sum. The prefix sums are taken
-// modulo 2^32 first: a CTA-wide vote finds whether any count of the tile reaches
-// 2^32 / (2H + 1); if none does, every span sum is below 2^32, so the 32-bit difference is
-// exact and converts to the same float. Otherwise the tile is staged again in 64 bits.
+// span [i - w, i + w] is one difference. An output's disc sum is the integer total of its row
+// spans, converted to float once (as k_disc). The prefix sums are taken modulo 2^32 first; a
+// CTA-wide vote on the tile's largest count picks how the spans are added:
+//   every count below 2^32 / (2H + 1)^2: the whole disc sum is below 2^32, so the span
+//     differences add up exactly in 32 bits;
+//   every count below 2^32 / (2H + 1): each span sum is below 2^32 and its 32-bit difference is
+//     exact; the spans add up in 64 bits;
+//   otherwise the tile is staged again as 64-bit prefix sums.
+// The three ways give the same integer, hence the same float.
 template <typename P>
-__device__ __forceinline__ int disc_prefix_rows(const unsigned *cin, int n, int r0, int c0, int H, int W, P *pre,
-                                                unsigned small_count)
+__device__ __forceinline__ void disc_prefix_rows(const unsigned *cin, int n, int r0, int c0, int H, int W, P *pre,
+                                                 unsigned &maxc)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int large = 0;
     for (int rr = warp; rr < kDiscTileH + 2 * H; rr += 8) {       // prefix sums of tile row rr
         const int j = r0 - H + rr;
         P carry = 0;
@@ -184,7 +238,7 @@ __device__ __forceinline__ int disc_prefix_rows(const unsigned *cin, int n, int 
         for (int x0 = 0; x0 < W - 1; x0 += 32) {
             const int x = x0 + lane, i = c0 - H + x;
             const unsigned cnt = (x < W - 1 && j >= 0 && j < n && i >= 0 && i < n) ? cin[(long long)j * n + i] : 0u;
-            large |= cnt >= small_count;
+            maxc = max(maxc, cnt);
             P v = cnt;
             for (int o = 1; o < 32; o <<= 1) {
                 const P u = __shfl_up_sync(0xffffffffu, v, o);
@@ -194,29 +248,36 @@ __device__ __forceinline__ int disc_prefix_rows(const unsigned *cin, int n, int 
             carry += __shfl_sync(0xffffffffu, v, 31);
         }
     }
-    return large;
 }
 
-template <typename P>
+// Thread (column c, row group rg) computes the 8 outputs of rows rg, rg + 4, ..., rg + 28 of the
+// tile together (8 independent sums). P: prefix type; A: accumulator type.
+template <typename P, typename A>
 __device__ __forceinline__ void disc_outputs(const P *pre, const int *sp, float *out, int n, int r0, int c0, int H,
                                              int W, float scale)
 {
+    constexpr int kPer = kDiscTileH / 4;
     const int c = threadIdx.x & (kDiscTileW - 1), rg = threadIdx.x / kDiscTileW;   // 4 row groups
     const int i = c0 + c;
-    for (int r = rg; r < kDiscTileH; r += 4) {
-        const int j = r0 + r;
-        if (i >= n || j >= n) continue;
-        float o = __int_as_float(0x7fc00000);
-        if (i - H >= 0 && i + H < n && j - H >= 0 && j + H < n) {
-            float acc = 0.f;
-            for (int dj = -H; dj <= H; ++dj) {
-                const int w = sp[dj + H];
-                const P *row = pre + (size_t)(r + dj + H) * W;
-                acc += (float)(P)(row[c + H + w + 1] - row[c + H - w]);
-            }
-            o = acc * scale;
+    A acc[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) acc[u] = 0;
+    for (int dj = -H; dj <= H; ++dj) {
+        const int w = sp[dj + H];
+        const P *row = pre + (size_t)(rg + dj + H) * W + c + H;
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const P *ru = row + (size_t)(4 * u) * W;
+            acc[u] += (A)(P)(ru[w + 1] - ru[-w]);
         }
-        out[(long long)j * n + i] = o;
+    }
+    const bool col_ok = i - H >= 0 && i + H < n;
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int j = r0 + rg + 4 * u;
+        if (i < n && j < n)
+            out[(long long)j * n + i] = (col_ok && j - H >= 0 && j + H < n) ? (float)acc[u] * scale
+                                                                            : __int_as_float(0x7fc00000);
     }
 }
 
@@ -231,18 +292,24 @@ __global__ void __launch_bounds__(256) k_disc_tiled(const unsigned *cin, float *
     for (int k = threadIdx.x; k < 2 * H + 1; k += blockDim.x) sp[k] = span[k];
     const int cols = (n + kDiscTileW - 1) / kDiscTileW, rows = (n + kDiscTileH - 1) / kDiscTileH;
     const long long tiles = (long long)cols * rows;
-    const unsigned small_count = (unsigned)(0xffffffffull / (unsigned long long)(2 * H + 1));
+    const unsigned long long taps1 = (unsigned long long)(2 * H + 1);
+    const unsigned small_span = (unsigned)(0xffffffffull / taps1);             // span sums below 2^32
+    const unsigned small_disc = (unsigned)(0xffffffffull / (taps1 * taps1));   // disc sums below 2^32
     for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
         const int c0 = (int)(t % cols) * kDiscTileW, r0 = (int)(t / cols) * kDiscTileH;
         __syncthreads();
-        const int large = disc_prefix_rows<unsigned>(cin, n, r0, c0, H, W, pre32, small_count);
-        if (!__syncthreads_or(large)) {
-            disc_outputs<unsigned>(pre32, sp, out, n, r0, c0, H, W, scale);
+        unsigned maxc = 0;
+        disc_prefix_rows<unsigned>(cin, n, r0, c0, H, W, pre32, maxc);
+        const bool not_disc32 = __syncthreads_or(maxc >= small_disc), not_span32 = __syncthreads_or(maxc >= small_span);
+        if (!not_disc32) {
+            disc_outputs<unsigned, unsigned>(pre32, sp, out, n, r0, c0, H, W, scale);
+        } else if (!not_span32) {
+            disc_outputs<unsigned, unsigned long long>(pre32, sp, out, n, r0, c0, H, W, scale);
         } else {                                           // a count of 2^32 / (2H + 1) or more: 64 bits
             __syncthreads();
-            disc_prefix_rows<unsigned long long>(cin, n, r0, c0, H, W, pre64, small_count);
+            disc_prefix_rows<unsigned long long>(cin, n, r0, c0, H, W, pre64, maxc);
             __syncthreads();
-            disc_outputs<unsigned long long>(pre64, sp, out, n, r0, c0, H, W, scale);
+            disc_outputs<unsigned long long, unsigned long long>(pre64, sp, out, n, r0, c0, H, W, scale);
         }
     }
 }
@@ -288,7 +355,7 @@ int convolve(mm_ctx *ctx, const MapObj &M, int profile, double size_re, float *d
         if ((e = cudaMemcpyAsync(dg, g.data(), g.size() * sizeof(float), cudaMemcpyHostToDevice, s)) == cudaSuccess) {
             const size_t srow = gauss_row_smem(h), scol = gauss_col_smem(h);
             if (srow <= kTileSmemMax)
-                k_gauss_rows<true><<<grid, kGaussRowThreads, srow, s>>>(M.counts, nullptr, tmp, n, dg, h, inv_nrays);
+                k_gauss_rows<true><<<grid, 256, srow, s>>>(M.counts, nullptr, tmp, n, dg, h, inv_nrays);
             else
                 k_gauss_pass<true><<<grid, 256, 0, s>>>(M.counts, nullptr, tmp, n, dg, h, 0, inv_nrays);
             if (scol <= kTileSmemMax)

@@ -23,8 +23,8 @@
 namespace mm {
 namespace {
 
-// Shared-memory histograms: up to 96 KB per CTA (12288 bins per map); 200 KB of an SM's
-// shared memory shared between the CTAs of a launch.
+// Shared-memory histograms: up to 96 KB per CTA (8 warp copies of 1024 bins per map, 64 KB);
+// 200 KB of an SM's shared memory shared between the CTAs of a launch.
 constexpr size_t kHistSmemMax = 96 * 1024;
 constexpr size_t kSmemPerSm = 200 * 1024;
 
@@ -114,19 +114,22 @@ __device__ __forceinline__ void hist_add(unsigned *h, unsigned key, unsigned lan
 //                         = -2.5 (ta[N_a] - tb[N_b]),
 // the difference and its square in float-float (about 1e-14 relative), summed per thread in
 // float-float and then in FP64; and the two count histograms (bins 0 .. nbins - 1,
-// nbins = largest count + 1), kept per CTA in shared memory when SHARED and added to ha / hb.
-template <bool SHARED>
+// nbins = largest count + 1) added to ha / hb. Each warp keeps its own copy of the bins below
+// wb = min(nbins, kWarpBins) in shared memory and adds to it with plain shared-memory atomics:
+// only the lanes of one warp can collide on a bin, so no merging of equal keys is needed for the
+// common small counts. The rare larger counts go to the global histograms, merged per warp.
+constexpr int kWarpBins = 1024;
+
 __global__ void __launch_bounds__(256) k_rms_hist(const unsigned *a, const unsigned *b, long long n, const float2 *ta,
                                                   const float2 *tb, long long nbins, unsigned *ha, unsigned *hb,
                                                   StatSums *out)
 {
-    extern __shared__ unsigned sh[];                          // SHARED: [2 nbins]
-    unsigned *const sa = SHARED ? sh : ha, *const sb = SHARED ? sh + nbins : hb;
-    if (SHARED) {
-        for (long long k = threadIdx.x; k < 2 * nbins; k += blockDim.x) sh[k] = 0u;
-        __syncthreads();
-    }
-    const unsigned lane = threadIdx.x & 31;
+    extern __shared__ unsigned sh[];                          // [8 warps][2 maps][wb]
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long wb = min(nbins, (long long)kWarpBins);
+    unsigned *const sa = sh + warp * 2 * wb, *const sb = sa + wb;
+    for (long long k = threadIdx.x; k < 16 * wb; k += blockDim.x) sh[k] = 0u;
+    __syncthreads();
     float qh = 0.f, ql = 0.f;                                 // float-float sum of (Delta m_a - Delta m_b)^2 / 6.25
     unsigned long long both = 0;
     // warp-uniform trip count: the lanes of a warp take consecutive pixels, those past n hold no key
@@ -147,8 +150,11 @@ __global__ void __launch_bounds__(256) k_rms_hist(const unsigned *a, const unsig
             ff_accumulate(qh, ql, ph, pl);
             both += 1;
         }
-        hist_add(sa, na, lane);
-        hist_add(sb, nb, lane);
+        if (in && na < (unsigned)wb) atomicAdd(sa + na, 1u);
+        if (in && nb < (unsigned)wb) atomicAdd(sb + nb, 1u);
+        const bool big_a = in && na >= (unsigned)wb, big_b = in && nb >= (unsigned)wb;
+        if (__any_sync(0xffffffffu, big_a)) hist_add(ha, big_a ? na : kNoKey, lane);
+        if (__any_sync(0xffffffffu, big_b)) hist_add(hb, big_b ? nb : kNoKey, lane);
     }
     double sq = 6.25 * ((double)qh + (double)ql);              // Delta m differences carry the factor -2.5
     for (int o = 16; o > 0; o >>= 1) {
@@ -159,10 +165,11 @@ __global__ void __launch_bounds__(256) k_rms_hist(const unsigned *a, const unsig
         atomicAdd(&out->sum_sq, sq);
         atomicAdd(&out->n_both, both);
     }
-    if (SHARED) {
-        __syncthreads();
-        for (long long k = threadIdx.x; k < 2 * nbins; k += blockDim.x)
-            if (sh[k]) atomicAdd(k < nbins ? ha + k : hb + (k - nbins), sh[k]);
+    __syncthreads();
+    for (long long k = threadIdx.x; k < 2 * wb; k += blockDim.x) {   // the 8 warp copies of each bin
+        unsigned v = 0;
+        for (int q = 0; q < 8; ++q) v += sh[q * 2 * wb + k];
+        if (v) atomicAdd(k < wb ? ha + k : hb + (k - wb), v);
     }
 }
 
@@ -303,17 +310,16 @@ extern "C" int mm_map_compare(mm_ctx *ctx, mm_map a, mm_map b, mm_compare *out)
     const double lra = std::log10(A->p.nrays_per_pix), lrb = std::log10(B->p.nrays_per_pix);
     k_log_table<<<std::max(1, std::min(ctx->sms, (int)((nbins + 255) / 256))), 256, 0, s>>>(nbins, lra, lrb, tab,
                                                                                            tab + nbins);
-    const size_t smem = (size_t)(2 * nbins) * sizeof(unsigned);
-    if (smem <= kHistSmemMax) {                                // histograms per CTA in shared memory
-        if ((e = cudaFuncSetAttribute(k_rms_hist<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)kHistSmemMax)) != cudaSuccess)
-            return cuda_fail(e, "k_rms_hist shared memory");
+    // histograms: per warp in shared memory (the bins below kWarpBins), so that the common small
+    // counts need no merging of equal keys; the few larger counts go to the global histograms
+    const size_t smem = (size_t)16 * (size_t)std::min<long long>(nbins, kWarpBins) * sizeof(unsigned);
+    if ((e = cudaFuncSetAttribute(k_rms_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kHistSmemMax)) != cudaSuccess)
+        return cuda_fail(e, "k_rms_hist shared memory");
+    {
         const int per_sm = std::max(1, std::min(4, (int)(kSmemPerSm / std::max<size_t>(smem, 1))));
-        k_rms_hist<true><<<std::max(1, std::min(per_sm * ctx->sms, (int)((n + 255) / 256))), 256, smem, s>>>(
+        k_rms_hist<<<std::max(1, std::min(per_sm * ctx->sms, (int)((n + 255) / 256))), 256, smem, s>>>(
             A->counts, B->counts, n, tab, tab + nbins, nbins, hist, hist + nbins, d_sum);
-    } else {
-        k_rms_hist<false><<<grid, 256, 0, s>>>(A->counts, B->counts, n, tab, tab + nbins, nbins, hist, hist + nbins,
-                                               d_sum);
     }
     k_scan<<<1, 1024, 0, s>>>(hist, hist + nbins, nbins, cum, cum + nbins);
     const int egrid = std::max(1, std::min(4 * ctx->sms, (int)((2 * nbins + 255) / 256)));

@@ -57,8 +57,9 @@ def test_profile_wider_than_map_rejected(shot):
 
 
 # Wide supports: the tiled kernels stage a support in 48 KB of shared memory (the Gaussian's
-# column pass up to a half-width of 155 pixels, the disc up to a radius of 15 pixels); wider
-# ones run the untiled kernels. Sizes on both sides of each limit, on a 320^2 map.
+# row pass up to a half-width of 123 pixels and its column pass up to 124, the disc up to a
+# radius of 15 pixels); wider ones run the untiled kernels. Sizes on both sides of each limit,
+# on a 320^2 map.
 CFG_WIDE = dict(CFG, npix_side=320, side=7.5)            # pixel 0.0234375 R_E
 
 
@@ -76,7 +77,7 @@ def shot_wide():
 
 
 @pytest.mark.parametrize("profile,size,half_width", [
-    (mm.MM_PROFILE_GAUSSIAN, 0.905, 155), (mm.MM_PROFILE_GAUSSIAN, 0.93, 159),
+    (mm.MM_PROFILE_GAUSSIAN, 0.7177734375, 123), (mm.MM_PROFILE_GAUSSIAN, 0.7294921875, 125),
     (mm.MM_PROFILE_DISC, 0.3633, 15), (mm.MM_PROFILE_DISC, 0.5039, 21)])
 def test_wide_supports_match_oracle(shot_wide, profile, size, half_width):
     ctx, m, counts = shot_wide
@@ -92,11 +93,12 @@ def test_wide_supports_match_oracle(shot_wide, profile, size, half_width):
 
 
 def test_disc_tiles_with_large_counts_use_64_bit_sums():
-    """The tiled disc kernel sums each tile's rows in 32 bits unless a count of the tile reaches
-    2^32 / (2H + 1), when the tile is summed again in 64 bits. A seeded synthetic map (put on the
-    device by mm_map_restore) with a few pixels above that bound in one corner, convolved with a disc of
-    radius 8 pixels (under the tiled limit of 15), has tiles of both kinds in one launch; all match
-    the oracle."""
+    """The tiled disc kernel takes each tile's row prefix sums in 32 bits and adds an output's spans
+    in 32 bits while every count of the tile is below 2^32 / (2H + 1)^2, in 64 bits while below
+    2^32 / (2H + 1), and otherwise stages the tile again as 64-bit prefix sums. A seeded synthetic
+    map (put on the device by mm_map_restore) with a few pixels above each bound, convolved with a
+    disc of radius 8 pixels (under the tiled limit of 15), has tiles of all three kinds in one
+    launch; all match the oracle."""
     mm.build()
     c = mm.mm_init(0)
     try:
@@ -105,7 +107,8 @@ def test_disc_tiles_with_large_counts_use_64_bit_sums():
         size = 8.5 * pix                                   # H = 8: bound 2^32 / 17 = 252645135
         rng = np.random.default_rng(5)
         counts = rng.poisson(1000.0, (n, n)).astype(np.uint32)
-        counts[10:14, 20:22] = np.uint32(300_000_000)      # 8 pixels above the bound
+        counts[10:14, 20:22] = np.uint32(300_000_000)      # 8 pixels above the bound: 64-bit prefix sums
+        counts[200:202, 150:152] = np.uint32(50_000_000)   # above 2^32 / 17^2: 32-bit spans added in 64 bits
         p = mm.params(sigma=0.4, gamma=0.0, smooth_frac=1.0, side=side, npix_side=n, nrays=nrays)
         g = mm.mm_geometry_of(p)
         tot = int(counts.sum(dtype=np.int64))

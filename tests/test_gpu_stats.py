@@ -22,19 +22,39 @@ def ctx():
     mm.mm_destroy(c)
 
 
-# The device builds the count histograms per CTA in shared memory up to 12288 bins (the
-# largest count + 1) and in global memory beyond; the second case has counts above that.
-@pytest.mark.parametrize("npix,nrays_a,nrays_b,shared_hist", [(256, 64.0, 25.0, True), (64, 4000.0, 1000.0, False)])
-def test_compare_matches_oracle_statistics(ctx, npix, nrays_a, nrays_b, shared_hist):
-    cfg = dict(CFG, npix_side=npix, nrays=nrays_a)
-    n, r = field.nstar_rule(cfg["sigma"], cfg["gamma"], cfg["smooth_frac"], cfg["side"])
-    f = synth.lens_field(n, r, 31)
-    lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
-    a = mm.mm_shoot(ctx, lh, mm.params(**cfg))
-    b = mm.mm_shoot(ctx, lh, mm.params(**dict(cfg, nrays=nrays_b)))     # a noisier map of the same field
-    ca, _ = mm.mm_map_fetch(ctx, a)
-    cb, _ = mm.mm_map_fetch(ctx, b)
-    assert (max(int(ca.max()), int(cb.max())) + 1 <= 12288) == shared_hist
+def restore_counts(ctx, counts, nrays, side=6.0):
+    """A map on the device holding the given host counts (mm_map_restore of a lens-free map whose
+    totals are the counts' sum): seeded synthetic input for the downstream kernels."""
+    n = counts.shape[0]
+    # sigma = 0.9, gamma = 0.05: a ray grid 300 N_side^2 N_rays large, room for any test's counts
+    p = mm.params(sigma=0.9, gamma=0.05, smooth_frac=1.0, side=side, npix_side=n, nrays=nrays)
+    g = mm.mm_geometry_of(p)
+    tot = int(counts.sum(dtype=np.int64))
+    assert tot <= g["nx"] * g["ny"]
+    st = dict(rays_shot=tot, rays_in=tot, rays_out=0, interactions=0, nx=g["nx"], ny=g["ny"], nstar=0, seconds=0.0,
+              mu_mean=0.0, lens_splits=1, far_bound=0.0, far_block=0)
+    return mm.mm_map_restore(ctx, 0, p, counts, st)
+
+
+# The device keeps per-warp histograms of the counts below 1024 in shared memory and sends larger
+# counts to global histograms. Seeded synthetic count maps (put on the device by mm_map_restore, as
+# restore_counts below) cover both: the first has only small counts, the second a long tail of
+# counts up to about 10^5, and both have empty pixels and different N_rays.
+@pytest.mark.parametrize("nside,tail", [(256, False), (192, True)])
+def test_compare_matches_oracle_statistics(ctx, nside, tail):
+    rng = np.random.default_rng(nside)
+    mu = rng.lognormal(0.0, 0.6, (nside, nside))
+    if tail:
+        mu[rng.random((nside, nside)) < 0.02] *= 300.0
+    nrays_a, nrays_b = 64.0, 25.0
+    ca = rng.poisson(mu * nrays_a).astype(np.uint32)
+    cb = rng.poisson(mu * nrays_b * rng.lognormal(0.0, 0.05, mu.shape)).astype(np.uint32)   # a noisier map
+    ca.ravel()[rng.integers(0, nside * nside, 5)] = 0                                        # empty pixels
+    cb.ravel()[rng.integers(0, nside * nside, 9)] = 0
+    assert (int(max(ca.max(), cb.max())) >= 1024) == tail
+    assert (ca == 0).any() and (cb == 0).any()
+    a = restore_counts(ctx, ca, nrays_a)
+    b = restore_counts(ctx, cb, nrays_b)
     got = mm.mm_map_compare(ctx, a, b)
     ref = ostats.compare(ca, nrays_a, cb, nrays_b)
     print(got, ref)
@@ -63,19 +83,6 @@ def test_fp32_and_fp64_maps_agree_excellently(ctx):
     assert r["rms_dm"] < 1e-3           # in fact only a few rays per million differ
     for m in (a, b):
         mm.mm_release_map(ctx, m)
-
-
-def restore_counts(ctx, counts, nrays, side=6.0):
-    """A map on the device holding the given host counts (mm_map_restore of a lens-free map whose
-    totals are the counts' sum): seeded synthetic input for the downstream kernels."""
-    n = counts.shape[0]
-    p = mm.params(sigma=0.45, gamma=0.2, smooth_frac=1.0, side=side, npix_side=n, nrays=nrays)
-    g = mm.mm_geometry_of(p)
-    tot = int(counts.sum(dtype=np.int64))
-    assert tot <= g["nx"] * g["ny"]
-    st = dict(rays_shot=tot, rays_in=tot, rays_out=0, interactions=0, nx=g["nx"], ny=g["ny"], nstar=0, seconds=0.0,
-              mu_mean=0.0, lens_splits=1, far_bound=0.0, far_block=0)
-    return mm.mm_map_restore(ctx, 0, p, counts, st)
 
 
 @pytest.mark.parametrize("nside,lam", [(129, 3.0), (256, 400.0)])
