@@ -38,7 +38,8 @@ class _Params(C.Structure):
 
 
 class _Far(C.Structure):
-    _fields_ = [("order", C.c_int32), ("ratio", C.c_double), ("block_tiles", C.c_int32)]
+    _fields_ = [("order", C.c_int32), ("ratio", C.c_double), ("block_tiles", C.c_int32),
+                ("group_order", C.c_int32), ("group_theta", C.c_double), ("group_leaf", C.c_int32)]
 
 
 class _Geom(C.Structure):
@@ -140,12 +141,16 @@ def shoot_rays(p, field, ray_i, ray_j, threads: int = 0):
 
 
 def _far(far) -> _Far:
-    return _Far(int(far["order"]), float(far["ratio"]), int(far["block_tiles"]))
+    """far = {order P, ratio q, block_tiles bt} and, for grouped far lenses, group_order K (0: none),
+    group_theta and group_leaf."""
+    return _Far(int(far["order"]), float(far["ratio"]), int(far["block_tiles"]), int(far.get("group_order", 0)),
+                float(far.get("group_theta", 0.5)), int(far.get("group_leaf", 64)))
 
 
 def far_map(p, field, far, rect=None, threads: int = 0):
     """Far-field approximation of the map (the tree code's idea on blocks of rays, Sect. 2.1,
-    Eq. hierarchical): far = {order P, ratio q, block_tiles bt}. Returns counts [N_side, N_side],
+    Eq. hierarchical): far = {order P, ratio q, block_tiles bt}, plus group_order K, group_theta and
+    group_leaf to group distant lenses by cells of a lens tree. Returns counts [N_side, N_side],
     totals {shot, in, out} and the largest truncation bound of any block."""
     x, y, m = _lens_arrays(field)
     n = int(p["npix_side"] if isinstance(p, dict) else p.npix_side)

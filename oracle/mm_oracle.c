@@ -215,74 +215,332 @@ int orc_rays(const orc_params *P, const double *lx, const double *ly, const doub
  * P = 1 keeps only c_0: the far lenses' deflection at the test ray, unchanged
  * across the block. A ratio q so small that every lens is near gives the
  * direct sum of Eq. sigma back, bit for bit.
+ *
+ * Grouped far lenses (group_order K > 0): the tree code also groups distant
+ * lenses into cells of a tree and lets each cell act through its multipole
+ * moments. The statement used here:
+ *
+ *   - Lens tree. R0 is the smallest power of two above every |x_i| and |y_i|.
+ *     Level L cuts the square [-R0, R0)^2 into 2^L x 2^L cells of side
+ *     s_L = 2 R0 / 2^L; lens i lies in cell (floor((x_i + R0) / s_L),
+ *     floor((y_i + R0) / s_L)) (each index capped at 2^L - 1). The root is the
+ *     level-0 cell; a cell with more than group_leaf lenses, below level 16, has
+ *     its non-empty sub-cells of the next level as children; other cells are
+ *     leaves. A cell C has centre z_C (the square's centre), half-diagonal
+ *     r_C = s_L / sqrt(2), and moments a_k = sum_{i in C} m_i (z_i - z_C)^k,
+ *     k < K.
+ *   - Grouping. For block B, a cell C with D = z_C - z_B is grouped when
+ *     |D| - r_C >= rho / q (every lens of C is far) and rho + r_C <= theta |D|.
+ *     The tree is walked from the root: a grouped cell adds
+ *     c_l += -sum_{k<K} (-1)^k C(l+k, k) a_k / D^(l+k+1)
+ *     (the series of 1 / (D + e)^(l+1) in e = z_i - z_C, term by term, summed
+ *     over the cell's lenses); a leaf that is not grouped adds its lenses one
+ *     by one (near or far, as above); any other cell passes to its children.
+ *     The near lenses are therefore the same as without grouping.
+ *   - Bound. For a lens of a grouped cell, the double series of
+ *     1 / (w - D - e) in w and e has terms bounded by C(l+k, k) x^l y^k / |D|,
+ *     x = |w| / |D|, y = |e| / |D| <= r_C / |D|, x + y < 1. The terms kept are
+ *     l < P, k < K, so the cell adds at most
+ *     (M_C / |D|) E(x, y), M_C = sum of its masses,
+ *     E = (x / (1 - y))^P / (1 - x - y) + sum_{l<P} x^l sum_{k>=K} C(l+k, k) y^k,
+ *     to the bound of the lenses taken one by one.
  * ======================================================================== */
+
+#define TREE_LMAX 16
+
+typedef struct {
+    int level;
+    double xc, yc;          /* cell centre z_C */
+    double rc;              /* half-diagonal r_C */
+    int64_t n;              /* lenses in the cell */
+    int64_t *idx;           /* their indices, ascending */
+    int child[4], nchild;   /* non-empty sub-cells; a leaf has none */
+    double mass;            /* M_C */
+    double complex *a;      /* [K] moments */
+} tree_node;
+
+typedef struct {
+    tree_node *nodes;
+    int nn, cap;
+    double r0;
+    int K;
+} lens_tree;
 
 typedef struct {
     double xb, yb;          /* block centre z_B */
     double rho;             /* block radius */
     int64_t nnear;
     int64_t *near;          /* near lens indices, ascending */
-    char *is_near;          /* [nstar] */
+    int64_t nfar;
+    int64_t *far;           /* lenses in the series one by one, ascending */
+    int nacc;
+    double *acc;            /* grouped cells: (M_C, |D|, r_C) triples */
     double complex *c;      /* [P] far-series coefficients */
 } far_block;
 
 static int far_params_ok(const orc_far_params *F)
 {
-    return F && F->order >= 1 && F->order <= 64 && F->ratio > 0.0 && F->ratio < 1.0 && F->block_tiles >= 1;
+    if (!F || F->order < 1 || F->order > 64 || !(F->ratio > 0.0) || !(F->ratio < 1.0) || F->block_tiles < 1)
+        return 0;
+    if (F->group_order < 0 || F->group_order > 64) return 0;
+    if (F->group_order > 0 && (!(F->group_theta > 0.0) || !(F->group_theta < 1.0) || F->group_leaf < 1)) return 0;
+    return 1;
 }
 
 static void far_block_free(far_block *B)
 {
     free(B->near);
-    free(B->is_near);
+    free(B->far);
+    free(B->acc);
     free(B->c);
 }
 
+/* Smallest power of two above every |x_i| and |y_i| (1 for no lenses or all at the origin). */
+static double tree_root_half(const double *lx, const double *ly, int64_t n)
+{
+    double m = 0.0;
+    for (int64_t i = 0; i < n; ++i) m = fmax(m, fmax(fabs(lx[i]), fabs(ly[i])));
+    if (m == 0.0) return 1.0;
+    int e;
+    frexp(m, &e);                    /* m = f 2^e, 1/2 <= f < 1 */
+    return ldexp(1.0, e);
+}
+
+/* Cell index of coordinate v at level L (cells of side s from -R0). */
+static int64_t cell_index(double v, double r0, double s, int level)
+{
+    int64_t c = (int64_t)floor((v + r0) / s);
+    const int64_t top = ((int64_t)1 << level) - 1;
+    return c < 0 ? 0 : (c > top ? top : c);
+}
+
+static void tree_free(lens_tree *T)
+{
+    for (int k = 0; k < T->nn; ++k) {
+        free(T->nodes[k].idx);
+        free(T->nodes[k].a);
+    }
+    free(T->nodes);
+    T->nodes = NULL;
+    T->nn = T->cap = 0;
+}
+
+/* Add the cell (level, ix, iy) holding lenses idx[0..n) (ascending, taken over by the
+ * node) and its subtree; returns its node index, or -1 when memory runs out. */
+static int tree_add(lens_tree *T, int level, int64_t ix, int64_t iy, int64_t *idx, int64_t n, const double *lx,
+                    const double *ly, const double *lm, int leaf)
+{
+    if (T->nn == T->cap) {
+        const int cap = T->cap ? 2 * T->cap : 64;
+        tree_node *p = (tree_node *)realloc(T->nodes, (size_t)cap * sizeof(tree_node));
+        if (!p) { free(idx); return -1; }
+        T->nodes = p;
+        T->cap = cap;
+    }
+    const int me = T->nn++;
+    tree_node *N = &T->nodes[me];
+    memset(N, 0, sizeof(*N));
+    const double s = ldexp(T->r0, 1 - level);
+    N->level = level;
+    N->xc = -T->r0 + ((double)ix + 0.5) * s;
+    N->yc = -T->r0 + ((double)iy + 0.5) * s;
+    N->rc = s * 0.70710678118654752440;
+    N->n = n;
+    N->idx = idx;
+    N->a = (double complex *)calloc((size_t)T->K, sizeof(double complex));
+    if (!N->a) return -1;
+    for (int64_t q = 0; q < n; ++q) {
+        const int64_t i = idx[q];
+        const double complex e = (lx[i] - N->xc) + I * (ly[i] - N->yc);
+        double complex pw = 1.0;
+        N->mass += lm[i];
+        for (int k = 0; k < T->K; ++k) {
+            N->a[k] += lm[i] * pw;
+            pw *= e;
+        }
+    }
+    if (n <= leaf || level >= TREE_LMAX) return me;
+    /* children: the sub-cells of level + 1, in the order (0,0), (1,0), (0,1), (1,1) */
+    const double sc = ldexp(T->r0, -level);
+    int64_t *part[4];
+    int64_t cnt[4] = {0, 0, 0, 0};
+    for (int q = 0; q < 4; ++q) {
+        part[q] = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+        if (!part[q]) { for (int r = 0; r < q; ++r) free(part[r]); return -1; }
+    }
+    for (int64_t q = 0; q < n; ++q) {
+        const int64_t i = idx[q];
+        const int64_t cx = cell_index(lx[i], T->r0, sc, level + 1) - 2 * ix;
+        const int64_t cy = cell_index(ly[i], T->r0, sc, level + 1) - 2 * iy;
+        const int k = (int)(cy * 2 + cx);
+        part[k][cnt[k]++] = i;
+    }
+    for (int q = 0; q < 4; ++q) {
+        if (cnt[q] == 0) { free(part[q]); continue; }
+        const int ch = tree_add(T, level + 1, 2 * ix + (q & 1), 2 * iy + (q >> 1), part[q], cnt[q], lx, ly, lm, leaf);
+        if (ch < 0) { for (int r = q + 1; r < 4; ++r) free(part[r]); return -1; }
+        N = &T->nodes[me];                  /* the node array may have moved */
+        N->child[N->nchild++] = ch;
+    }
+    return me;
+}
+
+static int tree_build(lens_tree *T, const orc_far_params *F, const double *lx, const double *ly, const double *lm,
+                      int64_t nstar)
+{
+    memset(T, 0, sizeof(*T));
+    T->K = F->group_order;
+    if (T->K == 0 || nstar == 0) return 0;
+    T->r0 = tree_root_half(lx, ly, nstar);
+    int64_t *all = (int64_t *)malloc((size_t)nstar * sizeof(int64_t));
+    if (!all) return -1;
+    for (int64_t i = 0; i < nstar; ++i) all[i] = i;
+    return tree_add(T, 0, 0, 0, all, nstar, lx, ly, lm, F->group_leaf) < 0 ? -1 : 0;
+}
+
+/* Lens at offset (d1, d2) from a block centre is near iff |d|^2 < (rho / q)^2. */
+static int is_near(double d1, double d2, double rn)
+{
+    return d1 * d1 + d2 * d2 < rn * rn;
+}
+
+static int cmp_i64(const void *p, const void *q)
+{
+    const int64_t a = *(const int64_t *)p, b = *(const int64_t *)q;
+    return (a > b) - (a < b);
+}
+
+/* Walk the tree for block B: grouped cells go to B->acc (and their series into c),
+ * lenses of the other leaves to the near or the one-by-one list. */
+static void tree_visit(const lens_tree *T, int k, const orc_far_params *F, const double *lx, const double *ly,
+                       double rn, far_block *B, double complex *cg, const double *binom)
+{
+    const tree_node *N = &T->nodes[k];
+    const double complex D = (N->xc - B->xb) + I * (N->yc - B->yb);
+    const double dabs = cabs(D);
+    if (dabs - N->rc >= rn && B->rho + N->rc <= F->group_theta * dabs) {
+        const int P = F->order, K = T->K;
+        const double complex u = 1.0 / D;
+        double complex up[130];              /* u^j, j <= P + K */
+        up[0] = 1.0;
+        for (int j = 1; j <= P + K; ++j) up[j] = up[j - 1] * u;
+        for (int l = 0; l < P; ++l)
+            for (int q = 0; q < K; ++q) {
+                const double sg = (q & 1) ? 1.0 : -1.0;           /* -(-1)^q */
+                cg[l] += sg * binom[(l + q) * 130 + q] * N->a[q] * up[l + q + 1];
+            }
+        B->acc[3 * B->nacc] = N->mass;
+        B->acc[3 * B->nacc + 1] = dabs;
+        B->acc[3 * B->nacc + 2] = N->rc;
+        B->nacc++;
+        return;
+    }
+    if (N->nchild == 0) {
+        for (int64_t q = 0; q < N->n; ++q) {
+            const int64_t i = N->idx[q];
+            if (is_near(lx[i] - B->xb, ly[i] - B->yb, rn)) B->near[B->nnear++] = i;
+            else B->far[B->nfar++] = i;
+        }
+        return;
+    }
+    for (int q = 0; q < N->nchild; ++q) tree_visit(T, N->child[q], F, lx, ly, rn, B, cg, binom);
+}
+
+/* Pascal's triangle C(n, k), n, k < 130, row-major [n * 130 + k]. */
+static double *binom_table(void)
+{
+    double *b = (double *)calloc(130 * 130, sizeof(double));
+    if (!b) return NULL;
+    for (int n = 0; n < 130; ++n) {
+        b[n * 130] = 1.0;
+        for (int k = 1; k <= n; ++k) b[n * 130 + k] = b[(n - 1) * 130 + k - 1] + (k < n ? b[(n - 1) * 130 + k] : 0.0);
+    }
+    return b;
+}
+
 /* Block (BX, BY) of the rectangle with origin (i0, j0): centre, near list and series. */
-static int far_block_build(const orc_far_params *F, const orc_geometry_t *G, const double *lx, const double *ly,
-                           const double *lm, int64_t nstar, int64_t i0, int64_t j0, int64_t BX, int64_t BY,
-                           far_block *B)
+static int far_block_build(const orc_far_params *F, const orc_geometry_t *G, const lens_tree *T, const double *binom,
+                           const double *lx, const double *ly, const double *lm, int64_t nstar, int64_t i0,
+                           int64_t j0, int64_t BX, int64_t BY, far_block *B)
 {
     const int64_t bw = 64 * (int64_t)F->block_tiles, bh = 32 * (int64_t)F->block_tiles;
+    memset(B, 0, sizeof(*B));
     B->xb = ((double)(i0 + BX * bw + bw / 2) - 0.5 * (double)G->nx) * G->delta;
     B->yb = ((double)(j0 + BY * bh + bh / 2) - 0.5 * (double)G->ny) * G->delta;
     B->rho = G->delta * sqrt((double)(bw / 2) * (double)(bw / 2) + (double)(bh / 2) * (double)(bh / 2));
     const double rn = B->rho / F->ratio;
-    B->nnear = 0;
-    B->near = (int64_t *)malloc((size_t)(nstar > 0 ? nstar : 1) * sizeof(int64_t));
-    B->is_near = (char *)calloc((size_t)(nstar > 0 ? nstar : 1), 1);
+    const size_t cap = (size_t)(nstar > 0 ? nstar : 1);
+    B->near = (int64_t *)malloc(cap * sizeof(int64_t));
+    B->far = (int64_t *)malloc(cap * sizeof(int64_t));
+    B->acc = (double *)malloc((size_t)(T->nn > 0 ? T->nn : 1) * 3 * sizeof(double));
     B->c = (double complex *)calloc((size_t)F->order, sizeof(double complex));
-    if (!B->near || !B->is_near || !B->c) {
+    double complex *cg = (double complex *)calloc((size_t)F->order, sizeof(double complex));
+    if (!B->near || !B->far || !B->acc || !B->c || !cg) {
+        free(cg);
         far_block_free(B);
         return -1;
     }
-    for (int64_t i = 0; i < nstar; ++i) {
-        const double d1 = lx[i] - B->xb, d2 = ly[i] - B->yb;
-        if (d1 * d1 + d2 * d2 < rn * rn) {
-            B->near[B->nnear++] = i;
-            B->is_near[i] = 1;
-            continue;
+    if (T->nn > 0) {
+        tree_visit(T, 0, F, lx, ly, rn, B, cg, binom);
+        qsort(B->near, (size_t)B->nnear, sizeof(int64_t), cmp_i64);
+        qsort(B->far, (size_t)B->nfar, sizeof(int64_t), cmp_i64);
+    } else {
+        for (int64_t i = 0; i < nstar; ++i) {
+            if (is_near(lx[i] - B->xb, ly[i] - B->yb, rn)) B->near[B->nnear++] = i;
+            else B->far[B->nfar++] = i;
         }
-        const double complex u = 1.0 / (d1 + I * d2);           /* 1 / d_i */
+    }
+    /* lenses one by one, in index order, then the grouped cells */
+    for (int64_t q = 0; q < B->nfar; ++q) {
+        const int64_t i = B->far[q];
+        const double complex u = 1.0 / ((lx[i] - B->xb) + I * (ly[i] - B->yb));   /* 1 / d_i */
         double complex t = -lm[i] * u;                          /* -m_i / d_i^(l+1) for l = 0 */
         for (int l = 0; l < F->order; ++l) {
             B->c[l] += t;
             t *= u;
         }
     }
+    for (int l = 0; l < F->order; ++l) B->c[l] += cg[l];
+    free(cg);
     return 0;
 }
 
+/* sum_{k>=K} C(l+k, k) y^k, summed term by term; the terms beyond the last one kept
+ * fall off faster than a geometric series of the last ratio, which bounds them. */
+static double binom_tail(int l, int K, double y, const double *binom)
+{
+    double term = binom[(l + K) * 130 + K] * pow(y, K);
+    double sum = 0.0;
+    for (int k = K; k < K + 100000; ++k) {
+        sum += term;
+        const double r = y * (double)(l + k + 1) / (double)(k + 1);       /* term(k+1) / term(k) */
+        term *= r;
+        if (r < 1.0 && term / (1.0 - r) <= 1e-17 * sum) return sum + term / (1.0 - r);
+    }
+    return INFINITY;
+}
+
 /* Truncation bound at offset |w| from the block centre. */
-static double far_bound(const far_block *B, const orc_far_params *F, const double *lx, const double *ly,
-                        const double *lm, int64_t nstar, double wabs)
+static double far_bound(const far_block *B, const orc_far_params *F, const double *binom, const double *lx,
+                        const double *ly, const double *lm, double wabs)
 {
     double b = 0.0;
-    for (int64_t i = 0; i < nstar; ++i) {
-        if (B->is_near[i]) continue;
+    for (int64_t q = 0; q < B->nfar; ++q) {
+        const int64_t i = B->far[q];
         const double d = hypot(lx[i] - B->xb, ly[i] - B->yb);
         const double t = wabs / d;
         b += lm[i] * pow(t, F->order) / (d * (1.0 - t));
+    }
+    for (int k = 0; k < B->nacc; ++k) {
+        const double mass = B->acc[3 * k], dabs = B->acc[3 * k + 1], rc = B->acc[3 * k + 2];
+        const double x = wabs / dabs, y = rc / dabs;
+        double e = pow(x / (1.0 - y), F->order) / (1.0 - x - y);
+        double xl = 1.0;
+        for (int l = 0; l < F->order; ++l) {
+            e += xl * binom_tail(l, F->group_order, y, binom);
+            xl *= x;
+        }
+        b += mass / dabs * e;
     }
     return b;
 }
@@ -317,6 +575,13 @@ int orc_far_map(const orc_params *P, const orc_far_params *F, const double *lx, 
     if (i1 > G.nx) i1 = G.nx;
     if (j1 > G.ny) j1 = G.ny;
     if (i1 < i0 || j1 < j0) return -1;
+    lens_tree T;
+    double *binom = binom_table();
+    if (!binom || tree_build(&T, F, lx, ly, lm, nstar) != 0) {
+        free(binom);
+        tree_free(&T);
+        return -1;
+    }
     const int64_t bw = 64 * (int64_t)F->block_tiles, bh = 32 * (int64_t)F->block_tiles;
     const int64_t nbx = (i1 - i0 + bw - 1) / bw, nby = (j1 - j0 + bh - 1) / bh;
     memset(counts, 0, (size_t)P->npix_side * (size_t)P->npix_side * sizeof(uint32_t));
@@ -332,11 +597,11 @@ int orc_far_map(const orc_params *P, const orc_far_params *F, const double *lx, 
     for (int64_t b = 0; b < nbx * nby; ++b) {
         const int64_t BX = b % nbx, BY = b / nbx;
         far_block B;
-        if (far_block_build(F, &G, lx, ly, lm, nstar, i0, j0, BX, BY, &B) != 0) {
+        if (far_block_build(F, &G, &T, binom, lx, ly, lm, nstar, i0, j0, BX, BY, &B) != 0) {
             err += 1;
             continue;
         }
-        const double bb = far_bound(&B, F, lx, ly, lm, nstar, B.rho);
+        const double bb = far_bound(&B, F, binom, lx, ly, lm, B.rho);
         if (bb > bmax) bmax = bb;
         const int64_t ie = i0 + (BX + 1) * bw < i1 ? i0 + (BX + 1) * bw : i1;
         const int64_t je = j0 + (BY + 1) * bh < j1 ? j0 + (BY + 1) * bh : j1;
@@ -358,6 +623,8 @@ int orc_far_map(const orc_params *P, const orc_far_params *F, const double *lx, 
         }
         far_block_free(&B);
     }
+    tree_free(&T);
+    free(binom);
     if (err) return -1;
     totals[0] = shot;
     totals[1] = in;
@@ -374,6 +641,13 @@ int orc_far_rays(const orc_params *P, const orc_far_params *F, const double *lx,
     if (orc_geometry(P, &G) != 0 || !far_params_ok(F) || n < 0 || !ray_i || !ray_j || !alpha || !ysrc || !pixel ||
         !bound || i0 < 0 || j0 < 0)
         return -1;
+    lens_tree T;
+    double *binom = binom_table();
+    if (!binom || tree_build(&T, F, lx, ly, lm, nstar) != 0) {
+        free(binom);
+        tree_free(&T);
+        return -1;
+    }
     const int64_t bw = 64 * (int64_t)F->block_tiles, bh = 32 * (int64_t)F->block_tiles;
     int err = 0;
 #ifdef _OPENMP
@@ -388,7 +662,8 @@ int orc_far_rays(const orc_params *P, const orc_far_params *F, const double *lx,
             continue;
         }
         far_block B;
-        if (far_block_build(F, &G, lx, ly, lm, nstar, i0, j0, (ray_i[k] - i0) / bw, (ray_j[k] - j0) / bh, &B) != 0) {
+        if (far_block_build(F, &G, &T, binom, lx, ly, lm, nstar, i0, j0, (ray_i[k] - i0) / bw, (ray_j[k] - j0) / bh,
+                            &B) != 0) {
             err += 1;
             continue;
         }
@@ -396,9 +671,11 @@ int orc_far_rays(const orc_params *P, const orc_far_params *F, const double *lx,
         ray_position(&G, ray_i[k], ray_j[k], &x1, &x2);
         const int on_lens = far_deflection(&B, F, lx, ly, lm, x1, x2, &a1, &a2);
         pixel[k] = source_pixel(P, &G, x1, x2, a1, a2, on_lens, alpha + 2 * k, ysrc + 2 * k);
-        bound[k] = far_bound(&B, F, lx, ly, lm, nstar, hypot(x1 - B.xb, x2 - B.yb));
+        bound[k] = far_bound(&B, F, binom, lx, ly, lm, hypot(x1 - B.xb, x2 - B.yb));
         far_block_free(&B);
     }
+    tree_free(&T);
+    free(binom);
     return err ? -1 : 0;
 }
 

@@ -40,6 +40,9 @@ typedef struct {
     int32_t order;        /* P >= 1 */
     double ratio;         /* q in (0, 1) */
     int32_t block_tiles;  /* bt >= 1: a block is 64 bt x 32 bt rays */
+    int32_t group_order;  /* K: multipole terms of a lens cell; 0: no grouping (every far lens alone) */
+    double group_theta;   /* theta in (0, 1): a cell is grouped when (rho + r_C) <= theta |z_C - z_B| */
+    int32_t group_leaf;   /* a cell of the lens tree with more lenses than this is split (>= 1) */
 } orc_far_params;
 
 /* Map of the rectangle [i0,i1) x [j0,j1) (i0 < 0: the whole grid) with the far

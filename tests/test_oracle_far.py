@@ -120,3 +120,100 @@ def test_ragged_rectangle_counts_every_ray_once():
 def test_bad_far_parameters_rejected(far):
     with pytest.raises(ValueError):
         oracle.far_map(CFG0, field0(), far)
+
+
+# ---- grouped far lenses (the tree code's cells of distant lenses, Sect. 2.1) ----
+# A field of 4000 lognormal lenses in a disc of 100 Einstein radii around a 10 x 10 R_E ray grid:
+# blocks of 2 x 2 tiles (radius 1.1 R_E) see most lenses from far away, so many cells of the lens
+# tree are grouped.
+CFG_G = dict(sigma=0.4, gamma=0.0, smooth_frac=0.0, side=4.0, npix_side=64, nrays=16.0, margin=1.5)
+FAR_G = dict(order=10, ratio=0.3, block_tiles=2)
+
+
+def field_g():
+    return synth.lens_field(4000, field.radius_for_nstar(4000, 0.4), 21, synth.MASS_LOGNORMAL)
+
+
+def rays_g(n=600, seed=1):
+    g = oracle.geometry(CFG_G)
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, g["nx"], n), rng.integers(0, g["ny"], n)
+
+
+def test_grouping_that_groups_no_cell_is_the_ungrouped_method_bit_for_bit():
+    """theta -> 0: no cell is ever far enough, every leaf gives up its lenses one by one, and the
+    near and one-by-one lists (each lens exactly once, in index order) are the ungrouped ones."""
+    f = field_g()
+    ri, rj = rays_g()
+    au, _, pu, bu = oracle.far_rays(CFG_G, f, FAR_G, ri, rj)
+    ag, _, pg, bg = oracle.far_rays(CFG_G, f, dict(FAR_G, group_order=8, group_theta=1e-9, group_leaf=3), ri, rj)
+    assert np.array_equal(au, ag) and np.array_equal(pu, pg) and np.array_equal(bu, bg)
+    mu, tu, bmu = oracle.far_map(CFG_G, f, FAR_G)
+    mg, tg, bmg = oracle.far_map(CFG_G, f, dict(FAR_G, group_order=8, group_theta=1e-9, group_leaf=3))
+    assert np.array_equal(mu, mg) and tu == tg and bmu == bmg
+
+
+def test_grouped_series_converges_to_the_ungrouped_series():
+    """With K = 64 multipole terms and theta = 0.5 the cells' expansions are exact to rounding
+    (their remainder is below 0.5^64 of a cell's pull), so grouping changes the deflection by
+    rounding only; with a monopole alone (K = 1) the same grouping visibly changes it."""
+    f = field_g()
+    ri, rj = rays_g()
+    au, _, _, _ = oracle.far_rays(CFG_G, f, FAR_G, ri, rj)
+    a64, _, _, _ = oracle.far_rays(CFG_G, f, dict(FAR_G, group_order=64, group_theta=0.5, group_leaf=16), ri, rj)
+    a1, _, _, _ = oracle.far_rays(CFG_G, f, dict(FAR_G, group_order=1, group_theta=0.5, group_leaf=16), ri, rj)
+    assert np.hypot(*(a64 - au).T).max() < 1e-12
+    assert np.hypot(*(a1 - au).T).max() > 1e-3
+    # small leaves next to a wide near disc (q = 0.1, rho / q = 11 rho): cells close to the block are
+    # grouped only when all their lenses are far, so the near lenses stay exact
+    near = dict(FAR_G, ratio=0.1)
+    au, _, _, _ = oracle.far_rays(CFG_G, f, near, ri, rj)
+    a64, _, _, _ = oracle.far_rays(CFG_G, f, dict(near, group_order=64, group_theta=0.5, group_leaf=1), ri, rj)
+    assert np.hypot(*(a64 - au).T).max() < 1e-12
+
+
+def test_grouped_error_within_its_bound_and_shrinking_with_the_order():
+    """Against the direct sum of Eq. sigma, the grouped far field's error stays within its bound
+    (series tail of the lenses taken one by one plus the double-series remainder of every grouped
+    cell) for each multipole order, and both the error and the bound fall as K grows."""
+    f = field_g()
+    ri, rj = rays_g(800, 4)
+    a0, _, _ = oracle.shoot_rays(CFG_G, f, ri, rj)
+    errs, bounds = [], []
+    for K in (2, 4, 8, 16, 64):
+        for P in (1, 2, 3, 10):
+            a, _, _, b = oracle.far_rays(CFG_G, f, dict(FAR_G, order=P, group_order=K, group_theta=0.5, group_leaf=16),
+                                         ri, rj)
+            err = np.hypot(*(a - a0).T)
+            assert np.all(err <= b * (1 + 1e-9) + 1e-12), (K, P)
+            if P == 10 and K < 64:
+                errs.append(err.max())
+                bounds.append(b.max())
+    assert all(errs[k + 1] < errs[k] for k in range(3)) and all(bounds[k + 1] < bounds[k] for k in range(3))
+    # every lens beyond rho / q in a grouped cell (q = 0.05, single-lens leaves): the bound is the
+    # cells' remainders alone, the part in w (l >= P) included
+    for P in (1, 2):
+        a, _, _, b = oracle.far_rays(CFG_G, f, dict(FAR_G, ratio=0.05, order=P, group_order=64, group_theta=0.5,
+                                                    group_leaf=1), ri, rj)
+        err = np.hypot(*(a - a0).T)
+        assert np.all(err <= b * (1 + 1e-9) + 1e-12), P
+        assert (err / b).max() > 0.01, P                       # and it is not vacuous
+
+
+def test_grouped_map_matches_the_direct_map():
+    """The default-like grouping (P = 10, K = 24, theta = 0.3) leaves the map of the exact method
+    unchanged up to a few rays, with a bound of about 1e-6 Einstein radii at this coarse block."""
+    f = field_g()
+    exact, te = oracle.shoot_map(CFG_G, f)
+    got, tg, bmax = oracle.far_map(CFG_G, f, dict(FAR_G, group_order=24, group_theta=0.3, group_leaf=32))
+    assert tg == te and bmax < 1e-5
+    assert int(np.abs(got.astype(np.int64) - exact).sum()) <= 8
+
+
+@pytest.mark.parametrize("extra", [dict(group_order=65, group_theta=0.5, group_leaf=8),
+                                   dict(group_order=8, group_theta=0.0, group_leaf=8),
+                                   dict(group_order=8, group_theta=1.0, group_leaf=8),
+                                   dict(group_order=8, group_theta=0.5, group_leaf=0)])
+def test_bad_grouping_parameters_rejected(extra):
+    with pytest.raises(ValueError):
+        oracle.far_map(CFG0, field0(), dict(order=8, ratio=0.3, block_tiles=8, **extra))

@@ -39,10 +39,20 @@ FAR_MUTATIONS = [
     ("far series power", "        t *= u;\n", "        t *= u * u;\n"),
     ("far series index shift", "f += B->c[l] * wl;", "f += B->c[l] * wl * w;"),
     ("far conjugate dropped", "*a2 = -cimag(f) + s2;", "*a2 = cimag(f) + s2;"),
-    ("near radius squared twice", "if (d1 * d1 + d2 * d2 < rn * rn) {", "if (d1 * d1 + d2 * d2 < rn) {"),
+    ("near radius squared twice", "return d1 * d1 + d2 * d2 < rn * rn;", "return d1 * d1 + d2 * d2 < rn;"),
     ("near lenses dropped", "for (int64_t k = 0; k < B->nnear; ++k)", "for (int64_t k = 0; k < 0; ++k)"),
     ("tail bound exponent", "pow(t, F->order)", "pow(t, F->order + 1)"),
     ("block radius halved", "B->rho = G->delta * sqrt(", "B->rho = 0.5 * G->delta * sqrt("),
+    # grouped far lenses: the lens tree, the cells' expansions and their bound
+    ("group binomial index", "binom[(l + q) * 130 + q]", "binom[(l + q + 1) * 130 + q]"),
+    ("group sign alternation dropped", "const double sg = (q & 1) ? 1.0 : -1.0;", "const double sg = -1.0;"),
+    ("group moments about the origin", "(lx[i] - N->xc) + I * (ly[i] - N->yc)", "lx[i] + I * ly[i]"),
+    ("group power off by one", "up[l + q + 1]", "up[l + q]"),
+    ("grouping ignores the near radius", "if (dabs - N->rc >= rn && ", "if ("),
+    ("group bound drops the l >= P tail", "double e = pow(x / (1.0 - y), F->order) / (1.0 - x - y);",
+     "double e = 0.0;"),
+    ("tree loses a lens in a split", "part[k][cnt[k]++] = i;", "if (q > 0) part[k][cnt[k]++] = i;"),
+    ("cell radius halved", "N->rc = s * 0.70710678118654752440;", "N->rc = s * 0.35355339059327376220;"),
 ]
 
 
