@@ -108,6 +108,24 @@ typedef struct {
                                 per block), from the whole ray grid, the lens count and the
                                 largest lens distance from the origin.
                                 Blocks are counted from the origin of the shot rectangle */
+    int32_t  far_group_order;/* MM_FAR32: grouped far lenses (the tree code's cells, Sect. 2.1):
+                                K multipole moments per cell of a lens quadtree, 1 .. 32 (needs
+                                far_order <= 16); 0: every far lens enters its block's series
+                                alone; -1 (default): 24 when the lens set has 32768 lenses or
+                                more, else 0. The tree: R0 = the smallest power of two above every
+                                |x_i|, |y_i|; level L cuts [-R0, R0)^2 into cells of side
+                                2 R0 / 2^L; a cell with more than far_group_leaf lenses (below
+                                level 16) splits into its four quadrants. For block B a cell C
+                                (centre z_C, half-diagonal r_C, D = z_C - z_B) is grouped when
+                                |D| - r_C >= rho / far_ratio and rho + r_C <= far_group_theta |D|;
+                                its moments a_k = sum m_i (z_i - z_C)^k then add
+                                -sum_{k<K} (-1)^k C(l+k, k) a_k / D^(l+k+1) to c_l, and its lenses
+                                are not examined one by one. The near lenses are the same as
+                                without grouping. A grouped cell adds (M_C / |D|) E(x, y) to the
+                                bound, x = rho / |D|, y = r_C / |D|,
+                                E = (x / (1 - y))^P / (1 - x - y) + sum_{l<P} x^l sum_{k>=K} C(l+k, k) y^k */
+    double   far_group_theta;/* MM_FAR32 grouping: separation theta, 0 < theta <= 0.9 (default 0.3) */
+    int32_t  far_group_leaf; /* MM_FAR32 grouping: most lenses of a leaf cell, 1 .. 2^20 (default 64) */
 } mm_params;
 
 /* Lens-field derivation used by mm_create_lenses when nstar < 0 or
@@ -133,6 +151,7 @@ typedef struct {
     double   far_bound;     /* MM_FAR32: largest truncation bound of any ray (Einstein radii,
                                evaluated at the block radius); 0 for the exact precisions */
     int32_t  far_block;     /* MM_FAR32: the block side (tiles) used; 0 for the exact precisions */
+    int32_t  far_group;     /* MM_FAR32: the multipole order K of grouped cells (0: no grouping) */
 } mm_stats;
 
 typedef struct {

@@ -55,14 +55,15 @@ class mm_params(C.Structure):
                 ("precision", C.c_int32), ("nstar", C.c_int64), ("disc_radius", C.c_double),
                 ("mass_model", C.c_int32), ("mass_mu", C.c_double), ("mass_s", C.c_double), ("seed", C.c_uint64),
                 ("ray_rect", C.c_int64 * 4), ("far_order", C.c_int32), ("far_ratio", C.c_double),
-                ("far_block", C.c_int32)]
+                ("far_block", C.c_int32), ("far_group_order", C.c_int32), ("far_group_theta", C.c_double),
+                ("far_group_leaf", C.c_int32)]
 
 
 class mm_stats(C.Structure):
     _fields_ = [("rays_shot", C.c_uint64), ("rays_in", C.c_uint64), ("rays_out", C.c_uint64),
                 ("interactions", C.c_uint64), ("nx", C.c_uint64), ("ny", C.c_uint64), ("nstar", C.c_int64),
                 ("seconds", C.c_double), ("mu_mean", C.c_double), ("lens_splits", C.c_int32),
-                ("far_bound", C.c_double), ("far_block", C.c_int32)]
+                ("far_bound", C.c_double), ("far_block", C.c_int32), ("far_group", C.c_int32)]
 
 
 class mm_compare(C.Structure):

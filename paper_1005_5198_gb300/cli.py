@@ -12,7 +12,7 @@
 
 A config is a JSON object whose keys are mm_params field names (sigma, gamma, smooth_frac,
 side_re, npix_side, nrays_per_pix, shoot_margin, nstar, disc_radius, mass_mu, mass_s, seed,
-far_order, far_ratio, far_block), plus precision ("fp32c", "fp64" or "far32"), mass_model
+far_order, far_ratio, far_block, far_group_order, far_group_theta, far_group_leaf), plus precision ("fp32c", "fp64" or "far32"), mass_model
 ("unit" or "lognormal") and an optional "name"; --set key=value overrides one. A bare name
 selects a config shipped in paper_1005_5198_gb300/configs. Lenses come from the seeded
 generator (mm_create_lenses): N* and the disc follow Eq. nstar and the disc rule unless given.
@@ -48,8 +48,9 @@ CONFIG_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "configs")
 PRECISIONS = {"fp32c": MM_FP32C, "fp64": MM_FP64, "far32": MM_FAR32}
 MASS_MODELS = {"unit": MM_MASS_UNIT, "lognormal": MM_MASS_LOGNORMAL}
 NUMERIC = {"sigma", "gamma", "smooth_frac", "side_re", "npix_side", "nrays_per_pix", "shoot_margin", "nstar",
-           "disc_radius", "mass_mu", "mass_s", "seed", "far_order", "far_ratio", "far_block"}
-INTEGER = {"npix_side", "nstar", "seed", "far_order", "far_block"}
+           "disc_radius", "mass_mu", "mass_s", "seed", "far_order", "far_ratio", "far_block", "far_group_order",
+           "far_group_theta", "far_group_leaf"}
+INTEGER = {"npix_side", "nstar", "seed", "far_order", "far_block", "far_group_order", "far_group_leaf"}
 EXIT_INTERRUPTED = 3
 
 

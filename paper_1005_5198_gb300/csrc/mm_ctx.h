@@ -71,13 +71,32 @@ private:
     std::unordered_map<void *, size_t> live_;
 };
 
+// Lens tree of a lens set for the grouped far field (mm_tree.cu), built on first use
+// and kept with the set for its (K, leaf size).
+struct LensTree {
+    int K = 0, leaf = 0;
+    double r0 = 0.0;
+    long long nodes = 0;
+    int *perm = nullptr;
+    unsigned char *level = nullptr;
+    int *ix = nullptr, *iy = nullptr, *begin = nullptr, *end = nullptr, *first_child = nullptr, *nchild = nullptr;
+    double2 *centre = nullptr;
+    double *rc = nullptr, *mass = nullptr;
+    double2 *mom = nullptr;
+    double *binom = nullptr;
+    void release(DeviceArena *a);
+    TreeView view() const;
+};
+
 struct LensSet {
+    std::mutex tree_mu;                    // guards the tree's build (maps sharing the set)
     long long n = 0, n_pad = 0;
     double *dx = nullptr, *dy = nullptr, *dm = nullptr;
     float4 *lh = nullptr;
     float *lmf = nullptr;
     bool unit_mass = true;
     double radius = 0.0;                   // largest |x_i| of the set (the far field's density estimate)
+    LensTree tree;                         // grouped far field: built on first use
     DeviceArena *arena = nullptr;
     ~LensSet();
     static size_t footprint(long long n);
@@ -166,10 +185,17 @@ void fill_desc(const MapObj &m, MapDesc *d);
 // once, to size the near lists; its kernels record failed bounds checks in *check in
 // checked builds); free them.
 int far_prepare(mm_ctx *ctx, MapObj &m, cudaStream_t s, unsigned int *check);
+// Lens tree of L for K moments and leaves of up to `leaf` lenses (kept in L.tree; rebuilt only
+// for other K or leaf). Exclusive prefix sum of a[0 .. n) in place with a[n] = the total.
+int build_lens_tree(mm_ctx *ctx, LensSet &L, int K, int leaf, cudaStream_t s);
+int scan_exclusive(mm_ctx *ctx, unsigned long long *a, long long n, cudaStream_t s);
 void far_release(MapObj &m);
 // The far field's block side for parameters p, a grid g and N* lenses in a disc of the given
 // radius: p.far_block, or for 0 the side that minimises the modelled time (mm_far.cu).
 int far_block_for(const Geo &g, const mm_params &p, long long nstar, double radius);
+// The multipole order of grouped far lenses for a map (0: no grouping): far_group_order, or for -1
+// (automatic) 24 from 32768 lenses on when far_order allows it.
+int far_group_for(const mm_params &p, long long nstar);
 int choose_variant(mm_ctx *ctx, bool unit_mass, long long nstar);
 int scratch_reserve(mm_ctx *ctx, LaunchScratch *sc, int n_maps);
 void scratch_free(mm_ctx *ctx, LaunchScratch *sc);

@@ -24,6 +24,7 @@
 // code one tile at a time.
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "mm_ctx.h"
 #include "mm_device.cuh"
@@ -680,8 +681,251 @@ __global__ void __launch_bounds__(kShootThreads, 2) k_shoot_far_dump(const Launc
     });
 }
 
+// ---- grouped far lenses: block setup by a walk of the lens tree ----------------
+//
+// One warp per block (4 per CTA). The warp walks the lens tree from the root, up to 32
+// nodes per step (lane l takes the l-th newest entry of its stack), in a fixed order:
+//   * a cell with |D| - r_C >= rho / q and rho + r_C <= theta |D| (D = z_C - z_B, FP64
+//     with explicit roundings, as the oracle decides) is grouped: its K moments enter the
+//     lane's series, c_l += -sum_k (-1)^k C(l+k, k) a_k / D^(l+k+1), and its remainder
+//     (M_C / |D|) E(rho / |D|, r_C / |D|) the lane's bound;
+//   * a leaf that is not grouped gives its lenses to the whole warp (lanes over lenses):
+//     a lens is near by the FP32 test of the ungrouped setup; a far lens adds its FP64 series
+//     terms -m / d^(l+1) and its tail m t^P / (|d| (1 - t)) to the lane's sums;
+//   * any other node pushes its children.
+// The lanes' sums are reduced in a fixed butterfly at the end. The count pass writes the
+// near counts, the coefficients (c'_l = rho^l c_l; c'_0 as float-float) and the bound; the
+// fill pass repeats the walk and writes the near lists.
+constexpr int kGroupThreads = 128;
+
+struct Cx {
+    double r, i;
+};
+
+__device__ __forceinline__ Cx cmul(Cx a, Cx b)
+{
+    return {__dsub_rn(__dmul_rn(a.r, b.r), __dmul_rn(a.i, b.i)), __dadd_rn(__dmul_rn(a.r, b.i), __dmul_rn(a.i, b.r))};
+}
+
+__device__ __forceinline__ Cx cinv(Cx a)
+{
+    const double d = __dadd_rn(__dmul_rn(a.r, a.r), __dmul_rn(a.i, a.i));
+    return {__ddiv_rn(a.r, d), __ddiv_rn(-a.i, d)};
+}
+
+// sum_{k>=K} C(l+k, k) y^k, term by term; the terms after the last one kept fall off faster
+// than a geometric series of the last ratio, which bounds them (as the oracle sums it).
+__device__ double group_tail(int l, int K, double y, const double *binom)
+{
+    double term = binom[(l + K) * kBinomN + K] * pow(y, (double)K);
+    double sum = 0.0;
+    for (int k = K; k < K + 100000; ++k) {
+        sum += term;
+        const double r = y * (double)(l + k + 1) / (double)(k + 1);
+        term *= r;
+        if (r < 1.0 && term / (1.0 - r) <= 1e-17 * sum) return sum + term / (1.0 - r);
+    }
+    return __longlong_as_double(0x7ff0000000000000LL);       // +inf: no bound
+}
+
+template <int PMAX>
+__global__ void __launch_bounds__(kGroupThreads) k_far_group(const MapDesc M, const FarDesc F, float *coef,
+                                                             unsigned long long *cnt, int *near_idx)
+{
+    const int lane = threadIdx.x & 31;
+    const long long gw = ((long long)blockIdx.x * kGroupThreads + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * kGroupThreads) >> 5;
+    int *const stack = F.stack + gw * kGroupStack;
+    const TreeView &T = F.tree;
+    const int P = F.order, K = F.group;
+    const bool fill = near_idx != nullptr;
+    for (long long b = gw; b < F.nblocks; b += nw) {
+        double xb, yb;
+        far_centre(M, F, b % F.blocks_x, b / F.blocks_x, xb, yb);
+        float cxh, cxl, cyh, cyl;
+        split_d(xb, cxh, cxl);
+        split_d(yb, cyh, cyl);
+        double cr[PMAX], ci[PMAX];
+#pragma unroll
+        for (int l = 0; l < PMAX; ++l) cr[l] = ci[l] = 0.0;
+        double bnd = 0.0;
+        unsigned long long nnear = 0, out = fill ? F.near_off[b] : 0ULL;
+        if (lane == 0) stack[0] = 0;
+        int sp = 1;
+        bool ovf = false;
+        __syncwarp();
+        while (sp > 0 && !ovf) {
+            const int take = min(sp, 32);
+            const int v = lane < take ? stack[sp - take + lane] : -1;
+            sp -= take;
+            __syncwarp();                                   // the stack entries are read before new pushes
+            bool leaf = false;
+            int nch = 0;
+            if (v >= 0) {
+                const double2 zc = T.centre[v];
+                const double dx = __dsub_rn(zc.x, xb), dy = __dsub_rn(zc.y, yb);
+                const double dabs = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+                const double rc = T.rc[v];
+                const bool grouped = __dsub_rn(dabs, rc) >= F.rn64 && __dadd_rn(F.rho64, rc) <= __dmul_rn(F.theta, dabs);
+                if (grouped) {
+                    if (!fill) {
+                        const Cx u = cinv({dx, dy});
+                        Cx up = u;                          // u^(k+1)
+                        double sr[PMAX], si[PMAX];
+#pragma unroll
+                        for (int l = 0; l < PMAX; ++l) sr[l] = si[l] = 0.0;
+                        for (int k = 0; k < K; ++k) {
+                            const double2 a = T.mom[(long long)v * K + k];
+                            const Cx t = cmul({a.x, a.y}, up);
+                            const double sg = (k & 1) ? 1.0 : -1.0;          // -(-1)^k
+#pragma unroll
+                            for (int l = 0; l < PMAX; ++l) {
+                                if (l < P) {
+                                    const double c = sg * T.binom[(l + k) * kBinomN + k];
+                                    sr[l] = fma(c, t.r, sr[l]);
+                                    si[l] = fma(c, t.i, si[l]);
+                                }
+                            }
+                            up = cmul(up, u);
+                        }
+                        Cx pw = {1.0, 0.0};                 // u^l
+#pragma unroll
+                        for (int l = 0; l < PMAX; ++l) {
+                            if (l < P) {
+                                const Cx q = cmul({sr[l], si[l]}, pw);
+                                cr[l] += q.r;
+                                ci[l] += q.i;
+                                pw = cmul(pw, u);
+                            }
+                        }
+                        const double x = F.rho64 / dabs, y = rc / dabs;
+                        double e = pow(x / (1.0 - y), (double)P) / (1.0 - x - y), xl = 1.0;
+                        for (int l = 0; l < P; ++l) {
+                            e += xl * group_tail(l, K, y, T.binom);
+                            xl *= x;
+                        }
+                        bnd += T.mass[v] / dabs * e;
+                    }
+                } else if (T.nchild[v] == 0) {
+                    leaf = true;
+                } else {
+                    nch = T.nchild[v];
+                }
+            }
+            // children onto the stack, in lane order
+            int pre = nch;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, pre, o);
+                if (lane >= o) pre += y;
+            }
+            const int total = __shfl_sync(kFull, pre, 31);
+            pre -= nch;
+            if (sp + total > kGroupStack) {
+                ovf = true;                                 // warp-uniform
+            } else {
+                for (int c = 0; c < nch; ++c) stack[sp + pre + c] = T.first_child[v] + c;
+                sp += total;
+            }
+            __syncwarp();
+            // the leaves of this step, in lane order, their lenses over the lanes
+            unsigned lm = __ballot_sync(kFull, leaf);
+            while (lm && !ovf) {
+                const int src = __ffs(lm) - 1;
+                lm &= lm - 1u;
+                const int lv = __shfl_sync(kFull, v, src);
+                const int lb = T.begin[lv], le = T.end[lv];
+                for (int e0 = lb; e0 < le; e0 += 32) {
+                    const int e = e0 + lane;
+                    bool nr = false, fr = false;
+                    int g = 0;
+                    if (e < le) {
+                        g = T.perm[e];
+                        float ddx, ddy, r2;
+                        far_offset(M.lh[g], cxh, cxl, cyh, cyl, ddx, ddy, r2);
+                        nr = r2 < F.rn2;
+                        fr = !nr;
+                    }
+                    const unsigned nb = __ballot_sync(kFull, nr);
+                    if (fill) {
+                        const unsigned long long at = out + __popc(nb & ((1u << lane) - 1u));
+                        if (nr && MM_BOUNDS(F.check, at < F.near_off[b + 1], kChkNearList)) near_idx[at] = g;
+                        out += __popc(nb);
+                    } else {
+                        nnear += __popc(nb);
+                        if (fr) {
+                            const Cx d = {__dsub_rn(M.lx[g], xb), __dsub_rn(M.ly[g], yb)};
+                            const Cx u = cinv(d);
+                            const double m = M.unit_mass ? 1.0 : M.lm[g];
+                            Cx t = {-m * u.r, -m * u.i};
+#pragma unroll
+                            for (int l = 0; l < PMAX; ++l) {
+                                if (l < P) {
+                                    cr[l] += t.r;
+                                    ci[l] += t.i;
+                                    t = cmul(t, u);
+                                }
+                            }
+                            const double da = __dsqrt_rn(__dadd_rn(__dmul_rn(d.r, d.r), __dmul_rn(d.i, d.i)));
+                            const double tt = F.rho64 / da;
+                            bnd += m * pow(tt, (double)P) / (da * (1.0 - tt));
+                        }
+                    }
+                }
+            }
+        }
+        if (ovf) {
+            if (lane == 0) atomicExch(F.overflow, 1u);
+            continue;
+        }
+        if (fill) continue;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int l = 0; l < PMAX; ++l) {
+                if (l < P) {
+                    cr[l] += __shfl_xor_sync(kFull, cr[l], o);
+                    ci[l] += __shfl_xor_sync(kFull, ci[l], o);
+                }
+            }
+            bnd += __shfl_xor_sync(kFull, bnd, o);
+        }
+        if (lane == 0) {
+            cnt[b] = nnear;
+            float *cb = coef + b * (long long)F.stride;
+            float h, l0;
+            split_d(cr[0], h, l0);
+            cb[0] = h;
+            cb[1] = l0;
+            split_d(ci[0], h, l0);
+            cb[2] = h;
+            cb[3] = l0;
+            double rl = 1.0;
+#pragma unroll
+            for (int l = 1; l < PMAX; ++l) {
+                if (l < P) {
+                    rl *= F.rho64;
+                    cb[4 + 2 * (l - 1)] = __double2float_rn(cr[l] * rl);
+                    cb[5 + 2 * (l - 1)] = __double2float_rn(ci[l] * rl);
+                }
+            }
+            atomicMax(F.bound_max, __float_as_uint(__double2float_ru(bnd)));
+        }
+    }
+}
+
 }  // namespace
 }  // namespace dev
+
+int far_group_warps(int sms) { return sms * 4 * (dev::kGroupThreads / 32); }
+
+cudaError_t launch_far_group(const MapDesc &M, const FarDesc &F, float *coef, unsigned long long *a, int *near_idx,
+                             int warps, cudaStream_t s)
+{
+    const int grid = std::max(1, warps / (dev::kGroupThreads / 32));
+    if (F.order <= 8) dev::k_far_group<8><<<grid, dev::kGroupThreads, 0, s>>>(M, F, coef, a, near_idx);
+    else dev::k_far_group<16><<<grid, dev::kGroupThreads, 0, s>>>(M, F, coef, a, near_idx);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_far_count(const MapDesc &M, const FarDesc &F, unsigned long long *a, int grid, cudaStream_t s)
 {
@@ -746,12 +990,28 @@ constexpr double kSetupCost = 2.15e-12;      // seconds per block x lens x term
 constexpr double kNearCost = 0.81e-12;       // seconds per ray x near lens
 constexpr double kBlockCost = 2.0e-9;        // seconds per block
 
+// Grouped setup: the lens-tree walk of a block prices its grouped cells (about kGroupCells per
+// tree level, each P (2K + 120) FP64 operations with its bound) and the lenses it takes one by
+// one (those of leaves within (rho + r_leaf) / theta + r_leaf of the block, 8 P operations each)
+// at kGroupOpCost seconds per FP64 operation, the walk's rate over the whole GPU.
+constexpr double kGroupCells = 50.0;
+constexpr double kGroupOpCost = 5.0e-12;
+
+int far_group_for(const mm_params &p, long long nstar)
+{
+    if (p.far_group_order >= 0) return p.far_group_order;
+    return (nstar >= 32768 && p.far_order <= kGroupMaxSeries) ? 24 : 0;
+}
+
 int far_block_for(const Geo &g, const mm_params &p, long long nstar, double radius)
 {
     if (p.far_block > 0) return p.far_block;
     // the whole ray grid, so that every part of a map (mm_shoot_into) chooses alike
     const double rays = (double)g.nx * (double)g.ny;
     const double density = radius > 0.0 ? (double)nstar / (M_PI * radius * radius) : 0.0;
+    const int K = far_group_for(p, nstar);
+    const double levels = std::max(1.0, std::log((double)std::max(nstar, 1LL) / p.far_group_leaf) / std::log(4.0));
+    const double r_leaf = density > 0.0 ? std::sqrt(p.far_group_leaf / density) * 0.7071 : 0.0;
     double best = 0.0;
     int best_bt = 8;
     for (int bt = 1; bt <= kFarMaxBlock; bt *= 2) {
@@ -759,8 +1019,14 @@ int far_block_for(const Geo &g, const mm_params &p, long long nstar, double radi
         const double blocks = std::ceil((double)g.nx / bw) * std::ceil((double)g.ny / bh);
         const double rho = g.delta * std::sqrt(0.25 * (bw * bw + bh * bh));
         const double near = density * M_PI * (rho / p.far_ratio) * (rho / p.far_ratio);
-        const double cost = blocks * (double)nstar * (double)p.far_order * kSetupCost + rays * near * kNearCost +
-                            blocks * kBlockCost;
+        double setup = blocks * (double)nstar * (double)p.far_order * kSetupCost;
+        if (K > 0) {
+            const double reach = (rho + r_leaf) / p.far_group_theta + r_leaf;
+            const double alone = std::min((double)nstar, density * M_PI * reach * reach);
+            const double per_block = kGroupCells * levels * p.far_order * (2.0 * K + 120.0) + alone * 8.0 * p.far_order;
+            setup = blocks * per_block * kGroupOpCost;
+        }
+        const double cost = setup + rays * near * kNearCost + blocks * kBlockCost;
         if (bt == 1 || cost < best) {
             best = cost;
             best_bt = bt;
@@ -806,6 +1072,49 @@ int far_prepare(mm_ctx *ctx, MapObj &m, cudaStream_t s, unsigned int *check)
         return rc;
     MapDesc d;
     fill_desc(m, &d);
+    const int K = far_group_for(p, m.lenses->n);
+    if (K > 0 && m.lenses->n > 0) {              // grouped far lenses: walk the lens set's tree
+        {
+            std::lock_guard<std::mutex> lk(m.lenses->tree_mu);
+            if ((rc = build_lens_tree(ctx, *m.lenses, K, p.far_group_leaf, s))) return rc;
+            F.tree = m.lenses->tree.view();
+        }
+        F.group = K;
+        F.theta = p.far_group_theta;
+        F.rho64 = rho;
+        F.rn64 = rn;
+        F.coef = m.far_coef;
+        F.near_off = m.far_off;
+        const int warps = far_group_warps(ctx->sms);
+        struct Tmp {
+            DeviceArena *a;
+            std::vector<void *> v;
+            ~Tmp() { for (void *q : v) a->free(q); }
+        } tmp{&ctx->arena, {}};
+        if ((rc = ctx->arena.alloc((size_t)warps * kGroupStack * sizeof(int), (void **)&F.stack))) return rc;
+        tmp.v.push_back(F.stack);
+        if ((rc = ctx->arena.alloc(sizeof(unsigned), (void **)&F.overflow))) return rc;
+        tmp.v.push_back(F.overflow);
+        MM_CUDA(cudaMemsetAsync(F.overflow, 0, sizeof(unsigned), s));
+        MM_CUDA(launch_far_group(d, F, m.far_coef, m.far_off, nullptr, warps, s));
+        unsigned ovf = 0;
+        MM_CUDA(cudaMemcpyAsync(&ovf, F.overflow, sizeof(ovf), cudaMemcpyDeviceToHost, s));
+        MM_CUDA(cudaStreamSynchronize(s));
+        if (ovf) return fail(MM_EINVAL, "far field: the lens-tree walk of a block outgrew its stack (lower far_block "
+                                        "or raise far_group_leaf)");
+        if ((rc = scan_exclusive(ctx, m.far_off, F.nblocks, s))) return rc;
+        unsigned long long total = 0;
+        MM_CUDA(cudaMemcpyAsync(&total, m.far_off + F.nblocks, sizeof(total), cudaMemcpyDeviceToHost, s));
+        MM_CUDA(cudaStreamSynchronize(s));
+        if (total > (unsigned long long)INT32_MAX) return fail(MM_ENOMEM, "far field: near lists too long (lower far_block)");
+        if ((rc = ctx->arena.alloc(std::max<size_t>(1, (size_t)total) * sizeof(int), (void **)&m.far_idx))) return rc;
+        F.near_idx = m.far_idx;
+        MM_CUDA(launch_far_group(d, F, m.far_coef, m.far_off, m.far_idx, warps, s));
+        MM_CUDA(cudaStreamSynchronize(s));            // the stack goes back to the arena
+        F.stack = nullptr;
+        F.overflow = nullptr;
+        return MM_OK;
+    }
     const int grid = (int)std::max(1LL, std::min(F.nblocks, (long long)ctx->sms * 8));
     MM_CUDA(launch_far_count(d, F, m.far_off, grid, s));
     MM_CUDA(launch_far_scan(m.far_off, F.nblocks, s));

@@ -100,6 +100,13 @@ int compute_geo(const mm_params *p, Geo *g)
         if (!finite(p->far_ratio) || !(p->far_ratio > 0.0) || p->far_ratio > 0.9)
             return fail(MM_EINVAL, "far_ratio must be in (0, 0.9]");
         if (p->far_block < 0 || p->far_block > kFarMaxBlock) return fail(MM_EINVAL, "far_block must be in 0..64");
+        if (p->far_group_order < -1 || p->far_group_order > kGroupMaxOrder)
+            return fail(MM_EINVAL, "far_group_order must be -1 (automatic), 0 or 1..32");
+        if (p->far_group_order > 0 && p->far_order > kGroupMaxSeries)
+            return fail(MM_EINVAL, "grouped far lenses need far_order <= 16");
+        if (!finite(p->far_group_theta) || !(p->far_group_theta > 0.0) || p->far_group_theta > 0.9)
+            return fail(MM_EINVAL, "far_group_theta must be in (0, 0.9]");
+        if (p->far_group_leaf < 1 || p->far_group_leaf > (1 << 20)) return fail(MM_EINVAL, "far_group_leaf must be in 1..2^20");
     }
     if (p->mass_model != MM_MASS_UNIT && p->mass_model != MM_MASS_LOGNORMAL) return fail(MM_EINVAL, "bad mass_model");
     if (!finite(p->sigma) || !finite(p->gamma) || p->sigma < 0.0) return fail(MM_EINVAL, "sigma must be finite and >= 0, gamma finite");
@@ -241,6 +248,7 @@ LensSet::~LensSet()
 {
     if (!arena) return;
     arena->free(dx); arena->free(dy); arena->free(dm); arena->free(lh); arena->free(lmf);
+    tree.release(arena);
 }
 
 size_t LensSet::footprint(long long n)
@@ -763,6 +771,9 @@ int mm_params_default(mm_params *p)
     p->far_order = 10;
     p->far_ratio = 0.15;
     p->far_block = 0;
+    p->far_group_order = -1;
+    p->far_group_theta = 0.3;
+    p->far_group_leaf = 64;
     return MM_OK;
 }
 
@@ -918,7 +929,9 @@ int mm_shoot_into(mm_ctx *ctx, mm_lenses lenses, const mm_params *p, mm_map map)
         p->npix_side != q.npix_side || p->nrays_per_pix != q.nrays_per_pix || margin_p != margin_q ||
         p->precision != q.precision ||
         (p->precision == MM_FAR32 &&
-         (p->far_order != q.far_order || p->far_ratio != q.far_ratio || p->far_block != q.far_block)))
+         (p->far_order != q.far_order || p->far_ratio != q.far_ratio || p->far_block != q.far_block ||
+          p->far_group_order != q.far_group_order || p->far_group_theta != q.far_group_theta ||
+          p->far_group_leaf != q.far_group_leaf)))
         return fail(MM_EINVAL, "parameters differ from the map's (only ray_rect may change)");
     cudaSetDevice(ctx->device);
     std::shared_ptr<LensSet> L = T->lenses;
@@ -1006,6 +1019,7 @@ int mm_map_fetch(mm_ctx *ctx, mm_map map, uint32_t *host_counts, size_t n_elems,
         st->lens_splits = M->splits;
         st->far_bound = M->far_bound;
         st->far_block = M->p.precision == MM_FAR32 ? far_block_for(M->g, M->p, M->lenses->n, M->lenses->radius) : 0;
+        st->far_group = M->p.precision == MM_FAR32 ? far_group_for(M->p, M->lenses->n) : 0;
     }
     return MM_OK;
 }

@@ -143,8 +143,14 @@ def test_far_block_choice():
     cfg2 = dict(sigma=0.8, gamma=0.3, smooth_frac=0.5, side=40.0, npix_side=2048, nrays=500.0, nstar=25000,
                 disc_radius=250.0, precision=mm.MM_FAR32)
     assert mm.mm_geometry_of(mm.params(**cfg2))["far_block"] == 16
-    sides = [mm.mm_geometry_of(mm.params(**dict(fig1, nstar=n)))["far_block"] for n in (10 ** 3, 10 ** 5, 10 ** 7, 10 ** 9)]
-    assert sides == sorted(sides) and sides[-1] == 64             # more lenses: larger blocks
+    counts = (10 ** 3, 10 ** 5, 10 ** 7, 10 ** 9)
+    # every far lens alone: block preparation grows as blocks x N*, so more lenses want larger blocks
+    alone = [mm.mm_geometry_of(mm.params(**dict(fig1, nstar=n, far_group_order=0)))["far_block"] for n in counts]
+    assert alone == sorted(alone) and alone[-1] == 64
+    # grouped far lenses (the default from 32768 lenses): preparation grows only with the tree's
+    # depth, so the side stops growing
+    grouped = [mm.mm_geometry_of(mm.params(**dict(fig1, nstar=n)))["far_block"] for n in counts]
+    assert grouped == sorted(grouped) and grouped[-1] < alone[-1]
     assert mm.mm_geometry_of(mm.params(**dict(fig1, far_block=3)))["far_block"] == 3
     bad = mm.params(**fig1)
     bad.far_block = -1

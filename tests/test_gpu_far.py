@@ -34,8 +34,10 @@ def ctx():
 
 
 def P(cfg, far, **kw):
+    """Far-field parameters of the oracle's statement `far` (no grouping unless it says so)."""
     d = dict(cfg, precision=mm.MM_FAR32, far_order=far["order"], far_ratio=far["ratio"],
-             far_block=far["block_tiles"])
+             far_block=far["block_tiles"], far_group_order=far.get("group_order", 0),
+             far_group_theta=far.get("group_theta", 0.5), far_group_leaf=far.get("group_leaf", 64))
     d.update(kw)
     return mm.params(**d)
 
@@ -304,3 +306,85 @@ def test_no_lenses_gives_the_smooth_map_exactly(ctx):
     np.testing.assert_array_equal(maps[0][0], maps[1][0])
     assert maps[0][1]["far_bound"] == 0.0 and maps[0][1]["rays_in"] == tot["inside"]
     mm.mm_release_lenses(ctx, lh)
+
+
+# ---- grouped far lenses: cells of the lens tree act through their moments (Sect. 2.1) ----
+# 20 000 lognormal lenses in a disc of 238 Einstein radii around a 10 x 10 R_E ray grid, blocks
+# of 2 x 2 tiles: most cells are far from every block and are grouped.
+CFG_G = dict(sigma=0.4, gamma=0.0, smooth_frac=0.0, side=4.0, npix_side=64, nrays=16.0)
+FAR_GROUP = [dict(order=10, ratio=0.3, block_tiles=2, group_order=16, group_theta=0.5, group_leaf=16),
+             dict(order=6, ratio=0.15, block_tiles=4, group_order=8, group_theta=0.6, group_leaf=5),
+             dict(order=16, ratio=0.2, block_tiles=1, group_order=32, group_theta=0.3, group_leaf=64)]
+
+
+def field_g():
+    mmean = field.mean_mass(1, 0.0, 0.5)
+    return synth.lens_field(20000, field.radius_for_nstar(20000, 0.4, mmean), 23, synth.MASS_LOGNORMAL)
+
+
+@pytest.mark.parametrize("far", FAR_GROUP, ids=["K16", "K8-leaf5", "K32-P16"])
+def test_grouped_rays_and_map_match_the_oracle(ctx, far):
+    """The lens tree built on the device, the cells grouped by each block and their series agree
+    with the oracle's statement of the grouped far field: per-ray deflections within 1e-5 R_E,
+    pixels within the FP32 margin, the map within 2e-4 of the rays, and the bound the oracle's."""
+    f = field_g()
+    lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
+    g = mm.mm_geometry_of(mm.params(**CFG_G))
+    ii, jj = sample_rays(g["nx"], g["ny"], 4000, 3)
+    check_rays(ctx, lh, f, CFG_G, far, ii, jj)
+    m = mm.mm_shoot(ctx, lh, P(CFG_G, far))
+    got, st = mm.mm_map_fetch(ctx, m)
+    mm.mm_release_map(ctx, m)
+    ref, tot, bmax = oracle.far_map(ocfg(CFG_G), f, far)
+    assert st["far_group"] == far["group_order"]
+    assert st["rays_shot"] == tot["shot"] and st["rays_in"] + st["rays_out"] == st["rays_shot"]
+    assert int(np.abs(got.astype(np.int64) - ref).sum()) <= 2 * MISBIN * tot["shot"]
+    assert st["far_bound"] == pytest.approx(bmax, rel=2e-3)
+    mm.mm_release_lenses(ctx, lh)
+
+
+def test_grouped_maps_are_deterministic_and_close_to_ungrouped(ctx):
+    """Grouping changes a map only within its bound: against the same map without grouping, and
+    the tree walk and the moments have a fixed order, so repeated maps are identical."""
+    f = field_g()
+    lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
+    far = FAR_GROUP[0]
+    maps = []
+    for _ in range(3):
+        m = mm.mm_shoot(ctx, lh, P(CFG_G, far))
+        maps.append(mm.mm_map_fetch(ctx, m)[0].copy())
+        mm.mm_release_map(ctx, m)
+    assert np.array_equal(maps[0], maps[1]) and np.array_equal(maps[0], maps[2])
+    m = mm.mm_shoot(ctx, lh, P(CFG_G, dict(far, group_order=0)))
+    plain, st = mm.mm_map_fetch(ctx, m)
+    mm.mm_release_map(ctx, m)
+    assert int(np.abs(maps[0].astype(np.int64) - plain).sum()) <= 2 * MISBIN * st["rays_shot"]
+    mm.mm_release_lenses(ctx, lh)
+
+
+def test_automatic_grouping_from_32768_lenses(ctx):
+    """far_group_order = -1 (the default) groups with K = 24, theta = 0.3 and leaves of 64 lenses
+    from 32768 lenses on, and not below; the grouped rays match the oracle's statement."""
+    cfg = dict(CFG_G, nrays=4.0)
+    for n, k_expected in ((32767, 0), (40000, 24)):
+        f = synth.lens_field(n, field.radius_for_nstar(n, 0.4), 29)
+        lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
+        p = mm.params(**cfg, precision=mm.MM_FAR32, far_block=2)
+        m = mm.mm_shoot(ctx, lh, p)
+        _, st = mm.mm_map_fetch(ctx, m, want_counts=False)
+        mm.mm_release_map(ctx, m)
+        assert st["far_group"] == k_expected
+        if k_expected:
+            far = dict(order=10, ratio=0.15, block_tiles=2, group_order=24, group_theta=0.3, group_leaf=64)
+            g = mm.mm_geometry_of(mm.params(**cfg))
+            ii, jj = sample_rays(g["nx"], g["ny"], 1500, 5)
+            check_rays(ctx, lh, f, cfg, far, ii, jj)
+        mm.mm_release_lenses(ctx, lh)
+
+
+def test_grouping_parameters_validated(ctx):
+    for kw in (dict(far_group_order=33), dict(far_group_order=-2), dict(far_group_order=8, far_order=17),
+               dict(far_group_theta=0.0), dict(far_group_theta=0.95), dict(far_group_leaf=0)):
+        with pytest.raises(mm.MMError) as e:
+            mm.mm_geometry_of(mm.params(**CFG_G, precision=mm.MM_FAR32, **kw))
+        assert e.value.code == mm.MM_EINVAL

@@ -669,7 +669,8 @@ def test_large_lens_count_streams_through_chunks(ctx):
     ii, jj = rng.integers(0, g["nx"], 300), rng.integers(0, g["ny"], 300)
     far = dict(order=10, ratio=0.15, block_tiles=8)
     a_g, _ = mm.mm_debug_deflect(ctx, lh, P(cfg, precision=mm.MM_FAR32, far_order=far["order"],
-                                           far_ratio=far["ratio"], far_block=far["block_tiles"]), ii, jj)
+                                           far_ratio=far["ratio"], far_block=far["block_tiles"],
+                                           far_group_order=0), ii, jj)
     a_o, _, _, _ = oracle.far_rays(oracle_cfg(cfg), f, far, ii, jj)
     assert np.hypot(*(a_g - a_o).T).max() <= 1e-5
 
