@@ -46,6 +46,20 @@ def main():
         got, st = mm.mm_map_fetch(ctx, m)
         mm.mm_release_map(ctx, m)
         close(got, ref_b, tot_b["shot"], "far, all near")
+        # grouped far lenses (the lens tree's walk writes the near lists under the checks)
+        gf = synth.lens_field(6000, 40.0, 9, model=synth.MASS_LOGNORMAL)
+        lg = mm.mm_create_lenses_from(ctx, gf.x, gf.y, gf.m)
+        pg = mm.params(**SPLIT, precision=mm.MM_FAR32, far_block=2, far_group_order=12, far_group_theta=0.5,
+                       far_group_leaf=8)
+        m = mm.mm_shoot(ctx, lg, pg)
+        got, st = mm.mm_map_fetch(ctx, m)
+        mm.mm_release_map(ctx, m)
+        ref_g, tot_g, _ = oracle.far_map(dict(SPLIT, margin=1.5), gf, dict(order=10, ratio=0.15, block_tiles=2,
+                                                                             group_order=12, group_theta=0.5,
+                                                                             group_leaf=8))
+        assert st["far_group"] == 12
+        close(got, ref_g, tot_g["shot"], "far, grouped")
+        mm.mm_release_lenses(ctx, lg)
         # mixed batch, debug dump, parts
         maps = mm.mm_shoot_batch(ctx, [lh, lb, lh], [mm.params(**CFG0), mm.params(**SPLIT),
                                                     mm.params(**CFG0, precision=mm.MM_FAR32)])
