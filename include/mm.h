@@ -111,8 +111,10 @@ typedef struct {
     int32_t  far_group_order;/* MM_FAR32: grouped far lenses (the tree code's cells, Sect. 2.1):
                                 K multipole moments per cell of a lens quadtree, 1 .. 32 (needs
                                 far_order <= 16); 0: every far lens enters its block's series
-                                alone; -1 (default): 24 when the lens set has 32768 lenses or
-                                more, else 0. The tree: R0 = the smallest power of two above every
+                                alone; -1 (default): 24 when a cost model of the block setup finds
+                                grouping faster (in practice from about 1e6 lenses on), else 0. The
+                                automatic block side (far_block = 0) comes from the same model.
+                                The tree: R0 = the smallest power of two above every
                                 |x_i|, |y_i|; level L cuts [-R0, R0)^2 into cells of side
                                 2 R0 / 2^L; a cell with more than far_group_leaf lenses (below
                                 level 16) splits into its four quadrants. For block B a cell C
@@ -166,6 +168,8 @@ typedef struct {
     int32_t far_block;  /* MM_FAR32: the block side in tiles for these parameters (the automatic
                            choice when far_block = 0, for the N* and disc radius above; a map
                            shot with another lens set reports its own in mm_stats) */
+    int32_t far_group;  /* MM_FAR32: the multipole order K of grouped cells for these parameters
+                           (the automatic choice when far_group_order = -1), 0: no grouping */
 } mm_geometry;
 
 /* ---- context ------------------------------------------------------------ */

@@ -80,7 +80,7 @@ class mm_serve_stats_t(C.Structure):
 class mm_geometry(C.Structure):
     _fields_ = [("pix", C.c_double), ("delta", C.c_double), ("width", C.c_double), ("height", C.c_double),
                 ("nx", C.c_int64), ("ny", C.c_int64), ("nstar", C.c_int64), ("disc_radius", C.c_double),
-                ("mu_theory", C.c_double), ("far_block", C.c_int32)]
+                ("mu_theory", C.c_double), ("far_block", C.c_int32), ("far_group", C.c_int32)]
 
 
 _lib = None

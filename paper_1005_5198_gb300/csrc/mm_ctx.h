@@ -194,8 +194,8 @@ void far_release(MapObj &m);
 // radius: p.far_block, or for 0 the side that minimises the modelled time (mm_far.cu).
 int far_block_for(const Geo &g, const mm_params &p, long long nstar, double radius);
 // The multipole order of grouped far lenses for a map (0: no grouping): far_group_order, or for -1
-// (automatic) 24 from 32768 lenses on when far_order allows it.
-int far_group_for(const mm_params &p, long long nstar);
+// (automatic) 24 when the far field's cost model finds grouping faster (and far_order <= 16).
+int far_group_for(const Geo &g, const mm_params &p, long long nstar, double radius);
 int choose_variant(mm_ctx *ctx, bool unit_mass, long long nstar);
 int scratch_reserve(mm_ctx *ctx, LaunchScratch *sc, int n_maps);
 void scratch_free(mm_ctx *ctx, LaunchScratch *sc);

@@ -993,46 +993,76 @@ constexpr double kBlockCost = 2.0e-9;        // seconds per block
 // Grouped setup: the lens-tree walk of a block prices its grouped cells (about kGroupCells per
 // tree level, each P (2K + 120) FP64 operations with its bound) and the lenses it takes one by
 // one (those of leaves within (rho + r_leaf) / theta + r_leaf of the block, 8 P operations each)
-// at kGroupOpCost seconds per FP64 operation, the walk's rate over the whole GPU.
+// at kGroupOpCost seconds per operation, the walk's measured rate over the whole GPU (GB300:
+// about 11 us of GPU time per block on the Fig. 1 geometry with 1e5 to 1e8 lenses).
 constexpr double kGroupCells = 50.0;
-constexpr double kGroupOpCost = 5.0e-12;
+constexpr double kGroupOpCost = 1.0e-11;
+constexpr int kAutoGroupOrder = 24;          // K of the automatic choice (bound well below 1e-8 R_E)
 
-int far_group_for(const mm_params &p, long long nstar)
+// Modelled time of a map's far field with block side bt and multipole order K (0: no grouping).
+static double far_cost(const Geo &g, const mm_params &p, long long nstar, double radius, int bt, int K)
 {
-    if (p.far_group_order >= 0) return p.far_group_order;
-    return (nstar >= 32768 && p.far_order <= kGroupMaxSeries) ? 24 : 0;
+    const double rays = (double)g.nx * (double)g.ny;
+    const double density = radius > 0.0 ? (double)nstar / (M_PI * radius * radius) : 0.0;
+    const double bw = 64.0 * bt, bh = 32.0 * bt;
+    const double blocks = std::ceil((double)g.nx / bw) * std::ceil((double)g.ny / bh);
+    const double rho = g.delta * std::sqrt(0.25 * (bw * bw + bh * bh));
+    const double near = density * M_PI * (rho / p.far_ratio) * (rho / p.far_ratio);
+    double setup = blocks * (double)nstar * (double)p.far_order * kSetupCost;
+    if (K > 0) {
+        const double levels = std::max(1.0, std::log((double)std::max(nstar, 1LL) / p.far_group_leaf) / std::log(4.0));
+        const double r_leaf = density > 0.0 ? std::sqrt(p.far_group_leaf / density) * 0.7071 : 0.0;
+        const double reach = (rho + r_leaf) / p.far_group_theta + r_leaf;
+        const double alone = std::min((double)nstar, density * M_PI * reach * reach);
+        setup = blocks * (kGroupCells * levels * p.far_order * (2.0 * K + 120.0) + alone * 8.0 * p.far_order) *
+                kGroupOpCost;
+    }
+    return setup + rays * near * kNearCost + blocks * kBlockCost;
+}
+
+// The far field's plan for a map: block side (p.far_block, or the modelled best) and multipole
+// order (p.far_group_order, or for -1 grouping with K = 24 when the model finds it faster).
+// Computed from the whole ray grid, so that every part of a map (mm_shoot_into) plans alike.
+static void far_plan(const Geo &g, const mm_params &p, long long nstar, double radius, int *bt_out, int *k_out)
+{
+    const bool can_group = nstar > 0 && p.far_order <= kGroupMaxSeries;
+    int ks[2] = {0, kAutoGroupOrder}, nk = 2;
+    if (p.far_group_order >= 0) {
+        ks[0] = p.far_group_order;
+        nk = 1;
+    } else if (!can_group) {
+        nk = 1;
+    }
+    double best = 0.0;
+    int best_bt = 8, best_k = ks[0];
+    for (int q = 0; q < nk; ++q) {
+        for (int bt = 1; bt <= kFarMaxBlock; bt *= 2) {
+            if (p.far_block > 0 && bt != 1) break;
+            const int side = p.far_block > 0 ? p.far_block : bt;
+            const double c = far_cost(g, p, nstar, radius, side, ks[q]);
+            if ((q == 0 && bt == 1) || c < best) {
+                best = c;
+                best_bt = side;
+                best_k = ks[q];
+            }
+        }
+    }
+    *bt_out = best_bt;
+    *k_out = best_k;
+}
+
+int far_group_for(const Geo &g, const mm_params &p, long long nstar, double radius)
+{
+    int bt, K;
+    far_plan(g, p, nstar, radius, &bt, &K);
+    return K;
 }
 
 int far_block_for(const Geo &g, const mm_params &p, long long nstar, double radius)
 {
-    if (p.far_block > 0) return p.far_block;
-    // the whole ray grid, so that every part of a map (mm_shoot_into) chooses alike
-    const double rays = (double)g.nx * (double)g.ny;
-    const double density = radius > 0.0 ? (double)nstar / (M_PI * radius * radius) : 0.0;
-    const int K = far_group_for(p, nstar);
-    const double levels = std::max(1.0, std::log((double)std::max(nstar, 1LL) / p.far_group_leaf) / std::log(4.0));
-    const double r_leaf = density > 0.0 ? std::sqrt(p.far_group_leaf / density) * 0.7071 : 0.0;
-    double best = 0.0;
-    int best_bt = 8;
-    for (int bt = 1; bt <= kFarMaxBlock; bt *= 2) {
-        const double bw = 64.0 * bt, bh = 32.0 * bt;
-        const double blocks = std::ceil((double)g.nx / bw) * std::ceil((double)g.ny / bh);
-        const double rho = g.delta * std::sqrt(0.25 * (bw * bw + bh * bh));
-        const double near = density * M_PI * (rho / p.far_ratio) * (rho / p.far_ratio);
-        double setup = blocks * (double)nstar * (double)p.far_order * kSetupCost;
-        if (K > 0) {
-            const double reach = (rho + r_leaf) / p.far_group_theta + r_leaf;
-            const double alone = std::min((double)nstar, density * M_PI * reach * reach);
-            const double per_block = kGroupCells * levels * p.far_order * (2.0 * K + 120.0) + alone * 8.0 * p.far_order;
-            setup = blocks * per_block * kGroupOpCost;
-        }
-        const double cost = setup + rays * near * kNearCost + blocks * kBlockCost;
-        if (bt == 1 || cost < best) {
-            best = cost;
-            best_bt = bt;
-        }
-    }
-    return best_bt;
+    int bt, K;
+    far_plan(g, p, nstar, radius, &bt, &K);
+    return bt;
 }
 
 int far_prepare(mm_ctx *ctx, MapObj &m, cudaStream_t s, unsigned int *check)
@@ -1072,7 +1102,7 @@ int far_prepare(mm_ctx *ctx, MapObj &m, cudaStream_t s, unsigned int *check)
         return rc;
     MapDesc d;
     fill_desc(m, &d);
-    const int K = far_group_for(p, m.lenses->n);
+    const int K = far_group_for(g, p, m.lenses->n, m.lenses->radius);
     if (K > 0 && m.lenses->n > 0) {              // grouped far lenses: walk the lens set's tree
         {
             std::lock_guard<std::mutex> lk(m.lenses->tree_mu);

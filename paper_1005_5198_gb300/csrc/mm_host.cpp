@@ -793,6 +793,7 @@ int mm_geometry_of(const mm_params *p, mm_geometry *out)
     out->disc_radius = g.radius;
     out->mu_theory = g.mu_theory;
     out->far_block = far_block_for(g, *p, g.nstar, g.radius);
+    out->far_group = p->precision == MM_FAR32 ? far_group_for(g, *p, g.nstar, g.radius) : 0;
     return MM_OK;
 }
 
@@ -1019,7 +1020,7 @@ int mm_map_fetch(mm_ctx *ctx, mm_map map, uint32_t *host_counts, size_t n_elems,
         st->lens_splits = M->splits;
         st->far_bound = M->far_bound;
         st->far_block = M->p.precision == MM_FAR32 ? far_block_for(M->g, M->p, M->lenses->n, M->lenses->radius) : 0;
-        st->far_group = M->p.precision == MM_FAR32 ? far_group_for(M->p, M->lenses->n) : 0;
+        st->far_group = M->p.precision == MM_FAR32 ? far_group_for(M->g, M->p, M->lenses->n, M->lenses->radius) : 0;
     }
     return MM_OK;
 }

@@ -362,22 +362,27 @@ def test_grouped_maps_are_deterministic_and_close_to_ungrouped(ctx):
     mm.mm_release_lenses(ctx, lh)
 
 
-def test_automatic_grouping_from_32768_lenses(ctx):
-    """far_group_order = -1 (the default) groups with K = 24, theta = 0.3 and leaves of 64 lenses
-    from 32768 lenses on, and not below; the grouped rays match the oracle's statement."""
+def test_automatic_grouping_follows_the_cost_model(ctx):
+    """far_group_order = -1 and far_block = 0 (the defaults): the map takes the plan that
+    mm_geometry_of reports for its lens count and disc -- here no grouping at 1e5 lenses and
+    K = 24 from 1e6 on -- and the grouped rays match the oracle's statement of that plan
+    (theta = 0.3, leaves of 64 lenses)."""
     cfg = dict(CFG_G, nrays=4.0)
-    for n, k_expected in ((32767, 0), (40000, 24)):
-        f = synth.lens_field(n, field.radius_for_nstar(n, 0.4), 29)
+    for n, k_expected in ((10 ** 5, 0), (10 ** 6, 24)):
+        r = field.radius_for_nstar(n, 0.4)
+        f = synth.lens_field(n, r, 29)
         lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
-        p = mm.params(**cfg, precision=mm.MM_FAR32, far_block=2)
-        m = mm.mm_shoot(ctx, lh, p)
+        plan = mm.mm_geometry_of(mm.params(**cfg, precision=mm.MM_FAR32, nstar=n, disc_radius=r))
+        assert plan["far_group"] == k_expected
+        m = mm.mm_shoot(ctx, lh, mm.params(**cfg, precision=mm.MM_FAR32))
         _, st = mm.mm_map_fetch(ctx, m, want_counts=False)
         mm.mm_release_map(ctx, m)
-        assert st["far_group"] == k_expected
+        assert (st["far_group"], st["far_block"]) == (plan["far_group"], plan["far_block"])
         if k_expected:
-            far = dict(order=10, ratio=0.15, block_tiles=2, group_order=24, group_theta=0.3, group_leaf=64)
+            far = dict(order=10, ratio=0.15, block_tiles=st["far_block"], group_order=24, group_theta=0.3,
+                       group_leaf=64)
             g = mm.mm_geometry_of(mm.params(**cfg))
-            ii, jj = sample_rays(g["nx"], g["ny"], 1500, 5)
+            ii, jj = sample_rays(g["nx"], g["ny"], 300, 5)
             check_rays(ctx, lh, f, cfg, far, ii, jj)
         mm.mm_release_lenses(ctx, lh)
 
