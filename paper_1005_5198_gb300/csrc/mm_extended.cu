@@ -156,14 +156,17 @@ __global__ void __launch_bounds__(256) k_gauss_rows(const unsigned *cin, const f
     for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
         const int c0 = (int)(t % cols) * kGRowOut, r0 = (int)(t / cols) * kGRows;
         __syncthreads();                                   // previous tile's outputs written; taps staged
-        for (int q = threadIdx.x; q < kGRows * W; q += blockDim.x) {
-            const int rr = q / W, x = q % W, j = r0 + rr, i = c0 - h + x;
-            float v = 0.f;
-            if (j < n && i >= 0 && i < n) {
-                const long long src = (long long)j * n + i;
-                v = FROM_COUNTS ? (float)cin[src] * inv_nrays : fin[src];
+        for (int rr = w; rr < kGRows; rr += 8) {              // warp w stages rows w, w + 8, ...
+            const int j = r0 + rr;
+            for (int x = lane; x < W; x += 32) {
+                const int i = c0 - h + x;
+                float v = 0.f;
+                if (j < n && i >= 0 && i < n) {
+                    const long long src = (long long)j * n + i;
+                    v = FROM_COUNTS ? (float)cin[src] * inv_nrays : fin[src];
+                }
+                tile[rr * S + x] = v;
             }
-            tile[rr * S + x] = v;
         }
         __syncthreads();
         float acc[kGG][8];
@@ -174,10 +177,13 @@ __global__ void __launch_bounds__(256) k_gauss_rows(const unsigned *cin, const f
 #pragma unroll
             for (int u = 0; u < 8; ++u) tile[lane * S + w * 8 * kGG + 8 * q + u] = acc[q][u];
         __syncthreads();
-        for (int q = threadIdx.x; q < kGRows * kGRowOut; q += blockDim.x) {
-            const int rr = q / kGRowOut, x = q % kGRowOut, j = r0 + rr, i = c0 + x;
-            if (j < n && i < n)
-                out[(long long)j * n + i] = (i - h >= 0 && i + h < n) ? tile[rr * S + x] : __int_as_float(0x7fc00000);
+        for (int rr = w; rr < kGRows; rr += 8) {
+            const int j = r0 + rr;
+            for (int x = lane; x < kGRowOut; x += 32) {
+                const int i = c0 + x;
+                if (j < n && i < n)
+                    out[(long long)j * n + i] = (i - h >= 0 && i + h < n) ? tile[rr * S + x] : __int_as_float(0x7fc00000);
+            }
         }
     }
 }

@@ -23,7 +23,7 @@
 namespace mm {
 namespace {
 
-// Shared-memory histograms: up to 96 KB per CTA (8 warp copies of 1024 bins per map, 64 KB);
+// Shared-memory histograms: up to 96 KB per CTA (8 warp copies of 512 bins per map, 32 KB);
 // 200 KB of an SM's shared memory shared between the CTAs of a launch.
 constexpr size_t kHistSmemMax = 96 * 1024;
 constexpr size_t kSmemPerSm = 200 * 1024;
@@ -118,7 +118,39 @@ __device__ __forceinline__ void hist_add(unsigned *h, unsigned key, unsigned lan
 // wb = min(nbins, kWarpBins) in shared memory and adds to it with plain shared-memory atomics:
 // only the lanes of one warp can collide on a bin, so no merging of equal keys is needed for the
 // common small counts. The rare larger counts go to the global histograms, merged per warp.
-constexpr int kWarpBins = 1024;
+// A thread takes four consecutive pixels of each map per step (16-byte loads; the counts come
+// from the arena, 256-byte aligned), so that several loads and table lookups are in flight; the
+// last n % 4 pixels go to the first threads of block 0.
+constexpr int kWarpBins = 512;
+
+__device__ __forceinline__ void rms_pixel(unsigned na, unsigned nb, const float2 *ta, const float2 *tb, float &qh,
+                                          float &ql, unsigned long long &both)
+{
+    if (na && nb) {
+        // d = ta[na] - tb[nb] in float-float, then d^2
+        const float2 x = ta[na], y = tb[nb];
+        float dh, dl;
+        ff_two_sum(x.x, -y.x, dh, dl);
+        dl = __fadd_rn(dl, __fsub_rn(x.y, y.y));
+        const float d = __fadd_rn(dh, dl), de = __fsub_rn(dl, __fsub_rn(d, dh));
+        const float ph = __fmul_rn(d, d);
+        const float pl = __fmaf_rn(d, d, -ph) + 2.f * d * de;
+        ff_accumulate(qh, ql, ph, pl);
+        both += 1;
+    }
+}
+
+// Count keys na, nb of one lane (in: the lane holds a pixel) into the warp's bins, or, for
+// counts of wb or more, into the global histograms.
+__device__ __forceinline__ void hist_pixel(bool in, unsigned na, unsigned nb, unsigned *sa, unsigned *sb,
+                                           unsigned *ha, unsigned *hb, long long wb, unsigned lane)
+{
+    if (in && na < (unsigned)wb) atomicAdd(sa + na, 1u);
+    if (in && nb < (unsigned)wb) atomicAdd(sb + nb, 1u);
+    const bool big_a = in && na >= (unsigned)wb, big_b = in && nb >= (unsigned)wb;
+    if (__any_sync(0xffffffffu, big_a)) hist_add(ha, big_a ? na : kNoKey, lane);
+    if (__any_sync(0xffffffffu, big_b)) hist_add(hb, big_b ? nb : kNoKey, lane);
+}
 
 __global__ void __launch_bounds__(256) k_rms_hist(const unsigned *a, const unsigned *b, long long n, const float2 *ta,
                                                   const float2 *tb, long long nbins, unsigned *ha, unsigned *hb,
@@ -132,29 +164,29 @@ __global__ void __launch_bounds__(256) k_rms_hist(const unsigned *a, const unsig
     __syncthreads();
     float qh = 0.f, ql = 0.f;                                 // float-float sum of (Delta m_a - Delta m_b)^2 / 6.25
     unsigned long long both = 0;
-    // warp-uniform trip count: the lanes of a warp take consecutive pixels, those past n hold no key
+    const uint4 *a4 = reinterpret_cast<const uint4 *>(a), *b4 = reinterpret_cast<const uint4 *>(b);
+    const long long n4 = n / 4;
+    // warp-uniform trip count: the lanes of a warp take consecutive groups, those past n4 hold no key
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long w0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31u); w0 < n; w0 += stride) {
+    for (long long w0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31u); w0 < n4; w0 += stride) {
         const long long k = w0 + lane;
+        const bool in = k < n4;
+        const uint4 va = in ? a4[k] : make_uint4(0u, 0u, 0u, 0u), vb = in ? b4[k] : make_uint4(0u, 0u, 0u, 0u);
+        rms_pixel(va.x, vb.x, ta, tb, qh, ql, both);
+        rms_pixel(va.y, vb.y, ta, tb, qh, ql, both);
+        rms_pixel(va.z, vb.z, ta, tb, qh, ql, both);
+        rms_pixel(va.w, vb.w, ta, tb, qh, ql, both);
+        hist_pixel(in, va.x, vb.x, sa, sb, ha, hb, wb, lane);
+        hist_pixel(in, va.y, vb.y, sa, sb, ha, hb, wb, lane);
+        hist_pixel(in, va.z, vb.z, sa, sb, ha, hb, wb, lane);
+        hist_pixel(in, va.w, vb.w, sa, sb, ha, hb, wb, lane);
+    }
+    if (blockIdx.x == 0 && warp == 0) {                        // the last n % 4 pixels
+        const long long k = 4 * n4 + lane;
         const bool in = k < n;
-        const unsigned na = in ? a[k] : kNoKey, nb = in ? b[k] : kNoKey;
-        if (in && na && nb) {
-            // d = ta[na] - tb[nb] in float-float, then d^2
-            const float2 x = ta[na], y = tb[nb];
-            float dh, dl;
-            ff_two_sum(x.x, -y.x, dh, dl);
-            dl = __fadd_rn(dl, __fsub_rn(x.y, y.y));
-            const float d = __fadd_rn(dh, dl), de = __fsub_rn(dl, __fsub_rn(d, dh));
-            const float ph = __fmul_rn(d, d);
-            const float pl = __fmaf_rn(d, d, -ph) + 2.f * d * de;
-            ff_accumulate(qh, ql, ph, pl);
-            both += 1;
-        }
-        if (in && na < (unsigned)wb) atomicAdd(sa + na, 1u);
-        if (in && nb < (unsigned)wb) atomicAdd(sb + nb, 1u);
-        const bool big_a = in && na >= (unsigned)wb, big_b = in && nb >= (unsigned)wb;
-        if (__any_sync(0xffffffffu, big_a)) hist_add(ha, big_a ? na : kNoKey, lane);
-        if (__any_sync(0xffffffffu, big_b)) hist_add(hb, big_b ? nb : kNoKey, lane);
+        const unsigned na = in ? a[k] : 0u, nb = in ? b[k] : 0u;
+        rms_pixel(na, nb, ta, tb, qh, ql, both);
+        hist_pixel(in, na, nb, sa, sb, ha, hb, wb, lane);
     }
     double sq = 6.25 * ((double)qh + (double)ql);              // Delta m differences carry the factor -2.5
     for (int o = 16; o > 0; o >>= 1) {
@@ -317,7 +349,7 @@ extern "C" int mm_map_compare(mm_ctx *ctx, mm_map a, mm_map b, mm_compare *out)
                                   (int)kHistSmemMax)) != cudaSuccess)
         return cuda_fail(e, "k_rms_hist shared memory");
     {
-        const int per_sm = std::max(1, std::min(4, (int)(kSmemPerSm / std::max<size_t>(smem, 1))));
+        const int per_sm = std::max(1, std::min(6, (int)(kSmemPerSm / std::max<size_t>(smem, 1))));
         k_rms_hist<<<std::max(1, std::min(per_sm * ctx->sms, (int)((n + 255) / 256))), 256, smem, s>>>(
             A->counts, B->counts, n, tab, tab + nbins, nbins, hist, hist + nbins, d_sum);
     }
