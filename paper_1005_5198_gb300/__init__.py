@@ -265,9 +265,10 @@ def _stats_dict(st: mm_stats) -> dict:
 
 
 def mm_map_restore(ctx: Ctx, lenses: int, p: mm_params, counts: np.ndarray, stats: dict) -> int:
-    """A new map from a checkpoint (the counts and stats dict of mm_map_fetch)."""
+    """A new map from a checkpoint (the counts and stats dict of mm_map_fetch; fields the dict lacks
+    are 0)."""
     c = np.ascontiguousarray(counts, dtype=np.uint32).ravel()
-    st = mm_stats(**{k: stats[k] for k, _ in mm_stats._fields_})
+    st = mm_stats(**{k: stats.get(k, 0) for k, _ in mm_stats._fields_})
     out = C.c_uint64()
     _check(_load().mm_map_restore(ctx.handle, lenses, C.byref(p), c.ctypes.data_as(C.POINTER(C.c_uint32)), c.size,
                                   C.byref(st), C.byref(out)), "mm_map_restore")
