@@ -418,7 +418,7 @@ def hbm_peak_gbs():
         return 6800.0, "fallback"
 
 
-def downstream_phase(mm, ctx, side=8192):
+def downstream_phase(mm, ctx, side=8192, fma_peak_per_s=None):
     """The rows after the map: the map statistics of Sect. 3.1 (mm_map_compare: RMS of Delta m and the
     K-S test) and an extended source's light curve (mm_map_lightcurve: the map convolved with a Gaussian
     or disc profile on the device, then sampled along a track), on two side^2 maps (256 MiB of counts
@@ -461,7 +461,12 @@ def downstream_phase(mm, ctx, side=8192):
            "hbm_peak_gbs": peak, "hbm_peak_source": peak_src,
            "compare": line(t_cmp, 8 * npix, {"rms_dm": st["rms_dm"], "ks_p": st["ks_p"]}),
            "lightcurve_gaussian": line(t_g, 16 * npix, {"size_re": g_size, "taps_per_pass": 2 * h + 1,
-                                                        "points": 1000}),
+                                                        "points": 1000,
+                                                        # the two passes' FMAs (one per tap and output)
+                                                        # against the FP32 FMA peak: this kernel pair is
+                                                        # bound by arithmetic before memory
+                                                        "fma_frac": 2 * (2 * h + 1) * npix / t_g
+                                                                    / (fma_peak_per_s or 1.0)}),
            "lightcurve_disc": line(t_d, 8 * npix, {"size_re": d_size, "radius_pixels": hd, "points": 1000})}
     mm.mm_release_map(ctx, ma)
     mm.mm_release_map(ctx, mb)
@@ -722,7 +727,7 @@ def main():
         import paper_1005_5198_gb300 as mm
         mm.build()
         ctx = mm.mm_init(0)
-        print(json.dumps(downstream_phase(mm, ctx)))
+        print(json.dumps(downstream_phase(mm, ctx, fma_peak_per_s=lane_peak_per_s(device_sms(0)))))
         mm.mm_destroy(ctx)
         return 0
     if args.profile_case:
@@ -823,7 +828,7 @@ def main():
     if not args.no_extras and world == 1:
         extra["config2_exact"] = config2_phase(mm, ctx, sms)
         extra["far_field"] = far_phase(mm, ctx, lh, sum(kern_ms) / len(kern_ms))
-        extra["downstream"] = downstream_phase(mm, ctx)
+        extra["downstream"] = downstream_phase(mm, ctx, fma_peak_per_s=lane_peak_per_s(sms))
         extra["batch"] = config3_phase(mm, ctx, sms)
         extra["batch_scaled"] = scaled_batch_phase(mm, ctx, sms)
         extra["serving"] = config4_phase(mm, ctx, extra["batch"]["batched_interactions_per_s"], args)
