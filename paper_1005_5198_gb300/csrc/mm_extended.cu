@@ -74,9 +74,9 @@ constexpr size_t kTileSmemMax = 48 * 1024;             // dynamic shared memory 
 
 // Gaussian passes, register-blocked: a thread owns kGG groups of 8 consecutive outputs along the
 // pass direction and runs the taps in chunks of 8. For a chunk it loads the 15 inputs that its 8
-// outputs need into registers once and makes 64 FMAs from them, so shared memory supplies about one
-// word per 4 FMAs instead of one or more per FMA. Every output still adds its taps in order
-// (fmaf, tap 0 first), exactly as k_gauss_pass does.
+// outputs need into registers once and makes 64 FMAs from them (32 packed f32x2 instructions), so
+// shared memory supplies about one word per 4 FMAs instead of one or more per FMA. Every output
+// still adds its taps in order (a correctly rounded FMA each, tap 0 first), exactly as k_gauss_pass.
 constexpr int kGG = 2;                                  // groups of 8 outputs per thread
 constexpr int kGRows = 32;                              // row pass: tile rows, one per lane
 constexpr int kGRowOut = 8 * kGG * 8;                   // row pass: outputs per tile row (8 warps)
@@ -99,29 +99,30 @@ __host__ __device__ inline size_t disc_smem(int H)
 }
 
 // acc[u] += sum over taps k of [k0, k0 + 8) of g[k] x[u + k - k0], tap by tap, for the 8 outputs
-// whose inputs start at x (stride st between consecutive inputs).
-__device__ __forceinline__ void gauss_chunk8(const float *gk, const float *x, int st, float *acc)
+// whose inputs start at x (stride st between consecutive inputs). The outputs go in pairs through
+// packed f32x2 FMAs (acc2[p] holds outputs 2p, 2p + 1; each lane rounds as fmaf does).
+__device__ __forceinline__ void gauss_chunk8(const float *gk, const float *x, int st, float2 *acc2)
 {
     float v[15];
 #pragma unroll
     for (int q = 0; q < 15; ++q) v[q] = x[q * st];
 #pragma unroll
     for (int kk = 0; kk < 8; ++kk) {
-        const float w = gk[kk];
+        const float2 w = make_float2(gk[kk], gk[kk]);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc[u] = fmaf(w, v[u + kk], acc[u]);
+        for (int p = 0; p < 4; ++p) acc2[p] = __ffma2_rn(w, make_float2(v[2 * p + kk], v[2 * p + 1 + kk]), acc2[p]);
     }
 }
 
 // The taps of one thread's groups over a staged tile: x0 = first input of the thread's first group,
 // gstep = distance between its groups, st = distance between consecutive inputs.
 __device__ __forceinline__ void gauss_taps(const float *gs, int taps, const float *x0, int gstep, int st,
-                                           float (&acc)[kGG][8])
+                                           float2 (&acc)[kGG][4])
 {
 #pragma unroll
     for (int q = 0; q < kGG; ++q)
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc[q][u] = 0.f;
+        for (int p = 0; p < 4; ++p) acc[q][p] = make_float2(0.f, 0.f);
     int k0 = 0;
     for (; k0 + 8 <= taps; k0 += 8) {
         float gk[8];
@@ -131,11 +132,13 @@ __device__ __forceinline__ void gauss_taps(const float *gs, int taps, const floa
         for (int q = 0; q < kGG; ++q) gauss_chunk8(gk, x0 + q * gstep + k0 * st, st, acc[q]);
     }
     for (; k0 < taps; ++k0) {                              // the last taps, one at a time
-        const float w = gs[k0];
+        const float2 w = make_float2(gs[k0], gs[k0]);
 #pragma unroll
         for (int q = 0; q < kGG; ++q)
 #pragma unroll
-            for (int u = 0; u < 8; ++u) acc[q][u] = fmaf(w, x0[q * gstep + (u + k0) * st], acc[q][u]);
+            for (int p = 0; p < 4; ++p)
+                acc[q][p] = __ffma2_rn(w, make_float2(x0[q * gstep + (2 * p + k0) * st], x0[q * gstep + (2 * p + 1 + k0) * st]),
+                                       acc[q][p]);
     }
 }
 
@@ -169,13 +172,16 @@ __global__ void __launch_bounds__(256) k_gauss_rows(const unsigned *cin, const f
             }
         }
         __syncthreads();
-        float acc[kGG][8];
+        float2 acc[kGG][4];
         gauss_taps(gs, taps, tile + lane * S + w * 8 * kGG, 8, 1, acc);
         __syncthreads();                                   // every thread has read the inputs
 #pragma unroll
         for (int q = 0; q < kGG; ++q)
 #pragma unroll
-            for (int u = 0; u < 8; ++u) tile[lane * S + w * 8 * kGG + 8 * q + u] = acc[q][u];
+            for (int p = 0; p < 4; ++p) {
+                tile[lane * S + w * 8 * kGG + 8 * q + 2 * p] = acc[q][p].x;
+                tile[lane * S + w * 8 * kGG + 8 * q + 2 * p + 1] = acc[q][p].y;
+            }
         __syncthreads();
         for (int rr = w; rr < kGRows; rr += 8) {
             const int j = r0 + rr;
@@ -207,7 +213,7 @@ __global__ void __launch_bounds__(256) k_gauss_cols(const float *fin, float *out
             tile[q] = (j >= 0 && j < n && i < n) ? fin[(long long)j * n + i] : 0.f;
         }
         __syncthreads();
-        float acc[kGG][8];
+        float2 acc[kGG][4];
         gauss_taps(gs, taps, tile + (w * 8 * kGG) * kGCols + lane, 8 * kGCols, kGCols, acc);
         const int i = c0 + lane;
 #pragma unroll
@@ -215,8 +221,8 @@ __global__ void __launch_bounds__(256) k_gauss_cols(const float *fin, float *out
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int j = r0 + w * 8 * kGG + 8 * q + u;
-                if (i < n && j < n)
-                    out[(long long)j * n + i] = (j - h >= 0 && j + h < n) ? acc[q][u] : __int_as_float(0x7fc00000);
+                const float a = (u & 1) ? acc[q][u >> 1].y : acc[q][u >> 1].x;
+                if (i < n && j < n) out[(long long)j * n + i] = (j - h >= 0 && j + h < n) ? a : __int_as_float(0x7fc00000);
             }
     }
 }
