@@ -243,7 +243,8 @@ int orc_rays(const orc_params *P, const double *lx, const double *ly, const doub
  *     l < P, k < K, so the cell adds at most
  *     (M_C / |D|) E(x, y), M_C = sum of its masses,
  *     E = (x / (1 - y))^P / (1 - x - y) + sum_{l<P} x^l sum_{k>=K} C(l+k, k) y^k,
- *     to the bound of the lenses taken one by one.
+ *     to the bound of the lenses taken one by one; the inner sum takes its first four terms
+ *     and bounds the rest by a geometric series (binom_tail).
  * ======================================================================== */
 
 #define TREE_LMAX 16
@@ -505,8 +506,10 @@ static int far_block_build(const orc_far_params *F, const orc_geometry_t *G, con
     return 0;
 }
 
-/* sum_{k>=K} C(l+k, k) y^k, summed term by term; the terms beyond the last one kept
- * fall off faster than a geometric series of the last ratio, which bounds them. */
+/* sum_{k>=K} C(l+k, k) y^k: the first four terms exactly, then the rest by a geometric series
+ * of the ratio of the last term kept to the one before -- the ratios y (l+k+1)/(k+1) fall with
+ * k, so every later term is at most that ratio times the one before it. When that ratio is not
+ * below 1 yet, more terms are kept until it is. */
 static double binom_tail(int l, int K, double y, const double *binom)
 {
     double term = binom[(l + K) * 130 + K] * pow(y, K);
@@ -515,7 +518,7 @@ static double binom_tail(int l, int K, double y, const double *binom)
         sum += term;
         const double r = y * (double)(l + k + 1) / (double)(k + 1);       /* term(k+1) / term(k) */
         term *= r;
-        if (r < 1.0 && term / (1.0 - r) <= 1e-17 * sum) return sum + term / (1.0 - r);
+        if (k >= K + 3 && r < 1.0) return sum + term / (1.0 - r);
     }
     return INFINITY;
 }

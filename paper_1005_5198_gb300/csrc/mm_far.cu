@@ -713,17 +713,17 @@ __device__ __forceinline__ Cx cinv(Cx a)
     return {__ddiv_rn(a.r, d), __ddiv_rn(-a.i, d)};
 }
 
-// sum_{k>=K} C(l+k, k) y^k, term by term; the terms after the last one kept fall off faster
-// than a geometric series of the last ratio, which bounds them (as the oracle sums it).
-__device__ double group_tail(int l, int K, double y, const double *binom)
+// sum_{k>=K} C(l+k, k) y^k (the oracle's rule): the first four terms exactly, the rest bounded by a
+// geometric series of the last ratio y (l+k+1)/(k+1), which falls with k; yK = y^K.
+__device__ double group_tail(int l, int K, double y, double yK, const double *binom)
 {
-    double term = binom[(l + K) * kBinomN + K] * pow(y, (double)K);
+    double term = binom[(l + K) * kBinomN + K] * yK;
     double sum = 0.0;
     for (int k = K; k < K + 100000; ++k) {
         sum += term;
         const double r = y * (double)(l + k + 1) / (double)(k + 1);
         term *= r;
-        if (r < 1.0 && term / (1.0 - r) <= 1e-17 * sum) return sum + term / (1.0 - r);
+        if (k >= K + 3 && r < 1.0) return sum + term / (1.0 - r);
     }
     return __longlong_as_double(0x7ff0000000000000LL);       // +inf: no bound
 }
@@ -798,10 +798,10 @@ __global__ void __launch_bounds__(kGroupThreads) k_far_group(const MapDesc M, co
                                 pw = cmul(pw, u);
                             }
                         }
-                        const double x = F.rho64 / dabs, y = rc / dabs;
+                        const double x = F.rho64 / dabs, y = rc / dabs, yK = pow(y, (double)K);
                         double e = pow(x / (1.0 - y), (double)P) / (1.0 - x - y), xl = 1.0;
                         for (int l = 0; l < P; ++l) {
-                            e += xl * group_tail(l, K, y, T.binom);
+                            e += xl * group_tail(l, K, y, yK, T.binom);
                             xl *= x;
                         }
                         bnd += T.mass[v] / dabs * e;
