@@ -991,12 +991,15 @@ constexpr double kNearCost = 0.81e-12;       // seconds per ray x near lens
 constexpr double kBlockCost = 2.0e-9;        // seconds per block
 
 // Grouped setup: the lens-tree walk of a block prices its grouped cells (about kGroupCells per
-// tree level, each P (2K + 120) FP64 operations with its bound) and the lenses it takes one by
-// one (those of leaves within (rho + r_leaf) / theta + r_leaf of the block, 8 P operations each)
-// at kGroupOpCost seconds per operation, the walk's measured rate over the whole GPU (GB300:
-// about 11 us of GPU time per block on the Fig. 1 geometry with 1e5 to 1e8 lenses).
+// tree level, each P (2K + 24) FP64 operations with its bound) at kGroupCellCost and the lenses it
+// takes one by one (those of leaves within (rho + r_leaf) / theta + r_leaf of the block, 8 P
+// operations each) at kGroupLensCost seconds per operation: the walk's rates over the whole GPU,
+// fitted to GB300 timings of the Fig. 1 geometry with 1e5 to 1e8 lenses at blocks of 8 to 32 tiles
+// (about 1.5 to 3 us of GPU time per block), with grouping found slower at 1e5 lenses and faster
+// from 3e5 on.
 constexpr double kGroupCells = 50.0;
-constexpr double kGroupOpCost = 1.0e-11;
+constexpr double kGroupCellCost = 1.4e-11;
+constexpr double kGroupLensCost = 8.2e-13;
 constexpr int kAutoGroupOrder = 24;          // K of the automatic choice (bound well below 1e-8 R_E)
 
 // Modelled time of a map's far field with block side bt and multipole order K (0: no grouping).
@@ -1014,8 +1017,8 @@ static double far_cost(const Geo &g, const mm_params &p, long long nstar, double
         const double r_leaf = density > 0.0 ? std::sqrt(p.far_group_leaf / density) * 0.7071 : 0.0;
         const double reach = (rho + r_leaf) / p.far_group_theta + r_leaf;
         const double alone = std::min((double)nstar, density * M_PI * reach * reach);
-        setup = blocks * (kGroupCells * levels * p.far_order * (2.0 * K + 120.0) + alone * 8.0 * p.far_order) *
-                kGroupOpCost;
+        setup = blocks * (kGroupCells * levels * p.far_order * (2.0 * K + 24.0) * kGroupCellCost +
+                          alone * 8.0 * p.far_order * kGroupLensCost);
     }
     return setup + rays * near * kNearCost + blocks * kBlockCost;
 }
