@@ -16,6 +16,7 @@
 #include <cmath>
 #include <vector>
 
+#include "mm_async.cuh"
 #include "mm_ctx.h"
 
 namespace mm {
@@ -69,14 +70,17 @@ __global__ void k_disc(const unsigned *cin, float *out, int n, const int *span, 
 // ---- tiled forms of the passes above: the same per-pixel sums in the same order ----
 
 constexpr int kDiscTileW = 64, kDiscTileH = 32;        // disc: 64 x 32 outputs per CTA
-constexpr size_t kTileSmemMax = 48 * 1024;             // dynamic shared memory of a tiled CTA (no opt-in);
-                                                       // wider supports take the untiled kernels
+constexpr size_t kTileSmemMax = 48 * 1024;             // dynamic shared memory of a tiled disc CTA (no opt-in);
+                                                       // wider supports take the untiled kernel
+constexpr size_t kGaussSmemMax = 95 * 1024;            // a double-buffered Gaussian CTA (rows: h <= 123,
+                                                       // columns: h <= 124); wider take the untiled kernel
 
 // Gaussian passes, register-blocked: a thread owns kGG groups of 8 consecutive outputs along the
 // pass direction and runs the taps in chunks of 8. For a chunk it loads the 15 inputs that its 8
 // outputs need into registers once and makes 64 FMAs from them (32 packed f32x2 instructions), so
 // shared memory supplies about one word per 4 FMAs instead of one or more per FMA. Every output
 // still adds its taps in order (a correctly rounded FMA each, tap 0 first), exactly as k_gauss_pass.
+// A CTA holds two tiles: while it computes one, the next one's inputs arrive by cp.async.
 constexpr int kGG = 2;                                  // groups of 8 outputs per thread
 constexpr int kGRows = 32;                              // row pass: tile rows, one per lane
 constexpr int kGRowOut = 8 * kGG * 8;                   // row pass: outputs per tile row (8 warps)
@@ -85,13 +89,15 @@ constexpr int kGCols = 32;                              // column pass: tile col
 
 __host__ __device__ inline int gauss_row_stride(int h) { return (kGRowOut + 2 * h) | 1; }   // odd: rows hit distinct banks
 __host__ __device__ inline int gauss_taps_padded(int h) { return (2 * h + 1 + 7) & ~7; }
+__host__ __device__ inline int gauss_row_tile(int h) { return kGRows * gauss_row_stride(h); }
+__host__ __device__ inline int gauss_col_tile(int h) { return (kGColOut + 2 * h) * kGCols; }
 __host__ __device__ inline size_t gauss_row_smem(int h)
 {
-    return ((size_t)gauss_taps_padded(h) + (size_t)kGRows * gauss_row_stride(h)) * 4;
+    return ((size_t)gauss_taps_padded(h) + 2 * (size_t)gauss_row_tile(h)) * 4;
 }
 __host__ __device__ inline size_t gauss_col_smem(int h)
 {
-    return ((size_t)gauss_taps_padded(h) + (size_t)(kGColOut + 2 * h) * kGCols) * 4;
+    return ((size_t)gauss_taps_padded(h) + 2 * (size_t)gauss_col_tile(h)) * 4;
 }
 __host__ __device__ inline size_t disc_smem(int H)
 {
@@ -142,36 +148,54 @@ __device__ __forceinline__ void gauss_taps(const float *gs, int taps, const floa
     }
 }
 
-// Row pass (dir 0 of k_gauss_pass): a CTA stages rows [r0, r0 + 32) x columns [c0 - h, c0 + 128 + h)
-// (the inputs, as floats) and the taps; lane l takes row r0 + l, warp w outputs c0 + 16 w .. + 16.
-// The outputs go back through shared memory so that the global stores run along rows.
+// Row pass (dir 0 of k_gauss_pass): a tile is rows [r0, r0 + 32) x columns [c0 - h, c0 + 128 + h)
+// (the inputs, as floats; zeros outside the map); lane l takes row r0 + l, warp w outputs
+// c0 + 16 w .. + 16. The outputs go back through the tile's shared memory so that the global stores
+// run along rows. Tiles t, t + gridDim.x, ...; each thread copies the same elements of every tile
+// (4-byte cp.async, zero-filled outside the map) and, from counts, converts those it copied once
+// they have landed.
 template <bool FROM_COUNTS>
 __global__ void __launch_bounds__(256) k_gauss_rows(const unsigned *cin, const float *fin, float *out, int n,
                                                     const float *g, int h, float inv_nrays)
 {
     extern __shared__ float sm[];
     const int taps = 2 * h + 1, S = gauss_row_stride(h), W = kGRowOut + 2 * h;
-    float *const gs = sm, *const tile = sm + gauss_taps_padded(h);
+    float *const gs = sm;
+    float *const buf0 = sm + gauss_taps_padded(h), *const buf1 = buf0 + gauss_row_tile(h);
     for (int k = threadIdx.x; k < taps; k += blockDim.x) gs[k] = g[k];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int cols = (n + kGRowOut - 1) / kGRowOut, rows = (n + kGRows - 1) / kGRows;
     const long long tiles = (long long)cols * rows;
-    for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+    auto stage = [&](long long t, float *tile) {
         const int c0 = (int)(t % cols) * kGRowOut, r0 = (int)(t / cols) * kGRows;
-        __syncthreads();                                   // previous tile's outputs written; taps staged
         for (int rr = w; rr < kGRows; rr += 8) {              // warp w stages rows w, w + 8, ...
             const int j = r0 + rr;
             for (int x = lane; x < W; x += 32) {
                 const int i = c0 - h + x;
-                float v = 0.f;
-                if (j < n && i >= 0 && i < n) {
-                    const long long src = (long long)j * n + i;
-                    v = FROM_COUNTS ? (float)cin[src] * inv_nrays : fin[src];
-                }
-                tile[rr * S + x] = v;
+                const bool ok = j < n && i >= 0 && i < n;
+                const long long src = ok ? (long long)j * n + i : 0;
+                cp_async4(tile + rr * S + x, FROM_COUNTS ? (const void *)(cin + src) : (const void *)(fin + src),
+                          ok ? 4u : 0u);
             }
         }
-        __syncthreads();
+        cp_async_commit();
+    };
+    if (blockIdx.x < tiles) stage(blockIdx.x, buf0);
+    int b = 0;
+    for (long long t = blockIdx.x; t < tiles; t += gridDim.x, b ^= 1) {
+        float *const tile = b ? buf1 : buf0;
+        const long long tn = t + gridDim.x;
+        if (tn < tiles) {                                  // the other buffer was released at the end of
+            stage(tn, b ? buf0 : buf1);                    // the previous tile
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        if (FROM_COUNTS)                                   // the elements this thread copied, now landed
+            for (int rr = w; rr < kGRows; rr += 8)
+                for (int x = lane; x < W; x += 32)
+                    tile[rr * S + x] = (float)__float_as_uint(tile[rr * S + x]) * inv_nrays;
+        __syncthreads();                                   // tile t staged; taps staged
         float2 acc[kGG][4];
         gauss_taps(gs, taps, tile + lane * S + w * 8 * kGG, 8, 1, acc);
         __syncthreads();                                   // every thread has read the inputs
@@ -183,6 +207,7 @@ __global__ void __launch_bounds__(256) k_gauss_rows(const unsigned *cin, const f
                 tile[lane * S + w * 8 * kGG + 8 * q + 2 * p + 1] = acc[q][p].y;
             }
         __syncthreads();
+        const int c0 = (int)(t % cols) * kGRowOut, r0 = (int)(t / cols) * kGRows;
         for (int rr = w; rr < kGRows; rr += 8) {
             const int j = r0 + rr;
             for (int x = lane; x < kGRowOut; x += 32) {
@@ -191,30 +216,48 @@ __global__ void __launch_bounds__(256) k_gauss_rows(const unsigned *cin, const f
                     out[(long long)j * n + i] = (i - h >= 0 && i + h < n) ? tile[rr * S + x] : __int_as_float(0x7fc00000);
             }
         }
+        __syncthreads();                                   // the tile's buffer is free for tile t + 2 gridDim.x
     }
 }
 
-// Column pass (dir 1): a CTA stages rows [r0 - h, r0 + 128 + h) of 32 columns; lane l takes column
-// c0 + l, warp w the output rows r0 + 16 w .. + 16 (stores along rows of 32 columns).
+// Column pass (dir 1): a tile is rows [r0 - h, r0 + 128 + h) of 32 columns; lane l takes column
+// c0 + l, warp w the output rows r0 + 16 w .. + 16 (stores along rows of 32 columns). Tiles and
+// copies as in the row pass.
 __global__ void __launch_bounds__(256) k_gauss_cols(const float *fin, float *out, int n, const float *g, int h)
 {
     extern __shared__ float sm[];
-    const int taps = 2 * h + 1;
-    float *const gs = sm, *const tile = sm + gauss_taps_padded(h);      // taps, then [(128 + 2h) x 32]
+    const int taps = 2 * h + 1, E = gauss_col_tile(h);
+    float *const gs = sm;
+    float *const buf0 = sm + gauss_taps_padded(h), *const buf1 = buf0 + E;   // [(128 + 2h) x 32] each
     for (int k = threadIdx.x; k < taps; k += blockDim.x) gs[k] = g[k];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int cols = (n + kGCols - 1) / kGCols, rows = (n + kGColOut - 1) / kGColOut;
     const long long tiles = (long long)cols * rows;
-    for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+    auto stage = [&](long long t, float *tile) {
         const int c0 = (int)(t % cols) * kGCols, r0 = (int)(t / cols) * kGColOut;
-        __syncthreads();
-        for (int q = threadIdx.x; q < (kGColOut + 2 * h) * kGCols; q += blockDim.x) {
-            const int j = r0 - h + q / kGCols, i = c0 + q % kGCols;
-            tile[q] = (j >= 0 && j < n && i < n) ? fin[(long long)j * n + i] : 0.f;
+        const int i = c0 + lane;
+        for (int q = threadIdx.x; q < E; q += blockDim.x) {   // row q / 32, column lane (blockDim 256)
+            const int j = r0 - h + q / kGCols;
+            const bool ok = j >= 0 && j < n && i < n;
+            cp_async4(tile + q, fin + (ok ? (long long)j * n + i : 0), ok ? 4u : 0u);
+        }
+        cp_async_commit();
+    };
+    if (blockIdx.x < tiles) stage(blockIdx.x, buf0);
+    int b = 0;
+    for (long long t = blockIdx.x; t < tiles; t += gridDim.x, b ^= 1) {
+        float *const tile = b ? buf1 : buf0;
+        const long long tn = t + gridDim.x;
+        if (tn < tiles) {
+            stage(tn, b ? buf0 : buf1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
         float2 acc[kGG][4];
         gauss_taps(gs, taps, tile + (w * 8 * kGG) * kGCols + lane, 8 * kGCols, kGCols, acc);
+        const int c0 = (int)(t % cols) * kGCols, r0 = (int)(t / cols) * kGColOut;
         const int i = c0 + lane;
 #pragma unroll
         for (int q = 0; q < kGG; ++q)
@@ -224,6 +267,7 @@ __global__ void __launch_bounds__(256) k_gauss_cols(const float *fin, float *out
                 const float a = (u & 1) ? acc[q][u >> 1].y : acc[q][u >> 1].x;
                 if (i < n && j < n) out[(long long)j * n + i] = (j - h >= 0 && j + h < n) ? a : __int_as_float(0x7fc00000);
             }
+        __syncthreads();                                   // every thread has read the tile
     }
 }
 
@@ -366,15 +410,32 @@ int convolve(mm_ctx *ctx, const MapObj &M, int profile, double size_re, float *d
         if (rc) return rc;
         if ((e = cudaMemcpyAsync(dg, g.data(), g.size() * sizeof(float), cudaMemcpyHostToDevice, s)) == cudaSuccess) {
             const size_t srow = gauss_row_smem(h), scol = gauss_col_smem(h);
-            if (srow <= kTileSmemMax)
-                k_gauss_rows<true><<<grid, 256, srow, s>>>(M.counts, nullptr, tmp, n, dg, h, inv_nrays);
-            else
+            // tiled passes: as many CTAs as fit the SMs at once (each loops over its tiles)
+            auto resident = [&](const void *fn, size_t smem, long long tiles) {
+                int per_sm = 1;
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem) != cudaSuccess) per_sm = 1;
+                return (int)std::max(1LL, std::min(tiles, (long long)std::max(1, per_sm) * ctx->sms));
+            };
+            if (srow <= kGaussSmemMax) {
+                const void *fn = (const void *)k_gauss_rows<true>;
+                e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGaussSmemMax);
+                const long long tiles = (long long)((n + kGRowOut - 1) / kGRowOut) * ((n + kGRows - 1) / kGRows);
+                if (e == cudaSuccess)
+                    k_gauss_rows<true><<<resident(fn, srow, tiles), 256, srow, s>>>(M.counts, nullptr, tmp, n, dg, h,
+                                                                                  inv_nrays);
+            } else {
                 k_gauss_pass<true><<<grid, 256, 0, s>>>(M.counts, nullptr, tmp, n, dg, h, 0, inv_nrays);
-            if (scol <= kTileSmemMax)
-                k_gauss_cols<<<grid, 256, scol, s>>>(tmp, dst, n, dg, h);
-            else
+            }
+            if (e == cudaSuccess && scol <= kGaussSmemMax) {
+                const void *fn = (const void *)k_gauss_cols;
+                e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGaussSmemMax);
+                const long long tiles = (long long)((n + kGCols - 1) / kGCols) * ((n + kGColOut - 1) / kGColOut);
+                if (e == cudaSuccess)
+                    k_gauss_cols<<<resident(fn, scol, tiles), 256, scol, s>>>(tmp, dst, n, dg, h);
+            } else if (e == cudaSuccess) {
                 k_gauss_pass<false><<<grid, 256, 0, s>>>(nullptr, tmp, dst, n, dg, h, 1, 1.0f);
-            e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         }
         ctx->arena.free(dg);

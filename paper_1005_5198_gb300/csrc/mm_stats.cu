@@ -18,15 +18,21 @@
 #include <algorithm>
 #include <cmath>
 
+#include "mm_async.cuh"
 #include "mm_ctx.h"
 
 namespace mm {
 namespace {
 
-// Shared-memory histograms: up to 96 KB per CTA (8 warp copies of 512 bins per map, 32 KB);
-// 200 KB of an SM's shared memory shared between the CTAs of a launch.
-constexpr size_t kHistSmemMax = 96 * 1024;
-constexpr size_t kSmemPerSm = 200 * 1024;
+// The comparison reads both maps once (k_compare), streaming them through shared memory in chunks
+// of kCmpChunk bytes per map with bulk copies, kCmpStages chunks in flight per CTA; a chunk's pixels
+// are then read from shared memory with 16-byte loads. Histograms: per-warp copies of the bins below
+// kWarpBins in shared memory (8 warps x 2 maps x 512 bins, 32 KB).
+constexpr int kCmpThreads = 256;
+constexpr int kCmpStages = 4;
+constexpr int kCmpChunk = 4096;
+constexpr int kWarpBins = 512;
+constexpr size_t kCmpSmem = (size_t)kCmpStages * 2 * kCmpChunk + 64 + (size_t)8 * 2 * kWarpBins * 4;
 
 struct StatSums {
     double sum_sq;                 // sum of (Delta m_a - Delta m_b)^2 over pixels counted in both maps
@@ -34,50 +40,28 @@ struct StatSums {
     unsigned long long zero_a, zero_b;
     unsigned long long sum_a, sum_b;
     unsigned int max_count;
-    int pad;
+    unsigned int fault;            // a copy into shared memory did not complete in time
     long long ks_num;              // max_k |c_a(k) n_b - c_b(k) n_a|
+    unsigned long long over_a, over_b;   // pixels with counts of nbins or more (sent to the lists)
 };
 
-// Pass 1 over both maps: sums, empty pixels and the largest count (no logarithms).
-__global__ void k_scan_stats(const unsigned *a, const unsigned *b, long long n, StatSums *out)
+// Delta m up to the factor -2.5 of a count k >= 1 of a map with N_rays = 10^lr,
+// log10(k) - lr, as a float-float pair (hi, lo) of its FP64 value: the RMS then forms the
+// per-pixel differences in FP32 arithmetic (the FP64 pipe runs at 1/64 of the FP32 rate).
+__device__ __forceinline__ float2 log_pair(unsigned k, double lr)
 {
-    unsigned long long za = 0, zb = 0, sa = 0, sb = 0;
-    unsigned mx = 0;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-        const unsigned na = a[k], nb = b[k];
-        sa += na;
-        sb += nb;
-        mx = max(mx, max(na, nb));
-        za += na == 0u;
-        zb += nb == 0u;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        za += __shfl_down_sync(0xffffffffu, za, o);
-        zb += __shfl_down_sync(0xffffffffu, zb, o);
-        sa += __shfl_down_sync(0xffffffffu, sa, o);
-        sb += __shfl_down_sync(0xffffffffu, sb, o);
-        mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&out->zero_a, za);
-        atomicAdd(&out->zero_b, zb);
-        atomicAdd(&out->sum_a, sa);
-        atomicAdd(&out->sum_b, sb);
-        atomicMax(&out->max_count, mx);
-    }
+    const double v = (k ? log10((double)k) : 0.0) - lr;
+    const float hi = __double2float_rn(v);
+    return make_float2(hi, __double2float_rn(v - (double)hi));
 }
 
-// Per count k >= 1 that a pixel can hold, Delta m up to the factor -2.5 of each map,
-// log10(k) - log10(N_rays), as a float-float pair (hi, lo) of its FP64 value: pass 2
-// then forms the per-pixel differences in FP32 arithmetic (the FP64 pipe runs at 1/64 of
-// the FP32 rate). ta[0], tb[0] unused.
+// The pairs of every count below nbins, for both maps (ta[0], tb[0] unused); larger counts are
+// converted where they occur, by the same function, so that every pixel sees the same value.
 __global__ void k_log_table(long long nbins, double log10_ra, double log10_rb, float2 *ta, float2 *tb)
 {
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nbins; k += (long long)gridDim.x * blockDim.x) {
-        const double l = k ? log10((double)k) : 0.0, va = l - log10_ra, vb = l - log10_rb;
-        const float ah = __double2float_rn(va), bh = __double2float_rn(vb);
-        ta[k] = make_float2(ah, __double2float_rn(va - (double)ah));
-        tb[k] = make_float2(bh, __double2float_rn(vb - (double)bh));
+        ta[k] = log_pair((unsigned)k, log10_ra);
+        tb[k] = log_pair((unsigned)k, log10_rb);
     }
 }
 
@@ -109,101 +93,184 @@ __device__ __forceinline__ void hist_add(unsigned *h, unsigned key, unsigned lan
     if (key != kNoKey && lane == (unsigned)(__ffs(same) - 1)) atomicAdd(h + key, (unsigned)__popc(same));
 }
 
-// Pass 2 over both maps: the RMS of Delta m_a - Delta m_b over pixels counted in both,
-//   Delta m_a - Delta m_b = -2.5 [(log10 N_a - log10 N_rays_a) - (log10 N_b - log10 N_rays_b)]
-//                         = -2.5 (ta[N_a] - tb[N_b]),
-// the difference and its square in float-float (about 1e-14 relative), summed per thread in
-// float-float and then in FP64; and the two count histograms (bins 0 .. nbins - 1,
-// nbins = largest count + 1) added to ha / hb. Each warp keeps its own copy of the bins below
-// wb = min(nbins, kWarpBins) in shared memory and adds to it with plain shared-memory atomics:
-// only the lanes of one warp can collide on a bin, so no merging of equal keys is needed for the
-// common small counts. The rare larger counts go to the global histograms, merged per warp.
-// A thread takes four consecutive pixels of each map per step (16-byte loads; the counts come
-// from the arena, 256-byte aligned), so that several loads and table lookups are in flight; the
-// last n % 4 pixels go to the first threads of block 0. (Two such groups per step were timed and
-// kept out: 205 against 192 us on two 8192^2 maps.)
-constexpr int kWarpBins = 512;
+// Per-thread running totals of k_compare.
+struct CmpAcc {
+    float qh = 0.f, ql = 0.f;                  // float-float sum of (Delta m_a - Delta m_b)^2 / 6.25
+    unsigned long long both = 0, za = 0, zb = 0, sa = 0, sb = 0;
+    unsigned mx = 0;
+};
 
-__device__ __forceinline__ void rms_pixel(unsigned na, unsigned nb, const float2 *ta, const float2 *tb, float &qh,
-                                          float &ql, unsigned long long &both)
+// What k_compare computes and where it sends each count.
+struct CmpArgs {
+    const float2 *ta, *tb;                     // log pairs of the counts below nbins
+    double lra, lrb;                           // log10 N_rays of each map
+    long long nbins;                           // bins of ha, hb
+    unsigned *ha, *hb;                         // histograms of the counts below nbins
+    unsigned *la, *lb;                         // counts of nbins or more, listed (room for cap each)
+    unsigned long long cap;
+    int hist_only;                             // 1: histograms alone (every count is below nbins)
+};
+
+// The RMS term of one pixel:
+//   Delta m_a - Delta m_b = -2.5 [(log10 N_a - log10 N_rays_a) - (log10 N_b - log10 N_rays_b)]
+//                         = -2.5 (pair_a(N_a) - pair_b(N_b)),
+// the difference and its square in float-float (about 1e-14 relative), over pixels counted in both.
+__device__ __forceinline__ void rms_pixel(unsigned na, unsigned nb, const CmpArgs &g, CmpAcc &acc)
 {
     if (na && nb) {
-        // d = ta[na] - tb[nb] in float-float, then d^2
-        const float2 x = ta[na], y = tb[nb];
+        const float2 x = na < (unsigned long long)g.nbins ? __ldg(g.ta + na) : log_pair(na, g.lra);
+        const float2 y = nb < (unsigned long long)g.nbins ? __ldg(g.tb + nb) : log_pair(nb, g.lrb);
         float dh, dl;
         ff_two_sum(x.x, -y.x, dh, dl);
         dl = __fadd_rn(dl, __fsub_rn(x.y, y.y));
         const float d = __fadd_rn(dh, dl), de = __fsub_rn(dl, __fsub_rn(d, dh));
         const float ph = __fmul_rn(d, d);
         const float pl = __fmaf_rn(d, d, -ph) + 2.f * d * de;
-        ff_accumulate(qh, ql, ph, pl);
-        both += 1;
+        ff_accumulate(acc.qh, acc.ql, ph, pl);
+        acc.both += 1;
     }
 }
 
-// Count keys na, nb of one lane (in: the lane holds a pixel) into the warp's bins, or, for
-// counts of wb or more, into the global histograms.
-__device__ __forceinline__ void hist_pixel(bool in, unsigned na, unsigned nb, unsigned *sa, unsigned *sb,
-                                           unsigned *ha, unsigned *hb, long long wb, unsigned lane)
+// Count the key of one lane (in: the lane holds a pixel) into the warp's shared bins (keys below
+// kWarpBins), the global histogram (below nbins, merged per warp) or the list of large counts.
+__device__ __forceinline__ void hist_key(bool in, unsigned key, unsigned *sbins, unsigned *h, unsigned *list,
+                                         unsigned long long *n_list, unsigned long long cap, long long nbins,
+                                         unsigned lane)
 {
-    if (in && na < (unsigned)wb) atomicAdd(sa + na, 1u);
-    if (in && nb < (unsigned)wb) atomicAdd(sb + nb, 1u);
-    const bool big_a = in && na >= (unsigned)wb, big_b = in && nb >= (unsigned)wb;
-    if (__any_sync(0xffffffffu, big_a)) hist_add(ha, big_a ? na : kNoKey, lane);
-    if (__any_sync(0xffffffffu, big_b)) hist_add(hb, big_b ? nb : kNoKey, lane);
+    if (in && key < (unsigned)kWarpBins) atomicAdd(sbins + key, 1u);
+    const bool mid = in && key >= (unsigned)kWarpBins && key < (unsigned long long)nbins;
+    if (__any_sync(0xffffffffu, mid)) hist_add(h, mid ? key : kNoKey, lane);
+    const bool big = in && key >= (unsigned long long)nbins;
+    const unsigned bigm = __ballot_sync(0xffffffffu, big);
+    if (bigm) {
+        unsigned long long base = 0;
+        if (lane == (unsigned)(__ffs(bigm) - 1)) base = atomicAdd(n_list, (unsigned long long)__popc(bigm));
+        base = __shfl_sync(0xffffffffu, base, __ffs(bigm) - 1);
+        const unsigned long long slot = base + __popc(bigm & ((1u << lane) - 1u));
+        if (big && slot < cap) list[slot] = key;
+    }
 }
 
-__global__ void __launch_bounds__(256) k_rms_hist(const unsigned *a, const unsigned *b, long long n, const float2 *ta,
-                                                  const float2 *tb, long long nbins, unsigned *ha, unsigned *hb,
-                                                  StatSums *out)
+__device__ __forceinline__ void cmp_pixel(bool in, unsigned na, unsigned nb, const CmpArgs &g, CmpAcc &acc,
+                                          unsigned *sa, unsigned *sb, StatSums *out, unsigned lane)
 {
-    extern __shared__ unsigned sh[];                          // [8 warps][2 maps][wb]
+    if (!g.hist_only) {
+        acc.sa += na;
+        acc.sb += nb;
+        acc.za += in && na == 0u;
+        acc.zb += in && nb == 0u;
+        acc.mx = max(acc.mx, max(na, nb));
+        rms_pixel(na, nb, g, acc);
+    }
+    hist_key(in, na, sa, g.ha, g.la, &out->over_a, g.cap, g.nbins, lane);
+    hist_key(in, nb, sb, g.hb, g.lb, &out->over_b, g.cap, g.nbins, lane);
+}
+
+// One pass over both maps: the sums, empty pixels and largest count; the RMS of
+// Delta m_a - Delta m_b; the count histograms below nbins and the lists of larger counts.
+// A CTA takes chunks blockIdx.x, blockIdx.x + gridDim.x, ... of kCmpChunk bytes of each map (the
+// first 4 floor(n / 4) pixels; the last n % 4 go to warp 0 of block 0 with plain loads); thread 0
+// keeps kCmpStages chunks in flight. A copy that does not land within the wait limit sets
+// out->fault; the CTA then waits (again with the limit) for its other copies and leaves.
+__global__ void __launch_bounds__(kCmpThreads) k_compare(const unsigned *a, const unsigned *b, long long n, CmpArgs g,
+                                                          StatSums *out)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint4 *const stage = reinterpret_cast<uint4 *>(smem);                     // [stage][map][chunk / 16]
+    uint64_t *const full = reinterpret_cast<uint64_t *>(smem + (size_t)kCmpStages * 2 * kCmpChunk);
+    unsigned *const bins = reinterpret_cast<unsigned *>(smem + (size_t)kCmpStages * 2 * kCmpChunk + 64);
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long wb = min(nbins, (long long)kWarpBins);
-    unsigned *const sa = sh + warp * 2 * wb, *const sb = sa + wb;
-    for (long long k = threadIdx.x; k < 16 * wb; k += blockDim.x) sh[k] = 0u;
-    __syncthreads();
-    float qh = 0.f, ql = 0.f;                                 // float-float sum of (Delta m_a - Delta m_b)^2 / 6.25
-    unsigned long long both = 0;
-    const uint4 *a4 = reinterpret_cast<const uint4 *>(a), *b4 = reinterpret_cast<const uint4 *>(b);
-    const long long n4 = n / 4;
-    // warp-uniform trip count: the lanes of a warp take consecutive groups, those past n4 hold no key
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long w0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31u); w0 < n4; w0 += stride) {
-        const long long k = w0 + lane;
-        const bool in = k < n4;
-        const uint4 va = in ? a4[k] : make_uint4(0u, 0u, 0u, 0u), vb = in ? b4[k] : make_uint4(0u, 0u, 0u, 0u);
-        rms_pixel(va.x, vb.x, ta, tb, qh, ql, both);
-        rms_pixel(va.y, vb.y, ta, tb, qh, ql, both);
-        rms_pixel(va.z, vb.z, ta, tb, qh, ql, both);
-        rms_pixel(va.w, vb.w, ta, tb, qh, ql, both);
-        hist_pixel(in, va.x, vb.x, sa, sb, ha, hb, wb, lane);
-        hist_pixel(in, va.y, vb.y, sa, sb, ha, hb, wb, lane);
-        hist_pixel(in, va.z, vb.z, sa, sb, ha, hb, wb, lane);
-        hist_pixel(in, va.w, vb.w, sa, sb, ha, hb, wb, lane);
+    unsigned *const sa = bins + warp * 2 * kWarpBins, *const sb = sa + kWarpBins;
+    for (int k = threadIdx.x; k < 8 * 2 * kWarpBins; k += kCmpThreads) bins[k] = 0u;
+    const long long bytes = (n / 4) * 16;
+    const long long chunks = (bytes + kCmpChunk - 1) / kCmpChunk;
+    const long long mine = chunks > blockIdx.x ? (chunks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    auto chunk_bytes = [&](long long i) {
+        const long long off = (blockIdx.x + i * gridDim.x) * (long long)kCmpChunk;
+        return (unsigned)min((long long)kCmpChunk, bytes - off);
+    };
+    auto issue = [&](long long i) {                                           // thread 0: chunk i -> its stage
+        const int s = (int)(i % kCmpStages);
+        const long long off = (blockIdx.x + i * gridDim.x) * (long long)kCmpChunk;
+        const unsigned nb = chunk_bytes(i);
+        mbar_arrive_expect(full + s, 2 * nb);
+        bulk_load(stage + (size_t)s * 2 * (kCmpChunk / 16), reinterpret_cast<const unsigned char *>(a) + off, nb,
+                  full + s);
+        bulk_load(stage + ((size_t)s * 2 + 1) * (kCmpChunk / 16), reinterpret_cast<const unsigned char *>(b) + off,
+                  nb, full + s);
+    };
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kCmpStages; ++s) mbar_init(full + s, 1);
+        mbar_fence_init();
     }
-    if (blockIdx.x == 0 && warp == 0) {                        // the last n % 4 pixels
-        const long long k = 4 * n4 + lane;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (long long i = 0; i < min(mine, (long long)kCmpStages); ++i) issue(i);
+    CmpAcc acc;
+    for (long long i = 0; i < mine; ++i) {
+        const int s = (int)(i % kCmpStages);
+        const bool ok = mbar_wait(full + s, (unsigned)((i / kCmpStages) & 1));
+        if (__syncthreads_or(!ok)) {                                         // give up, the same in every thread
+            if (threadIdx.x == 0) {
+                atomicExch(&out->fault, 1u);
+                for (long long j = i; j < min(mine, i + kCmpStages); ++j)   // copies still in flight
+                    mbar_wait(full + (int)(j % kCmpStages), (unsigned)((j / kCmpStages) & 1));
+            }
+            return;
+        }
+        const uint4 *const va = stage + (size_t)s * 2 * (kCmpChunk / 16), *const vb = va + kCmpChunk / 16;
+        const int quads = (int)(chunk_bytes(i) / 16);
+        for (int q0 = warp * 32; q0 < quads; q0 += kCmpThreads) {            // warp-uniform trip count
+            const int q = q0 + (int)lane;
+            const bool in = q < quads;
+            const uint4 x = in ? va[q] : make_uint4(0u, 0u, 0u, 0u), y = in ? vb[q] : make_uint4(0u, 0u, 0u, 0u);
+            cmp_pixel(in, x.x, y.x, g, acc, sa, sb, out, lane);
+            cmp_pixel(in, x.y, y.y, g, acc, sa, sb, out, lane);
+            cmp_pixel(in, x.z, y.z, g, acc, sa, sb, out, lane);
+            cmp_pixel(in, x.w, y.w, g, acc, sa, sb, out, lane);
+        }
+        __syncthreads();                                                     // stage s read by every thread
+        if (threadIdx.x == 0 && i + kCmpStages < mine) issue(i + kCmpStages);
+    }
+    if (blockIdx.x == 0 && warp == 0) {                                      // the last n % 4 pixels
+        const long long k = 4 * (n / 4) + lane;
         const bool in = k < n;
-        const unsigned na = in ? a[k] : 0u, nb = in ? b[k] : 0u;
-        rms_pixel(na, nb, ta, tb, qh, ql, both);
-        hist_pixel(in, na, nb, sa, sb, ha, hb, wb, lane);
+        cmp_pixel(in, in ? a[k] : 0u, in ? b[k] : 0u, g, acc, sa, sb, out, lane);
     }
-    double sq = 6.25 * ((double)qh + (double)ql);              // Delta m differences carry the factor -2.5
-    for (int o = 16; o > 0; o >>= 1) {
-        sq += __shfl_down_sync(0xffffffffu, sq, o);
-        both += __shfl_down_sync(0xffffffffu, both, o);
-    }
-    if (lane == 0) {
-        atomicAdd(&out->sum_sq, sq);
-        atomicAdd(&out->n_both, both);
+    if (!g.hist_only) {
+        double sq = 6.25 * ((double)acc.qh + (double)acc.ql);                // Delta m differences carry -2.5
+        for (int o = 16; o > 0; o >>= 1) {
+            sq += __shfl_down_sync(0xffffffffu, sq, o);
+            acc.both += __shfl_down_sync(0xffffffffu, acc.both, o);
+            acc.za += __shfl_down_sync(0xffffffffu, acc.za, o);
+            acc.zb += __shfl_down_sync(0xffffffffu, acc.zb, o);
+            acc.sa += __shfl_down_sync(0xffffffffu, acc.sa, o);
+            acc.sb += __shfl_down_sync(0xffffffffu, acc.sb, o);
+            acc.mx = max(acc.mx, __shfl_down_sync(0xffffffffu, acc.mx, o));
+        }
+        if (lane == 0) {
+            atomicAdd(&out->sum_sq, sq);
+            atomicAdd(&out->n_both, acc.both);
+            atomicAdd(&out->zero_a, acc.za);
+            atomicAdd(&out->zero_b, acc.zb);
+            atomicAdd(&out->sum_a, acc.sa);
+            atomicAdd(&out->sum_b, acc.sb);
+            atomicMax(&out->max_count, acc.mx);
+        }
     }
     __syncthreads();
-    for (long long k = threadIdx.x; k < 2 * wb; k += blockDim.x) {   // the 8 warp copies of each bin
+    for (int k = threadIdx.x; k < 2 * kWarpBins; k += kCmpThreads) {         // the 8 warp copies of each bin
         unsigned v = 0;
-        for (int q = 0; q < 8; ++q) v += sh[q * 2 * wb + k];
-        if (v) atomicAdd(k < wb ? ha + k : hb + (k - wb), v);
+        for (int q = 0; q < 8; ++q) v += bins[q * 2 * kWarpBins + k];
+        if (v) atomicAdd(k < kWarpBins ? g.ha + k : g.hb + (k - kWarpBins), v);
     }
+}
+
+// The listed large counts of one map added to its histogram (bins up to the largest count).
+__global__ void k_list_hist(const unsigned *list, unsigned long long m, unsigned *h)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < (long long)m; k += (long long)gridDim.x * blockDim.x)
+        atomicAdd(h + list[k], 1u);
 }
 
 // One CTA of 1024 threads: inclusive prefix sums ca[k], cb[k] of the two count
@@ -315,53 +382,87 @@ extern "C" int mm_map_compare(mm_ctx *ctx, mm_map a, mm_map b, mm_compare *out)
         std::vector<void *> v;
         ~Tmp() { for (void *p : v) ar->free(p); }
     } tmp{&ctx->arena, {}};
+    // One pass over both maps with histograms of nbins = T bins, T a power of two from 32 N_rays
+    // (4096 .. 2^20); counts of T or more go to lists of room cap. The prefix sums and the K-S
+    // numerator run on these bins at once: they are exact whenever the largest count is below T.
+    // Otherwise the histograms are widened to the largest count and filled from the lists (or, if a
+    // list ran out of room, by a second, histogram-only pass) and the K-S steps run again.
+    const double nr_max = std::max(A->p.nrays_per_pix, B->p.nrays_per_pix);
+    long long T = 4096;
+    while (T < (1LL << 20) && (double)T < 32.0 * nr_max) T <<= 1;
+    const unsigned long long cap = (unsigned long long)std::max(4096LL, n / 16);
     StatSums *d_sum = nullptr;
-    int rc = ctx->arena.alloc(sizeof(StatSums), (void **)&d_sum);
-    if (rc) return rc;
+    unsigned *hist = nullptr, *lists = nullptr;
+    long long *cum = nullptr;
+    float2 *tab = nullptr;                                     // [2 T]: map a, then map b
+    int rc;
+    if ((rc = ctx->arena.alloc(sizeof(StatSums), (void **)&d_sum))) return rc;
     tmp.v.push_back(d_sum);
-    if ((e = cudaMemsetAsync(d_sum, 0, sizeof(StatSums), s)) != cudaSuccess) return cuda_fail(e, "memset");
-    const int grid = std::max(1, std::min(4 * ctx->sms, (int)((n + 255) / 256)));
-    k_scan_stats<<<grid, 256, 0, s>>>(A->counts, B->counts, n, d_sum);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_scan_stats");
+    if ((rc = ctx->arena.alloc((size_t)(2 * T) * sizeof(unsigned), (void **)&hist))) return rc;
+    tmp.v.push_back(hist);
+    if ((rc = ctx->arena.alloc((size_t)(2 * T) * sizeof(long long), (void **)&cum))) return rc;
+    tmp.v.push_back(cum);
+    if ((rc = ctx->arena.alloc((size_t)(2 * T) * sizeof(float2), (void **)&tab))) return rc;
+    tmp.v.push_back(tab);
+    if ((rc = ctx->arena.alloc((size_t)(2 * cap) * sizeof(unsigned), (void **)&lists))) return rc;
+    tmp.v.push_back(lists);
+    if ((e = cudaMemsetAsync(d_sum, 0, sizeof(StatSums), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(hist, 0, (size_t)(2 * T) * sizeof(unsigned), s)) != cudaSuccess)
+        return cuda_fail(e, "memset");
+    const double lra = std::log10(A->p.nrays_per_pix), lrb = std::log10(B->p.nrays_per_pix);
+    k_log_table<<<std::max(1, std::min(ctx->sms, (int)((T + 255) / 256))), 256, 0, s>>>(T, lra, lrb, tab, tab + T);
+    if ((e = cudaFuncSetAttribute(k_compare, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCmpSmem)) !=
+        cudaSuccess)
+        return cuda_fail(e, "k_compare shared memory");
+    const long long chunks = ((n / 4) * 16 + kCmpChunk - 1) / kCmpChunk;
+    const int cgrid = (int)std::max(1LL, std::min((long long)(3 * ctx->sms), chunks));   // 3 CTAs fit an SM
+    CmpArgs g{tab, tab + T, lra, lrb, T, hist, hist + T, lists, lists + cap, cap, 0};
+    k_compare<<<cgrid, kCmpThreads, kCmpSmem, s>>>(A->counts, B->counts, n, g, d_sum);
+    auto ks_steps = [&](const unsigned *h2, long long *c2, long long nb) {
+        k_scan<<<1, 1024, 0, s>>>(h2, h2 + nb, nb, c2, c2 + nb);
+        const int egrid = std::max(1, std::min(4 * ctx->sms, (int)((2 * nb + 255) / 256)));
+        k_ks_eval<<<egrid, 256, 0, s>>>(h2, h2 + nb, c2, c2 + nb, nb, n, n, A->p.nrays_per_pix, B->p.nrays_per_pix,
+                                        d_sum);
+    };
+    ks_steps(hist, cum, T);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_log_table/k_compare/k_scan/k_ks_eval");
     StatSums h{};
     if ((e = cudaMemcpyAsync(&h, d_sum, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return cuda_fail(e, "stats readback");
-    // log10 table over the counts, histograms of the counts over 0..max with the RMS pass,
-    // then their prefix sums and the exact K-S numerator
-    const long long nbins = (long long)h.max_count + 1;
-    unsigned *hist = nullptr;
-    long long *cum = nullptr;
-    float2 *tab = nullptr;                                     // [2 nbins]: map a, then map b
-    if ((rc = ctx->arena.alloc((size_t)(2 * nbins) * sizeof(unsigned), (void **)&hist))) return rc;
-    tmp.v.push_back(hist);
-    if ((rc = ctx->arena.alloc((size_t)(2 * nbins) * sizeof(long long), (void **)&cum))) return rc;
-    tmp.v.push_back(cum);
-    if ((rc = ctx->arena.alloc((size_t)(2 * nbins) * sizeof(float2), (void **)&tab))) return rc;
-    tmp.v.push_back(tab);
-    if ((e = cudaMemsetAsync(hist, 0, (size_t)(2 * nbins) * sizeof(unsigned), s)) != cudaSuccess) return cuda_fail(e, "memset");
-    const double lra = std::log10(A->p.nrays_per_pix), lrb = std::log10(B->p.nrays_per_pix);
-    k_log_table<<<std::max(1, std::min(ctx->sms, (int)((nbins + 255) / 256))), 256, 0, s>>>(nbins, lra, lrb, tab,
-                                                                                           tab + nbins);
-    // histograms: per warp in shared memory (the bins below kWarpBins), so that the common small
-    // counts need no merging of equal keys; the few larger counts go to the global histograms
-    const size_t smem = (size_t)16 * (size_t)std::min<long long>(nbins, kWarpBins) * sizeof(unsigned);
-    if ((e = cudaFuncSetAttribute(k_rms_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kHistSmemMax)) != cudaSuccess)
-        return cuda_fail(e, "k_rms_hist shared memory");
-    {
-        const int per_sm = std::max(1, std::min(6, (int)(kSmemPerSm / std::max<size_t>(smem, 1))));
-        k_rms_hist<<<std::max(1, std::min(per_sm * ctx->sms, (int)((n + 255) / 256))), 256, smem, s>>>(
-            A->counts, B->counts, n, tab, tab + nbins, nbins, hist, hist + nbins, d_sum);
+    if (h.fault) return fail(MM_EDEVICE, "k_compare: a copy into shared memory did not complete");
+    if ((long long)h.max_count >= T) {                         // counts beyond the first histograms
+        const long long nb = (long long)h.max_count + 1;
+        unsigned *hist2 = nullptr;
+        long long *cum2 = nullptr;
+        if ((rc = ctx->arena.alloc((size_t)(2 * nb) * sizeof(unsigned), (void **)&hist2))) return rc;
+        tmp.v.push_back(hist2);
+        if ((rc = ctx->arena.alloc((size_t)(2 * nb) * sizeof(long long), (void **)&cum2))) return rc;
+        tmp.v.push_back(cum2);
+        if ((e = cudaMemsetAsync(hist2, 0, (size_t)(2 * nb) * sizeof(unsigned), s)) != cudaSuccess ||
+            (e = cudaMemsetAsync(&d_sum->ks_num, 0, sizeof(long long), s)) != cudaSuccess)
+            return cuda_fail(e, "memset");
+        if (h.over_a <= cap && h.over_b <= cap) {
+            for (int m = 0; m < 2; ++m) {
+                if ((e = cudaMemcpyAsync(hist2 + m * nb, hist + m * T, (size_t)T * sizeof(unsigned),
+                                         cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+                    return cuda_fail(e, "histogram copy");
+                const unsigned long long cnt = m ? h.over_b : h.over_a;
+                if (cnt)
+                    k_list_hist<<<(int)std::min<unsigned long long>(4ULL * ctx->sms, (cnt + 255) / 256), 256, 0, s>>>(
+                        lists + m * cap, cnt, hist2 + m * nb);
+            }
+        } else {
+            CmpArgs g2{nullptr, nullptr, lra, lrb, nb, hist2, hist2 + nb, nullptr, nullptr, 0, 1};
+            k_compare<<<cgrid, kCmpThreads, kCmpSmem, s>>>(A->counts, B->counts, n, g2, d_sum);
+        }
+        ks_steps(hist2, cum2, nb);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_list_hist/k_compare/k_scan/k_ks_eval");
+        if ((e = cudaMemcpyAsync(&h, d_sum, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return cuda_fail(e, "stats readback");
+        if (h.fault) return fail(MM_EDEVICE, "k_compare: a copy into shared memory did not complete");
     }
-    k_scan<<<1, 1024, 0, s>>>(hist, hist + nbins, nbins, cum, cum + nbins);
-    const int egrid = std::max(1, std::min(4 * ctx->sms, (int)((2 * nbins + 255) / 256)));
-    k_ks_eval<<<egrid, 256, 0, s>>>(hist, hist + nbins, cum, cum + nbins, nbins, n, n, A->p.nrays_per_pix,
-                                    B->p.nrays_per_pix, d_sum);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_rms_hist/k_scan/k_ks_eval");
-    if ((e = cudaMemcpyAsync(&h, d_sum, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(s)) != cudaSuccess)
-        return cuda_fail(e, "stats readback");
     out->n_rms = (int64_t)h.n_both;
     out->rms_dm = h.n_both ? std::sqrt(h.sum_sq / (double)h.n_both) : 0.0;
     out->zero_a = (int64_t)h.zero_a;

@@ -56,10 +56,10 @@ def test_profile_wider_than_map_rejected(shot):
     assert e.value.code == mm.MM_EINVAL
 
 
-# Wide supports: the tiled kernels stage a support in 48 KB of shared memory (the Gaussian's
-# row pass up to a half-width of 123 pixels and its column pass up to 124, the disc up to a
-# radius of 15 pixels); wider ones run the untiled kernels. Sizes on both sides of each limit,
-# on a 320^2 map.
+# Wide supports: the tiled kernels stage their tiles in shared memory, two tiles of a Gaussian pass
+# in 95 KB (the row pass up to a half-width of 123 pixels, the column pass up to 124) and a disc's
+# tile in 48 KB (up to a radius of 15 pixels); wider supports run the untiled kernels. Sizes on both
+# sides of each limit, on a 320^2 map.
 CFG_WIDE = dict(CFG, npix_side=320, side=7.5)            # pixel 0.0234375 R_E
 
 

@@ -36,22 +36,27 @@ def restore_counts(ctx, counts, nrays, side=6.0):
     return mm.mm_map_restore(ctx, 0, p, counts, st)
 
 
-# The device keeps per-warp histograms of the counts below 512 in shared memory and sends larger
-# counts to global histograms. Seeded synthetic count maps (put on the device by mm_map_restore, as
-# restore_counts below) cover both: the first has only small counts, the second a long tail of
-# counts up to about 10^5, and both have empty pixels and different N_rays.
-@pytest.mark.parametrize("nside,tail", [(256, False), (192, True)])
+# The device keeps per-warp histograms of the counts below 512 in shared memory, sends counts below
+# T = 4096 (at these N_rays) to global histograms and lists the larger ones (room for
+# max(4096, N_side^2 / 16) per map), widening the histograms afterwards; when a list runs out of
+# room, a second pass over the maps builds the wide histograms. Seeded synthetic count maps (put on
+# the device by mm_map_restore, as restore_counts above) cover each way: only small counts; a tail
+# up to about 10^5 on 2 % of the pixels (listed); the same tail on 12 % of a 256^2 map (about 7900
+# pixels above T, more than the list holds). All have empty pixels and different N_rays.
+@pytest.mark.parametrize("nside,tail", [(256, 0.0), (192, 0.02), (256, 0.12)])
 def test_compare_matches_oracle_statistics(ctx, nside, tail):
-    rng = np.random.default_rng(nside)
+    rng = np.random.default_rng(nside + int(100 * tail))
     mu = rng.lognormal(0.0, 0.6, (nside, nside))
     if tail:
-        mu[rng.random((nside, nside)) < 0.02] *= 300.0
+        mu[rng.random((nside, nside)) < tail] *= 300.0
     nrays_a, nrays_b = 32.0, 25.0
     ca = rng.poisson(mu * nrays_a).astype(np.uint32)
     cb = rng.poisson(mu * nrays_b * rng.lognormal(0.0, 0.05, mu.shape)).astype(np.uint32)   # a noisier map
     ca.ravel()[rng.integers(0, nside * nside, 5)] = 0                                        # empty pixels
     cb.ravel()[rng.integers(0, nside * nside, 9)] = 0
-    assert (int(max(ca.max(), cb.max())) >= 512) == tail
+    assert (int(max(ca.max(), cb.max())) >= 4096) == (tail > 0)
+    big = int(np.sum(ca >= 4096))
+    assert (big > max(4096, nside * nside // 16)) == (tail > 0.1)
     assert (ca == 0).any() and (cb == 0).any()
     a = restore_counts(ctx, ca, nrays_a)
     b = restore_counts(ctx, cb, nrays_b)
