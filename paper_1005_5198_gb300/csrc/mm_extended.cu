@@ -72,110 +72,91 @@ __global__ void k_disc(const unsigned *cin, float *out, int n, const int *span, 
 constexpr int kDiscTileW = 64, kDiscTileH = 32;        // disc: 64 x 32 outputs per CTA
 constexpr size_t kTileSmemMax = 48 * 1024;             // dynamic shared memory of a tiled disc CTA (no opt-in);
                                                        // wider supports take the untiled kernel
-constexpr size_t kGaussSmemMax = 95 * 1024;            // a double-buffered Gaussian CTA (rows: h <= 123,
-                                                       // columns: h <= 124); wider take the untiled kernel
+constexpr size_t kGaussSmemMax = 200 * 1024;           // a double-buffered Gaussian CTA (h <= 131; wider
+                                                       // supports take the untiled kernel)
 
-// Gaussian passes, register-blocked: a thread owns kGG groups of 8 consecutive outputs along the
-// pass direction and runs the taps in chunks of 8. For a chunk it loads the 15 inputs that its 8
-// outputs need into registers once and makes 64 FMAs from them (32 packed f32x2 instructions), so
-// shared memory supplies about one word per 4 FMAs instead of one or more per FMA. Every output
-// still adds its taps in order (a correctly rounded FMA each, tap 0 first), exactly as k_gauss_pass.
-// A CTA holds two tiles: while it computes one, the next one's inputs arrive by cp.async.
-constexpr int kGG = 2;                                  // groups of 8 outputs per thread
-constexpr int kGRows = 32;                              // row pass: tile rows, one per lane
-constexpr int kGRowOut = 8 * kGG * 8;                   // row pass: outputs per tile row (8 warps)
-constexpr int kGColOut = 8 * kGG * 8;                   // column pass: output rows per tile (8 warps)
-constexpr int kGCols = 32;                              // column pass: tile columns, one per lane
+// Gaussian passes on packed pairs: the two lanes of every packed f32x2 FMA are the same output of two
+// neighbouring rows (row pass) or columns (column pass), so that one 8-byte shared load gives an
+// operand pair and the taps are pairs (g, g). A thread owns 16 consecutive outputs along the pass
+// direction of its pair of rows or columns and runs the taps in chunks of 8: per chunk it loads the
+// 23 input pairs the 16 outputs need once and makes 128 packed FMAs from them. The taps are padded
+// with zero weights to TP, a multiple of 8; a padded tap reads a zero staged beyond the support and
+// leaves a sum unchanged (every sum is non-negative). Every output adds its taps in order (a
+// correctly rounded FMA each, tap 0 first), exactly as k_gauss_pass. A CTA holds two tiles: while
+// it computes one, the next one's inputs arrive by cp.async.
+constexpr int kGOut = 128;                              // outputs per tile along the pass (8 warps x 16)
+constexpr int kGPairs = 32;                             // pairs of rows (columns) per tile, one per lane
 
-__host__ __device__ inline int gauss_row_stride(int h) { return (kGRowOut + 2 * h) | 1; }   // odd: rows hit distinct banks
 __host__ __device__ inline int gauss_taps_padded(int h) { return (2 * h + 1 + 7) & ~7; }
-__host__ __device__ inline int gauss_row_tile(int h) { return kGRows * gauss_row_stride(h); }
-__host__ __device__ inline int gauss_col_tile(int h) { return (kGColOut + 2 * h) * kGCols; }
-__host__ __device__ inline size_t gauss_row_smem(int h)
+// inputs staged along the pass: 128 + TP - 1 (odd, so that the pairs' rows hit distinct banks)
+__host__ __device__ inline int gauss_span(int h) { return kGOut + gauss_taps_padded(h) - 1; }
+__host__ __device__ inline size_t gauss_tile_floats(int h) { return (size_t)2 * kGPairs * gauss_span(h); }
+__host__ __device__ inline size_t gauss_smem(int h)
 {
-    return ((size_t)gauss_taps_padded(h) + 2 * (size_t)gauss_row_tile(h)) * 4;
-}
-__host__ __device__ inline size_t gauss_col_smem(int h)
-{
-    return ((size_t)gauss_taps_padded(h) + 2 * (size_t)gauss_col_tile(h)) * 4;
+    return ((size_t)2 * gauss_taps_padded(h) + 2 * gauss_tile_floats(h)) * 4;
 }
 __host__ __device__ inline size_t disc_smem(int H)
 {
     return (size_t)(kDiscTileH + 2 * H) * (kDiscTileW + 2 * H + 1) * 8 + (size_t)(2 * H + 1) * 4;
 }
 
-// acc[u] += sum over taps k of [k0, k0 + 8) of g[k] x[u + k - k0], tap by tap, for the 8 outputs
-// whose inputs start at x (stride st between consecutive inputs). The outputs go in pairs through
-// packed f32x2 FMAs (acc2[p] holds outputs 2p, 2p + 1; each lane rounds as fmaf does).
-__device__ __forceinline__ void gauss_chunk8(const float *gk, const float *x, int st, float2 *acc2)
+// acc[u] = sum over taps k < TP of g[k] x[(u + k) st], u < 16: x the thread's first input pair,
+// st the distance between consecutive input pairs (in pairs), gs2 the taps as pairs (g, g).
+__device__ __forceinline__ void gauss_taps2(const float2 *gs2, int tp, const float2 *x, int st, float2 (&acc)[16])
 {
-    float v[15];
 #pragma unroll
-    for (int q = 0; q < 15; ++q) v[q] = x[q * st];
+    for (int u = 0; u < 16; ++u) acc[u] = make_float2(0.f, 0.f);
+    for (int k0 = 0; k0 < tp; k0 += 8) {
+        float2 v[23];
 #pragma unroll
-    for (int kk = 0; kk < 8; ++kk) {
-        const float2 w = make_float2(gk[kk], gk[kk]);
+        for (int q = 0; q < 23; ++q) v[q] = x[(k0 + q) * st];
 #pragma unroll
-        for (int p = 0; p < 4; ++p) acc2[p] = __ffma2_rn(w, make_float2(v[2 * p + kk], v[2 * p + 1 + kk]), acc2[p]);
+        for (int kk = 0; kk < 8; ++kk) {
+            const float2 w = gs2[k0 + kk];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) acc[u] = __ffma2_rn(w, v[u + kk], acc[u]);
+        }
     }
 }
 
-// The taps of one thread's groups over a staged tile: x0 = first input of the thread's first group,
-// gstep = distance between its groups, st = distance between consecutive inputs.
-__device__ __forceinline__ void gauss_taps(const float *gs, int taps, const float *x0, int gstep, int st,
-                                           float2 (&acc)[kGG][4])
+// Taps g[0 .. 2h] as pairs (g, g), zero up to TP.
+__device__ __forceinline__ void gauss_stage_taps(const float *g, int h, float2 *gs2)
 {
-#pragma unroll
-    for (int q = 0; q < kGG; ++q)
-#pragma unroll
-        for (int p = 0; p < 4; ++p) acc[q][p] = make_float2(0.f, 0.f);
-    int k0 = 0;
-    for (; k0 + 8 <= taps; k0 += 8) {
-        float gk[8];
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk) gk[kk] = gs[k0 + kk];
-#pragma unroll
-        for (int q = 0; q < kGG; ++q) gauss_chunk8(gk, x0 + q * gstep + k0 * st, st, acc[q]);
-    }
-    for (; k0 < taps; ++k0) {                              // the last taps, one at a time
-        const float2 w = make_float2(gs[k0], gs[k0]);
-#pragma unroll
-        for (int q = 0; q < kGG; ++q)
-#pragma unroll
-            for (int p = 0; p < 4; ++p)
-                acc[q][p] = __ffma2_rn(w, make_float2(x0[q * gstep + (2 * p + k0) * st], x0[q * gstep + (2 * p + 1 + k0) * st]),
-                                       acc[q][p]);
+    for (int k = threadIdx.x; k < gauss_taps_padded(h); k += blockDim.x) {
+        const float v = k <= 2 * h ? g[k] : 0.f;
+        gs2[k] = make_float2(v, v);
     }
 }
 
-// Row pass (dir 0 of k_gauss_pass): a tile is rows [r0, r0 + 32) x columns [c0 - h, c0 + 128 + h)
-// (the inputs, as floats; zeros outside the map); lane l takes row r0 + l, warp w outputs
-// c0 + 16 w .. + 16. The outputs go back through the tile's shared memory so that the global stores
-// run along rows. Tiles t, t + gridDim.x, ...; each thread copies the same elements of every tile
-// (4-byte cp.async, zero-filled outside the map) and, from counts, converts those it copied once
-// they have landed.
+// Row pass (dir 0 of k_gauss_pass): a tile is rows [r0, r0 + 64) x input columns
+// [c0 - h, c0 - h + span), staged as pairs of rows: element (row 2p + e, column x) at float
+// 2 (p span + x) + e, as floats (zeros outside the map and beyond the support). Lane l takes rows
+// r0 + 2l, r0 + 2l + 1, warp w outputs c0 + 16 w .. + 16. The outputs go back through the tile's
+// shared memory so that the global stores run along rows. Tiles t, t + gridDim.x, ...; each thread
+// copies the same elements of every tile (4-byte cp.async, zero-filled) and, from counts, converts
+// those it copied once they have landed.
 template <bool FROM_COUNTS>
-__global__ void __launch_bounds__(256) k_gauss_rows(const unsigned *cin, const float *fin, float *out, int n,
-                                                    const float *g, int h, float inv_nrays)
+__global__ void __launch_bounds__(256, 1) k_gauss_rows(const unsigned *cin, const float *fin, float *out, int n,
+                                                       const float *g, int h, float inv_nrays)
 {
-    extern __shared__ float sm[];
-    const int taps = 2 * h + 1, S = gauss_row_stride(h), W = kGRowOut + 2 * h;
-    float *const gs = sm;
-    float *const buf0 = sm + gauss_taps_padded(h), *const buf1 = buf0 + gauss_row_tile(h);
-    for (int k = threadIdx.x; k < taps; k += blockDim.x) gs[k] = g[k];
+    extern __shared__ float4 sm4[];
+    const int tp = gauss_taps_padded(h), S = gauss_span(h), W = kGOut + 2 * h;
+    float2 *const gs2 = reinterpret_cast<float2 *>(sm4);
+    float *const buf0 = reinterpret_cast<float *>(gs2 + tp), *const buf1 = buf0 + gauss_tile_floats(h);
+    gauss_stage_taps(g, h, gs2);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int cols = (n + kGRowOut - 1) / kGRowOut, rows = (n + kGRows - 1) / kGRows;
+    const int cols = (n + kGOut - 1) / kGOut, rows = (n + 2 * kGPairs - 1) / (2 * kGPairs);
     const long long tiles = (long long)cols * rows;
     auto stage = [&](long long t, float *tile) {
-        const int c0 = (int)(t % cols) * kGRowOut, r0 = (int)(t / cols) * kGRows;
-        for (int rr = w; rr < kGRows; rr += 8) {              // warp w stages rows w, w + 8, ...
+        const int c0 = (int)(t % cols) * kGOut, r0 = (int)(t / cols) * (2 * kGPairs);
+        for (int rr = w; rr < 2 * kGPairs; rr += 8) {       // warp w stages rows w, w + 8, ...
             const int j = r0 + rr;
-            for (int x = lane; x < W; x += 32) {
+            float *const dst = tile + 2 * (rr >> 1) * S + (rr & 1);
+            for (int x = lane; x < S; x += 32) {
                 const int i = c0 - h + x;
-                const bool ok = j < n && i >= 0 && i < n;
+                const bool ok = x < W && j < n && i >= 0 && i < n;
                 const long long src = ok ? (long long)j * n + i : 0;
-                cp_async4(tile + rr * S + x, FROM_COUNTS ? (const void *)(cin + src) : (const void *)(fin + src),
-                          ok ? 4u : 0u);
+                cp_async4(dst + 2 * x, FROM_COUNTS ? (const void *)(cin + src) : (const void *)(fin + src), ok ? 4u : 0u);
             }
         }
         cp_async_commit();
@@ -192,53 +173,52 @@ __global__ void __launch_bounds__(256) k_gauss_rows(const unsigned *cin, const f
             cp_async_wait<0>();
         }
         if (FROM_COUNTS)                                   // the elements this thread copied, now landed
-            for (int rr = w; rr < kGRows; rr += 8)
-                for (int x = lane; x < W; x += 32)
-                    tile[rr * S + x] = (float)__float_as_uint(tile[rr * S + x]) * inv_nrays;
+            for (int rr = w; rr < 2 * kGPairs; rr += 8) {
+                float *const row = tile + 2 * (rr >> 1) * S + (rr & 1);
+                for (int x = lane; x < S; x += 32) row[2 * x] = (float)__float_as_uint(row[2 * x]) * inv_nrays;
+            }
         __syncthreads();                                   // tile t staged; taps staged
-        float2 acc[kGG][4];
-        gauss_taps(gs, taps, tile + lane * S + w * 8 * kGG, 8, 1, acc);
+        float2 *const t2 = reinterpret_cast<float2 *>(tile);
+        float2 acc[16];
+        gauss_taps2(gs2, tp, t2 + lane * S + w * 16, 1, acc);
         __syncthreads();                                   // every thread has read the inputs
 #pragma unroll
-        for (int q = 0; q < kGG; ++q)
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                tile[lane * S + w * 8 * kGG + 8 * q + 2 * p] = acc[q][p].x;
-                tile[lane * S + w * 8 * kGG + 8 * q + 2 * p + 1] = acc[q][p].y;
-            }
+        for (int u = 0; u < 16; ++u) t2[lane * S + w * 16 + u] = acc[u];
         __syncthreads();
-        const int c0 = (int)(t % cols) * kGRowOut, r0 = (int)(t / cols) * kGRows;
-        for (int rr = w; rr < kGRows; rr += 8) {
+        const int c0 = (int)(t % cols) * kGOut, r0 = (int)(t / cols) * (2 * kGPairs);
+        for (int rr = w; rr < 2 * kGPairs; rr += 8) {
             const int j = r0 + rr;
-            for (int x = lane; x < kGRowOut; x += 32) {
+            const float *const row = tile + 2 * (rr >> 1) * S + (rr & 1);
+            for (int x = lane; x < kGOut; x += 32) {
                 const int i = c0 + x;
                 if (j < n && i < n)
-                    out[(long long)j * n + i] = (i - h >= 0 && i + h < n) ? tile[rr * S + x] : __int_as_float(0x7fc00000);
+                    out[(long long)j * n + i] = (i - h >= 0 && i + h < n) ? row[2 * x] : __int_as_float(0x7fc00000);
             }
         }
         __syncthreads();                                   // the tile's buffer is free for tile t + 2 gridDim.x
     }
 }
 
-// Column pass (dir 1): a tile is rows [r0 - h, r0 + 128 + h) of 32 columns; lane l takes column
-// c0 + l, warp w the output rows r0 + 16 w .. + 16 (stores along rows of 32 columns). Tiles and
-// copies as in the row pass.
-__global__ void __launch_bounds__(256) k_gauss_cols(const float *fin, float *out, int n, const float *g, int h)
+// Column pass (dir 1): a tile is input rows [r0 - h, r0 - h + span) of 64 columns [c0, c0 + 64),
+// row-major, so that columns 2l, 2l + 1 of a row form a pair. Lane l takes columns c0 + 2l,
+// c0 + 2l + 1, warp w the output rows r0 + 16 w .. + 16 (stores along rows). Tiles and copies as
+// in the row pass.
+__global__ void __launch_bounds__(256, 1) k_gauss_cols(const float *fin, float *out, int n, const float *g, int h)
 {
-    extern __shared__ float sm[];
-    const int taps = 2 * h + 1, E = gauss_col_tile(h);
-    float *const gs = sm;
-    float *const buf0 = sm + gauss_taps_padded(h), *const buf1 = buf0 + E;   // [(128 + 2h) x 32] each
-    for (int k = threadIdx.x; k < taps; k += blockDim.x) gs[k] = g[k];
+    extern __shared__ float4 sm4[];
+    const int tp = gauss_taps_padded(h), S = gauss_span(h), H2 = kGOut + 2 * h;
+    float2 *const gs2 = reinterpret_cast<float2 *>(sm4);
+    float *const buf0 = reinterpret_cast<float *>(gs2 + tp), *const buf1 = buf0 + gauss_tile_floats(h);
+    gauss_stage_taps(g, h, gs2);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int cols = (n + kGCols - 1) / kGCols, rows = (n + kGColOut - 1) / kGColOut;
+    const int cols = (n + 2 * kGPairs - 1) / (2 * kGPairs), rows = (n + kGOut - 1) / kGOut;
     const long long tiles = (long long)cols * rows;
+    const int E = 2 * kGPairs * S;
     auto stage = [&](long long t, float *tile) {
-        const int c0 = (int)(t % cols) * kGCols, r0 = (int)(t / cols) * kGColOut;
-        const int i = c0 + lane;
-        for (int q = threadIdx.x; q < E; q += blockDim.x) {   // row q / 32, column lane (blockDim 256)
-            const int j = r0 - h + q / kGCols;
-            const bool ok = j >= 0 && j < n && i < n;
+        const int c0 = (int)(t % cols) * (2 * kGPairs), r0 = (int)(t / cols) * kGOut;
+        for (int q = threadIdx.x; q < E; q += blockDim.x) {   // row q / 64, column q % 64
+            const int rr = q >> 6, i = c0 + (q & 63), j = r0 - h + rr;
+            const bool ok = rr < H2 && j >= 0 && j < n && i < n;
             cp_async4(tile + q, fin + (ok ? (long long)j * n + i : 0), ok ? 4u : 0u);
         }
         cp_async_commit();
@@ -255,18 +235,20 @@ __global__ void __launch_bounds__(256) k_gauss_cols(const float *fin, float *out
             cp_async_wait<0>();
         }
         __syncthreads();
-        float2 acc[kGG][4];
-        gauss_taps(gs, taps, tile + (w * 8 * kGG) * kGCols + lane, 8 * kGCols, kGCols, acc);
-        const int c0 = (int)(t % cols) * kGCols, r0 = (int)(t / cols) * kGColOut;
-        const int i = c0 + lane;
+        float2 acc[16];
+        gauss_taps2(gs2, tp, reinterpret_cast<const float2 *>(tile) + (w * 16) * kGPairs + lane, kGPairs, acc);
+        const int c0 = (int)(t % cols) * (2 * kGPairs), r0 = (int)(t / cols) * kGOut;
+        const int i = c0 + 2 * lane;
 #pragma unroll
-        for (int q = 0; q < kGG; ++q)
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int j = r0 + w * 8 * kGG + 8 * q + u;
-                const float a = (u & 1) ? acc[q][u >> 1].y : acc[q][u >> 1].x;
-                if (i < n && j < n) out[(long long)j * n + i] = (j - h >= 0 && j + h < n) ? a : __int_as_float(0x7fc00000);
+        for (int u = 0; u < 16; ++u) {
+            const int j = r0 + w * 16 + u;
+            if (j < n) {
+                const bool edge = j - h < 0 || j + h >= n;
+                float *const o = out + (long long)j * n + i;
+                if (i < n) o[0] = edge ? __int_as_float(0x7fc00000) : acc[u].x;
+                if (i + 1 < n) o[1] = edge ? __int_as_float(0x7fc00000) : acc[u].y;
             }
+        }
         __syncthreads();                                   // every thread has read the tile
     }
 }
@@ -409,30 +391,25 @@ int convolve(mm_ctx *ctx, const MapObj &M, int profile, double size_re, float *d
         int rc = ctx->arena.alloc(g.size() * sizeof(float), (void **)&dg);
         if (rc) return rc;
         if ((e = cudaMemcpyAsync(dg, g.data(), g.size() * sizeof(float), cudaMemcpyHostToDevice, s)) == cudaSuccess) {
-            const size_t srow = gauss_row_smem(h), scol = gauss_col_smem(h);
+            const size_t smem = gauss_smem(h);
             // tiled passes: as many CTAs as fit the SMs at once (each loops over its tiles)
-            auto resident = [&](const void *fn, size_t smem, long long tiles) {
+            auto resident = [&](const void *fn, long long tiles) {
                 int per_sm = 1;
                 if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem) != cudaSuccess) per_sm = 1;
                 return (int)std::max(1LL, std::min(tiles, (long long)std::max(1, per_sm) * ctx->sms));
             };
-            if (srow <= kGaussSmemMax) {
-                const void *fn = (const void *)k_gauss_rows<true>;
-                e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGaussSmemMax);
-                const long long tiles = (long long)((n + kGRowOut - 1) / kGRowOut) * ((n + kGRows - 1) / kGRows);
-                if (e == cudaSuccess)
-                    k_gauss_rows<true><<<resident(fn, srow, tiles), 256, srow, s>>>(M.counts, nullptr, tmp, n, dg, h,
-                                                                                  inv_nrays);
+            const long long tiles = (long long)((n + kGOut - 1) / kGOut) * ((n + 2 * kGPairs - 1) / (2 * kGPairs));
+            if (smem <= kGaussSmemMax) {
+                const void *fr = (const void *)k_gauss_rows<true>, *fc = (const void *)k_gauss_cols;
+                if ((e = cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGaussSmemMax)) ==
+                        cudaSuccess &&
+                    (e = cudaFuncSetAttribute(fc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGaussSmemMax)) ==
+                        cudaSuccess) {
+                    k_gauss_rows<true><<<resident(fr, tiles), 256, smem, s>>>(M.counts, nullptr, tmp, n, dg, h, inv_nrays);
+                    k_gauss_cols<<<resident(fc, tiles), 256, smem, s>>>(tmp, dst, n, dg, h);
+                }
             } else {
                 k_gauss_pass<true><<<grid, 256, 0, s>>>(M.counts, nullptr, tmp, n, dg, h, 0, inv_nrays);
-            }
-            if (e == cudaSuccess && scol <= kGaussSmemMax) {
-                const void *fn = (const void *)k_gauss_cols;
-                e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGaussSmemMax);
-                const long long tiles = (long long)((n + kGCols - 1) / kGCols) * ((n + kGColOut - 1) / kGColOut);
-                if (e == cudaSuccess)
-                    k_gauss_cols<<<resident(fn, scol, tiles), 256, scol, s>>>(tmp, dst, n, dg, h);
-            } else if (e == cudaSuccess) {
                 k_gauss_pass<false><<<grid, 256, 0, s>>>(nullptr, tmp, dst, n, dg, h, 1, 1.0f);
             }
             if (e == cudaSuccess) e = cudaGetLastError();

@@ -39,7 +39,7 @@ struct StatSums {
     unsigned long long n_both;
     unsigned long long zero_a, zero_b;
     unsigned long long sum_a, sum_b;
-    unsigned int max_count;
+    unsigned int max_count;        // largest count of nbins or more (0: none)
     unsigned int fault;            // a copy into shared memory did not complete in time
     long long ks_num;              // max_k |c_a(k) n_b - c_b(k) n_a|
     unsigned long long over_a, over_b;   // pixels with counts of nbins or more (sent to the lists)
@@ -96,8 +96,8 @@ __device__ __forceinline__ void hist_add(unsigned *h, unsigned key, unsigned lan
 // Per-thread running totals of k_compare.
 struct CmpAcc {
     float qh = 0.f, ql = 0.f;                  // float-float sum of (Delta m_a - Delta m_b)^2 / 6.25
-    unsigned long long both = 0, za = 0, zb = 0, sa = 0, sb = 0;
-    unsigned mx = 0;
+    unsigned long long both = 0;
+    unsigned big_max = 0;                      // largest listed count
 };
 
 // What k_compare computes and where it sends each count.
@@ -135,7 +135,7 @@ __device__ __forceinline__ void rms_pixel(unsigned na, unsigned nb, const CmpArg
 // kWarpBins), the global histogram (below nbins, merged per warp) or the list of large counts.
 __device__ __forceinline__ void hist_key(bool in, unsigned key, unsigned *sbins, unsigned *h, unsigned *list,
                                          unsigned long long *n_list, unsigned long long cap, long long nbins,
-                                         unsigned lane)
+                                         unsigned &big_max, unsigned lane)
 {
     if (in && key < (unsigned)kWarpBins) atomicAdd(sbins + key, 1u);
     const bool mid = in && key >= (unsigned)kWarpBins && key < (unsigned long long)nbins;
@@ -148,30 +148,50 @@ __device__ __forceinline__ void hist_key(bool in, unsigned key, unsigned *sbins,
         base = __shfl_sync(0xffffffffu, base, __ffs(bigm) - 1);
         const unsigned long long slot = base + __popc(bigm & ((1u << lane) - 1u));
         if (big && slot < cap) list[slot] = key;
+        if (big) big_max = max(big_max, key);
     }
 }
 
-__device__ __forceinline__ void cmp_pixel(bool in, unsigned na, unsigned nb, const CmpArgs &g, CmpAcc &acc,
-                                          unsigned *sa, unsigned *sb, StatSums *out, unsigned lane)
+// Four pixels of each map held by every lane of a warp (in: the lane holds pixels). When every count
+// of the warp's 256 is below kWarpBins (the usual case) they go straight to the warp's shared bins;
+// otherwise each key takes hist_key's way.
+__device__ __forceinline__ void cmp_quad(bool in, uint4 x, uint4 y, const CmpArgs &g, CmpAcc &acc, unsigned *sa,
+                                         unsigned *sb, StatSums *out, unsigned lane)
 {
     if (!g.hist_only) {
-        acc.sa += na;
-        acc.sb += nb;
-        acc.za += in && na == 0u;
-        acc.zb += in && nb == 0u;
-        acc.mx = max(acc.mx, max(na, nb));
-        rms_pixel(na, nb, g, acc);
+        rms_pixel(x.x, y.x, g, acc);
+        rms_pixel(x.y, y.y, g, acc);
+        rms_pixel(x.z, y.z, g, acc);
+        rms_pixel(x.w, y.w, g, acc);
     }
-    hist_key(in, na, sa, g.ha, g.la, &out->over_a, g.cap, g.nbins, lane);
-    hist_key(in, nb, sb, g.hb, g.lb, &out->over_b, g.cap, g.nbins, lane);
+    const unsigned m = max(max(max(x.x, x.y), max(x.z, x.w)), max(max(y.x, y.y), max(y.z, y.w)));
+    if (__all_sync(0xffffffffu, m < (unsigned)kWarpBins)) {
+        if (in) {
+            atomicAdd(sa + x.x, 1u);
+            atomicAdd(sa + x.y, 1u);
+            atomicAdd(sa + x.z, 1u);
+            atomicAdd(sa + x.w, 1u);
+            atomicAdd(sb + y.x, 1u);
+            atomicAdd(sb + y.y, 1u);
+            atomicAdd(sb + y.z, 1u);
+            atomicAdd(sb + y.w, 1u);
+        }
+        return;
+    }
+    const unsigned ka[4] = {x.x, x.y, x.z, x.w}, kb[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        hist_key(in, ka[u], sa, g.ha, g.la, &out->over_a, g.cap, g.nbins, acc.big_max, lane);
+        hist_key(in, kb[u], sb, g.hb, g.lb, &out->over_b, g.cap, g.nbins, acc.big_max, lane);
+    }
 }
 
-// One pass over both maps: the sums, empty pixels and largest count; the RMS of
-// Delta m_a - Delta m_b; the count histograms below nbins and the lists of larger counts.
-// A CTA takes chunks blockIdx.x, blockIdx.x + gridDim.x, ... of kCmpChunk bytes of each map (the
-// first 4 floor(n / 4) pixels; the last n % 4 go to warp 0 of block 0 with plain loads); thread 0
-// keeps kCmpStages chunks in flight. A copy that does not land within the wait limit sets
-// out->fault; the CTA then waits (again with the limit) for its other copies and leaves.
+// One pass over both maps: the RMS of Delta m_a - Delta m_b and the count histograms below nbins,
+// with the larger counts listed (their number per map and the largest go to out). A CTA takes
+// chunks blockIdx.x, blockIdx.x + gridDim.x, ... of kCmpChunk bytes of each map (the first
+// 4 floor(n / 4) pixels; the last n % 4 go to warp 0 of block 0 with plain loads); thread 0 keeps
+// kCmpStages chunks in flight. A copy that does not land within the wait limit sets out->fault; the
+// CTA then waits (again with the limit) for its other copies and leaves.
 __global__ void __launch_bounds__(kCmpThreads) k_compare(const unsigned *a, const unsigned *b, long long n, CmpArgs g,
                                                           StatSums *out)
 {
@@ -223,40 +243,32 @@ __global__ void __launch_bounds__(kCmpThreads) k_compare(const unsigned *a, cons
         for (int q0 = warp * 32; q0 < quads; q0 += kCmpThreads) {            // warp-uniform trip count
             const int q = q0 + (int)lane;
             const bool in = q < quads;
-            const uint4 x = in ? va[q] : make_uint4(0u, 0u, 0u, 0u), y = in ? vb[q] : make_uint4(0u, 0u, 0u, 0u);
-            cmp_pixel(in, x.x, y.x, g, acc, sa, sb, out, lane);
-            cmp_pixel(in, x.y, y.y, g, acc, sa, sb, out, lane);
-            cmp_pixel(in, x.z, y.z, g, acc, sa, sb, out, lane);
-            cmp_pixel(in, x.w, y.w, g, acc, sa, sb, out, lane);
+            cmp_quad(in, in ? va[q] : make_uint4(0u, 0u, 0u, 0u), in ? vb[q] : make_uint4(0u, 0u, 0u, 0u), g, acc, sa,
+                     sb, out, lane);
         }
         __syncthreads();                                                     // stage s read by every thread
         if (threadIdx.x == 0 && i + kCmpStages < mine) issue(i + kCmpStages);
     }
-    if (blockIdx.x == 0 && warp == 0) {                                      // the last n % 4 pixels
+    if (blockIdx.x == 0 && warp == 0) {                                      // the last n % 4 pixels, one each
         const long long k = 4 * (n / 4) + lane;
         const bool in = k < n;
-        cmp_pixel(in, in ? a[k] : 0u, in ? b[k] : 0u, g, acc, sa, sb, out, lane);
+        const unsigned ka = in ? a[k] : 0u, kb = in ? b[k] : 0u;
+        if (!g.hist_only) rms_pixel(ka, kb, g, acc);
+        hist_key(in, ka, sa, g.ha, g.la, &out->over_a, g.cap, g.nbins, acc.big_max, lane);
+        hist_key(in, kb, sb, g.hb, g.lb, &out->over_b, g.cap, g.nbins, acc.big_max, lane);
     }
-    if (!g.hist_only) {
-        double sq = 6.25 * ((double)acc.qh + (double)acc.ql);                // Delta m differences carry -2.5
-        for (int o = 16; o > 0; o >>= 1) {
-            sq += __shfl_down_sync(0xffffffffu, sq, o);
-            acc.both += __shfl_down_sync(0xffffffffu, acc.both, o);
-            acc.za += __shfl_down_sync(0xffffffffu, acc.za, o);
-            acc.zb += __shfl_down_sync(0xffffffffu, acc.zb, o);
-            acc.sa += __shfl_down_sync(0xffffffffu, acc.sa, o);
-            acc.sb += __shfl_down_sync(0xffffffffu, acc.sb, o);
-            acc.mx = max(acc.mx, __shfl_down_sync(0xffffffffu, acc.mx, o));
-        }
-        if (lane == 0) {
+    double sq = 6.25 * ((double)acc.qh + (double)acc.ql);                    // Delta m differences carry -2.5
+    for (int o = 16; o > 0; o >>= 1) {
+        sq += __shfl_down_sync(0xffffffffu, sq, o);
+        acc.both += __shfl_down_sync(0xffffffffu, acc.both, o);
+        acc.big_max = max(acc.big_max, __shfl_down_sync(0xffffffffu, acc.big_max, o));
+    }
+    if (lane == 0) {
+        if (!g.hist_only) {
             atomicAdd(&out->sum_sq, sq);
             atomicAdd(&out->n_both, acc.both);
-            atomicAdd(&out->zero_a, acc.za);
-            atomicAdd(&out->zero_b, acc.zb);
-            atomicAdd(&out->sum_a, acc.sa);
-            atomicAdd(&out->sum_b, acc.sb);
-            atomicMax(&out->max_count, acc.mx);
         }
+        if (acc.big_max) atomicMax(&out->max_count, acc.big_max);
     }
     __syncthreads();
     for (int k = threadIdx.x; k < 2 * kWarpBins; k += kCmpThreads) {         // the 8 warp copies of each bin
@@ -274,22 +286,46 @@ __global__ void k_list_hist(const unsigned *list, unsigned long long m, unsigned
 }
 
 // One CTA of 1024 threads: inclusive prefix sums ca[k], cb[k] of the two count
-// histograms (so P(N >= k) = (n - c[k-1]) / n).
+// histograms (so P(N >= k) = (n - c[k-1]) / n), and from the histograms the empty pixels
+// (bin 0) and the total count sum_k k h[k] of each map, written to out.
 __global__ void __launch_bounds__(1024) k_scan(const unsigned *ha, const unsigned *hb, long long nbins, long long *ca,
-                                               long long *cb)
+                                               long long *cb, StatSums *out)
 {
     __shared__ long long sa[1024], sb[1024];
+    __shared__ unsigned long long wsum[2][32];
     const int t = threadIdx.x;
     const long long per = (nbins + 1023) / 1024;
     const long long lo = min(nbins, t * per), hi = min(nbins, lo + per);
     long long ta = 0, tb = 0;
+    unsigned long long ma = 0, mb = 0;             // sum of k h[k] over this thread's bins
     for (long long k = lo; k < hi; ++k) {
         ta += ha[k];
         tb += hb[k];
+        ma += (unsigned long long)k * ha[k];
+        mb += (unsigned long long)k * hb[k];
     }
     sa[t] = ta;
     sb[t] = tb;
+    for (int o = 16; o > 0; o >>= 1) {
+        ma += __shfl_down_sync(0xffffffffu, ma, o);
+        mb += __shfl_down_sync(0xffffffffu, mb, o);
+    }
+    if ((t & 31) == 0) {
+        wsum[0][t >> 5] = ma;
+        wsum[1][t >> 5] = mb;
+    }
     __syncthreads();
+    if (t == 0) {
+        unsigned long long za = 0, zb = 0;
+        for (int w = 0; w < 32; ++w) {
+            za += wsum[0][w];
+            zb += wsum[1][w];
+        }
+        out->sum_a = za;
+        out->sum_b = zb;
+        out->zero_a = nbins > 0 ? ha[0] : 0u;
+        out->zero_b = nbins > 0 ? hb[0] : 0u;
+    }
     for (int o = 1; o < 1024; o <<= 1) {           // inclusive scan of the per-thread totals
         const long long va = (t >= o) ? sa[t - o] : 0, vb = (t >= o) ? sb[t - o] : 0;
         __syncthreads();
@@ -419,7 +455,7 @@ extern "C" int mm_map_compare(mm_ctx *ctx, mm_map a, mm_map b, mm_compare *out)
     CmpArgs g{tab, tab + T, lra, lrb, T, hist, hist + T, lists, lists + cap, cap, 0};
     k_compare<<<cgrid, kCmpThreads, kCmpSmem, s>>>(A->counts, B->counts, n, g, d_sum);
     auto ks_steps = [&](const unsigned *h2, long long *c2, long long nb) {
-        k_scan<<<1, 1024, 0, s>>>(h2, h2 + nb, nb, c2, c2 + nb);
+        k_scan<<<1, 1024, 0, s>>>(h2, h2 + nb, nb, c2, c2 + nb, d_sum);
         const int egrid = std::max(1, std::min(4 * ctx->sms, (int)((2 * nb + 255) / 256)));
         k_ks_eval<<<egrid, 256, 0, s>>>(h2, h2 + nb, c2, c2 + nb, nb, n, n, A->p.nrays_per_pix, B->p.nrays_per_pix,
                                         d_sum);

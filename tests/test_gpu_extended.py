@@ -57,9 +57,9 @@ def test_profile_wider_than_map_rejected(shot):
 
 
 # Wide supports: the tiled kernels stage their tiles in shared memory, two tiles of a Gaussian pass
-# in 95 KB (the row pass up to a half-width of 123 pixels, the column pass up to 124) and a disc's
-# tile in 48 KB (up to a radius of 15 pixels); wider supports run the untiled kernels. Sizes on both
-# sides of each limit, on a 320^2 map.
+# in at most 200 KB (up to a half-width of 131 pixels) and a disc's tile in 48 KB (up to a radius of
+# 15 pixels); wider supports run the untiled kernels. Sizes on both sides of each limit, on a 320^2
+# map.
 CFG_WIDE = dict(CFG, npix_side=320, side=7.5)            # pixel 0.0234375 R_E
 
 
@@ -77,7 +77,8 @@ def shot_wide():
 
 
 @pytest.mark.parametrize("profile,size,half_width", [
-    (mm.MM_PROFILE_GAUSSIAN, 0.7177734375, 123), (mm.MM_PROFILE_GAUSSIAN, 0.7294921875, 125),
+    (mm.MM_PROFILE_GAUSSIAN, 0.7177734375, 123), (mm.MM_PROFILE_GAUSSIAN, 0.7646484375, 131),
+    (mm.MM_PROFILE_GAUSSIAN, 0.7705078125, 132),
     (mm.MM_PROFILE_DISC, 0.3633, 15), (mm.MM_PROFILE_DISC, 0.5039, 21)])
 def test_wide_supports_match_oracle(shot_wide, profile, size, half_width):
     ctx, m, counts = shot_wide
