@@ -26,6 +26,12 @@ __device__ __forceinline__ void mbar_arrive_expect(uint64_t *bar, unsigned bytes
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
 }
 
+// Arrive once on bar (no copies announced).
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 // Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned) from global to this CTA's
 // shared memory, counted on bar when it lands.
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar)
@@ -64,6 +70,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
 __device__ __forceinline__ void cp_async4(void *dst, const void *src, unsigned src_bytes)
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+// 16-byte asynchronous copy global -> shared (both addresses 16-byte aligned); bytes past src_bytes
+// (0, 4, 8, 12 or 16) are written as zeros.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, unsigned src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src), "r"(src_bytes)
                  : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }

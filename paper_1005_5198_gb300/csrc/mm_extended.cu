@@ -23,7 +23,8 @@ namespace mm {
 namespace {
 
 // Separable pass: out[j][i] = sum_k g[k] in[j][i + k - h] (dir 0) or in[j + k - h][i] (dir 1);
-// NaN where the support leaves the map. Input counts (dir 0, scaled by inv_nrays) or floats.
+// NaN where the support leaves the map. Input counts (scaled by inv_nrays) or floats. Untiled
+// maps run dir 1 from the counts, then dir 0.
 template <bool FROM_COUNTS>
 __global__ void k_gauss_pass(const unsigned *cin, const float *fin, float *out, int n, const float *g, int h, int dir,
                              float inv_nrays)
@@ -75,20 +76,23 @@ constexpr size_t kTileSmemMax = 48 * 1024;             // dynamic shared memory 
 constexpr size_t kGaussSmemMax = 200 * 1024;           // a double-buffered Gaussian CTA (h <= 131; wider
                                                        // supports take the untiled kernel)
 
-// Gaussian passes on packed pairs: the two lanes of every packed f32x2 FMA are the same output of two
-// neighbouring rows (row pass) or columns (column pass), so that one 8-byte shared load gives an
-// operand pair and the taps are pairs (g, g). A thread owns 16 consecutive outputs along the pass
-// direction of its pair of rows or columns and runs the taps in chunks of 8: per chunk it loads the
-// 23 input pairs the 16 outputs need once and makes 128 packed FMAs from them. The taps are padded
-// with zero weights to TP, a multiple of 8; a padded tap reads a zero staged beyond the support and
-// leaves a sum unchanged (every sum is non-negative). Every output adds its taps in order (a
-// correctly rounded FMA each, tap 0 first), exactly as k_gauss_pass. A CTA holds two tiles: while
-// it computes one, the next one's inputs arrive by cp.async.
-constexpr int kGOut = 128;                              // outputs per tile along the pass (8 warps x 16)
-constexpr int kGPairs = 32;                             // pairs of rows (columns) per tile, one per lane
+// Gaussian passes (tiled): one kernel, k_gauss_vt, convolves its input down the columns and writes
+// the result transposed. Run on the counts it gives V^T, V the column pass; run on V^T it gives the
+// row pass of V in the map's own orientation. The two lanes of every packed f32x2 FMA are the same
+// output of two neighbouring columns, so one 8-byte shared load gives an operand pair and the taps
+// are pairs (g, g). A thread owns 16 consecutive outputs down its pair of columns and runs the taps
+// in chunks of 8: per chunk it loads the 23 input pairs the 16 outputs need once and makes 128
+// packed FMAs from them. The taps are padded with zero weights to TP, a multiple of 8; a padded tap
+// leaves a sum unchanged (0 times a finite input is 0, and every sum is non-negative) or meets only
+// an input column that is NaN throughout, whose outputs are NaN anyway. Every output adds its taps
+// in order (a correctly rounded FMA each, tap 0 first), exactly as k_gauss_pass. A CTA holds two
+// tiles: while it computes one, the next one's inputs arrive by cp.async (16-byte copies when
+// N_side is a multiple of 4, 4-byte copies otherwise).
+constexpr int kGOut = 128;                              // outputs per tile down the columns (8 warps x 16)
+constexpr int kGPairs = 32;                             // pairs of columns per tile (64 columns), one per lane
 
 __host__ __device__ inline int gauss_taps_padded(int h) { return (2 * h + 1 + 7) & ~7; }
-// inputs staged along the pass: 128 + TP - 1 (odd, so that the pairs' rows hit distinct banks)
+// input rows staged per tile: 128 + TP - 1
 __host__ __device__ inline int gauss_span(int h) { return kGOut + gauss_taps_padded(h) - 1; }
 __host__ __device__ inline size_t gauss_tile_floats(int h) { return (size_t)2 * kGPairs * gauss_span(h); }
 __host__ __device__ inline size_t gauss_smem(int h)
@@ -119,107 +123,42 @@ __device__ __forceinline__ void gauss_taps2(const float2 *gs2, int tp, const flo
     }
 }
 
-// Taps g[0 .. 2h] as pairs (g, g), zero up to TP.
-__device__ __forceinline__ void gauss_stage_taps(const float *g, int h, float2 *gs2)
+// out_t[i][j] = sum_k g[k] in[j + k - h][i] (NaN where j - h < 0 or j + h >= n): a tile is input rows
+// [r0 - h, r0 - h + span) of 64 columns [c0, c0 + 64), row-major (zeros outside the map), so that
+// columns 2l, 2l + 1 of a row form a pair; lane l takes those two columns, warp w the outputs
+// r0 + 16 w .. + 16. Tiles t, t + gridDim.x, ...; each thread copies the same elements of every tile
+// and, from counts (mu = N inv_nrays), converts those it copied once they have landed.
+template <bool FROM_COUNTS>
+__global__ void __launch_bounds__(256, 1) k_gauss_vt(const void *in, float *out_t, int n, const float *g, int h,
+                                                     float inv_nrays)
 {
-    for (int k = threadIdx.x; k < gauss_taps_padded(h); k += blockDim.x) {
+    extern __shared__ float4 sm4[];
+    const int tp = gauss_taps_padded(h), S = gauss_span(h);
+    float2 *const gs2 = reinterpret_cast<float2 *>(sm4);
+    float *const buf0 = reinterpret_cast<float *>(gs2 + tp), *const buf1 = buf0 + gauss_tile_floats(h);
+    for (int k = threadIdx.x; k < tp; k += blockDim.x) {       // taps as pairs, zero up to TP
         const float v = k <= 2 * h ? g[k] : 0.f;
         gs2[k] = make_float2(v, v);
     }
-}
-
-// Row pass (dir 0 of k_gauss_pass): a tile is rows [r0, r0 + 64) x input columns
-// [c0 - h, c0 - h + span), staged as pairs of rows: element (row 2p + e, column x) at float
-// 2 (p span + x) + e, as floats (zeros outside the map and beyond the support). Lane l takes rows
-// r0 + 2l, r0 + 2l + 1, warp w outputs c0 + 16 w .. + 16. The outputs go back through the tile's
-// shared memory so that the global stores run along rows. Tiles t, t + gridDim.x, ...; each thread
-// copies the same elements of every tile (4-byte cp.async, zero-filled) and, from counts, converts
-// those it copied once they have landed.
-template <bool FROM_COUNTS>
-__global__ void __launch_bounds__(256, 1) k_gauss_rows(const unsigned *cin, const float *fin, float *out, int n,
-                                                       const float *g, int h, float inv_nrays)
-{
-    extern __shared__ float4 sm4[];
-    const int tp = gauss_taps_padded(h), S = gauss_span(h), W = kGOut + 2 * h;
-    float2 *const gs2 = reinterpret_cast<float2 *>(sm4);
-    float *const buf0 = reinterpret_cast<float *>(gs2 + tp), *const buf1 = buf0 + gauss_tile_floats(h);
-    gauss_stage_taps(g, h, gs2);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int cols = (n + kGOut - 1) / kGOut, rows = (n + 2 * kGPairs - 1) / (2 * kGPairs);
-    const long long tiles = (long long)cols * rows;
-    auto stage = [&](long long t, float *tile) {
-        const int c0 = (int)(t % cols) * kGOut, r0 = (int)(t / cols) * (2 * kGPairs);
-        for (int rr = w; rr < 2 * kGPairs; rr += 8) {       // warp w stages rows w, w + 8, ...
-            const int j = r0 + rr;
-            float *const dst = tile + 2 * (rr >> 1) * S + (rr & 1);
-            for (int x = lane; x < S; x += 32) {
-                const int i = c0 - h + x;
-                const bool ok = x < W && j < n && i >= 0 && i < n;
-                const long long src = ok ? (long long)j * n + i : 0;
-                cp_async4(dst + 2 * x, FROM_COUNTS ? (const void *)(cin + src) : (const void *)(fin + src), ok ? 4u : 0u);
-            }
-        }
-        cp_async_commit();
-    };
-    if (blockIdx.x < tiles) stage(blockIdx.x, buf0);
-    int b = 0;
-    for (long long t = blockIdx.x; t < tiles; t += gridDim.x, b ^= 1) {
-        float *const tile = b ? buf1 : buf0;
-        const long long tn = t + gridDim.x;
-        if (tn < tiles) {                                  // the other buffer was released at the end of
-            stage(tn, b ? buf0 : buf1);                    // the previous tile
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        if (FROM_COUNTS)                                   // the elements this thread copied, now landed
-            for (int rr = w; rr < 2 * kGPairs; rr += 8) {
-                float *const row = tile + 2 * (rr >> 1) * S + (rr & 1);
-                for (int x = lane; x < S; x += 32) row[2 * x] = (float)__float_as_uint(row[2 * x]) * inv_nrays;
-            }
-        __syncthreads();                                   // tile t staged; taps staged
-        float2 *const t2 = reinterpret_cast<float2 *>(tile);
-        float2 acc[16];
-        gauss_taps2(gs2, tp, t2 + lane * S + w * 16, 1, acc);
-        __syncthreads();                                   // every thread has read the inputs
-#pragma unroll
-        for (int u = 0; u < 16; ++u) t2[lane * S + w * 16 + u] = acc[u];
-        __syncthreads();
-        const int c0 = (int)(t % cols) * kGOut, r0 = (int)(t / cols) * (2 * kGPairs);
-        for (int rr = w; rr < 2 * kGPairs; rr += 8) {
-            const int j = r0 + rr;
-            const float *const row = tile + 2 * (rr >> 1) * S + (rr & 1);
-            for (int x = lane; x < kGOut; x += 32) {
-                const int i = c0 + x;
-                if (j < n && i < n)
-                    out[(long long)j * n + i] = (i - h >= 0 && i + h < n) ? row[2 * x] : __int_as_float(0x7fc00000);
-            }
-        }
-        __syncthreads();                                   // the tile's buffer is free for tile t + 2 gridDim.x
-    }
-}
-
-// Column pass (dir 1): a tile is input rows [r0 - h, r0 - h + span) of 64 columns [c0, c0 + 64),
-// row-major, so that columns 2l, 2l + 1 of a row form a pair. Lane l takes columns c0 + 2l,
-// c0 + 2l + 1, warp w the output rows r0 + 16 w .. + 16 (stores along rows). Tiles and copies as
-// in the row pass.
-__global__ void __launch_bounds__(256, 1) k_gauss_cols(const float *fin, float *out, int n, const float *g, int h)
-{
-    extern __shared__ float4 sm4[];
-    const int tp = gauss_taps_padded(h), S = gauss_span(h), H2 = kGOut + 2 * h;
-    float2 *const gs2 = reinterpret_cast<float2 *>(sm4);
-    float *const buf0 = reinterpret_cast<float *>(gs2 + tp), *const buf1 = buf0 + gauss_tile_floats(h);
-    gauss_stage_taps(g, h, gs2);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int cols = (n + 2 * kGPairs - 1) / (2 * kGPairs), rows = (n + kGOut - 1) / kGOut;
     const long long tiles = (long long)cols * rows;
-    const int E = 2 * kGPairs * S;
+    const bool vec = (n & 3) == 0;                             // rows start on 16-byte boundaries
+    const unsigned *const src_u = static_cast<const unsigned *>(in);
     auto stage = [&](long long t, float *tile) {
         const int c0 = (int)(t % cols) * (2 * kGPairs), r0 = (int)(t / cols) * kGOut;
-        for (int q = threadIdx.x; q < E; q += blockDim.x) {   // row q / 64, column q % 64
-            const int rr = q >> 6, i = c0 + (q & 63), j = r0 - h + rr;
-            const bool ok = rr < H2 && j >= 0 && j < n && i < n;
-            cp_async4(tile + q, fin + (ok ? (long long)j * n + i : 0), ok ? 4u : 0u);
+        if (vec) {
+            for (int q = threadIdx.x; q < S * 16; q += blockDim.x) {   // row q / 16, columns 4 (q % 16) ..
+                const int j = r0 - h + (q >> 4), i = c0 + 4 * (q & 15);
+                const int cnt = (j >= 0 && j < n) ? max(0, min(4, n - i)) : 0;
+                cp_async16(tile + 4 * q, src_u + (cnt ? (long long)j * n + i : 0), 4u * cnt);
+            }
+        } else {
+            for (int q = threadIdx.x; q < S * 64; q += blockDim.x) {   // row q / 64, column q % 64
+                const int j = r0 - h + (q >> 6), i = c0 + (q & 63);
+                const bool ok = j >= 0 && j < n && i < n;
+                cp_async4(tile + q, src_u + (ok ? (long long)j * n + i : 0), ok ? 4u : 0u);
+            }
         }
         cp_async_commit();
     };
@@ -228,28 +167,51 @@ __global__ void __launch_bounds__(256, 1) k_gauss_cols(const float *fin, float *
     for (long long t = blockIdx.x; t < tiles; t += gridDim.x, b ^= 1) {
         float *const tile = b ? buf1 : buf0;
         const long long tn = t + gridDim.x;
-        if (tn < tiles) {
-            stage(tn, b ? buf0 : buf1);
+        if (tn < tiles) {                                      // the other buffer was released at the end
+            stage(tn, b ? buf0 : buf1);                        // of the previous tile
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
         }
-        __syncthreads();
+        if (FROM_COUNTS) {                                     // the elements this thread copied, now landed
+            if (vec) {
+                for (int q = threadIdx.x; q < S * 16; q += blockDim.x) {
+                    float4 *const p4 = reinterpret_cast<float4 *>(tile) + q;
+                    const uint4 c = *reinterpret_cast<const uint4 *>(p4);
+                    *p4 = make_float4((float)c.x * inv_nrays, (float)c.y * inv_nrays, (float)c.z * inv_nrays,
+                                      (float)c.w * inv_nrays);
+                }
+            } else {
+                for (int q = threadIdx.x; q < S * 64; q += blockDim.x)
+                    tile[q] = (float)__float_as_uint(tile[q]) * inv_nrays;
+            }
+        }
+        __syncthreads();                                       // tile t staged; taps staged
         float2 acc[16];
         gauss_taps2(gs2, tp, reinterpret_cast<const float2 *>(tile) + (w * 16) * kGPairs + lane, kGPairs, acc);
         const int c0 = (int)(t % cols) * (2 * kGPairs), r0 = (int)(t / cols) * kGOut;
-        const int i = c0 + 2 * lane;
+        const int j0 = r0 + w * 16;
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const int j = r0 + w * 16 + u;
-            if (j < n) {
-                const bool edge = j - h < 0 || j + h >= n;
-                float *const o = out + (long long)j * n + i;
-                if (i < n) o[0] = edge ? __int_as_float(0x7fc00000) : acc[u].x;
-                if (i + 1 < n) o[1] = edge ? __int_as_float(0x7fc00000) : acc[u].y;
+        for (int e = 0; e < 2; ++e) {
+            const int i = c0 + 2 * lane + e;
+            if (i >= n) continue;
+            float v[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int j = j0 + u;
+                v[u] = (j - h < 0 || j + h >= n) ? __int_as_float(0x7fc00000) : (e ? acc[u].y : acc[u].x);
+            }
+            float *const o = out_t + (long long)i * n + j0;
+            if (vec && j0 + 16 <= n) {
+#pragma unroll
+                for (int u = 0; u < 16; u += 4) *reinterpret_cast<float4 *>(o + u) = make_float4(v[u], v[u + 1], v[u + 2], v[u + 3]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 16; ++u)
+                    if (j0 + u < n) o[u] = v[u];
             }
         }
-        __syncthreads();                                   // every thread has read the tile
+        __syncthreads();                                       // every thread has read the tile
     }
 }
 
@@ -392,25 +354,26 @@ int convolve(mm_ctx *ctx, const MapObj &M, int profile, double size_re, float *d
         if (rc) return rc;
         if ((e = cudaMemcpyAsync(dg, g.data(), g.size() * sizeof(float), cudaMemcpyHostToDevice, s)) == cudaSuccess) {
             const size_t smem = gauss_smem(h);
-            // tiled passes: as many CTAs as fit the SMs at once (each loops over its tiles)
-            auto resident = [&](const void *fn, long long tiles) {
+            // tiled passes: as many CTAs as fit the SMs at once (each loops over its tiles); the
+            // column pass from the counts, written transposed, then the same kernel on it
+            const long long tiles = (long long)((n + 2 * kGPairs - 1) / (2 * kGPairs)) * ((n + kGOut - 1) / kGOut);
+            auto resident = [&](const void *fn) {
                 int per_sm = 1;
                 if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem) != cudaSuccess) per_sm = 1;
                 return (int)std::max(1LL, std::min(tiles, (long long)std::max(1, per_sm) * ctx->sms));
             };
-            const long long tiles = (long long)((n + kGOut - 1) / kGOut) * ((n + 2 * kGPairs - 1) / (2 * kGPairs));
             if (smem <= kGaussSmemMax) {
-                const void *fr = (const void *)k_gauss_rows<true>, *fc = (const void *)k_gauss_cols;
-                if ((e = cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGaussSmemMax)) ==
+                const void *f1 = (const void *)k_gauss_vt<true>, *f2 = (const void *)k_gauss_vt<false>;
+                if ((e = cudaFuncSetAttribute(f1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGaussSmemMax)) ==
                         cudaSuccess &&
-                    (e = cudaFuncSetAttribute(fc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGaussSmemMax)) ==
+                    (e = cudaFuncSetAttribute(f2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGaussSmemMax)) ==
                         cudaSuccess) {
-                    k_gauss_rows<true><<<resident(fr, tiles), 256, smem, s>>>(M.counts, nullptr, tmp, n, dg, h, inv_nrays);
-                    k_gauss_cols<<<resident(fc, tiles), 256, smem, s>>>(tmp, dst, n, dg, h);
+                    k_gauss_vt<true><<<resident(f1), 256, smem, s>>>(M.counts, tmp, n, dg, h, inv_nrays);
+                    k_gauss_vt<false><<<resident(f2), 256, smem, s>>>(tmp, dst, n, dg, h, 1.0f);
                 }
-            } else {
-                k_gauss_pass<true><<<grid, 256, 0, s>>>(M.counts, nullptr, tmp, n, dg, h, 0, inv_nrays);
-                k_gauss_pass<false><<<grid, 256, 0, s>>>(nullptr, tmp, dst, n, dg, h, 1, 1.0f);
+            } else {                                           // the same sums: columns, then rows
+                k_gauss_pass<true><<<grid, 256, 0, s>>>(M.counts, nullptr, tmp, n, dg, h, 1, inv_nrays);
+                k_gauss_pass<false><<<grid, 256, 0, s>>>(nullptr, tmp, dst, n, dg, h, 0, 1.0f);
             }
             if (e == cudaSuccess) e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -25,14 +25,17 @@ namespace mm {
 namespace {
 
 // The comparison reads both maps once (k_compare), streaming them through shared memory in chunks
-// of kCmpChunk bytes per map with bulk copies, kCmpStages chunks in flight per CTA; a chunk's pixels
-// are then read from shared memory with 16-byte loads. Histograms: per-warp copies of the bins below
-// kWarpBins in shared memory (8 warps x 2 maps x 512 bins, 32 KB).
-constexpr int kCmpThreads = 256;
+// of kCmpChunk bytes per map: a producer warp keeps kCmpStages chunks in flight with bulk copies,
+// and 8 consumer warps read each chunk's pixels with 16-byte loads, releasing its stage per warp.
+// Histograms: the bins below kWarpBins in shared memory, one copy per pair of consumer warps
+// (4 copies x 2 maps x 1024 bins, 32 KB); 64 KB of shared memory per CTA, 3 CTAs per SM.
+constexpr int kCmpConsumers = 8;
+constexpr int kCmpThreads = 32 * (kCmpConsumers + 1);
 constexpr int kCmpStages = 4;
 constexpr int kCmpChunk = 4096;
-constexpr int kWarpBins = 512;
-constexpr size_t kCmpSmem = (size_t)kCmpStages * 2 * kCmpChunk + 64 + (size_t)8 * 2 * kWarpBins * 4;
+constexpr int kWarpBins = 1024;
+constexpr int kBinCopies = kCmpConsumers / 2;
+constexpr size_t kCmpSmem = (size_t)kCmpStages * 2 * kCmpChunk + 128 + (size_t)kBinCopies * 2 * kWarpBins * 4;
 
 struct StatSums {
     double sum_sq;                 // sum of (Delta m_a - Delta m_b)^2 over pixels counted in both maps
@@ -96,7 +99,7 @@ __device__ __forceinline__ void hist_add(unsigned *h, unsigned key, unsigned lan
 // Per-thread running totals of k_compare.
 struct CmpAcc {
     float qh = 0.f, ql = 0.f;                  // float-float sum of (Delta m_a - Delta m_b)^2 / 6.25
-    unsigned long long both = 0;
+    unsigned both = 0;                         // pixels counted in both maps
     unsigned big_max = 0;                      // largest listed count
 };
 
@@ -117,18 +120,18 @@ struct CmpArgs {
 // the difference and its square in float-float (about 1e-14 relative), over pixels counted in both.
 __device__ __forceinline__ void rms_pixel(unsigned na, unsigned nb, const CmpArgs &g, CmpAcc &acc)
 {
-    if (na && nb) {
-        const float2 x = na < (unsigned long long)g.nbins ? __ldg(g.ta + na) : log_pair(na, g.lra);
-        const float2 y = nb < (unsigned long long)g.nbins ? __ldg(g.tb + nb) : log_pair(nb, g.lrb);
-        float dh, dl;
-        ff_two_sum(x.x, -y.x, dh, dl);
-        dl = __fadd_rn(dl, __fsub_rn(x.y, y.y));
-        const float d = __fadd_rn(dh, dl), de = __fsub_rn(dl, __fsub_rn(d, dh));
-        const float ph = __fmul_rn(d, d);
-        const float pl = __fmaf_rn(d, d, -ph) + 2.f * d * de;
-        ff_accumulate(acc.qh, acc.ql, ph, pl);
-        acc.both += 1;
-    }
+    // every pixel runs the arithmetic (no divergence); a pixel empty in either map adds zero
+    const bool use = na && nb;
+    const float2 x = na < (unsigned long long)g.nbins ? __ldg(g.ta + na) : log_pair(na, g.lra);
+    const float2 y = nb < (unsigned long long)g.nbins ? __ldg(g.tb + nb) : log_pair(nb, g.lrb);
+    float dh, dl;
+    ff_two_sum(x.x, -y.x, dh, dl);
+    dl = __fadd_rn(dl, __fsub_rn(x.y, y.y));
+    const float d = __fadd_rn(dh, dl), de = __fsub_rn(dl, __fsub_rn(d, dh));
+    const float ph = __fmul_rn(d, d);
+    const float pl = __fmaf_rn(d, d, -ph) + 2.f * d * de;
+    ff_accumulate(acc.qh, acc.ql, use ? ph : 0.f, use ? pl : 0.f);
+    acc.both += use;
 }
 
 // Count the key of one lane (in: the lane holds a pixel) into the warp's shared bins (keys below
@@ -152,9 +155,9 @@ __device__ __forceinline__ void hist_key(bool in, unsigned key, unsigned *sbins,
     }
 }
 
-// Four pixels of each map held by every lane of a warp (in: the lane holds pixels). When every count
-// of the warp's 256 is below kWarpBins (the usual case) they go straight to the warp's shared bins;
-// otherwise each key takes hist_key's way.
+// Four pixels of each map held by every lane of a warp (in: the lane holds pixels). Keys below
+// kWarpBins go straight to the shared bins; when a key of the warp's 256 is larger (rare), the
+// larger keys take hist_key's way, one key position at a time.
 __device__ __forceinline__ void cmp_quad(bool in, uint4 x, uint4 y, const CmpArgs &g, CmpAcc &acc, unsigned *sa,
                                          unsigned *sb, StatSums *out, unsigned lane)
 {
@@ -164,44 +167,43 @@ __device__ __forceinline__ void cmp_quad(bool in, uint4 x, uint4 y, const CmpArg
         rms_pixel(x.z, y.z, g, acc);
         rms_pixel(x.w, y.w, g, acc);
     }
-    const unsigned m = max(max(max(x.x, x.y), max(x.z, x.w)), max(max(y.x, y.y), max(y.z, y.w)));
-    if (__all_sync(0xffffffffu, m < (unsigned)kWarpBins)) {
-        if (in) {
-            atomicAdd(sa + x.x, 1u);
-            atomicAdd(sa + x.y, 1u);
-            atomicAdd(sa + x.z, 1u);
-            atomicAdd(sa + x.w, 1u);
-            atomicAdd(sb + y.x, 1u);
-            atomicAdd(sb + y.y, 1u);
-            atomicAdd(sb + y.z, 1u);
-            atomicAdd(sb + y.w, 1u);
-        }
-        return;
-    }
     const unsigned ka[4] = {x.x, x.y, x.z, x.w}, kb[4] = {y.x, y.y, y.z, y.w};
+    if (in) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        hist_key(in, ka[u], sa, g.ha, g.la, &out->over_a, g.cap, g.nbins, acc.big_max, lane);
-        hist_key(in, kb[u], sb, g.hb, g.lb, &out->over_b, g.cap, g.nbins, acc.big_max, lane);
+        for (int u = 0; u < 4; ++u) {
+            if (ka[u] < (unsigned)kWarpBins) atomicAdd(sa + ka[u], 1u);
+            if (kb[u] < (unsigned)kWarpBins) atomicAdd(sb + kb[u], 1u);
+        }
+    }
+    const unsigned m = max(max(max(x.x, x.y), max(x.z, x.w)), max(max(y.x, y.y), max(y.z, y.w)));
+    if (__all_sync(0xffffffffu, m < (unsigned)kWarpBins)) return;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {                          // only keys of kWarpBins or more are left
+        hist_key(in && ka[u] >= (unsigned)kWarpBins, ka[u], sa, g.ha, g.la, &out->over_a, g.cap, g.nbins, acc.big_max,
+                 lane);
+        hist_key(in && kb[u] >= (unsigned)kWarpBins, kb[u], sb, g.hb, g.lb, &out->over_b, g.cap, g.nbins, acc.big_max,
+                 lane);
     }
 }
 
 // One pass over both maps: the RMS of Delta m_a - Delta m_b and the count histograms below nbins,
 // with the larger counts listed (their number per map and the largest go to out). A CTA takes
 // chunks blockIdx.x, blockIdx.x + gridDim.x, ... of kCmpChunk bytes of each map (the first
-// 4 floor(n / 4) pixels; the last n % 4 go to warp 0 of block 0 with plain loads); thread 0 keeps
-// kCmpStages chunks in flight. A copy that does not land within the wait limit sets out->fault; the
-// CTA then waits (again with the limit) for its other copies and leaves.
+// 4 floor(n / 4) pixels; the last n % 4 go to consumer warp 0 of block 0 with plain loads).
+// Lane 0 of the producer warp (warp 8) fills stage i % kCmpStages with chunk i once the 8 consumer
+// warps have released it (empty barrier), and the copies complete on the stage's full barrier.
+// A wait that runs out of time sets out->fault and ends that warp's loop; the producer then waits
+// (again with the limit) for the copies it issued, so that none lands after the CTA has left.
 __global__ void __launch_bounds__(kCmpThreads) k_compare(const unsigned *a, const unsigned *b, long long n, CmpArgs g,
                                                           StatSums *out)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     uint4 *const stage = reinterpret_cast<uint4 *>(smem);                     // [stage][map][chunk / 16]
     uint64_t *const full = reinterpret_cast<uint64_t *>(smem + (size_t)kCmpStages * 2 * kCmpChunk);
-    unsigned *const bins = reinterpret_cast<unsigned *>(smem + (size_t)kCmpStages * 2 * kCmpChunk + 64);
+    uint64_t *const empty = full + kCmpStages;
+    unsigned *const bins = reinterpret_cast<unsigned *>(smem + (size_t)kCmpStages * 2 * kCmpChunk + 128);
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned *const sa = bins + warp * 2 * kWarpBins, *const sb = sa + kWarpBins;
-    for (int k = threadIdx.x; k < 8 * 2 * kWarpBins; k += kCmpThreads) bins[k] = 0u;
+    for (int k = threadIdx.x; k < kBinCopies * 2 * kWarpBins; k += kCmpThreads) bins[k] = 0u;
     const long long bytes = (n / 4) * 16;
     const long long chunks = (bytes + kCmpChunk - 1) / kCmpChunk;
     const long long mine = chunks > blockIdx.x ? (chunks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -209,71 +211,85 @@ __global__ void __launch_bounds__(kCmpThreads) k_compare(const unsigned *a, cons
         const long long off = (blockIdx.x + i * gridDim.x) * (long long)kCmpChunk;
         return (unsigned)min((long long)kCmpChunk, bytes - off);
     };
-    auto issue = [&](long long i) {                                           // thread 0: chunk i -> its stage
-        const int s = (int)(i % kCmpStages);
-        const long long off = (blockIdx.x + i * gridDim.x) * (long long)kCmpChunk;
-        const unsigned nb = chunk_bytes(i);
-        mbar_arrive_expect(full + s, 2 * nb);
-        bulk_load(stage + (size_t)s * 2 * (kCmpChunk / 16), reinterpret_cast<const unsigned char *>(a) + off, nb,
-                  full + s);
-        bulk_load(stage + ((size_t)s * 2 + 1) * (kCmpChunk / 16), reinterpret_cast<const unsigned char *>(b) + off,
-                  nb, full + s);
-    };
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kCmpStages; ++s) mbar_init(full + s, 1);
+        for (int s = 0; s < kCmpStages; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, kCmpConsumers);
+        }
         mbar_fence_init();
     }
     __syncthreads();
-    if (threadIdx.x == 0)
-        for (long long i = 0; i < min(mine, (long long)kCmpStages); ++i) issue(i);
     CmpAcc acc;
-    for (long long i = 0; i < mine; ++i) {
-        const int s = (int)(i % kCmpStages);
-        const bool ok = mbar_wait(full + s, (unsigned)((i / kCmpStages) & 1));
-        if (__syncthreads_or(!ok)) {                                         // give up, the same in every thread
-            if (threadIdx.x == 0) {
-                atomicExch(&out->fault, 1u);
-                for (long long j = i; j < min(mine, i + kCmpStages); ++j)   // copies still in flight
-                    mbar_wait(full + (int)(j % kCmpStages), (unsigned)((j / kCmpStages) & 1));
+    if (warp == kCmpConsumers) {                                             // producer
+        if (lane == 0) {
+            long long issued = 0;
+            for (long long i = 0; i < mine; ++i) {
+                const int s = (int)(i % kCmpStages);
+                if (i >= kCmpStages && !mbar_wait(empty + s, (unsigned)((i / kCmpStages - 1) & 1))) {
+                    atomicExch(&out->fault, 1u);
+                    break;
+                }
+                const long long off = (blockIdx.x + i * gridDim.x) * (long long)kCmpChunk;
+                const unsigned nb = chunk_bytes(i);
+                mbar_arrive_expect(full + s, 2 * nb);
+                bulk_load(stage + (size_t)s * 2 * (kCmpChunk / 16), reinterpret_cast<const unsigned char *>(a) + off,
+                          nb, full + s);
+                bulk_load(stage + ((size_t)s * 2 + 1) * (kCmpChunk / 16),
+                          reinterpret_cast<const unsigned char *>(b) + off, nb, full + s);
+                issued = i + 1;
             }
-            return;
+            // every issued copy has landed before the CTA leaves (normally the consumers saw them all)
+            for (long long j = max(0LL, issued - kCmpStages); j < issued; ++j)
+                if (!mbar_wait(full + (int)(j % kCmpStages), (unsigned)((j / kCmpStages) & 1)))
+                    atomicExch(&out->fault, 1u);
         }
-        const uint4 *const va = stage + (size_t)s * 2 * (kCmpChunk / 16), *const vb = va + kCmpChunk / 16;
-        const int quads = (int)(chunk_bytes(i) / 16);
-        for (int q0 = warp * 32; q0 < quads; q0 += kCmpThreads) {            // warp-uniform trip count
-            const int q = q0 + (int)lane;
-            const bool in = q < quads;
-            cmp_quad(in, in ? va[q] : make_uint4(0u, 0u, 0u, 0u), in ? vb[q] : make_uint4(0u, 0u, 0u, 0u), g, acc, sa,
-                     sb, out, lane);
+    } else {                                                                 // consumers
+        unsigned *const sa = bins + (warp >> 1) * 2 * kWarpBins, *const sb = sa + kWarpBins;
+        for (long long i = 0; i < mine; ++i) {
+            const int s = (int)(i % kCmpStages);
+            // every lane waits (and so sees the copies); the warp goes on only if all of them saw it
+            if (!__all_sync(0xffffffffu, mbar_wait(full + s, (unsigned)((i / kCmpStages) & 1)))) {
+                if (lane == 0) atomicExch(&out->fault, 1u);
+                break;
+            }
+            const uint4 *const va = stage + (size_t)s * 2 * (kCmpChunk / 16), *const vb = va + kCmpChunk / 16;
+            const int quads = (int)(chunk_bytes(i) / 16);
+            for (int q0 = warp * 32; q0 < quads; q0 += 32 * kCmpConsumers) {  // warp-uniform trip count
+                const int q = q0 + (int)lane;
+                const bool in = q < quads;
+                cmp_quad(in, in ? va[q] : make_uint4(0u, 0u, 0u, 0u), in ? vb[q] : make_uint4(0u, 0u, 0u, 0u), g, acc,
+                         sa, sb, out, lane);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty + s);                           // this warp is done with stage s
         }
-        __syncthreads();                                                     // stage s read by every thread
-        if (threadIdx.x == 0 && i + kCmpStages < mine) issue(i + kCmpStages);
-    }
-    if (blockIdx.x == 0 && warp == 0) {                                      // the last n % 4 pixels, one each
-        const long long k = 4 * (n / 4) + lane;
-        const bool in = k < n;
-        const unsigned ka = in ? a[k] : 0u, kb = in ? b[k] : 0u;
-        if (!g.hist_only) rms_pixel(ka, kb, g, acc);
-        hist_key(in, ka, sa, g.ha, g.la, &out->over_a, g.cap, g.nbins, acc.big_max, lane);
-        hist_key(in, kb, sb, g.hb, g.lb, &out->over_b, g.cap, g.nbins, acc.big_max, lane);
-    }
-    double sq = 6.25 * ((double)acc.qh + (double)acc.ql);                    // Delta m differences carry -2.5
-    for (int o = 16; o > 0; o >>= 1) {
-        sq += __shfl_down_sync(0xffffffffu, sq, o);
-        acc.both += __shfl_down_sync(0xffffffffu, acc.both, o);
-        acc.big_max = max(acc.big_max, __shfl_down_sync(0xffffffffu, acc.big_max, o));
-    }
-    if (lane == 0) {
-        if (!g.hist_only) {
-            atomicAdd(&out->sum_sq, sq);
-            atomicAdd(&out->n_both, acc.both);
+        if (blockIdx.x == 0 && warp == 0) {                                  // the last n % 4 pixels, one each
+            const long long k = 4 * (n / 4) + lane;
+            const bool in = k < n;
+            const unsigned ka = in ? a[k] : 0u, kb = in ? b[k] : 0u;
+            if (!g.hist_only) rms_pixel(ka, kb, g, acc);
+            hist_key(in, ka, sa, g.ha, g.la, &out->over_a, g.cap, g.nbins, acc.big_max, lane);
+            hist_key(in, kb, sb, g.hb, g.lb, &out->over_b, g.cap, g.nbins, acc.big_max, lane);
         }
-        if (acc.big_max) atomicMax(&out->max_count, acc.big_max);
+        double sq = 6.25 * ((double)acc.qh + (double)acc.ql);                // Delta m differences carry -2.5
+        unsigned long long both = acc.both;
+        for (int o = 16; o > 0; o >>= 1) {
+            sq += __shfl_down_sync(0xffffffffu, sq, o);
+            both += __shfl_down_sync(0xffffffffu, both, o);
+            acc.big_max = max(acc.big_max, __shfl_down_sync(0xffffffffu, acc.big_max, o));
+        }
+        if (lane == 0) {
+            if (!g.hist_only) {
+                atomicAdd(&out->sum_sq, sq);
+                atomicAdd(&out->n_both, both);
+            }
+            if (acc.big_max) atomicMax(&out->max_count, acc.big_max);
+        }
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < 2 * kWarpBins; k += kCmpThreads) {         // the 8 warp copies of each bin
+    for (int k = threadIdx.x; k < 2 * kWarpBins; k += kCmpThreads) {         // the copies of each bin
         unsigned v = 0;
-        for (int q = 0; q < 8; ++q) v += bins[q * 2 * kWarpBins + k];
+        for (int q = 0; q < kBinCopies; ++q) v += bins[q * 2 * kWarpBins + k];
         if (v) atomicAdd(k < kWarpBins ? g.ha + k : g.hb + (k - kWarpBins), v);
     }
 }

@@ -37,6 +37,30 @@ def test_convolved_map_matches_oracle(shot, profile, size):
     np.testing.assert_allclose(got[ok], ref[ok], rtol=2e-5, atol=1e-6)
 
 
+@pytest.mark.parametrize("nside", [203, 130])
+def test_convolution_of_sides_not_multiple_of_4(nside):
+    """Sides that are not multiples of 4 (the tiled Gaussian then copies 4-byte words instead of
+    16-byte groups and stores its outputs one by one) and leave ragged tiles: against the oracle."""
+    mm.build()
+    c = mm.mm_init(0)
+    try:
+        cfg = dict(CFG, npix_side=nside, side=6.0 * nside / 256)
+        n, r = field.nstar_rule(cfg["sigma"], cfg["gamma"], cfg["smooth_frac"], cfg["side"])
+        f = synth.lens_field(n, r, 47)
+        lh = mm.mm_create_lenses_from(c, f.x, f.y, f.m)
+        m = mm.mm_shoot(c, lh, mm.params(**cfg))
+        counts, _ = mm.mm_map_fetch(c, m)
+        for profile, size in ((mm.MM_PROFILE_GAUSSIAN, 0.05), (mm.MM_PROFILE_DISC, 0.12)):
+            got = mm.mm_map_convolve(c, m, profile, size)
+            ref = oext.convolve(counts, cfg["nrays"], profile, size, cfg["side"] / nside)
+            np.testing.assert_array_equal(np.isnan(got), np.isnan(ref))
+            ok = ~np.isnan(ref)
+            assert ok.sum() > 0.5 * ref.size
+            np.testing.assert_allclose(got[ok], ref[ok], rtol=2e-5, atol=1e-6)
+    finally:
+        mm.mm_destroy(c)
+
+
 def test_lightcurve_matches_oracle(shot):
     ctx, m, counts = shot
     start, end = (-2.5, -1.7), (2.3, 2.6)           # runs off the valid region at both ends

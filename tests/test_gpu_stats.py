@@ -36,7 +36,7 @@ def restore_counts(ctx, counts, nrays, side=6.0):
     return mm.mm_map_restore(ctx, 0, p, counts, st)
 
 
-# The device keeps per-warp histograms of the counts below 512 in shared memory, sends counts below
+# The device keeps histograms of the counts below 1024 in shared memory, sends counts below
 # T = 4096 (at these N_rays) to global histograms and lists the larger ones (room for
 # max(4096, N_side^2 / 16) per map), widening the histograms afterwards; when a list runs out of
 # room, a second pass over the maps builds the wide histograms. Seeded synthetic count maps (put on
