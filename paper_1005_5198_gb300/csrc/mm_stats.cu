@@ -26,10 +26,11 @@ namespace {
 
 // The comparison reads both maps once (k_compare), streaming them through shared memory in chunks
 // of kCmpChunk bytes per map: a producer warp keeps kCmpStages chunks in flight with bulk copies,
-// and 8 consumer warps read each chunk's pixels with 16-byte loads, releasing its stage per warp.
-// Histograms: the bins below kWarpBins in shared memory, one copy per pair of consumer warps
-// (4 copies x 2 maps x 1024 bins, 32 KB); 64 KB of shared memory per CTA, 3 CTAs per SM.
-constexpr int kCmpConsumers = 8;
+// and 4 consumer warps read each chunk's pixels with 16-byte loads (two groups of 4 pixels per lane
+// and map), releasing its stage per warp. Histograms: the bins below kWarpBins in shared memory, one
+// copy per pair of consumer warps (2 copies x 2 maps x 1024 bins, 16 KB); 48 KB of shared memory per
+// CTA, 4 CTAs per SM.
+constexpr int kCmpConsumers = 4;
 constexpr int kCmpThreads = 32 * (kCmpConsumers + 1);
 constexpr int kCmpStages = 4;
 constexpr int kCmpChunk = 4096;
@@ -118,12 +119,10 @@ struct CmpArgs {
 //   Delta m_a - Delta m_b = -2.5 [(log10 N_a - log10 N_rays_a) - (log10 N_b - log10 N_rays_b)]
 //                         = -2.5 (pair_a(N_a) - pair_b(N_b)),
 // the difference and its square in float-float (about 1e-14 relative), over pixels counted in both.
-__device__ __forceinline__ void rms_pixel(unsigned na, unsigned nb, const CmpArgs &g, CmpAcc &acc)
+// The square of pair_a - pair_b in float-float, added to the running sum (zero for a pixel empty in
+// either map: every pixel runs the arithmetic, so that a warp does not diverge).
+__device__ __forceinline__ void rms_add(float2 x, float2 y, bool use, CmpAcc &acc)
 {
-    // every pixel runs the arithmetic (no divergence); a pixel empty in either map adds zero
-    const bool use = na && nb;
-    const float2 x = na < (unsigned long long)g.nbins ? __ldg(g.ta + na) : log_pair(na, g.lra);
-    const float2 y = nb < (unsigned long long)g.nbins ? __ldg(g.tb + nb) : log_pair(nb, g.lrb);
     float dh, dl;
     ff_two_sum(x.x, -y.x, dh, dl);
     dl = __fadd_rn(dl, __fsub_rn(x.y, y.y));
@@ -132,6 +131,19 @@ __device__ __forceinline__ void rms_pixel(unsigned na, unsigned nb, const CmpArg
     const float pl = __fmaf_rn(d, d, -ph) + 2.f * d * de;
     ff_accumulate(acc.qh, acc.ql, use ? ph : 0.f, use ? pl : 0.f);
     acc.both += use;
+}
+
+__device__ __forceinline__ void rms_pixel(unsigned na, unsigned nb, const CmpArgs &g, CmpAcc &acc)
+{
+    const float2 x = na < (unsigned long long)g.nbins ? __ldg(g.ta + na) : log_pair(na, g.lra);
+    const float2 y = nb < (unsigned long long)g.nbins ? __ldg(g.tb + nb) : log_pair(nb, g.lrb);
+    rms_add(x, y, na && nb, acc);
+}
+
+// The same for counts known to be below nbins.
+__device__ __forceinline__ void rms_pixel_small(unsigned na, unsigned nb, const CmpArgs &g, CmpAcc &acc)
+{
+    rms_add(__ldg(g.ta + na), __ldg(g.tb + nb), na && nb, acc);
 }
 
 // Count the key of one lane (in: the lane holds a pixel) into the warp's shared bins (keys below
@@ -155,19 +167,33 @@ __device__ __forceinline__ void hist_key(bool in, unsigned key, unsigned *sbins,
     }
 }
 
-// Four pixels of each map held by every lane of a warp (in: the lane holds pixels). Keys below
-// kWarpBins go straight to the shared bins; when a key of the warp's 256 is larger (rare), the
-// larger keys take hist_key's way, one key position at a time.
+// Four pixels of each map held by every lane of a warp (in: the lane holds pixels). When every
+// count of the warp's 256 is below kWarpBins (the usual case; kWarpBins <= nbins) the RMS reads the
+// tables directly and the keys go straight to the shared bins; otherwise the keys below kWarpBins
+// still do, and the larger ones take hist_key's way, one key position at a time.
 __device__ __forceinline__ void cmp_quad(bool in, uint4 x, uint4 y, const CmpArgs &g, CmpAcc &acc, unsigned *sa,
                                          unsigned *sb, StatSums *out, unsigned lane)
 {
-    if (!g.hist_only) {
-        rms_pixel(x.x, y.x, g, acc);
-        rms_pixel(x.y, y.y, g, acc);
-        rms_pixel(x.z, y.z, g, acc);
-        rms_pixel(x.w, y.w, g, acc);
-    }
+    const unsigned m = max(max(max(x.x, x.y), max(x.z, x.w)), max(max(y.x, y.y), max(y.z, y.w)));
     const unsigned ka[4] = {x.x, x.y, x.z, x.w}, kb[4] = {y.x, y.y, y.z, y.w};
+    if (__all_sync(0xffffffffu, m < (unsigned)kWarpBins)) {
+        if (!g.hist_only) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) rms_pixel_small(ka[u], kb[u], g, acc);
+        }
+        if (in) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                atomicAdd(sa + ka[u], 1u);
+                atomicAdd(sb + kb[u], 1u);
+            }
+        }
+        return;
+    }
+    if (!g.hist_only) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) rms_pixel(ka[u], kb[u], g, acc);
+    }
     if (in) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -175,8 +201,6 @@ __device__ __forceinline__ void cmp_quad(bool in, uint4 x, uint4 y, const CmpArg
             if (kb[u] < (unsigned)kWarpBins) atomicAdd(sb + kb[u], 1u);
         }
     }
-    const unsigned m = max(max(max(x.x, x.y), max(x.z, x.w)), max(max(y.x, y.y), max(y.z, y.w)));
-    if (__all_sync(0xffffffffu, m < (unsigned)kWarpBins)) return;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {                          // only keys of kWarpBins or more are left
         hist_key(in && ka[u] >= (unsigned)kWarpBins, ka[u], sa, g.ha, g.la, &out->over_a, g.cap, g.nbins, acc.big_max,
@@ -253,12 +277,18 @@ __global__ void __launch_bounds__(kCmpThreads) k_compare(const unsigned *a, cons
                 break;
             }
             const uint4 *const va = stage + (size_t)s * 2 * (kCmpChunk / 16), *const vb = va + kCmpChunk / 16;
-            const int quads = (int)(chunk_bytes(i) / 16);
-            for (int q0 = warp * 32; q0 < quads; q0 += 32 * kCmpConsumers) {  // warp-uniform trip count
-                const int q = q0 + (int)lane;
-                const bool in = q < quads;
-                cmp_quad(in, in ? va[q] : make_uint4(0u, 0u, 0u, 0u), in ? vb[q] : make_uint4(0u, 0u, 0u, 0u), g, acc,
-                         sa, sb, out, lane);
+            if (i + 1 < mine || bytes % kCmpChunk == 0) {                    // a whole chunk
+#pragma unroll
+                for (int q0 = warp * 32; q0 < kCmpChunk / 16; q0 += 32 * kCmpConsumers)
+                    cmp_quad(true, va[q0 + lane], vb[q0 + lane], g, acc, sa, sb, out, lane);
+            } else {                                                         // the last, shorter chunk
+                const int quads = (int)(chunk_bytes(i) / 16);
+                for (int q0 = warp * 32; q0 < quads; q0 += 32 * kCmpConsumers) {  // warp-uniform trip count
+                    const int q = q0 + (int)lane;
+                    const bool in = q < quads;
+                    cmp_quad(in, in ? va[q] : make_uint4(0u, 0u, 0u, 0u), in ? vb[q] : make_uint4(0u, 0u, 0u, 0u), g,
+                             acc, sa, sb, out, lane);
+                }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(empty + s);                           // this warp is done with stage s
@@ -467,7 +497,7 @@ extern "C" int mm_map_compare(mm_ctx *ctx, mm_map a, mm_map b, mm_compare *out)
         cudaSuccess)
         return cuda_fail(e, "k_compare shared memory");
     const long long chunks = ((n / 4) * 16 + kCmpChunk - 1) / kCmpChunk;
-    const int cgrid = (int)std::max(1LL, std::min((long long)(3 * ctx->sms), chunks));   // 3 CTAs fit an SM
+    const int cgrid = (int)std::max(1LL, std::min((long long)(4 * ctx->sms), chunks));   // 4 CTAs fit an SM
     CmpArgs g{tab, tab + T, lra, lrb, T, hist, hist + T, lists, lists + cap, cap, 0};
     k_compare<<<cgrid, kCmpThreads, kCmpSmem, s>>>(A->counts, B->counts, n, g, d_sum);
     auto ks_steps = [&](const unsigned *h2, long long *c2, long long nb) {
