@@ -333,13 +333,26 @@ __global__ void k_list_hist(const unsigned *list, unsigned long long m, unsigned
 
 // One CTA of 1024 threads: inclusive prefix sums ca[k], cb[k] of the two count
 // histograms (so P(N >= k) = (n - c[k-1]) / n), and from the histograms the empty pixels
-// (bin 0) and the total count sum_k k h[k] of each map, written to out.
+// (bin 0) and the total count sum_k k h[k] of each map, written to out. Thread t takes a run of
+// consecutive bins; the runs' totals are scanned with warp shuffles (within a warp, then over the
+// 32 warp totals).
+__device__ __forceinline__ long long warp_incl_scan(long long v, unsigned lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= (unsigned)o) v += u;
+    }
+    return v;
+}
+
 __global__ void __launch_bounds__(1024) k_scan(const unsigned *ha, const unsigned *hb, long long nbins, long long *ca,
                                                long long *cb, StatSums *out)
 {
-    __shared__ long long sa[1024], sb[1024];
+    __shared__ long long wa[32], wb[32];
     __shared__ unsigned long long wsum[2][32];
     const int t = threadIdx.x;
+    const unsigned lane = t & 31, warp = t >> 5;
     const long long per = (nbins + 1023) / 1024;
     const long long lo = min(nbins, t * per), hi = min(nbins, lo + per);
     long long ta = 0, tb = 0;
@@ -350,37 +363,40 @@ __global__ void __launch_bounds__(1024) k_scan(const unsigned *ha, const unsigne
         ma += (unsigned long long)k * ha[k];
         mb += (unsigned long long)k * hb[k];
     }
-    sa[t] = ta;
-    sb[t] = tb;
     for (int o = 16; o > 0; o >>= 1) {
         ma += __shfl_down_sync(0xffffffffu, ma, o);
         mb += __shfl_down_sync(0xffffffffu, mb, o);
     }
-    if ((t & 31) == 0) {
-        wsum[0][t >> 5] = ma;
-        wsum[1][t >> 5] = mb;
+    const long long ia = warp_incl_scan(ta, lane), ib = warp_incl_scan(tb, lane);
+    if (lane == 31) {
+        wa[warp] = ia;
+        wb[warp] = ib;
+    }
+    if (lane == 0) {
+        wsum[0][warp] = ma;
+        wsum[1][warp] = mb;
     }
     __syncthreads();
-    if (t == 0) {
-        unsigned long long za = 0, zb = 0;
-        for (int w = 0; w < 32; ++w) {
-            za += wsum[0][w];
-            zb += wsum[1][w];
+    if (warp == 0) {                               // exclusive scan of the warp totals
+        const long long xa = warp_incl_scan(wa[lane], lane), xb = warp_incl_scan(wb[lane], lane);
+        unsigned long long sa = wsum[0][lane], sb = wsum[1][lane];
+        for (int o = 16; o > 0; o >>= 1) {
+            sa += __shfl_down_sync(0xffffffffu, sa, o);
+            sb += __shfl_down_sync(0xffffffffu, sb, o);
         }
-        out->sum_a = za;
-        out->sum_b = zb;
-        out->zero_a = nbins > 0 ? ha[0] : 0u;
-        out->zero_b = nbins > 0 ? hb[0] : 0u;
+        __syncwarp();
+        wa[lane] = xa - wa[lane];
+        wb[lane] = xb - wb[lane];
+        if (lane == 0) {
+            out->sum_a = sa;
+            out->sum_b = sb;
+            out->zero_a = nbins > 0 ? ha[0] : 0u;
+            out->zero_b = nbins > 0 ? hb[0] : 0u;
+        }
     }
-    for (int o = 1; o < 1024; o <<= 1) {           // inclusive scan of the per-thread totals
-        const long long va = (t >= o) ? sa[t - o] : 0, vb = (t >= o) ? sb[t - o] : 0;
-        __syncthreads();
-        sa[t] += va;
-        sb[t] += vb;
-        __syncthreads();
-    }
-    ta = (t > 0) ? sa[t - 1] : 0;
-    tb = (t > 0) ? sb[t - 1] : 0;
+    __syncthreads();
+    ta = wa[warp] + ia - ta;                       // bins before this thread's run
+    tb = wb[warp] + ib - tb;
     for (long long k = lo; k < hi; ++k) {
         ta += ha[k];
         tb += hb[k];
@@ -492,7 +508,8 @@ extern "C" int mm_map_compare(mm_ctx *ctx, mm_map a, mm_map b, mm_compare *out)
         (e = cudaMemsetAsync(hist, 0, (size_t)(2 * T) * sizeof(unsigned), s)) != cudaSuccess)
         return cuda_fail(e, "memset");
     const double lra = std::log10(A->p.nrays_per_pix), lrb = std::log10(B->p.nrays_per_pix);
-    k_log_table<<<std::max(1, std::min(ctx->sms, (int)((T + 255) / 256))), 256, 0, s>>>(T, lra, lrb, tab, tab + T);
+    // small blocks, so that the FP64 logarithms spread over many SMs
+    k_log_table<<<std::max(1, std::min(4 * ctx->sms, (int)((T + 31) / 32))), 32, 0, s>>>(T, lra, lrb, tab, tab + T);
     if ((e = cudaFuncSetAttribute(k_compare, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCmpSmem)) !=
         cudaSuccess)
         return cuda_fail(e, "k_compare shared memory");
@@ -502,8 +519,8 @@ extern "C" int mm_map_compare(mm_ctx *ctx, mm_map a, mm_map b, mm_compare *out)
     k_compare<<<cgrid, kCmpThreads, kCmpSmem, s>>>(A->counts, B->counts, n, g, d_sum);
     auto ks_steps = [&](const unsigned *h2, long long *c2, long long nb) {
         k_scan<<<1, 1024, 0, s>>>(h2, h2 + nb, nb, c2, c2 + nb, d_sum);
-        const int egrid = std::max(1, std::min(4 * ctx->sms, (int)((2 * nb + 255) / 256)));
-        k_ks_eval<<<egrid, 256, 0, s>>>(h2, h2 + nb, c2, c2 + nb, nb, n, n, A->p.nrays_per_pix, B->p.nrays_per_pix,
+        const int egrid = std::max(1, std::min(8 * ctx->sms, (int)((2 * nb + 63) / 64)));
+        k_ks_eval<<<egrid, 64, 0, s>>>(h2, h2 + nb, c2, c2 + nb, nb, n, n, A->p.nrays_per_pix, B->p.nrays_per_pix,
                                         d_sum);
     };
     ks_steps(hist, cum, T);
