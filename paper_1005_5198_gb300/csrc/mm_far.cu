@@ -483,12 +483,15 @@ __device__ void far_tile(const LaunchArgs &A, const FarDesc &F, const MapDesc &M
         const float tyh = __fmul_rn(ky, dlt), tyl = __fmaf_rn(ky, dll, __fmaf_rn(ky, dlt, -tyh));
         const float rxn = (float)iloc - 31.5f;
         const float rx = __fmaf_rn(rxn, dlt, __fmul_rn(rxn, dll));
-        float ry[K], nxs[K], nys[K];
+        // per row pair q (rows 2q, 2q + 1): -y offsets of the rays, and the FP32 partial sums; the
+        // near terms of a row pair go through packed f32x2 operations (each lane rounds as the
+        // scalar operation would)
+        float2 RYN[H], NXS[H], NYS[H];
 #pragma unroll
-        for (int r = 0; r < K; ++r) {
-            const float ryn = (float)(jloc0 + r) - 15.5f;
-            ry[r] = __fmaf_rn(ryn, dlt, __fmul_rn(ryn, dll));
-            nxs[r] = nys[r] = 0.f;
+        for (int q = 0; q < H; ++q) {
+            const float na = (float)(jloc0 + 2 * q) - 15.5f, nb = (float)(jloc0 + 2 * q + 1) - 15.5f;
+            RYN[q] = make_float2(-__fmaf_rn(na, dlt, __fmul_rn(na, dll)), -__fmaf_rn(nb, dlt, __fmul_rn(nb, dll)));
+            NXS[q] = NYS[q] = make_float2(0.f, 0.f);
         }
         const float hx = 32.0f * dlt + kNearRadius, hy = 16.0f * dlt + kNearRadius;
         for (long long c0 = 0; c0 < n_near; c0 += kNearCap) {
@@ -523,15 +526,17 @@ __device__ void far_tile(const LaunchArgs &A, const FarDesc &F, const MapDesc &M
                         }
                         continue;
                     }
-                    const float m = MASS ? S.nm[j] : 1.f;
-                    const float dX = lx - rx;
-                    const float dX2 = dX * dX;
+                    const float dX = __fsub_rn(lx, rx);
+                    const float2 DX = make_float2(dX, dX), DX2 = dup2(__fmul_rn(dX, dX)), LY = make_float2(ly, ly);
+                    const float2 MM = dup2(MASS ? S.nm[j] : 1.f);
 #pragma unroll
-                    for (int r = 0; r < K; ++r) {
-                        const float dY = ly - ry[r];
-                        const float t = m * rcp_approx(fmaf(dY, dY, dX2));
-                        nxs[r] = fmaf(t, dX, nxs[r]);
-                        nys[r] = fmaf(t, dY, nys[r]);
+                    for (int q = 0; q < H; ++q) {
+                        const float2 dY = __fadd2_rn(LY, RYN[q]);                 // ly - ry
+                        const float2 r2 = __ffma2_rn(dY, dY, DX2);
+                        float2 t = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+                        if (MASS) t = __fmul2_rn(MM, t);
+                        NXS[q] = __ffma2_rn(t, DX, NXS[q]);
+                        NYS[q] = __ffma2_rn(t, dY, NYS[q]);
                     }
                 }
 #pragma unroll
@@ -539,14 +544,15 @@ __device__ void far_tile(const LaunchArgs &A, const FarDesc &F, const MapDesc &M
                     float s, e;
                     float &xh = lane(SXh[r >> 1], r & 1), &xl = lane(SXl[r >> 1], r & 1);
                     float &yh = lane(SYh[r >> 1], r & 1), &yl = lane(SYl[r >> 1], r & 1);
-                    two_sum(xh, nxs[r], s, e);
+                    two_sum(xh, lane(NXS[r >> 1], r & 1), s, e);
                     xh = s;
                     xl = __fadd_rn(xl, e);
-                    two_sum(yh, nys[r], s, e);
+                    two_sum(yh, lane(NYS[r >> 1], r & 1), s, e);
                     yh = s;
                     yl = __fadd_rn(yl, e);
-                    nxs[r] = nys[r] = 0.f;
                 }
+#pragma unroll
+                for (int q = 0; q < H; ++q) NXS[q] = NYS[q] = make_float2(0.f, 0.f);
             }
         }
     }
