@@ -443,6 +443,18 @@ int mm_debug_deflect(mm_ctx *ctx, mm_lenses lenses, const mm_params *p,
                      const int64_t *ray_i, const int64_t *ray_j, int64_t n,
                      double *alpha_out, int64_t *pixel_out);
 
+/* Test hook for the device's own time limits: arm a one-shot failure that the
+ * next call of the named kind meets on the device, so that a test can check the
+ * error path without faulting the GPU.
+ *   MM_INJECT_COMPARE_NO_COPY  the next mm_map_compare issues none of its bulk
+ *     copies into shared memory: its waits for them give up after their limit
+ *     (about one second of SM clocks), the call returns MM_EDEVICE, and the
+ *     context stays usable.
+ * MM_INJECT_NONE disarms. Errors: MM_EINVAL (null context, unknown kind). */
+#define MM_INJECT_NONE             0
+#define MM_INJECT_COMPARE_NO_COPY  1
+int mm_debug_inject(mm_ctx *ctx, int32_t kind);
+
 /* ---- shooting without allocation --------------------------------------------
  * The paper has no counterpart to this call; it serves callers that cannot
  * allocate device memory, such as code running under another runtime or

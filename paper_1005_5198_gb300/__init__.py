@@ -41,6 +41,7 @@ MM_FP32C, MM_FP64, MM_FAR32 = 0, 1, 2
 MM_MASS_UNIT, MM_MASS_LOGNORMAL = 0, 1
 MM_PROFILE_GAUSSIAN, MM_PROFILE_DISC = 0, 1
 MM_MAP_MU, MM_MAP_DELTA_M = 0, 1
+MM_INJECT_NONE, MM_INJECT_COMPARE_NO_COPY = 0, 1
 
 
 class MMError(RuntimeError):
@@ -130,6 +131,7 @@ def _load():
         "mm_layout_count": [],
         "mm_layout_name": [C.c_int32],
         "mm_debug_deflect": [C.c_void_p, U64, P(mm_params), P(I64), P(I64), I64, P(D), P(I64)],
+        "mm_debug_inject": [C.c_void_p, C.c_int32],
         "mm_last_kernel_ms": [C.c_void_p, P(D), P(C.c_int32)],
         "mm_shoot_noalloc": [C.c_void_p, C.c_void_p, C.c_void_p, I64, P(mm_params), C.c_void_p, C.c_void_p,
                              C.c_void_p],
@@ -411,6 +413,11 @@ def mm_layout_name(v: int) -> str:
     return _load().mm_layout_name(v).decode()
 
 
+def mm_debug_inject(ctx: Ctx, kind: int) -> None:
+    """Arm a one-shot device-side failure for the next call of the named kind (test hook)."""
+    _check(_load().mm_debug_inject(ctx.handle, kind), "mm_debug_inject")
+
+
 def mm_debug_deflect(ctx: Ctx, lenses: int, p: mm_params, ray_i, ray_j):
     """(alpha [n, 2] float64, pixel [n] int64, -1 = out) through the map kernel's code."""
     ri = np.ascontiguousarray(ray_i, dtype=np.int64)
@@ -474,7 +481,7 @@ EXPORTED = [
     "mm_map_restore", "mm_map_fetch", "mm_map_fetch_mu",
     "mm_map_device_ptr", "mm_release_map", "mm_submit", "mm_poll", "mm_wait", "mm_cancel", "mm_req_times", "mm_serve_stats",
     "mm_serve_config", "mm_serve_priority", "mm_serve_plan", "mm_autotune", "mm_set_variant", "mm_variant_count", "mm_variant_name", "mm_set_layout",
-    "mm_get_layout", "mm_layout_count", "mm_layout_name", "mm_debug_deflect",
+    "mm_get_layout", "mm_layout_count", "mm_layout_name", "mm_debug_deflect", "mm_debug_inject",
     "mm_last_kernel_ms", "mm_shoot_noalloc", "mm_map_compare", "mm_map_convolve",
     "mm_map_lightcurve", "mm_strerror", "mm_last_error",
 ]

@@ -168,6 +168,7 @@ struct mm_ctx {
     int last_launches = 0;
     int forced_variant = -1;
     int layout = 1;                                           // FP32 thread layout (bit-identical maps)
+    std::atomic<int> inject{0};                               // one-shot test failure (mm_debug_inject)
     std::map<int, int> tuned;                                 // class key -> variant
     mm::Server *server = nullptr;
 };

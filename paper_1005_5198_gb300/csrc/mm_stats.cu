@@ -113,6 +113,7 @@ struct CmpArgs {
     unsigned *la, *lb;                         // counts of nbins or more, listed (room for cap each)
     unsigned long long cap;
     int hist_only;                             // 1: histograms alone (every count is below nbins)
+    int no_copy;                               // test hook: the producer issues no copies
 };
 
 // The RMS term of one pixel:
@@ -247,7 +248,7 @@ __global__ void __launch_bounds__(kCmpThreads) k_compare(const unsigned *a, cons
     if (warp == kCmpConsumers) {                                             // producer
         if (lane == 0) {
             long long issued = 0;
-            for (long long i = 0; i < mine; ++i) {
+            for (long long i = 0; i < (g.no_copy ? 0 : mine); ++i) {
                 const int s = (int)(i % kCmpStages);
                 if (i >= kCmpStages && !mbar_wait(empty + s, (unsigned)((i / kCmpStages - 1) & 1))) {
                     atomicExch(&out->fault, 1u);
@@ -515,7 +516,8 @@ extern "C" int mm_map_compare(mm_ctx *ctx, mm_map a, mm_map b, mm_compare *out)
         return cuda_fail(e, "k_compare shared memory");
     const long long chunks = ((n / 4) * 16 + kCmpChunk - 1) / kCmpChunk;
     const int cgrid = (int)std::max(1LL, std::min((long long)(4 * ctx->sms), chunks));   // 4 CTAs fit an SM
-    CmpArgs g{tab, tab + T, lra, lrb, T, hist, hist + T, lists, lists + cap, cap, 0};
+    CmpArgs g{tab, tab + T, lra, lrb, T, hist, hist + T, lists, lists + cap, cap, 0,
+              ctx->inject.exchange(MM_INJECT_NONE) == MM_INJECT_COMPARE_NO_COPY ? 1 : 0};
     k_compare<<<cgrid, kCmpThreads, kCmpSmem, s>>>(A->counts, B->counts, n, g, d_sum);
     auto ks_steps = [&](const unsigned *h2, long long *c2, long long nb) {
         k_scan<<<1, 1024, 0, s>>>(h2, h2 + nb, nb, c2, c2 + nb, d_sum);
@@ -552,7 +554,7 @@ extern "C" int mm_map_compare(mm_ctx *ctx, mm_map a, mm_map b, mm_compare *out)
                         lists + m * cap, cnt, hist2 + m * nb);
             }
         } else {
-            CmpArgs g2{nullptr, nullptr, lra, lrb, nb, hist2, hist2 + nb, nullptr, nullptr, 0, 1};
+            CmpArgs g2{nullptr, nullptr, lra, lrb, nb, hist2, hist2 + nb, nullptr, nullptr, 0, 1, 0};
             k_compare<<<cgrid, kCmpThreads, kCmpSmem, s>>>(A->counts, B->counts, n, g2, d_sum);
         }
         ks_steps(hist2, cum2, nb);
@@ -647,5 +649,13 @@ extern "C" int mm_map_fetch_mu(mm_ctx *ctx, mm_map map, int32_t kind, float *hos
     ctx->arena.free(buf);
     if (e != cudaSuccess) return cuda_fail(e, "normalised map");
     if (n_empty) *n_empty = (int64_t)h_empty;
+    return MM_OK;
+}
+
+extern "C" int mm_debug_inject(mm_ctx *ctx, int32_t kind)
+{
+    if (!ctx) return fail(MM_EINVAL, "null context");
+    if (kind != MM_INJECT_NONE && kind != MM_INJECT_COMPARE_NO_COPY) return fail(MM_EINVAL, "unknown injection");
+    ctx->inject.store(kind);
     return MM_OK;
 }

@@ -74,6 +74,28 @@ def test_compare_matches_oracle_statistics(ctx, nside, tail):
         mm.mm_release_map(ctx, m)
 
 
+def test_compare_wait_that_runs_out_reports_a_device_error(ctx):
+    """The comparison streams the maps through shared memory and waits on mbarriers for the bulk copies.
+    With the copies withheld (test hook), every wait gives up after its limit (about a second), the call
+    returns MM_EDEVICE instead of hanging, and the same context then compares correctly."""
+    rng = np.random.default_rng(5)
+    ca = rng.poisson(20.0, (128, 128)).astype(np.uint32)
+    cb = rng.poisson(20.0, (128, 128)).astype(np.uint32)
+    a, b = restore_counts(ctx, ca, 20.0), restore_counts(ctx, cb, 20.0)
+    mm.mm_debug_inject(ctx, mm.MM_INJECT_COMPARE_NO_COPY)
+    with pytest.raises(mm.MMError) as e:
+        mm.mm_map_compare(ctx, a, b)
+    assert e.value.code == mm.MM_EDEVICE
+    got = mm.mm_map_compare(ctx, a, b)                      # the hook is one-shot; the context still works
+    ref = ostats.compare(ca, 20.0, cb, 20.0)
+    assert got["ks_d"] == pytest.approx(ref["ks_d"], abs=1e-15)
+    assert got["rms_dm"] == pytest.approx(ref["rms_dm"], rel=1e-9)
+    with pytest.raises(mm.MMError):
+        mm.mm_debug_inject(ctx, 99)
+    for m in (a, b):
+        mm.mm_release_map(ctx, m)
+
+
 def test_fp32_and_fp64_maps_agree_excellently(ctx):
     """The paper's criterion for 'excellent agreement' (RMS < 0.2 mag, K-S probability > 99.7 %)
     between the compensated FP32 path and the plain FP64 path on a config-0 map."""
