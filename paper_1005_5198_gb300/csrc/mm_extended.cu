@@ -71,8 +71,8 @@ __global__ void k_disc(const unsigned *cin, float *out, int n, const int *span, 
 // ---- tiled forms of the passes above: the same per-pixel sums in the same order ----
 
 constexpr int kDiscTileW = 64, kDiscTileH = 32;        // disc: 64 x 32 outputs per CTA
-constexpr size_t kTileSmemMax = 48 * 1024;             // dynamic shared memory of a tiled disc CTA (no opt-in);
-                                                       // wider supports take the untiled kernel
+constexpr size_t kDiscSmemMax = 72 * 1024;             // dynamic shared memory of a tiled disc CTA (radius up
+                                                       // to 15 pixels); wider supports take the untiled kernel
 constexpr size_t kGaussSmemMax = 200 * 1024;           // a double-buffered Gaussian CTA (h <= 131; wider
                                                        // supports take the untiled kernel)
 
@@ -99,9 +99,12 @@ __host__ __device__ inline size_t gauss_smem(int h)
 {
     return ((size_t)2 * gauss_taps_padded(h) + 2 * gauss_tile_floats(h)) * 4;
 }
+// Disc tile: prefix rows [(32 + 2H) x W] (room for 64-bit sums), then the raw counts of the next
+// tile [(32 + 2H) x (W - 1)], then the spans [2H + 1]; W = 64 + 2H + 1.
 __host__ __device__ inline size_t disc_smem(int H)
 {
-    return (size_t)(kDiscTileH + 2 * H) * (kDiscTileW + 2 * H + 1) * 8 + (size_t)(2 * H + 1) * 4;
+    const size_t rows = (size_t)(kDiscTileH + 2 * H), W = (size_t)(kDiscTileW + 2 * H + 1);
+    return rows * W * 8 + rows * (W - 1) * 4 + (size_t)(2 * H + 1) * 4;
 }
 
 // acc[u] = sum over taps k < TP of g[k] x[(u + k) st], u < 16: x the thread's first input pair,
@@ -250,6 +253,50 @@ __device__ __forceinline__ void disc_prefix_rows(const unsigned *cin, int n, int
     }
 }
 
+// The raw counts of tile rows [r0 - H, r0 + 32 + H) x columns [c0 - H, c0 + 64 + H) into raw
+// [(32 + 2H) x (W - 1)] by 4-byte cp.async (zeros outside the map); warp w copies rows w, w + 8, ...
+__device__ __forceinline__ void disc_stage_raw(const unsigned *cin, int n, int r0, int c0, int H, int W, unsigned *raw)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int rr = warp; rr < kDiscTileH + 2 * H; rr += 8) {
+        const int j = r0 - H + rr;
+        for (int x = lane; x < W - 1; x += 32) {
+            const int i = c0 - H + x;
+            const bool ok = j >= 0 && j < n && i >= 0 && i < n;
+            cp_async4(raw + (size_t)rr * (W - 1) + x, cin + (ok ? (long long)j * n + i : 0), ok ? 4u : 0u);
+        }
+    }
+    cp_async_commit();
+}
+
+// 32-bit prefix rows (modulo 2^32, a leading zero) from the staged raw counts: lane l of the row's
+// warp adds its three consecutive counts (columns 3l .. 3l + 2; W - 1 <= 96), then the warp scans
+// the lanes' totals. Also the largest count seen, for the CTA's choice of sums.
+__device__ __forceinline__ void disc_scan_rows(const unsigned *raw, int H, int W, unsigned *pre, unsigned &maxc)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int rr = warp; rr < kDiscTileH + 2 * H; rr += 8) {
+        const unsigned *const r = raw + (size_t)rr * (W - 1);
+        unsigned *const p = pre + (size_t)rr * W;
+        const int x = 3 * lane;
+        const unsigned a0 = x < W - 1 ? r[x] : 0u, a1 = x + 1 < W - 1 ? r[x + 1] : 0u,
+                       a2 = x + 2 < W - 1 ? r[x + 2] : 0u;
+        maxc = max(maxc, max(a0, max(a1, a2)));
+        const unsigned s0 = a0, s1 = a0 + a1, s2 = s1 + a2;
+        unsigned incl = s2;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        const unsigned excl = incl - s2;
+        if (lane == 0) p[0] = 0u;
+        if (x < W - 1) p[x + 1] = excl + s0;
+        if (x + 1 < W - 1) p[x + 2] = excl + s1;
+        if (x + 2 < W - 1) p[x + 3] = excl + s2;
+    }
+}
+
 // Thread (column c, row group rg) computes the 8 outputs of rows rg, rg + 4, ..., rg + 28 of the
 // tile together (8 independent sums). P: prefix type; A: accumulator type.
 template <typename P, typename A>
@@ -281,26 +328,36 @@ __device__ __forceinline__ void disc_outputs(const P *pre, const int *sp, float 
     }
 }
 
+// A CTA takes tiles t, t + gridDim.x, ...: while it computes the outputs of one tile, the raw counts of
+// the next arrive by cp.async; the 64-bit way (rare) reads its tile from global memory again.
 __global__ void __launch_bounds__(256) k_disc_tiled(const unsigned *cin, float *out, int n, const int *span, int H,
                                                     float scale)
 {
     extern __shared__ unsigned long long psm[];
     const int W = kDiscTileW + 2 * H + 1;                  // prefix row length
+    const int rows_t = kDiscTileH + 2 * H;
     unsigned long long *const pre64 = psm;                 // [(32 + 2H) x W], or the same bytes as
     unsigned *const pre32 = (unsigned *)psm;               // [(32 + 2H) x W] 32-bit sums
-    int *const sp = (int *)(psm + (size_t)(kDiscTileH + 2 * H) * W);
+    unsigned *const raw = (unsigned *)(psm + (size_t)rows_t * W);               // [(32 + 2H) x (W - 1)]
+    int *const sp = (int *)(raw + (size_t)rows_t * (W - 1));
     for (int k = threadIdx.x; k < 2 * H + 1; k += blockDim.x) sp[k] = span[k];
     const int cols = (n + kDiscTileW - 1) / kDiscTileW, rows = (n + kDiscTileH - 1) / kDiscTileH;
     const long long tiles = (long long)cols * rows;
     const unsigned long long taps1 = (unsigned long long)(2 * H + 1);
     const unsigned small_span = (unsigned)(0xffffffffull / taps1);             // span sums below 2^32
     const unsigned small_disc = (unsigned)(0xffffffffull / (taps1 * taps1));   // disc sums below 2^32
+    if (blockIdx.x < tiles)
+        disc_stage_raw(cin, n, (int)(blockIdx.x / cols) * kDiscTileH, (int)(blockIdx.x % cols) * kDiscTileW, H, W, raw);
     for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
         const int c0 = (int)(t % cols) * kDiscTileW, r0 = (int)(t / cols) * kDiscTileH;
-        __syncthreads();
+        cp_async_wait<0>();
+        __syncthreads();                                   // tile t's counts staged; the previous outputs done
         unsigned maxc = 0;
-        disc_prefix_rows<unsigned>(cin, n, r0, c0, H, W, pre32, maxc);
+        disc_scan_rows(raw, H, W, pre32, maxc);
+        // (both votes are also barriers: the raw counts are read and the prefix rows written)
         const bool not_disc32 = __syncthreads_or(maxc >= small_disc), not_span32 = __syncthreads_or(maxc >= small_span);
+        const long long tn = t + gridDim.x;
+        if (tn < tiles) disc_stage_raw(cin, n, (int)(tn / cols) * kDiscTileH, (int)(tn % cols) * kDiscTileW, H, W, raw);
         if (!not_disc32) {
             disc_outputs<unsigned, unsigned>(pre32, sp, out, n, r0, c0, H, W, scale);
         } else if (!not_span32) {
@@ -396,11 +453,19 @@ int convolve(mm_ctx *ctx, const MapObj &M, int profile, double size_re, float *d
     if (rc) return rc;
     if ((e = cudaMemcpyAsync(ds, span.data(), span.size() * sizeof(int), cudaMemcpyHostToDevice, s)) == cudaSuccess) {
         const float scale = (float)(1.0 / ((double)taps * M.p.nrays_per_pix));
-        if (disc_smem(H) <= kTileSmemMax)
-            k_disc_tiled<<<grid, 256, disc_smem(H), s>>>(M.counts, dst, n, ds, H, scale);
-        else
+        const size_t smem = disc_smem(H);
+        if (smem <= kDiscSmemMax) {
+            e = cudaFuncSetAttribute(k_disc_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDiscSmemMax);
+            int per_sm = 1;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_disc_tiled, 256, smem) != cudaSuccess) per_sm = 1;
+            const long long tiles =
+                (long long)((n + kDiscTileW - 1) / kDiscTileW) * ((n + kDiscTileH - 1) / kDiscTileH);
+            const int dgrid = (int)std::max(1LL, std::min(tiles, (long long)std::max(1, per_sm) * ctx->sms));
+            if (e == cudaSuccess) k_disc_tiled<<<dgrid, 256, smem, s>>>(M.counts, dst, n, ds, H, scale);
+        } else {
             k_disc<<<grid, 256, 0, s>>>(M.counts, dst, n, ds, H, scale);
-        e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     }
     ctx->arena.free(ds);

@@ -489,7 +489,7 @@ extern "C" int mm_map_compare(mm_ctx *ctx, mm_map a, mm_map b, mm_compare *out)
     const double nr_max = std::max(A->p.nrays_per_pix, B->p.nrays_per_pix);
     long long T = 4096;
     while (T < (1LL << 20) && (double)T < 32.0 * nr_max) T <<= 1;
-    const unsigned long long cap = (unsigned long long)std::max(4096LL, n / 16);
+    const unsigned long long cap = (unsigned long long)std::max(4096LL, n / 64);
     StatSums *d_sum = nullptr;
     unsigned *hist = nullptr, *lists = nullptr;
     long long *cum = nullptr;

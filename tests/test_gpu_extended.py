@@ -81,9 +81,9 @@ def test_profile_wider_than_map_rejected(shot):
 
 
 # Wide supports: the tiled kernels stage their tiles in shared memory, two tiles of a Gaussian pass
-# in at most 200 KB (up to a half-width of 131 pixels) and a disc's tile in 48 KB (up to a radius of
-# 15 pixels); wider supports run the untiled kernels. Sizes on both sides of each limit, on a 320^2
-# map.
+# in at most 200 KB (up to a half-width of 131 pixels) and a disc's tile with its staging buffer in
+# 72 KB (up to a radius of 15 pixels); wider supports run the untiled kernels. Sizes on both sides of
+# each limit, on a 320^2 map.
 CFG_WIDE = dict(CFG, npix_side=320, side=7.5)            # pixel 0.0234375 R_E
 
 

@@ -38,7 +38,7 @@ def restore_counts(ctx, counts, nrays, side=6.0):
 
 # The device keeps histograms of the counts below 1024 in shared memory, sends counts below
 # T = 4096 (at these N_rays) to global histograms and lists the larger ones (room for
-# max(4096, N_side^2 / 16) per map), widening the histograms afterwards; when a list runs out of
+# max(4096, N_side^2 / 64) per map), widening the histograms afterwards; when a list runs out of
 # room, a second pass over the maps builds the wide histograms. Seeded synthetic count maps (put on
 # the device by mm_map_restore, as restore_counts above) cover each way: only small counts; a tail
 # up to about 10^5 on 2 % of the pixels (listed); the same tail on 12 % of a 256^2 map (about 7900
@@ -56,7 +56,7 @@ def test_compare_matches_oracle_statistics(ctx, nside, tail):
     cb.ravel()[rng.integers(0, nside * nside, 9)] = 0
     assert (int(max(ca.max(), cb.max())) >= 4096) == (tail > 0)
     big = int(np.sum(ca >= 4096))
-    assert (big > max(4096, nside * nside // 16)) == (tail > 0.1)
+    assert (big > max(4096, nside * nside // 64)) == (tail > 0.1)
     assert (ca == 0).any() and (cb == 0).any()
     a = restore_counts(ctx, ca, nrays_a)
     b = restore_counts(ctx, cb, nrays_b)
