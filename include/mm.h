@@ -450,9 +450,16 @@ int mm_debug_deflect(mm_ctx *ctx, mm_lenses lenses, const mm_params *p,
  *     copies into shared memory: its waits for them give up after their limit
  *     (about one second of SM clocks), the call returns MM_EDEVICE, and the
  *     context stays usable.
+ *   MM_INJECT_DISC_NO_COPY  the next disc convolution (mm_map_convolve or
+ *     mm_map_lightcurve with MM_PROFILE_DISC, radius up to 15 pixels) announces
+ *     but issues none of the bulk copies that stage its interior tiles: those
+ *     waits give up after their limit, the call returns MM_EDEVICE, and the
+ *     context stays usable.
+ * An armed failure stays armed until a call of its kind takes it.
  * MM_INJECT_NONE disarms. Errors: MM_EINVAL (null context, unknown kind). */
 #define MM_INJECT_NONE             0
 #define MM_INJECT_COMPARE_NO_COPY  1
+#define MM_INJECT_DISC_NO_COPY     2
 int mm_debug_inject(mm_ctx *ctx, int32_t kind);
 
 /* ---- shooting without allocation --------------------------------------------

@@ -41,7 +41,7 @@ MM_FP32C, MM_FP64, MM_FAR32 = 0, 1, 2
 MM_MASS_UNIT, MM_MASS_LOGNORMAL = 0, 1
 MM_PROFILE_GAUSSIAN, MM_PROFILE_DISC = 0, 1
 MM_MAP_MU, MM_MAP_DELTA_M = 0, 1
-MM_INJECT_NONE, MM_INJECT_COMPARE_NO_COPY = 0, 1
+MM_INJECT_NONE, MM_INJECT_COMPARE_NO_COPY, MM_INJECT_DISC_NO_COPY = 0, 1, 2
 
 
 class MMError(RuntimeError):

@@ -174,6 +174,12 @@ struct mm_ctx {
 };
 
 namespace mm {
+// The test failure armed by mm_debug_inject, if it is `kind`: true once, and disarms it.
+inline bool take_injection(mm_ctx *ctx, int kind)
+{
+    int expected = kind;
+    return ctx->inject.compare_exchange_strong(expected, 0);
+}
 // Shared helpers used by the synchronous API and the server.
 int make_lenses_from_params(mm_ctx *ctx, const mm_params *p, const Geo &g, cudaStream_t s,
                             std::shared_ptr<LensSet> *out);

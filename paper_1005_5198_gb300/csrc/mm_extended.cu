@@ -70,9 +70,10 @@ __global__ void k_disc(const unsigned *cin, float *out, int n, const int *span, 
 
 // ---- tiled forms of the passes above: the same per-pixel sums in the same order ----
 
-constexpr int kDiscTileW = 64, kDiscTileH = 32;        // disc: 64 x 32 outputs per CTA
-constexpr size_t kDiscSmemMax = 72 * 1024;             // dynamic shared memory of a tiled disc CTA (radius up
-                                                       // to 15 pixels); wider supports take the untiled kernel
+constexpr int kDiscTileW = 64, kDiscTileH = 64;        // disc: 64 x 64 outputs per CTA
+constexpr int kDiscPer = 16;                           // outputs per thread, down its column (4 row groups)
+constexpr int kDiscMaxH = 15;                          // widest radius (pixels) of the tiled disc kernel; wider
+                                                       // supports take the untiled kernel
 constexpr size_t kGaussSmemMax = 200 * 1024;           // a double-buffered Gaussian CTA (h <= 131; wider
                                                        // supports take the untiled kernel)
 
@@ -99,13 +100,38 @@ __host__ __device__ inline size_t gauss_smem(int h)
 {
     return ((size_t)2 * gauss_taps_padded(h) + 2 * gauss_tile_floats(h)) * 4;
 }
-// Disc tile: prefix rows [(32 + 2H) x W] (room for 64-bit sums), then the raw counts of the next
-// tile [(32 + 2H) x (W - 1)], then the spans [2H + 1]; W = 64 + 2H + 1.
-__host__ __device__ inline size_t disc_smem(int H)
+// Disc tile of radius H: rows [r0 - H, r0 + 64 + H) x columns [c0 - H4, c0 + 64 + H4) of the counts,
+// H4 = H rounded up to a multiple of 4 (so that a staged row starts on a 16-byte boundary when N_side
+// is a multiple of 4). Shared memory: 32-bit prefix rows [rows x pitch] (pitch = columns + 1, a leading
+// zero), then, from the next 16-byte boundary, the raw counts of the next tile [rows x columns]. The
+// rare 64-bit prefix rows [rows x pitch] take the bytes of both.
+__host__ __device__ constexpr int disc_halo_cols(int H) { return (H + 3) & ~3; }
+__host__ __device__ constexpr int disc_cols(int H) { return kDiscTileW + 2 * disc_halo_cols(H); }
+__host__ __device__ constexpr int disc_rows(int H) { return kDiscTileH + 2 * H; }
+__host__ __device__ constexpr int disc_pitch(int H) { return disc_cols(H) + 1; }
+__host__ __device__ constexpr size_t disc_raw_offset(int H)
 {
-    const size_t rows = (size_t)(kDiscTileH + 2 * H), W = (size_t)(kDiscTileW + 2 * H + 1);
-    return rows * W * 8 + rows * (W - 1) * 4 + (size_t)(2 * H + 1) * 4;
+    return ((size_t)disc_rows(H) * disc_pitch(H) * 4 + 15) & ~(size_t)15;
 }
+__host__ __device__ constexpr size_t disc_smem(int H) { return (size_t)disc_rows(H) * disc_pitch(H) * 8; }
+__host__ __device__ constexpr bool disc_layout_fits()
+{
+    for (int H = 0; H <= kDiscMaxH; ++H)
+        if (disc_raw_offset(H) + (size_t)disc_rows(H) * disc_cols(H) * 4 > disc_smem(H) || disc_cols(H) > 96) return false;
+    return true;
+}
+static_assert(disc_layout_fits(), "the raw counts fit beside the 32-bit prefix rows, at most 96 columns");
+
+// CTAs of the tiled disc kernel per SM: as many as its shared memory allows, up to 4 (64 registers).
+__host__ __device__ constexpr int disc_ctas_per_sm(int H)
+{
+    return disc_smem(H) * 4 <= 220 * 1024 ? 4 : disc_smem(H) * 3 <= 220 * 1024 ? 3 : 2;
+}
+
+// Row half-widths of a disc, span w[k] on row offset k - H (passed by value to the kernel).
+struct DiscSpans {
+    int w[2 * kDiscMaxH + 1];
+};
 
 // acc[u] = sum over taps k < TP of g[k] x[(u + k) st], u < 16: x the thread's first input pair,
 // st the distance between consecutive input pairs (in pairs), gs2 the taps as pairs (g, g).
@@ -218,69 +244,84 @@ __global__ void __launch_bounds__(256, 1) k_gauss_vt(const void *in, float *out_
     }
 }
 
-// Disc: a CTA stages the counts of rows [r0 - H, r0 + 32 + H) x columns [c0 - H, c0 + 64 + H)
-// as prefix sums along each row (one warp per row, with a leading zero), so the sum over a row
-// span [i - w, i + w] is one difference. An output's disc sum is the integer total of its row
-// spans, converted to float once (as k_disc). The prefix sums are taken modulo 2^32 first; a
-// CTA-wide vote on the tile's largest count picks how the spans are added:
+// Disc (tiled): a CTA stages the counts of its tile with a halo of H rows and H4 columns, and takes
+// prefix sums along each staged row (with a leading zero), so the sum over a row span [i - w, i + w]
+// is one difference. An output's disc sum is the integer total of its row spans, converted to float
+// once (as k_disc). The prefix sums are taken modulo 2^32 first; a CTA-wide vote on the tile's
+// largest count picks how the spans are added:
 //   every count below 2^32 / (2H + 1)^2: the whole disc sum is below 2^32, so the span
 //     differences add up exactly in 32 bits;
 //   every count below 2^32 / (2H + 1): each span sum is below 2^32 and its 32-bit difference is
 //     exact; the spans add up in 64 bits;
 //   otherwise the tile is staged again as 64-bit prefix sums.
-// The three ways give the same integer, hence the same float.
-template <typename P>
-__device__ __forceinline__ void disc_prefix_rows(const unsigned *cin, int n, int r0, int c0, int H, int W, P *pre,
-                                                 unsigned &maxc)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int rr = warp; rr < kDiscTileH + 2 * H; rr += 8) {       // prefix sums of tile row rr
-        const int j = r0 - H + rr;
-        P carry = 0;
-        if (lane == 0) pre[(size_t)rr * W] = 0;
-        for (int x0 = 0; x0 < W - 1; x0 += 32) {
-            const int x = x0 + lane, i = c0 - H + x;
-            const unsigned cnt = (x < W - 1 && j >= 0 && j < n && i >= 0 && i < n) ? cin[(long long)j * n + i] : 0u;
-            maxc = max(maxc, cnt);
-            P v = cnt;
-            for (int o = 1; o < 32; o <<= 1) {
-                const P u = __shfl_up_sync(0xffffffffu, v, o);
-                if (lane >= o) v += u;
-            }
-            if (x < W - 1) pre[(size_t)rr * W + x + 1] = carry + v;
-            carry += __shfl_sync(0xffffffffu, v, 31);
-        }
-    }
-}
+// The three ways give the same integer, hence the same float. The kernel is compiled for each radius
+// H <= 15: the tap rows and the 16 outputs of a thread are unrolled, so every shared load of a span
+// end is an immediate offset from one of two addresses per tap row.
 
-// The raw counts of tile rows [r0 - H, r0 + 32 + H) x columns [c0 - H, c0 + 64 + H) into raw
-// [(32 + 2H) x (W - 1)] by 4-byte cp.async (zeros outside the map); warp w copies rows w, w + 8, ...
-__device__ __forceinline__ void disc_stage_raw(const unsigned *cin, int n, int r0, int c0, int H, int W, unsigned *raw)
+// The raw counts of tile (r0, c0) into raw [rows x columns], zeros outside the map: 16-byte cp.async
+// when N_side is a multiple of 4 (a 4-column group is then wholly inside or outside the map), else
+// 4-byte copies.
+template <int H>
+__device__ __forceinline__ void disc_stage(const unsigned *cin, int n, int r0, int c0, bool vec, unsigned *raw)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int rr = warp; rr < kDiscTileH + 2 * H; rr += 8) {
-        const int j = r0 - H + rr;
-        for (int x = lane; x < W - 1; x += 32) {
-            const int i = c0 - H + x;
+    constexpr int RT = disc_rows(H), CW = disc_cols(H), H4 = disc_halo_cols(H);
+    if (vec) {
+        constexpr int G = CW / 4;                          // 16-byte groups per row
+        for (int q = threadIdx.x; q < RT * G; q += blockDim.x) {
+            const int rr = q / G, x = 4 * (q - rr * G);
+            const int j = r0 - H + rr, i = c0 - H4 + x;
             const bool ok = j >= 0 && j < n && i >= 0 && i < n;
-            cp_async4(raw + (size_t)rr * (W - 1) + x, cin + (ok ? (long long)j * n + i : 0), ok ? 4u : 0u);
+            cp_async16(raw + rr * CW + x, cin + (ok ? (long long)j * n + i : 0), ok ? 16u : 0u);
+        }
+    } else {
+        for (int q = threadIdx.x; q < RT * CW; q += blockDim.x) {
+            const int rr = q / CW, x = q - rr * CW;
+            const int j = r0 - H + rr, i = c0 - H4 + x;
+            const bool ok = j >= 0 && j < n && i >= 0 && i < n;
+            cp_async4(raw + q, cin + (ok ? (long long)j * n + i : 0), ok ? 4u : 0u);
         }
     }
     cp_async_commit();
 }
 
-// 32-bit prefix rows (modulo 2^32, a leading zero) from the staged raw counts: lane l of the row's
-// warp adds its three consecutive counts (columns 3l .. 3l + 2; W - 1 <= 96), then the warp scans
-// the lanes' totals. Also the largest count seen, for the CTA's choice of sums.
-__device__ __forceinline__ void disc_scan_rows(const unsigned *raw, int H, int W, unsigned *pre, unsigned &maxc)
+// A tile whose staged rectangle lies inside the map (and N_side a multiple of 4, so that every staged
+// row starts on a 16-byte boundary) is staged by one bulk copy per row, completing on bar; warp 0 issues
+// them once lane 0 has announced their bytes. Other tiles take disc_stage.
+template <int H>
+__device__ __forceinline__ bool disc_interior(int n, int r0, int c0)
 {
+    constexpr int H4 = disc_halo_cols(H);
+    return (n & 3) == 0 && r0 - H >= 0 && r0 + kDiscTileH + H <= n && c0 - H4 >= 0 && c0 + kDiscTileW + H4 <= n;
+}
+
+template <int H>
+__device__ __forceinline__ void disc_stage_bulk(const unsigned *cin, int n, int r0, int c0, unsigned *raw,
+                                                uint64_t *bar, bool withhold)
+{
+    constexpr int RT = disc_rows(H), CW = disc_cols(H), H4 = disc_halo_cols(H);
+    if (threadIdx.x < 32) {
+        if (threadIdx.x == 0) mbar_arrive_expect(bar, (unsigned)(RT * CW * 4));
+        __syncwarp();
+        if (!withhold)                                     // (test hook: announce the bytes, copy nothing)
+            for (int rr = threadIdx.x; rr < RT; rr += 32)
+                bulk_load(raw + rr * CW, cin + (long long)(r0 - H + rr) * n + (c0 - H4), (unsigned)(CW * 4), bar);
+    }
+}
+
+// 32-bit prefix rows (modulo 2^32, a leading zero) from the staged raw counts: lane l of the row's
+// warp adds its three consecutive counts (columns 3l .. 3l + 2; at most 96 columns), then the warp
+// scans the lanes' totals. Also the largest count seen, for the CTA's choice of sums.
+template <int H>
+__device__ __forceinline__ void disc_scan(const unsigned *raw, unsigned *pre, unsigned &maxc)
+{
+    constexpr int RT = disc_rows(H), CW = disc_cols(H), P = disc_pitch(H);
+    static_assert(CW <= 96, "three columns per lane");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int rr = warp; rr < kDiscTileH + 2 * H; rr += 8) {
-        const unsigned *const r = raw + (size_t)rr * (W - 1);
-        unsigned *const p = pre + (size_t)rr * W;
+    for (int rr = warp; rr < RT; rr += 8) {
+        const unsigned *const r = raw + rr * CW;
+        unsigned *const p = pre + rr * P;
         const int x = 3 * lane;
-        const unsigned a0 = x < W - 1 ? r[x] : 0u, a1 = x + 1 < W - 1 ? r[x + 1] : 0u,
-                       a2 = x + 2 < W - 1 ? r[x + 2] : 0u;
+        const unsigned a0 = x < CW ? r[x] : 0u, a1 = x + 1 < CW ? r[x + 1] : 0u, a2 = x + 2 < CW ? r[x + 2] : 0u;
         maxc = max(maxc, max(a0, max(a1, a2)));
         const unsigned s0 = a0, s1 = a0 + a1, s2 = s1 + a2;
         unsigned incl = s2;
@@ -291,85 +332,181 @@ __device__ __forceinline__ void disc_scan_rows(const unsigned *raw, int H, int W
         }
         const unsigned excl = incl - s2;
         if (lane == 0) p[0] = 0u;
-        if (x < W - 1) p[x + 1] = excl + s0;
-        if (x + 1 < W - 1) p[x + 2] = excl + s1;
-        if (x + 2 < W - 1) p[x + 3] = excl + s2;
+        if (x < CW) p[x + 1] = excl + s0;
+        if (x + 1 < CW) p[x + 2] = excl + s1;
+        if (x + 2 < CW) p[x + 3] = excl + s2;
     }
 }
 
-// Thread (column c, row group rg) computes the 8 outputs of rows rg, rg + 4, ..., rg + 28 of the
-// tile together (8 independent sums). P: prefix type; A: accumulator type.
-template <typename P, typename A>
-__device__ __forceinline__ void disc_outputs(const P *pre, const int *sp, float *out, int n, int r0, int c0, int H,
-                                             int W, float scale)
+// 64-bit prefix rows of tile (r0, c0) read from global memory (the rare tiles with a count of
+// 2^32 / (2H + 1) or more); one warp per row.
+__device__ __forceinline__ void disc_prefix64(const unsigned *cin, int n, int r0, int c0, int H, unsigned long long *pre)
 {
-    constexpr int kPer = kDiscTileH / 4;
-    const int c = threadIdx.x & (kDiscTileW - 1), rg = threadIdx.x / kDiscTileW;   // 4 row groups
-    const int i = c0 + c;
-    A acc[kPer];
+    const int RT = disc_rows(H), CW = disc_cols(H), P = disc_pitch(H), H4 = disc_halo_cols(H);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll 1
+    for (int rr = warp; rr < RT; rr += 8) {
+        const int j = r0 - H + rr;
+        unsigned long long carry = 0;
+        if (lane == 0) pre[rr * P] = 0;
+#pragma unroll 1
+        for (int x0 = 0; x0 < CW; x0 += 32) {
+            const int x = x0 + lane, i = c0 - H4 + x;
+            const unsigned cnt = (x < CW && j >= 0 && j < n && i >= 0 && i < n) ? cin[(long long)j * n + i] : 0u;
+            unsigned long long v = cnt;
 #pragma unroll
-    for (int u = 0; u < kPer; ++u) acc[u] = 0;
-    for (int dj = -H; dj <= H; ++dj) {
-        const int w = sp[dj + H];
-        const P *row = pre + (size_t)(rg + dj + H) * W + c + H;
-#pragma unroll
-        for (int u = 0; u < kPer; ++u) {
-            const P *ru = row + (size_t)(4 * u) * W;
-            acc[u] += (A)(P)(ru[w + 1] - ru[-w]);
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += u;
+            }
+            if (x < CW) pre[rr * P + x + 1] = carry + v;
+            carry += __shfl_sync(0xffffffffu, v, 31);
         }
     }
+}
+
+// Thread (column c, row group g) computes outputs r0 + 16 g + u, u < 16, of column c0 + c: for tap row
+// k (row offset k - H) and output u the staged row is 16 g + u + k, and the span of half-width w[k]
+// is pre[.. + w + 1] - pre[.. - w]. PT: prefix type; A: accumulator type. The integer totals go out
+// as floats, NaN where the disc leaves the map.
+template <typename A>
+__device__ __forceinline__ void disc_store(const A (&acc)[kDiscPer], float *out, int n, int r0, int c0, int H,
+                                           float scale)
+{
+    const int c = threadIdx.x & (kDiscTileW - 1), g = threadIdx.x / kDiscTileW;
+    const int i = c0 + c;
     const bool col_ok = i - H >= 0 && i + H < n;
 #pragma unroll
-    for (int u = 0; u < kPer; ++u) {
-        const int j = r0 + rg + 4 * u;
+    for (int u = 0; u < kDiscPer; ++u) {
+        const int j = r0 + kDiscPer * g + u;
         if (i < n && j < n)
             out[(long long)j * n + i] = (col_ok && j - H >= 0 && j + H < n) ? (float)acc[u] * scale
                                                                             : __int_as_float(0x7fc00000);
     }
 }
 
-// A CTA takes tiles t, t + gridDim.x, ...: while it computes the outputs of one tile, the raw counts of
-// the next arrive by cp.async; the 64-bit way (rare) reads its tile from global memory again.
-__global__ void __launch_bounds__(256) k_disc_tiled(const unsigned *cin, float *out, int n, const int *span, int H,
-                                                    float scale)
+// The common way (32-bit prefix rows and sums), compiled for each radius: the tap rows and the 16
+// outputs unrolled, so that every load is an immediate offset from base (the thread's column on its
+// first staged row) plus the tap row's span end, which is the same for every thread of the launch.
+template <int H>
+__device__ __forceinline__ void disc_outputs32(const unsigned *base, const DiscSpans &sp, float *out, int n, int r0,
+                                               int c0, float scale)
 {
-    extern __shared__ unsigned long long psm[];
-    const int W = kDiscTileW + 2 * H + 1;                  // prefix row length
-    const int rows_t = kDiscTileH + 2 * H;
-    unsigned long long *const pre64 = psm;                 // [(32 + 2H) x W], or the same bytes as
-    unsigned *const pre32 = (unsigned *)psm;               // [(32 + 2H) x W] 32-bit sums
-    unsigned *const raw = (unsigned *)(psm + (size_t)rows_t * W);               // [(32 + 2H) x (W - 1)]
-    int *const sp = (int *)(raw + (size_t)rows_t * (W - 1));
-    for (int k = threadIdx.x; k < 2 * H + 1; k += blockDim.x) sp[k] = span[k];
+    constexpr int P = disc_pitch(H);
+    unsigned acc[kDiscPer];
+#pragma unroll
+    for (int u = 0; u < kDiscPer; ++u) acc[u] = 0u;
+#pragma unroll
+    for (int k = 0; k <= 2 * H; ++k) {
+        const unsigned *const hi = base + k * P + sp.w[k] + 1, *const lo = base + k * P - sp.w[k];
+#pragma unroll
+        for (int u = 0; u < kDiscPer; ++u) acc[u] += hi[u * P] - lo[u * P];
+    }
+    disc_store<unsigned>(acc, out, n, r0, c0, H, scale);
+}
+
+// The rare ways (64-bit sums of 32-bit spans, or 64-bit prefix rows): the same sums, tap rows not
+// unrolled.
+template <typename PT>
+__device__ __forceinline__ void disc_outputs64(const PT *pre, const int *sp, float *out, int n, int r0, int c0,
+                                            int H, float scale)
+{
+    const int P = disc_pitch(H), H4 = disc_halo_cols(H);
+    const int c = threadIdx.x & (kDiscTileW - 1), g = threadIdx.x / kDiscTileW;
+    const PT *const base = pre + (kDiscPer * g) * P + c + H4;
+    unsigned long long acc[kDiscPer];
+#pragma unroll
+    for (int u = 0; u < kDiscPer; ++u) acc[u] = 0ull;
+#pragma unroll 1
+    for (int k = 0; k <= 2 * H; ++k) {
+        const int w = sp[k];
+        const PT *const hi = base + k * P + w + 1, *const lo = base + k * P - w;
+#pragma unroll
+        for (int u = 0; u < kDiscPer; ++u) acc[u] += (unsigned long long)(PT)(hi[u * P] - lo[u * P]);
+    }
+    disc_store<unsigned long long>(acc, out, n, r0, c0, H, scale);
+}
+
+// A CTA takes tiles t, t + gridDim.x, ...: while it computes the outputs of one tile, the raw counts of
+// the next arrive (bulk copies for interior tiles, cp.async otherwise). A 64-bit tile (rare) waits for
+// its outputs before the next copy starts, since its prefix rows cover the staging buffer. A wait for
+// bulk copies that runs out of time sets *fault and ends the CTA.
+template <int H>
+__global__ void __launch_bounds__(256, disc_ctas_per_sm(H)) k_disc_tiled(const unsigned *cin, float *out, int n,
+                                                                         const DiscSpans sp, float scale,
+                                                                         unsigned *fault, int withhold)
+{
+    extern __shared__ uint4 dsm[];
+    __shared__ int spans[2 * H + 1];                       // the spans, read by index in the 64-bit ways
+    __shared__ uint64_t bar;                               // completion of a tile's bulk copies
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k <= 2 * H; ++k) spans[k] = sp.w[k];
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    unsigned *const pre32 = reinterpret_cast<unsigned *>(dsm);
+    unsigned long long *const pre64 = reinterpret_cast<unsigned long long *>(dsm);
+    unsigned *const raw = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(dsm) + disc_raw_offset(H));
+    // this thread's column on its first staged row (the same for every tile)
+    const unsigned *const base = pre32 + (kDiscPer * (threadIdx.x / kDiscTileW)) * disc_pitch(H) +
+                                 (threadIdx.x & (kDiscTileW - 1)) + disc_halo_cols(H);
+    const bool vec = (n & 3) == 0;
     const int cols = (n + kDiscTileW - 1) / kDiscTileW, rows = (n + kDiscTileH - 1) / kDiscTileH;
     const long long tiles = (long long)cols * rows;
     const unsigned long long taps1 = (unsigned long long)(2 * H + 1);
     const unsigned small_span = (unsigned)(0xffffffffull / taps1);             // span sums below 2^32
     const unsigned small_disc = (unsigned)(0xffffffffull / (taps1 * taps1));   // disc sums below 2^32
-    if (blockIdx.x < tiles)
-        disc_stage_raw(cin, n, (int)(blockIdx.x / cols) * kDiscTileH, (int)(blockIdx.x % cols) * kDiscTileW, H, W, raw);
+    auto stage = [&](long long t) {
+        const int c0 = (int)(t % cols) * kDiscTileW, r0 = (int)(t / cols) * kDiscTileH;
+        if (disc_interior<H>(n, r0, c0)) disc_stage_bulk<H>(cin, n, r0, c0, raw, &bar, withhold != 0);
+        else disc_stage<H>(cin, n, r0, c0, vec, raw);
+    };
+    unsigned phase = 0u;
+    if (blockIdx.x < tiles) stage(blockIdx.x);
     for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
         const int c0 = (int)(t % cols) * kDiscTileW, r0 = (int)(t / cols) * kDiscTileH;
-        cp_async_wait<0>();
-        __syncthreads();                                   // tile t's counts staged; the previous outputs done
+        if (disc_interior<H>(n, r0, c0)) {
+            const bool ok = mbar_wait(&bar, phase);
+            if (__syncthreads_or(!ok)) {                   // (also the barrier below)
+                if (threadIdx.x == 0) {
+                    atomicExch(fault, 1u);
+                    mbar_wait(&bar, phase);                // copies still in flight land before the CTA ends
+                }
+                return;
+            }
+            phase ^= 1u;
+        } else {
+            cp_async_wait<0>();
+            __syncthreads();                               // tile t's counts staged; the previous outputs done
+        }
         unsigned maxc = 0;
-        disc_scan_rows(raw, H, W, pre32, maxc);
+        disc_scan<H>(raw, pre32, maxc);
         // (both votes are also barriers: the raw counts are read and the prefix rows written)
         const bool not_disc32 = __syncthreads_or(maxc >= small_disc), not_span32 = __syncthreads_or(maxc >= small_span);
         const long long tn = t + gridDim.x;
-        if (tn < tiles) disc_stage_raw(cin, n, (int)(tn / cols) * kDiscTileH, (int)(tn % cols) * kDiscTileW, H, W, raw);
-        if (!not_disc32) {
-            disc_outputs<unsigned, unsigned>(pre32, sp, out, n, r0, c0, H, W, scale);
-        } else if (!not_span32) {
-            disc_outputs<unsigned, unsigned long long>(pre32, sp, out, n, r0, c0, H, W, scale);
+        if (!not_span32) {
+            if (tn < tiles) stage(tn);
+            if (!not_disc32) disc_outputs32<H>(base, sp, out, n, r0, c0, scale);
+            else disc_outputs64<unsigned>(pre32, spans, out, n, r0, c0, H, scale);
         } else {                                           // a count of 2^32 / (2H + 1) or more: 64 bits
+            disc_prefix64(cin, n, r0, c0, H, pre64);
             __syncthreads();
-            disc_prefix_rows<unsigned long long>(cin, n, r0, c0, H, W, pre64, maxc);
-            __syncthreads();
-            disc_outputs<unsigned long long, unsigned long long>(pre64, sp, out, n, r0, c0, H, W, scale);
+            disc_outputs64<unsigned long long>(pre64, spans, out, n, r0, c0, H, scale);
+            __syncthreads();                               // the prefix rows over the staging buffer are read
+            if (tn < tiles) stage(tn);
         }
     }
 }
+
+using DiscKernel = void (*)(const unsigned *, float *, int, const DiscSpans, float, unsigned *, int);
+template <int... Hs>
+struct DiscKernels {
+    static constexpr DiscKernel table[] = {k_disc_tiled<Hs>...};
+};
+static_assert(kDiscMaxH == 15, "the kernel table lists H = 0 .. 15");
+using DiscTable = DiscKernels<0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15>;
 
 // Bilinear samples of the convolved map at source positions (Einstein radii).
 __global__ void k_track(const float *f, int n, double half_side, double pix, double y1a, double y2a, double y1b,
@@ -448,23 +585,35 @@ int convolve(mm_ctx *ctx, const MapObj &M, int profile, double size_re, float *d
         span[dj + H] = w;
         taps += 2 * w + 1;
     }
+    const float scale = (float)(1.0 / ((double)taps * M.p.nrays_per_pix));
+    if (H <= kDiscMaxH) {                                  // tiled: the kernel compiled for this radius
+        DiscSpans sp{};
+        for (int k = 0; k <= 2 * H; ++k) sp.w[k] = span[k];
+        const DiscKernel fn = DiscTable::table[H];
+        const size_t smem = disc_smem(H);
+        e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem) != cudaSuccess) per_sm = 1;
+        const long long tiles = (long long)((n + kDiscTileW - 1) / kDiscTileW) * ((n + kDiscTileH - 1) / kDiscTileH);
+        const int dgrid = (int)std::max(1LL, std::min(tiles, (long long)std::max(1, per_sm) * ctx->sms));
+        unsigned *dfault = nullptr, hfault = 0;
+        int rc = ctx->arena.alloc(sizeof(unsigned), (void **)&dfault);
+        if (rc) return rc;
+        const int withhold = take_injection(ctx, MM_INJECT_DISC_NO_COPY) ? 1 : 0;
+        if (e == cudaSuccess) e = cudaMemsetAsync(dfault, 0, sizeof(unsigned), s);
+        if (e == cudaSuccess) fn<<<dgrid, 256, smem, s>>>(M.counts, dst, n, sp, scale, dfault, withhold);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hfault, dfault, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        ctx->arena.free(dfault);
+        if (e != cudaSuccess) return cuda_fail(e, "disc convolution");
+        return hfault ? fail(MM_EDEVICE, "k_disc_tiled: a copy into shared memory did not complete") : MM_OK;
+    }
     int *ds = nullptr;
     int rc = ctx->arena.alloc(span.size() * sizeof(int), (void **)&ds);
     if (rc) return rc;
     if ((e = cudaMemcpyAsync(ds, span.data(), span.size() * sizeof(int), cudaMemcpyHostToDevice, s)) == cudaSuccess) {
-        const float scale = (float)(1.0 / ((double)taps * M.p.nrays_per_pix));
-        const size_t smem = disc_smem(H);
-        if (smem <= kDiscSmemMax) {
-            e = cudaFuncSetAttribute(k_disc_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDiscSmemMax);
-            int per_sm = 1;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_disc_tiled, 256, smem) != cudaSuccess) per_sm = 1;
-            const long long tiles =
-                (long long)((n + kDiscTileW - 1) / kDiscTileW) * ((n + kDiscTileH - 1) / kDiscTileH);
-            const int dgrid = (int)std::max(1LL, std::min(tiles, (long long)std::max(1, per_sm) * ctx->sms));
-            if (e == cudaSuccess) k_disc_tiled<<<dgrid, 256, smem, s>>>(M.counts, dst, n, ds, H, scale);
-        } else {
-            k_disc<<<grid, 256, 0, s>>>(M.counts, dst, n, ds, H, scale);
-        }
+        k_disc<<<grid, 256, 0, s>>>(M.counts, dst, n, ds, H, scale);
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     }

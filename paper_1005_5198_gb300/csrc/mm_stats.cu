@@ -517,7 +517,7 @@ extern "C" int mm_map_compare(mm_ctx *ctx, mm_map a, mm_map b, mm_compare *out)
     const long long chunks = ((n / 4) * 16 + kCmpChunk - 1) / kCmpChunk;
     const int cgrid = (int)std::max(1LL, std::min((long long)(4 * ctx->sms), chunks));   // 4 CTAs fit an SM
     CmpArgs g{tab, tab + T, lra, lrb, T, hist, hist + T, lists, lists + cap, cap, 0,
-              ctx->inject.exchange(MM_INJECT_NONE) == MM_INJECT_COMPARE_NO_COPY ? 1 : 0};
+              take_injection(ctx, MM_INJECT_COMPARE_NO_COPY) ? 1 : 0};
     k_compare<<<cgrid, kCmpThreads, kCmpSmem, s>>>(A->counts, B->counts, n, g, d_sum);
     auto ks_steps = [&](const unsigned *h2, long long *c2, long long nb) {
         k_scan<<<1, 1024, 0, s>>>(h2, h2 + nb, nb, c2, c2 + nb, d_sum);
@@ -655,7 +655,8 @@ extern "C" int mm_map_fetch_mu(mm_ctx *ctx, mm_map map, int32_t kind, float *hos
 extern "C" int mm_debug_inject(mm_ctx *ctx, int32_t kind)
 {
     if (!ctx) return fail(MM_EINVAL, "null context");
-    if (kind != MM_INJECT_NONE && kind != MM_INJECT_COMPARE_NO_COPY) return fail(MM_EINVAL, "unknown injection");
+    if (kind != MM_INJECT_NONE && kind != MM_INJECT_COMPARE_NO_COPY && kind != MM_INJECT_DISC_NO_COPY)
+        return fail(MM_EINVAL, "unknown injection");
     ctx->inject.store(kind);
     return MM_OK;
 }

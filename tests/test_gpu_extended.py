@@ -73,6 +73,24 @@ def test_lightcurve_matches_oracle(shot):
     np.testing.assert_allclose(got[ok], ref[ok], rtol=2e-5, atol=1e-6)
 
 
+def test_disc_wait_that_runs_out_reports_a_device_error(shot):
+    """The tiled disc kernel stages the tiles that lie inside the map by bulk copies and waits for them on
+    an mbarrier with a time limit. With those copies withheld (test hook), the waits give up after their
+    limit (about a second), the call returns MM_EDEVICE instead of hanging, and the same context then
+    convolves correctly. The 256^2 map at radius 5 pixels has four such tiles."""
+    ctx, m, counts = shot
+    mm.mm_debug_inject(ctx, mm.MM_INJECT_DISC_NO_COPY)
+    mm.mm_map_convolve(ctx, m, mm.MM_PROFILE_GAUSSIAN, 0.05)    # another kind of call leaves it armed
+    with pytest.raises(mm.MMError) as e:
+        mm.mm_map_convolve(ctx, m, mm.MM_PROFILE_DISC, 0.12)
+    assert e.value.code == mm.MM_EDEVICE
+    got = mm.mm_map_convolve(ctx, m, mm.MM_PROFILE_DISC, 0.12)  # the hook is one-shot
+    ref = oext.convolve(counts, CFG["nrays"], mm.MM_PROFILE_DISC, 0.12, CFG["side"] / CFG["npix_side"])
+    np.testing.assert_array_equal(np.isnan(got), np.isnan(ref))
+    ok = ~np.isnan(ref)
+    np.testing.assert_allclose(got[ok], ref[ok], rtol=2e-5, atol=1e-6)
+
+
 def test_profile_wider_than_map_rejected(shot):
     ctx, m, _ = shot
     with pytest.raises(mm.MMError) as e:
