@@ -9,7 +9,8 @@ ray-shooting estimator of Sect. 2), used to prove the CUDA path right.
 The arithmetic lives in `mm_oracle.c` (plain C, FP64, lenses summed in
 index order, OpenMP over ray rows); `field.py` holds the lens-field rules.
 Parameters are passed as a mapping with keys sigma, gamma, smooth_frac, side,
-npix_side, nrays and margin (default 1.5).
+npix_side, nrays and margin (default 1.5), and optionally ray_mode (RAYS_LATTICE,
+the default, or RAYS_RANDOM) and ray_seed.
 """
 from __future__ import annotations
 
@@ -34,7 +35,10 @@ _lib = None
 class _Params(C.Structure):
     _fields_ = [("sigma", C.c_double), ("gamma", C.c_double), ("smooth_frac", C.c_double),
                 ("side", C.c_double), ("npix_side", C.c_int32), ("nrays", C.c_double),
-                ("margin", C.c_double)]
+                ("margin", C.c_double), ("ray_mode", C.c_int32), ("ray_seed", C.c_uint64)]
+
+
+RAYS_LATTICE, RAYS_RANDOM = 0, 1
 
 
 class _Far(C.Structure):
@@ -83,7 +87,8 @@ def _load():
 def _params(p) -> _Params:
     g = p.get if isinstance(p, dict) else (lambda k, dflt=None: getattr(p, k, dflt))
     return _Params(float(g("sigma")), float(g("gamma")), float(g("smooth_frac", 0.0) or 0.0),
-                   float(g("side")), int(g("npix_side")), float(g("nrays")), float(g("margin", 1.5) or 1.5))
+                   float(g("side")), int(g("npix_side")), float(g("nrays")), float(g("margin", 1.5) or 1.5),
+                   int(g("ray_mode", RAYS_LATTICE) or RAYS_LATTICE), int(g("ray_seed", 0) or 0))
 
 
 def _ptr(a, t):

@@ -37,6 +37,12 @@
  *       source position is "out".
  *   Lenses are summed in index order.
  *
+ *   Random rays (ray_mode ORC_RAYS_RANDOM): the paper's GPU code shoots rays from
+ *   pseudo-random positions, so that a pixel receives N_rays rays on average only
+ *   (Sect. 2.3, step 2; Sect. 3.1). Reading taken: the same nx * ny rays are shot,
+ *   ray (i, j) uniformly at random in the 64 x 32-cell tile of the lattice that
+ *   holds cell (i, j), independently of every other ray (see ray_position).
+ *
  * The far-field approximation (orc_far_map, orc_far_rays) is at the end of
  * this file, with its own statement.
  */
@@ -70,11 +76,43 @@ int orc_geometry(const orc_params *P, orc_geometry_t *G)
     return 0;
 }
 
-/* Image-plane position of ray (i, j) on the regular grid. */
-static void ray_position(const orc_geometry_t *G, int64_t i, int64_t j, double *x1, double *x2)
+/* SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number generators",
+ * OOPSLA 2014): output k >= 1 of the generator seeded with s is mix(s + k * gamma mod 2^64),
+ * gamma = 0x9E3779B97F4A7C15, with the finaliser mix(z): z ^= z >> 30, z *= 0xBF58476D1CE4E5B9,
+ * z ^= z >> 27, z *= 0x94D049BB133111EB, z ^= z >> 31. */
+static uint64_t splitmix64_output(uint64_t s, uint64_t k)
 {
-    *x1 = ((double)i + 0.5 - 0.5 * (double)G->nx) * G->delta;
-    *x2 = ((double)j + 0.5 - 0.5 * (double)G->ny) * G->delta;
+    uint64_t z = s + k * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* Image-plane position of ray (i, j).
+ * Lattice: the centre of cell (i, j).
+ * Random: with q = j nx + i, u1 and u2 are the top 18 bits of outputs 2q + 1 and 2q + 2 of
+ * SplitMix64(ray_seed), as fractions in [0, 1) (18 bits, so that u w below is exact in single
+ * precision too); the tile is (Ti, Tj) = (floor(i / 64), floor(j / 32)), its width in cells
+ * wi = min(64, nx - 64 Ti) and height wj = min(32, ny - 32 Tj), and the ray sits at
+ *     x1 = (64 Ti + u1 wi - nx/2) Delta,   x2 = (32 Tj + u2 wj - ny/2) Delta,
+ * so that every ray is uniform over its (possibly partial) tile and the shot rectangle keeps
+ * the lattice's ray density. */
+static void ray_position(const orc_params *P, const orc_geometry_t *G, int64_t i, int64_t j, double *x1,
+                         double *x2)
+{
+    if (P->ray_mode != ORC_RAYS_RANDOM) {
+        *x1 = ((double)i + 0.5 - 0.5 * (double)G->nx) * G->delta;
+        *x2 = ((double)j + 0.5 - 0.5 * (double)G->ny) * G->delta;
+        return;
+    }
+    const uint64_t q = (uint64_t)j * (uint64_t)G->nx + (uint64_t)i;
+    const double u1 = (double)(splitmix64_output(P->ray_seed, 2 * q + 1) >> 46) / 262144.0;
+    const double u2 = (double)(splitmix64_output(P->ray_seed, 2 * q + 2) >> 46) / 262144.0;
+    const int64_t ti = i / 64, tj = j / 32;
+    const int64_t wi = G->nx - 64 * ti < 64 ? G->nx - 64 * ti : 64;
+    const int64_t wj = G->ny - 32 * tj < 32 ? G->ny - 32 * tj : 32;
+    *x1 = ((double)(64 * ti) + u1 * (double)wi - 0.5 * (double)G->nx) * G->delta;
+    *x2 = ((double)(32 * tj) + u2 * (double)wj - 0.5 * (double)G->ny) * G->delta;
 }
 
 /* Add lens i's term m_i (x - x_i) / |x - x_i|^2 of Eq. sigma to (s1, s2).
@@ -127,7 +165,7 @@ static int64_t shoot_one(const orc_params *P, const orc_geometry_t *G,
                          int64_t i, int64_t j, double *alpha, double *ysrc)
 {
     double x1, x2, a1 = NAN, a2 = NAN;
-    ray_position(G, i, j, &x1, &x2);
+    ray_position(P, G, i, j, &x1, &x2);
     int on_lens = deflection(lx, ly, lm, nstar, x1, x2, &a1, &a2);
     return source_pixel(P, G, x1, x2, a1, a2, on_lens, alpha, ysrc);
 }
@@ -572,7 +610,9 @@ int orc_far_map(const orc_params *P, const orc_far_params *F, const double *lx, 
                 uint32_t *counts, uint64_t totals[3], double *bound_max, int nthreads)
 {
     orc_geometry_t G;
-    if (orc_geometry(P, &G) != 0 || !far_params_ok(F) || !counts || !totals || nstar < 0) return -1;
+    if (orc_geometry(P, &G) != 0 || !far_params_ok(F) || !counts || !totals || nstar < 0 ||
+        P->ray_mode != ORC_RAYS_LATTICE)
+        return -1;
     if (nstar > 0 && (!lx || !ly || !lm)) return -1;
     if (i0 < 0) { i0 = 0; i1 = G.nx; j0 = 0; j1 = G.ny; }
     if (i1 > G.nx) i1 = G.nx;
@@ -611,7 +651,7 @@ int orc_far_map(const orc_params *P, const orc_far_params *F, const double *lx, 
         for (int64_t j = j0 + BY * bh; j < je; ++j) {
             for (int64_t i = i0 + BX * bw; i < ie; ++i) {
                 double x1, x2, a1 = NAN, a2 = NAN;
-                ray_position(&G, i, j, &x1, &x2);
+                ray_position(P, &G, i, j, &x1, &x2);
                 const int on_lens = far_deflection(&B, F, lx, ly, lm, x1, x2, &a1, &a2);
                 const int64_t k = source_pixel(P, &G, x1, x2, a1, a2, on_lens, NULL, NULL);
                 shot += 1;
@@ -642,7 +682,7 @@ int orc_far_rays(const orc_params *P, const orc_far_params *F, const double *lx,
 {
     orc_geometry_t G;
     if (orc_geometry(P, &G) != 0 || !far_params_ok(F) || n < 0 || !ray_i || !ray_j || !alpha || !ysrc || !pixel ||
-        !bound || i0 < 0 || j0 < 0)
+        !bound || i0 < 0 || j0 < 0 || P->ray_mode != ORC_RAYS_LATTICE)
         return -1;
     lens_tree T;
     double *binom = binom_table();
@@ -671,7 +711,7 @@ int orc_far_rays(const orc_params *P, const orc_far_params *F, const double *lx,
             continue;
         }
         double x1, x2, a1 = NAN, a2 = NAN;
-        ray_position(&G, ray_i[k], ray_j[k], &x1, &x2);
+        ray_position(P, &G, ray_i[k], ray_j[k], &x1, &x2);
         const int on_lens = far_deflection(&B, F, lx, ly, lm, x1, x2, &a1, &a2);
         pixel[k] = source_pixel(P, &G, x1, x2, a1, a2, on_lens, alpha + 2 * k, ysrc + 2 * k);
         bound[k] = far_bound(&B, F, binom, lx, ly, lm, hypot(x1 - B.xb, x2 - B.yb));

@@ -11,7 +11,14 @@ typedef struct {
     int32_t npix_side;   /* N_side; the map has N_side^2 pixels */
     double nrays;        /* N_rays: mean rays per pixel without lensing */
     double margin;       /* shot rectangle = margin x (L/|a|, L/|b|) per side */
+    int32_t ray_mode;    /* ORC_RAYS_LATTICE (0): ray (i, j) at the centre of lattice cell (i, j);
+                            ORC_RAYS_RANDOM (1): at a pseudo-random position in the 64 x 32-cell
+                            tile of the lattice that holds cell (i, j) (see ray_position) */
+    uint64_t ray_seed;   /* seed of the random positions (ORC_RAYS_RANDOM) */
 } orc_params;
+
+#define ORC_RAYS_LATTICE 0
+#define ORC_RAYS_RANDOM  1
 
 typedef struct {
     double pix, delta, width, height;

@@ -3,8 +3,9 @@
 The copy is built in a temporary directory on the CPU; the real oracle is
 never modified. This shows that the pins in test_oracle_pins.py constrain
 every term of the lens equation, the lattice, the binning and the layout,
-those in test_oracle_far.py the far-field series, and those in
-test_oracle_stats.py the K-S probability of the map statistics.
+those in test_oracle_far.py the far-field series, those in
+test_oracle_stats.py the K-S probability of the map statistics, and those in
+test_oracle_random_rays.py the random ray positions.
 """
 import os
 import shutil
@@ -67,8 +68,21 @@ STATS_MUTATIONS = [
      "kolmogorov((s + 0.12 + 0.11 * s) * d)"),
 ]
 
+# random rays (Sect. 2.3, step 2), pinned by test_oracle_random_rays.py
+RANDOM = "tests/test_oracle_random_rays.py"
+RANDOM_MUTATIONS = [
+    ("random stream shifted", "splitmix64_output(P->ray_seed, 2 * q + 1)", "splitmix64_output(P->ray_seed, 2 * q)"),
+    ("random draws shared by the two axes", "splitmix64_output(P->ray_seed, 2 * q + 2)",
+     "splitmix64_output(P->ray_seed, 2 * q + 1)"),
+    ("random fraction from the wrong bits", "2 * q + 1) >> 46)", "2 * q + 1) >> 40)"),
+    ("random tiles 64 rows high", "tj = j / 32;", "tj = j / 64;"),
+    ("partial tile taken as whole", "G->nx - 64 * ti < 64 ? G->nx - 64 * ti : 64", "64"),
+    ("random finaliser step dropped", "z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;", ""),
+    ("random counter per ray index only", "(uint64_t)j * (uint64_t)G->nx + (uint64_t)i", "(uint64_t)i"),
+]
+
 CASES = ([m + (PINS, "mm_oracle.c") for m in MUTATIONS] + [m + (FAR, "mm_oracle.c") for m in FAR_MUTATIONS]
-         + [m + (STATS, "stats.py") for m in STATS_MUTATIONS])
+         + [m + (STATS, "stats.py") for m in STATS_MUTATIONS] + [m + (RANDOM, "mm_oracle.c") for m in RANDOM_MUTATIONS])
 
 
 @pytest.mark.parametrize("name,old,new,pins,target", CASES, ids=[c[0] for c in CASES])
