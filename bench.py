@@ -474,6 +474,35 @@ def downstream_phase(mm, ctx, side=8192, fma_peak_per_s=None):
     return out
 
 
+def random_phase(mm, ctx, lh_fig1, exact_ms, sms):
+    """Random rays (MM_RAYS_RANDOM: the paper's GPU code shoots rays from pseudo-random positions,
+    Sect. 2.3 step 2) on the Fig. 1 map: the exact FP32 path at the same ray count as the lattice,
+    timed like the headline (device time of the shoot, best of 3), and the paper's comparison of the
+    random-ray map with the regular-grid map (Sect. 3.1: RMS of Delta m, K-S probability) made on the
+    device by mm_map_compare."""
+    p_lat = mm.params(**CFG1)
+    p_rnd = mm.params(**CFG1, ray_mode=mm.MM_RAYS_RANDOM, ray_seed=SEED)
+    best, m_rnd, st = 1e30, None, None
+    for _ in range(3):
+        if m_rnd:
+            mm.mm_release_map(ctx, m_rnd)
+        m_rnd = mm.mm_shoot(ctx, lh_fig1, p_rnd)
+        kms, _ = mm.mm_last_kernel_ms(ctx)
+        best = min(best, kms)
+    _, st = mm.mm_map_fetch(ctx, m_rnd, want_counts=False)
+    m_lat = mm.mm_shoot(ctx, lh_fig1, p_lat)
+    cmp = mm.mm_map_compare(ctx, m_lat, m_rnd)
+    for m in (m_lat, m_rnd):
+        mm.mm_release_map(ctx, m)
+    rate = st["interactions"] / (best * 1e-3)
+    return {"workload": WORKLOAD + ", rays at random positions (each uniform in its 64 x 32-cell tile)",
+            "ms": best, "interactions_per_s": rate, "vs_lattice_time": best / exact_ms,
+            "frac_nflop10": FLOP_PER_INTERACTION * rate / 1e12 / fp32_peak_tflops(sms),
+            "rays_in": st["rays_in"], "rays_shot": st["rays_shot"],
+            "vs_lattice_rms_delta_m": cmp["rms_dm"], "vs_lattice_ks_probability": cmp["ks_p"],
+            "excellent_agreement": bool(cmp["rms_dm"] < 0.2 and cmp["ks_p"] > 0.997)}
+
+
 def far_phase(mm, ctx, lh_fig1, exact_ms):
     """The far-field approximation MM_FAR32 (the tree code's idea, Sect. 2.1; the library's default
     order, ratio and block), timed outside the headline region: the Fig. 1 map against the
@@ -602,7 +631,7 @@ def profile_case(kind="fp32", window=4096):
     the Fig. 1 map (4096: 1.68e7 rays, 9.36e9 interactions), launched three times; kind
     "far" shoots it with the far-field approximation (MM_FAR32, default order, ratio and
     block; from 16384, 2048 blocks of 8 x 8 tiles, its work items are whole blocks as on
-    the full map)."""
+    the full map), kind "random" exactly with random rays (the window moved onto the tile grid)."""
     import paper_1005_5198_gb300 as mm
     import synth
     mm.build()
@@ -613,8 +642,13 @@ def profile_case(kind="fp32", window=4096):
     g = mm.mm_geometry_of(mm.params(**CFG1))
     c = g["nx"] // 2
     h = window // 2
-    p = mm.params(**CFG1, ray_rect=(c - h, c + h, c - h, c + h),
-                  precision=mm.MM_FAR32 if kind == "far" else mm.MM_FP32C)
+    i0, j0 = c - h, c - h
+    extra = {}
+    if kind == "random":                                 # random rays: a window on the 64 x 32 tile grid
+        i0, j0 = i0 // 64 * 64, j0 // 32 * 32
+        extra = dict(ray_mode=mm.MM_RAYS_RANDOM, ray_seed=SEED)
+    p = mm.params(**CFG1, ray_rect=(i0, i0 + window, j0, j0 + window),
+                  precision=mm.MM_FAR32 if kind == "far" else mm.MM_FP32C, **extra)
     for _ in range(3):
         m = mm.mm_shoot(ctx, lh, p)
         ms, _ = mm.mm_last_kernel_ms(ctx)
@@ -708,10 +742,11 @@ def main():
     ap.add_argument("--clocks-dir", default=None,
                     help="where the nvidia-smi samples of the timed region go (clocks_rank<N>.csv; default: the "
                          "system's temporary directory)")
-    ap.add_argument("--profile-case", nargs="?", const="fp32", choices=["fp32", "far", "downstream"],
+    ap.add_argument("--profile-case", nargs="?", const="fp32", choices=["fp32", "far", "random", "downstream"],
                     help="for ncu captures, then exit: shoot a window (--profile-window, 4096^2 rays) of the Fig. 1 map "
-                         "three times, exactly (fp32) or with the far-field approximation MM_FAR32 (far); or run the "
-                         "map statistics and light curves on two 8192^2 maps (downstream)")
+                         "three times, exactly (fp32), with the far-field approximation MM_FAR32 (far) or exactly with "
+                         "random rays (random); or run the map statistics and light curves on two 8192^2 maps "
+                         "(downstream)")
     ap.add_argument("--far-scaling", action="store_true",
                     help="time the far field on the Fig. 1 geometry for N* = 1e4 .. 1e8 and exit")
     ap.add_argument("--alu-rates", action="store_true",
@@ -830,6 +865,7 @@ def main():
     if not args.no_extras and world == 1:
         extra["config2_exact"] = config2_phase(mm, ctx, sms)
         extra["far_field"] = far_phase(mm, ctx, lh, sum(kern_ms) / len(kern_ms))
+        extra["random_rays"] = random_phase(mm, ctx, lh, sum(kern_ms) / len(kern_ms), sms)
         extra["downstream"] = downstream_phase(mm, ctx, fma_peak_per_s=lane_peak_per_s(sms))
         extra["batch"] = config3_phase(mm, ctx, sms)
         extra["batch_scaled"] = scaled_batch_phase(mm, ctx, sms)

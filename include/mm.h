@@ -128,7 +128,27 @@ typedef struct {
                                 E = (x / (1 - y))^P / (1 - x - y) + sum_{l<P} x^l sum_{k>=K} C(l+k, k) y^k */
     double   far_group_theta;/* MM_FAR32 grouping: separation theta, 0 < theta <= 0.9 (default 0.3) */
     int32_t  far_group_leaf; /* MM_FAR32 grouping: most lenses of a leaf cell, 1 .. 2^20 (default 64) */
+    int32_t  ray_mode;       /* MM_RAYS_LATTICE (0, default): ray (i, j) at the centre of lattice
+                                cell (i, j), the tree code's regular grid (Sect. 3.1).
+                                MM_RAYS_RANDOM (1): at a pseudo-random position, as the paper's GPU
+                                code shoots its rays (Sect. 2.3, step 2), so that a pixel receives
+                                N_rays rays on average only (Sect. 3.1). The same nx * ny rays are
+                                shot; ray (i, j) is uniform in the 64 x 32-cell tile of the lattice
+                                that holds cell (i, j): with q = j nx + i, u1 and u2 the top 18 bits
+                                of outputs 2q + 1 and 2q + 2 of SplitMix64(ray_seed) (output k of
+                                the generator seeded with s is mix(s + k 0x9E3779B97F4A7C15)), as
+                                fractions in [0, 1), Ti = floor(i / 64), Tj = floor(j / 32),
+                                wi = min(64, nx - 64 Ti), wj = min(32, ny - 32 Tj):
+                                x1 = (64 Ti + u1 wi - nx/2) Delta, x2 = (32 Tj + u2 wj - ny/2) Delta.
+                                For MM_FP32C and MM_FP64 through mm_shoot, mm_shoot_batch,
+                                mm_shoot_into and mm_debug_deflect; ray_rect must start on the
+                                64 x 32-ray tile grid (i0 % 64 == 0, j0 % 32 == 0). MM_FAR32,
+                                mm_submit and mm_shoot_noalloc take the lattice only (MM_EINVAL). */
+    uint64_t ray_seed;       /* MM_RAYS_RANDOM: seed of the ray positions (default 1) */
 } mm_params;
+
+#define MM_RAYS_LATTICE 0
+#define MM_RAYS_RANDOM  1
 
 /* Lens-field derivation used by mm_create_lenses when nstar < 0 or
  * disc_radius <= 0 (reading of Sect. 2, after Eq. nstar: lenses fill a

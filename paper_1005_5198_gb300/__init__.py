@@ -39,6 +39,7 @@ MM_OK, MM_EINVAL, MM_ENOMEM, MM_EBUSY, MM_ENOTFOUND = 0, -1, -2, -3, -4
 MM_ETIMEDOUT, MM_EDEVICE, MM_EAGAIN, MM_ECANCELED = -5, -6, -7, -8
 MM_FP32C, MM_FP64, MM_FAR32 = 0, 1, 2
 MM_MASS_UNIT, MM_MASS_LOGNORMAL = 0, 1
+MM_RAYS_LATTICE, MM_RAYS_RANDOM = 0, 1
 MM_PROFILE_GAUSSIAN, MM_PROFILE_DISC = 0, 1
 MM_MAP_MU, MM_MAP_DELTA_M = 0, 1
 MM_INJECT_NONE, MM_INJECT_COMPARE_NO_COPY, MM_INJECT_DISC_NO_COPY = 0, 1, 2
@@ -57,7 +58,7 @@ class mm_params(C.Structure):
                 ("mass_model", C.c_int32), ("mass_mu", C.c_double), ("mass_s", C.c_double), ("seed", C.c_uint64),
                 ("ray_rect", C.c_int64 * 4), ("far_order", C.c_int32), ("far_ratio", C.c_double),
                 ("far_block", C.c_int32), ("far_group_order", C.c_int32), ("far_group_theta", C.c_double),
-                ("far_group_leaf", C.c_int32)]
+                ("far_group_leaf", C.c_int32), ("ray_mode", C.c_int32), ("ray_seed", C.c_uint64)]
 
 
 class mm_stats(C.Structure):

@@ -21,7 +21,7 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["mm_fp64.cu", "mm_fp32_c1r8.cu", "mm_fp32_c2r4.cu", "mm_fp32_c2r8.cu", "mm_fp32_c2r4w.cu",
+CU_SOURCES = ["mm_fp64.cu", "mm_fp32_c1r8.cu", "mm_fp32_c2r4.cu", "mm_fp32_c2r8.cu", "mm_fp32_c2r4w.cu", "mm_fp32_random.cu",
               "mm_noalloc.cu", "mm_stats.cu", "mm_extended.cu", "mm_far.cu", "mm_tree.cu"]
 CPP_SOURCES = ["mm_host.cpp", "mm_serve.cpp"]
 HEADERS = ["mm_internal.h", "mm_ctx.h", "mm_device.cuh", "mm_fp32.cuh", "mm_far.h"]

@@ -85,6 +85,53 @@ __device__ __forceinline__ float ff_pixel(float uh, float ul, float sh, float sl
     return __fadd_rn(I, floorf(f));
 }
 
+// Float-float u = (ch + cl) * (n + f) + base for an exactly representable integer-valued n and an
+// exactly representable f (the offset of a random ray within its tile, in half cells).
+__device__ __forceinline__ void ff_axis_frac(float ch, float cl, float n, float f, float base, float &uh, float &ul)
+{
+    ff_axis(ch, cl, n, base, uh, ul);
+    const float ph = __fmul_rn(ch, f);
+    float pe = __fmaf_rn(ch, f, -ph);
+    pe = __fmaf_rn(cl, f, pe);
+    float s, e;
+    two_sum(uh, ph, s, e);
+    uh = s;
+    ul = __fadd_rn(ul, __fadd_rn(e, pe));
+}
+
+// Random rays (MapDesc::random_rays), as the paper's GPU code shoots them (Sect. 2.3, step 2):
+// output k >= 1 of SplitMix64 seeded with s (Steele, Lea & Flood, OOPSLA 2014) is
+// mix(s + k * 0x9E3779B97F4A7C15 mod 2^64), mix the generator's finaliser.
+__device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long s, unsigned long long k)
+{
+    unsigned long long z = s + k * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Random ray (gi, gj) lies at (fx, fy) cells from the corner of its 64 x 32-cell tile: fx = u1 wi,
+// fy = u2 wj, u1 and u2 the top 18 bits of outputs 2q + 1 and 2q + 2 (q = gj nx + gi) as fractions,
+// wi and wj the tile's width and height in cells (partial at the grid's far edges). Both are exact in
+// single precision (at most 24 significant bits).
+__device__ __forceinline__ void random_cell(const MapDesc &M, long long gi, long long gj, float &fx, float &fy)
+{
+    const unsigned long long q = (unsigned long long)gj * (unsigned long long)M.nx + (unsigned long long)gi;
+    const unsigned u1 = (unsigned)(splitmix64_at(M.ray_seed, 2 * q + 1) >> 46);
+    const unsigned u2 = (unsigned)(splitmix64_at(M.ray_seed, 2 * q + 2) >> 46);
+    const long long ti = gi / kTileX, tj = gj / kTileY;
+    const unsigned wi = (unsigned)min((long long)kTileX, M.nx - kTileX * ti);
+    const unsigned wj = (unsigned)min((long long)kTileY, M.ny - kTileY * tj);
+    fx = (float)(u1 * wi) * (1.0f / 262144.0f);
+    fy = (float)(u2 * wj) * (1.0f / 262144.0f);
+}
+
+// FP64 coordinate of a random ray along one axis: (t0 + f - n/2) delta, t0 its tile's first cell.
+__device__ __forceinline__ double random_coord(long long t0, float f, double half_n, double delta)
+{
+    return __dmul_rn(__dsub_rn(__dadd_rn((double)t0, (double)f), half_n), delta);
+}
+
 // Shared state of the persistent loop (first member of each kernel's shared block).
 struct LoopSmem {
     unsigned long long g;          // the next work item (fetched ahead) and its map

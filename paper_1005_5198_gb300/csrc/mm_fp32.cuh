@@ -108,7 +108,43 @@ __device__ __forceinline__ void pair_step(const float4 P, const float2 Mm, const
     }
 }
 
-template <class L, int C, int R, int SHARED4, int FOLD, bool MASS, bool DUMP, bool SPLIT>
+// The same for random rays: every ray has its own offsets (NRXr, NRYr: minus the ray's offset from the
+// tile centre, in both lanes), so neither difference is shared between rays.
+template <int C, int R, bool MASS, bool SHARED_RCP>
+__device__ __forceinline__ void pair_step_random(const float4 P, const float2 Mm, const float2 (&NRXr)[C][R],
+                                                 const float2 (&NRYr)[C][R], float2 (&AX)[C][R], float2 (&AY)[C][R])
+{
+    const float2 LX = make_float2(P.x, P.y);
+    const float2 LY = make_float2(P.z, P.w);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const float2 dX = __fadd2_rn(LX, NRXr[c][r]);
+            const float2 dY = __fadd2_rn(LY, NRYr[c][r]);
+            const float2 R2 = __ffma2_rn(dY, dY, __fmul2_rn(dX, dX));
+            float2 W;
+            if (SHARED_RCP) {
+                const float q = rcp_approx(__fmul_rn(R2.x, R2.y));
+                if (MASS) {
+                    W.x = __fmul_rn(q, __fmul_rn(R2.y, Mm.x));
+                    W.y = __fmul_rn(q, __fmul_rn(R2.x, Mm.y));
+                } else {
+                    W.x = __fmul_rn(q, R2.y);
+                    W.y = __fmul_rn(q, R2.x);
+                }
+            } else {
+                W.x = rcp_approx(R2.x);
+                W.y = rcp_approx(R2.y);
+                if (MASS) W = __fmul2_rn(W, Mm);
+            }
+            AX[c][r] = __ffma2_rn(W, dX, AX[c][r]);
+            AY[c][r] = __ffma2_rn(W, dY, AY[c][r]);
+        }
+    }
+}
+
+template <class L, int C, int R, int SHARED4, int FOLD, bool MASS, bool DUMP, bool SPLIT, bool RANDOM = false>
 __device__ void tile_fp32(const LaunchArgs &A, const MapDesc &M, unsigned long long tile, int seg, int item,
                           SmemFP32 &S, unsigned &cnt_in, unsigned &cnt_out)
 {
@@ -144,6 +180,22 @@ __device__ void tile_fp32(const LaunchArgs &A, const MapDesc &M, unsigned long l
         const float n = (float)(row0 + r) - 15.5f;
         const float ry = __fmaf_rn(n, dlt, __fmul_rn(n, dll));
         NRY[r] = make_float2(-ry, -ry);
+    }
+    // random rays: each ray's offset from the tile centre (a random ray stays inside its tile box)
+    float2 NRXr[RANDOM ? C : 1][RANDOM ? R : 1], NRYr[RANDOM ? C : 1][RANDOM ? R : 1];
+    if constexpr (RANDOM) {
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float fx, fy;
+                random_cell(M, ib + col0 + 32 * c, jb + row0 + r, fx, fy);
+                const float nx_ = fx - 32.0f, ny_ = fy - 16.0f;      // cells from the centre, exact
+                const float rx = __fmaf_rn(nx_, dlt, __fmul_rn(nx_, dll));
+                const float ry = __fmaf_rn(ny_, dlt, __fmul_rn(ny_, dll));
+                NRXr[c][r] = make_float2(-rx, -rx);
+                NRYr[c][r] = make_float2(-ry, -ry);
+            }
     }
     const float hx = 32.0f * dlt + kNearRadius;
     const float hy = 16.0f * dlt + kNearRadius;
@@ -208,8 +260,13 @@ __device__ void tile_fp32(const LaunchArgs &A, const MapDesc &M, unsigned long l
                 for (int u = 0; u < 4; ++u) {
                     const float4 P = S.pos[p + u];
                     const float2 Mm = MASS ? S.mass[p + u] : make_float2(1.f, 1.f);
-                    if (u < SHARED4) pair_step<C, R, MASS, true>(P, Mm, NRX, NRY, AX, AY);
-                    else pair_step<C, R, MASS, false>(P, Mm, NRX, NRY, AX, AY);
+                    if constexpr (RANDOM) {
+                        if (u < SHARED4) pair_step_random<C, R, MASS, true>(P, Mm, NRXr, NRYr, AX, AY);
+                        else pair_step_random<C, R, MASS, false>(P, Mm, NRXr, NRYr, AX, AY);
+                    } else {
+                        if (u < SHARED4) pair_step<C, R, MASS, true>(P, Mm, NRX, NRY, AX, AY);
+                        else pair_step<C, R, MASS, false>(P, Mm, NRX, NRY, AX, AY);
+                    }
                 }
             }
 #pragma unroll
@@ -246,10 +303,16 @@ __device__ void tile_fp32(const LaunchArgs &A, const MapDesc &M, unsigned long l
                     const double ml = MASS ? M.lm[g] : 1.0;
 #pragma unroll
                     for (int c = 0; c < C; ++c) {
-                        const double x1 = ((double)(ib + col0 + 32 * c) + 0.5 - M.half_nx) * M.delta;
+                        double x1 = ((double)(ib + col0 + 32 * c) + 0.5 - M.half_nx) * M.delta;
 #pragma unroll
                         for (int r = 0; r < R; ++r) {
-                            const double x2 = ((double)(jb + row0 + r) + 0.5 - M.half_ny) * M.delta;
+                            double x2 = ((double)(jb + row0 + r) + 0.5 - M.half_ny) * M.delta;
+                            if constexpr (RANDOM) {
+                                float fx, fy;
+                                random_cell(M, ib + col0 + 32 * c, jb + row0 + r, fx, fy);
+                                x1 = random_coord(ib, fx, M.half_nx, M.delta);
+                                x2 = random_coord(jb, fy, M.half_ny, M.delta);
+                            }
                             const double d1 = xl - x1, d2 = yl - x2;
                             const double r2 = d1 * d1 + d2 * d2;
                             if (r2 == 0.0) {
@@ -310,7 +373,14 @@ __device__ void tile_fp32(const LaunchArgs &A, const MapDesc &M, unsigned long l
         for (int r = 0; r < R; ++r) {
             const long long gj = jb + row0 + r;
             float uyh, uyl;
-            ff_axis(M.ay_h, M.ay_l, (float)(int)(2 * gj + 1 - M.ny), M.half_n, uyh, uyl);
+            if constexpr (RANDOM) {                       // u = A (2 t0 - n + 2 f) + N/2 per ray
+                float fx, fy;
+                random_cell(M, gi, gj, fx, fy);
+                ff_axis_frac(M.ax_h, M.ax_l, (float)(int)(2 * ib - M.nx), 2.0f * fx, M.half_n, uxh, uxl);
+                ff_axis_frac(M.ay_h, M.ay_l, (float)(int)(2 * jb - M.ny), 2.0f * fy, M.half_n, uyh, uyl);
+            } else {
+                ff_axis(M.ay_h, M.ay_l, (float)(int)(2 * gj + 1 - M.ny), M.half_n, uyh, uyl);
+            }
             float4 a;
             if (SPLIT && part) {                          // split tile: segments in order
                 const int local = (col0 + 32 * c) + kTileX * (row0 + r);
@@ -331,19 +401,24 @@ __device__ void tile_fp32(const LaunchArgs &A, const MapDesc &M, unsigned long l
     }
 }
 
-template <class L, int C, int R, int SHARED4, int FOLD, bool DUMP, bool SPLIT>
+template <class L, int C, int R, int SHARED4, int FOLD, bool DUMP, bool SPLIT, bool RANDOM = false>
 __device__ __forceinline__ void tile_fp32_any_mass(const LaunchArgs &A, const MapDesc &M, unsigned long long tile,
                                                    int seg, int item, SmemFP32 &S, unsigned &ci, unsigned &co)
 {
-    if (M.unit_mass) tile_fp32<L, C, R, SHARED4, FOLD, false, DUMP, SPLIT>(A, M, tile, seg, item, S, ci, co);
-    else tile_fp32<L, C, R, SHARED4, FOLD, true, DUMP, SPLIT>(A, M, tile, seg, item, S, ci, co);
+    if (M.unit_mass) tile_fp32<L, C, R, SHARED4, FOLD, false, DUMP, SPLIT, RANDOM>(A, M, tile, seg, item, S, ci, co);
+    else tile_fp32<L, C, R, SHARED4, FOLD, true, DUMP, SPLIT, RANDOM>(A, M, tile, seg, item, S, ci, co);
 }
 
-// Runtime variant of a map (shared-reciprocal pairs per 4, fold interval).
-template <class L, int C, int R, bool DUMP, bool SPLIT>
+// Runtime variant of a map (shared-reciprocal pairs per 4, fold interval). Random rays take the
+// default variant (3 shared pairs of 4, fold every 64 pairs) whatever the map's.
+template <class L, int C, int R, bool DUMP, bool SPLIT, bool RANDOM = false>
 __device__ void tile_fp32_dispatch(const LaunchArgs &A, const MapDesc &M, unsigned long long tile, int seg,
                                    int item, SmemFP32 &S, unsigned &ci, unsigned &co)
 {
+    if constexpr (RANDOM) {
+        tile_fp32_any_mass<L, C, R, 3, 64, DUMP, SPLIT, true>(A, M, tile, seg, item, S, ci, co);
+        return;
+    }
     switch (M.variant) {
     case 1: tile_fp32_any_mass<L, C, R, 3, 32, DUMP, SPLIT>(A, M, tile, seg, item, S, ci, co); break;
     case 2: tile_fp32_any_mass<L, C, R, 2, 64, DUMP, SPLIT>(A, M, tile, seg, item, S, ci, co); break;
@@ -354,27 +429,28 @@ __device__ void tile_fp32_dispatch(const LaunchArgs &A, const MapDesc &M, unsign
 
 // SPLIT: the launch contains maps whose tiles are split over lens segments (kept out of
 // the kernel used for unsplit launches, whose register allocation it would crowd).
-template <int C, int R, bool SREG, int MINB, bool DUMP, bool SPLIT>
+template <int C, int R, bool SREG, int MINB, bool DUMP, bool SPLIT, bool RANDOM = false>
 __global__ void __launch_bounds__(Layout<C, R, SREG, MINB>::NT, MINB) k_shoot_fp32(const LaunchArgs A)
 {
     using L = Layout<C, R, SREG, MINB>;
     __shared__ SmemFP32 S;
     persistent_loop<DUMP>(A, S.loop, [&](const MapDesc &M, unsigned long long tile, int seg, int item, unsigned &ci,
                                           unsigned &co) {
-        tile_fp32_dispatch<L, C, R, DUMP, SPLIT>(A, M, tile, seg, item, S, ci, co);
+        tile_fp32_dispatch<L, C, R, DUMP, SPLIT, RANDOM>(A, M, tile, seg, item, S, ci, co);
     });
 }
 
-template <int C, int R, bool SREG, int MINB>
+// RANDOM: the kernel for maps of random rays (every map of the launch has MapDesc::random_rays set).
+template <int C, int R, bool SREG, int MINB, bool RANDOM = false>
 cudaError_t launch_fp32_layout(const LaunchArgs &args, int grid, bool dump, bool split, cudaStream_t s)
 {
     constexpr int NT = Layout<C, R, SREG, MINB>::NT;
     if (split) {
-        if (dump) k_shoot_fp32<C, R, SREG, MINB, true, true><<<grid, NT, 0, s>>>(args);
-        else k_shoot_fp32<C, R, SREG, MINB, false, true><<<grid, NT, 0, s>>>(args);
+        if (dump) k_shoot_fp32<C, R, SREG, MINB, true, true, RANDOM><<<grid, NT, 0, s>>>(args);
+        else k_shoot_fp32<C, R, SREG, MINB, false, true, RANDOM><<<grid, NT, 0, s>>>(args);
     } else {
-        if (dump) k_shoot_fp32<C, R, SREG, MINB, true, false><<<grid, NT, 0, s>>>(args);
-        else k_shoot_fp32<C, R, SREG, MINB, false, false><<<grid, NT, 0, s>>>(args);
+        if (dump) k_shoot_fp32<C, R, SREG, MINB, true, false, RANDOM><<<grid, NT, 0, s>>>(args);
+        else k_shoot_fp32<C, R, SREG, MINB, false, false, RANDOM><<<grid, NT, 0, s>>>(args);
     }
     return cudaGetLastError();
 }

@@ -70,12 +70,19 @@ __device__ void tile_fp64(const LaunchArgs &A, const MapDesc &M, unsigned long l
     const long long ib = M.i0 + tx * kTileX;
     const long long jb = M.j0 + ty * kTileY;
     const long long gi = ib + iloc;
-    const double x1 = fp64_lattice(gi, M.half_nx, M.delta);
-    double x2[K64], a1[K64], a2[K64];
+    double x1[K64], x2[K64], a1[K64], a2[K64];
     bool on[K64];
 #pragma unroll
     for (int r = 0; r < K64; ++r) {
-        x2[r] = fp64_lattice(jb + jloc0 + r, M.half_ny, M.delta);
+        if (M.random_rays) {                          // random rays: each at its own place in the tile
+            float fx, fy;
+            random_cell(M, gi, jb + jloc0 + r, fx, fy);
+            x1[r] = random_coord(ib, fx, M.half_nx, M.delta);
+            x2[r] = random_coord(jb, fy, M.half_ny, M.delta);
+        } else {
+            x1[r] = fp64_lattice(gi, M.half_nx, M.delta);
+            x2[r] = fp64_lattice(jb + jloc0 + r, M.half_ny, M.delta);
+        }
         a1[r] = a2[r] = 0.0;
         on[r] = false;
     }
@@ -94,14 +101,14 @@ __device__ void tile_fp64(const LaunchArgs &A, const MapDesc &M, unsigned long l
             const double2 Lp = S.lens64[k];
             const double m = S.m64[k];
 #pragma unroll
-            for (int r = 0; r < K64; ++r) fp64_term(x1, x2[r], Lp, m, a1[r], a2[r], on[r]);
+            for (int r = 0; r < K64; ++r) fp64_term(x1[r], x2[r], Lp, m, a1[r], a2[r], on[r]);
         }
     }
     const bool col_ok = gi < M.i0 + M.ni;
 #pragma unroll
     for (int r = 0; r < K64; ++r) {
         const long long gj = jb + jloc0 + r;
-        const long long px = fp64_pixel(M, x1, x2[r], a1[r], a2[r]);
+        const long long px = fp64_pixel(M, x1[r], x2[r], a1[r], a2[r]);
         const bool valid = col_ok && gj < M.j0 + M.nj;
         const bool inside = valid && !on[r] && px >= 0;
         const unsigned pix = inside ? (unsigned)px : 0xffffffffu;
@@ -146,8 +153,14 @@ __global__ void __launch_bounds__(256) k_rays_fp64(const MapDesc M, const long l
     __shared__ double m64[kChunkPairs];
     const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const bool act = k < n;
-    const double x1 = act ? fp64_lattice(ri[k], M.half_nx, M.delta) : 0.0;
-    const double x2 = act ? fp64_lattice(rj[k], M.half_ny, M.delta) : 0.0;
+    double x1 = act ? fp64_lattice(ri[k], M.half_nx, M.delta) : 0.0;
+    double x2 = act ? fp64_lattice(rj[k], M.half_ny, M.delta) : 0.0;
+    if (act && M.random_rays) {                       // the ray's tile starts at cell (64 Ti, 32 Tj)
+        float fx, fy;
+        random_cell(M, ri[k], rj[k], fx, fy);
+        x1 = random_coord(ri[k] / kTileX * kTileX, fx, M.half_nx, M.delta);
+        x2 = random_coord(rj[k] / kTileY * kTileY, fy, M.half_ny, M.delta);
+    }
     double a1 = 0.0, a2 = 0.0;
     bool on = false;
     for (long long base = 0; base < M.nstar; base += kChunkPairs) {

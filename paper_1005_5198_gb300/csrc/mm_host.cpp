@@ -163,6 +163,12 @@ int compute_geo(const mm_params *p, Geo *g)
             return fail(MM_EINVAL, "ray_rect outside the ray grid");
         g->i0 = r[0]; g->ni = r[1] - r[0]; g->j0 = r[2]; g->nj = r[3] - r[2];
     }
+    if (p->ray_mode != MM_RAYS_LATTICE && p->ray_mode != MM_RAYS_RANDOM) return fail(MM_EINVAL, "bad ray_mode");
+    if (p->ray_mode == MM_RAYS_RANDOM) {
+        if (p->precision == MM_FAR32) return fail(MM_EINVAL, "random rays: MM_FP32C or MM_FP64 only");
+        if (g->i0 % kTileX != 0 || g->j0 % kTileY != 0)
+            return fail(MM_EINVAL, "random rays: ray_rect must start on the 64 x 32 tile grid");
+    }
     g->tiles_x = (g->ni + kTileX - 1) / kTileX;
     g->tiles_y = (g->nj + kTileY - 1) / kTileY;
     return MM_OK;
@@ -441,6 +447,8 @@ void fill_desc(const MapObj &m, MapDesc *d)
     d->seg_lenses = m.splits > 1 ? m.seg_lenses : std::max(m.lenses->n, 1LL);
     d->partial = m.partial;
     d->seg_done = m.seg_done;
+    d->random_rays = m.p.ray_mode == MM_RAYS_RANDOM ? 1 : 0;
+    d->ray_seed = m.p.ray_seed;
 }
 
 static int class_key(bool unit_mass, long long nstar)
@@ -551,8 +559,13 @@ static int launch_group(mm_ctx *ctx, std::vector<MapObj *> &group, int precision
     MM_CUDA(cudaMemsetAsync(sc->d_check, 0, sizeof(unsigned int), s));
 #endif
     const unsigned long long work = sc->h_hdr->total_work;
-    const long long cap =
-        (long long)ctx->sms * (far ? far_ctas_per_sm() : shoot_ctas_per_sm(fp64, ctx->layout));
+    // a launch holds maps of one ray mode (the batch groups them; the other callers launch one map)
+    const bool random = group[0]->p.ray_mode == MM_RAYS_RANDOM;
+    for (const MapObj *m : group)
+        if ((m->p.ray_mode == MM_RAYS_RANDOM) != random) return fail(MM_EINVAL, "a launch mixes ray modes");
+    const long long cap = (long long)ctx->sms * (far      ? far_ctas_per_sm()
+                                                 : random ? shoot_ctas_per_sm(fp64, kRandomLayout)
+                                                          : shoot_ctas_per_sm(fp64, ctx->layout));
     const int grid = (int)std::max(1LL, std::min((long long)work, cap));
     MM_CUDA(cudaEventRecord(ctx->ev0, s));
     unsigned long long far_items = 0;
@@ -574,6 +587,7 @@ static int launch_group(mm_ctx *ctx, std::vector<MapObj *> &group, int precision
                                      false, s));
         else if (far) MM_CUDA(launch_shoot_far(a, sc->d_far, 0, grid, true, s));
         else if (fp64) MM_CUDA(launch_shoot_fp64(a, grid, dump != nullptr, s));
+        else if (random) MM_CUDA(launch_shoot_fp32_random(a, grid, dump != nullptr, split, s));
         else MM_CUDA(launch_shoot_fp32(a, ctx->layout, grid, dump != nullptr, split, s));
     }
     MM_CUDA(cudaEventRecord(ctx->ev1, s));
@@ -774,6 +788,8 @@ int mm_params_default(mm_params *p)
     p->far_group_order = -1;
     p->far_group_theta = 0.3;
     p->far_group_leaf = 64;
+    p->ray_mode = MM_RAYS_LATTICE;
+    p->ray_seed = 1;
     return MM_OK;
 }
 
@@ -901,17 +917,20 @@ int mm_shoot_batch(mm_ctx *ctx, int32_t n, const mm_lenses *lenses, const mm_par
         if (rc) return rc;
     }
     ctx->last_launches = 0;
-    std::vector<MapObj *> groups[3];                  // by precision: MM_FP32C, MM_FP64, MM_FAR32
-    for (auto &o : objs) groups[o->p.precision].push_back(o.get());
-    float ms[3] = {0.f, 0.f, 0.f};
-    for (int k = 0; k < 3; ++k) {
-        int rc = launch_group(ctx, groups[k], k, nullptr, 0, ctx->stream, &ms[k]);
+    // one launch per precision (MM_FP32C, MM_FP64, MM_FAR32) and ray mode (lattice, random)
+    auto group_of = [](const MapObj &o) { return o.p.precision + (o.p.ray_mode == MM_RAYS_RANDOM ? 3 : 0); };
+    std::vector<MapObj *> groups[6];
+    for (auto &o : objs) groups[group_of(*o)].push_back(o.get());
+    float ms[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    ctx->last_ms = 0.0;
+    for (int k = 0; k < 6; ++k) {
+        int rc = launch_group(ctx, groups[k], k % 3, nullptr, 0, ctx->stream, &ms[k]);
         if (rc) return rc;
     }
-    ctx->last_ms = ms[0] + ms[1] + ms[2];
+    ctx->last_ms = ms[0] + ms[1] + ms[2] + ms[3] + ms[4] + ms[5];
     for (int k = 0; k < n; ++k) {
         auto &o = objs[(size_t)k];
-        o->seconds = ms[o->p.precision] * 1e-3;
+        o->seconds = ms[group_of(*o)] * 1e-3;
         MM_CUDA(cudaEventRecord(o->done, ctx->stream));
         maps_out[k] = register_map(ctx, o);
     }
@@ -928,7 +947,8 @@ int mm_shoot_into(mm_ctx *ctx, mm_lenses lenses, const mm_params *p, mm_map map)
     const double margin_p = p->shoot_margin > 0 ? p->shoot_margin : 1.5, margin_q = q.shoot_margin > 0 ? q.shoot_margin : 1.5;
     if (p->sigma != q.sigma || p->gamma != q.gamma || p->smooth_frac != q.smooth_frac || p->side_re != q.side_re ||
         p->npix_side != q.npix_side || p->nrays_per_pix != q.nrays_per_pix || margin_p != margin_q ||
-        p->precision != q.precision ||
+        p->precision != q.precision || p->ray_mode != q.ray_mode ||
+        (p->ray_mode == MM_RAYS_RANDOM && p->ray_seed != q.ray_seed) ||
         (p->precision == MM_FAR32 &&
          (p->far_order != q.far_order || p->far_ratio != q.far_ratio || p->far_block != q.far_block ||
           p->far_group_order != q.far_group_order || p->far_group_theta != q.far_group_theta ||

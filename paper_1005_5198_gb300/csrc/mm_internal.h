@@ -70,6 +70,10 @@ struct MapDesc {
     // tile the number of segments finished
     float4 *partial;
     unsigned int *seg_done;
+    // ray positions: 0 the lattice's cell centres, 1 random in the ray's 64 x 32-cell tile
+    // (SplitMix64(ray_seed) outputs 2q + 1, 2q + 2 of ray q = j nx + i)
+    int random_rays;
+    unsigned long long ray_seed;
 };
 
 // Lens segments per tile of a map: split the lens set when a map has too few tiles to
@@ -123,6 +127,9 @@ cudaError_t launch_rays_fp64(const MapDesc &M, const long long *ri, const long l
 // thread layout `layout`; grid = number of CTAs (persistent); split: some map of the
 // launch has lens-split tiles.
 cudaError_t launch_shoot_fp32(const LaunchArgs &args, int layout, int grid, bool dump, bool split, cudaStream_t s);
+// The FP32 kernel for maps of random rays (MapDesc::random_rays), in thread layout kRandomLayout.
+constexpr int kRandomLayout = 3;
+cudaError_t launch_shoot_fp32_random(const LaunchArgs &args, int grid, bool dump, bool split, cudaStream_t s);
 // Plain FP64 shoot (every map precision MM_FP64).
 cudaError_t launch_shoot_fp64(const LaunchArgs &args, int grid, bool dump, cudaStream_t s);
 // CTAs per SM the kernels are compiled for (FP32: per thread layout).

@@ -79,6 +79,7 @@ extern "C" int mm_shoot_noalloc(const double *x, const double *y, const double *
     int rc = compute_geo(p, &g);
     if (rc) return rc;
     if (p->precision != MM_FP32C) return fail(MM_EINVAL, "mm_shoot_noalloc runs the FP32 kernel only (precision MM_FP32C)");
+    if (p->ray_mode != MM_RAYS_LATTICE) return fail(MM_EINVAL, "mm_shoot_noalloc shoots lattice rays only");
     if (nstar < 0) return fail(MM_EINVAL, "nstar must be >= 0");
     if (nstar > kNoAllocMaxLenses)
         return fail(MM_EINVAL, "nstar exceeds the no-alloc scratch capacity of 131072 lenses");

@@ -618,6 +618,7 @@ int mm_submit(mm_ctx *ctx, mm_lenses lenses, const mm_params *p, mm_req *out)
     auto r = std::make_shared<Request>();
     int rc = compute_geo(p, &r->g);
     if (rc) return rc;
+    if (p->ray_mode != MM_RAYS_LATTICE) return fail(MM_EINVAL, "mm_submit serves lattice rays only");
     r->p = *p;
     if (lenses) {
         std::lock_guard<std::mutex> lk(ctx->mu);

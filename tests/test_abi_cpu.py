@@ -49,6 +49,10 @@ def test_init_without_gpu_fails_cleanly():
     dict(sigma=0.4, gamma=0.0, precision=7), dict(sigma=0.4, gamma=0.0, mass_model=9),
     dict(sigma=0.4, gamma=0.0, ray_rect=(0, 10 ** 9, 0, 10)),
     dict(sigma=0.4, gamma=0.0, side=20.0, npix_side=8, nrays=1e12),
+    dict(sigma=0.4, gamma=0.0, ray_mode=2),
+    dict(sigma=0.4, gamma=0.0, ray_mode=1, precision=2),                      # random rays: not MM_FAR32
+    dict(sigma=0.4, gamma=0.0, ray_mode=1, ray_rect=(10, 100, 0, 64)),        # random rays: tile-aligned parts
+    dict(sigma=0.4, gamma=0.0, ray_mode=1, ray_rect=(64, 100, 16, 64)),
 ])
 def test_invalid_parameters_rejected(bad):
     kw = dict(side=4.0, npix_side=64, nrays=100.0)
@@ -56,6 +60,12 @@ def test_invalid_parameters_rejected(bad):
     with pytest.raises(mm.MMError) as e:
         mm.mm_geometry_of(mm.params(**kw))
     assert e.value.code == mm.MM_EINVAL
+
+
+def test_random_rays_accepted_on_the_tile_grid():
+    for kw in (dict(ray_mode=1), dict(ray_mode=1, precision=1), dict(ray_mode=1, ray_rect=(64, 100, 32, 64))):
+        g = mm.mm_geometry_of(mm.params(sigma=0.4, gamma=0.0, side=4.0, npix_side=64, nrays=100.0, **kw))
+        assert g["nx"] > 0
 
 
 def test_geometry_matches_oracle_on_random_maps():
