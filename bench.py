@@ -419,14 +419,17 @@ def hbm_peak_gbs():
 
 
 def downstream_phase(mm, ctx, side=8192, fma_peak_per_s=None):
-    """The rows after the map: the map statistics of Sect. 3.1 (mm_map_compare: RMS of Delta m and the
-    K-S test) and an extended source's light curve (mm_map_lightcurve: the map convolved with a Gaussian
-    or disc profile on the device, then sampled along a track), on two side^2 maps (256 MiB of counts
-    each at 8192^2, more than L2) of the Fig. 1 field at N_rays = 10, shot with the far field (default
-    order and order 14). Each call returns with its result on the host; times are host clocks around
-    it (best of 3 after one warm-up). Algorithmic bytes: compare reads both maps once (8 B/pixel); the
-    Gaussian's two separable passes read and write a map each (16 B/pixel); the disc reads the counts
-    and writes the convolved map (8 B/pixel)."""
+    """The rows after the map, on two side^2 maps (256 MiB of counts each at 8192^2, more than L2) of
+    the Fig. 1 field at N_rays = 10, shot with the far field (default order and order 14):
+    - the map statistics of Sect. 3.1 (mm_map_compare: RMS of Delta m and the K-S test), host clock
+      around the call; algorithmic bytes: both maps read once (8 B/pixel);
+    - the extended-source magnification maps (mm_map_convolve with a Gaussian or disc profile):
+      device time of the convolution kernels (CUDA events, mm_last_kernel_ms); algorithmic bytes: the
+      Gaussian's two separable passes read and write a map each (16 B/pixel), the disc reads the
+      counts and writes the convolved map (8 B/pixel);
+    - light curves along a track (mm_map_lightcurve, 1000 samples), which convolve only the four
+      pixels around each sample: host clock around the call and the device time of its kernel.
+    Each is the best of 3 after one warm-up."""
     peak, peak_src = hbm_peak_gbs()
     base = dict(sigma=0.4, gamma=0.0, smooth_frac=0.0, side=20.0, npix_side=side, nrays=10.0, seed=SEED)
     pa = mm.params(**base, precision=mm.MM_FAR32)
@@ -437,37 +440,47 @@ def downstream_phase(mm, ctx, side=8192, fma_peak_per_s=None):
     pix_re = 20.0 / side
 
     def timed(fn):
+        """Best host time and best device time (mm_last_kernel_ms) of fn over 3 calls after a warm-up."""
         fn()
-        best, res = 1e30, None
+        best, best_dev, res = 1e30, 1e30, None
         for _ in range(3):
             t0 = time.perf_counter()
             res = fn()
             best = min(best, time.perf_counter() - t0)
-        return best, res
+            best_dev = min(best_dev, mm.mm_last_kernel_ms(ctx)[0] * 1e-3)
+        return best, best_dev, res
 
     def line(sec, nbytes, extra):
         gbs = nbytes / sec / 1e9
         return dict(extra, ms=sec * 1e3, pixels_per_s=npix / sec, algorithmic_bytes=nbytes, achieved_gbs=gbs,
                     hbm_frac=gbs / peak)
 
-    t_cmp, st = timed(lambda: mm.mm_map_compare(ctx, ma, mb))
+    t_cmp, _, st = timed(lambda: mm.mm_map_compare(ctx, ma, mb))
     track = ((-8.0, -3.0), (8.0, 3.0))
     g_size, d_size = 0.02, 0.02
-    t_g, _ = timed(lambda: mm.mm_map_lightcurve(ctx, ma, mm.MM_PROFILE_GAUSSIAN, g_size, *track, 1000))
-    t_d, _ = timed(lambda: mm.mm_map_lightcurve(ctx, ma, mm.MM_PROFILE_DISC, d_size, *track, 1000))
     h = int(np.ceil(4.0 * g_size / pix_re))
     hd = int(d_size / pix_re)
+    _, k_cg, _ = timed(lambda: mm.mm_map_convolve(ctx, ma, mm.MM_PROFILE_GAUSSIAN, g_size))
+    _, k_cd, _ = timed(lambda: mm.mm_map_convolve(ctx, ma, mm.MM_PROFILE_DISC, d_size))
+    t_g, k_g, _ = timed(lambda: mm.mm_map_lightcurve(ctx, ma, mm.MM_PROFILE_GAUSSIAN, g_size, *track, 1000))
+    t_d, k_d, _ = timed(lambda: mm.mm_map_lightcurve(ctx, ma, mm.MM_PROFILE_DISC, d_size, *track, 1000))
+    route = "the four pixels around each sample, one CTA per sample (less work than the whole map)"
     out = {"workload": f"two {side}^2 maps of the Fig. 1 field (N_rays = 10, far field), {npix:.3e} pixels each",
            "hbm_peak_gbs": peak, "hbm_peak_source": peak_src,
            "compare": line(t_cmp, 8 * npix, {"rms_dm": st["rms_dm"], "ks_p": st["ks_p"]}),
-           "lightcurve_gaussian": line(t_g, 16 * npix, {"size_re": g_size, "taps_per_pass": 2 * h + 1,
-                                                        "points": 1000,
+           "convolve_gaussian": line(k_cg, 16 * npix, {"size_re": g_size, "taps_per_pass": 2 * h + 1,
+                                                        "time": "device time of the two passes",
                                                         # the two passes' FMAs (one per tap and output)
                                                         # against the FP32 FMA peak: this kernel pair is
                                                         # bound by arithmetic before memory
-                                                        "fma_frac": 2 * (2 * h + 1) * npix / t_g
+                                                        "fma_frac": 2 * (2 * h + 1) * npix / k_cg
                                                                     / (fma_peak_per_s or 1.0)}),
-           "lightcurve_disc": line(t_d, 8 * npix, {"size_re": d_size, "radius_pixels": hd, "points": 1000})}
+           "convolve_disc": line(k_cd, 8 * npix, {"size_re": d_size, "radius_pixels": hd,
+                                                  "time": "device time of the disc kernel"}),
+           "lightcurve_gaussian": {"size_re": g_size, "taps_per_pass": 2 * h + 1, "points": 1000, "route": route,
+                                   "ms": t_g * 1e3, "kernel_ms": k_g * 1e3},
+           "lightcurve_disc": {"size_re": d_size, "radius_pixels": hd, "points": 1000, "route": route,
+                               "ms": t_d * 1e3, "kernel_ms": k_d * 1e3}}
     mm.mm_release_map(ctx, ma)
     mm.mm_release_map(ctx, mb)
     mm.mm_release_lenses(ctx, lh)

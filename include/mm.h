@@ -424,7 +424,12 @@ int mm_map_convolve(mm_ctx *ctx, mm_map map, int32_t profile, double size_re, fl
  * y2_start) to (y1_end, y2_end) (source-plane Einstein radii, origin at the map
  * centre): n_points samples, evenly spaced including both ends, of the convolved
  * map, bilinearly interpolated between pixel centres (-L/2 + (I + 1/2) p);
- * host_mu[k] is NaN where a sample needs a pixel without value. */
+ * host_mu[k] is NaN where a sample needs a pixel without value. When it is less
+ * work, only the four pixels around each sample are convolved (one CTA per
+ * sample) instead of the whole map; either way every pixel, and so every sample,
+ * equals what sampling mm_map_convolve's map gives, bit for bit. Errors:
+ * MM_EINVAL (bad profile or size, profile wider than the map, n_points <= 0,
+ * NULL host_mu), MM_ENOTFOUND, MM_ENOMEM, MM_EDEVICE. */
 int mm_map_lightcurve(mm_ctx *ctx, mm_map map, int32_t profile, double size_re, double y1_start, double y2_start,
                       double y1_end, double y2_end, int64_t n_points, double *host_mu);
 
@@ -518,9 +523,9 @@ int mm_debug_inject(mm_ctx *ctx, int32_t kind);
 int mm_shoot_noalloc(const double *x, const double *y, const double *m, int64_t nstar, const mm_params *p,
                      uint32_t *counts, uint64_t *totals, void *cuda_stream);
 
-/* Device time (ms) of the last kernel launch of the most recent shoot, batch
- * or debug call, measured with CUDA events on the context's stream, and the
- * number of kernels that call launched. */
+/* Device time (ms) of the kernels of the most recent shoot, batch, debug,
+ * convolution or light-curve call, measured with CUDA events on the context's
+ * stream around them, and the number of kernels in that time. */
 int mm_last_kernel_ms(mm_ctx *ctx, double *ms, int32_t *launches);
 
 const char *mm_strerror(int code);

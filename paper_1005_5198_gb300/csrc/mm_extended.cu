@@ -508,27 +508,203 @@ struct DiscKernels {
 static_assert(kDiscMaxH == 15, "the kernel table lists H = 0 .. 15");
 using DiscTable = DiscKernels<0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15>;
 
+// Sample k of a light curve: t = k / (npts - 1) along the track, the pixel (i, j) below and left of
+// the sample (pixel centres at -L/2 + (I + 1/2) p) and the bilinear weights (a, b). False where the
+// sample needs a pixel outside the map (tested in FP64, before any conversion to int).
+__device__ __forceinline__ bool lc_sample(long long k, long long npts, int n, double half_side, double pix, double y1a,
+                                          double y2a, double y1b, double y2b, int &i, int &j, double &a, double &b)
+{
+    const double t = npts > 1 ? (double)k / (double)(npts - 1) : 0.0;
+    const double y1 = y1a + t * (y1b - y1a), y2 = y2a + t * (y2b - y2a);
+    const double u = (y1 + half_side) / pix - 0.5, v = (y2 + half_side) / pix - 0.5;
+    const double fu = floor(u), fv = floor(v);
+    if (!(u >= 0.0 && v >= 0.0) || !(fu + 1.0 < (double)n) || !(fv + 1.0 < (double)n)) return false;
+    i = (int)fu;
+    j = (int)fv;
+    a = u - fu;
+    b = v - fv;
+    return true;
+}
+
+// The bilinear interpolation of the four pixels (i, j), (i + 1, j), (i, j + 1), (i + 1, j + 1); one
+// function for every light-curve kernel, so that equal pixels give equal samples.
+__device__ __forceinline__ double lc_bilinear(double a, double b, float f00, float f10, float f01, float f11)
+{
+    return (1 - a) * (1 - b) * f00 + a * (1 - b) * f10 + (1 - a) * b * f01 + a * b * f11;
+}
+
 // Bilinear samples of the convolved map at source positions (Einstein radii).
 __global__ void k_track(const float *f, int n, double half_side, double pix, double y1a, double y2a, double y1b,
                         double y2b, long long npts, double *mu)
 {
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < npts; k += (long long)gridDim.x * blockDim.x) {
-        const double t = npts > 1 ? (double)k / (double)(npts - 1) : 0.0;
-        const double y1 = y1a + t * (y1b - y1a), y2 = y2a + t * (y2b - y2a);
-        const double u = (y1 + half_side) / pix - 0.5, v = (y2 + half_side) / pix - 0.5;
-        const double fu = floor(u), fv = floor(v);
-        const int i = (int)fu, j = (int)fv;
-        if (!(u >= 0.0 && v >= 0.0) || i + 1 >= n || j + 1 >= n) {
+        int i, j;
+        double a, b;
+        if (!lc_sample(k, npts, n, half_side, pix, y1a, y2a, y1b, y2b, i, j, a, b)) {
             mu[k] = nan("");
             continue;
         }
-        const double a = u - fu, b = v - fv;
         const long long q = (long long)j * n + i;
-        mu[k] = (1 - a) * (1 - b) * f[q] + a * (1 - b) * f[q + 1] + (1 - a) * b * f[q + n] + a * b * f[q + n + 1];
+        mu[k] = lc_bilinear(a, b, f[q], f[q + 1], f[q + n], f[q + n + 1]);
     }
 }
 
-// Convolve map M into the device float buffer dst (n^2). Returns MM_OK or an error.
+// ---- light curves without the whole convolved map ----
+// A light curve needs the convolved map at four pixels per sample only. When that is less work than
+// convolving the map, a CTA per sample computes its four pixels directly, with the same arithmetic as
+// the passes above, so that every pixel, and hence every sample, equals what sampling the convolved
+// map gives, bit for bit.
+
+constexpr int kLcChunk = 256;                           // column sums per row and round (Gaussian)
+
+// Gaussian: for rows j and j + 1 the column sums V[r][x] = sum_k g[k] mu[j + r + k - h][x] (FMA chain in
+// tap order, as the column pass) over the columns the row sums need, in rounds of kLcChunk + 1
+// columns; then thread o < 4 extends the row sum of pixel (i + (o & 1), j + (o >> 1)) over the round's
+// taps (FMA chain in tap order, as the row pass). A pixel whose support leaves the map is NaN.
+__global__ void __launch_bounds__(256) k_track_gauss(const unsigned *cin, int n, const float *g, int h, float inv_nrays,
+                                                     double half_side, double pix, double y1a, double y2a, double y1b,
+                                                     double y2b, long long npts, double *mu)
+{
+    __shared__ float V[2][kLcChunk + 1];
+    __shared__ float f[4];
+    const int T = 2 * h + 1, o = threadIdx.x;
+    for (long long k = blockIdx.x; k < npts; k += gridDim.x) {
+        int i, j;
+        double a, b;
+        if (!lc_sample(k, npts, n, half_side, pix, y1a, y2a, y1b, y2b, i, j, a, b)) {   // the same for the CTA
+            if (o == 0) mu[k] = nan("");
+            continue;
+        }
+        const int I = i + (o & 1), J = j + (o >> 1);
+        const bool valid = o < 4 && I - h >= 0 && I + h < n && J - h >= 0 && J + h < n;
+        float s = 0.f;
+        for (int c0 = 0; c0 < T; c0 += kLcChunk) {
+            for (int q = o; q < 2 * (kLcChunk + 1); q += blockDim.x) {
+                const int r = q / (kLcChunk + 1), t = q - r * (kLcChunk + 1);
+                const int x = i - h + c0 + t, row = j + r;
+                float v = 0.f;
+                if (c0 + t <= T && x >= 0 && x < n && row - h >= 0 && row + h < n) {
+                    const unsigned *col = cin + (long long)(row - h) * n + x;
+#pragma unroll 8
+                    for (int kk = 0; kk < T; ++kk) v = fmaf(g[kk], __fmul_rn((float)col[(long long)kk * n], inv_nrays), v);
+                }
+                V[r][t] = v;
+            }
+            __syncthreads();
+            if (valid) {
+                const int end = min(T, c0 + kLcChunk);
+                for (int kk = c0; kk < end; ++kk) s = fmaf(g[kk], V[o >> 1][(o & 1) + kk - c0], s);
+            }
+            __syncthreads();
+        }
+        if (o < 4) f[o] = valid ? s : __int_as_float(0x7fc00000);
+        __syncthreads();
+        if (o == 0) mu[k] = lc_bilinear(a, b, f[0], f[1], f[2], f[3]);
+        __syncthreads();
+    }
+}
+
+// Disc: the integer totals of the four pixels' discs (warp w takes staged rows w, w + 8, ... of rows
+// j - H .. j + 1 + H, its lanes the columns), reduced exactly and converted to float once, as the
+// disc kernels do. span[dj + H] = half-width of the disc on row offset dj.
+__global__ void __launch_bounds__(256) k_track_disc(const unsigned *cin, int n, const int *span, int H, float scale,
+                                                    double half_side, double pix, double y1a, double y2a, double y1b,
+                                                    double y2b, long long npts, double *mu)
+{
+    __shared__ unsigned long long tot[8][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (long long k = blockIdx.x; k < npts; k += gridDim.x) {
+        int i, j;
+        double a, b;
+        if (!lc_sample(k, npts, n, half_side, pix, y1a, y2a, y1b, y2b, i, j, a, b)) {
+            if (threadIdx.x == 0) mu[k] = nan("");
+            continue;
+        }
+        unsigned long long p[4] = {0ull, 0ull, 0ull, 0ull};   // pixels (i, j), (i + 1, j), (i, j + 1), (i + 1, j + 1)
+        for (int rr = warp; rr < 2 * H + 2; rr += 8) {
+            const int row = j - H + rr;
+            if (row < 0 || row >= n) continue;
+            const int d0 = rr - H, d1 = rr - H - 1;          // row offset from j and from j + 1
+            const int w0 = d0 <= H ? span[d0 + H] : -1, w1 = d1 >= -H ? span[d1 + H] : -1;
+            const int wm = max(w0, w1);
+            const unsigned *const r = cin + (long long)row * n;
+            for (int dx = -wm + lane; dx <= wm + 1; dx += 32) {
+                const int x = i + dx;
+                if (x < 0 || x >= n) continue;
+                const unsigned long long c = r[x];
+                if (dx >= -w0 && dx <= w0) p[0] += c;
+                if (dx - 1 >= -w0 && dx - 1 <= w0) p[1] += c;
+                if (dx >= -w1 && dx <= w1) p[2] += c;
+                if (dx - 1 >= -w1 && dx - 1 <= w1) p[3] += c;
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) p[e] += __shfl_down_sync(0xffffffffu, p[e], off);
+            if (lane == 0) tot[warp][e] = p[e];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float fv[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                unsigned long long t = 0;
+                for (int w = 0; w < 8; ++w) t += tot[w][e];
+                const int I = i + (e & 1), J = j + (e >> 1);
+                fv[e] = (I - H >= 0 && I + H < n && J - H >= 0 && J + H < n) ? (float)t * scale
+                                                                            : __int_as_float(0x7fc00000);
+            }
+            mu[k] = lc_bilinear(a, b, fv[0], fv[1], fv[2], fv[3]);
+        }
+        __syncthreads();
+    }
+}
+
+// The Gaussian's normalised taps g[0 .. 2h] (FP64, rounded to float once), h = ceil(4 s / p).
+std::vector<float> gauss_taps(double size_re, double pix, int *h_out)
+{
+    const int h = (int)std::ceil(4.0 * size_re / pix);
+    std::vector<double> gd(2 * h + 1);
+    double tot = 0.0;
+    for (int k = -h; k <= h; ++k) tot += gd[k + h] = std::exp(-(k * pix) * (k * pix) / (2.0 * size_re * size_re));
+    std::vector<float> g(gd.size());
+    for (size_t k = 0; k < gd.size(); ++k) g[k] = (float)(gd[k] / tot);
+    *h_out = h;
+    return g;
+}
+
+// The disc's row half-widths span[dj + H], H = floor(R / p), and its pixel count.
+std::vector<int> disc_spans(double size_re, double pix, int *H_out, long long *taps_out)
+{
+    const double rp = size_re / pix;
+    const int H = (int)std::floor(rp);
+    std::vector<int> span(2 * H + 1);
+    long long taps = 0;
+    for (int dj = -H; dj <= H; ++dj) {
+        int w = 0;
+        while ((double)(w + 1) * (w + 1) + (double)dj * dj <= rp * rp) ++w;
+        span[dj + H] = w;
+        taps += 2 * w + 1;
+    }
+    *H_out = H;
+    *taps_out = taps;
+    return span;
+}
+
+// The device time between ctx->ev0 and ctx->ev1 (both recorded and complete) becomes the context's
+// last kernel time, over `launches` kernels.
+void note_kernel_time(mm_ctx *ctx, int launches)
+{
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1) == cudaSuccess) {
+        ctx->last_ms = ms;
+        ctx->last_launches = launches;
+    }
+}
+
+// Convolve map M into the device float buffer dst (n^2) on stream s and wait for it; the convolution
+// kernels are bracketed by the context's events (note_kernel_time). Returns MM_OK or an error.
 int convolve(mm_ctx *ctx, const MapObj &M, int profile, double size_re, float *dst, float *tmp, cudaStream_t s)
 {
     const int n = M.p.npix_side;
@@ -537,12 +713,8 @@ int convolve(mm_ctx *ctx, const MapObj &M, int profile, double size_re, float *d
     const int grid = std::max(1, std::min(8 * ctx->sms, (int)(((long long)n * n + 255) / 256)));
     cudaError_t e;
     if (profile == MM_PROFILE_GAUSSIAN) {
-        const int h = (int)std::ceil(4.0 * size_re / pix);
-        std::vector<double> gd(2 * h + 1);
-        double tot = 0.0;
-        for (int k = -h; k <= h; ++k) tot += gd[k + h] = std::exp(-(k * pix) * (k * pix) / (2.0 * size_re * size_re));
-        std::vector<float> g(gd.size());
-        for (size_t k = 0; k < gd.size(); ++k) g[k] = (float)(gd[k] / tot);
+        int h = 0;
+        const std::vector<float> g = gauss_taps(size_re, pix, &h);
         float *dg = nullptr;
         int rc = ctx->arena.alloc(g.size() * sizeof(float), (void **)&dg);
         if (rc) return rc;
@@ -562,29 +734,27 @@ int convolve(mm_ctx *ctx, const MapObj &M, int profile, double size_re, float *d
                         cudaSuccess &&
                     (e = cudaFuncSetAttribute(f2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGaussSmemMax)) ==
                         cudaSuccess) {
+                    cudaEventRecord(ctx->ev0, s);
                     k_gauss_vt<true><<<resident(f1), 256, smem, s>>>(M.counts, tmp, n, dg, h, inv_nrays);
                     k_gauss_vt<false><<<resident(f2), 256, smem, s>>>(tmp, dst, n, dg, h, 1.0f);
+                    cudaEventRecord(ctx->ev1, s);
                 }
             } else {                                           // the same sums: columns, then rows
+                cudaEventRecord(ctx->ev0, s);
                 k_gauss_pass<true><<<grid, 256, 0, s>>>(M.counts, nullptr, tmp, n, dg, h, 1, inv_nrays);
                 k_gauss_pass<false><<<grid, 256, 0, s>>>(nullptr, tmp, dst, n, dg, h, 0, 1.0f);
+                cudaEventRecord(ctx->ev1, s);
             }
             if (e == cudaSuccess) e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e == cudaSuccess) note_kernel_time(ctx, 2);
         }
         ctx->arena.free(dg);
         return e == cudaSuccess ? MM_OK : cuda_fail(e, "gaussian convolution");
     }
-    const double rp = size_re / pix;
-    const int H = (int)std::floor(rp);
-    std::vector<int> span(2 * H + 1);
+    int H = 0;
     long long taps = 0;
-    for (int dj = -H; dj <= H; ++dj) {
-        int w = 0;
-        while ((double)(w + 1) * (w + 1) + (double)dj * dj <= rp * rp) ++w;
-        span[dj + H] = w;
-        taps += 2 * w + 1;
-    }
+    const std::vector<int> span = disc_spans(size_re, pix, &H, &taps);
     const float scale = (float)(1.0 / ((double)taps * M.p.nrays_per_pix));
     if (H <= kDiscMaxH) {                                  // tiled: the kernel compiled for this radius
         DiscSpans sp{};
@@ -601,10 +771,13 @@ int convolve(mm_ctx *ctx, const MapObj &M, int profile, double size_re, float *d
         if (rc) return rc;
         const int withhold = take_injection(ctx, MM_INJECT_DISC_NO_COPY) ? 1 : 0;
         if (e == cudaSuccess) e = cudaMemsetAsync(dfault, 0, sizeof(unsigned), s);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev0, s);
         if (e == cudaSuccess) fn<<<dgrid, 256, smem, s>>>(M.counts, dst, n, sp, scale, dfault, withhold);
         if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev1, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&hfault, dfault, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) note_kernel_time(ctx, 1);
         ctx->arena.free(dfault);
         if (e != cudaSuccess) return cuda_fail(e, "disc convolution");
         return hfault ? fail(MM_EDEVICE, "k_disc_tiled: a copy into shared memory did not complete") : MM_OK;
@@ -613,9 +786,12 @@ int convolve(mm_ctx *ctx, const MapObj &M, int profile, double size_re, float *d
     int rc = ctx->arena.alloc(span.size() * sizeof(int), (void **)&ds);
     if (rc) return rc;
     if ((e = cudaMemcpyAsync(ds, span.data(), span.size() * sizeof(int), cudaMemcpyHostToDevice, s)) == cudaSuccess) {
+        cudaEventRecord(ctx->ev0, s);
         k_disc<<<grid, 256, 0, s>>>(M.counts, dst, n, ds, H, scale);
+        cudaEventRecord(ctx->ev1, s);
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) note_kernel_time(ctx, 1);
     }
     ctx->arena.free(ds);
     return e == cudaSuccess ? MM_OK : cuda_fail(e, "disc convolution");
@@ -675,24 +851,76 @@ extern "C" int mm_map_lightcurve(mm_ctx *ctx, mm_map map, int32_t profile, doubl
     int rc = prepare(ctx, map, profile, size_re, &M);
     if (rc) return rc;
     if (n_points <= 0 || !host_mu) return fail(MM_EINVAL, "need n_points > 0 and an output buffer");
-    const size_t npix = (size_t)M->p.npix_side * M->p.npix_side;
-    float *buf = nullptr;
+    const int n = M->p.npix_side;
+    const size_t npix = (size_t)n * n;
+    const double pix = M->g.pix, half = 0.5 * M->p.side_re;
+    cudaStream_t s = ctx->stream;
+    // Work of the two routes, in operations per light curve: four pixels per sample (the Gaussian's
+    // column sums of two rows, 2 (T + 1) T, and four row sums, 4 T; the disc's four pixel totals) or
+    // the whole convolution (2 T per pixel for the Gaussian; 2 (2H + 1) span ends per pixel for the
+    // tiled disc, its pixel count for the untiled one).
+    int h = 0, H = 0;
+    long long taps = 0;
+    std::vector<float> g;
+    std::vector<int> span;
+    double local_ops, full_ops;
+    if (profile == MM_PROFILE_GAUSSIAN) {
+        g = gauss_taps(size_re, pix, &h);
+        const double T = 2.0 * h + 1.0;
+        local_ops = (double)n_points * (2.0 * (T + 1.0) * T + 4.0 * T);
+        full_ops = (double)npix * 2.0 * T;
+    } else {
+        span = disc_spans(size_re, pix, &H, &taps);
+        local_ops = (double)n_points * 4.0 * (double)taps;
+        full_ops = (double)npix * (H <= kDiscMaxH ? 2.0 * (2 * H + 1) : (double)taps);
+    }
     double *dmu = nullptr;
-    if ((rc = ctx->arena.alloc(2 * npix * sizeof(float), (void **)&buf))) return rc;
-    if ((rc = ctx->arena.alloc((size_t)n_points * sizeof(double), (void **)&dmu))) {
-        ctx->arena.free(buf);
+    if ((rc = ctx->arena.alloc((size_t)n_points * sizeof(double), (void **)&dmu))) return rc;
+    cudaError_t e = cudaSuccess;
+    const int grid = (int)std::min<long long>(n_points, 64LL * ctx->sms);
+    if (local_ops <= full_ops) {                           // a CTA per sample: its four pixels only
+        void *dw = nullptr;
+        const size_t wbytes = profile == MM_PROFILE_GAUSSIAN ? g.size() * sizeof(float) : span.size() * sizeof(int);
+        if ((rc = ctx->arena.alloc(wbytes, &dw))) {
+            ctx->arena.free(dmu);
+            return rc;
+        }
+        const void *src = profile == MM_PROFILE_GAUSSIAN ? (const void *)g.data() : (const void *)span.data();
+        e = cudaMemcpyAsync(dw, src, wbytes, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev0, s);
+        if (e == cudaSuccess) {
+            if (profile == MM_PROFILE_GAUSSIAN)
+                k_track_gauss<<<grid, 256, 0, s>>>(M->counts, n, (const float *)dw, h, (float)(1.0 / M->p.nrays_per_pix),
+                                                   half, pix, y1_start, y2_start, y1_end, y2_end, n_points, dmu);
+            else
+                k_track_disc<<<grid, 256, 0, s>>>(M->counts, n, (const int *)dw, H,
+                                                  (float)(1.0 / ((double)taps * M->p.nrays_per_pix)), half, pix, y1_start,
+                                                  y2_start, y1_end, y2_end, n_points, dmu);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev1, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(host_mu, dmu, (size_t)n_points * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) note_kernel_time(ctx, 1);
+        ctx->arena.free(dw);
+        ctx->arena.free(dmu);
+        return e == cudaSuccess ? MM_OK : cuda_fail(e, "light curve");
+    }
+    float *buf = nullptr;                                  // the whole convolved map, then samples of it
+    if ((rc = ctx->arena.alloc(2 * npix * sizeof(float), (void **)&buf))) {
+        ctx->arena.free(dmu);
         return rc;
     }
-    rc = convolve(ctx, *M, profile, size_re, buf, buf + npix, ctx->stream);
-    cudaError_t e = cudaSuccess;
+    rc = convolve(ctx, *M, profile, size_re, buf, buf + npix, s);
     if (!rc) {
-        const int grid = (int)std::min<long long>((n_points + 255) / 256, 1024);
-        k_track<<<grid, 256, 0, ctx->stream>>>(buf, M->p.npix_side, 0.5 * M->p.side_re, M->g.pix, y1_start, y2_start,
-                                                y1_end, y2_end, n_points, dmu);
+        k_track<<<(int)std::min<long long>((n_points + 255) / 256, 1024), 256, 0, s>>>(buf, n, half, pix, y1_start,
+                                                                                      y2_start, y1_end, y2_end,
+                                                                                      n_points, dmu);
         e = cudaGetLastError();
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(host_mu, dmu, (size_t)n_points * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+            e = cudaMemcpyAsync(host_mu, dmu, (size_t)n_points * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     }
     ctx->arena.free(buf);
     ctx->arena.free(dmu);

@@ -168,3 +168,77 @@ def test_disc_tiles_with_large_counts_use_64_bit_sums():
         assert np.nanmax(ref) > 100 * np.nanmedian(ref)     # the large pixels reach some outputs
     finally:
         mm.mm_destroy(c)
+
+
+# Light curves: a sample needs the convolved map at four pixels only, and when that is less work the
+# library convolves just those (one CTA per sample) instead of the whole map. Both routes must give
+# the pixels of mm_map_convolve bit for bit.
+
+def _centre_track(n, side, i0, j, steps):
+    """A track along pixel row j from the centre of pixel i0 to that of pixel i0 + steps. With a pixel
+    and a step count that are exact binary fractions, every sample lies exactly on a pixel centre, so
+    the bilinear weights are 0 and each sample is the convolved pixel itself."""
+    p = side / n
+    y = lambda i: -side / 2 + (i + 0.5) * p
+    return (y(i0), y(j)), (y(i0 + steps), y(j))
+
+
+@pytest.mark.parametrize("profile,size", [(mm.MM_PROFILE_GAUSSIAN, 0.05), (mm.MM_PROFILE_DISC, 0.12)])
+def test_lightcurve_on_pixel_centres_equals_the_convolved_map(shot, profile, size):
+    ctx, m, _ = shot
+    conv = mm.mm_map_convolve(ctx, m, profile, size)
+    i0, j, steps = 40, 100, 64
+    start, end = _centre_track(CFG["npix_side"], CFG["side"], i0, j, steps)
+    got = mm.mm_map_lightcurve(ctx, m, profile, size, start, end, steps + 1)
+    assert mm.mm_last_kernel_ms(ctx)[1] == 1            # the four-pixel route: one kernel
+    assert np.isfinite(got).all()
+    np.testing.assert_array_equal(got, conv[j, i0:i0 + steps + 1].astype(np.float64))
+
+
+@pytest.mark.parametrize("profile,size", [(mm.MM_PROFILE_GAUSSIAN, 0.7705078125), (mm.MM_PROFILE_DISC, 0.5039)])
+def test_lightcurve_of_wide_supports_on_pixel_centres(shot_wide, profile, size):
+    """Supports past the tiled kernels' limits (Gaussian half-width 132: 265 taps, more than one round
+    of the four-pixel kernel's column sums; disc radius 21 pixels)."""
+    ctx, m, _ = shot_wide
+    conv = mm.mm_map_convolve(ctx, m, profile, size)
+    i0, j, steps = 140, 160, 32
+    start, end = _centre_track(CFG_WIDE["npix_side"], CFG_WIDE["side"], i0, j, steps)
+    got = mm.mm_map_lightcurve(ctx, m, profile, size, start, end, steps + 1)
+    assert np.isfinite(got).all()
+    np.testing.assert_array_equal(got, conv[j, i0:i0 + steps + 1].astype(np.float64))
+
+
+@pytest.mark.parametrize("profile,size", [(mm.MM_PROFILE_GAUSSIAN, 0.015), (mm.MM_PROFILE_DISC, 0.08)])
+def test_lightcurve_routes_agree_and_match_oracle(profile, size):
+    """On a 64^2 map (Gaussian half-width 3; disc radius 3 pixels, 37 taps), 300 samples are less work
+    than the whole convolution and take the four-pixel route; 599 samples are more and take the
+    whole-map route. Sample 2k of the second track is sample k of the first (the same t in FP64), so
+    the two routes must agree bit for bit there; both match the oracle, NaN where the support leaves
+    the map."""
+    mm.build()
+    c = mm.mm_init(0)
+    try:
+        cfg = dict(CFG, npix_side=64, side=1.5)
+        n, r = field.nstar_rule(cfg["sigma"], cfg["gamma"], cfg["smooth_frac"], cfg["side"])
+        f = synth.lens_field(n, r, 53)
+        lh = mm.mm_create_lenses_from(c, f.x, f.y, f.m)
+        m = mm.mm_shoot(c, lh, mm.params(**cfg))
+        counts, _ = mm.mm_map_fetch(c, m)
+        start, end = (-0.7, -0.6), (0.65, 0.7)
+        few = mm.mm_map_lightcurve(c, m, profile, size, start, end, 300)
+        few_launches = mm.mm_last_kernel_ms(c)[1]
+        many = mm.mm_map_lightcurve(c, m, profile, size, start, end, 599)
+        many_launches = mm.mm_last_kernel_ms(c)[1]
+        if profile == mm.MM_PROFILE_GAUSSIAN:               # one kernel, or the two convolution passes
+            assert (few_launches, many_launches) == (1, 2)
+        np.testing.assert_array_equal(few, many[::2])
+        pix = cfg["side"] / cfg["npix_side"]
+        field_ref = oext.convolve(counts, cfg["nrays"], profile, size, pix)
+        for got, npts in ((few, 300), (many, 599)):
+            ref = oext.lightcurve(field_ref, cfg["side"], start, end, npts)
+            np.testing.assert_array_equal(np.isnan(got), np.isnan(ref))
+            ok = ~np.isnan(ref)
+            assert 0.5 * npts < ok.sum() < npts
+            np.testing.assert_allclose(got[ok], ref[ok], rtol=2e-5, atol=1e-6)
+    finally:
+        mm.mm_destroy(c)
