@@ -388,6 +388,8 @@ __device__ __forceinline__ void disc_store(const A (&acc)[kDiscPer], float *out,
 // The common way (32-bit prefix rows and sums), compiled for each radius: the tap rows and the 16
 // outputs unrolled, so that every load is an immediate offset from base (the thread's column on its
 // first staged row) plus the tap row's span end, which is the same for every thread of the launch.
+// Tap rows k and 2H - k have the same span, so the two span ends loaded on staged row r serve output
+// r - k and output r - (2H - k) alike: 27 instead of 34 loads per output at H = 8.
 template <int H>
 __device__ __forceinline__ void disc_outputs32(const unsigned *base, const DiscSpans &sp, float *out, int n, int r0,
                                                int c0, float scale)
@@ -397,10 +399,17 @@ __device__ __forceinline__ void disc_outputs32(const unsigned *base, const DiscS
 #pragma unroll
     for (int u = 0; u < kDiscPer; ++u) acc[u] = 0u;
 #pragma unroll
-    for (int k = 0; k <= 2 * H; ++k) {
-        const unsigned *const hi = base + k * P + sp.w[k] + 1, *const lo = base + k * P - sp.w[k];
+    for (int k = 0; k <= H; ++k) {
+        const int km = 2 * H - k;                          // the mirrored tap row
+        const unsigned *const hi = base + sp.w[k] + 1, *const lo = base - sp.w[k];
 #pragma unroll
-        for (int u = 0; u < kDiscPer; ++u) acc[u] += hi[u * P] - lo[u * P];
+        for (int r = k; r < kDiscPer + km; ++r) {          // staged rows of output r - k or r - km
+            const bool first = r - k < kDiscPer, second = km != k && r - km >= 0;
+            if (!first && !second) continue;
+            const unsigned span = hi[r * P] - lo[r * P];
+            if (first) acc[r - k] += span;
+            if (second) acc[r - km] += span;
+        }
     }
     disc_store<unsigned>(acc, out, n, r0, c0, H, scale);
 }
