@@ -317,7 +317,8 @@ __device__ __forceinline__ void disc_scan(const unsigned *raw, unsigned *pre, un
     constexpr int RT = disc_rows(H), CW = disc_cols(H), P = disc_pitch(H);
     static_assert(CW <= 96, "three columns per lane");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int rr = warp; rr < RT; rr += 8) {
+#pragma unroll
+    for (int rr = warp; rr < RT; rr += 8) {                // unrolled: the rows' shuffle scans overlap
         const unsigned *const r = raw + rr * CW;
         unsigned *const p = pre + rr * P;
         const int x = 3 * lane;
