@@ -74,7 +74,8 @@ constexpr int kDiscTileW = 64, kDiscTileH = 64;        // disc: 64 x 64 outputs 
 constexpr int kDiscPer = 16;                           // outputs per thread, down its column (4 row groups)
 constexpr int kDiscMaxH = 15;                          // widest radius (pixels) of the tiled disc kernel; wider
                                                        // supports take the untiled kernel
-constexpr size_t kGaussSmemMax = 200 * 1024;           // a double-buffered Gaussian CTA (h <= 131; wider
+constexpr int kGaussMaxTiledH = 131;                   // widest Gaussian half-width of the tiled passes
+constexpr size_t kGaussSmemMax = 200 * 1024;           // the Gaussian CTA's shared-memory limit (wider
                                                        // supports take the untiled kernel)
 
 // Gaussian passes (tiled): one kernel, k_gauss_vt, convolves its input down the columns and writes
@@ -86,9 +87,9 @@ constexpr size_t kGaussSmemMax = 200 * 1024;           // a double-buffered Gaus
 // packed FMAs from them. The taps are padded with zero weights to TP, a multiple of 8; a padded tap
 // leaves a sum unchanged (0 times a finite input is 0, and every sum is non-negative) or meets only
 // an input column that is NaN throughout, whose outputs are NaN anyway. Every output adds its taps
-// in order (a correctly rounded FMA each, tap 0 first), exactly as k_gauss_pass. A CTA holds two
-// tiles: while it computes one, the next one's inputs arrive by cp.async (16-byte copies when
-// N_side is a multiple of 4, 4-byte copies otherwise).
+// in order (a correctly rounded FMA each, tap 0 first), exactly as k_gauss_pass. A CTA holds one
+// tile, copied in by cp.async (16-byte copies when N_side is a multiple of 4, 4-byte copies
+// otherwise); three CTAs per SM hide each other's copies (faster than two double-buffered CTAs).
 constexpr int kGOut = 128;                              // outputs per tile down the columns (8 warps x 16)
 constexpr int kGPairs = 32;                             // pairs of columns per tile (64 columns), one per lane
 
@@ -98,7 +99,7 @@ __host__ __device__ inline int gauss_span(int h) { return kGOut + gauss_taps_pad
 __host__ __device__ inline size_t gauss_tile_floats(int h) { return (size_t)2 * kGPairs * gauss_span(h); }
 __host__ __device__ inline size_t gauss_smem(int h)
 {
-    return ((size_t)2 * gauss_taps_padded(h) + 2 * gauss_tile_floats(h)) * 4;
+    return ((size_t)2 * gauss_taps_padded(h) + gauss_tile_floats(h)) * 4;
 }
 // Disc tile of radius H: rows [r0 - H, r0 + 64 + H) x columns [c0 - H4, c0 + 64 + H4) of the counts,
 // H4 = H rounded up to a multiple of 4 (so that a staged row starts on a 16-byte boundary when N_side
@@ -158,13 +159,13 @@ __device__ __forceinline__ void gauss_taps2(const float2 *gs2, int tp, const flo
 // r0 + 16 w .. + 16. Tiles t, t + gridDim.x, ...; each thread copies the same elements of every tile
 // and, from counts (mu = N inv_nrays), converts those it copied once they have landed.
 template <bool FROM_COUNTS>
-__global__ void __launch_bounds__(256, 1) k_gauss_vt(const void *in, float *out_t, int n, const float *g, int h,
+__global__ void __launch_bounds__(256, 3) k_gauss_vt(const void *in, float *out_t, int n, const float *g, int h,
                                                      float inv_nrays)
 {
     extern __shared__ float4 sm4[];
     const int tp = gauss_taps_padded(h), S = gauss_span(h);
     float2 *const gs2 = reinterpret_cast<float2 *>(sm4);
-    float *const buf0 = reinterpret_cast<float *>(gs2 + tp), *const buf1 = buf0 + gauss_tile_floats(h);
+    float *const tile = reinterpret_cast<float *>(gs2 + tp);
     for (int k = threadIdx.x; k < tp; k += blockDim.x) {       // taps as pairs, zero up to TP
         const float v = k <= 2 * h ? g[k] : 0.f;
         gs2[k] = make_float2(v, v);
@@ -174,34 +175,26 @@ __global__ void __launch_bounds__(256, 1) k_gauss_vt(const void *in, float *out_
     const long long tiles = (long long)cols * rows;
     const bool vec = (n & 3) == 0;                             // rows start on 16-byte boundaries
     const unsigned *const src_u = static_cast<const unsigned *>(in);
-    auto stage = [&](long long t, float *tile) {
+    auto stage = [&](long long t, float *dst) {
         const int c0 = (int)(t % cols) * (2 * kGPairs), r0 = (int)(t / cols) * kGOut;
         if (vec) {
             for (int q = threadIdx.x; q < S * 16; q += blockDim.x) {   // row q / 16, columns 4 (q % 16) ..
                 const int j = r0 - h + (q >> 4), i = c0 + 4 * (q & 15);
                 const int cnt = (j >= 0 && j < n) ? max(0, min(4, n - i)) : 0;
-                cp_async16(tile + 4 * q, src_u + (cnt ? (long long)j * n + i : 0), 4u * cnt);
+                cp_async16(dst + 4 * q, src_u + (cnt ? (long long)j * n + i : 0), 4u * cnt);
             }
         } else {
             for (int q = threadIdx.x; q < S * 64; q += blockDim.x) {   // row q / 64, column q % 64
                 const int j = r0 - h + (q >> 6), i = c0 + (q & 63);
                 const bool ok = j >= 0 && j < n && i < n;
-                cp_async4(tile + q, src_u + (ok ? (long long)j * n + i : 0), ok ? 4u : 0u);
+                cp_async4(dst + q, src_u + (ok ? (long long)j * n + i : 0), ok ? 4u : 0u);
             }
         }
         cp_async_commit();
     };
-    if (blockIdx.x < tiles) stage(blockIdx.x, buf0);
-    int b = 0;
-    for (long long t = blockIdx.x; t < tiles; t += gridDim.x, b ^= 1) {
-        float *const tile = b ? buf1 : buf0;
-        const long long tn = t + gridDim.x;
-        if (tn < tiles) {                                      // the other buffer was released at the end
-            stage(tn, b ? buf0 : buf1);                        // of the previous tile
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
+    for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+        stage(t, tile);                                        // the previous tile was released below
+        cp_async_wait<0>();
         if (FROM_COUNTS) {                                     // the elements this thread copied, now landed
             if (vec) {
                 for (int q = threadIdx.x; q < S * 16; q += blockDim.x) {
@@ -738,7 +731,7 @@ int convolve(mm_ctx *ctx, const MapObj &M, int profile, double size_re, float *d
                 if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem) != cudaSuccess) per_sm = 1;
                 return (int)std::max(1LL, std::min(tiles, (long long)std::max(1, per_sm) * ctx->sms));
             };
-            if (smem <= kGaussSmemMax) {
+            if (h <= kGaussMaxTiledH) {
                 const void *f1 = (const void *)k_gauss_vt<true>, *f2 = (const void *)k_gauss_vt<false>;
                 if ((e = cudaFuncSetAttribute(f1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGaussSmemMax)) ==
                         cudaSuccess &&
