@@ -1,7 +1,11 @@
-"""Extended-source maps and light curves on the device (Sect. 1) against the oracle."""
+"""Extended-source maps and light curves on the device (Sect. 1) against the oracle. The maps they
+start from are the oracle's own maps of seeded lens fields (or seeded synthetic counts), put on the
+device by mm_map_restore, so the device and the oracle convolve the same counts and none of the
+oracle's input comes from the device."""
 import numpy as np
 import pytest
 
+import oracle
 import paper_1005_5198_gb300 as mm
 import synth
 from oracle import extended as oext
@@ -12,15 +16,25 @@ pytestmark = pytest.mark.gpu
 CFG = dict(sigma=0.45, gamma=0.2, smooth_frac=0.3, side=6.0, npix_side=256, nrays=64.0)
 
 
+def oracle_map_on_device(ctx, cfg, seed):
+    """The oracle's map (FP64, Sect. 2) of a seeded lens field drawn by the rules of Sect. 2 for cfg,
+    put on the device by mm_map_restore. Returns the device map and the oracle's counts."""
+    n, r = field.nstar_rule(cfg["sigma"], cfg["gamma"], cfg["smooth_frac"], cfg["side"])
+    f = synth.lens_field(n, r, seed)
+    counts, tot = oracle.shoot_map(dict(cfg, margin=1.5), f)
+    lh = mm.mm_create_lenses_from(ctx, f.x, f.y, f.m)
+    p = mm.params(**cfg)
+    g = mm.mm_geometry_of(p)
+    st = dict(rays_shot=tot["shot"], rays_in=tot["inside"], rays_out=tot["out"], interactions=0, nx=g["nx"],
+              ny=g["ny"], nstar=n, seconds=0.0, mu_mean=0.0, lens_splits=1, far_bound=0.0, far_block=0)
+    return mm.mm_map_restore(ctx, lh, p, counts, st), counts
+
+
 @pytest.fixture(scope="module")
 def shot():
     mm.build()
     c = mm.mm_init(0)
-    n, r = field.nstar_rule(CFG["sigma"], CFG["gamma"], CFG["smooth_frac"], CFG["side"])
-    f = synth.lens_field(n, r, 41)
-    lh = mm.mm_create_lenses_from(c, f.x, f.y, f.m)
-    m = mm.mm_shoot(c, lh, mm.params(**CFG))
-    counts, _ = mm.mm_map_fetch(c, m)
+    m, counts = oracle_map_on_device(c, CFG, 41)
     yield c, m, counts
     mm.mm_destroy(c)
 
@@ -45,11 +59,7 @@ def test_convolution_of_sides_not_multiple_of_4(nside):
     c = mm.mm_init(0)
     try:
         cfg = dict(CFG, npix_side=nside, side=6.0 * nside / 256)
-        n, r = field.nstar_rule(cfg["sigma"], cfg["gamma"], cfg["smooth_frac"], cfg["side"])
-        f = synth.lens_field(n, r, 47)
-        lh = mm.mm_create_lenses_from(c, f.x, f.y, f.m)
-        m = mm.mm_shoot(c, lh, mm.params(**cfg))
-        counts, _ = mm.mm_map_fetch(c, m)
+        m, counts = oracle_map_on_device(c, cfg, 47)
         for profile, size in ((mm.MM_PROFILE_GAUSSIAN, 0.05), (mm.MM_PROFILE_DISC, 0.12)):
             got = mm.mm_map_convolve(c, m, profile, size)
             ref = oext.convolve(counts, cfg["nrays"], profile, size, cfg["side"] / nside)
@@ -109,11 +119,7 @@ CFG_WIDE = dict(CFG, npix_side=320, side=7.5)            # pixel 0.0234375 R_E
 def shot_wide():
     mm.build()
     c = mm.mm_init(0)
-    n, r = field.nstar_rule(CFG_WIDE["sigma"], CFG_WIDE["gamma"], CFG_WIDE["smooth_frac"], CFG_WIDE["side"])
-    f = synth.lens_field(n, r, 43)
-    lh = mm.mm_create_lenses_from(c, f.x, f.y, f.m)
-    m = mm.mm_shoot(c, lh, mm.params(**CFG_WIDE))
-    counts, _ = mm.mm_map_fetch(c, m)
+    m, counts = oracle_map_on_device(c, CFG_WIDE, 43)
     yield c, m, counts
     mm.mm_destroy(c)
 
@@ -219,11 +225,7 @@ def test_lightcurve_routes_agree_and_match_oracle(profile, size):
     c = mm.mm_init(0)
     try:
         cfg = dict(CFG, npix_side=64, side=1.5)
-        n, r = field.nstar_rule(cfg["sigma"], cfg["gamma"], cfg["smooth_frac"], cfg["side"])
-        f = synth.lens_field(n, r, 53)
-        lh = mm.mm_create_lenses_from(c, f.x, f.y, f.m)
-        m = mm.mm_shoot(c, lh, mm.params(**cfg))
-        counts, _ = mm.mm_map_fetch(c, m)
+        m, counts = oracle_map_on_device(c, cfg, 53)
         start, end = (-0.7, -0.6), (0.65, 0.7)
         few = mm.mm_map_lightcurve(c, m, profile, size, start, end, 300)
         few_launches = mm.mm_last_kernel_ms(c)[1]
