@@ -83,8 +83,9 @@ constexpr size_t kGaussSmemMax = 200 * 1024;           // the Gaussian CTA's sha
 // row pass of V in the map's own orientation. The two lanes of every packed f32x2 FMA are the same
 // output of two neighbouring columns, so one 8-byte shared load gives an operand pair and the taps
 // are pairs (g, g). A thread owns 16 consecutive outputs down its pair of columns and runs the taps
-// in chunks of 8: per chunk it loads the 23 input pairs the 16 outputs need once and makes 128
-// packed FMAs from them. The taps are padded with zero weights to TP, a multiple of 8; a padded tap
+// in chunks of 8 (the last one of 4 when TP is not a multiple of 8): per chunk of 8 it loads the 23
+// input pairs the 16 outputs need once and makes 128 packed FMAs from them. The taps are padded with
+// zero weights to TP, a multiple of 4; a padded tap
 // leaves a sum unchanged (0 times a finite input is 0, and every sum is non-negative) or meets only
 // an input column that is NaN throughout, whose outputs are NaN anyway. Every output adds its taps
 // in order (a correctly rounded FMA each, tap 0 first), exactly as k_gauss_pass. A CTA holds one
@@ -93,7 +94,7 @@ constexpr size_t kGaussSmemMax = 200 * 1024;           // the Gaussian CTA's sha
 constexpr int kGOut = 128;                              // outputs per tile down the columns (8 warps x 16)
 constexpr int kGPairs = 32;                             // pairs of columns per tile (64 columns), one per lane
 
-__host__ __device__ inline int gauss_taps_padded(int h) { return (2 * h + 1 + 7) & ~7; }
+__host__ __device__ inline int gauss_taps_padded(int h) { return (2 * h + 1 + 3) & ~3; }
 // input rows staged per tile: 128 + TP - 1
 __host__ __device__ inline int gauss_span(int h) { return kGOut + gauss_taps_padded(h) - 1; }
 __host__ __device__ inline size_t gauss_tile_floats(int h) { return (size_t)2 * kGPairs * gauss_span(h); }
@@ -140,12 +141,24 @@ __device__ __forceinline__ void gauss_taps2(const float2 *gs2, int tp, const flo
 {
 #pragma unroll
     for (int u = 0; u < 16; ++u) acc[u] = make_float2(0.f, 0.f);
-    for (int k0 = 0; k0 < tp; k0 += 8) {
+    int k0 = 0;
+    for (; k0 + 8 <= tp; k0 += 8) {
         float2 v[23];
 #pragma unroll
         for (int q = 0; q < 23; ++q) v[q] = x[(k0 + q) * st];
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) {
+            const float2 w = gs2[k0 + kk];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) acc[u] = __ffma2_rn(w, v[u + kk], acc[u]);
+        }
+    }
+    if (k0 < tp) {                                            // the last 4 taps
+        float2 v[19];
+#pragma unroll
+        for (int q = 0; q < 19; ++q) v[q] = x[(k0 + q) * st];
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
             const float2 w = gs2[k0 + kk];
 #pragma unroll
             for (int u = 0; u < 16; ++u) acc[u] = __ffma2_rn(w, v[u + kk], acc[u]);
