@@ -572,18 +572,27 @@ __global__ void k_track(const float *f, int n, double half_side, double pix, dou
 // map gives, bit for bit.
 
 constexpr int kLcChunk = 256;                           // column sums per row and round (Gaussian)
+constexpr int kLcTaps = 2048;                           // taps held in shared memory (wider Gaussians read
+                                                        // them from global memory)
 
 // Gaussian: for rows j and j + 1 the column sums V[r][x] = sum_k g[k] mu[j + r + k - h][x] (FMA chain in
 // tap order, as the column pass) over the columns the row sums need, in rounds of kLcChunk + 1
 // columns; then thread o < 4 extends the row sum of pixel (i + (o & 1), j + (o >> 1)) over the round's
-// taps (FMA chain in tap order, as the row pass). A pixel whose support leaves the map is NaN.
+// taps (FMA chain in tap order, as the row pass). The taps sit in shared memory and the chains are
+// unrolled, so that their loads are issued ahead of the FMAs. A pixel whose support leaves the map is
+// NaN.
 __global__ void __launch_bounds__(256) k_track_gauss(const unsigned *cin, int n, const float *g, int h, float inv_nrays,
                                                      double half_side, double pix, double y1a, double y2a, double y1b,
                                                      double y2b, long long npts, double *mu)
 {
     __shared__ float V[2][kLcChunk + 1];
+    __shared__ float gsh[kLcTaps];
     __shared__ float f[4];
     const int T = 2 * h + 1, o = threadIdx.x;
+    if (T <= kLcTaps)
+        for (int k = o; k < T; k += blockDim.x) gsh[k] = g[k];
+    __syncthreads();
+    const float *const gt = T <= kLcTaps ? gsh : g;
     for (long long k = blockIdx.x; k < npts; k += gridDim.x) {
         int i, j;
         double a, b;
@@ -601,15 +610,16 @@ __global__ void __launch_bounds__(256) k_track_gauss(const unsigned *cin, int n,
                 float v = 0.f;
                 if (c0 + t <= T && x >= 0 && x < n && row - h >= 0 && row + h < n) {
                     const unsigned *col = cin + (long long)(row - h) * n + x;
-#pragma unroll 8
-                    for (int kk = 0; kk < T; ++kk) v = fmaf(g[kk], __fmul_rn((float)col[(long long)kk * n], inv_nrays), v);
+#pragma unroll 16
+                    for (int kk = 0; kk < T; ++kk) v = fmaf(gt[kk], __fmul_rn((float)col[(long long)kk * n], inv_nrays), v);
                 }
                 V[r][t] = v;
             }
             __syncthreads();
             if (valid) {
                 const int end = min(T, c0 + kLcChunk);
-                for (int kk = c0; kk < end; ++kk) s = fmaf(g[kk], V[o >> 1][(o & 1) + kk - c0], s);
+#pragma unroll 16
+                for (int kk = c0; kk < end; ++kk) s = fmaf(gt[kk], V[o >> 1][(o & 1) + kk - c0], s);
             }
             __syncthreads();
         }
