@@ -578,9 +578,9 @@ constexpr int kLcTaps = 2048;                           // taps held in shared m
 // Gaussian: for rows j and j + 1 the column sums V[r][x] = sum_k g[k] mu[j + r + k - h][x] (FMA chain in
 // tap order, as the column pass) over the columns the row sums need, in rounds of kLcChunk + 1
 // columns; then thread o < 4 extends the row sum of pixel (i + (o & 1), j + (o >> 1)) over the round's
-// taps (FMA chain in tap order, as the row pass). The taps sit in shared memory and the chains are
-// unrolled, so that their loads are issued ahead of the FMAs. A pixel whose support leaves the map is
-// NaN.
+// taps (FMA chain in tap order, as the row pass). The taps sit in shared memory (up to kLcTaps of
+// them) and the chains are unrolled, so that their loads are issued ahead of the FMAs. A pixel whose
+// support leaves the map is NaN.
 __global__ void __launch_bounds__(256) k_track_gauss(const unsigned *cin, int n, const float *g, int h, float inv_nrays,
                                                      double half_side, double pix, double y1a, double y2a, double y1b,
                                                      double y2b, long long npts, double *mu)
